@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Golub-Kahan partial SVD (arXiv 2104.10785).
+
+Metric: converged top-k singular triplets per second at <= 1e-8 relative residual.
+Default workload: dense 100000 x 40000 operator stored in bf16, A = U diag(i^-1.5) V^T
+with seeded orthonormal factors, top-100 triplets, Krylov dimension 200, tol 1e-8.
+One step = one full gk_psvd call (start vector, bidiagonalization sweeps with
+reorthogonalization, small SVDs, restarts, Ritz vectors) on inputs resident in HBM.
+The same solve on the f32-stored copy (the plain path) is timed beside it, and the
+end-to-end figure times the C-ABI call on pinned host buffers (host-to-device copy of
+the operator and device-to-host copy of U, S, V inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gk|reference] [--workload NAME]
+
+With N > 1 (torchrun) every rank solves its own replica (the method has no exchange
+step at this size); value = triplets of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.lines = []
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": float(np.median(power)) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def make_workload(name, device, want_plain=True):
+    import torch
+
+    import synth
+
+    w = dict(synth.WORKLOADS[name])
+    w["name"] = name
+    t0 = time.time()
+    if w["kind"] == "spectrum_pow":
+        sig = synth.sigma_power(w["n"], w["e"])
+        A32, Ut, Vt = synth.torch_prescribed_spectrum(w["m"], w["n"], sig, w["seed"], device=device, keep_top=w["k"])
+        w["sigma_true"] = sig[: w["k"]]
+        w["A"] = A32.to(torch.bfloat16)
+        w["A_plain"] = A32 if want_plain else None
+        if not want_plain:
+            del A32
+    elif w["kind"] == "spectrum":
+        sig = synth.sigma_geometric(w["n"], w["q"])
+        A, U0, V0 = synth.prescribed_spectrum(w["m"], w["n"], sig, w["seed"])
+        w["sigma_true"] = sig[: w["k"]]
+        w["A"] = torch.from_numpy(A).to(device)
+        w["A_plain"] = None
+    elif w["kind"] == "product":
+        w["A"] = synth.torch_gaussian_product(w["m"], w["n"], w["r"], w["noise"], w["seed"], device=device)
+        w["A_plain"] = None
+    else:
+        raise SystemExit(f"workload {name} is not benchmarked by this script")
+    torch.cuda.synchronize()
+    w["gen_seconds"] = time.time() - t0
+    return w
+
+
+def algorithmic_bytes(w, which):
+    """Bytes one launch of the product kernel must move: the stored operator once,
+    the f32 input vector, the f64 output and the f64 vector it subtracts."""
+    m, n = w["m"], w["n"]
+    es = w["A"].element_size()
+    if which == "matvec":
+        return es * m * n + 4 * n + 8 * m + 8 * m
+    return es * m * n + 4 * m + 8 * n + 8 * n
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle samples
+# ---------------------------------------------------------------------------
+def oracle_operator(w):
+    import torch
+
+    import oracle
+
+    A = w["A"]
+    if A.dtype == torch.bfloat16:
+        bits = A.view(torch.int16).cpu().numpy().view(np.uint16)
+        return oracle.Operator.dense(None, dtype="bf16", bits=bits)
+    return oracle.Operator.dense(A.cpu().numpy())
+
+
+def oracle_step_seconds(op, w, steps, q1):
+    """Seconds per bidiagonalization step (A v, A^T u, two Gram-Schmidt passes) of the oracle on
+    the full operator, from the first `steps` steps of its upper-bidiagonal process."""
+    import oracle
+
+    t = time.perf_counter()
+    oracle.gk_upper(op, steps, q1)
+    return (time.perf_counter() - t) / steps
+
+
+def oracle_reduced_steps(w):
+    """Steps the oracle's own complete solve needs on a reduced instance of the same recipe
+    (m, n / 10; same spectrum law, k, K, tol)."""
+    import oracle
+    import synth
+
+    m, n = w["m"] // 10, w["n"] // 10
+    if w["kind"] == "spectrum_pow":
+        sig = synth.sigma_power(n, w["e"])
+    else:
+        sig = synth.sigma_geometric(n, w.get("q", 0.9))
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, w["seed"], dtype=np.float32)
+    if w["dtype"] == "bf16":
+        op = oracle.Operator.dense(None, dtype="bf16", bits=synth.to_bf16_bits(A))
+    else:
+        op = oracle.Operator.dense(A)
+    k, K = w["k"], w["K"]
+    t = time.perf_counter()
+    _, _, _, info = oracle.psvd(op, k, K, synth.start_vector(m, 1), tol=w["tol"], max_restarts=400)
+    return info["matvecs"] / 2.0, time.perf_counter() - t, (m, n)
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on the host cores: each step is a bounded sample
+    (the oracle's bidiagonalization steps on the full operator), scaled by the number
+    of steps the oracle's own solve of a reduced instance needed."""
+    import torch
+
+    import oracle
+    import synth
+
+    if rank != 0:
+        return None
+    device = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    if device is None:
+        return {"impl": "reference", "unavailable": "the synthetic operator is generated on the GPU and no GPU is visible"}
+    w = make_workload(args.workload, device, want_plain=False)
+    op = oracle_operator(w)
+    del w["A"]
+    torch.cuda.empty_cache()
+    cores = cpu_threads()
+    oracle.set_threads(cores)
+    steps_needed, t_red, red_shape = oracle_reduced_steps(w)
+    q1 = synth.start_vector(w["m"], w["seed"])
+    sample_steps = 2
+    for _ in range(args.warmup):
+        oracle_step_seconds(op, w, sample_steps, q1)
+    per = []
+    for _ in range(args.steps):
+        per.append(oracle_step_seconds(op, w, sample_steps, q1))
+    t_step = float(np.mean(per))
+    value = w["k"] / (t_step * steps_needed)
+    sample = (f"{sample_steps} oracle bidiagonalization steps on the full {w['m']}x{w['n']} {w['dtype']} operator "
+              f"per step ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps the oracle's complete solve "
+              f"of the {red_shape[0]}x{red_shape[1]} instance of the same recipe needed")
+    return {
+        "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
+        "value": value, "unit": "triplets/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * steps_needed * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": w["k"], "krylov_dim": w["K"],
+                   "tol": w["tol"], "storage": w["dtype"]},
+        "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_gk(args, rank, world):
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+    import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    gk.lib()
+    w = make_workload(args.workload, device, want_plain=not args.no_plain)
+    k, K, tol = w["k"], w["K"], w["tol"]
+    A = w["A"]
+    stream = torch.cuda.current_stream(device)
+    kw = dict(krylov_dim=K, seed=w["seed"])
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        U, S, V, st, info = gk.gk_psvd(A, k, tol, **kw)
+    torch.cuda.synchronize()
+
+    # timed region: inputs resident in HBM (8 GB operator > 129 MB L2)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos, statuses = [], []
+    for _ in range(args.steps):
+        U, S, V, st, info = gk.gk_psvd(A, k, tol, profile=True, **kw)
+        infos.append(info)
+        statuses.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = k * args.steps * world / (ms / 1e3)
+
+    # accuracy of the returned triplets on the stored operator (GPU residual kernels)
+    r_av, r_atu = gk.gk_residuals(A, U, S, V)
+    s1 = float(S[0])
+    resid_rel = float(torch.maximum(r_av, r_atu).max()) / s1
+    sig_err = float(np.max(np.abs(S.cpu().numpy() - w["sigma_true"]) / w["sigma_true"])) if "sigma_true" in w else None
+
+    # dominant kernel roofline from the CUDA events recorded around each product launch
+    tot = {key: sum(i[key] for i in infos) for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "ms_small",
+                                                        "ms_restart", "n_matvec", "n_matvec_t")}
+    hbm, peak_kind = peaks()
+    which = "matvec" if tot["ms_matvec"] >= tot["ms_matvec_t"] else "matvec_t"
+    nl = tot["n_" + which]
+    avg_ms = tot["ms_" + which] / max(1, nl)
+    bpl = algorithmic_bytes(w, which)
+    achieved = bpl / (avg_ms / 1e3) / 1e9
+    other = "matvec_t" if which == "matvec" else "matvec"
+    avg_other = tot["ms_" + other] / max(1, tot["n_" + other])
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": args.traffic, "kernel": "k_gemv_lp" if which == "matvec" else "k_gemvt_lp+k_gemvt_reduce",
+            "bytes_per_launch": bpl, "avg_launch_ms": avg_ms, "launches": nl, "peak_source": peak_kind,
+            "other_product_GBs": algorithmic_bytes(w, other) / (avg_other / 1e3) / 1e9 if avg_other > 0 else None}
+    step_ms = ms / args.steps
+    breakdown = {key: tot[key] / args.steps for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "ms_small",
+                                                          "ms_restart")}
+
+    # plain path: the same solve on the f32-stored copy
+    plain = None
+    if w.get("A_plain") is not None and not args.no_plain:
+        Ap = w["A_plain"]
+        gk.gk_psvd(Ap, k, tol, **kw)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = max(1, min(args.steps, 3))
+        for _ in range(reps):
+            Up, Sp, Vp, stp, infop = gk.gk_psvd(Ap, k, tol, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / reps
+        ra, rb = gk.gk_residuals(Ap, Up, Sp, Vp)
+        plain = {"value": k / (pms / 1e3), "unit": "triplets/s", "ms_per_step": pms, "storage": "f32",
+                 "status": stp, "matvecs": infop["matvecs"], "restarts": infop["restarts"],
+                 "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sp[0]),
+                 "bf16_speedup": (k / (step_ms / 1e3)) / (k / (pms / 1e3))}
+        del Ap, w["A_plain"]
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+        Ah.copy_(A)
+        outs = (torch.empty((k, w["m"]), dtype=torch.float64, pin_memory=True),
+                torch.empty(k, dtype=torch.float64, pin_memory=True),
+                torch.empty((k, w["n"]), dtype=torch.float64, pin_memory=True))
+        gk.gk_psvd(Ah, k, tol, out=outs, **kw)
+        barrier()
+        reps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            Uh, Sh, Vh, sth, infoh = gk.gk_psvd(Ah, k, tol, out=outs, **kw)
+            float(Sh[0])  # the result is read on the host
+        te = (time.perf_counter() - t0) / reps
+        if dist:
+            t = torch.tensor([te], device=device)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": k * world / te, "unit": "triplets/s",
+               "h2d_bytes_per_step": int(Ah.numel() * Ah.element_size()),
+               "d2h_bytes_per_step": int(8 * k * (w["m"] + w["n"] + 1)), "ms_per_step": te * 1e3}
+        del Ah
+
+    # CPU oracle sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        op = oracle_operator(w)
+        cores = cpu_threads()
+        oracle.set_threads(cores)
+        q1 = synth.start_vector(w["m"], w["seed"])
+        sample_steps = args.cpu_steps
+        t_step = oracle_step_seconds(op, w, sample_steps, q1)
+        steps_needed = infos[-1]["matvecs"] / 2.0
+        cpu = {"value": k / (t_step * steps_needed), "unit": "triplets/s", "cores": cores, "kind": "oracle",
+               "sample": (f"{sample_steps} oracle bidiagonalization steps on the same {w['m']}x{w['n']} "
+                          f"{w['dtype']} operator ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps "
+                          f"the solve needed")}
+
+    last = infos[-1]
+    out = {
+        "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
+        "value": value, "unit": "triplets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if A.dtype == torch.bfloat16 else ("f64" if A.dtype == torch.float64 else "f32"),
+        "data": "synthetic",
+        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": K, "tol": tol,
+                   "storage": w["dtype"], "accumulate": "f32 runs combined in f64; f64 basis, small SVD, residuals",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (operator %.1f GB)" % (A.numel() * A.element_size() / 1e9)},
+        "status": statuses[-1], "resid_max_rel": resid_rel, "sigma_rel_err_vs_prescribed": sig_err,
+        "restarts": last["restarts"], "matvecs": last["matvecs"], "steps_per_solve": last["steps"],
+        "breakdown_ms_per_step": breakdown,
+        "roofline": roof, "clocks": clk, "gpu_launches": None,
+        "e2e": e2e, "cpu_baseline": cpu, "plain_f32": plain, "gen_seconds": w["gen_seconds"],
+    }
+    out["gpu_launches"] = int(sum(i["launches"] for i in infos))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
+    ap.add_argument("--workload", default="dense_bf16_100000x40000_top100")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture of this kernel")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and args.impl == "gk":
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_gk(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1 and args.impl == "gk":
+        import torch.distributed as tdist
+
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * gk.h -- C ABI of the GB300 Golub-Kahan partial-SVD / numerical-rank library
+ * (libgk.so).  Method: "Accurate and fast matrix factorization for low-rank
+ * learning", arXiv 2104.10785.
+ *
+ * Conventions shared by every entry point
+ *  - All matrices are read-only and caller-owned.  Dense operators are
+ *    row-major with leading dimension ld (elements between consecutive rows).
+ *    Vectors and output factors are column-major (each vector contiguous).
+ *  - Pointers may be device pointers or host pointers (pageable or pinned):
+ *    the library detects host memory with cudaPointerGetAttributes, copies
+ *    host inputs to its device workspace before computing and copies results
+ *    back to host outputs before returning.
+ *  - Calls are synchronous: they return after the result is final, because the
+ *    method's control flow (break test, convergence test) depends on device
+ *    results.  Work is issued on opts->stream (0 = the legacy default stream).
+ *  - Every call returns a gk_status; nothing aborts or throws across the ABI.
+ *  - The library never falls back to host computation: without a usable CUDA
+ *    device every call returns GK_NO_DEVICE.
+ *  - Workspace: if opts->workspace is NULL the library allocates its device
+ *    workspace with cudaMallocAsync on the call's stream and frees it before
+ *    returning.  Otherwise opts->workspace must point to at least
+ *    gk_*_workspace() bytes of device memory, 256-byte aligned.
+ *  - Calls on different streams with different workspaces may run
+ *    concurrently; two calls sharing one workspace must not overlap.
+ */
+#ifndef GK_H
+#define GK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GK_OK = 0,
+  GK_NOT_CONVERGED = 1,    /* restart budget spent; outputs hold the best Ritz triplets */
+  GK_RANK_DEFICIENT = 2,   /* fewer than k nonzero singular values exist; outputs padded */
+  GK_INVALID_ARG = -1,     /* bad sizes, null pointers, unsupported dtype/kind combination */
+  GK_CUDA_ERROR = -2,      /* a CUDA runtime call failed (see gk_last_cuda_error) */
+  GK_NUMERICAL = -3,       /* NaN or Inf appeared in a norm */
+  GK_TIMEOUT = -4,         /* a bounded device wait gave up */
+  GK_OUT_OF_MEMORY = -5,   /* workspace allocation failed or caller workspace too small */
+  GK_NOT_IMPLEMENTED = -6,
+  GK_NO_DEVICE = -7        /* no CUDA device usable by this library */
+} gk_status;
+
+typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
+
+/* opts->flags bits */
+#define GK_FLAG_PROFILE 1 /* time kernel groups with CUDA events on opts->stream (gk_info.ms_*) */
+typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
+
+/* The operator A (m x n).
+ *  dense: vals points to m*ld values of dtype (row-major); rowptr/colind unused.
+ *  CSR:   vals/rowptr/colind hold A (rowptr: m+1 int32 offsets, colind: int32,
+ *         nnz = rowptr[m]); t_vals/t_rowptr/t_colind hold the CSR of A^T (n
+ *         rows).  Both are required for CSR: the library never transposes.
+ *  scale multiplies every stored value (use 1.0; for f16 storage a power of two
+ *  that keeps the stored values in the normal range). */
+typedef struct {
+  int32_t kind;
+  int32_t dtype;
+  int64_t m, n, ld;
+  double scale;
+  const void *vals;
+  const int32_t *rowptr;
+  const int32_t *colind;
+  const void *t_vals;
+  const int32_t *t_rowptr;
+  const int32_t *t_colind;
+} gk_matrix;
+
+typedef struct {
+  int32_t krylov_dim;    /* K, the Krylov dimension of one restart cycle (0 = default min(max(2k, k+16), min(m,n))) */
+  int32_t keep;          /* Ritz vectors kept at a restart (0 = k + (K-k)/2) */
+  int32_t max_restarts;  /* restart budget of gk_psvd (default 200) */
+  int32_t reorth_passes; /* classical Gram-Schmidt passes per vector: 2 (default) or 1 (as printed in the paper) */
+  int32_t eps_absolute;  /* gk_numrank: 0 = eps relative to sigma_1 (default), 1 = absolute threshold */
+  int32_t flags;         /* GK_FLAG_* bits (0 = none) */
+  uint64_t seed;         /* seed of the start vector and of replacement directions */
+  const double *start;   /* optional m-vector q1 (device or host); NULL = draw q1 ~ N(2,1)^m from seed */
+  void *stream;          /* cudaStream_t, NULL = legacy default stream */
+  void *workspace;       /* optional caller-owned device workspace */
+  size_t workspace_bytes;
+} gk_opts;
+
+typedef struct {
+  int32_t steps;         /* bidiagonalization steps taken (left+right half-steps count as one) */
+  int32_t restarts;
+  int32_t cycles;
+  int32_t kprime;        /* gk_numrank: k' of Algorithm 1 (columns of B_{k'+1,k'}) */
+  int32_t stop_reason;   /* gk_numrank: 0 reached kmax, 1 beta break, 2 alpha break */
+  int32_t breakdowns;    /* exact breakdowns replaced by fresh directions */
+  int64_t matvecs;       /* products with A or A^T */
+  double resid_est_max;  /* gk_psvd: max_i<k |beta_K X_{K,i}| / sigma_1 (Ritz residual estimate) */
+  double sigma_est;      /* running lower bound on sigma_1 used by the break test */
+  double seconds;        /* wall time of the call */
+  /* with GK_FLAG_PROFILE: device milliseconds and launch counts of kernel
+   * groups, from CUDA events recorded on opts->stream around each group */
+  double ms_matvec;      /* A x products */
+  double ms_matvec_t;    /* A^T x products (partial sums + their reduction) */
+  double ms_orth;        /* Gram-Schmidt passes, norms, normalization */
+  double ms_small;       /* small SVD, Ritz residual test, rank count */
+  double ms_restart;     /* Ritz vectors U_K X, V_K Y (restarts and outputs) */
+  int64_t n_matvec;
+  int64_t n_matvec_t;
+  int64_t launches;      /* kernels this call launched (all of them the library's own) */
+} gk_info;
+
+/* Fill *opts with the defaults above. */
+void gk_default_opts(gk_opts *opts);
+
+/* Device workspace (bytes) gk_psvd needs for this operator, k and opts. */
+size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *opts);
+
+/* Partial SVD: the k largest singular triplets of A.
+ * Method: Golub-Kahan bidiagonalization (Section 2.2, Eqs. 2.1-2.4) in the
+ * upper-bidiagonal form started from v1 = A^T q1 / ||A^T q1|| (Algorithm 1,
+ * lines 1-2), full reorthogonalization by classical Gram-Schmidt (Algorithm 1,
+ * lines 6 and 13; two passes by default), Ritz pairs from the SVD of the small
+ * projected matrix (Eq. 2.13, Algorithm 2 lines 2-5), and thick restarts that
+ * keep the leading Ritz vectors (the paper cites augmented restarting; the
+ * restart itself is this library's choice).
+ *  tol: a triplet is converged when ||A^T u_i - s_i v_i|| (the Ritz residual,
+ *       = |beta_K X_{K,i}|; A v_i = s_i u_i holds by construction) is at most
+ *       tol * s_1.
+ *  U:   m x k, column-major, f64 (device or host).
+ *  S:   k singular values, f64, descending.
+ *  V:   n x k, column-major, f64.
+ * Each pair (u_i, v_i) is signed so that the largest-magnitude entry of v_i is
+ * positive.  Returns GK_OK, GK_NOT_CONVERGED (outputs hold the last Ritz
+ * triplets), or an error.  1 <= k <= min(m,n). */
+int gk_psvd(const gk_matrix *A, int k, double tol, const gk_opts *opts, double *U, double *S, double *V,
+            gk_info *info);
+
+/* Device workspace (bytes) gk_numrank needs. */
+size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *opts);
+
+/* Numerical rank (Algorithm 3): run Algorithm 1 (lower-bidiagonal GK with
+ * reorthogonalization) for at most kmax iterations (kmax <= 0 or > min(m,n)
+ * means min(m,n), Algorithm 3 line 1), stopping when the new left norm
+ * beta_{j+1} (or right norm alpha_{j+1}) is <= eps * sigma_est (relative
+ * reading; opts->eps_absolute = 1 compares with eps itself), then count the
+ * singular values of B_{k'+1,k'} (square roots of the eigenvalues of
+ * B^T B, Algorithm 3 lines 3-4) that exceed eps * sigma_1(B) (or eps).
+ *  rank:  host int, written on success.
+ *  sigma: optional (may be NULL) output of the k' singular values of B,
+ *         descending (device or host, f64, capacity kmax).
+ * The workspace holds two bases of kmax+1 columns: pass a realistic kmax
+ * for large matrices. */
+int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, int *rank, double *sigma,
+               gk_info *info);
+
+/* y = A x (trans = 0; x: n, y: m) or y = A^T x (trans = 1; x: m, y: n), f64
+ * vectors (device or host).  These are the products of Eq. 2.2 (Algorithm 1,
+ * lines 5 and 12) run by the same kernels as the sweep: f32/bf16/f16 operators
+ * multiply in f32 with x rounded to f32 and combine short f32 runs in f64;
+ * f64 and CSR operators multiply in f64. */
+int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const gk_opts *opts);
+
+/* True residuals of k triplets (columns of U m x k, V n x k, column-major,
+ * f64; S k values): res_av[i] = ||A v_i - s_i u_i||, res_atu[i] =
+ * ||A^T u_i - s_i v_i|| (the quantities behind the paper's err_rel of
+ * Section 5 and the tolerance of gk_psvd).  Outputs f64, device or host. */
+int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, const double *V, double *res_av,
+                 double *res_atu, const gk_opts *opts);
+
+/* Human-readable name of a status code. */
+const char *gk_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char *gk_last_cuda_error(void);
+
+/* Library version string. */
+const char *gk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GK_H */

@@ -1,0 +1,21 @@
+"""GB300 Golub-Kahan partial SVD and numerical rank (arXiv 2104.10785).
+
+The compute path is libgk.so (CUDA, sm_103a) behind the C ABI in include/gk.h;
+this package holds the kernels' sources (csrc/), the build step and the ctypes
+binding.
+"""
+from .gk import (  # noqa: F401
+    CSR,
+    GKError,
+    gk_matvec,
+    gk_numrank,
+    gk_numrank_workspace,
+    gk_psvd,
+    gk_psvd_workspace,
+    gk_residuals,
+    last_cuda_error,
+    lib,
+    library_path,
+    status_string,
+    version,
+)

@@ -1,0 +1,977 @@
+// gk_api.cu -- the C ABI of libgk.so and the host drivers of the two methods.
+//
+// gk_numrank: Algorithm 1 (lower-bidiagonal Golub-Kahan with reorthogonalization
+//   and the break test) followed by the rank count of Algorithm 3.
+// gk_psvd:    the upper-bidiagonal Golub-Kahan process from v1 = A^T q1/||A^T q1||
+//   with thick restarts: each cycle extends the basis to K columns, takes the SVD
+//   of the K x K projected matrix, tests the Ritz residuals |beta_K X_{K,i}| and
+//   either returns the leading Ritz triplets or keeps `keep` of them plus
+//   v_{K+1} and continues.
+//
+// The host only enqueues kernels.  Data-dependent decisions (break, breakdown,
+// convergence) are taken on the device and recorded in a control block; after
+// an event every later kernel of the sweep returns at entry, and the host reads
+// the block once per chunk of steps (numrank) or once per cycle (psvd).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "gk_internal.cuh"
+
+using namespace gk;
+
+namespace gk {
+namespace {
+thread_local int64_t t_launches = 0;
+}
+void note_launch() { ++t_launches; }
+int64_t launch_count() { return t_launches; }
+}  // namespace gk
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+struct Status {
+  int code;
+};
+
+#define GK_CUDA(x)                                                                                          \
+  do {                                                                                                      \
+    cudaError_t e_ = (x);                                                                                   \
+    if (e_ != cudaSuccess) {                                                                                \
+      snprintf(g_err, sizeof(g_err), "%s -> %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+      return GK_CUDA_ERROR;                                                                                 \
+    }                                                                                                       \
+  } while (0)
+
+bool get_device(Dev *d) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
+    cudaGetLastError();
+    return false;
+  }
+  int id = 0;
+  if (cudaGetDevice(&id) != cudaSuccess) return false;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, id) != cudaSuccess) return false;
+  d->sms = sms;
+  d->id = id;
+  return true;
+}
+
+// true if p is host memory (pageable or pinned) rather than device/managed memory
+bool on_host(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+size_t esize(int dtype) { return dtype == GK_F64 ? 8 : (dtype == GK_F32 ? 4 : 2); }
+
+// bump allocator over the workspace (a null base only measures)
+struct Carve {
+  char *base;
+  size_t off;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) / 256 * 256;
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T) + 256;
+    return p;
+  }
+};
+
+gk_opts defaults() {
+  gk_opts o;
+  memset(&o, 0, sizeof(o));
+  o.krylov_dim = 0;
+  o.keep = 0;
+  o.max_restarts = 200;
+  o.reorth_passes = 2;
+  o.eps_absolute = 0;
+  o.flags = 0;
+  o.seed = 2104107ull;
+  o.start = nullptr;
+  o.stream = nullptr;
+  o.workspace = nullptr;
+  o.workspace_bytes = 0;
+  return o;
+}
+
+int check_matrix(const gk_matrix *A) {
+  if (!A || A->m <= 0 || A->n <= 0 || !A->vals) return GK_INVALID_ARG;
+  if (A->dtype < GK_F64 || A->dtype > GK_F16) return GK_INVALID_ARG;
+  if (!(A->scale == A->scale) || A->scale == 0.0) return GK_INVALID_ARG;
+  if (A->m > INT32_MAX || A->n > INT32_MAX) return GK_INVALID_ARG;
+  if (A->kind == GK_DENSE) {
+    if (A->ld < A->n) return GK_INVALID_ARG;
+  } else if (A->kind == GK_CSR) {
+    if (!A->rowptr || !A->colind || !A->t_vals || !A->t_rowptr || !A->t_colind) return GK_INVALID_ARG;
+  } else {
+    return GK_INVALID_ARG;
+  }
+  return GK_OK;
+}
+
+// number of stored entries of a CSR array (reads rowptr[rows])
+int csr_nnz(const int32_t *rowptr, int64_t rows, int64_t *nnz) {
+  int32_t v = 0;
+  if (on_host(rowptr)) {
+    v = rowptr[rows];
+  } else {
+    GK_CUDA(cudaMemcpy(&v, rowptr + rows, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  }
+  if (v < 0) return GK_INVALID_ARG;
+  *nnz = v;
+  return GK_OK;
+}
+
+// Device copy of a host operator inside the workspace.
+struct OpStage {
+  bool host = false;
+  int64_t nnz = 0, tnnz = 0;
+  size_t vals_bytes = 0;
+};
+
+int stage_plan(const gk_matrix *A, OpStage *st) {
+  st->host = on_host(A->vals);
+  if (A->kind == GK_DENSE) {
+    st->vals_bytes = (size_t)((A->m - 1) * A->ld + A->n) * esize(A->dtype);
+  } else {
+    int rc = csr_nnz(A->rowptr, A->m, &st->nnz);
+    if (rc) return rc;
+    rc = csr_nnz(A->t_rowptr, A->n, &st->tnnz);
+    if (rc) return rc;
+    if (st->nnz != st->tnnz) return GK_INVALID_ARG;
+  }
+  return GK_OK;
+}
+
+void stage_carve(const gk_matrix *A, const OpStage &st, Carve &cv, Op *op, char **dense_dst, void **v, int32_t **rp,
+                 int32_t **ci, void **tv, int32_t **trp, int32_t **tci) {
+  *dense_dst = nullptr;
+  if (!st.host) return;
+  if (A->kind == GK_DENSE) {
+    *dense_dst = cv.take<char>(st.vals_bytes);
+    op->vals = *dense_dst;
+  } else {
+    *v = cv.take<char>((size_t)st.nnz * esize(A->dtype));
+    *rp = cv.take<int32_t>((size_t)A->m + 1);
+    *ci = cv.take<int32_t>((size_t)st.nnz);
+    *tv = cv.take<char>((size_t)st.nnz * esize(A->dtype));
+    *trp = cv.take<int32_t>((size_t)A->n + 1);
+    *tci = cv.take<int32_t>((size_t)st.nnz);
+    op->vals = *v;
+    op->rowptr = *rp;
+    op->colind = *ci;
+    op->t_vals = *tv;
+    op->t_rowptr = *trp;
+    op->t_colind = *tci;
+  }
+}
+
+int stage_copy(const gk_matrix *A, const OpStage &st, const Op &op, cudaStream_t s) {
+  if (!st.host) return GK_OK;
+  if (A->kind == GK_DENSE) {
+    GK_CUDA(cudaMemcpyAsync(const_cast<void *>(op.vals), A->vals, st.vals_bytes, cudaMemcpyHostToDevice, s));
+  } else {
+    const size_t es = esize(A->dtype);
+    GK_CUDA(cudaMemcpyAsync(const_cast<void *>(op.vals), A->vals, st.nnz * es, cudaMemcpyHostToDevice, s));
+    GK_CUDA(cudaMemcpyAsync(const_cast<int32_t *>(op.rowptr), A->rowptr, (A->m + 1) * 4, cudaMemcpyHostToDevice, s));
+    GK_CUDA(cudaMemcpyAsync(const_cast<int32_t *>(op.colind), A->colind, st.nnz * 4, cudaMemcpyHostToDevice, s));
+    GK_CUDA(cudaMemcpyAsync(const_cast<void *>(op.t_vals), A->t_vals, st.nnz * es, cudaMemcpyHostToDevice, s));
+    GK_CUDA(
+        cudaMemcpyAsync(const_cast<int32_t *>(op.t_rowptr), A->t_rowptr, (A->n + 1) * 4, cudaMemcpyHostToDevice, s));
+    GK_CUDA(cudaMemcpyAsync(const_cast<int32_t *>(op.t_colind), A->t_colind, st.nnz * 4, cudaMemcpyHostToDevice, s));
+  }
+  return GK_OK;
+}
+
+Op make_op(const gk_matrix *A) {
+  Op op;
+  op.kind = A->kind;
+  op.dtype = A->dtype;
+  op.m = A->m;
+  op.n = A->n;
+  op.ld = A->kind == GK_DENSE ? A->ld : 0;
+  op.scale = A->scale;
+  op.vals = A->vals;
+  op.rowptr = A->rowptr;
+  op.colind = A->colind;
+  op.t_vals = A->t_vals;
+  op.t_rowptr = A->t_rowptr;
+  op.t_colind = A->t_colind;
+  return op;
+}
+
+// Workspace owner: caller memory or a stream-ordered allocation freed on exit.
+struct Workspace {
+  char *base = nullptr;
+  bool owned = false;
+  cudaStream_t s = nullptr;
+  ~Workspace() {
+    if (owned && base) {
+      cudaFreeAsync(base, s);
+      cudaStreamSynchronize(s);
+    }
+  }
+};
+
+int acquire(Workspace &ws, size_t bytes, const gk_opts &o, cudaStream_t s) {
+  ws.s = s;
+  if (o.workspace) {
+    if (o.workspace_bytes < bytes) return GK_OUT_OF_MEMORY;
+    if ((uintptr_t)o.workspace % 256 != 0) return GK_INVALID_ARG;
+    ws.base = (char *)o.workspace;
+    return GK_OK;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_err, sizeof(g_err), "cudaMallocAsync(%zu) -> %s", bytes, cudaGetErrorString(e));
+    return GK_OUT_OF_MEMORY;
+  }
+  ws.base = (char *)p;
+  ws.owned = true;
+  return GK_OK;
+}
+
+// CUDA-event timing of kernel groups (GK_FLAG_PROFILE); events are pooled per thread
+enum ProfCat { PC_MATVEC = 0, PC_MATVEC_T = 1, PC_ORTH = 2, PC_SMALL = 3, PC_RESTART = 4, PC_N = 5 };
+thread_local std::vector<cudaEvent_t> t_event_pool;
+
+struct Prof {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  size_t used = 0;
+  struct Rec {
+    int cat;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  int cur = -1;
+  cudaEvent_t cur_ev = nullptr;
+  cudaEvent_t get() {
+    if (used == t_event_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on = false;
+        return nullptr;
+      }
+      t_event_pool.push_back(e);
+    }
+    return t_event_pool[used++];
+  }
+  void begin(int cat) {
+    if (!on) return;
+    cur_ev = get();
+    if (!on) return;
+    cudaEventRecord(cur_ev, s);
+    cur = cat;
+  }
+  void end() {
+    if (!on || cur < 0) return;
+    cudaEvent_t e = get();
+    if (!on) return;
+    cudaEventRecord(e, s);
+    recs.push_back({cur, cur_ev, e});
+    cur = -1;
+  }
+  void finish(gk_info *inf) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    double ms[PC_N] = {0, 0, 0, 0, 0};
+    int64_t cnt[PC_N] = {0, 0, 0, 0, 0};
+    for (const Rec &r : recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.cat] += t;
+        cnt[r.cat]++;
+      }
+    }
+    inf->ms_matvec = ms[PC_MATVEC];
+    inf->ms_matvec_t = ms[PC_MATVEC_T];
+    inf->ms_orth = ms[PC_ORTH];
+    inf->ms_small = ms[PC_SMALL];
+    inf->ms_restart = ms[PC_RESTART];
+    inf->n_matvec = cnt[PC_MATVEC];
+    inf->n_matvec_t = cnt[PC_MATVEC_T];
+  }
+};
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// ---------------------------------------------------------------------------
+// gk_psvd
+// ---------------------------------------------------------------------------
+struct PsvdPlan {
+  int64_t m, n, ldu, ldv;
+  int k, K, keep, passes, max_restarts;
+};
+
+struct PsvdBufs {
+  Ctl *ctl;
+  double *Ub, *Ub2, *Vb, *Vb2, *w, *z, *t, *part, *h, *alpha, *beta, *Bm, *Yw, *X, *Y, *sigma, *rho, *out;
+  float *x32;
+  int *sweeps;
+  double *Uo, *So, *Vo, *q1;
+};
+
+size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const OpStage &st, bool host_out,
+                   bool host_start, char *base, PsvdBufs *b, Op *op) {
+  Carve cv{base, 0};
+  const int K = p.K;
+  b->ctl = cv.take<Ctl>(1);
+  b->Ub = cv.take<double>((size_t)p.ldu * K);
+  b->Ub2 = cv.take<double>((size_t)p.ldu * K);
+  b->Vb = cv.take<double>((size_t)p.ldv * (K + 1));
+  b->Vb2 = cv.take<double>((size_t)p.ldv * (K + 1));
+  b->w = cv.take<double>(p.ldu);
+  b->t = cv.take<double>(p.ldu);
+  b->z = cv.take<double>(p.ldv);
+  b->x32 = cv.take<float>(p.ldu > p.ldv ? p.ldu : p.ldv);
+  const int64_t gmax = cgs_blocks(p.m, d) > cgs_blocks(p.n, d) ? cgs_blocks(p.m, d) : cgs_blocks(p.n, d);
+  int64_t pcount = gmax * (K + 2) + gmax;
+  const int64_t gp = gemvt_partials(*op, d);
+  if (gp > pcount) pcount = gp;
+  b->part = cv.take<double>(pcount);
+  b->h = cv.take<double>(K + 2);
+  b->alpha = cv.take<double>(K + 2);
+  b->beta = cv.take<double>(K + 2);
+  b->Bm = cv.take<double>((size_t)K * K);
+  b->Yw = cv.take<double>((size_t)K * K);
+  b->X = cv.take<double>((size_t)K * K);
+  b->Y = cv.take<double>((size_t)K * K);
+  b->sigma = cv.take<double>(K);
+  b->rho = cv.take<double>(K);
+  b->out = cv.take<double>(8);
+  b->sweeps = cv.take<int>(4);
+  b->Uo = host_out ? cv.take<double>((size_t)p.m * p.k) : nullptr;
+  b->Vo = host_out ? cv.take<double>((size_t)p.n * p.k) : nullptr;
+  b->So = host_out ? cv.take<double>(p.k) : nullptr;
+  b->q1 = host_start ? cv.take<double>(p.ldu) : nullptr;
+  char *dd;
+  void *v, *tv;
+  int32_t *rp, *ci, *trp, *tci;
+  stage_carve(A, st, cv, op, &dd, &v, &rp, &ci, &tv, &trp, &tci);
+  return cv.off + 256;
+}
+
+int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
+  const int64_t mn = A->m < A->n ? A->m : A->n;
+  if (k < 1 || k > mn) return GK_INVALID_ARG;
+  int K = o.krylov_dim;
+  if (K <= 0) {
+    int64_t d = 2 * (int64_t)k;
+    if (d < k + 16) d = k + 16;
+    if (d > mn) d = mn;
+    K = (int)d;
+  }
+  if (K < k || K > mn) return GK_INVALID_ARG;
+  if (K == k && K < mn) return GK_INVALID_ARG;  // a restart needs room beyond the wanted vectors
+  if (K > 1024) return GK_INVALID_ARG;
+  int keep = o.keep > 0 ? o.keep : k + (K - k) / 2;
+  if (keep < k) keep = k;
+  if (keep >= K) keep = K - 1;
+  if (keep < 0) keep = 0;
+  if (o.reorth_passes < 1 || o.reorth_passes > 3) return GK_INVALID_ARG;
+  if (o.max_restarts < 0) return GK_INVALID_ARG;
+  p->m = A->m;
+  p->n = A->n;
+  p->ldu = round_up(A->m, 32);
+  p->ldv = round_up(A->n, 32);
+  p->k = k;
+  p->K = K;
+  p->keep = keep;
+  p->passes = o.reorth_passes;
+  p->max_restarts = o.max_restarts;
+  return GK_OK;
+}
+
+struct HostCtl {
+  Ctl ctl;
+  double out[8];
+};
+
+int read_ctl(const Ctl *dctl, const double *dout, HostCtl *hc, cudaStream_t s) {
+  GK_CUDA(cudaMemcpyAsync(&hc->ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  if (dout) GK_CUDA(cudaMemcpyAsync(hc->out, dout, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  return GK_OK;
+}
+
+int clear_halt(Ctl *ctl, cudaStream_t s) {
+  GK_CUDA(cudaMemsetAsync(ctl, 0, 2 * sizeof(int), s));  // halt and event
+  return GK_OK;
+}
+
+// replacement direction for a basis column: fresh values, orthogonalized twice
+// against the first `jcols` columns, normalized (or zero if the basis is full)
+int fresh_column(double *wbuf, int64_t len, const double *Qb, int64_t ld, int jcols, double *dst, float *x32,
+                 uint64_t seed, int64_t *nfresh, PsvdBufs &b, cudaStream_t s, const Dev &d) {
+  GK_CUDA(draw_fresh(wbuf, len, seed, (*nfresh)++, s));
+  GK_CUDA(orthonormalize(wbuf, len, Qb, ld, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
+  GK_CUDA(orthonormalize(wbuf, len, Qb, ld, jcols, 2, b.part, b.h, b.ctl, NM_FRESH, -1, 0, nullptr, nullptr, s, d));
+  GK_CUDA(normalize_append(wbuf, len, dst, x32, b.ctl, s, d));
+  return GK_OK;
+}
+
+int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, double *U, double *S, double *V,
+              gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  g_err[0] = 0;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  if (info) *info = inf;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  if (!U || !S || !V || !(tol >= 0.0) || !isfinite(tol)) return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  PsvdPlan p;
+  rc = psvd_plan(Ain, k, o, &p);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  OpStage st;
+  rc = stage_plan(Ain, &st);
+  if (rc) return rc;
+  const bool host_out = on_host(U) || on_host(S) || on_host(V);
+  const bool host_start = o.start && on_host(o.start);
+  Op op = make_op(Ain);
+  PsvdBufs b;
+  const size_t bytes = psvd_layout(Ain, p, d, st, host_out, host_start, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, s);
+  if (rc) return rc;
+  op = make_op(Ain);
+  psvd_layout(Ain, p, d, st, host_out, host_start, ws.base, &b, &op);
+  rc = stage_copy(Ain, st, op, s);
+  if (rc) return rc;
+
+  const int64_t m = p.m, n = p.n, ldu = p.ldu, ldv = p.ldv;
+  const int K = p.K;
+  Prof prof;
+  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
+  prof.s = s;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
+  GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (K + 2), s));
+  GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (K + 2), s));
+  // start vector q1 (Algorithm 1, line 1) and v1 = A^T q1 / ||A^T q1|| (line 2)
+  if (o.start) {
+    const double *src = o.start;
+    if (host_start) {
+      GK_CUDA(cudaMemcpyAsync(b.q1, o.start, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+      src = b.q1;
+    }
+    GK_CUDA(copy_vec(b.t, nullptr, src, m, s));
+  } else {
+    GK_CUDA(draw_start(b.t, m, o.seed, s));
+  }
+  GK_CUDA(orthonormalize(b.t, m, nullptr, ldu, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
+  GK_CUDA(normalize_append(b.t, m, b.t, b.x32, b.ctl, s, d));
+  GK_CUDA(matvec_t(op, b.x32, b.t, b.z, nullptr, nullptr, b.part, b.ctl, s, d));
+  GK_CUDA(orthonormalize(b.z, n, b.Vb, ldv, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 1, nullptr, nullptr, s, d));
+  GK_CUDA(normalize_append(b.z, n, b.Vb, b.x32, b.ctl, s, d));
+  inf.matvecs = 1;
+  HostCtl hc;
+  rc = read_ctl(b.ctl, nullptr, &hc, s);
+  if (rc) return rc;
+  if (!isfinite(hc.ctl.norm)) return GK_NUMERICAL;
+  int64_t nfresh = 0;
+  if (hc.ctl.norm == 0.0) {  // A^T q1 = 0
+    rc = fresh_column(b.z, n, b.Vb, ldv, 0, b.Vb, b.x32, o.seed, &nfresh, b, s, d);
+    if (rc) return rc;
+    inf.breakdowns++;
+  }
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
+
+  int l = 0;
+  int status = GK_NOT_CONVERGED;
+  for (int cycle = 0;; ++cycle) {
+    int j0 = l, side0 = 0;
+    for (;;) {
+      for (int j = j0; j < K; ++j) {
+        if (!(j == j0 && side0 == 1)) {
+          // left half-step: A v_j minus its component along the previous u's
+          const double *vj = b.Vb + (int64_t)j * ldv;
+          prof.begin(PC_MATVEC);
+          if (j == l && l > 0) {
+            GK_CUDA(matvec(op, b.x32, vj, b.w, nullptr, nullptr, b.part, b.ctl, s, d));
+            prof.end();
+            prof.begin(PC_ORTH);
+            GK_CUDA(sub_combination(b.w, m, b.Ub, ldu, l, b.rho, b.ctl, s, d));
+          } else if (j > 0) {
+            GK_CUDA(matvec(op, b.x32, vj, b.w, b.Ub + (int64_t)(j - 1) * ldu, b.beta + (j - 1), b.part, b.ctl, s, d));
+            prof.end();
+            prof.begin(PC_ORTH);
+          } else {
+            GK_CUDA(matvec(op, b.x32, vj, b.w, nullptr, nullptr, b.part, b.ctl, s, d));
+            prof.end();
+            prof.begin(PC_ORTH);
+          }
+          GK_CUDA(orthonormalize(b.w, m, b.Ub, ldu, j, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 0, b.alpha + j,
+                                 nullptr, s, d));
+          GK_CUDA(normalize_append(b.w, m, b.Ub + (int64_t)j * ldu, b.x32, b.ctl, s, d));
+          prof.end();
+          inf.matvecs++;
+        }
+        // right half-step: A^T u_j - alpha_j v_j, orthogonalized against V_{j+1}
+        prof.begin(PC_MATVEC_T);
+        GK_CUDA(matvec_t(op, b.x32, b.Ub + (int64_t)j * ldu, b.z, b.Vb + (int64_t)j * ldv, b.alpha + j, b.part,
+                         b.ctl, s, d));
+        prof.end();
+        prof.begin(PC_ORTH);
+        GK_CUDA(orthonormalize(b.z, n, b.Vb, ldv, j + 1, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 1,
+                               b.beta + j, nullptr, s, d));
+        GK_CUDA(normalize_append(b.z, n, b.Vb + (int64_t)(j + 1) * ldv, b.x32, b.ctl, s, d));
+        prof.end();
+        inf.matvecs++;
+        inf.steps++;
+      }
+      prof.begin(PC_SMALL);
+      GK_CUDA(assemble_B(b.Bm, K, l, b.sigma, b.rho, b.alpha, b.beta, b.ctl, s));
+      GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.sweeps, b.ctl, s));
+      GK_CUDA(ritz_check(b.sigma, b.X, K, k, b.beta + (K - 1), tol, b.rho, b.out, b.ctl, s));
+      prof.end();
+      rc = read_ctl(b.ctl, b.out, &hc, s);
+      if (rc) return rc;
+      if (hc.ctl.event == EV_NUMERICAL) return GK_NUMERICAL;
+      if (hc.ctl.event != EV_BREAKDOWN) break;
+      // exact breakdown: replace the vanished vector and resume the cycle after it
+      const int jb = hc.ctl.step, sb = hc.ctl.side;
+      rc = clear_halt(b.ctl, s);
+      if (rc) return rc;
+      inf.breakdowns++;
+      if (sb == 0) {
+        rc = fresh_column(b.w, m, b.Ub, ldu, jb, b.Ub + (int64_t)jb * ldu, b.x32, o.seed, &nfresh, b, s, d);
+        j0 = jb;
+        side0 = 1;
+      } else {
+        rc = fresh_column(b.z, n, b.Vb, ldv, jb + 1, b.Vb + (int64_t)(jb + 1) * ldv, b.x32, o.seed, &nfresh, b, s,
+                          d);
+        j0 = jb + 1;
+        side0 = 0;
+      }
+      if (rc) return rc;
+    }
+    inf.cycles = cycle + 1;
+    inf.resid_est_max = hc.out[1] > 0.0 ? hc.out[0] / hc.out[1] : 0.0;
+    const bool conv = hc.out[2] != 0.0;
+    if (conv || cycle >= p.max_restarts) {
+      status = conv ? GK_OK : GK_NOT_CONVERGED;
+      break;
+    }
+    // thick restart: U' = U_K X_keep, V' = [V_K Y_keep, v_{K+1}]
+    prof.begin(PC_RESTART);
+    GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, p.keep, b.Ub2, ldu, s, d));
+    GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, p.keep, b.Vb2, ldv, s, d));
+    GK_CUDA(copy_vec(b.Vb2 + (int64_t)p.keep * ldv, b.x32, b.Vb + (int64_t)K * ldv, n, s));
+    prof.end();
+    double *tmp = b.Ub;
+    b.Ub = b.Ub2;
+    b.Ub2 = tmp;
+    tmp = b.Vb;
+    b.Vb = b.Vb2;
+    b.Vb2 = tmp;
+    l = p.keep;
+    inf.restarts++;
+  }
+
+  // outputs: U = U_K X_k, V = V_K Y_k, S = sigma_k, sign convention on v
+  double *Uo = host_out ? b.Uo : U, *Vo = host_out ? b.Vo : V, *So = host_out ? b.So : S;
+  prof.begin(PC_RESTART);
+  GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, k, Uo, m, s, d));
+  GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, k, Vo, n, s, d));
+  prof.end();
+  GK_CUDA(cudaMemcpyAsync(So, b.sigma, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
+  GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, k, s));
+  double sk = 0.0;
+  GK_CUDA(cudaMemcpyAsync(&sk, b.sigma + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (host_out) {
+    GK_CUDA(cudaMemcpyAsync(U, Uo, sizeof(double) * m * k, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(V, Vo, sizeof(double) * n * k, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(S, So, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  }
+  GK_CUDA(cudaMemcpyAsync(&hc.ctl, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  if (status == GK_OK && sk == 0.0) status = GK_RANK_DEFICIENT;
+  prof.finish(&inf);
+  inf.sigma_est = hc.ctl.sest;
+  inf.seconds = seconds_since(t0);
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// gk_numrank
+// ---------------------------------------------------------------------------
+struct RankBufs {
+  Ctl *ctl;
+  double *Q, *P, *w, *z, *t, *part, *h, *alpha, *beta, *sig, *sigma1, *q1;
+  float *x32;
+  int *rank;
+};
+
+size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpStage &st, bool host_sigma,
+                      bool host_start, char *base, RankBufs *b, Op *op) {
+  Carve cv{base, 0};
+  const int64_t ldu = round_up(A->m, 32), ldv = round_up(A->n, 32);
+  b->ctl = cv.take<Ctl>(1);
+  b->Q = cv.take<double>((size_t)ldu * (kmax + 1));
+  b->P = cv.take<double>((size_t)ldv * (kmax + 1));
+  b->w = cv.take<double>(ldu);
+  b->t = cv.take<double>(ldu);
+  b->z = cv.take<double>(ldv);
+  b->x32 = cv.take<float>(ldu > ldv ? ldu : ldv);
+  const int64_t gmax = cgs_blocks(A->m, d) > cgs_blocks(A->n, d) ? cgs_blocks(A->m, d) : cgs_blocks(A->n, d);
+  int64_t pcount = gmax * (kmax + 2) + gmax;
+  const int64_t gp = gemvt_partials(*op, d);
+  if (gp > pcount) pcount = gp;
+  b->part = cv.take<double>(pcount);
+  b->h = cv.take<double>(kmax + 2);
+  b->alpha = cv.take<double>(kmax + 2);
+  b->beta = cv.take<double>(kmax + 2);
+  b->sig = host_sigma ? cv.take<double>(kmax + 1) : nullptr;
+  b->sigma1 = cv.take<double>(1);
+  b->rank = cv.take<int>(1);
+  b->q1 = host_start ? cv.take<double>(ldu) : nullptr;
+  char *dd;
+  void *v, *tv;
+  int32_t *rp, *ci, *trp, *tci;
+  stage_carve(A, st, cv, op, &dd, &v, &rp, &ci, &tv, &trp, &tci);
+  return cv.off + 256;
+}
+
+int64_t clamp_kmax(const gk_matrix *A, int kmax) {
+  const int64_t mn = A->m < A->n ? A->m : A->n;
+  return (kmax <= 0 || kmax > mn) ? mn : kmax;
+}
+
+int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *oin, int *rank, double *sigma,
+                 gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  g_err[0] = 0;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  if (info) *info = inf;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  if (!rank || !(eps >= 0.0) || !isfinite(eps)) return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  if (o.reorth_passes < 1 || o.reorth_passes > 3) return GK_INVALID_ARG;
+  const int64_t kmax = clamp_kmax(Ain, kmax_in);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  OpStage st;
+  rc = stage_plan(Ain, &st);
+  if (rc) return rc;
+  const bool host_sigma = sigma && on_host(sigma);
+  const bool host_start = o.start && on_host(o.start);
+  Op op = make_op(Ain);
+  RankBufs b;
+  const size_t bytes = numrank_layout(Ain, kmax, d, st, host_sigma, host_start, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, s);
+  if (rc) return rc;
+  op = make_op(Ain);
+  numrank_layout(Ain, kmax, d, st, host_sigma, host_start, ws.base, &b, &op);
+  rc = stage_copy(Ain, st, op, s);
+  if (rc) return rc;
+
+  const int64_t m = Ain->m, n = Ain->n, ldu = round_up(m, 32), ldv = round_up(n, 32);
+  const int passes = o.reorth_passes;
+  const int eps_rel = o.eps_absolute ? 0 : 1;
+  Prof prof;
+  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
+  prof.s = s;
+  GK_CUDA(reset_ctl(b.ctl, eps, eps_rel, s));
+  GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (kmax + 2), s));
+  GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (kmax + 2), s));
+  // line 1: q1 ~ N(2,1)^m, q1 = q1 / ||q1||, Q_1 = q1
+  if (o.start) {
+    const double *src = o.start;
+    if (host_start) {
+      GK_CUDA(cudaMemcpyAsync(b.q1, o.start, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+      src = b.q1;
+    }
+    GK_CUDA(copy_vec(b.t, nullptr, src, m, s));
+  } else {
+    GK_CUDA(draw_start(b.t, m, o.seed, s));
+  }
+  GK_CUDA(orthonormalize(b.t, m, nullptr, ldu, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
+  GK_CUDA(normalize_append(b.t, m, b.Q, b.x32, b.ctl, s, d));
+  // line 2: p1 = A^T q1, alpha_1 = ||p1||, p1 = p1 / alpha_1
+  GK_CUDA(matvec_t(op, b.x32, b.Q, b.z, nullptr, nullptr, b.part, b.ctl, s, d));
+  GK_CUDA(orthonormalize(b.z, n, b.P, ldv, 0, 0, b.part, b.h, b.ctl, NM_BREAK, 0, 1, b.alpha, nullptr, s, d));
+  GK_CUDA(normalize_append(b.z, n, b.P, b.x32, b.ctl, s, d));
+  inf.matvecs = 1;
+  HostCtl hc;
+  rc = read_ctl(b.ctl, nullptr, &hc, s);
+  if (rc) return rc;
+  // lines 4-17, in chunks of steps between reads of the control block
+  const int chunk = 8;
+  int64_t j = 1;
+  while (!hc.ctl.halt && j <= kmax) {
+    const int64_t jend = (j + chunk - 1 < kmax) ? j + chunk - 1 : kmax;
+    for (; j <= jend; ++j) {
+      const int jj = (int)j;
+      // beta_{j+1} q_{j+1} = A p_j - alpha_j q_j, reorthogonalized against Q_j
+      prof.begin(PC_MATVEC);
+      GK_CUDA(matvec(op, b.x32, b.P + (j - 1) * ldv, b.w, b.Q + (j - 1) * ldu, b.alpha + (j - 1), b.part, b.ctl, s,
+                     d));
+      prof.end();
+      prof.begin(PC_ORTH);
+      GK_CUDA(orthonormalize(b.w, m, b.Q, ldu, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 0, b.beta + j,
+                             b.alpha + (j - 1), s, d));
+      GK_CUDA(normalize_append(b.w, m, b.Q + j * ldu, b.x32, b.ctl, s, d));
+      prof.end();
+      // alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j
+      prof.begin(PC_MATVEC_T);
+      GK_CUDA(matvec_t(op, b.x32, b.Q + j * ldu, b.z, b.P + (j - 1) * ldv, b.beta + j, b.part, b.ctl, s, d));
+      prof.end();
+      prof.begin(PC_ORTH);
+      GK_CUDA(orthonormalize(b.z, n, b.P, ldv, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 1, b.alpha + j,
+                             b.beta + j, s, d));
+      GK_CUDA(normalize_append(b.z, n, b.P + j * ldv, b.x32, b.ctl, s, d));
+      prof.end();
+    }
+    rc = read_ctl(b.ctl, nullptr, &hc, s);
+    if (rc) return rc;
+  }
+  if (hc.ctl.event == EV_NUMERICAL) return GK_NUMERICAL;
+  int kp;
+  if (hc.ctl.halt) {
+    kp = hc.ctl.step;
+    inf.stop_reason = hc.ctl.event == EV_BETA_BREAK ? 1 : 2;
+    inf.matvecs += 2 * (int64_t)kp + (hc.ctl.side == 0 ? 1 : 2) - (kp > 0 ? 0 : 1);
+  } else {
+    kp = (int)kmax;
+    inf.stop_reason = 0;
+    inf.matvecs += 2 * (int64_t)kp;
+  }
+  inf.kprime = kp;
+  inf.steps = kp;
+  // Algorithm 3, lines 3-4: singular values of B_{k'+1,k'} above the threshold
+  double *sig_dev = sigma ? (host_sigma ? b.sig : sigma) : nullptr;
+  prof.begin(PC_SMALL);
+  GK_CUDA(bidiag_rank(b.alpha, b.beta, kp, eps, eps_rel, b.rank, b.sigma1, sig_dev, s));
+  prof.end();
+  int r = 0;
+  GK_CUDA(cudaMemcpyAsync(&r, b.rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (host_sigma && kp > 0) GK_CUDA(cudaMemcpyAsync(sigma, b.sig, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  *rank = r;
+  prof.finish(&inf);
+  inf.sigma_est = hc.ctl.sest;
+  inf.seconds = seconds_since(t0);
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  return GK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gk_matvec / gk_residuals
+// ---------------------------------------------------------------------------
+struct VecBufs {
+  Ctl *ctl;
+  double *x, *y, *part, *h, *U, *S, *V, *r1, *r2;
+  float *x32;
+};
+
+size_t vec_layout(const gk_matrix *A, const Dev &d, const OpStage &st, int k, char *base, VecBufs *b, Op *op) {
+  Carve cv{base, 0};
+  const int64_t ld = round_up(A->m > A->n ? A->m : A->n, 32);
+  b->ctl = cv.take<Ctl>(1);
+  b->x = cv.take<double>(ld);
+  b->y = cv.take<double>(ld);
+  b->x32 = cv.take<float>(ld);
+  const int64_t g = cgs_blocks(A->m > A->n ? A->m : A->n, d);
+  int64_t pc = 2 * g + 8;
+  const int64_t gp = gemvt_partials(*op, d);
+  if (gp > pc) pc = gp;
+  b->part = cv.take<double>(pc);
+  b->h = cv.take<double>(4);
+  if (k > 0) {
+    b->U = cv.take<double>((size_t)A->m * k);
+    b->V = cv.take<double>((size_t)A->n * k);
+    b->S = cv.take<double>(k);
+    b->r1 = cv.take<double>(k);
+    b->r2 = cv.take<double>(k);
+  }
+  char *dd;
+  void *v, *tv;
+  int32_t *rp, *ci, *trp, *tci;
+  stage_carve(A, st, cv, op, &dd, &v, &rp, &ci, &tv, &trp, &tci);
+  return cv.off + 256;
+}
+
+int matvec_impl(const gk_matrix *Ain, int trans, const double *x, double *y, const gk_opts *oin) {
+  g_err[0] = 0;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  if (!x || !y || (trans != 0 && trans != 1)) return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  cudaStream_t s = (cudaStream_t)o.stream;
+  OpStage st;
+  rc = stage_plan(Ain, &st);
+  if (rc) return rc;
+  Op op = make_op(Ain);
+  VecBufs b;
+  const size_t bytes = vec_layout(Ain, d, st, 0, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, s);
+  if (rc) return rc;
+  op = make_op(Ain);
+  vec_layout(Ain, d, st, 0, ws.base, &b, &op);
+  rc = stage_copy(Ain, st, op, s);
+  if (rc) return rc;
+  const int64_t nin = trans ? Ain->m : Ain->n, nout = trans ? Ain->n : Ain->m;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
+  GK_CUDA(cudaMemcpyAsync(b.x, x, sizeof(double) * nin, cudaMemcpyDefault, s));
+  GK_CUDA(copy_vec(nullptr, b.x32, b.x, nin, s));
+  if (trans)
+    GK_CUDA(matvec_t(op, b.x32, b.x, b.y, nullptr, nullptr, b.part, b.ctl, s, d));
+  else
+    GK_CUDA(matvec(op, b.x32, b.x, b.y, nullptr, nullptr, b.part, b.ctl, s, d));
+  GK_CUDA(cudaMemcpyAsync(y, b.y, sizeof(double) * nout, cudaMemcpyDefault, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  return GK_OK;
+}
+
+int residuals_impl(const gk_matrix *Ain, int k, const double *U, const double *S, const double *V, double *r_av,
+                   double *r_atu, const gk_opts *oin) {
+  g_err[0] = 0;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  if (!U || !S || !V || !r_av || !r_atu || k < 1) return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  cudaStream_t s = (cudaStream_t)o.stream;
+  OpStage st;
+  rc = stage_plan(Ain, &st);
+  if (rc) return rc;
+  Op op = make_op(Ain);
+  VecBufs b;
+  const size_t bytes = vec_layout(Ain, d, st, k, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, s);
+  if (rc) return rc;
+  op = make_op(Ain);
+  vec_layout(Ain, d, st, k, ws.base, &b, &op);
+  rc = stage_copy(Ain, st, op, s);
+  if (rc) return rc;
+  const int64_t m = Ain->m, n = Ain->n;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
+  GK_CUDA(cudaMemcpyAsync(b.U, U, sizeof(double) * m * k, cudaMemcpyDefault, s));
+  GK_CUDA(cudaMemcpyAsync(b.V, V, sizeof(double) * n * k, cudaMemcpyDefault, s));
+  GK_CUDA(cudaMemcpyAsync(b.S, S, sizeof(double) * k, cudaMemcpyDefault, s));
+  for (int i = 0; i < k; ++i) {
+    const double *ui = b.U + (int64_t)i * m, *vi = b.V + (int64_t)i * n;
+    GK_CUDA(copy_vec(nullptr, b.x32, vi, n, s));
+    GK_CUDA(matvec(op, b.x32, vi, b.y, ui, b.S + i, b.part, b.ctl, s, d));
+    GK_CUDA(orthonormalize(b.y, m, nullptr, m, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, b.r1 + i, nullptr, s, d));
+    GK_CUDA(copy_vec(nullptr, b.x32, ui, m, s));
+    GK_CUDA(matvec_t(op, b.x32, ui, b.y, vi, b.S + i, b.part, b.ctl, s, d));
+    GK_CUDA(orthonormalize(b.y, n, nullptr, n, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 1, b.r2 + i, nullptr, s, d));
+  }
+  GK_CUDA(cudaMemcpyAsync(r_av, b.r1, sizeof(double) * k, cudaMemcpyDefault, s));
+  GK_CUDA(cudaMemcpyAsync(r_atu, b.r2, sizeof(double) * k, cudaMemcpyDefault, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  return GK_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void gk_default_opts(gk_opts *opts) {
+  if (opts) *opts = defaults();
+}
+
+size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *oin) {
+  Dev d;
+  if (!get_device(&d) || check_matrix(A) != GK_OK) return 0;
+  const gk_opts o = oin ? *oin : defaults();
+  PsvdPlan p;
+  if (psvd_plan(A, k, o, &p) != GK_OK) return 0;
+  OpStage st;
+  if (stage_plan(A, &st) != GK_OK) return 0;
+  PsvdBufs b;
+  Op op = make_op(A);
+  return psvd_layout(A, p, d, st, false, false, nullptr, &b, &op);
+}
+
+int gk_psvd(const gk_matrix *A, int k, double tol, const gk_opts *opts, double *U, double *S, double *V,
+            gk_info *info) {
+  return psvd_impl(A, k, tol, opts, U, S, V, info);
+}
+
+size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *oin) {
+  Dev d;
+  if (!get_device(&d) || check_matrix(A) != GK_OK) return 0;
+  (void)oin;
+  OpStage st;
+  if (stage_plan(A, &st) != GK_OK) return 0;
+  RankBufs b;
+  Op op = make_op(A);
+  return numrank_layout(A, clamp_kmax(A, kmax), d, st, false, false, nullptr, &b, &op);
+}
+
+int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, int *rank, double *sigma,
+               gk_info *info) {
+  return numrank_impl(A, eps, kmax, opts, rank, sigma, info);
+}
+
+int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const gk_opts *opts) {
+  return matvec_impl(A, trans, x, y, opts);
+}
+
+int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, const double *V, double *res_av,
+                 double *res_atu, const gk_opts *opts) {
+  return residuals_impl(A, k, U, S, V, res_av, res_atu, opts);
+}
+
+const char *gk_status_string(int status) {
+  switch (status) {
+    case GK_OK: return "GK_OK";
+    case GK_NOT_CONVERGED: return "GK_NOT_CONVERGED";
+    case GK_RANK_DEFICIENT: return "GK_RANK_DEFICIENT";
+    case GK_INVALID_ARG: return "GK_INVALID_ARG";
+    case GK_CUDA_ERROR: return "GK_CUDA_ERROR";
+    case GK_NUMERICAL: return "GK_NUMERICAL";
+    case GK_TIMEOUT: return "GK_TIMEOUT";
+    case GK_OUT_OF_MEMORY: return "GK_OUT_OF_MEMORY";
+    case GK_NOT_IMPLEMENTED: return "GK_NOT_IMPLEMENTED";
+    case GK_NO_DEVICE: return "GK_NO_DEVICE";
+    default: return "GK_UNKNOWN_STATUS";
+  }
+}
+
+const char *gk_last_cuda_error(void) { return g_err; }
+
+const char *gk_version(void) { return "gk-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

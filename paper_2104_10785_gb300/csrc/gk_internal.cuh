@@ -1,0 +1,136 @@
+// gk_internal.cuh -- declarations shared by the translation units of libgk.so.
+//
+// Layout in device memory (all f64 unless noted):
+//   basis U: ldu x (cols) column-major, one Lanczos/Ritz vector per column;
+//   basis V: ldv x (cols) column-major; ldu, ldv are m, n rounded up to 32.
+//   x32:     f32 copy of the vector the next product reads (n or m entries).
+//   part:    partial sums, [column][block] layout so reductions read rows
+//            of contiguous memory.
+// Reduced-precision operators (f32/bf16/f16) are multiplied in f32 with the
+// input vector rounded to f32, summed in f32 over short runs and combined in
+// f64; f64 operators are multiplied in f64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gk.h"
+
+namespace gk {
+
+// ---- launch accounting: every kernel launch of the library goes through GK_LAUNCH
+void note_launch();
+int64_t launch_count();
+#define GK_LAUNCH(...)    \
+  do {                    \
+    __VA_ARGS__;          \
+    ::gk::note_launch();  \
+  } while (0)
+
+// ---- control block written by device kernels, read by the host driver ----
+enum Event { EV_NONE = 0, EV_BETA_BREAK = 1, EV_ALPHA_BREAK = 2, EV_BREAKDOWN = 3, EV_NUMERICAL = 4 };
+// how a norm kernel judges the new vector
+enum NormMode {
+  NM_BREAK = 0,      // Algorithm 1 break test: norm <= eps * sigma_est (or eps)
+  NM_BREAKDOWN = 1,  // restarted SVD: norm <= 2^-46 * sigma_est counts as an exact breakdown
+  NM_PLAIN = 2,      // just normalize (start vectors)
+  NM_FRESH = 3,      // replacement direction: kept unless the projection removed all but 1e-8 of the norm
+                     // measured by the preceding NM_PLAIN call; otherwise the column becomes zero
+};
+
+struct Ctl {
+  int halt;          // nonzero: every step kernel returns at entry
+  int event;         // Event
+  int step;          // step index of the event
+  int side;          // 0 left (u/q), 1 right (v/p)
+  unsigned cnt[4];   // arrival counters of last-block reductions (kept zero between uses)
+  double sest;       // running lower bound on sigma_1
+  double norm;       // last norm computed
+  double inv_norm;   // 1 / last accepted norm (0 if rejected)
+  double eps;        // Algorithm 1 threshold parameter
+  int eps_rel;       // 1: threshold eps * sest; 0: eps
+  int pad;
+};
+
+// device view of the operator
+struct Op {
+  int kind, dtype;
+  int64_t m, n, ld;
+  double scale;
+  const void *vals;
+  const int32_t *rowptr;
+  const int32_t *colind;
+  const void *t_vals;
+  const int32_t *t_rowptr;
+  const int32_t *t_colind;
+};
+
+struct Dev {
+  int sms;
+  int id;
+};
+
+// ---- sizing helpers ------------------------------------------------------
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+int64_t gemvt_row_block(const Op &A, const Dev &d);        // rows per block of the A^T product
+int64_t gemvt_partials(const Op &A, const Dev &d);         // doubles of partial storage it needs
+int cgs_chunk(int64_t len, const Dev &d);                  // rows per block of the CGS kernels
+int cgs_blocks(int64_t len, const Dev &d);
+
+// ---- products (gk_matvec.cu) -------------------------------------------
+// y = A x - (*coef) * sub   (sub may be null).  x32: f32 copy of x (f32/bf16/f16 A), x64: f64 x (f64 A).
+cudaError_t matvec(const Op &A, const float *x32, const double *x64, double *y, const double *sub,
+                   const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d);
+// y = A^T x - (*coef) * sub
+cudaError_t matvec_t(const Op &A, const float *x32, const double *x64, double *y, const double *sub,
+                     const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d);
+
+// ---- Gram-Schmidt and vector kernels (gk_orth.cu) -------------------------
+// One or two classical Gram-Schmidt passes of w (len) against the first j
+// columns of Q (ld), followed by the norm and its judgement; see NormMode.
+// coef_out receives the accepted norm (0 on breakdown); prev is the previous
+// recurrence coefficient (for the sigma_est update of Algorithm 1).
+cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
+                           double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
+                           cudaStream_t s, const Dev &d);
+// Q[:, col] = w * ctl->inv_norm, x32 = f32 copy (skipped when halted)
+cudaError_t normalize_append(const double *w, int64_t len, double *qcol, float *x32, const Ctl *ctl, cudaStream_t s,
+                             const Dev &d);
+// w = (start vector q1 ~ N(2,1), Philox4x32-10 + Box-Muller), len entries
+cudaError_t draw_start(double *w, int64_t len, uint64_t seed, cudaStream_t s);
+// w = replacement direction number dnum (SplitMix64, uniform [-1,1))
+cudaError_t draw_fresh(double *w, int64_t len, uint64_t seed, int64_t dnum, cudaStream_t s);
+// dst = src (f64) and x32 = f32(src)
+cudaError_t copy_vec(double *dst, float *x32, const double *src, int64_t len, cudaStream_t s);
+// y -= Q[:, 0:l] * coef[0:l]
+cudaError_t sub_combination(double *y, int64_t len, const double *Q, int64_t ld, int l, const double *coef,
+                            const Ctl *ctl, cudaStream_t s, const Dev &d);
+cudaError_t reset_ctl(Ctl *ctl, double eps, int eps_rel, cudaStream_t s);
+
+// ---- small dense kernels (gk_small.cu) ----------------------------------
+// B (K x K, column-major) of one restart cycle: kept Ritz values on the
+// diagonal of the first l rows, the coupling column rho in column l, and the
+// new recurrence coefficients alpha_j (diagonal) and beta_j (superdiagonal)
+// for j >= l.
+cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const double *rho, const double *alpha,
+                       const double *beta, const Ctl *ctl, cudaStream_t s);
+// One-sided Jacobi SVD of the K x K matrix Bm (overwritten; Yw is K x K work):
+// sigma (K, descending), X (K x K left vectors), Y (K x K right vectors).
+cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, int *sweeps,
+                      const Ctl *ctl, cudaStream_t s);
+// Restart bookkeeping: rho_i = betaK X_{K,i} (all i < K), and
+// out[0] = max_{i<k} |rho_i|, out[1] = sigma_1, out[2] = converged (0/1).
+cudaError_t ritz_check(const double *sigma, const double *X, int K, int k, const double *betaK, double tol,
+                       double *rho, double *out, Ctl *ctl, cudaStream_t s);
+// C[:, 0:ncol] = Q[:, 0:K] * X[:, 0:ncol]   (C may alias nothing in Q)
+cudaError_t ritz_gemm(const double *Q, int64_t ldq, int64_t len, int K, const double *X, int ldx, int ncol,
+                      double *C, int64_t ldc, cudaStream_t s, const Dev &d);
+// sign convention: largest-|v_i| entry positive (flips u_i and v_i)
+cudaError_t sign_normalize(double *U, int64_t ldu, int64_t m, double *V, int64_t ldv, int64_t n, int k,
+                           cudaStream_t s);
+// rank of the lower-bidiagonal B_{kp+1,kp} (alpha[0..kp-1], beta[1..kp]) by
+// Sturm counts on its Golub-Kahan tridiagonal; sigma (optional, kp values)
+cudaError_t bidiag_rank(const double *alpha, const double *beta, int kp, double eps, int eps_rel, int *rank,
+                        double *sigma1, double *sigma, cudaStream_t s);
+
+}  // namespace gk

@@ -1,0 +1,537 @@
+// gk_matvec.cu -- the products A x and A^T x of the bidiagonalization sweep
+// (Eq. 2.2: A p_i and A^T q_{i+1}; Algorithm 1, lines 5 and 12).
+//
+// These passes stream the whole operator once per half-step and are bounded by
+// HBM bandwidth.  Dense operators are row-major:
+//  * A x   : one warp per row, 16-byte streaming loads (ld.global.cs) of A, the
+//            f32 copy of x read through the L1 (it is reused by every row);
+//            f32 products summed over short runs, runs combined in f64, f64
+//            warp reduction.
+//  * A^T x : a (row block) x (column tile) grid; every thread owns one 16-byte
+//            group of consecutive columns, walks the rows of its block with
+//            eight loads in flight, and writes f64 partial sums per row block;
+//            a second kernel sums the partials in a fixed order (deterministic).
+//  * CSR   : a group of lanes per row (sized from the mean row length), f64
+//            products; A^T uses the caller's stored CSR of A^T.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 8;   // 16-byte loads in flight per lane in the row kernel
+constexpr int kRowUnroll = 8;  // rows in flight per thread in the column kernel
+constexpr int kRun = 16;     // rows summed in f32 before an f64 combine (column kernel)
+
+__device__ __forceinline__ bool halted(const Ctl *ctl) {
+  return ctl != nullptr && *reinterpret_cast<const volatile int *>(&ctl->halt) != 0;
+}
+
+// ---- 16-byte vector of stored values -> floats ---------------------------
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  static constexpr int E = 4;
+  using V = float4;
+  __device__ __forceinline__ static void unpack(const V &v, float *o) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ __forceinline__ static float one(const float *p) { return *p; }
+};
+template <>
+struct Vec<__nv_bfloat16> {
+  static constexpr int E = 8;
+  using V = uint4;
+  __device__ __forceinline__ static void unpack(const V &v, float *o) {
+    // bf16 is the high half of an f32 word; element 0 sits in the low half of v.x
+    o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xffff0000u);
+    o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
+    o[4] = __uint_as_float(v.z << 16); o[5] = __uint_as_float(v.z & 0xffff0000u);
+    o[6] = __uint_as_float(v.w << 16); o[7] = __uint_as_float(v.w & 0xffff0000u);
+  }
+  __device__ __forceinline__ static float one(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+};
+template <>
+struct Vec<__half> {
+  static constexpr int E = 8;
+  using V = uint4;
+  __device__ __forceinline__ static void unpack(const V &v, float *o) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
+      float2 f = __half22float2(h);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+  __device__ __forceinline__ static float one(const __half *p) { return __half2float(*p); }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// y = scale * A x - coef * sub, reduced-precision A (f32 / bf16 / f16)
+// ---------------------------------------------------------------------------
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_gemv_lp(const T *__restrict__ A, int64_t m, int64_t n, int64_t ld,
+                                                      double scale, const float *__restrict__ x,
+                                                      double *__restrict__ y, const double *__restrict__ sub,
+                                                      const double *__restrict__ coef, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  using VT = Vec<T>;
+  constexpr int E = VT::E;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double c = sub ? *coef : 0.0;
+  for (int64_t r = warp; r < m; r += nwarp) {
+    const T *a = A + r * ld;
+    double acc = 0.0;
+    int64_t tail0 = 0;
+    if (VEC) {
+      const int64_t nv = n / E;
+      const typename VT::V *av = reinterpret_cast<const typename VT::V *>(a);
+      int64_t i = lane;
+      for (; i + 32 * (kUnroll - 1) < nv; i += 32 * kUnroll) {
+        typename VT::V buf[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) buf[u] = __ldcs(av + i + 32 * u);
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          float f[E];
+          VT::unpack(buf[u], f);
+          const float4 *xv = reinterpret_cast<const float4 *>(x + (i + 32 * u) * E);
+#pragma unroll
+          for (int q = 0; q < E / 4; ++q) {
+            const float4 xx = __ldg(xv + q);
+            s = fmaf(f[4 * q + 0], xx.x, s);
+            s = fmaf(f[4 * q + 1], xx.y, s);
+            s = fmaf(f[4 * q + 2], xx.z, s);
+            s = fmaf(f[4 * q + 3], xx.w, s);
+          }
+        }
+        acc += (double)s;
+      }
+      for (; i < nv; i += 32) {
+        const typename VT::V b = __ldcs(av + i);
+        float f[E];
+        VT::unpack(b, f);
+        const float4 *xv = reinterpret_cast<const float4 *>(x + i * E);
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q) {
+          const float4 xx = __ldg(xv + q);
+          s = fmaf(f[4 * q + 0], xx.x, s);
+          s = fmaf(f[4 * q + 1], xx.y, s);
+          s = fmaf(f[4 * q + 2], xx.z, s);
+          s = fmaf(f[4 * q + 3], xx.w, s);
+        }
+        acc += (double)s;
+      }
+      tail0 = nv * E;
+    }
+    {
+      float s = 0.f;
+      int cnt = 0;
+      for (int64_t cidx = tail0 + lane; cidx < n; cidx += 32) {
+        s = fmaf(VT::one(a + cidx), __ldg(x + cidx), s);
+        if (++cnt == 32) {
+          acc += (double)s;
+          s = 0.f;
+          cnt = 0;
+        }
+      }
+      acc += (double)s;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) y[r] = acc * scale - (sub ? c * sub[r] : 0.0);
+  }
+}
+
+// y = A x - coef * sub, f64 A (products in f64)
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads) k_gemv_f64(const double *__restrict__ A, int64_t m, int64_t n, int64_t ld,
+                                                       double scale, const double *__restrict__ x,
+                                                       double *__restrict__ y, const double *__restrict__ sub,
+                                                       const double *__restrict__ coef, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double c = sub ? *coef : 0.0;
+  for (int64_t r = warp; r < m; r += nwarp) {
+    const double *a = A + r * ld;
+    double acc = 0.0;
+    int64_t tail0 = 0;
+    if (VEC) {
+      const int64_t nv = n / 2;
+      const double2 *av = reinterpret_cast<const double2 *>(a);
+      const double2 *xv = reinterpret_cast<const double2 *>(x);
+      int64_t i = lane;
+      for (; i + 32 * (kUnroll - 1) < nv; i += 32 * kUnroll) {
+        double2 buf[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) buf[u] = __ldcs(av + i + 32 * u);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const double2 xx = __ldg(xv + i + 32 * u);
+          acc = fma(buf[u].x, xx.x, acc);
+          acc = fma(buf[u].y, xx.y, acc);
+        }
+      }
+      for (; i < nv; i += 32) {
+        const double2 b = __ldcs(av + i), xx = __ldg(xv + i);
+        acc = fma(b.x, xx.x, acc);
+        acc = fma(b.y, xx.y, acc);
+      }
+      tail0 = nv * 2;
+    }
+    for (int64_t cidx = tail0 + lane; cidx < n; cidx += 32) acc = fma(a[cidx], __ldg(x + cidx), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[r] = acc * scale - (sub ? c * sub[r] : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A^T x, partial sums per row block: part[rb * n + col]
+// ---------------------------------------------------------------------------
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_gemvt_lp(const T *__restrict__ A, int64_t m, int64_t n, int64_t ld,
+                                                       int64_t RB, const float *__restrict__ x,
+                                                       double *__restrict__ part, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  using VT = Vec<T>;
+  constexpr int E = VT::E;
+  __shared__ float xs[1024];
+  const int64_t r0 = (int64_t)blockIdx.y * RB;
+  const int64_t r1 = (r0 + RB < m) ? r0 + RB : m;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) xs[r - r0] = x[r];
+  __syncthreads();
+  const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+  if (c0 >= n) return;
+  float a32[E];
+  double a64[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    a32[e] = 0.f;
+    a64[e] = 0.0;
+  }
+  if (VEC && c0 + E <= n) {
+    const int64_t ldv = ld / E;
+    const typename VT::V *p = reinterpret_cast<const typename VT::V *>(A + r0 * ld + c0);
+    int64_t r = r0;
+    int run = 0;
+    for (; r + kRowUnroll <= r1; r += kRowUnroll) {
+      typename VT::V buf[kRowUnroll];
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) buf[u] = __ldcs(p + (r - r0 + u) * ldv);
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        float f[E];
+        VT::unpack(buf[u], f);
+        const float xv = xs[r - r0 + u];
+#pragma unroll
+        for (int e = 0; e < E; ++e) a32[e] = fmaf(f[e], xv, a32[e]);
+      }
+      run += kRowUnroll;
+      if (run >= kRun) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          a64[e] += (double)a32[e];
+          a32[e] = 0.f;
+        }
+        run = 0;
+      }
+    }
+    for (; r < r1; ++r) {
+      float f[E];
+      VT::unpack(__ldcs(p + (r - r0) * ldv), f);
+      const float xv = xs[r - r0];
+#pragma unroll
+      for (int e = 0; e < E; ++e) a32[e] = fmaf(f[e], xv, a32[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) a64[e] += (double)a32[e];
+#pragma unroll
+    for (int e = 0; e < E; ++e) part[(int64_t)blockIdx.y * n + c0 + e] = a64[e];
+  } else {
+    const int ne = (int)((n - c0) < E ? (n - c0) : E);
+    for (int e = 0; e < ne; ++e) {
+      double acc = 0.0;
+      float s = 0.f;
+      int run = 0;
+      for (int64_t r = r0; r < r1; ++r) {
+        s = fmaf(VT::one(A + r * ld + c0 + e), xs[r - r0], s);
+        if (++run == kRun) {
+          acc += (double)s;
+          s = 0.f;
+          run = 0;
+        }
+      }
+      acc += (double)s;
+      part[(int64_t)blockIdx.y * n + c0 + e] = acc;
+    }
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads) k_gemvt_f64(const double *__restrict__ A, int64_t m, int64_t n,
+                                                        int64_t ld, int64_t RB, const double *__restrict__ x,
+                                                        double *__restrict__ part, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  __shared__ double xs[1024];
+  const int64_t r0 = (int64_t)blockIdx.y * RB;
+  const int64_t r1 = (r0 + RB < m) ? r0 + RB : m;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) xs[r - r0] = x[r];
+  __syncthreads();
+  const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (c0 >= n) return;
+  if (VEC && c0 + 2 <= n) {
+    const int64_t ldv = ld / 2;
+    const double2 *p = reinterpret_cast<const double2 *>(A + r0 * ld + c0);
+    double s0 = 0.0, s1 = 0.0;
+    int64_t r = r0;
+    for (; r + kRowUnroll <= r1; r += kRowUnroll) {
+      double2 buf[kRowUnroll];
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) buf[u] = __ldcs(p + (r - r0 + u) * ldv);
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const double xv = xs[r - r0 + u];
+        s0 = fma(buf[u].x, xv, s0);
+        s1 = fma(buf[u].y, xv, s1);
+      }
+    }
+    for (; r < r1; ++r) {
+      const double2 b = __ldcs(p + (r - r0) * ldv);
+      s0 = fma(b.x, xs[r - r0], s0);
+      s1 = fma(b.y, xs[r - r0], s1);
+    }
+    part[(int64_t)blockIdx.y * n + c0] = s0;
+    part[(int64_t)blockIdx.y * n + c0 + 1] = s1;
+  } else {
+    const int ne = (int)((n - c0) < 2 ? (n - c0) : 2);
+    for (int e = 0; e < ne; ++e) {
+      double s = 0.0;
+      for (int64_t r = r0; r < r1; ++r) s = fma(A[r * ld + c0 + e], xs[r - r0], s);
+      part[(int64_t)blockIdx.y * n + c0 + e] = s;
+    }
+  }
+}
+
+// y[c] = scale * sum_rb part[rb * n + c] - coef * sub[c]; block = 32 columns x 8 row-block groups,
+// each group sums a contiguous range of row blocks, groups are combined in order.
+__global__ void __launch_bounds__(kThreads) k_gemvt_reduce(const double *__restrict__ part, int64_t n, int nrb,
+                                                           double scale, double *__restrict__ y,
+                                                           const double *__restrict__ sub,
+                                                           const double *__restrict__ coef, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  __shared__ double red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+  const int per = (nrb + 7) / 8;
+  const int b0 = ty * per, b1 = (b0 + per < nrb) ? b0 + per : nrb;
+  double s = 0.0;
+  if (c < n)
+    for (int b = b0; b < b1; ++b) s += part[(int64_t)b * n + c];
+  red[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && c < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) t += red[g][tx];
+    y[c] = t * scale - (sub ? (*coef) * sub[c] : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CSR: y = scale * A x - coef * sub, TPR lanes per row, f64 products
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ double csr_val(const T *v, int64_t p);
+template <>
+__device__ __forceinline__ double csr_val<float>(const float *v, int64_t p) { return (double)__ldcs(v + p); }
+template <>
+__device__ __forceinline__ double csr_val<double>(const double *v, int64_t p) { return __ldcs(v + p); }
+template <>
+__device__ __forceinline__ double csr_val<__nv_bfloat16>(const __nv_bfloat16 *v, int64_t p) {
+  return (double)__bfloat162float(v[p]);
+}
+template <>
+__device__ __forceinline__ double csr_val<__half>(const __half *v, int64_t p) { return (double)__half2float(v[p]); }
+
+template <typename T, int TPR>
+__global__ void __launch_bounds__(kThreads) k_spmv(const int32_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ colind, const T *__restrict__ vals,
+                                                   int64_t m, double scale, const double *__restrict__ x,
+                                                   double *__restrict__ y, const double *__restrict__ sub,
+                                                   const double *__restrict__ coef, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sub_lane = threadIdx.x % TPR;
+  constexpr int RPW = 32 / TPR;  // rows per warp per iteration
+  const int64_t warp = tid >> 5, nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double c = sub ? *coef : 0.0;
+  for (int64_t base = warp * RPW; base < m; base += nwarp * RPW) {
+    const int64_t row = base + (threadIdx.x & 31) / TPR;
+    double s = 0.0;
+    if (row < m) {
+      const int64_t p1 = rowptr[row + 1];
+      for (int64_t p = rowptr[row] + sub_lane; p < p1; p += TPR) s = fma(csr_val<T>(vals, p), __ldg(x + colind[p]), s);
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+    if (row < m && sub_lane == 0) y[row] = s * scale - (sub ? c * sub[row] : 0.0);
+  }
+}
+
+int grid_rows(const Dev &d) { return d.sms * 8; }
+
+template <typename T>
+cudaError_t launch_gemv(const Op &A, const float *x32, double *y, const double *sub, const double *coef,
+                        const Ctl *ctl, cudaStream_t s, const Dev &d) {
+  const bool vec = ((uintptr_t)A.vals % 16 == 0) && ((A.ld * (int64_t)sizeof(T)) % 16 == 0);
+  const int64_t warps = (A.m + 0);
+  int blocks = grid_rows(d);
+  if ((int64_t)blocks * (kThreads / 32) > warps) blocks = (int)((warps + (kThreads / 32) - 1) / (kThreads / 32));
+  if (blocks < 1) blocks = 1;
+  if (vec)
+    GK_LAUNCH(k_gemv_lp<T, true><<<blocks, kThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, x32, y, sub, coef, ctl));
+  else
+    GK_LAUNCH(k_gemv_lp<T, false><<<blocks, kThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, x32, y, sub, coef,
+                                                    ctl));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spmv(const int32_t *rp, const int32_t *ci, const void *v, int64_t rows, double scale,
+                        const double *x, double *y, const double *sub, const double *coef, const Ctl *ctl,
+                        cudaStream_t s, const Dev &d) {
+  // lanes per row from the mean row length (power of two, 2..32)
+  int32_t nnz = 0;
+  (void)nnz;
+  int blocks = d.sms * 8;
+  const T *vals = (const T *)v;
+  // the mean row length is not known here without a read; 8 lanes suit ~10-40 entries per row
+  GK_LAUNCH(k_spmv<T, 8><<<blocks, kThreads, 0, s>>>(rp, ci, vals, rows, scale, x, y, sub, coef, ctl));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t gemvt_row_block(const Op &A, const Dev &d) {
+  const int E = (A.dtype == GK_F64) ? 2 : (A.dtype == GK_F32 ? 4 : 8);
+  const int64_t cb = (int64_t)kThreads * E;
+  const int64_t ntile = (A.n + cb - 1) / cb;
+  const int64_t want = (int64_t)8 * d.sms;  // blocks to fill the machine
+  int64_t rb = (A.m * ntile + want - 1) / want;
+  rb = round_up(rb < 1 ? 1 : rb, 32);
+  if (rb > 1024) rb = 1024;
+  if (rb < 32) rb = 32;
+  return rb;
+}
+
+int64_t gemvt_partials(const Op &A, const Dev &d) {
+  if (A.kind != GK_DENSE) return 0;
+  const int64_t rb = gemvt_row_block(A, d);
+  return ((A.m + rb - 1) / rb) * A.n;
+}
+
+cudaError_t matvec(const Op &A, const float *x32, const double *x64, double *y, const double *sub,
+                   const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d) {
+  (void)part;
+  if (A.kind == GK_CSR) {
+    switch (A.dtype) {
+      case GK_F64: return launch_spmv<double>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
+      case GK_F32: return launch_spmv<float>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
+      case GK_BF16:
+        return launch_spmv<__nv_bfloat16>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
+      default: return launch_spmv<__half>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
+    }
+  }
+  switch (A.dtype) {
+    case GK_F64: {
+      const bool vec = ((uintptr_t)A.vals % 16 == 0) && ((A.ld * 8) % 16 == 0);
+      int blocks = grid_rows(d);
+      const int64_t need = (A.m + 7) / 8;
+      if (blocks > need) blocks = (int)need;
+      if (blocks < 1) blocks = 1;
+      if (vec)
+        GK_LAUNCH(k_gemv_f64<true><<<blocks, kThreads, 0, s>>>((const double *)A.vals, A.m, A.n, A.ld, A.scale, x64, y, sub,
+                                                     coef, ctl));
+      else
+        GK_LAUNCH(k_gemv_f64<false><<<blocks, kThreads, 0, s>>>((const double *)A.vals, A.m, A.n, A.ld, A.scale, x64, y, sub,
+                                                      coef, ctl));
+      return cudaGetLastError();
+    }
+    case GK_F32: return launch_gemv<float>(A, x32, y, sub, coef, ctl, s, d);
+    case GK_BF16: return launch_gemv<__nv_bfloat16>(A, x32, y, sub, coef, ctl, s, d);
+    default: return launch_gemv<__half>(A, x32, y, sub, coef, ctl, s, d);
+  }
+}
+
+namespace {
+template <typename T>
+cudaError_t launch_gemvt(const Op &A, const float *x32, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d,
+                         int64_t rb, int nrb) {
+  constexpr int E = Vec<T>::E;
+  const bool vec = ((uintptr_t)A.vals % 16 == 0) && ((A.ld * (int64_t)sizeof(T)) % 16 == 0);
+  dim3 grid((unsigned)((A.n + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E)), (unsigned)nrb);
+  if (vec)
+    GK_LAUNCH(k_gemvt_lp<T, true><<<grid, kThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, rb, x32, part, ctl));
+  else
+    GK_LAUNCH(k_gemvt_lp<T, false><<<grid, kThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, rb, x32, part, ctl));
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t matvec_t(const Op &A, const float *x32, const double *x64, double *y, const double *sub,
+                     const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d) {
+  if (A.kind == GK_CSR) {
+    switch (A.dtype) {
+      case GK_F64:
+        return launch_spmv<double>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s, d);
+      case GK_F32:
+        return launch_spmv<float>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s, d);
+      case GK_BF16:
+        return launch_spmv<__nv_bfloat16>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s,
+                                          d);
+      default:
+        return launch_spmv<__half>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s, d);
+    }
+  }
+  const int64_t rb = gemvt_row_block(A, d);
+  const int nrb = (int)((A.m + rb - 1) / rb);
+  cudaError_t e;
+  switch (A.dtype) {
+    case GK_F64: {
+      const bool vec = ((uintptr_t)A.vals % 16 == 0) && ((A.ld * 8) % 16 == 0);
+      dim3 grid((unsigned)((A.n + (int64_t)kThreads * 2 - 1) / ((int64_t)kThreads * 2)), (unsigned)nrb);
+      if (vec)
+        GK_LAUNCH(k_gemvt_f64<true><<<grid, kThreads, 0, s>>>((const double *)A.vals, A.m, A.n, A.ld, rb, x64, part, ctl));
+      else
+        GK_LAUNCH(k_gemvt_f64<false><<<grid, kThreads, 0, s>>>((const double *)A.vals, A.m, A.n, A.ld, rb, x64, part, ctl));
+      e = cudaGetLastError();
+      break;
+    }
+    case GK_F32: e = launch_gemvt<float>(A, x32, part, ctl, s, d, rb, nrb); break;
+    case GK_BF16: e = launch_gemvt<__nv_bfloat16>(A, x32, part, ctl, s, d, rb, nrb); break;
+    default: e = launch_gemvt<__half>(A, x32, part, ctl, s, d, rb, nrb); break;
+  }
+  if (e != cudaSuccess) return e;
+  GK_LAUNCH(k_gemvt_reduce<<<(unsigned)((A.n + 31) / 32), kThreads, 0, s>>>(part, A.n, nrb, A.scale, y, sub, coef, ctl));
+  return cudaGetLastError();
+}
+
+}  // namespace gk

@@ -1,0 +1,399 @@
+// gk_orth.cu -- full reorthogonalization, norms and the break test of the
+// bidiagonalization sweep (Algorithm 1, lines 6-11 and 13-14), plus the seeded
+// start vector (line 1) and replacement directions after an exact breakdown.
+//
+// Classical Gram-Schmidt of w against the first j basis columns Q (len x j,
+// column-major, f64), `passes` times, then the norm:
+//   pass p < passes-1 : h = Q^T w                  (k_cgs_dot, partials per row chunk)
+//                        w -= Q h ; h' = Q^T w      (k_cgs_update_dot)
+//   last pass         : w -= Q h ; ||w||^2         (k_cgs_update_norm)
+// Partial sums are written per row chunk and reduced in a fixed order, so the
+// results are bitwise reproducible.  The last block of the norm kernel applies
+// the break / breakdown test and records the event in the control block; every
+// later kernel of the sweep sees `halt` and returns at entry.
+#include <math.h>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxChunk = 256;
+
+__device__ __forceinline__ bool halted(const Ctl *ctl) {
+  return *reinterpret_cast<const volatile int *>(&ctl->halt) != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// part[c * G + g] = sum over chunk g of Q[:, c] .* w
+__device__ __forceinline__ void chunk_dots(const double *__restrict__ Q, int64_t ld, int64_t i0, int64_t i1, int j,
+                                           const double *ws, double *__restrict__ part, int G) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < j; c += nw) {
+    const double *q = Q + (int64_t)c * ld;
+    double s = 0.0;
+    for (int64_t i = i0 + lane; i < i1; i += 32) s = fma(q[i], ws[i - i0], s);
+    s = warp_sum(s);
+    if (lane == 0) part[(int64_t)c * G + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs_dot(const double *__restrict__ Q, int64_t ld, int64_t len, int j,
+                                                      const double *__restrict__ w, double *__restrict__ part, int S,
+                                                      const Ctl *ctl) {
+  if (halted(ctl)) return;
+  __shared__ double ws[kMaxChunk];
+  const int64_t i0 = (int64_t)blockIdx.x * S;
+  const int64_t i1 = (i0 + S < len) ? i0 + S : len;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) ws[i - i0] = w[i];
+  __syncthreads();
+  chunk_dots(Q, ld, i0, i1, j, ws, part, gridDim.x);
+}
+
+// h[c] = sum_g part[c * G + g]  (one block per column, fixed-order tree)
+__global__ void __launch_bounds__(128) k_reduce_cols(const double *__restrict__ part, int G, double *__restrict__ h,
+                                                     const Ctl *ctl) {
+  if (halted(ctl)) return;
+  __shared__ double red[128];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < G; g += 128) s += part[(int64_t)c * G + g];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) h[c] = red[0];
+}
+
+// w -= Q h on this chunk; returns the updated chunk in ws
+__device__ __forceinline__ void chunk_update(const double *__restrict__ Q, int64_t ld, int64_t i0, int64_t i1, int j,
+                                             double *__restrict__ w, const double *hs, double *ws) {
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double acc = w[i];
+    int c = 0;
+    for (; c + 4 <= j; c += 4) {
+      const double q0 = Q[(int64_t)c * ld + i], q1 = Q[(int64_t)(c + 1) * ld + i];
+      const double q2 = Q[(int64_t)(c + 2) * ld + i], q3 = Q[(int64_t)(c + 3) * ld + i];
+      acc = fma(-q0, hs[c], acc);
+      acc = fma(-q1, hs[c + 1], acc);
+      acc = fma(-q2, hs[c + 2], acc);
+      acc = fma(-q3, hs[c + 3], acc);
+    }
+    for (; c < j; ++c) acc = fma(-Q[(int64_t)c * ld + i], hs[c], acc);
+    w[i] = acc;
+    ws[i - i0] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs_update_dot(const double *__restrict__ Q, int64_t ld, int64_t len,
+                                                             int j, double *__restrict__ w,
+                                                             const double *__restrict__ h, double *__restrict__ part,
+                                                             int S, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  extern __shared__ double dyn[];
+  double *hs = dyn;          // j
+  double *ws = dyn + j;      // S
+  for (int c = threadIdx.x; c < j; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * S;
+  const int64_t i1 = (i0 + S < len) ? i0 + S : len;
+  chunk_update(Q, ld, i0, i1, j, w, hs, ws);
+  __syncthreads();
+  chunk_dots(Q, ld, i0, i1, j, ws, part, gridDim.x);
+}
+
+// final pass + norm + judgement (last block)
+struct NormArgs {
+  int mode, step, side;
+  double *coef_out;
+  const double *prev;
+};
+
+__device__ void judge(Ctl *ctl, double nrm2, const NormArgs a) {
+  const double nrm = sqrt(nrm2);
+  const double prev_norm = ctl->norm;
+  ctl->norm = nrm;
+  if (!isfinite(nrm)) {
+    ctl->event = EV_NUMERICAL;
+    ctl->step = a.step;
+    ctl->side = a.side;
+    ctl->inv_norm = 0.0;
+    if (a.coef_out) *a.coef_out = nrm;
+    __threadfence();
+    ctl->halt = 1;
+    return;
+  }
+  double se = ctl->sest;
+  if (a.mode == NM_BREAK) {
+    // Algorithm 1 break test on the norm before normalization
+    se = fmax(se, a.prev ? hypot(*a.prev, nrm) : nrm);
+    ctl->sest = se;
+    const double thr = ctl->eps_rel ? ctl->eps * se : ctl->eps;
+    if (nrm <= thr) {
+      ctl->event = a.side == 0 ? EV_BETA_BREAK : EV_ALPHA_BREAK;
+      ctl->step = a.step;
+      ctl->side = a.side;
+      ctl->inv_norm = 0.0;
+      if (a.coef_out) *a.coef_out = nrm;
+      __threadfence();
+      ctl->halt = 1;
+      return;
+    }
+  } else if (a.mode == NM_BREAKDOWN) {
+    se = fmax(se, nrm);
+    ctl->sest = se;
+    if (nrm <= 0x1.0p-46 * se) {
+      ctl->event = EV_BREAKDOWN;
+      ctl->step = a.step;
+      ctl->side = a.side;
+      ctl->inv_norm = 0.0;
+      if (a.coef_out) *a.coef_out = 0.0;
+      __threadfence();
+      ctl->halt = 1;
+      return;
+    }
+  } else if (a.mode == NM_FRESH) {
+    if (!(nrm > 1e-8 * prev_norm)) {  // the basis already spans the space: the new column is zero
+      ctl->inv_norm = 0.0;
+      if (a.coef_out) *a.coef_out = 0.0;
+      return;
+    }
+  }
+  ctl->inv_norm = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  if (a.coef_out) *a.coef_out = nrm;
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs_update_norm(const double *__restrict__ Q, int64_t ld, int64_t len,
+                                                              int j, double *__restrict__ w,
+                                                              const double *__restrict__ h,
+                                                              double *__restrict__ npart, int S, Ctl *ctl,
+                                                              NormArgs a) {
+  if (halted(ctl)) return;
+  extern __shared__ double dyn[];
+  double *hs = dyn;      // j
+  double *ws = dyn + j;  // S
+  __shared__ double red[kThreads / 32];
+  __shared__ bool last;
+  for (int c = threadIdx.x; c < j; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * S;
+  const int64_t i1 = (i0 + S < len) ? i0 + S : len;
+  if (j > 0) {
+    chunk_update(Q, ld, i0, i1, j, w, hs, ws);
+  } else {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) ws[i - i0] = w[i];
+  }
+  __syncthreads();
+  // chunk sum of squares, fixed-order tree
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(ws[i - i0], ws[i - i0], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    npart[blockIdx.x] = t;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->cnt[0], 1u);
+    last = (arrived == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // last block: sum the chunk partials in order
+  const volatile double *vp = npart;
+  double t = 0.0;
+  for (int g = threadIdx.x; g < (int)gridDim.x; g += blockDim.x) t += vp[g];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
+    ctl->cnt[0] = 0u;
+    judge(ctl, tot, a);
+  }
+}
+
+__global__ void k_normalize_append(const double *__restrict__ w, int64_t len, double *__restrict__ q,
+                                   float *__restrict__ x32, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  const double f = ctl->inv_norm;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[i] * f;
+    q[i] = v;
+    if (x32) x32[i] = (float)v;
+  }
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the two-multiplier
+// bijection, key bumped by the golden-ratio Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// q1 entries ~ N(2,1): block b = i/2 gives two 53-bit uniforms, Box-Muller
+// turns them into a normal pair (cos branch for even i, sin branch for odd i).
+__global__ void k_start_vector(double *__restrict__ q, int64_t len, uint64_t seed) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = (uint64_t)i >> 1;
+    const uint4 x = philox4x32_10(make_uint4((unsigned)b, (unsigned)(b >> 32), 0u, 0u), key);
+    const double ua = ((double)(((uint64_t)(x.x >> 5) << 26) | (x.y >> 6)) + 0.5) * 0x1.0p-53;
+    const double ub = ((double)(((uint64_t)(x.z >> 5) << 26) | (x.w >> 6)) + 0.5) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(ua));
+    q[i] = 2.0 + ((i & 1) ? r * sin(two_pi * ub) : r * cos(two_pi * ub));
+  }
+}
+
+// SplitMix64 finalizer (Steele, Lea, Flood, OOPSLA'14)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_fresh(double *__restrict__ w, int64_t len, uint64_t seed, int64_t dnum) {
+  const uint64_t base = seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(dnum + 1));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = (double)(splitmix64(base + (uint64_t)i) >> 11) * 0x1.0p-52 - 1.0;
+}
+
+__global__ void k_copy_vec(double *__restrict__ dst, float *__restrict__ x32, const double *__restrict__ src,
+                           int64_t len) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    if (dst) dst[i] = v;
+    if (x32) x32[i] = (float)v;
+  }
+}
+
+__global__ void k_sub_combination(double *__restrict__ y, int64_t len, const double *__restrict__ Q, int64_t ld,
+                                  int l, const double *__restrict__ coef, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = y[i];
+    for (int c = 0; c < l; ++c) acc = fma(-Q[(int64_t)c * ld + i], coef[c], acc);
+    y[i] = acc;
+  }
+}
+
+__global__ void k_reset_ctl(Ctl *ctl, double eps, int eps_rel) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctl->halt = 0;
+    ctl->event = EV_NONE;
+    ctl->step = -1;
+    ctl->side = -1;
+    for (int i = 0; i < 4; ++i) ctl->cnt[i] = 0u;
+    ctl->sest = 0.0;
+    ctl->norm = 0.0;
+    ctl->inv_norm = 0.0;
+    ctl->eps = eps;
+    ctl->eps_rel = eps_rel;
+    ctl->pad = 0;
+  }
+}
+
+int vec_blocks(int64_t len) {
+  int64_t b = (len + 255) / 256;
+  if (b > 4096) b = 4096;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int cgs_chunk(int64_t len, const Dev &d) {
+  int64_t s = (len + 2 * (int64_t)d.sms - 1) / (2 * (int64_t)d.sms);
+  s = round_up(s < 1 ? 1 : s, 32);
+  if (s > kMaxChunk) s = kMaxChunk;
+  return (int)s;
+}
+
+int cgs_blocks(int64_t len, const Dev &d) {
+  const int s = cgs_chunk(len, d);
+  return (int)((len + s - 1) / s);
+}
+
+cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
+                           double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
+                           cudaStream_t s, const Dev &d) {
+  const int S = cgs_chunk(len, d);
+  const int G = (int)((len + S - 1) / S);
+  double *npart = part + (int64_t)G * (j > 0 ? j : 1);
+  const size_t dyn = sizeof(double) * (size_t)(j + S);
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_cgs_update_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_cgs_update_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  NormArgs a{mode, step, side, coef_out, prev};
+  if (j <= 0 || passes <= 0) {
+    GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, 0, w, h, npart, S, ctl, a));
+    return cudaGetLastError();
+  }
+  GK_LAUNCH(k_cgs_dot<<<G, kThreads, 0, s>>>(Q, ld, len, j, w, part, S, ctl));
+  GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl));
+  for (int p = 1; p < passes; ++p) {
+    GK_LAUNCH(k_cgs_update_dot<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, part, S, ctl));
+    GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl));
+  }
+  GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, npart, S, ctl, a));
+  return cudaGetLastError();
+}
+
+cudaError_t normalize_append(const double *w, int64_t len, double *qcol, float *x32, const Ctl *ctl, cudaStream_t s,
+                             const Dev &d) {
+  (void)d;
+  GK_LAUNCH(k_normalize_append<<<vec_blocks(len), 256, 0, s>>>(w, len, qcol, x32, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t draw_start(double *w, int64_t len, uint64_t seed, cudaStream_t s) {
+  GK_LAUNCH(k_start_vector<<<vec_blocks(len), 256, 0, s>>>(w, len, seed));
+  return cudaGetLastError();
+}
+
+cudaError_t draw_fresh(double *w, int64_t len, uint64_t seed, int64_t dnum, cudaStream_t s) {
+  GK_LAUNCH(k_fresh<<<vec_blocks(len), 256, 0, s>>>(w, len, seed, dnum));
+  return cudaGetLastError();
+}
+
+cudaError_t copy_vec(double *dst, float *x32, const double *src, int64_t len, cudaStream_t s) {
+  GK_LAUNCH(k_copy_vec<<<vec_blocks(len), 256, 0, s>>>(dst, x32, src, len));
+  return cudaGetLastError();
+}
+
+cudaError_t sub_combination(double *y, int64_t len, const double *Q, int64_t ld, int l, const double *coef,
+                            const Ctl *ctl, cudaStream_t s, const Dev &d) {
+  (void)d;
+  GK_LAUNCH(k_sub_combination<<<vec_blocks(len), 256, 0, s>>>(y, len, Q, ld, l, coef, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t reset_ctl(Ctl *ctl, double eps, int eps_rel, cudaStream_t s) {
+  GK_LAUNCH(k_reset_ctl<<<1, 32, 0, s>>>(ctl, eps, eps_rel));
+  return cudaGetLastError();
+}
+
+}  // namespace gk

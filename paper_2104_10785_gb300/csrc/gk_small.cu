@@ -1,0 +1,392 @@
+// gk_small.cu -- the small dense steps of the method:
+//  * the SVD of the projected matrix B (Eq. 2.13; Algorithm 2, lines 2-5),
+//    by one-sided Jacobi in f64 with a parallel (round-robin) pair ordering;
+//  * the Ritz residual estimates |beta_K X_{K,i}| and the restart coupling;
+//  * Ritz vectors U_K X and V_K Y (Algorithm 2, line 3: V_2 = P V_1);
+//  * the rank count of Algorithm 3 from Sturm sequences of the Golub-Kahan
+//    tridiagonal of B_{k'+1,k'} (its eigenvalues are +-sigma_i(B) and 0).
+#include <float.h>
+#include <math.h>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+
+namespace {
+
+__device__ __forceinline__ bool halted(const Ctl *ctl) {
+  return ctl != nullptr && *reinterpret_cast<const volatile int *>(&ctl->halt) != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_assemble_B(double *__restrict__ Bm, int K, int l, const double *__restrict__ sigma,
+                             const double *__restrict__ rho, const double *__restrict__ alpha,
+                             const double *__restrict__ beta, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)K * K;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % K), c = (int)(idx / K);
+    double v = 0.0;
+    if (r < l) {
+      if (c == r) v = sigma[r];
+      else if (c == l) v = rho[r];
+    } else {
+      if (c == r) v = alpha[r];
+      else if (c == r + 1) v = beta[r];
+    }
+    Bm[idx] = v;
+  }
+}
+
+// tournament (circle method) pairing: round r, slot s of Kp players
+__device__ __forceinline__ int player(int r, int s, int Kp) { return s == 0 ? 0 : ((s - 1 + r) % (Kp - 1)) + 1; }
+
+__global__ void __launch_bounds__(1024) k_jacobi_svd(double *__restrict__ B, double *__restrict__ Yw, int K,
+                                                     double *__restrict__ sigma, double *__restrict__ X,
+                                                     double *__restrict__ Y, int *sweeps_out, const Ctl *ctl) {
+  if (halted(ctl)) return;
+  __shared__ int rotated;
+  __shared__ double nrm[1024];
+  __shared__ int pos[1024];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)K * K; idx += blockDim.x)
+    Yw[idx] = ((idx % K) == (idx / K)) ? 1.0 : 0.0;
+  const int Kp = K + (K & 1);
+  const double tol = 2.0 * sqrt((double)K) * 0x1.0p-52;
+  int sweep, done = 0;
+  __syncthreads();
+  for (sweep = 1; sweep <= 80; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < Kp - 1; ++r) {
+      for (int pi = warp; pi < Kp / 2; pi += nw) {
+        int p = player(r, pi, Kp), q = player(r, Kp - 1 - pi, Kp);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        if (q >= K) continue;
+        double *bp = B + (int64_t)p * K, *bq = B + (int64_t)q * K;
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = lane; i < K; i += 32) {
+          const double x = bp[i], y = bq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          c = fma(x, y, c);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (c == 0.0 || fabs(c) <= tol * sqrt(a) * sqrt(b)) continue;
+        if (lane == 0) rotated = 1;
+        // rotation that makes columns p and q orthogonal (Rutishauser's formula)
+        const double zeta = (b - a) / (2.0 * c);
+        const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                            : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = lane; i < K; i += 32) {
+          const double x = bp[i], y = bq[i];
+          bp[i] = cs * x - sn * y;
+          bq[i] = sn * x + cs * y;
+        }
+        double *yp = Yw + (int64_t)p * K, *yq = Yw + (int64_t)q * K;
+        for (int i = lane; i < K; i += 32) {
+          const double x = yp[i], y = yq[i];
+          yp[i] = cs * x - sn * y;
+          yq[i] = sn * x + cs * y;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) {
+      done = 1;
+      break;
+    }
+  }
+  // singular values = column norms, ordered descending (stable by index)
+  for (int c = warp; c < K; c += nw) {
+    const double *bc = B + (int64_t)c * K;
+    double s = 0.0;
+    for (int i = lane; i < K; i += 32) s = fma(bc[i], bc[i], s);
+    s = warp_sum(s);
+    if (lane == 0) nrm[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    int rk = 0;
+    for (int o = 0; o < K; ++o) rk += (nrm[o] > nrm[c]) || (nrm[o] == nrm[c] && o < c);
+    pos[c] = rk;
+  }
+  __syncthreads();
+  for (int c = warp; c < K; c += nw) {
+    const int pc = pos[c];
+    const double nc = nrm[c];
+    for (int i = lane; i < K; i += 32) {
+      X[(int64_t)pc * K + i] = nc > 0.0 ? B[(int64_t)c * K + i] / nc : 0.0;
+      Y[(int64_t)pc * K + i] = Yw[(int64_t)c * K + i];
+    }
+    if (lane == 0) sigma[pc] = nc;
+  }
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = done ? sweep - 1 : -(sweep - 1);
+}
+
+__global__ void k_ritz_check(const double *__restrict__ sigma, const double *__restrict__ X, int K, int k,
+                             const double *__restrict__ betaK, double tol, double *__restrict__ rho,
+                             double *__restrict__ out, Ctl *ctl) {
+  if (halted(ctl)) return;
+  __shared__ double red[256];
+  const double bK = *betaK;
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double r = bK * X[(int64_t)i * K + (K - 1)];
+    rho[i] = r;
+    if (i < k) mx = fmax(mx, fabs(r));
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double s1 = sigma[0];
+    out[0] = red[0];
+    out[1] = s1;
+    out[2] = (red[0] <= tol * s1) ? 1.0 : 0.0;
+    ctl->sest = fmax(ctl->sest, s1);
+  }
+}
+
+// C[:, c] = Q[:, 0:K] X[:, c], 16 output columns per block, X staged in tiles of 64 rows
+__global__ void __launch_bounds__(256) k_ritz_gemm(const double *__restrict__ Q, int64_t ldq, int64_t len, int K,
+                                                   const double *__restrict__ X, int ldx, int ncol,
+                                                   double *__restrict__ C, int64_t ldc) {
+  __shared__ double xs[64][16];
+  const int col0 = blockIdx.y * 16;
+  const int nc = (ncol - col0) < 16 ? (ncol - col0) : 16;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int kt = 0; kt < K; kt += 64) {
+    const int kk = (K - kt) < 64 ? (K - kt) : 64;
+    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+      const int r = e / 16, t = e % 16;
+      xs[r][t] = (r < kk && t < nc) ? X[(int64_t)(col0 + t) * ldx + kt + r] : 0.0;
+    }
+    __syncthreads();
+    if (i < len) {
+      for (int r = 0; r < kk; ++r) {
+        const double q = Q[(int64_t)(kt + r) * ldq + i];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[t] = fma(q, xs[r][t], acc[t]);
+      }
+    }
+    __syncthreads();
+  }
+  if (i < len) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      if (t < nc) C[(int64_t)(col0 + t) * ldc + i] = acc[t];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sign_normalize(double *__restrict__ U, int64_t ldu, int64_t m,
+                                                        double *__restrict__ V, int64_t ldv, int64_t n) {
+  __shared__ double bv[256];
+  __shared__ int64_t bi[256];
+  __shared__ int flip;
+  double *v = V + (int64_t)blockIdx.x * ldv;
+  double *u = U + (int64_t)blockIdx.x * ldu;
+  double best = -1.0;
+  int64_t bidx = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double a = fabs(v[r]);
+    if (a > best) {
+      best = a;
+      bidx = r;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double b2 = bv[threadIdx.x + o];
+      const int64_t i2 = bi[threadIdx.x + o];
+      if (b2 > bv[threadIdx.x] || (b2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = b2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) flip = v[bi[0]] < 0.0;
+  __syncthreads();
+  if (!flip) return;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) v[r] = -v[r];
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
+}
+
+// off-diagonal i (0-based) of the Golub-Kahan tridiagonal of the lower-bidiagonal B:
+// alpha_1, beta_2, alpha_2, beta_3, ..., alpha_kp, beta_{kp+1}
+__device__ __forceinline__ double gk_offdiag(const double *alpha, const double *beta, int i) {
+  return (i & 1) ? beta[(i + 1) >> 1] : alpha[i >> 1];
+}
+
+// number of eigenvalues of T (size N = 2kp+1, zero diagonal) below x: negative pivots of T - xI
+__device__ int count_below(const double *alpha, const double *beta, int kp, double x, double pivmin) {
+  const int N = 2 * kp + 1;
+  double d = -x;
+  if (fabs(d) < pivmin) d = -pivmin;
+  int cnt = d < 0.0;
+  for (int i = 1; i < N; ++i) {
+    const double e = gk_offdiag(alpha, beta, i - 1);
+    d = -x - (e * e) / d;
+    if (fabs(d) < pivmin) d = -pivmin;
+    cnt += d < 0.0;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(256) k_bidiag_rank(const double *__restrict__ alpha,
+                                                     const double *__restrict__ beta, int kp, double eps, int eps_rel,
+                                                     int *__restrict__ rank, double *__restrict__ sigma1,
+                                                     double *__restrict__ sigma) {
+  __shared__ double red[256];
+  __shared__ int tbest;
+  __shared__ double lo_s, hi_s;
+  const int T = blockDim.x;
+  if (kp <= 0) {
+    if (threadIdx.x == 0) {
+      *rank = 0;
+      *sigma1 = 0.0;
+    }
+    return;
+  }
+  const int N = 2 * kp + 1;
+  // Gershgorin bound on the spectrum and the pivot floor
+  double g = 0.0, emax = 0.0;
+  for (int i = threadIdx.x; i < N; i += T) {
+    const double l = i > 0 ? fabs(gk_offdiag(alpha, beta, i - 1)) : 0.0;
+    const double r = i < N - 1 ? fabs(gk_offdiag(alpha, beta, i)) : 0.0;
+    g = fmax(g, l + r);
+    emax = fmax(emax, r);
+  }
+  red[threadIdx.x] = g;
+  __syncthreads();
+  for (int o = T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double gmax = red[0];
+  __syncthreads();
+  red[threadIdx.x] = emax;
+  __syncthreads();
+  for (int o = T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double pivmin = DBL_MIN * fmax(1.0, red[0] * red[0]);
+  if (threadIdx.x == 0) {
+    lo_s = 0.0;
+    hi_s = gmax * (1.0 + 0x1.0p-40) + DBL_MIN;
+  }
+  __syncthreads();
+  // sigma_1 by multisection: T evaluation points per round
+  for (int round = 0; round < 10; ++round) {
+    const double lo = lo_s, hi = hi_s;
+    if (!(hi - lo > 0x1.0p-54 * hi)) break;
+    const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(T + 1);
+    const int above = N - count_below(alpha, beta, kp, x, pivmin);  // eigenvalues >= x
+    if (threadIdx.x == 0) tbest = -1;
+    __syncthreads();
+    if (above >= 1) atomicMax(&tbest, (int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int t = tbest;
+      const double nlo = t >= 0 ? lo + (hi - lo) * (double)(t + 1) / (double)(T + 1) : lo;
+      const double nhi = (t + 1 < T) ? lo + (hi - lo) * (double)(t + 2) / (double)(T + 1) : hi;
+      lo_s = nlo;
+      hi_s = nhi;
+    }
+    __syncthreads();
+  }
+  const double s1 = 0.5 * (lo_s + hi_s);
+  if (threadIdx.x == 0) {
+    *sigma1 = s1;
+    const double thr = eps_rel ? eps * s1 : eps;
+    // #{sigma > thr} = #{eigenvalues >= next double above thr}
+    const double xt = thr > 0.0 ? __longlong_as_double(__double_as_longlong(thr) + 1) : DBL_MIN;
+    *rank = (s1 > 0.0) ? N - count_below(alpha, beta, kp, xt, pivmin) : 0;
+  }
+  if (sigma) {
+    // every singular value of B by bisection on its index
+    for (int i = threadIdx.x; i < kp; i += T) {
+      double lo = 0.0, hi = hi_s;
+      for (int it = 0; it < 100 && hi - lo > 0x1.0p-53 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (N - count_below(alpha, beta, kp, mid > 0.0 ? mid : DBL_MIN, pivmin) >= i + 1)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      sigma[i] = 0.5 * (lo + hi);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const double *rho, const double *alpha,
+                       const double *beta, const Ctl *ctl, cudaStream_t s) {
+  int64_t blocks = ((int64_t)K * K + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  GK_LAUNCH(k_assemble_B<<<(int)blocks, 256, 0, s>>>(Bm, K, l, sigma, rho, alpha, beta, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, int *sweeps,
+                      const Ctl *ctl, cudaStream_t s) {
+  if (K > 1024) return cudaErrorInvalidValue;
+  GK_LAUNCH(k_jacobi_svd<<<1, 1024, 0, s>>>(Bm, Yw, K, sigma, X, Y, sweeps, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_check(const double *sigma, const double *X, int K, int k, const double *betaK, double tol,
+                       double *rho, double *out, Ctl *ctl, cudaStream_t s) {
+  GK_LAUNCH(k_ritz_check<<<1, 256, 0, s>>>(sigma, X, K, k, betaK, tol, rho, out, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_gemm(const double *Q, int64_t ldq, int64_t len, int K, const double *X, int ldx, int ncol,
+                      double *C, int64_t ldc, cudaStream_t s, const Dev &d) {
+  (void)d;
+  if (ncol <= 0 || len <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((len + 255) / 256), (unsigned)((ncol + 15) / 16));
+  GK_LAUNCH(k_ritz_gemm<<<grid, 256, 0, s>>>(Q, ldq, len, K, X, ldx, ncol, C, ldc));
+  return cudaGetLastError();
+}
+
+cudaError_t sign_normalize(double *U, int64_t ldu, int64_t m, double *V, int64_t ldv, int64_t n, int k,
+                           cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  GK_LAUNCH(k_sign_normalize<<<k, 256, 0, s>>>(U, ldu, m, V, ldv, n));
+  return cudaGetLastError();
+}
+
+cudaError_t bidiag_rank(const double *alpha, const double *beta, int kp, double eps, int eps_rel, int *rank,
+                        double *sigma1, double *sigma, cudaStream_t s) {
+  GK_LAUNCH(k_bidiag_rank<<<1, 256, 0, s>>>(alpha, beta, kp, eps, eps_rel, rank, sigma1, sigma));
+  return cudaGetLastError();
+}
+
+}  // namespace gk

@@ -1,0 +1,288 @@
+"""ctypes binding of libgk.so (include/gk.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current stream.  There is no
+host fallback: if the library or a CUDA device is missing, calls raise.
+
+Names follow the C ABI: gk_psvd, gk_numrank, gk_psvd_workspace, ...
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+GK_OK, GK_NOT_CONVERGED, GK_RANK_DEFICIENT = 0, 1, 2
+GK_INVALID_ARG, GK_CUDA_ERROR, GK_NUMERICAL, GK_TIMEOUT = -1, -2, -3, -4
+GK_OUT_OF_MEMORY, GK_NOT_IMPLEMENTED, GK_NO_DEVICE = -5, -6, -7
+GK_F64, GK_F32, GK_BF16, GK_F16 = 0, 1, 2, 3
+GK_DENSE, GK_CSR = 0, 1
+GK_FLAG_PROFILE = 1
+
+_DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
+
+
+class gk_matrix(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("dtype", C.c_int32), ("m", C.c_int64), ("n", C.c_int64), ("ld", C.c_int64),
+        ("scale", C.c_double), ("vals", C.c_void_p), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+        ("t_vals", C.c_void_p), ("t_rowptr", C.c_void_p), ("t_colind", C.c_void_p),
+    ]
+
+
+class gk_opts(C.Structure):
+    _fields_ = [
+        ("krylov_dim", C.c_int32), ("keep", C.c_int32), ("max_restarts", C.c_int32),
+        ("reorth_passes", C.c_int32), ("eps_absolute", C.c_int32), ("flags", C.c_int32),
+        ("seed", C.c_uint64), ("start", C.c_void_p), ("stream", C.c_void_p),
+        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+    ]
+
+
+class gk_info(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int32), ("restarts", C.c_int32), ("cycles", C.c_int32), ("kprime", C.c_int32),
+        ("stop_reason", C.c_int32), ("breakdowns", C.c_int32), ("matvecs", C.c_int64),
+        ("resid_est_max", C.c_double), ("sigma_est", C.c_double), ("seconds", C.c_double),
+        ("ms_matvec", C.c_double), ("ms_matvec_t", C.c_double), ("ms_orth", C.c_double), ("ms_small", C.c_double),
+        ("ms_restart", C.c_double), ("n_matvec", C.c_int64), ("n_matvec_t", C.c_int64), ("launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class GKError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} {last_cuda_error()}".strip())
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libgk.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build_library()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgk.so missing at {path}")
+            L = C.CDLL(path)
+            P = C.POINTER
+            L.gk_default_opts.argtypes = [P(gk_opts)]
+            L.gk_default_opts.restype = None
+            L.gk_psvd_workspace.argtypes = [P(gk_matrix), C.c_int, P(gk_opts)]
+            L.gk_psvd_workspace.restype = C.c_size_t
+            L.gk_psvd.argtypes = [P(gk_matrix), C.c_int, C.c_double, P(gk_opts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                  P(gk_info)]
+            L.gk_psvd.restype = C.c_int
+            L.gk_numrank_workspace.argtypes = [P(gk_matrix), C.c_int, P(gk_opts)]
+            L.gk_numrank_workspace.restype = C.c_size_t
+            L.gk_numrank.argtypes = [P(gk_matrix), C.c_double, C.c_int, P(gk_opts), P(C.c_int), C.c_void_p,
+                                     P(gk_info)]
+            L.gk_numrank.restype = C.c_int
+            L.gk_matvec.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
+            L.gk_matvec.restype = C.c_int
+            L.gk_residuals.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, P(gk_opts)]
+            L.gk_residuals.restype = C.c_int
+            L.gk_status_string.argtypes = [C.c_int]
+            L.gk_status_string.restype = C.c_char_p
+            L.gk_last_cuda_error.argtypes = []
+            L.gk_last_cuda_error.restype = C.c_char_p
+            L.gk_version.argtypes = []
+            L.gk_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().gk_status_string(int(s)).decode()
+
+
+def last_cuda_error() -> str:
+    return lib().gk_last_cuda_error().decode()
+
+
+def version() -> str:
+    return lib().gk_version().decode()
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class CSR:
+    """A CSR operator and the CSR of its transpose (both required by the library)."""
+    m: int
+    n: int
+    rowptr: torch.Tensor
+    colind: torch.Tensor
+    vals: torch.Tensor
+    t_rowptr: torch.Tensor
+    t_colind: torch.Tensor
+    t_vals: torch.Tensor
+
+    @property
+    def device(self):
+        return self.vals.device
+
+
+def make_matrix(A, scale: float = 1.0) -> tuple[gk_matrix, tuple]:
+    """gk_matrix describing a dense row-major tensor (m x n, unit column stride) or a CSR."""
+    if isinstance(A, CSR):
+        for t in (A.rowptr, A.colind, A.t_rowptr, A.t_colind):
+            if t.dtype != torch.int32 or not t.is_contiguous():
+                raise ValueError("CSR index arrays must be contiguous int32")
+        if A.vals.dtype not in _DTYPE or A.t_vals.dtype != A.vals.dtype:
+            raise ValueError("unsupported CSR value dtype")
+        M = gk_matrix(GK_CSR, _DTYPE[A.vals.dtype], A.m, A.n, 0, float(scale), A.vals.data_ptr(),
+                      A.rowptr.data_ptr(), A.colind.data_ptr(), A.t_vals.data_ptr(), A.t_rowptr.data_ptr(),
+                      A.t_colind.data_ptr())
+        return M, (A,)
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("dense operator must be a 2-D row-major tensor with unit column stride")
+    if A.dtype not in _DTYPE:
+        raise ValueError(f"unsupported dtype {A.dtype}")
+    M = gk_matrix(GK_DENSE, _DTYPE[A.dtype], A.shape[0], A.shape[1], A.stride(0), float(scale), A.data_ptr(),
+                  None, None, None, None, None)
+    return M, (A,)
+
+
+def default_opts() -> gk_opts:
+    o = gk_opts()
+    lib().gk_default_opts(C.byref(o))
+    return o
+
+
+def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, eps_absolute=False, seed=None,
+          start=None, stream=None, workspace=None, profile=False):
+    o = default_opts()
+    o.flags = GK_FLAG_PROFILE if profile else 0
+    o.krylov_dim = int(krylov_dim)
+    o.keep = int(keep)
+    if max_restarts is not None:
+        o.max_restarts = int(max_restarts)
+    if reorth_passes is not None:
+        o.reorth_passes = int(reorth_passes)
+    o.eps_absolute = int(bool(eps_absolute))
+    if seed is not None:
+        o.seed = int(seed) & (2**64 - 1)
+    keep_alive = []
+    if start is not None:
+        st = start.to(torch.float64).contiguous()
+        keep_alive.append(st)
+        o.start = st.data_ptr()
+    if device.type == "cuda":
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        o.stream = s.cuda_stream
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o, keep_alive
+
+
+def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0, max_restarts: int | None = None,
+            reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
+            scale: float = 1.0, out=None, check: bool = True, profile: bool = False):
+    """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
+
+    Outputs live where A lives (device tensors for a CUDA operator, host tensors
+    for a host operator: the library copies host data itself).
+    """
+    M, keep_a = make_matrix(A, scale)
+    dev = A.device
+    if dev.type != "cuda" and not torch.cuda.is_available():
+        raise RuntimeError("gk_psvd needs a CUDA device (no host fallback)")
+    m, n = M.m, M.n
+    if out is None:
+        pin = dev.type == "cpu"
+        U = torch.empty((k, m), dtype=torch.float64, device=dev, pin_memory=pin)
+        V = torch.empty((k, n), dtype=torch.float64, device=dev, pin_memory=pin)
+        S = torch.empty(k, dtype=torch.float64, device=dev, pin_memory=pin)
+    else:
+        U, S, V = out
+    o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
+                  reorth_passes, False, seed, start, stream, workspace, profile)
+    info = gk_info()
+    st = lib().gk_psvd(C.byref(M), int(k), float(tol), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
+    if check and st < 0:
+        raise GKError(st, "gk_psvd")
+    return U.T, S, V.T, st, info.as_dict()
+
+
+def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = False, reorth_passes: int | None = None,
+               seed: int | None = None, start=None, stream=None, workspace=None, scale: float = 1.0,
+               want_sigma: bool = False, check: bool = True, profile: bool = False):
+    """Numerical rank by Algorithm 3.  Returns (rank, sigma(B) or None, status, info dict)."""
+    M, keep_a = make_matrix(A, scale)
+    dev = A.device
+    if dev.type != "cuda" and not torch.cuda.is_available():
+        raise RuntimeError("gk_numrank needs a CUDA device (no host fallback)")
+    mn = min(M.m, M.n)
+    km = mn if kmax <= 0 or kmax > mn else kmax
+    sig = torch.zeros(km + 1, dtype=torch.float64, device=dev) if want_sigma else None
+    o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), 0, 0, None, reorth_passes, eps_absolute,
+                  seed, start, stream, workspace, profile)
+    info = gk_info()
+    r = C.c_int(-1)
+    st = lib().gk_numrank(C.byref(M), float(eps), int(kmax), C.byref(o), C.byref(r), _ptr(sig), C.byref(info))
+    if check and st < 0:
+        raise GKError(st, "gk_numrank")
+    d = info.as_dict()
+    return r.value, (sig[: d["kprime"]] if sig is not None else None), st, d
+
+
+def gk_matvec(A, x, trans: bool = False, *, stream=None, scale: float = 1.0):
+    """y = A x (or A^T x) through the library's product kernels; x, y f64."""
+    M, keep_a = make_matrix(A, scale)
+    dev = A.device
+    xx = x.to(torch.float64).contiguous()
+    y = torch.empty(M.n if trans else M.m, dtype=torch.float64, device=xx.device)
+    o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), stream=stream)
+    st = lib().gk_matvec(C.byref(M), int(bool(trans)), _ptr(xx), _ptr(y), C.byref(o))
+    if st < 0:
+        raise GKError(st, "gk_matvec")
+    return y
+
+
+def gk_residuals(A, U, S, V, *, stream=None, scale: float = 1.0):
+    """(||A v_i - s_i u_i||, ||A^T u_i - s_i v_i||) for the columns of U, V."""
+    M, keep_a = make_matrix(A, scale)
+    dev = A.device
+    k = S.numel()
+    Uc = U.T.contiguous().to(torch.float64)
+    Vc = V.T.contiguous().to(torch.float64)
+    Sc = S.to(torch.float64).contiguous()
+    r1 = torch.empty(k, dtype=torch.float64, device=Sc.device)
+    r2 = torch.empty(k, dtype=torch.float64, device=Sc.device)
+    o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), stream=stream)
+    st = lib().gk_residuals(C.byref(M), int(k), _ptr(Uc), _ptr(Sc), _ptr(Vc), _ptr(r1), _ptr(r2), C.byref(o))
+    if st < 0:
+        raise GKError(st, "gk_residuals")
+    return r1, r2
+
+
+def gk_psvd_workspace(A, k: int, krylov_dim: int = 0) -> int:
+    M, _ = make_matrix(A)
+    o = default_opts()
+    o.krylov_dim = int(krylov_dim)
+    return int(lib().gk_psvd_workspace(C.byref(M), int(k), C.byref(o)))
+
+
+def gk_numrank_workspace(A, kmax: int = 0) -> int:
+    M, _ = make_matrix(A)
+    return int(lib().gk_numrank_workspace(C.byref(M), int(kmax), None))

@@ -1,0 +1,306 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on identical seeded
+inputs.  Sizes are chosen so that the oracle finishes in seconds while the kernels
+still span several tiles, chunks and ragged tails.
+
+Tolerances:
+  * f64 operators: the method's own tolerance (tol) bounds the residuals on both
+    sides, so singular values agree to ~tol^2/gap and vectors to ~tol*sigma_1/gap.
+  * f32/bf16/f16 operators are multiplied in f32 with the vector rounded to f32 and
+    runs of at most 64 products summed in f32 (then combined in f64): every entry of
+    a product is within 2^-24 (64 + 2) sum_j |a_ij x_j| of the exact product of the
+    stored values, and the residual floor of the Krylov relations is of order
+    2^-24 ||A||_F / sqrt(n); bounds below are stated from these.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0**-24
+
+
+def gk():
+    import paper_2104_10785_gb300 as m
+
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def dense_pair(A, dtype):
+    """(oracle operator on the stored bytes, device tensor with the same bytes, f64 copy of stored values)."""
+    if dtype == "f64":
+        A64 = np.asarray(A, dtype=np.float64)
+        return oracle.Operator.dense(A64), cuda(A64), A64
+    if dtype == "f32":
+        A32 = np.asarray(A, dtype=np.float32)
+        return oracle.Operator.dense(A32), cuda(A32), A32.astype(np.float64)
+    if dtype == "bf16":
+        bits = synth.to_bf16_bits(np.asarray(A, dtype=np.float32))
+        t = cuda(bits.view(np.int16)).view(torch.bfloat16)
+        return oracle.Operator.dense(None, dtype="bf16", bits=bits), t, synth.bf16_bits_to_f32(bits).astype(np.float64)
+    if dtype == "f16":
+        h = np.asarray(A, dtype=np.float16)
+        bits = h.view(np.uint16)
+        t = cuda(h)
+        return oracle.Operator.dense(None, dtype="f16", bits=bits), t, h.astype(np.float64)
+    raise ValueError(dtype)
+
+
+def angle_err(X, Y):
+    """max_i || x_i - sign * y_i || for unit columns (sign-invariant)."""
+    X = np.asarray(X)
+    Y = np.asarray(Y)
+    s = np.sign(np.sum(X * Y, axis=0))
+    s[s == 0] = 1
+    return np.linalg.norm(X - Y * s[None, :], axis=0).max()
+
+
+# ---------------------------------------------------------------------------
+# the products of Eq. 2.2
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("shape", [(1, 1), (7, 3), (33, 65), (1000, 1537), (3001, 2049), (64, 40000)])
+def test_dense_products_match_oracle(dtype, shape):
+    m, n = shape
+    g = synth.rng(11 + m + n)
+    A = g.standard_normal((m, n))
+    op, At, Ad = dense_pair(A, dtype)
+    x = g.standard_normal(n)
+    y = g.standard_normal(m)
+    M = gk()
+    got = M.gk_matvec(At, cuda(x)).cpu().numpy()
+    got_t = M.gk_matvec(At, cuda(y), trans=True).cpu().numpy()
+    ref = op.matvec(x)
+    ref_t = op.rmatvec(y)
+    if dtype == "f64":
+        # f64 products: within a few ulps of sum_j |a_ij x_j| (different summation order)
+        assert np.all(np.abs(got - ref) <= 1e-13 * (np.abs(Ad) @ np.abs(x)) + 1e-300)
+        assert np.all(np.abs(got_t - ref_t) <= 1e-13 * (np.abs(Ad).T @ np.abs(y)) + 1e-300)
+    else:
+        bound = U32 * 66 * (np.abs(Ad) @ np.abs(x)) + 1e-300
+        assert np.all(np.abs(got - ref) <= bound)
+        bound_t = U32 * 66 * (np.abs(Ad).T @ np.abs(y)) + 1e-300
+        assert np.all(np.abs(got_t - ref_t) <= bound_t)
+
+
+def test_dense_products_padded_rows_and_unaligned_ld():
+    """ld > n with rows that are not 16-byte aligned takes the scalar path."""
+    g = synth.rng(5)
+    m, n, ld = 257, 101, 103
+    full = g.standard_normal((m, ld)).astype(np.float32)
+    At = cuda(full)[:, :n]
+    assert At.stride(0) == ld
+    op = oracle.Operator(full, m, n, "f32", ld=ld)
+    x = g.standard_normal(n)
+    y = g.standard_normal(m)
+    M = gk()
+    A64 = full[:, :n].astype(np.float64)
+    assert np.all(np.abs(M.gk_matvec(At, cuda(x)).cpu().numpy() - op.matvec(x)) <= U32 * 66 * (np.abs(A64) @ np.abs(x)))
+    assert np.all(np.abs(M.gk_matvec(At, cuda(y), trans=True).cpu().numpy() - op.rmatvec(y))
+                  <= U32 * 66 * (np.abs(A64).T @ np.abs(y)))
+
+
+def _csr_pair(m, n, per_row, sig, seed, dtype=np.float32):
+    d = synth.sparse_planted(m, n, per_row, sig, seed, usup=min(200, m // max(1, len(sig))),
+                             vsup=min(100, n // max(1, len(sig))), dtype=dtype)
+    dt = "f32" if dtype == np.float32 else "f64"
+    op = oracle.Operator.csr(m, n, d["rowptr"], d["colind"], d["vals"], dt)
+    M = gk()
+    A = M.CSR(m, n, cuda(d["rowptr"]), cuda(d["colind"]), cuda(d["vals"]), cuda(d["t_rowptr"]), cuda(d["t_colind"]),
+              cuda(d["t_vals"]))
+    return op, A, d
+
+
+def test_csr_products_match_oracle():
+    op, A, d = _csr_pair(5003, 2999, 20, 10.0 * 0.9 ** np.arange(1, 6), 3)
+    g = synth.rng(9)
+    x = g.standard_normal(2999)
+    y = g.standard_normal(5003)
+    M = gk()
+    np.testing.assert_allclose(M.gk_matvec(A, cuda(x)).cpu().numpy(), op.matvec(x), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(M.gk_matvec(A, cuda(y), trans=True).cpu().numpy(), op.rmatvec(y), rtol=1e-12,
+                               atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 3: numerical rank (exact equality with the oracle)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n,r,dtype,eps", [(2000, 1200, 50, "f32", 1e-5), (1200, 2000, 50, "f32", 1e-5),
+                                             (5000, 2000, 200, "f32", 1e-5), (777, 555, 31, "f64", 1e-5),
+                                             (3000, 1000, 40, "bf16", 1e-2)])
+def test_numrank_matches_oracle(m, n, r, dtype, eps):
+    # bf16 storage perturbs the product by ~3e-4 sigma_1, so its numerical rank at eps = 1e-5 is full;
+    # eps = 1e-2 sits between that floor and sigma_r / sigma_1 ~ 0.5
+    A = synth.gaussian_product(m, n, r, 1e-7, seed=100 + m + r, dtype=np.float64)
+    op, At, Ad = dense_pair(A, dtype)
+    q1 = synth.start_vector(m, 7)
+    r_or, kp_or, sig_or = oracle.numrank(op, q1, eps=eps, kmax=min(m, n, 400))
+    rk, sig, st, info = gk().gk_numrank(At, eps, min(m, n, 400), start=cuda(q1), want_sigma=True)
+    assert st == 0
+    assert rk == r_or == r
+    sig = sig.cpu().numpy()
+    np.testing.assert_allclose(sig[:r], sig_or[:r], rtol=2e-6 if dtype != "f64" else 1e-11)
+    assert abs(info["kprime"] - kp_or) <= 8
+
+
+def test_numrank_seeded_start_matches_oracle_philox():
+    """The device draws q1 ~ N(2,1) with Philox4x32-10 + Box-Muller; the oracle draws the same stream."""
+    m, n = 900, 700
+    A = synth.gaussian_product(m, n, 25, 0.0, seed=3, dtype=np.float64)
+    op, At, _ = dense_pair(A, "f64")
+    seed = 123456789
+    q1 = oracle.start_vector(seed, m)
+    r1, s1, _, i1 = gk().gk_numrank(At, 1e-8, 0, seed=seed, want_sigma=True)
+    r2, s2, _, i2 = gk().gk_numrank(At, 1e-8, 0, start=cuda(q1), want_sigma=True)
+    assert r1 == r2 == 25 and i1["kprime"] == i2["kprime"]
+    # the 25 singular values of the rank-25 operator agree; the rest sit at the rounding floor
+    np.testing.assert_allclose(s1.cpu().numpy()[:25], s2.cpu().numpy()[:25], rtol=1e-12)
+
+
+def test_numrank_special_cases():
+    M = gk()
+    # zero matrix: rank 0
+    Z = torch.zeros((50, 30), dtype=torch.float64, device="cuda")
+    r, _, st, info = M.gk_numrank(Z, 1e-8)
+    assert st == 0 and r == 0 and info["kprime"] == 0
+    # rank one
+    g = synth.rng(4)
+    x, y = g.standard_normal(60), g.standard_normal(45)
+    r, sig, st, info = M.gk_numrank(cuda(np.outer(x, y)), 1e-8, want_sigma=True)
+    assert r == 1
+    np.testing.assert_allclose(sig.cpu().numpy()[0], np.linalg.norm(x) * np.linalg.norm(y), rtol=1e-13)
+    # identity: the Krylov space of I is one-dimensional (Algorithm 3 returns 1)
+    r, _, _, info = M.gk_numrank(torch.eye(40, dtype=torch.float64, device="cuda"), 1e-8)
+    assert r == 1 and info["kprime"] == 1
+    # absolute threshold reading
+    A = synth.gaussian_product(80, 60, 5, 0.0, seed=8, dtype=np.float64) * 1e-3
+    r, _, _, _ = M.gk_numrank(cuda(A), 10.0, eps_absolute=True)
+    op = oracle.Operator.dense(A)
+    r_or, _, _ = oracle.numrank(op, synth.start_vector(80, 1), eps=10.0, relative=False)
+    assert r == r_or
+
+
+# ---------------------------------------------------------------------------
+# restarted partial SVD
+# ---------------------------------------------------------------------------
+
+def _compare_psvd(op, At, A64, k, K, tol, q1, s_rtol, v_tol, res_tol, **kw):
+    Uo, So, Vo, io = oracle.psvd(op, k, K, q1, tol=min(tol, 1e-12), max_restarts=500)
+    assert io["converged"]
+    U, S, V, st, info = gk().gk_psvd(At, k, tol, krylov_dim=K, start=cuda(q1), **kw)
+    assert st == 0, info
+    U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    np.testing.assert_allclose(S, So, rtol=s_rtol)
+    assert angle_err(V, Vo) <= v_tol
+    assert angle_err(U, Uo) <= v_tol
+    # true residuals of the GPU triplets on the stored operator, in f64 on the CPU
+    r1, r2 = oracle.residuals(op, U, S, V)
+    assert max(r1.max(), r2.max()) <= res_tol * So[0], (r1.max(), r2.max())
+    # sign convention
+    idx = np.argmax(np.abs(V), axis=0)
+    assert np.all(V[idx, np.arange(k)] > 0)
+    return U, S, V, info
+
+
+def test_psvd_dense_f64_2000x1000_prescribed_spectrum():
+    """Dense f64 2000 x 1000, sigma_i = 0.9^i, top 10, Krylov dimension 30, tol 1e-10."""
+    w = synth.WORKLOADS["dense_f64_2000x1000_top10"]
+    sig = synth.sigma_geometric(w["n"], w["q"])
+    A, U0, V0 = synth.prescribed_spectrum(w["m"], w["n"], sig, w["seed"])
+    op, At, _ = dense_pair(A, "f64")
+    q1 = synth.start_vector(w["m"], w["seed"])
+    U, S, V, info = _compare_psvd(op, At, A, w["k"], w["K"], w["tol"], q1, s_rtol=1e-10, v_tol=1e-8, res_tol=1e-10)
+    np.testing.assert_allclose(S, sig[: w["k"]], rtol=1e-10)
+    assert angle_err(V, V0[:, : w["k"]]) <= 1e-8
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_psvd_reduced_precision_storage(dtype):
+    """sigma_i = i^-1.5 spectrum stored in f32 / bf16; parity with the oracle on the stored bytes."""
+    m, n, k, K = 3001, 1499, 12, 40
+    sig = synth.sigma_power(n, 1.5)
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, seed=77, dtype=np.float64)
+    op, At, A64 = dense_pair(A, dtype)
+    q1 = synth.start_vector(m, 77)
+    nf = np.linalg.norm(A64)
+    floor = 64 * U32 * nf / np.sqrt(n)  # f32 accumulation floor of the Krylov relations
+    gaps = np.abs(np.diff(sig[: k + 1])).min()
+    _compare_psvd(op, At, A64, k, K, 1e-8, q1, s_rtol=1e-7, v_tol=max(1e-6, 10 * (1e-8 + floor) / gaps),
+                  res_tol=1e-8 + 10 * floor)
+
+
+def test_psvd_csr_planted():
+    sigp = 100.0 * 0.95 ** np.arange(1, 11)
+    op, A, d = _csr_pair(20011, 9973, 20, sigp, 21)
+    q1 = synth.start_vector(20011, 21)
+    _compare_psvd(op, A, None, 10, 30, 1e-8, q1, s_rtol=1e-9, v_tol=1e-5, res_tol=2e-8)
+
+
+def test_psvd_wide_and_tiny_shapes():
+    M = gk()
+    g = synth.rng(31)
+    for m, n, k, K in [(1, 1, 1, 1), (3, 1, 1, 1), (1, 4, 1, 1), (5, 5, 5, 5), (7, 3, 2, 3), (40, 300, 4, 12)]:
+        A = g.standard_normal((m, n))
+        U, S, V, st, info = M.gk_psvd(cuda(A), k, 1e-12, krylov_dim=K, start=cuda(synth.start_vector(m, 1)))
+        assert st in (0, 2)
+        np.testing.assert_allclose(S.cpu().numpy(), np.linalg.svd(A, compute_uv=False)[:k], rtol=1e-11, atol=1e-13)
+
+
+def test_psvd_zero_and_rank_deficient():
+    M = gk()
+    Z = torch.zeros((30, 20), dtype=torch.float64, device="cuda")
+    U, S, V, st, info = M.gk_psvd(Z, 3, 1e-10, krylov_dim=8)
+    assert torch.all(S == 0) and torch.isfinite(V).all() and torch.isfinite(U).all()
+    g = synth.rng(2)
+    A = g.standard_normal((40, 3)) @ g.standard_normal((3, 30))
+    U, S, V, st, info = M.gk_psvd(cuda(A), 5, 1e-12, krylov_dim=10)
+    s = np.linalg.svd(A, compute_uv=False)
+    S = S.cpu().numpy()
+    np.testing.assert_allclose(S[:3], s[:3], rtol=1e-12)
+    assert np.all(S[3:] < 1e-12 * s[0]) and torch.isfinite(V).all()
+
+
+def test_psvd_host_buffers_end_to_end():
+    """Host (pinned) operator and outputs: the library copies in and out itself."""
+    M = gk()
+    sig = synth.sigma_geometric(300, 0.9)
+    A, _, _ = synth.prescribed_spectrum(1200, 300, sig, seed=5, dtype=np.float32)
+    Ah = torch.from_numpy(A).pin_memory()
+    U, S, V, st, info = M.gk_psvd(Ah, 6, 1e-8, krylov_dim=20)
+    assert st == 0 and U.device.type == "cpu"
+    np.testing.assert_allclose(S.numpy(), sig[:6], rtol=1e-6)
+    Ud, Sd, Vd, st2, _ = M.gk_psvd(Ah.cuda(), 6, 1e-8, krylov_dim=20)
+    np.testing.assert_array_equal(S.numpy(), Sd.cpu().numpy())
+
+
+def test_invalid_arguments_are_rejected():
+    M = gk()
+    A = torch.ones((10, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(M.GKError):
+        M.gk_psvd(A, 9, 1e-8)  # k > min(m, n)
+    with pytest.raises(M.GKError):
+        M.gk_psvd(A, 4, 1e-8, krylov_dim=4)  # no room to restart
+    with pytest.raises(M.GKError):
+        M.gk_psvd(A, 2, -1.0)
+    with pytest.raises(M.GKError):
+        M.gk_numrank(A, float("nan"))
+
+
+def test_gpu_residuals_entry_point():
+    sig = synth.sigma_geometric(200, 0.8)
+    A, U0, V0 = synth.prescribed_spectrum(500, 200, sig, seed=9)
+    M = gk()
+    r1, r2 = M.gk_residuals(cuda(A), cuda(U0[:, :5]), cuda(sig[:5]), cuda(V0[:, :5]))
+    assert r1.max().item() < 1e-13 and r2.max().item() < 1e-13
+    Sp = sig[:5] * 1.001
+    r1, r2 = M.gk_residuals(cuda(A), cuda(U0[:, :5]), cuda(Sp), cuda(V0[:, :5]))
+    np.testing.assert_allclose(r1.cpu().numpy(), 0.001 * sig[:5], rtol=1e-9)

@@ -1,0 +1,76 @@
+"""Host-side checks of the CUDA library that need no GPU: it builds for sm_103a, loads,
+exports every entry point declared in include/gk.h, and refuses to compute without a
+device (no host fallback)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:int|void|size_t|char)\s*\*?\s*(gk_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["gk_psvd", "gk_numrank", "gk_psvd_workspace", "gk_numrank_workspace", "gk_matvec",
+                 "gk_residuals", "gk_status_string", "gk_default_opts"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2104_10785_gb300 as gk
+
+    path = gk.library_path()
+    gk.lib()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(gk_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm_103a():
+    import paper_2104_10785_gb300 as gk
+
+    gk.lib()
+    out = subprocess.run(["cuobjdump", "--list-elf", gk.library_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_status_strings_and_defaults():
+    import paper_2104_10785_gb300 as gk
+    from paper_2104_10785_gb300 import gk as raw
+
+    assert gk.status_string(0) == "GK_OK"
+    assert gk.status_string(-7) == "GK_NO_DEVICE"
+    o = raw.default_opts()
+    assert o.reorth_passes == 2 and o.max_restarts == 200 and o.krylov_dim == 0
+    assert "sm_103a" in gk.version()
+
+
+def test_no_device_means_no_compute():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes as C
+
+    import numpy as np
+    from paper_2104_10785_gb300 import gk as raw
+
+    A = np.ones((4, 3))
+    M = raw.gk_matrix(raw.GK_DENSE, raw.GK_F64, 4, 3, 3, 1.0, A.ctypes.data, None, None, None, None, None)
+    r = C.c_int(-1)
+    st = raw.lib().gk_numrank(C.byref(M), 1e-8, 0, None, C.byref(r), None, None)
+    assert st == raw.GK_NO_DEVICE and r.value == -1
+    U = np.zeros((3, 4)); S = np.zeros(3); V = np.zeros((3, 3))
+    st = raw.lib().gk_psvd(C.byref(M), 1, 1e-8, None, U.ctypes.data, S.ctypes.data, V.ctypes.data, None)
+    assert st == raw.GK_NO_DEVICE
