@@ -168,6 +168,33 @@ int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const g
 int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, const double *V, double *res_av,
                  double *res_atu, const gk_opts *opts);
 
+/* Size of the device array behind gk_matvec_static (bytes). */
+#define GK_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* gk_matvec_static: y = A x (trans = 0) or y = A^T x (trans = 1) exactly as
+ * gk_matvec computes them, but without allocating any device memory.  The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc: code whose device memory is all owned by another
+ * allocator (a framework's caching allocator that has reserved the GPU, so a
+ * raw allocation would fail or fragment its pool), and latency-critical loops
+ * where an allocation could block or synchronize the device.
+ *  - Its scratch is a static device array of GK_STATIC_SCRATCH_BYTES (32 MiB)
+ *    that every GPU loading this library holds until the process exits.
+ *    A x needs 256 + 4*max(m,n) bytes of it; dense A^T x also needs its
+ *    partial sums, 8*n*(row blocks) bytes (about m*n/128 bytes for large m).
+ *    A problem that needs more returns GK_OUT_OF_MEMORY and computes nothing.
+ *  - A, x and y must be device memory (host pointers give GK_INVALID_ARG:
+ *    staging them would need an allocation).  x: n (or m) f64, y: m (or n) f64.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents;
+ *    the call clears what must start at zero.  Calls that overlap on the GPU
+ *    (concurrent calls on different streams or host threads) race on it.
+ *  - Synchronous like the other entry points; work runs on opts->stream
+ *    (opts may be NULL: legacy default stream). */
+int gk_matvec_static(const gk_matrix *A, int trans, const double *x, double *y, const gk_opts *opts);
+
 /* Human-readable name of a status code. */
 const char *gk_status_string(int status);
 

@@ -8,6 +8,7 @@ from .gk import (  # noqa: F401
     CSR,
     GKError,
     gk_matvec,
+    gk_matvec_static,
     gk_numrank,
     gk_numrank_workspace,
     gk_psvd,

@@ -98,6 +98,8 @@ def lib():
             L.gk_residuals.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, P(gk_opts)]
             L.gk_residuals.restype = C.c_int
+            L.gk_matvec_static.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
+            L.gk_matvec_static.restype = C.c_int
             L.gk_status_string.argtypes = [C.c_int]
             L.gk_status_string.restype = C.c_char_p
             L.gk_last_cuda_error.argtypes = []
@@ -257,6 +259,20 @@ def gk_matvec(A, x, trans: bool = False, *, stream=None, scale: float = 1.0):
     if st < 0:
         raise GKError(st, "gk_matvec")
     return y
+
+
+def gk_matvec_static(A, x, out, trans: bool = False, *, stream=None, scale: float = 1.0) -> int:
+    """y = A x (or A^T x) into the caller's device tensor `out`, with the library's
+    static scratch instead of any device allocation (see gk_matvec_static in gk.h).
+    Returns the status code."""
+    M, keep_a = make_matrix(A, scale)
+    if x.dtype != torch.float64 or not x.is_contiguous() or out.dtype != torch.float64 or not out.is_contiguous():
+        raise ValueError("x and out must be contiguous float64 device tensors")
+    o = gk_opts()
+    lib().gk_default_opts(C.byref(o))
+    s = stream if stream is not None else torch.cuda.current_stream(out.device)
+    o.stream = s.cuda_stream
+    return int(lib().gk_matvec_static(C.byref(M), int(bool(trans)), _ptr(x), _ptr(out), C.byref(o)))
 
 
 def gk_residuals(A, U, S, V, *, stream=None, scale: float = 1.0):
