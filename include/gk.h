@@ -94,6 +94,8 @@ typedef struct {
   int32_t kprime;        /* gk_numrank: k' of Algorithm 1 (columns of B_{k'+1,k'}) */
   int32_t stop_reason;   /* gk_numrank: 0 reached kmax, 1 beta break, 2 alpha break */
   int32_t breakdowns;    /* exact breakdowns replaced by fresh directions */
+  int32_t svd_sweeps;    /* gk_psvd: Jacobi sweeps of the last small SVD (negative: sweep limit reached) */
+  int32_t reserved;
   int64_t matvecs;       /* products with A or A^T */
   double resid_est_max;  /* gk_psvd: max_i<k |beta_K X_{K,i}| / sigma_1 (Ritz residual estimate) */
   double sigma_est;      /* running lower bound on sigma_1 used by the break test */
@@ -180,8 +182,9 @@ int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, co
  * where an allocation could block or synchronize the device.
  *  - Its scratch is a static device array of GK_STATIC_SCRATCH_BYTES (32 MiB)
  *    that every GPU loading this library holds until the process exits.
- *    A x needs 256 + 4*max(m,n) bytes of it; dense A^T x also needs its
- *    partial sums, 8*n*(row blocks) bytes (about m*n/128 bytes for large m).
+ *    A x needs 256 + 4*max(m,n) bytes of it (it runs the row-streaming
+ *    kernel, which keeps no partial sums); dense A^T x also needs its partial
+ *    sums, 8*n*(row blocks) bytes (about m*n/128 bytes for large m).
  *    A problem that needs more returns GK_OUT_OF_MEMORY and computes nothing.
  *  - A, x and y must be device memory (host pointers give GK_INVALID_ARG:
  *    staging them would need an allocation).  x: n (or m) f64, y: m (or n) f64.

@@ -326,7 +326,8 @@ struct PsvdBufs {
   double *Ub, *Ub2, *Vb, *Vb2, *w, *z, *t, *part, *h, *alpha, *beta, *Bm, *Yw, *X, *Y, *sigma, *rho, *out;
   float *x32;
   int *sweeps;
-  double *Uo, *So, *Vo, *q1;
+  double *Uo, *So, *Vo, *q1, *svd_nrm;
+  int *svd_pos;
 };
 
 size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const OpStage &st, bool host_out,
@@ -358,6 +359,8 @@ size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const Op
   b->rho = cv.take<double>(K);
   b->out = cv.take<double>(8);
   b->sweeps = cv.take<int>(4);
+  b->svd_nrm = cv.take<double>(K);
+  b->svd_pos = cv.take<int>(K);
   b->Uo = host_out ? cv.take<double>((size_t)p.m * p.k) : nullptr;
   b->Vo = host_out ? cv.take<double>((size_t)p.n * p.k) : nullptr;
   b->So = host_out ? cv.take<double>(p.k) : nullptr;
@@ -544,12 +547,13 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
       }
       prof.begin(PC_SMALL);
       GK_CUDA(assemble_B(b.Bm, K, l, b.sigma, b.rho, b.alpha, b.beta, b.ctl, s));
-      GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.sweeps, b.ctl, s));
+      GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.svd_nrm, b.svd_pos, b.sweeps, b.ctl, s));
       GK_CUDA(ritz_check(b.sigma, b.X, K, k, b.beta + (K - 1), tol, b.rho, b.out, b.ctl, s));
       prof.end();
       rc = read_ctl(b.ctl, b.out, &hc, s);
       if (rc) return rc;
       if (hc.ctl.event == EV_NUMERICAL) return GK_NUMERICAL;
+      if (hc.ctl.event == EV_TIMEOUT) return GK_TIMEOUT;
       if (hc.ctl.event != EV_BREAKDOWN) break;
       // exact breakdown: replace the vanished vector and resume the cycle after it
       const int jb = hc.ctl.step, sb = hc.ctl.side;
@@ -600,7 +604,9 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   GK_CUDA(cudaMemcpyAsync(So, b.sigma, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
   GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, k, s));
   double sk = 0.0;
+  int sweeps = 0;
   GK_CUDA(cudaMemcpyAsync(&sk, b.sigma + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaMemcpyAsync(&sweeps, b.sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (host_out) {
     GK_CUDA(cudaMemcpyAsync(U, Uo, sizeof(double) * m * k, cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaMemcpyAsync(V, Vo, sizeof(double) * n * k, cudaMemcpyDeviceToHost, s));
@@ -611,6 +617,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   if (status == GK_OK && sk == 0.0) status = GK_RANK_DEFICIENT;
   prof.finish(&inf);
   inf.sigma_est = hc.ctl.sest;
+  inf.svd_sweeps = sweeps;
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
   if (info) *info = inf;
@@ -756,6 +763,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
     if (rc) return rc;
   }
   if (hc.ctl.event == EV_NUMERICAL) return GK_NUMERICAL;
+  if (hc.ctl.event == EV_TIMEOUT) return GK_TIMEOUT;
   int kp;
   if (hc.ctl.halt) {
     kp = hc.ctl.step;
@@ -853,8 +861,10 @@ int matvec_impl(const gk_matrix *Ain, int trans, const double *x, double *y, con
   else
     GK_CUDA(matvec(op, b.x32, b.x, b.y, nullptr, nullptr, b.part, b.ctl, s, d));
   GK_CUDA(cudaMemcpyAsync(y, b.y, sizeof(double) * nout, cudaMemcpyDefault, s));
-  GK_CUDA(cudaStreamSynchronize(s));
-  return GK_OK;
+  HostCtl hc;
+  rc = read_ctl(b.ctl, nullptr, &hc, s);
+  if (rc) return rc;
+  return hc.ctl.event == EV_TIMEOUT ? GK_TIMEOUT : GK_OK;
 }
 
 int residuals_impl(const gk_matrix *Ain, int k, const double *U, const double *S, const double *V, double *r_av,

@@ -28,7 +28,7 @@ int64_t launch_count();
   } while (0)
 
 // ---- control block written by device kernels, read by the host driver ----
-enum Event { EV_NONE = 0, EV_BETA_BREAK = 1, EV_ALPHA_BREAK = 2, EV_BREAKDOWN = 3, EV_NUMERICAL = 4 };
+enum Event { EV_NONE = 0, EV_BETA_BREAK = 1, EV_ALPHA_BREAK = 2, EV_BREAKDOWN = 3, EV_NUMERICAL = 4, EV_TIMEOUT = 5 };
 // how a norm kernel judges the new vector
 enum NormMode {
   NM_BREAK = 0,      // Algorithm 1 break test: norm <= eps * sigma_est (or eps)
@@ -49,7 +49,7 @@ struct Ctl {
   double inv_norm;   // 1 / last accepted norm (0 if rejected)
   double eps;        // Algorithm 1 threshold parameter
   int eps_rel;       // 1: threshold eps * sest; 0: eps
-  int pad;
+  int timeout;       // a bounded device wait gave up (the kernel recorded where: 1 full, 2 empty barrier)
 };
 
 // device view of the operator
@@ -79,6 +79,8 @@ int cgs_blocks(int64_t len, const Dev &d);
 
 // ---- products (gk_matvec.cu) -------------------------------------------
 // y = A x - (*coef) * sub   (sub may be null).  x32: f32 copy of x (f32/bf16/f16 A), x64: f64 x (f64 A).
+// part: scratch for partial sums (gemvt_partials() doubles); with part == null a dense
+// reduced-precision A x runs the row-streaming kernel, which needs none.
 cudaError_t matvec(const Op &A, const float *x32, const double *x64, double *y, const double *sub,
                    const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d);
 // y = A^T x - (*coef) * sub
@@ -114,10 +116,12 @@ cudaError_t reset_ctl(Ctl *ctl, double eps, int eps_rel, cudaStream_t s);
 // for j >= l.
 cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const double *rho, const double *alpha,
                        const double *beta, const Ctl *ctl, cudaStream_t s);
-// One-sided Jacobi SVD of the K x K matrix Bm (overwritten; Yw is K x K work):
-// sigma (K, descending), X (K x K left vectors), Y (K x K right vectors).
-cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, int *sweeps,
-                      const Ctl *ctl, cudaStream_t s);
+// One-sided Jacobi SVD of the K x K matrix Bm (overwritten; Yw is K x K work,
+// nrm/pos K-entry work) on one thread-block cluster: sigma (K, descending),
+// X (K x K left vectors), Y (K x K right vectors), sweeps (negative if the
+// sweep limit was reached).
+cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
+                      int *sweeps, const Ctl *ctl, cudaStream_t s);
 // Restart bookkeeping: rho_i = betaK X_{K,i} (all i < K), and
 // out[0] = max_{i<k} |rho_i|, out[1] = sigma_1, out[2] = converged (0/1).
 cudaError_t ritz_check(const double *sigma, const double *X, int K, int k, const double *betaK, double tol,

@@ -7,7 +7,8 @@
 // never passes the symbol g_scratch itself to a kernel: in host code that name
 // is only a stand-in for the device array, so the device address is looked up
 // once per device with cudaGetSymbolAddress (with that device current) and
-// cached.  The products run the same kernels as gk_matvec.
+// cached.  A^T x runs the same kernels as gk_matvec; A x runs the row-streaming
+// kernel, which needs no partial sums.
 #include <mutex>
 
 #include "gk_internal.cuh"
@@ -113,8 +114,10 @@ extern "C" int gk_matvec_static(const gk_matrix *A, int trans, const double *x, 
   // overwritten before they are read
   if (gk::reset_ctl(ctl, 0.0, 1, s) != cudaSuccess) return GK_CUDA_ERROR;
   if (gk::copy_vec(nullptr, x32, x, nin, s) != cudaSuccess) return GK_CUDA_ERROR;
+  // A x gets no partial-sum buffer: the product then runs the row-streaming kernel,
+  // which needs none (the scratch budget above counts partial sums for A^T x only)
   const cudaError_t e = trans ? gk::matvec_t(op, x32, x, y, nullptr, nullptr, part, ctl, s, d)
-                              : gk::matvec(op, x32, x, y, nullptr, nullptr, part, ctl, s, d);
+                              : gk::matvec(op, x32, x, y, nullptr, nullptr, nullptr, ctl, s, d);
   if (e != cudaSuccess) return GK_CUDA_ERROR;
   if (cudaStreamSynchronize(s) != cudaSuccess) return GK_CUDA_ERROR;
   return GK_OK;

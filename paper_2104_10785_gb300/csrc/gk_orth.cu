@@ -310,7 +310,7 @@ __global__ void k_reset_ctl(Ctl *ctl, double eps, int eps_rel) {
     ctl->inv_norm = 0.0;
     ctl->eps = eps;
     ctl->eps_rel = eps_rel;
-    ctl->pad = 0;
+    ctl->timeout = 0;
   }
 }
 

@@ -8,7 +8,11 @@
 #include <float.h>
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "gk_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gk {
 
@@ -46,25 +50,36 @@ __global__ void k_assemble_B(double *__restrict__ Bm, int K, int l, const double
 // tournament (circle method) pairing: round r, slot s of Kp players
 __device__ __forceinline__ int player(int r, int s, int Kp) { return s == 0 ? 0 : ((s - 1 + r) % (Kp - 1)) + 1; }
 
-__global__ void __launch_bounds__(1024) k_jacobi_svd(double *__restrict__ B, double *__restrict__ Yw, int K,
-                                                     double *__restrict__ sigma, double *__restrict__ X,
-                                                     double *__restrict__ Y, int *sweeps_out, const Ctl *ctl) {
-  if (halted(ctl)) return;
-  __shared__ int rotated;
-  __shared__ double nrm[1024];
-  __shared__ int pos[1024];
+// One-sided (Hestenes) Jacobi SVD of the K x K matrix B on one thread-block
+// cluster.  Each round of the tournament ordering rotates Kp/2 disjoint column
+// pairs, one pair per warp across the whole cluster; the cluster barrier
+// (release/acquire at cluster scope) separates the rounds.  The columns of B
+// and of the accumulated right rotations Yw live in global memory (L2), read
+// with ld.global.cg so that no stale L1 line survives a round.  A sweep that
+// rotates no pair ends the iteration; the cluster agrees on that through the
+// CTAs' shared-memory flags (distributed shared memory).
+__global__ void __launch_bounds__(256) k_jacobi_cluster(double *__restrict__ B, double *__restrict__ Yw, int K,
+                                                        double *__restrict__ sigma, double *__restrict__ X,
+                                                        double *__restrict__ Y, double *__restrict__ nrm,
+                                                        int *__restrict__ pos, int *sweeps_out, const Ctl *ctl) {
+  cg::cluster_group cl = cg::this_cluster();
+  if (halted(ctl)) return;  // every CTA of the cluster sees the same flag
+  __shared__ int s_rot;
+  __shared__ int s_any;
+  const unsigned crank = cl.block_rank(), csize = cl.num_blocks();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)K * K; idx += blockDim.x)
-    Yw[idx] = ((idx % K) == (idx / K)) ? 1.0 : 0.0;
+  const int gw = (int)crank * nw + warp, gnw = (int)csize * nw;
+  const int64_t gtid = (int64_t)crank * blockDim.x + threadIdx.x, gthreads = (int64_t)csize * blockDim.x;
+  for (int64_t idx = gtid; idx < (int64_t)K * K; idx += gthreads) Yw[idx] = ((idx % K) == (idx / K)) ? 1.0 : 0.0;
   const int Kp = K + (K & 1);
-  const double tol = 2.0 * sqrt((double)K) * 0x1.0p-52;
+  const double tol = fmax(2.0 * sqrt((double)K) * 0x1.0p-52, (double)K * 0x1.0p-53);
   int sweep, done = 0;
-  __syncthreads();
+  cl.sync();
   for (sweep = 1; sweep <= 80; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+    if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int r = 0; r < Kp - 1; ++r) {
-      for (int pi = warp; pi < Kp / 2; pi += nw) {
+      for (int pi = gw; pi < Kp / 2; pi += gnw) {
         int p = player(r, pi, Kp), q = player(r, Kp - 1 - pi, Kp);
         if (p > q) {
           const int t = p;
@@ -75,7 +90,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double *__restrict__ B, dou
         double *bp = B + (int64_t)p * K, *bq = B + (int64_t)q * K;
         double a = 0.0, b = 0.0, c = 0.0;
         for (int i = lane; i < K; i += 32) {
-          const double x = bp[i], y = bq[i];
+          const double x = __ldcg(bp + i), y = __ldcg(bq + i);
           a = fma(x, x, a);
           b = fma(y, y, b);
           c = fma(x, y, c);
@@ -84,58 +99,69 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double *__restrict__ B, dou
         b = warp_sum(b);
         c = warp_sum(c);
         if (c == 0.0 || fabs(c) <= tol * sqrt(a) * sqrt(b)) continue;
-        if (lane == 0) rotated = 1;
+        if (lane == 0) s_rot = 1;
         // rotation that makes columns p and q orthogonal (Rutishauser's formula)
         const double zeta = (b - a) / (2.0 * c);
         const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
                                             : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
         for (int i = lane; i < K; i += 32) {
-          const double x = bp[i], y = bq[i];
+          const double x = __ldcg(bp + i), y = __ldcg(bq + i);
           bp[i] = cs * x - sn * y;
           bq[i] = sn * x + cs * y;
         }
         double *yp = Yw + (int64_t)p * K, *yq = Yw + (int64_t)q * K;
         for (int i = lane; i < K; i += 32) {
-          const double x = yp[i], y = yq[i];
+          const double x = __ldcg(yp + i), y = __ldcg(yq + i);
           yp[i] = cs * x - sn * y;
           yq[i] = sn * x + cs * y;
         }
       }
-      __syncthreads();
+      cl.sync();
     }
-    const int any = rotated;
-    __syncthreads();
-    if (!any) {
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (unsigned qr = 0; qr < csize; ++qr) any |= *cl.map_shared_rank(&s_rot, qr);
+      s_any = any;
+    }
+    cl.sync();  // every CTA has read every flag before any CTA clears its own
+    if (!s_any) {
       done = 1;
       break;
     }
   }
   // singular values = column norms, ordered descending (stable by index)
-  for (int c = warp; c < K; c += nw) {
+  for (int c = gw; c < K; c += gnw) {
     const double *bc = B + (int64_t)c * K;
-    double s = 0.0;
-    for (int i = lane; i < K; i += 32) s = fma(bc[i], bc[i], s);
-    s = warp_sum(s);
-    if (lane == 0) nrm[c] = sqrt(s);
+    double sq = 0.0;
+    for (int i = lane; i < K; i += 32) {
+      const double v = __ldcg(bc + i);
+      sq = fma(v, v, sq);
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) nrm[c] = sqrt(sq);
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+  cl.sync();
+  for (int64_t c = gtid; c < K; c += gthreads) {
+    const double nc = __ldcg(nrm + c);
     int rk = 0;
-    for (int o = 0; o < K; ++o) rk += (nrm[o] > nrm[c]) || (nrm[o] == nrm[c] && o < c);
+    for (int o = 0; o < K; ++o) {
+      const double no = __ldcg(nrm + o);
+      rk += (no > nc) || (no == nc && o < c);
+    }
     pos[c] = rk;
   }
-  __syncthreads();
-  for (int c = warp; c < K; c += nw) {
-    const int pc = pos[c];
-    const double nc = nrm[c];
+  cl.sync();
+  for (int c = gw; c < K; c += gnw) {
+    const int pc = __ldcg(pos + c);
+    const double nc = __ldcg(nrm + c);
     for (int i = lane; i < K; i += 32) {
-      X[(int64_t)pc * K + i] = nc > 0.0 ? B[(int64_t)c * K + i] / nc : 0.0;
-      Y[(int64_t)pc * K + i] = Yw[(int64_t)c * K + i];
+      X[(int64_t)pc * K + i] = nc > 0.0 ? __ldcg(B + (int64_t)c * K + i) / nc : 0.0;
+      Y[(int64_t)pc * K + i] = __ldcg(Yw + (int64_t)c * K + i);
     }
     if (lane == 0) sigma[pc] = nc;
   }
-  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = done ? sweep - 1 : -(sweep - 1);
+  if (gtid == 0 && sweeps_out) *sweeps_out = done ? sweep : -(sweep - 1);
 }
 
 __global__ void k_ritz_check(const double *__restrict__ sigma, const double *__restrict__ X, int K, int k,
@@ -354,11 +380,43 @@ cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const doub
   return cudaGetLastError();
 }
 
-cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, int *sweeps,
-                      const Ctl *ctl, cudaStream_t s) {
-  if (K > 1024) return cudaErrorInvalidValue;
-  GK_LAUNCH(k_jacobi_svd<<<1, 1024, 0, s>>>(Bm, Yw, K, sigma, X, Y, sweeps, ctl));
-  return cudaGetLastError();
+cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
+                      int *sweeps, const Ctl *ctl, cudaStream_t s) {
+  // cluster size: enough warps for the Kp/2 pairs of a round (8 per CTA), a power of two up to 16
+  const int pairs = (K + (K & 1)) / 2;
+  int want = 1;
+  while (want < 16 && want * 8 < pairs) want *= 2;
+  {
+    const cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  for (int cs = want; cs >= 1; cs /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int maxc = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&maxc, k_jacobi_cluster, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (maxc < cs) continue;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Bm, Yw, K, sigma, X, Y, nrm, pos, sweeps, ctl);
+    if (e == cudaSuccess) {
+      note_launch();
+      return cudaSuccess;
+    }
+    cudaGetLastError();
+  }
+  return cudaErrorLaunchFailure;
 }
 
 cudaError_t ritz_check(const double *sigma, const double *X, int K, int k, const double *betaK, double tol,

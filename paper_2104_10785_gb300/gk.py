@@ -47,7 +47,8 @@ class gk_opts(C.Structure):
 class gk_info(C.Structure):
     _fields_ = [
         ("steps", C.c_int32), ("restarts", C.c_int32), ("cycles", C.c_int32), ("kprime", C.c_int32),
-        ("stop_reason", C.c_int32), ("breakdowns", C.c_int32), ("matvecs", C.c_int64),
+        ("stop_reason", C.c_int32), ("breakdowns", C.c_int32), ("svd_sweeps", C.c_int32), ("reserved", C.c_int32),
+        ("matvecs", C.c_int64),
         ("resid_est_max", C.c_double), ("sigma_est", C.c_double), ("seconds", C.c_double),
         ("ms_matvec", C.c_double), ("ms_matvec_t", C.c_double), ("ms_orth", C.c_double), ("ms_small", C.c_double),
         ("ms_restart", C.c_double), ("n_matvec", C.c_int64), ("n_matvec_t", C.c_int64), ("launches", C.c_int64),
