@@ -18,8 +18,10 @@
  *  - The library never falls back to host computation: without a usable CUDA
  *    device every call returns GK_NO_DEVICE.
  *  - Workspace: if opts->workspace is NULL the library allocates its device
- *    workspace with cudaMallocAsync on the call's stream and frees it before
- *    returning.  Otherwise opts->workspace must point to at least
+ *    workspace (plus a staging copy of a host operator) on the call's stream
+ *    from its own stream-ordered memory pool and frees it before returning;
+ *    the pool keeps freed memory mapped for the next call (until the process
+ *    exits).  Otherwise opts->workspace must point to at least
  *    gk_*_workspace() bytes of device memory, 256-byte aligned.
  *  - Calls on different streams with different workspaces may run
  *    concurrently; two calls sharing one workspace must not overlap.

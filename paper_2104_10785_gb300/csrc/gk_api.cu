@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "gk_internal.cuh"
@@ -226,6 +227,32 @@ struct Workspace {
   }
 };
 
+// The library's own stream-ordered pool per device.  Its release threshold is
+// unbounded, so workspace freed at the end of a call stays mapped and the next
+// call reuses it instead of mapping fresh memory (which costs tens of
+// milliseconds for multi-GB operator staging buffers).
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {nullptr};
+
+int library_pool(int dev, cudaMemPool_t *out) {
+  if (dev < 0 || dev >= 64) return GK_NO_DEVICE;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    GK_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t thr = UINT64_MAX;
+    GK_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+    g_pool[dev] = p;
+  }
+  *out = g_pool[dev];
+  return GK_OK;
+}
+
 int acquire(Workspace &ws, size_t bytes, const gk_opts &o, cudaStream_t s) {
   ws.s = s;
   if (o.workspace) {
@@ -234,11 +261,16 @@ int acquire(Workspace &ws, size_t bytes, const gk_opts &o, cudaStream_t s) {
     ws.base = (char *)o.workspace;
     return GK_OK;
   }
+  int dev = 0;
+  GK_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  const int rc = library_pool(dev, &pool);
+  if (rc) return rc;
   void *p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    snprintf(g_err, sizeof(g_err), "cudaMallocAsync(%zu) -> %s", bytes, cudaGetErrorString(e));
+    snprintf(g_err, sizeof(g_err), "cudaMallocFromPoolAsync(%zu) -> %s", bytes, cudaGetErrorString(e));
     return GK_OUT_OF_MEMORY;
   }
   ws.base = (char *)p;

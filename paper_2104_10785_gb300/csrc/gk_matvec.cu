@@ -25,7 +25,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;   // 16-byte loads in flight per lane in the row kernel
 constexpr int kRowUnroll = 8;  // rows in flight per thread in the column kernel
-constexpr int kRun = 16;     // rows summed in f32 before an f64 combine (column kernel)
+constexpr int kRun = 32;     // rows summed in f32 before an f64 combine (column kernel)
 
 __device__ __forceinline__ bool halted(const Ctl *ctl) {
   return ctl != nullptr && *reinterpret_cast<const volatile int *>(&ctl->halt) != 0;
