@@ -52,7 +52,8 @@ typedef enum {
 typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 
 /* opts->flags bits */
-#define GK_FLAG_PROFILE 1 /* time kernel groups with CUDA events on opts->stream (gk_info.ms_*) */
+#define GK_FLAG_PROFILE 1  /* time kernel groups with CUDA events on opts->stream (gk_info.ms_*) */
+#define GK_FLAG_AUTOTUNE 2 /* batched calls: time each candidate cluster size on this batch, keep the fastest */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).
@@ -97,7 +98,7 @@ typedef struct {
   int32_t stop_reason;   /* gk_numrank: 0 reached kmax, 1 beta break, 2 alpha break */
   int32_t breakdowns;    /* exact breakdowns replaced by fresh directions */
   int32_t svd_sweeps;    /* gk_psvd: Jacobi sweeps of the last small SVD (negative: sweep limit reached) */
-  int32_t reserved;
+  int32_t reserved;      /* batched calls: cluster size used */
   int64_t matvecs;       /* products with A or A^T */
   double resid_est_max;  /* gk_psvd: max_i<k |beta_K X_{K,i}| / sigma_1 (Ritz residual estimate) */
   double sigma_est;      /* running lower bound on sigma_1 used by the break test */
@@ -171,6 +172,44 @@ int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const g
  * Section 5 and the tolerance of gk_psvd).  Outputs f64, device or host. */
 int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, const double *V, double *res_av,
                  double *res_atu, const gk_opts *opts);
+
+/* One problem of a batched call.  The operator is dense, in device memory,
+ * with n <= 4096 columns; outputs are device pointers.  The call writes the
+ * result fields. */
+typedef struct {
+  gk_matrix A;
+  int32_t k;             /* gk_psvd_batched: triplets wanted; gk_numrank_batched: kmax (0 = min(m, n, 256)) */
+  int32_t krylov_dim;    /* gk_psvd_batched: K (0 = the gk_psvd default), at most 510 */
+  double tol;            /* gk_psvd_batched: tolerance; gk_numrank_batched: eps */
+  double *U, *S, *V;     /* psvd: U m x k, S k, V n x k (column-major, f64); numrank: S optional sigma(B), kmax+1 */
+  const double *start;   /* optional start vector q1 (m, device) */
+  int32_t status;        /* result: per-problem status */
+  int32_t rank;          /* result (numrank): estimated rank */
+  int32_t steps;         /* result: bidiagonalization steps (numrank: k') */
+  int32_t restarts;      /* result (psvd) */
+  int32_t cycles;        /* result (psvd) */
+  int32_t breakdowns;    /* result (psvd) */
+  int64_t matvecs;       /* result: products with A or A^T */
+  double resid_est_max;  /* result (psvd): max Ritz residual estimate / sigma_1 */
+  double sigma_est;      /* result: running lower bound on sigma_1 */
+} gk_batch_item;
+
+/* Many independent partial SVDs (the method of gk_psvd) in ONE persistent
+ * launch.  The grid is a set of thread-block clusters; each cluster takes
+ * problems from a device queue ordered longest-first by a cost model (bytes of
+ * A times the expected passes, plus the Gram-Schmidt work) and solves each one
+ * entirely on the device, its CTAs splitting the rows and combining partial
+ * sums through distributed shared memory.  Cluster size: the autotuned choice
+ * for this batch signature (opts->flags GK_FLAG_AUTOTUNE times 2, 4, 8 and 16
+ * on the batch itself and remembers the fastest), else 8.  opts->seed + i
+ * seeds problem i's start vector when no start is given.  Returns GK_OK, or the
+ * worst per-problem status (errors first); gk_info sums the problems' counters
+ * and reports the cluster size used in its `reserved` field. */
+int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
+
+/* Many independent rank estimates (Algorithm 3 on Algorithm 1, as in
+ * gk_numrank) in one persistent launch, scheduled as gk_psvd_batched. */
+int gk_numrank_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
 
 /* Size of the device array behind gk_matvec_static (bytes). */
 #define GK_STATIC_SCRATCH_BYTES (32u << 20)

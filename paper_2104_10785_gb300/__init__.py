@@ -10,8 +10,10 @@ from .gk import (  # noqa: F401
     gk_matvec,
     gk_matvec_static,
     gk_numrank,
+    gk_numrank_batched,
     gk_numrank_workspace,
     gk_psvd,
+    gk_psvd_batched,
     gk_psvd_workspace,
     gk_residuals,
     last_cuda_error,

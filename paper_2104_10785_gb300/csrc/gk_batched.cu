@@ -1,0 +1,1010 @@
+// gk_batched.cu -- many independent problems in one persistent launch.
+//
+// The grid is a set of thread-block clusters; each cluster is a worker that
+// takes problems from a device queue (ordered longest-first by the host's cost
+// model) and solves each one completely on the device: the restarted partial
+// SVD (upper-bidiagonal Golub-Kahan with two-pass Gram-Schmidt, Jacobi SVD of
+// B, thick restarts) or Algorithm 3 (lower-bidiagonal Algorithm 1 with the
+// break test, then the Sturm-count rank of B).  The CTAs of a cluster split the
+// rows of A and of the basis vectors; coefficient vectors and the partial sums
+// of A^T u are combined through distributed shared memory in a fixed CTA order,
+// so every CTA obtains bitwise the same norms and takes the same decisions.
+// Rounds are separated by hardware cluster barriers: the kernel has no
+// software spin-wait.
+#include <cooperative_groups.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include "gk_device.cuh"
+#include "gk_internal.cuh"
+
+namespace gk {
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int kBThreads = 256;
+constexpr int kNMax = 4096;  // columns per problem (shared-memory copies of v and of A^T u partial sums)
+constexpr int kKMax = 512;   // basis columns per problem
+constexpr int kRunRows = 32; // f32 run length in rows before an f64 combine (A^T u)
+
+struct BProb {
+  const void *A;
+  int dtype, mode;  // mode 0: restarted partial SVD, 1: Algorithm 3
+  int64_t m, n, ld;
+  double scale;
+  int k, K, keep, max_restarts, passes, eps_rel;
+  double tol;  // psvd tolerance or Algorithm 3 eps
+  double *U, *S, *V;
+  const double *start;
+  uint64_t seed;
+  int64_t out;  // index of this problem's result row
+};
+
+struct BRes {
+  int status, cycles, restarts, steps, rank, breakdowns, sweeps, pad;
+  long long matvecs;
+  double resid_est, sigma_est;
+};
+
+struct BDims {
+  int64_t ldu, ldv;  // basis leading dimensions
+  int cols;          // basis columns per buffer
+  int K;             // small-matrix dimension
+};
+
+struct BWork {
+  double *Ub, *Ub2, *Vb, *Vb2, *w, *z, *alpha, *beta, *Bm, *Yw, *X, *Y, *sigma, *rho, *nrm;
+  int *pos;
+};
+
+__host__ __device__ inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+__host__ __device__ inline size_t work_bytes(const BDims &d) {
+  const size_t bu = al256(sizeof(double) * d.ldu * d.cols), bv = al256(sizeof(double) * d.ldv * d.cols);
+  const size_t kk = al256(sizeof(double) * (size_t)d.K * d.K), kv = al256(sizeof(double) * (d.K + 2));
+  return 2 * bu + 2 * bv + al256(8 * d.ldu) + al256(8 * d.ldv) + 2 * kv + 4 * kk + 3 * kv + al256(4 * (d.K + 2));
+}
+
+__device__ BWork carve(char *p, const BDims &d) {
+  BWork w;
+  auto take = [&](size_t bytes) {
+    char *q = p;
+    p += al256(bytes);
+    return q;
+  };
+  w.Ub = (double *)take(sizeof(double) * d.ldu * d.cols);
+  w.Ub2 = (double *)take(sizeof(double) * d.ldu * d.cols);
+  w.Vb = (double *)take(sizeof(double) * d.ldv * d.cols);
+  w.Vb2 = (double *)take(sizeof(double) * d.ldv * d.cols);
+  w.w = (double *)take(8 * d.ldu);
+  w.z = (double *)take(8 * d.ldv);
+  w.alpha = (double *)take(sizeof(double) * (d.K + 2));
+  w.beta = (double *)take(sizeof(double) * (d.K + 2));
+  w.Bm = (double *)take(sizeof(double) * (size_t)d.K * d.K);
+  w.Yw = (double *)take(sizeof(double) * (size_t)d.K * d.K);
+  w.X = (double *)take(sizeof(double) * (size_t)d.K * d.K);
+  w.Y = (double *)take(sizeof(double) * (size_t)d.K * d.K);
+  w.sigma = (double *)take(sizeof(double) * (d.K + 2));
+  w.rho = (double *)take(sizeof(double) * (d.K + 2));
+  w.nrm = (double *)take(sizeof(double) * (d.K + 2));
+  w.pos = (int *)take(4 * (d.K + 2));
+  return w;
+}
+
+// per-CTA shared memory of the solver
+struct Shm {
+  float *xs;     // kNMax: f32 copy of the vector A multiplies
+  double *zp;    // kNMax: this CTA's partial sums of A^T u (read by the others)
+  double *red;   // kKMax + 8: this CTA's partial coefficients (read by the others)
+  double *hv;    // kKMax + 8: the cluster totals
+  int *redi;     // kKMax: argmax indices
+  int *s_rot, *s_any, *s_idx;
+};
+
+__device__ __forceinline__ void slice(int64_t len, unsigned r, unsigned cs, int64_t *a, int64_t *b) {
+  *a = len * (int64_t)r / (int64_t)cs;
+  *b = len * (int64_t)(r + 1) / (int64_t)cs;
+}
+
+// sum of the CTAs' red[0..L) in rank order into hv[0..L) of every CTA
+__device__ void cl_allreduce(cg::cluster_group &cl, Shm &S, int L) {
+  cl.sync();
+  const unsigned cs = cl.num_blocks();
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    double t = 0.0;
+    for (unsigned c = 0; c < cs; ++c) t += cl.map_shared_rank(S.red, c)[i];
+    S.hv[i] = t;
+  }
+  cl.sync();
+}
+
+template <typename T>
+__device__ __forceinline__ float load_val(const T *p) {
+  return Vec<T>::one(p);
+}
+
+// w[r] = scale * (A x)_r - sum_c coefs[c] Qb[(c0 + c) ld + r], rows [r0, r1); x staged in S.xs (f32)
+template <typename T>
+__device__ void rows_matvec(const BProb &P, Shm &S, int64_t r0, int64_t r1, double *w, const double *Qb, int64_t ldq,
+                            int c0, int cn, const double *coefs) {
+  const T *A = (const T *)P.A;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t n = P.n;
+  const bool vec = std::is_same<T, double>::value ? false
+                                                   : (((uintptr_t)A % 16) == 0 && ((P.ld * (int64_t)sizeof(T)) % 16) == 0);
+  for (int64_t r = r0 + warp; r < r1; r += nw) {
+    const T *a = A + r * P.ld;
+    double acc = 0.0;
+    int64_t tail0 = 0;
+    if constexpr (!std::is_same<T, double>::value) {
+      if (vec) {
+        using VT = Vec<T>;
+        constexpr int E = VT::E;
+        const int64_t nv = n / E;
+        const typename VT::V *av = reinterpret_cast<const typename VT::V *>(a);
+        for (int64_t i = lane; i < nv; i += 32 * 4) {
+          float s = 0.f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t ii = i + 32 * q;
+            if (ii < nv) {
+              float f[E];
+              VT::unpack(__ldcs(av + ii), f);
+#pragma unroll
+              for (int e = 0; e < E; ++e) s = fmaf(f[e], S.xs[ii * E + e], s);
+            }
+          }
+          acc += (double)s;
+        }
+        tail0 = nv * E;
+      }
+      float s = 0.f;
+      int cnt = 0;
+      for (int64_t c = tail0 + lane; c < n; c += 32) {
+        s = fmaf(load_val<T>(a + c), S.xs[c], s);
+        if (++cnt == 32) {
+          acc += (double)s;
+          s = 0.f;
+          cnt = 0;
+        }
+      }
+      acc += (double)s;
+    }
+    acc = dev::warp_sum_d(acc);
+    if (lane == 0) {
+      double v = acc * P.scale;
+      for (int c = 0; c < cn; ++c) v -= coefs[c] * Qb[(int64_t)(c0 + c) * ldq + r];
+      w[r] = v;
+    }
+  }
+}
+
+// f64 operator: products in f64 with x read from the f64 basis column
+__device__ void rows_matvec_f64(const BProb &P, int64_t r0, int64_t r1, const double *x, double *w, const double *Qb,
+                                int64_t ldq, int c0, int cn, const double *coefs) {
+  const double *A = (const double *)P.A;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t r = r0 + warp; r < r1; r += nw) {
+    const double *a = A + r * P.ld;
+    double acc = 0.0;
+    for (int64_t c = lane; c < P.n; c += 32) acc = fma(a[c], x[c], acc);
+    acc = dev::warp_sum_d(acc);
+    if (lane == 0) {
+      double v = acc * P.scale;
+      for (int c = 0; c < cn; ++c) v -= coefs[c] * Qb[(int64_t)(c0 + c) * ldq + r];
+      w[r] = v;
+    }
+  }
+}
+
+// this CTA's partial sums zp[c] = sum_{r in [r0, r1)} a_rc u_r for all columns
+template <typename T>
+__device__ void rows_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *u) {
+  const T *A = (const T *)P.A;
+  const int64_t n = P.n;
+  constexpr int G = 8;  // column groups per sweep over the rows
+  for (int64_t g0 = 0; g0 * blockDim.x < n; g0 += G) {
+    float a32[G];
+    double a64[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      a32[g] = 0.f;
+      a64[g] = 0.0;
+    }
+    int run = 0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const T *a = A + r * P.ld;
+      const double ur = u[r];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int64_t c = (g0 + g) * blockDim.x + threadIdx.x;
+        if (c < n) {
+          if constexpr (std::is_same<T, double>::value)
+            a64[g] = fma(a[c], ur, a64[g]);
+          else
+            a32[g] = fmaf(load_val<T>(a + c), (float)ur, a32[g]);
+        }
+      }
+      if (++run == kRunRows) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          a64[g] += (double)a32[g];
+          a32[g] = 0.f;
+        }
+        run = 0;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t c = (g0 + g) * blockDim.x + threadIdx.x;
+      if (c < n) S.zp[c] = a64[g] + (double)a32[g];
+    }
+  }
+}
+
+// z[i] = scale * sum over CTAs of zp[i] - coef * sub[i] for i in [v0, v1)
+__device__ void reduce_matvec_t(cg::cluster_group &cl, const BProb &P, Shm &S, int64_t v0, int64_t v1, double *z,
+                                const double *sub, double coef) {
+  cl.sync();
+  const unsigned cs = cl.num_blocks();
+  for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
+    double t = 0.0;
+    for (unsigned c = 0; c < cs; ++c) t += cl.map_shared_rank(S.zp, c)[i];
+    z[i] = t * P.scale - (sub ? coef * sub[i] : 0.0);
+  }
+  cl.sync();
+}
+
+// classical Gram-Schmidt of the slice [s0, s1) of vec against j columns of Qb,
+// `passes` times, then the norm (the same value in every CTA)
+__device__ double cl_cgs_norm(cg::cluster_group &cl, Shm &S, double *vec, int64_t s0, int64_t s1, const double *Qb,
+                              int64_t ldq, int j, int passes) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = 0; p < passes && j > 0; ++p) {
+    for (int c = warp; c < j; c += nw) {
+      const double *q = Qb + (int64_t)c * ldq;
+      double s = 0.0;
+      for (int64_t r = s0 + lane; r < s1; r += 32) s = fma(q[r], vec[r], s);
+      s = dev::warp_sum_d(s);
+      if (lane == 0) S.red[c] = s;
+    }
+    cl_allreduce(cl, S, j);
+    for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) {
+      double acc = vec[r];
+      for (int c = 0; c < j; ++c) acc = fma(-Qb[(int64_t)c * ldq + r], S.hv[c], acc);
+      vec[r] = acc;
+    }
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) s = fma(vec[r], vec[r], s);
+  s = dev::warp_sum_d(s);
+  __shared__ double wred[32];
+  if (lane == 0) wred[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += wred[i];
+    S.red[0] = t;
+  }
+  cl_allreduce(cl, S, 1);
+  return sqrt(S.hv[0]);
+}
+
+__device__ void scale_slice(double *dst, const double *src, int64_t s0, int64_t s1, double f) {
+  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) dst[r] = src[r] * f;
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// q1 entries ~ N(2,1) (same stream as the single-problem start vector)
+__device__ double start_entry(uint64_t seed, int64_t i) {
+  const uint64_t b = (uint64_t)i >> 1;
+  const uint4 x = philox(make_uint4((unsigned)b, (unsigned)(b >> 32), 0u, 0u),
+                         make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  const double ua = ((double)(((uint64_t)(x.x >> 5) << 26) | (x.y >> 6)) + 0.5) * 0x1.0p-53;
+  const double ub = ((double)(((uint64_t)(x.z >> 5) << 26) | (x.w >> 6)) + 0.5) * 0x1.0p-53;
+  const double rr = sqrt(-2.0 * log(ua));
+  const double two_pi = 6.283185307179586476925286766559;
+  return 2.0 + ((i & 1) ? rr * sin(two_pi * ub) : rr * cos(two_pi * ub));
+}
+
+// replacement direction (SplitMix64) orthogonalized twice against j columns;
+// writes the normalized vector (or zero) into column dst; returns 1 if kept
+__device__ int cl_fresh(cg::cluster_group &cl, Shm &S, double *vec, int64_t s0, int64_t s1, const double *Qb,
+                        int64_t ldq, int j, double *dst, uint64_t seed, int64_t dnum) {
+  const uint64_t base = seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(dnum + 1));
+  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x)
+    vec[r] = (double)(splitmix64(base + (uint64_t)r) >> 11) * 0x1.0p-52 - 1.0;
+  __syncthreads();
+  const double n0 = cl_cgs_norm(cl, S, vec, s0, s1, Qb, ldq, 0, 0);
+  const double n1 = cl_cgs_norm(cl, S, vec, s0, s1, Qb, ldq, j, 2);
+  const bool keep = n1 > 1e-8 * n0;
+  scale_slice(dst, vec, s0, s1, keep ? 1.0 / n1 : 0.0);
+  return keep ? 1 : 0;
+}
+
+template <typename T>
+__device__ void stage_x(const BProb &P, Shm &S, const double *v) {
+  if constexpr (!std::is_same<T, double>::value) {
+    for (int64_t i = threadIdx.x; i < P.n; i += blockDim.x) S.xs[i] = (float)v[i];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void left_product(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *v, double *w,
+                             const double *Qb, int64_t ldq, int c0, int cn, const double *coefs) {
+  if constexpr (std::is_same<T, double>::value)
+    rows_matvec_f64(P, r0, r1, v, w, Qb, ldq, c0, cn, coefs);
+  else {
+    stage_x<T>(P, S, v);
+    rows_matvec<T>(P, S, r0, r1, w, Qb, ldq, c0, cn, coefs);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// restarted partial SVD of one problem on the calling cluster
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const BDims &D, Shm &S, BRes &res) {
+  const unsigned rank = cl.block_rank(), cs = cl.num_blocks();
+  const int64_t m = P.m, n = P.n, ldu = D.ldu, ldv = D.ldv;
+  const int K = P.K, k = P.k, keep = P.keep;
+  int64_t r0, r1, v0, v1;
+  slice(m, rank, cs, &r0, &r1);
+  slice(n, rank, cs, &v0, &v1);
+  double sest = 0.0;
+  int64_t nfresh = 0;
+  // start vector, normalized, in w
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) W.w[r] = P.start ? P.start[r] : start_entry(P.seed, r);
+  __syncthreads();
+  {
+    const double q = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, 0, 0);
+    scale_slice(W.w, W.w, r0, r1, q > 0.0 ? 1.0 / q : 0.0);
+  }
+  // v1 = A^T q1 / ||A^T q1||
+  rows_matvec_t<T>(P, S, r0, r1, W.w);
+  reduce_matvec_t(cl, P, S, v0, v1, W.z, nullptr, 0.0);
+  {
+    const double nv = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, 0, 0);
+    if (nv > 0.0)
+      scale_slice(W.Vb, W.z, v0, v1, 1.0 / nv);
+    else {
+      cl_fresh(cl, S, W.z, v0, v1, W.Vb, ldv, 0, W.Vb, P.seed, nfresh++);
+      res.breakdowns++;
+    }
+  }
+  res.matvecs = 1;
+  int l = 0;
+  for (int cycle = 0;; ++cycle) {
+    double bprev = 0.0;
+    for (int j = l; j < K; ++j) {
+      cl.sync();  // v_j complete in every slice
+      // left: w = A v_j - (beta_{j-1} u_{j-1} | sum_i rho_i u_i)
+      if (j == l && l > 0)
+        left_product<T>(P, S, r0, r1, W.Vb + (int64_t)j * ldv, W.w, W.Ub, ldu, 0, l, W.rho);
+      else if (j > 0)
+        left_product<T>(P, S, r0, r1, W.Vb + (int64_t)j * ldv, W.w, W.Ub, ldu, j - 1, 1, &bprev);
+      else
+        left_product<T>(P, S, r0, r1, W.Vb + (int64_t)j * ldv, W.w, W.Ub, ldu, 0, 0, nullptr);
+      double a = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, j, P.passes);
+      sest = fmax(sest, a);
+      if (!(a > 0x1.0p-46 * sest)) {
+        if (!isfinite(a)) {
+          res.status = GK_NUMERICAL;
+          return;
+        }
+        a = 0.0;
+        cl_fresh(cl, S, W.w, r0, r1, W.Ub, ldu, j, W.Ub + (int64_t)j * ldu, P.seed, nfresh++);
+        res.breakdowns++;
+      } else {
+        scale_slice(W.Ub + (int64_t)j * ldu, W.w, r0, r1, 1.0 / a);
+      }
+      if (rank == 0 && threadIdx.x == 0) W.alpha[j] = a;
+      // right: z = A^T u_j - alpha_j v_j
+      rows_matvec_t<T>(P, S, r0, r1, W.Ub + (int64_t)j * ldu);
+      reduce_matvec_t(cl, P, S, v0, v1, W.z, W.Vb + (int64_t)j * ldv, a);
+      double b = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, j + 1, P.passes);
+      sest = fmax(sest, b);
+      if (!(b > 0x1.0p-46 * sest)) {
+        if (!isfinite(b)) {
+          res.status = GK_NUMERICAL;
+          return;
+        }
+        b = 0.0;
+        cl_fresh(cl, S, W.z, v0, v1, W.Vb, ldv, j + 1, W.Vb + (int64_t)(j + 1) * ldv, P.seed, nfresh++);
+        res.breakdowns++;
+      } else {
+        scale_slice(W.Vb + (int64_t)(j + 1) * ldv, W.z, v0, v1, 1.0 / b);
+      }
+      if (rank == 0 && threadIdx.x == 0) W.beta[j] = b;
+      bprev = b;
+      res.matvecs += 2;
+      res.steps++;
+    }
+    // B of this cycle, its SVD, the Ritz residual test
+    cl.sync();
+    for (int64_t idx = (int64_t)rank * blockDim.x + threadIdx.x; idx < (int64_t)K * K; idx += (int64_t)cs * blockDim.x) {
+      const int r = (int)(idx % K), c = (int)(idx / K);
+      double v = 0.0;
+      if (r < l) {
+        if (c == r) v = W.sigma[r];
+        else if (c == l) v = W.rho[r];
+      } else {
+        if (c == r) v = W.alpha[r];
+        else if (c == r + 1) v = W.beta[r];
+      }
+      W.Bm[idx] = v;
+    }
+    res.sweeps = dev::cluster_jacobi(cl, W.Bm, W.Yw, K, W.sigma, W.X, W.Y, W.nrm, W.pos, S.s_rot, S.s_any);
+    const double bK = __ldcg(W.beta + (K - 1));
+    const double s1 = __ldcg(W.sigma);
+    double mx = 0.0;
+    for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(bK * __ldcg(W.X + (int64_t)i * K + (K - 1))));
+    res.cycles = cycle + 1;
+    res.resid_est = s1 > 0.0 ? mx / s1 : 0.0;
+    sest = fmax(sest, s1);
+    const bool conv = mx <= P.tol * s1;
+    if (conv || cycle >= P.max_restarts) {
+      res.status = conv ? GK_OK : GK_NOT_CONVERGED;
+      break;
+    }
+    // thick restart: U' = U_K X_keep, V' = [V_K Y_keep, v_{K+1}], rho = beta_K X_{K,:}
+    if (rank == 0)
+      for (int i = threadIdx.x; i < K; i += blockDim.x) W.rho[i] = bK * __ldcg(W.X + (int64_t)i * K + (K - 1));
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+      for (int i = 0; i < keep; ++i) {
+        double s = 0.0;
+        for (int c = 0; c < K; ++c) s = fma(W.Ub[(int64_t)c * ldu + r], __ldcg(W.X + (int64_t)i * K + c), s);
+        W.Ub2[(int64_t)i * ldu + r] = s;
+      }
+    for (int64_t r = v0 + threadIdx.x; r < v1; r += blockDim.x) {
+      for (int i = 0; i < keep; ++i) {
+        double s = 0.0;
+        for (int c = 0; c < K; ++c) s = fma(W.Vb[(int64_t)c * ldv + r], __ldcg(W.Y + (int64_t)i * K + c), s);
+        W.Vb2[(int64_t)i * ldv + r] = s;
+      }
+      W.Vb2[(int64_t)keep * ldv + r] = W.Vb[(int64_t)K * ldv + r];
+    }
+    double *t = W.Ub;
+    W.Ub = W.Ub2;
+    W.Ub2 = t;
+    t = W.Vb;
+    W.Vb = W.Vb2;
+    W.Vb2 = t;
+    l = keep;
+    res.restarts++;
+    cl.sync();
+  }
+  res.sigma_est = sest;
+  // outputs: U = U_K X_k, V = V_K Y_k, S = sigma_k; sign of the largest |v_i| entry positive
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+    for (int i = 0; i < k; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < K; ++c) s = fma(W.Ub[(int64_t)c * ldu + r], __ldcg(W.X + (int64_t)i * K + c), s);
+      P.U[(int64_t)i * m + r] = s;
+    }
+  for (int64_t r = v0 + threadIdx.x; r < v1; r += blockDim.x)
+    for (int i = 0; i < k; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < K; ++c) s = fma(W.Vb[(int64_t)c * ldv + r], __ldcg(W.Y + (int64_t)i * K + c), s);
+      P.V[(int64_t)i * n + r] = s;
+    }
+  if (rank == 0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) P.S[i] = __ldcg(W.sigma + i);
+  __syncthreads();
+  // this CTA's largest |v_i| entry (first index on ties) for every column i
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < k; i += nw) {
+    double best = -1.0;
+    int64_t bi = v0;
+    for (int64_t r = v0 + lane; r < v1; r += 32) {
+      const double a = fabs(P.V[(int64_t)i * n + r]);
+      if (a > best) {
+        best = a;
+        bi = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int64_t i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (b2 > best || (b2 == best && i2 < bi)) {
+        best = b2;
+        bi = i2;
+      }
+    }
+    if (lane == 0) {
+      S.red[i] = best;
+      S.redi[i] = (int)bi;
+    }
+  }
+  cl.sync();
+  // the cluster's choice: ranks hold consecutive slices, so the first maximum in rank order wins
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double best = -1.0;
+    int bi = 0;
+    for (unsigned c = 0; c < cs; ++c) {
+      const double b2 = cl.map_shared_rank(S.red, c)[i];
+      const int i2 = cl.map_shared_rank(S.redi, c)[i];
+      if (b2 > best) {
+        best = b2;
+        bi = i2;
+      }
+    }
+    S.hv[i] = (__ldcg(P.V + (int64_t)i * n + bi) < 0.0) ? -1.0 : 1.0;
+  }
+  cl.sync();
+  for (int i = 0; i < k; ++i) {
+    if (S.hv[i] > 0.0) continue;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) P.U[(int64_t)i * m + r] = -P.U[(int64_t)i * m + r];
+    for (int64_t r = v0 + threadIdx.x; r < v1; r += blockDim.x) P.V[(int64_t)i * n + r] = -P.V[(int64_t)i * n + r];
+  }
+  cl.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3 (on Algorithm 1) of one problem on the calling cluster
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, const BDims &D, Shm &S, BRes &res) {
+  const unsigned rank = cl.block_rank(), cs = cl.num_blocks();
+  const int64_t m = P.m, ldu = D.ldu, ldv = D.ldv;
+  const int kmax = P.K;
+  int64_t r0, r1, v0, v1;
+  slice(m, rank, cs, &r0, &r1);
+  slice(P.n, rank, cs, &v0, &v1);
+  const double eps = P.tol;
+  for (int i = rank * blockDim.x + threadIdx.x; i < kmax + 2; i += cs * blockDim.x) {
+    W.alpha[i] = 0.0;
+    W.beta[i] = 0.0;
+  }
+  // line 1: q1, normalized, is Q[:, 0]
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) W.w[r] = P.start ? P.start[r] : start_entry(P.seed, r);
+  __syncthreads();
+  {
+    const double q = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, 0, 0);
+    scale_slice(W.Ub, W.w, r0, r1, q > 0.0 ? 1.0 / q : 0.0);
+  }
+  // line 2: p1 = A^T q1, alpha_1 = ||p1||
+  rows_matvec_t<T>(P, S, r0, r1, W.Ub);
+  reduce_matvec_t(cl, P, S, v0, v1, W.z, nullptr, 0.0);
+  double a = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, 0, 0);
+  double sest = a;
+  res.matvecs = 1;
+  int kp = 0, reason = 0;
+  if (rank == 0 && threadIdx.x == 0) W.alpha[0] = a;
+  if (!isfinite(a)) {
+    res.status = GK_NUMERICAL;
+    return;
+  }
+  if (a <= (P.eps_rel ? eps * sest : eps)) {
+    reason = 2;
+  } else {
+    scale_slice(W.Vb, W.z, v0, v1, 1.0 / a);
+    int j;
+    for (j = 1; j <= kmax; ++j) {
+      cl.sync();  // p_j complete
+      const double aj = a;
+      left_product<T>(P, S, r0, r1, W.Vb + (int64_t)(j - 1) * ldv, W.w, W.Ub, ldu, j - 1, 1, &aj);
+      const double b = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, j, P.passes);
+      res.matvecs++;
+      if (rank == 0 && threadIdx.x == 0) W.beta[j] = b;
+      if (!isfinite(b)) {
+        res.status = GK_NUMERICAL;
+        return;
+      }
+      sest = fmax(sest, hypot(aj, b));
+      if (b <= (P.eps_rel ? eps * sest : eps)) {
+        kp = j;
+        reason = 1;
+        break;
+      }
+      scale_slice(W.Ub + (int64_t)j * ldu, W.w, r0, r1, 1.0 / b);
+      rows_matvec_t<T>(P, S, r0, r1, W.Ub + (int64_t)j * ldu);
+      reduce_matvec_t(cl, P, S, v0, v1, W.z, W.Vb + (int64_t)(j - 1) * ldv, b);
+      a = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, j, P.passes);
+      res.matvecs++;
+      if (rank == 0 && threadIdx.x == 0) W.alpha[j] = a;
+      if (!isfinite(a)) {
+        res.status = GK_NUMERICAL;
+        return;
+      }
+      sest = fmax(sest, hypot(b, a));
+      if (a <= (P.eps_rel ? eps * sest : eps)) {
+        kp = j;
+        reason = 2;
+        break;
+      }
+      scale_slice(W.Vb + (int64_t)j * ldv, W.z, v0, v1, 1.0 / a);
+    }
+    if (j > kmax) kp = kmax;
+  }
+  res.steps = kp;
+  res.sigma_est = sest;
+  cl.sync();
+  // lines 3-4 on one CTA: the singular values of B_{k'+1,k'} above the threshold
+  if (rank == 0) {
+    __shared__ int s_rank;
+    __shared__ double s_s1;
+    dev::block_bidiag_rank(W.alpha, W.beta, kp, eps, P.eps_rel, &s_rank, &s_s1, P.S);
+    __syncthreads();
+    res.rank = s_rank;
+  }
+  res.status = GK_OK;
+  res.pad = reason;
+  cl.sync();
+}
+
+__global__ void __launch_bounds__(kBThreads) k_batched(const BProb *__restrict__ probs, const int *__restrict__ order,
+                                                       int count, int *next, char *ws, size_t ws_stride, BDims D,
+                                                       BRes *results) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_rot, s_any, s_idx;
+  Shm S;
+  S.xs = reinterpret_cast<float *>(smem);
+  S.zp = reinterpret_cast<double *>(smem + sizeof(float) * kNMax);
+  S.red = S.zp + kNMax;
+  S.hv = S.red + kKMax + 8;
+  S.redi = reinterpret_cast<int *>(S.hv + kKMax + 8);
+  S.s_rot = &s_rot;
+  S.s_any = &s_any;
+  S.s_idx = &s_idx;
+  const unsigned cid = blockIdx.x / cl.num_blocks();
+  char *mine = ws + (size_t)cid * ws_stride;
+  for (;;) {
+    if (cl.block_rank() == 0 && threadIdx.x == 0) s_idx = atomicAdd(next, 1);
+    cl.sync();
+    const int idx = *cl.map_shared_rank(&s_idx, 0);
+    cl.sync();  // every CTA has read the index before the leader takes the next one
+    if (idx >= count) break;
+    const BProb P = probs[order[idx]];
+    BWork W = carve(mine, D);
+    BRes res;
+    memset(&res, 0, sizeof(res));
+    res.status = GK_OK;
+    if (P.mode == 0) {
+      switch (P.dtype) {
+        case GK_F64: solve_psvd<double>(cl, P, W, D, S, res); break;
+        case GK_F32: solve_psvd<float>(cl, P, W, D, S, res); break;
+        case GK_BF16: solve_psvd<__nv_bfloat16>(cl, P, W, D, S, res); break;
+        default: solve_psvd<__half>(cl, P, W, D, S, res); break;
+      }
+    } else {
+      switch (P.dtype) {
+        case GK_F64: solve_numrank<double>(cl, P, W, D, S, res); break;
+        case GK_F32: solve_numrank<float>(cl, P, W, D, S, res); break;
+        case GK_BF16: solve_numrank<__nv_bfloat16>(cl, P, W, D, S, res); break;
+        default: solve_numrank<__half>(cl, P, W, D, S, res); break;
+      }
+    }
+    cl.sync();
+    if (cl.block_rank() == 0 && threadIdx.x == 0) results[P.out] = res;
+  }
+}
+
+constexpr size_t kSmemBytes = sizeof(float) * kNMax + sizeof(double) * (kNMax + 2 * (kKMax + 8)) + sizeof(int) * kKMax;
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+bool dense_ok(const gk_matrix &A) {
+  return A.kind == GK_DENSE && A.m > 0 && A.n > 0 && A.n <= kNMax && A.ld >= A.n && A.vals && A.dtype >= GK_F64 &&
+         A.dtype <= GK_F16 && A.scale == A.scale && A.scale != 0.0 && A.m <= INT32_MAX;
+}
+
+size_t esz(int dtype) { return dtype == GK_F64 ? 8 : (dtype == GK_F32 ? 4 : 2); }
+
+struct TuneKey {
+  int count, mode, dtype;
+  int64_t work;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(count, mode, dtype, work) < std::tie(o.count, o.mode, o.dtype, o.work);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;  // cluster size chosen by the autotuner per batch signature
+
+int launch_batched(int cs, const BProb *dprobs, const int *dorder, int count, int *dnext, char *dws, size_t stride,
+                   const BDims &D, BRes *dres, int nclusters, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nclusters * cs, 1, 1);
+  cfg.blockDim = dim3(kBThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaMemsetAsync(dnext, 0, sizeof(int), s) != cudaSuccess) return GK_CUDA_ERROR;
+  if (cudaLaunchKernelEx(&cfg, k_batched, dprobs, dorder, count, dnext, dws, stride, D, dres) != cudaSuccess)
+    return GK_CUDA_ERROR;
+  note_launch();
+  return GK_OK;
+}
+
+int max_clusters(int cs, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(kBThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_batched, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  if (info) memset(info, 0, sizeof(*info));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return GK_NO_DEVICE;
+  }
+  if (!items || count <= 0) return GK_INVALID_ARG;
+  gk_opts o;
+  if (oin)
+    o = *oin;
+  else
+    gk_default_opts(&o);
+  if (o.reorth_passes < 1 || o.reorth_passes > 3 || o.max_restarts < 0) return GK_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  if (cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_CUDA_ERROR;
+  }
+  // problem table and the dimensions of the per-cluster workspace
+  std::vector<BProb> probs(count);
+  std::vector<double> cost(count);
+  BDims D{32, 32, 2, 2};
+  int dtype0 = items[0].A.dtype;
+  int64_t work = 0;
+  for (int i = 0; i < count; ++i) {
+    const gk_batch_item &it = items[i];
+    if (!dense_ok(it.A)) return GK_INVALID_ARG;
+    if (!(it.tol >= 0.0)) return GK_INVALID_ARG;
+    const int64_t m = it.A.m, n = it.A.n, mn = m < n ? m : n;
+    BProb &P = probs[i];
+    memset(&P, 0, sizeof(P));
+    P.A = it.A.vals;
+    P.dtype = it.A.dtype;
+    P.mode = mode;
+    P.m = m;
+    P.n = n;
+    P.ld = it.A.ld;
+    P.scale = it.A.scale;
+    P.tol = it.tol;
+    P.passes = o.reorth_passes;
+    P.max_restarts = o.max_restarts;
+    P.eps_rel = o.eps_absolute ? 0 : 1;
+    P.start = it.start;
+    P.seed = o.seed + (uint64_t)i;
+    P.out = i;
+    int cols;
+    if (mode == 0) {
+      const int k = it.k;
+      if (k < 1 || k > mn || !it.U || !it.S || !it.V) return GK_INVALID_ARG;
+      int K = it.krylov_dim;
+      if (K <= 0) {
+        int64_t d = 2 * (int64_t)k;
+        if (d < k + 16) d = k + 16;
+        if (d > mn) d = mn;
+        K = (int)d;
+      }
+      if (K < k || K > mn || (K == k && K < mn) || K > kKMax - 2) return GK_INVALID_ARG;
+      int keep = k + (K - k) / 2;
+      if (keep >= K) keep = K - 1;
+      if (keep < 0) keep = 0;
+      P.k = k;
+      P.K = K;
+      P.keep = keep;
+      P.U = it.U;
+      P.S = it.S;
+      P.V = it.V;
+      cols = K + 1;
+      D.K = std::max(D.K, K);
+    } else {
+      int km = it.k;
+      if (km <= 0 || km > mn) km = (int)std::min<int64_t>(mn, 256);
+      if (km > kKMax - 2) km = kKMax - 2;
+      P.K = km;
+      P.S = it.S;
+      cols = km + 2;
+      D.K = std::max(D.K, km + 2);
+    }
+    D.ldu = std::max<int64_t>(D.ldu, round_up(m, 32));
+    D.ldv = std::max<int64_t>(D.ldv, round_up(n, 32));
+    D.cols = std::max(D.cols, cols);
+    // cost model: the passes over A dominate, plus f64 Gram-Schmidt over the basis
+    const double kk = mode == 0 ? 2.0 * P.K : 1.2 * P.K;
+    cost[i] = (double)m * n * esz(P.dtype) * kk + 8.0 * (m + n) * (double)P.K * P.K * 1.5;
+    work += m * n;
+    if (P.dtype != dtype0) dtype0 = -1;
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+  // cluster size: the autotuned choice for this batch signature, else 8
+  const TuneKey key{count, mode, dtype0, work};
+  int cs = 8;
+  bool tune = (o.flags & GK_FLAG_AUTOTUNE) != 0;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto itk = g_tuned.find(key);
+    if (itk != g_tuned.end()) {
+      cs = itk->second;
+      tune = false;
+    }
+  }
+  const int cands[4] = {2, 4, 8, 16};
+  int ncl_max = 0;
+  for (int c : cands) ncl_max = std::max(ncl_max, max_clusters(c, s));
+  if (ncl_max <= 0) return GK_CUDA_ERROR;
+  const size_t stride = al256(work_bytes(D));
+  const int ncl_alloc = std::min(count, ncl_max);
+  const size_t bytes = al256(sizeof(BProb) * count) + al256(sizeof(int) * count) + 256 +
+                       al256(sizeof(BRes) * count) + stride * ncl_alloc;
+  void *base = nullptr;
+  if (o.workspace) {
+    if (o.workspace_bytes < bytes) return GK_OUT_OF_MEMORY;
+    base = o.workspace;
+  } else if (cudaMallocAsync(&base, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OUT_OF_MEMORY;
+  }
+  char *p = (char *)base;
+  BProb *dprobs = (BProb *)p;
+  p += al256(sizeof(BProb) * count);
+  int *dorder = (int *)p;
+  p += al256(sizeof(int) * count);
+  int *dnext = (int *)p;
+  p += 256;
+  BRes *dres = (BRes *)p;
+  p += al256(sizeof(BRes) * count);
+  char *dws = p;
+  int rc = GK_OK;
+  std::vector<BRes> res(count);
+  do {
+    if (cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dorder, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      rc = GK_CUDA_ERROR;
+      break;
+    }
+    if (tune) {
+      // autotuner: time the whole batch once per candidate cluster size, keep the fastest
+      float best = 1e30f;
+      int best_cs = cs;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int c : cands) {
+        const int ncl = std::min(count, max_clusters(c, s));
+        if (ncl <= 0) continue;
+        cudaEventRecord(e0, s);
+        if (launch_batched(c, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s) != GK_OK) {
+          cudaGetLastError();
+          continue;
+        }
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_cs = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cs = best_cs;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tuned[key] = cs;
+    }
+    const int ncl = std::min(count, max_clusters(cs, s));
+    if (ncl <= 0) {
+      rc = GK_CUDA_ERROR;
+      break;
+    }
+    rc = launch_batched(cs, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s);
+    if (rc) break;
+    if (cudaMemcpyAsync(res.data(), dres, sizeof(BRes) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = GK_CUDA_ERROR;
+      break;
+    }
+  } while (0);
+  if (!o.workspace) {
+    cudaFreeAsync(base, s);
+    cudaStreamSynchronize(s);
+  }
+  if (rc) return rc;
+  int worst = GK_OK;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  for (int i = 0; i < count; ++i) {
+    gk_batch_item &it = items[i];
+    const BRes &r = res[i];
+    it.status = r.status;
+    it.rank = r.rank;
+    it.steps = r.steps;
+    it.restarts = r.restarts;
+    it.cycles = r.cycles;
+    it.breakdowns = r.breakdowns;
+    it.matvecs = r.matvecs;
+    it.resid_est_max = r.resid_est;
+    it.sigma_est = r.sigma_est;
+    if (r.status < 0)
+      worst = r.status;
+    else if (worst == GK_OK && r.status != GK_OK)
+      worst = r.status;
+    inf.matvecs += r.matvecs;
+    inf.steps += r.steps;
+    inf.restarts += r.restarts;
+    inf.cycles += r.cycles;
+    inf.breakdowns += r.breakdowns;
+    inf.resid_est_max = std::max(inf.resid_est_max, r.resid_est);
+  }
+  inf.reserved = cs;  // cluster size used
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  return worst;
+}
+
+}  // namespace
+}  // namespace gk
+
+extern "C" int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info) {
+  return gk::batched_impl(items, count, 0, opts, info);
+}
+
+extern "C" int gk_numrank_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info) {
+  return gk::batched_impl(items, count, 1, opts, info);
+}

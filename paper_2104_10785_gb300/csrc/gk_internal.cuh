@@ -11,6 +11,8 @@
 // f64; f64 operators are multiplied in f64.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,6 +70,48 @@ struct Op {
 struct Dev {
   int sms;
   int id;
+};
+
+// ---- 16-byte vector of stored values -> floats (device helpers) ------------
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  static constexpr int E = 4;
+  using V = float4;
+  __device__ __forceinline__ static void unpack(const V &v, float *o) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ __forceinline__ static float one(const float *p) { return *p; }
+};
+template <>
+struct Vec<__nv_bfloat16> {
+  static constexpr int E = 8;
+  using V = uint4;
+  __device__ __forceinline__ static void unpack(const V &v, float *o) {
+    // bf16 is the high half of an f32 word; element 0 sits in the low half of v.x
+    o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xffff0000u);
+    o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
+    o[4] = __uint_as_float(v.z << 16); o[5] = __uint_as_float(v.z & 0xffff0000u);
+    o[6] = __uint_as_float(v.w << 16); o[7] = __uint_as_float(v.w & 0xffff0000u);
+  }
+  __device__ __forceinline__ static float one(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+};
+template <>
+struct Vec<__half> {
+  static constexpr int E = 8;
+  using V = uint4;
+  __device__ __forceinline__ static void unpack(const V &v, float *o) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
+      float2 f = __half22float2(h);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+  __device__ __forceinline__ static float one(const __half *p) { return __half2float(*p); }
 };
 
 // ---- sizing helpers ------------------------------------------------------

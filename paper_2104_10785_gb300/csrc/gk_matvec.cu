@@ -13,9 +13,6 @@
 //            a second kernel sums the partials in a fixed order (deterministic).
 //  * CSR   : a group of lanes per row (sized from the mean row length), f64
 //            products; A^T uses the caller's stored CSR of A^T.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
 #include "gk_internal.cuh"
 
 namespace gk {
@@ -30,48 +27,6 @@ constexpr int kRun = 32;     // rows summed in f32 before an f64 combine (column
 __device__ __forceinline__ bool halted(const Ctl *ctl) {
   return ctl != nullptr && *reinterpret_cast<const volatile int *>(&ctl->halt) != 0;
 }
-
-// ---- 16-byte vector of stored values -> floats ---------------------------
-template <typename T>
-struct Vec;
-template <>
-struct Vec<float> {
-  static constexpr int E = 4;
-  using V = float4;
-  __device__ __forceinline__ static void unpack(const V &v, float *o) {
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  }
-  __device__ __forceinline__ static float one(const float *p) { return *p; }
-};
-template <>
-struct Vec<__nv_bfloat16> {
-  static constexpr int E = 8;
-  using V = uint4;
-  __device__ __forceinline__ static void unpack(const V &v, float *o) {
-    // bf16 is the high half of an f32 word; element 0 sits in the low half of v.x
-    o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xffff0000u);
-    o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
-    o[4] = __uint_as_float(v.z << 16); o[5] = __uint_as_float(v.z & 0xffff0000u);
-    o[6] = __uint_as_float(v.w << 16); o[7] = __uint_as_float(v.w & 0xffff0000u);
-  }
-  __device__ __forceinline__ static float one(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-};
-template <>
-struct Vec<__half> {
-  static constexpr int E = 8;
-  using V = uint4;
-  __device__ __forceinline__ static void unpack(const V &v, float *o) {
-    const unsigned w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
-      float2 f = __half22float2(h);
-      o[2 * i] = f.x;
-      o[2 * i + 1] = f.y;
-    }
-  }
-  __device__ __forceinline__ static float one(const __half *p) { return __half2float(*p); }
-};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

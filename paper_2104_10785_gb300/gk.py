@@ -23,6 +23,7 @@ GK_OUT_OF_MEMORY, GK_NOT_IMPLEMENTED, GK_NO_DEVICE = -5, -6, -7
 GK_F64, GK_F32, GK_BF16, GK_F16 = 0, 1, 2, 3
 GK_DENSE, GK_CSR = 0, 1
 GK_FLAG_PROFILE = 1
+GK_FLAG_AUTOTUNE = 2
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -56,6 +57,16 @@ class gk_info(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class gk_batch_item(C.Structure):
+    _fields_ = [
+        ("A", gk_matrix), ("k", C.c_int32), ("krylov_dim", C.c_int32), ("tol", C.c_double),
+        ("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p), ("start", C.c_void_p),
+        ("status", C.c_int32), ("rank", C.c_int32), ("steps", C.c_int32), ("restarts", C.c_int32),
+        ("cycles", C.c_int32), ("breakdowns", C.c_int32), ("matvecs", C.c_int64),
+        ("resid_est_max", C.c_double), ("sigma_est", C.c_double),
+    ]
 
 
 class GKError(RuntimeError):
@@ -101,6 +112,10 @@ def lib():
             L.gk_residuals.restype = C.c_int
             L.gk_matvec_static.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
             L.gk_matvec_static.restype = C.c_int
+            L.gk_psvd_batched.argtypes = [P(gk_batch_item), C.c_int, P(gk_opts), P(gk_info)]
+            L.gk_psvd_batched.restype = C.c_int
+            L.gk_numrank_batched.argtypes = [P(gk_batch_item), C.c_int, P(gk_opts), P(gk_info)]
+            L.gk_numrank_batched.restype = C.c_int
             L.gk_status_string.argtypes = [C.c_int]
             L.gk_status_string.restype = C.c_char_p
             L.gk_last_cuda_error.argtypes = []
@@ -303,3 +318,95 @@ def gk_psvd_workspace(A, k: int, krylov_dim: int = 0) -> int:
 def gk_numrank_workspace(A, kmax: int = 0) -> int:
     M, _ = make_matrix(A)
     return int(lib().gk_numrank_workspace(C.byref(M), int(kmax), None))
+
+
+def _batch_opts(device, seed=None, max_restarts=None, reorth_passes=None, eps_absolute=False, autotune=False,
+                stream=None):
+    o, _ = _opts(device, 0, 0, max_restarts, reorth_passes, eps_absolute, seed, None, stream)
+    o.flags = GK_FLAG_AUTOTUNE if autotune else 0
+    return o
+
+
+def _item_result(it):
+    return dict(status=it.status, rank=it.rank, steps=it.steps, restarts=it.restarts, cycles=it.cycles,
+                breakdowns=it.breakdowns, matvecs=it.matvecs, resid_est_max=it.resid_est_max, sigma_est=it.sigma_est)
+
+
+def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=None, autotune=False, stream=None,
+                    check=True):
+    """Partial SVDs of many dense device operators in one persistent launch.
+
+    problems: sequence of dicts with keys A (2-D CUDA tensor, n <= 4096), k, and optionally
+    krylov_dim, tol (default 1e-8), start.  Returns (list of (U, S, V, result dict), status, info)."""
+    n = len(problems)
+    items = (gk_batch_item * n)()
+    keep = []
+    outs = []
+    dev = problems[0]["A"].device
+    for i, pr in enumerate(problems):
+        A = pr["A"]
+        M, _ = make_matrix(A)
+        k = int(pr["k"])
+        U = torch.empty((k, A.shape[0]), dtype=torch.float64, device=A.device)
+        S = torch.empty(k, dtype=torch.float64, device=A.device)
+        V = torch.empty((k, A.shape[1]), dtype=torch.float64, device=A.device)
+        st = None
+        if pr.get("start") is not None:
+            st = pr["start"].to(torch.float64).contiguous()
+            keep.append(st)
+        items[i].A = M
+        items[i].k = k
+        items[i].krylov_dim = int(pr.get("krylov_dim", 0))
+        items[i].tol = float(pr.get("tol", 1e-8))
+        items[i].U, items[i].S, items[i].V = U.data_ptr(), S.data_ptr(), V.data_ptr()
+        items[i].start = st.data_ptr() if st is not None else None
+        outs.append((U, S, V))
+        keep.append(A)
+    o = _batch_opts(dev, seed, max_restarts, reorth_passes, False, autotune, stream)
+    info = gk_info()
+    status = lib().gk_psvd_batched(items, n, C.byref(o), C.byref(info))
+    if check and status < 0:
+        raise GKError(status, "gk_psvd_batched")
+    return [(U.T, S, V.T, _item_result(items[i])) for i, (U, S, V) in enumerate(outs)], status, info.as_dict()
+
+
+def gk_numrank_batched(problems, *, seed=None, reorth_passes=None, eps_absolute=False, autotune=False, stream=None,
+                       want_sigma=False, check=True):
+    """Rank estimates (Algorithm 3) of many dense device operators in one persistent launch.
+
+    problems: sequence of dicts with keys A, and optionally kmax (0 = min(m, n, 256)), eps (default 1e-8),
+    start.  Returns (list of (rank, sigma or None, result dict), status, info)."""
+    n = len(problems)
+    items = (gk_batch_item * n)()
+    keep = []
+    sigs = []
+    dev = problems[0]["A"].device
+    for i, pr in enumerate(problems):
+        A = pr["A"]
+        M, _ = make_matrix(A)
+        km = int(pr.get("kmax", 0))
+        mn = min(A.shape)
+        cap = min(mn, 256) if km <= 0 or km > mn else km
+        sg = torch.zeros(cap + 2, dtype=torch.float64, device=A.device) if want_sigma else None
+        st = None
+        if pr.get("start") is not None:
+            st = pr["start"].to(torch.float64).contiguous()
+            keep.append(st)
+        items[i].A = M
+        items[i].k = km
+        items[i].tol = float(pr.get("eps", 1e-8))
+        items[i].S = sg.data_ptr() if sg is not None else None
+        items[i].start = st.data_ptr() if st is not None else None
+        sigs.append(sg)
+        keep.append(A)
+    o = _batch_opts(dev, seed, None, reorth_passes, eps_absolute, autotune, stream)
+    info = gk_info()
+    status = lib().gk_numrank_batched(items, n, C.byref(o), C.byref(info))
+    if check and status < 0:
+        raise GKError(status, "gk_numrank_batched")
+    res = []
+    for i in range(n):
+        r = _item_result(items[i])
+        sg = sigs[i][: r["steps"]] if sigs[i] is not None else None
+        res.append((items[i].rank, sg, r))
+    return res, status, info.as_dict()
