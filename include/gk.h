@@ -174,8 +174,8 @@ int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, co
                  double *res_atu, const gk_opts *opts);
 
 /* One problem of a batched call.  The operator is dense, in device memory,
- * with n <= 4096 columns; outputs are device pointers.  The call writes the
- * result fields. */
+ * with n <= 4096 columns; all problems of one call share one storage type;
+ * outputs are device pointers.  The call writes the result fields. */
 typedef struct {
   gk_matrix A;
   int32_t k;             /* gk_psvd_batched: triplets wanted; gk_numrank_batched: kmax (0 = min(m, n, 256)) */

@@ -139,51 +139,81 @@ __device__ void rows_matvec(const BProb &P, Shm &S, int64_t r0, int64_t r1, doub
   const T *A = (const T *)P.A;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t n = P.n;
-  const bool vec = std::is_same<T, double>::value ? false
-                                                   : (((uintptr_t)A % 16) == 0 && ((P.ld * (int64_t)sizeof(T)) % 16) == 0);
-  for (int64_t r = r0 + warp; r < r1; r += nw) {
-    const T *a = A + r * P.ld;
-    double acc = 0.0;
+  using VT = Vec<T>;
+  constexpr int E = VT::E;
+  const bool vec = (((uintptr_t)A % 16) == 0 && ((P.ld * (int64_t)sizeof(T)) % 16) == 0);
+  // two rows per warp at a time: 2 x 4 loads of 16 bytes in flight per lane
+  for (int64_t rb = r0 + 2 * warp; rb < r1; rb += 2 * nw) {
+    double acc[2] = {0.0, 0.0};
+    const int nr = (r1 - rb) >= 2 ? 2 : 1;  // the second row repeats the first when the slice is odd
     int64_t tail0 = 0;
-    if constexpr (!std::is_same<T, double>::value) {
-      if (vec) {
-        using VT = Vec<T>;
-        constexpr int E = VT::E;
-        const int64_t nv = n / E;
-        const typename VT::V *av = reinterpret_cast<const typename VT::V *>(a);
-        for (int64_t i = lane; i < nv; i += 32 * 4) {
-          float s = 0.f;
+    if (vec) {
+      const int64_t nv = n / E;
+      const typename VT::V *av0 = reinterpret_cast<const typename VT::V *>(A + rb * P.ld);
+      const typename VT::V *av1 = reinterpret_cast<const typename VT::V *>(A + (rb + (nr - 1)) * P.ld);
+      int64_t i = lane;
+      for (; i + 32 * 3 < nv; i += 32 * 4) {
+        typename VT::V b0[4], b1[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int64_t ii = i + 32 * q;
-            if (ii < nv) {
-              float f[E];
-              VT::unpack(__ldcs(av + ii), f);
-#pragma unroll
-              for (int e = 0; e < E; ++e) s = fmaf(f[e], S.xs[ii * E + e], s);
-            }
-          }
-          acc += (double)s;
+        for (int q = 0; q < 4; ++q) {
+          b0[q] = __ldcs(av0 + i + 32 * q);
+          b1[q] = __ldcs(av1 + i + 32 * q);
         }
-        tail0 = nv * E;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float f0[E], f1[E];
+          VT::unpack(b0[q], f0);
+          VT::unpack(b1[q], f1);
+          const int64_t ii = i + 32 * q;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const float xv = S.xs[ii * E + e];
+            s0 = fmaf(f0[e], xv, s0);
+            s1 = fmaf(f1[e], xv, s1);
+          }
+        }
+        acc[0] += (double)s0;
+        acc[1] += (double)s1;
       }
+      for (; i < nv; i += 32) {
+        float f0[E], f1[E];
+        VT::unpack(__ldcs(av0 + i), f0);
+        VT::unpack(__ldcs(av1 + i), f1);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          s0 = fmaf(f0[e], S.xs[i * E + e], s0);
+          s1 = fmaf(f1[e], S.xs[i * E + e], s1);
+        }
+        acc[0] += (double)s0;
+        acc[1] += (double)s1;
+      }
+      tail0 = nv * E;
+    }
+    for (int h = 0; h < nr; ++h) {
+      const T *a = A + (rb + h) * P.ld;
       float s = 0.f;
       int cnt = 0;
       for (int64_t c = tail0 + lane; c < n; c += 32) {
         s = fmaf(load_val<T>(a + c), S.xs[c], s);
         if (++cnt == 32) {
-          acc += (double)s;
+          acc[h] += (double)s;
           s = 0.f;
           cnt = 0;
         }
       }
-      acc += (double)s;
+      acc[h] += (double)s;
     }
-    acc = dev::warp_sum_d(acc);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) acc[h] = dev::warp_sum_d(acc[h]);
     if (lane == 0) {
-      double v = acc * P.scale;
-      for (int c = 0; c < cn; ++c) v -= coefs[c] * Qb[(int64_t)(c0 + c) * ldq + r];
-      w[r] = v;
+      for (int h = 0; h < nr; ++h) {
+        const int64_t r = rb + h;
+        double v = acc[h] * P.scale;
+        for (int c = 0; c < cn; ++c) v -= coefs[c] * Qb[(int64_t)(c0 + c) * ldq + r];
+        w[r] = v;
+      }
     }
   }
 }
@@ -206,47 +236,82 @@ __device__ void rows_matvec_f64(const BProb &P, int64_t r0, int64_t r1, const do
   }
 }
 
-// this CTA's partial sums zp[c] = sum_{r in [r0, r1)} a_rc u_r for all columns
+// this CTA's partial sums zp[c] = sum_{r in [r0, r1)} a_rc u_r for all columns.
+// Every thread owns one 16-byte group of columns per sweep (E columns), walks
+// the slice's rows eight at a time, sums f32 runs of kRunRows rows and combines
+// them in f64; rows that are not 16-byte aligned take the scalar path.
 template <typename T>
 __device__ void rows_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *u) {
   const T *A = (const T *)P.A;
   const int64_t n = P.n;
-  constexpr int G = 8;  // column groups per sweep over the rows
-  for (int64_t g0 = 0; g0 * blockDim.x < n; g0 += G) {
-    float a32[G];
-    double a64[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      a32[g] = 0.f;
-      a64[g] = 0.0;
+  if constexpr (std::is_same<T, double>::value) {
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      double acc = 0.0;
+      for (int64_t r = r0; r < r1; ++r) acc = fma(A[r * P.ld + c], u[r], acc);
+      S.zp[c] = acc;
     }
-    int run = 0;
-    for (int64_t r = r0; r < r1; ++r) {
-      const T *a = A + r * P.ld;
-      const double ur = u[r];
+  } else {
+    using VT = Vec<T>;
+    constexpr int E = VT::E;
+    const bool vec = ((uintptr_t)A % 16) == 0 && ((P.ld * (int64_t)sizeof(T)) % 16) == 0;
+    const int64_t nv = vec ? n / E : 0;  // whole 16-byte groups
+    const int64_t ldv = P.ld / E;
+    for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+      const typename VT::V *col = reinterpret_cast<const typename VT::V *>(A) + g;
+      float a32[E];
+      double a64[E];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int64_t c = (g0 + g) * blockDim.x + threadIdx.x;
-        if (c < n) {
-          if constexpr (std::is_same<T, double>::value)
-            a64[g] = fma(a[c], ur, a64[g]);
-          else
-            a32[g] = fmaf(load_val<T>(a + c), (float)ur, a32[g]);
+      for (int e = 0; e < E; ++e) {
+        a32[e] = 0.f;
+        a64[e] = 0.0;
+      }
+      int run = 0;
+      int64_t r = r0;
+      for (; r + 8 <= r1; r += 8) {
+        typename VT::V buf[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) buf[q] = __ldcs(col + (r + q) * ldv);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float f[E];
+          VT::unpack(buf[q], f);
+          const float ur = (float)u[r + q];
+#pragma unroll
+          for (int e = 0; e < E; ++e) a32[e] = fmaf(f[e], ur, a32[e]);
+        }
+        run += 8;
+        if (run >= kRunRows) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            a64[e] += (double)a32[e];
+            a32[e] = 0.f;
+          }
+          run = 0;
         }
       }
-      if (++run == kRunRows) {
+      for (; r < r1; ++r) {
+        float f[E];
+        VT::unpack(__ldcs(col + r * ldv), f);
+        const float ur = (float)u[r];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          a64[g] += (double)a32[g];
-          a32[g] = 0.f;
-        }
-        run = 0;
+        for (int e = 0; e < E; ++e) a32[e] = fmaf(f[e], ur, a32[e]);
       }
-    }
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int64_t c = (g0 + g) * blockDim.x + threadIdx.x;
-      if (c < n) S.zp[c] = a64[g] + (double)a32[g];
+      for (int e = 0; e < E; ++e) S.zp[g * E + e] = a64[e] + (double)a32[e];
+    }
+    for (int64_t c = nv * E + threadIdx.x; c < n; c += blockDim.x) {
+      double acc = 0.0;
+      float s = 0.f;
+      int run = 0;
+      for (int64_t r = r0; r < r1; ++r) {
+        s = fmaf(load_val<T>(A + r * P.ld + c), (float)u[r], s);
+        if (++run == kRunRows) {
+          acc += (double)s;
+          s = 0.f;
+          run = 0;
+        }
+      }
+      S.zp[c] = acc + (double)s;
     }
   }
 }
@@ -272,9 +337,16 @@ __device__ double cl_cgs_norm(cg::cluster_group &cl, Shm &S, double *vec, int64_
   for (int p = 0; p < passes && j > 0; ++p) {
     for (int c = warp; c < j; c += nw) {
       const double *q = Qb + (int64_t)c * ldq;
-      double s = 0.0;
-      for (int64_t r = s0 + lane; r < s1; r += 32) s = fma(q[r], vec[r], s);
-      s = dev::warp_sum_d(s);
+      double s0a = 0.0, s1a = 0.0, s2a = 0.0, s3a = 0.0;
+      int64_t r = s0 + lane;
+      for (; r + 96 < s1; r += 128) {
+        s0a = fma(q[r], vec[r], s0a);
+        s1a = fma(q[r + 32], vec[r + 32], s1a);
+        s2a = fma(q[r + 64], vec[r + 64], s2a);
+        s3a = fma(q[r + 96], vec[r + 96], s3a);
+      }
+      for (; r < s1; r += 32) s0a = fma(q[r], vec[r], s0a);
+      double s = dev::warp_sum_d((s0a + s1a) + (s2a + s3a));
       if (lane == 0) S.red[c] = s;
     }
     cl_allreduce(cl, S, j);
@@ -665,7 +737,8 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
   cl.sync();
 }
 
-__global__ void __launch_bounds__(kBThreads) k_batched(const BProb *__restrict__ probs, const int *__restrict__ order,
+template <typename T>
+__global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restrict__ probs, const int *__restrict__ order,
                                                        int count, int *next, char *ws, size_t ws_stride, BDims D,
                                                        BRes *results) {
   cg::cluster_group cl = cg::this_cluster();
@@ -693,21 +766,10 @@ __global__ void __launch_bounds__(kBThreads) k_batched(const BProb *__restrict__
     BRes res;
     memset(&res, 0, sizeof(res));
     res.status = GK_OK;
-    if (P.mode == 0) {
-      switch (P.dtype) {
-        case GK_F64: solve_psvd<double>(cl, P, W, D, S, res); break;
-        case GK_F32: solve_psvd<float>(cl, P, W, D, S, res); break;
-        case GK_BF16: solve_psvd<__nv_bfloat16>(cl, P, W, D, S, res); break;
-        default: solve_psvd<__half>(cl, P, W, D, S, res); break;
-      }
-    } else {
-      switch (P.dtype) {
-        case GK_F64: solve_numrank<double>(cl, P, W, D, S, res); break;
-        case GK_F32: solve_numrank<float>(cl, P, W, D, S, res); break;
-        case GK_BF16: solve_numrank<__nv_bfloat16>(cl, P, W, D, S, res); break;
-        default: solve_numrank<__half>(cl, P, W, D, S, res); break;
-      }
-    }
+    if (P.mode == 0)
+      solve_psvd<T>(cl, P, W, D, S, res);
+    else
+      solve_numrank<T>(cl, P, W, D, S, res);
     cl.sync();
     if (cl.block_rank() == 0 && threadIdx.x == 0) results[P.out] = res;
   }
@@ -735,8 +797,19 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;  // cluster size chosen by the autotuner per batch signature
 
-int launch_batched(int cs, const BProb *dprobs, const int *dorder, int count, int *dnext, char *dws, size_t stride,
-                   const BDims &D, BRes *dres, int nclusters, cudaStream_t s) {
+using BatchedKernel = void (*)(const BProb *, const int *, int, int *, char *, size_t, BDims, BRes *);
+
+BatchedKernel kernel_for(int dtype) {
+  switch (dtype) {
+    case GK_F64: return k_batched<double>;
+    case GK_F32: return k_batched<float>;
+    case GK_BF16: return k_batched<__nv_bfloat16>;
+    default: return k_batched<__half>;
+  }
+}
+
+int launch_batched(BatchedKernel kern, int cs, const BProb *dprobs, const int *dorder, int count, int *dnext, char *dws,
+                   size_t stride, const BDims &D, BRes *dres, int nclusters, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nclusters * cs, 1, 1);
   cfg.blockDim = dim3(kBThreads, 1, 1);
@@ -750,13 +823,13 @@ int launch_batched(int cs, const BProb *dprobs, const int *dorder, int count, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (cudaMemsetAsync(dnext, 0, sizeof(int), s) != cudaSuccess) return GK_CUDA_ERROR;
-  if (cudaLaunchKernelEx(&cfg, k_batched, dprobs, dorder, count, dnext, dws, stride, D, dres) != cudaSuccess)
+  if (cudaLaunchKernelEx(&cfg, kern, dprobs, dorder, count, dnext, dws, stride, D, dres) != cudaSuccess)
     return GK_CUDA_ERROR;
   note_launch();
   return GK_OK;
 }
 
-int max_clusters(int cs, cudaStream_t s) {
+int max_clusters(BatchedKernel kern, int cs, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, 1, 1);
   cfg.blockDim = dim3(kBThreads, 1, 1);
@@ -770,7 +843,7 @@ int max_clusters(int cs, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_batched, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -794,8 +867,13 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     gk_default_opts(&o);
   if (o.reorth_passes < 1 || o.reorth_passes > 3 || o.max_restarts < 0) return GK_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)o.stream;
-  if (cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+  const int dtype_all = items[0].A.dtype;
+  for (int i = 0; i < count; ++i)
+    if (items[i].A.dtype != dtype_all) return GK_INVALID_ARG;  // one storage type per batch
+  if (dtype_all < GK_F64 || dtype_all > GK_F16) return GK_INVALID_ARG;
+  const BatchedKernel kern = kernel_for(dtype_all);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
     return GK_CUDA_ERROR;
   }
@@ -885,7 +963,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
   }
   const int cands[4] = {2, 4, 8, 16};
   int ncl_max = 0;
-  for (int c : cands) ncl_max = std::max(ncl_max, max_clusters(c, s));
+  for (int c : cands) ncl_max = std::max(ncl_max, max_clusters(kern, c, s));
   if (ncl_max <= 0) return GK_CUDA_ERROR;
   const size_t stride = al256(work_bytes(D));
   const int ncl_alloc = std::min(count, ncl_max);
@@ -925,10 +1003,10 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       for (int c : cands) {
-        const int ncl = std::min(count, max_clusters(c, s));
+        const int ncl = std::min(count, max_clusters(kern, c, s));
         if (ncl <= 0) continue;
         cudaEventRecord(e0, s);
-        if (launch_batched(c, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s) != GK_OK) {
+        if (launch_batched(kern, c, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s) != GK_OK) {
           cudaGetLastError();
           continue;
         }
@@ -947,12 +1025,12 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
       std::lock_guard<std::mutex> lock(g_tune_mu);
       g_tuned[key] = cs;
     }
-    const int ncl = std::min(count, max_clusters(cs, s));
+    const int ncl = std::min(count, max_clusters(kern, cs, s));
     if (ncl <= 0) {
       rc = GK_CUDA_ERROR;
       break;
     }
-    rc = launch_batched(cs, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s);
+    rc = launch_batched(kern, cs, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s);
     if (rc) break;
     if (cudaMemcpyAsync(res.data(), dres, sizeof(BRes) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -136,6 +136,9 @@ WORKLOADS = {
     # CSR f32 1e6 x 5e5, 20 nnz/row + planted rank 50 (sigma_i = 100 * 0.95^i), top-50, tol 1e-8
     "csr_f32_1000000x500000_top50": dict(kind="sparse", m=1_000_000, n=500_000, per_row=20, k=50, K=100,
                                          tol=1e-8, dtype="f32", seed=BASE_SEED + 3),
+    # batched: 512 dense f32 problems, m ~ U[256, 4096], n ~ U[128, m], plus 784 x 256 and 256 x 784,
+    # rank r ~ U{5..64} products + 1e-6 noise; rank at eps = 1e-5, then the top-r triplets at tol 1e-8
+    "batched_f32_512_rank5to64": dict(kind="batched", count=512, eps=1e-5, tol=1e-8, dtype="f32", seed=BASE_SEED + 5),
     # dense bf16 1e5 x 4e4, sigma_i = i^-1.5, top-100, tol 1e-8
     "dense_bf16_100000x40000_top100": dict(kind="spectrum_pow", m=100000, n=40000, e=1.5, k=100, K=200,
                                            tol=1e-8, dtype="bf16", seed=BASE_SEED + 4),
@@ -189,3 +192,35 @@ def torch_prescribed_spectrum(m: int, n: int, sigma, seed: int, device="cuda", b
         return A, top[0], top[1]
     finally:
         torch.backends.cuda.matmul.allow_tf32 = tf32
+
+
+def batched_shapes(count: int, seed: int):
+    """(m, n, r) of a batch: m ~ U[256, 4096], n ~ U[128, m], r ~ U{5..64}; the first two problems
+    are the 784 x 256 and 256 x 784 shapes of the similarity-learning setting."""
+    g = rng(seed)
+    out = [(784, 256, int(g.integers(5, 65))), (256, 784, int(g.integers(5, 65)))]
+    while len(out) < count:
+        m = int(g.integers(256, 4097))
+        n = int(g.integers(128, m + 1))
+        out.append((m, n, int(g.integers(5, 65))))
+    return out[:count]
+
+
+def torch_batched_products(shapes, noise: float, seed: int, device="cuda"):
+    """Dense f32 operators G1 G2 + noise N(0,1) (formed in f64) for each (m, n, r); each stored
+    with its row stride rounded up to a multiple of 4 elements (16-byte rows); returns views m x n."""
+    import torch
+
+    g = torch.Generator(device=device).manual_seed(seed)
+    mats = []
+    for (m, n, r) in shapes:
+        G1 = torch.randn(m, r, generator=g, device=device, dtype=torch.float64)
+        G2 = torch.randn(r, n, generator=g, device=device, dtype=torch.float64)
+        A = G1 @ G2
+        if noise:
+            A += noise * torch.randn(m, n, generator=g, device=device, dtype=torch.float64)
+        ld = (n + 3) // 4 * 4
+        buf = torch.zeros(m, ld, device=device, dtype=torch.float32)
+        buf[:, :n] = A.to(torch.float32)
+        mats.append(buf[:, :n])
+    return mats
