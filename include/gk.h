@@ -183,8 +183,12 @@ typedef struct {
   double tol;            /* gk_psvd_batched: tolerance; gk_numrank_batched: eps */
   double *U, *S, *V;     /* psvd: U m x k, S k, V n x k (column-major, f64); numrank: S optional sigma(B), kmax+1 */
   const double *start;   /* optional start vector q1 (m, device) */
+  double rank_cut;       /* gk_psvd_batched: relative rank cut eps (0 = none): a Ritz triplet with
+                            theta_i + |residual estimate_i| <= eps * sigma_1 lies below the numerical
+                            rank (Algorithm 3's threshold) and is left out of the convergence test */
   int32_t status;        /* result: per-problem status */
-  int32_t rank;          /* result (numrank): estimated rank */
+  int32_t rank;          /* result: numrank: estimated rank; psvd: #{i <= k : theta_i > rank_cut * sigma_1}
+                            (k when rank_cut is 0) */
   int32_t steps;         /* result: bidiagonalization steps (numrank: k') */
   int32_t restarts;      /* result (psvd) */
   int32_t cycles;        /* result (psvd) */
@@ -192,6 +196,7 @@ typedef struct {
   int64_t matvecs;       /* result: products with A or A^T */
   double resid_est_max;  /* result (psvd): max Ritz residual estimate / sigma_1 */
   double sigma_est;      /* result: running lower bound on sigma_1 */
+  double sigma_next;     /* result (psvd): sigma_{k+1} of the last projected matrix B (a lower bound on sigma_{k+1}(A)) */
 } gk_batch_item;
 
 /* Many independent partial SVDs (the method of gk_psvd) in ONE persistent
@@ -210,6 +215,44 @@ int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_inf
 /* Many independent rank estimates (Algorithm 3 on Algorithm 1, as in
  * gk_numrank) in one persistent launch, scheduled as gk_psvd_batched. */
 int gk_numrank_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
+
+/* ---- learned predictor of the rank and the Krylov dimension ----------- */
+/* The paper has no counterpart: a small network that maps cheap sketch
+ * features of A to (log r, log K) so the batched solver can skip the separate
+ * rank pass and size its Krylov space; the solver's own convergence test
+ * judges the prediction and its restart loop is the fallback. */
+#define GK_SKETCH_COLS 32
+#define GK_FEATURES 35
+#define GK_MLP_TRAINABLE 75522 /* W1 256x35, b1 256, W2 256x256, b2 256, W3 2x256, b3 2 */
+#define GK_MLP_PARAMS 75596    /* trainable, then input mean/std (35+35), target mean/std (2+2) */
+
+/* Sketch features of `count` dense operators (device memory): Y = A Omega with
+ * Omega (n x 32) drawn N(0,1) from Philox4x32-10 + Box-Muller (entry (j,c) is
+ * draw 32j+c of the stream seeded with `seed`), the 32 singular values of Y
+ * (square roots of the eigenvalues of Y^T Y, f64 Jacobi), ||A||_F, m and n:
+ * features[p*35 + i] = log(sigma_i(Y) / (sqrt(32) ||A||_F)) for i < 32, then
+ * log ||A||_F, log m, log n (f32, device). */
+int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, float *features, const gk_opts *opts);
+
+/* Predictions out[b*2 + {0,1}] (de-standardized targets, f32, device or host)
+ * for B feature rows x (device), with the f32 parameters or their bf16
+ * rounding (bf16_weights != 0; sums stay f32). */
+int gk_mlp_forward(const float *params, const float *x, int B, float *out, int bf16_weights, const gk_opts *opts);
+
+/* Gradient of the training loss (0.5 * mean over rows of the squared error
+ * of the standardized outputs) w.r.t. the GK_MLP_TRAINABLE parameters, and the
+ * loss; all device pointers except loss (device or host). */
+int gk_mlp_grad(const float *params, const float *x, const float *y, int B, float *grad, float *loss,
+                const gk_opts *opts);
+
+/* Adam training (lr, betas 0.9/0.999, eps 1e-8) of the trainable parameters on
+ * n rows (x: n x 35, y: n x 2 targets, device) for `epochs` passes of
+ * minibatches of `batch` rows in a seeded order; adam_m/adam_v (device,
+ * GK_MLP_TRAINABLE each) carry the moments, t0 the step count so far;
+ * losses (device or host, `epochs` floats, optional) get each epoch's last
+ * minibatch loss. */
+int gk_mlp_train(float *params, float *adam_m, float *adam_v, int t0, const float *x, const float *y, int n,
+                 int batch, int epochs, float lr, uint64_t seed, float *losses, const gk_opts *opts);
 
 /* Size of the device array behind gk_matvec_static (bytes). */
 #define GK_STATIC_SCRATCH_BYTES (32u << 20)

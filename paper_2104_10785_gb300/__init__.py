@@ -8,6 +8,9 @@ from .gk import (  # noqa: F401
     CSR,
     GKError,
     gk_matvec,
+    gk_mlp_forward,
+    gk_mlp_grad,
+    gk_mlp_train,
     gk_matvec_static,
     gk_numrank,
     gk_numrank_batched,
@@ -16,6 +19,7 @@ from .gk import (  # noqa: F401
     gk_psvd_batched,
     gk_psvd_workspace,
     gk_residuals,
+    gk_sketch_batched,
     last_cuda_error,
     lib,
     library_path,

@@ -43,6 +43,7 @@ struct BProb {
   double scale;
   int k, K, keep, max_restarts, passes, eps_rel;
   double tol;  // psvd tolerance or Algorithm 3 eps
+  double cut;  // psvd: relative rank cut (0 = none)
   double *U, *S, *V;
   const double *start;
   uint64_t seed;
@@ -52,7 +53,7 @@ struct BProb {
 struct BRes {
   int status, cycles, restarts, steps, rank, breakdowns, sweeps, pad;
   long long matvecs;
-  double resid_est, sigma_est;
+  double resid_est, sigma_est, sigma_next;
 };
 
 struct BDims {
@@ -541,13 +542,22 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
     const double bK = __ldcg(W.beta + (K - 1));
     const double s1 = __ldcg(W.sigma);
     double mx = 0.0;
-    for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(bK * __ldcg(W.X + (int64_t)i * K + (K - 1))));
+    int above = 0;
+    for (int i = 0; i < k; ++i) {
+      const double ri = fabs(bK * __ldcg(W.X + (int64_t)i * K + (K - 1))), th = __ldcg(W.sigma + i);
+      // below the rank cut (with its residual bound) the triplet is not part of the answer
+      if (P.cut > 0.0 && th + ri <= P.cut * s1) continue;
+      mx = fmax(mx, ri);
+    }
+    for (int i = 0; i < k; ++i) above += !(P.cut > 0.0) || __ldcg(W.sigma + i) > P.cut * s1;
+    res.rank = above;
     res.cycles = cycle + 1;
     res.resid_est = s1 > 0.0 ? mx / s1 : 0.0;
     sest = fmax(sest, s1);
     const bool conv = mx <= P.tol * s1;
     if (conv || cycle >= P.max_restarts) {
       res.status = conv ? GK_OK : GK_NOT_CONVERGED;
+      res.sigma_next = k < K ? __ldcg(W.sigma + k) : 0.0;
       break;
     }
     // thick restart: U' = U_K X_keep, V' = [V_K Y_keep, v_{K+1}], rho = beta_K X_{K,:}
@@ -887,6 +897,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     const gk_batch_item &it = items[i];
     if (!dense_ok(it.A)) return GK_INVALID_ARG;
     if (!(it.tol >= 0.0)) return GK_INVALID_ARG;
+    if (mode == 0 && !(it.rank_cut >= 0.0 && it.rank_cut < 1.0)) return GK_INVALID_ARG;
     const int64_t m = it.A.m, n = it.A.n, mn = m < n ? m : n;
     BProb &P = probs[i];
     memset(&P, 0, sizeof(P));
@@ -902,6 +913,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     P.max_restarts = o.max_restarts;
     P.eps_rel = o.eps_absolute ? 0 : 1;
     P.start = it.start;
+    P.cut = mode == 0 ? it.rank_cut : 0.0;
     P.seed = o.seed + (uint64_t)i;
     P.out = i;
     int cols;
@@ -1058,6 +1070,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     it.matvecs = r.matvecs;
     it.resid_est_max = r.resid_est;
     it.sigma_est = r.sigma_est;
+    it.sigma_next = r.sigma_next;
     if (r.status < 0)
       worst = r.status;
     else if (worst == GK_OK && r.status != GK_OK)

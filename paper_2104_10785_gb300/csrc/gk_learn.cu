@@ -1,0 +1,598 @@
+// gk_learn.cu -- the learned predictor of the rank and the Krylov dimension.
+//
+// Sketch (per problem, one block): Y = A Omega with Omega (n x 32) drawn N(0,1)
+// from Philox4x32-10 + Box-Muller (entry (j, c) is draw number 32 j + c of the
+// stream seeded with the sketch seed), accumulated in f32 tiles; the 32 x 32
+// Gram matrix G = Y^T Y and ||A||_F^2 are accumulated in f64; the singular
+// values of Y are the square roots of G's eigenvalues (cyclic Jacobi, f64).
+// Features (35): log(sigma_i(Y) / (sqrt(32) ||A||_F)) for i = 1..32,
+// log ||A||_F, log m, log n.
+//
+// MLP 35 -> 256 -> 256 -> 2 with exact (erf) GELU, f32.  Parameter vector:
+// W1 (256 x 35), b1, W2 (256 x 256), b2, W3 (2 x 256), b3, then the input
+// mean/std (35 + 35) and target mean/std (2 + 2) used to standardize.
+// Training: forward, mean-squared-error loss on standardized targets,
+// backward, Adam; inference may use bf16-rounded weights with f32 sums.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+namespace {
+
+constexpr int kS = GK_SKETCH_COLS;  // 32
+constexpr int kF = GK_FEATURES;     // 35
+constexpr int kH = 256;
+
+// parameter offsets
+constexpr int oW1 = 0, ob1 = oW1 + kH * kF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH, ob3 = oW3 + 2 * kH;
+constexpr int oXmu = ob3 + 2, oXsd = oXmu + kF, oYmu = oXsd + kF, oYsd = oYmu + 2;
+static_assert(oYsd + 2 == GK_MLP_PARAMS, "parameter layout");
+static_assert(ob3 + 2 == GK_MLP_TRAINABLE, "trainable prefix");
+
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// draw i of the N(0,1) stream (the start-vector construction without the +2 shift)
+__device__ float normal_draw(uint64_t seed, int64_t i) {
+  const uint64_t b = (uint64_t)i >> 1;
+  const uint4 x = philox(make_uint4((unsigned)b, (unsigned)(b >> 32), 0u, 0u),
+                         make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  const double ua = ((double)(((uint64_t)(x.x >> 5) << 26) | (x.y >> 6)) + 0.5) * 0x1.0p-53;
+  const double ub = ((double)(((uint64_t)(x.z >> 5) << 26) | (x.w >> 6)) + 0.5) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * log(ua));
+  const double two_pi = 6.283185307179586476925286766559;
+  return (float)((i & 1) ? r * sin(two_pi * ub) : r * cos(two_pi * ub));
+}
+
+__global__ void k_omega(float *__restrict__ om, int64_t rows, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * kS; i += (int64_t)gridDim.x * blockDim.x)
+    om[i] = normal_draw(seed, i);
+}
+
+struct SkProb {
+  const void *A;
+  int dtype;
+  int64_t m, n, ld;
+  double scale;
+};
+
+template <typename T>
+__device__ __forceinline__ float ld_elem(const T *p) {
+  return Vec<T>::one(p);
+}
+template <>
+__device__ __forceinline__ float ld_elem<double>(const double *p) {
+  return (float)*p;
+}
+
+// one block per problem (grid-stride over the longest-first order)
+template <typename T>
+__device__ void sketch_one(const SkProb &P, const float *__restrict__ om, float *__restrict__ feat, float *sA,
+                           float *sO, float *sY, double *sG, double *sred) {
+  const T *A = (const T *)P.A;
+  const int tid = threadIdx.x;
+  const int tr = tid / 8, tc = (tid % 8) * 4;  // this thread's Y block entries: row tr, columns tc..tc+3
+  double g[4] = {0.0, 0.0, 0.0, 0.0};          // G entries (gi, gj..gj+3) this thread accumulates
+  const int gi = tid / 8, gj = (tid % 8) * 4;
+  double fro = 0.0;
+  for (int64_t r0 = 0; r0 < P.m; r0 += 32) {
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t c0 = 0; c0 < P.n; c0 += 128) {
+      // A tile 32 x 128 and Omega tile 128 x 32 into shared memory
+      for (int e = tid; e < 32 * 128; e += blockDim.x) {
+        const int rr = e / 128, cc = e % 128;
+        float v = 0.f;
+        if (r0 + rr < P.m && c0 + cc < P.n) v = ld_elem<T>(A + (r0 + rr) * P.ld + c0 + cc) * (float)P.scale;
+        sA[rr * 129 + cc] = v;
+        fro += (double)v * (double)v;
+      }
+      for (int e = tid; e < 128 * kS; e += blockDim.x) {
+        const int rr = e / kS, cc = e % kS;
+        sO[rr * kS + cc] = (c0 + rr < P.n) ? om[(c0 + rr) * kS + cc] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < 128; ++kk) {
+        const float a = sA[tr * 129 + kk];
+        const float4 o = *reinterpret_cast<const float4 *>(sO + kk * kS + tc);
+        y[0] = fmaf(a, o.x, y[0]);
+        y[1] = fmaf(a, o.y, y[1]);
+        y[2] = fmaf(a, o.z, y[2]);
+        y[3] = fmaf(a, o.w, y[3]);
+      }
+      __syncthreads();
+    }
+    // G += Y_blk^T Y_blk (f32 products summed in f64)
+    for (int q = 0; q < 4; ++q) sY[tr * 33 + tc + q] = y[q];
+    __syncthreads();
+    for (int rr = 0; rr < 32; ++rr) {
+      const double yi = sY[rr * 33 + gi];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g[q] = fma(yi, (double)sY[rr * 33 + gj + q], g[q]);
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 4; ++q) sG[gi * kS + gj + q] = g[q];
+  // ||A||_F^2: block sum in thread order
+  sred[tid] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += sred[i];
+    sred[0] = t;
+  }
+  __syncthreads();
+  const double fro2 = sred[0];
+  // eigenvalues of G by cyclic Jacobi (one warp performs the rotations)
+  if (tid < 32) {
+    const int lane = tid;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      int rotated = 0;
+      for (int p = 0; p < kS - 1; ++p)
+        for (int q = p + 1; q < kS; ++q) {
+          const double apq = sG[p * kS + q];
+          const double app = sG[p * kS + p], aqq = sG[q * kS + q];
+          if (apq == 0.0 || fabs(apq) <= 0x1.0p-52 * sqrt(fabs(app) * fabs(aqq))) continue;
+          rotated = 1;
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+          __syncwarp();
+          {  // columns p, q (row-major storage: G[i][p], G[i][q])
+            const double x = sG[lane * kS + p], y2 = sG[lane * kS + q];
+            sG[lane * kS + p] = c * x - s * y2;
+            sG[lane * kS + q] = s * x + c * y2;
+          }
+          __syncwarp();
+          {  // rows p, q
+            const double x = sG[p * kS + lane], y2 = sG[q * kS + lane];
+            sG[p * kS + lane] = c * x - s * y2;
+            sG[q * kS + lane] = s * x + c * y2;
+          }
+          __syncwarp();
+        }
+      if (!rotated) break;
+    }
+    // sort the eigenvalues descending and form the features
+    const double lam = sG[lane * kS + lane];
+    int rk = 0;
+    for (int o = 0; o < kS; ++o) {
+      const double lo = sG[o * kS + o];
+      rk += (lo > lam) || (lo == lam && o < lane);
+    }
+    const double nf = sqrt(fro2);
+    const double ref = sqrt((double)kS) * nf;
+    const double sv = sqrt(fmax(lam, 0.0));
+    feat[rk] = (float)log(fmax(sv, 1e-30 * fmax(ref, 1e-300)) / fmax(ref, 1e-300));
+    if (lane == 0) {
+      feat[kS] = (float)log(fmax(nf, 1e-300));
+      feat[kS + 1] = (float)log((double)P.m);
+      feat[kS + 2] = (float)log((double)P.n);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_sketch(const SkProb *__restrict__ probs, const int *__restrict__ order,
+                                                int count, const float *__restrict__ om, float *__restrict__ feats) {
+  __shared__ float sA[32 * 129];
+  __shared__ __align__(16) float sO[128 * kS];
+  __shared__ float sY[32 * 33];
+  __shared__ double sG[kS * kS];
+  __shared__ double sred[256];
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const int p = order[i];
+    const SkProb P = probs[p];
+    float *f = feats + (int64_t)p * kF;
+    switch (P.dtype) {
+      case GK_F64: sketch_one<double>(P, om, f, sA, sO, sY, sG, sred); break;
+      case GK_F32: sketch_one<float>(P, om, f, sA, sO, sY, sG, sred); break;
+      case GK_BF16: sketch_one<__nv_bfloat16>(P, om, f, sA, sO, sY, sG, sred); break;
+      default: sketch_one<__half>(P, om, f, sA, sO, sY, sG, sred); break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MLP kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// C (M x N) = A (M x K, row-major, lda) * op(B) + bias, op(B) = B^T when B is N x K (row-major, ldb);
+// weights may be bf16 (Wb) or f32 (B).  16 x 16 tiles of K.
+template <bool BF16W>
+__global__ void k_dense(const float *__restrict__ A, int lda, const float *__restrict__ B,
+                        const __nv_bfloat16 *__restrict__ Wb, int ldb, const float *__restrict__ bias, float *__restrict__ C,
+                        int ldc, int M, int N, int K, int act, float *__restrict__ Zsave) {
+  __shared__ float sa[16][17], sb[16][17];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    sa[ty][tx] = (row < M && k0 + tx < K) ? A[(int64_t)row * lda + k0 + tx] : 0.f;
+    const int brow = blockIdx.x * 16 + ty;  // output column index for the B tile load
+    float bv = 0.f;
+    if (brow < N && k0 + tx < K) bv = BF16W ? __bfloat162float(Wb[(int64_t)brow * ldb + k0 + tx]) : B[(int64_t)brow * ldb + k0 + tx];
+    sb[ty][tx] = bv;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fmaf(sa[ty][kk], sb[tx][kk], acc);
+    __syncthreads();
+  }
+  if (row < M && col < N) {
+    const float z = acc + (bias ? bias[col] : 0.f);
+    if (Zsave) Zsave[(int64_t)row * ldc + col] = z;
+    C[(int64_t)row * ldc + col] = act ? gelu(z) : z;
+  }
+}
+
+// C (M x N) = A^T (A: K x M row-major) * B (K x N row-major): weight gradients
+__global__ void k_dense_tn(const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
+                           float *__restrict__ C, int ldc, int M, int N, int K) {
+  __shared__ float sa[16][17], sb[16][17];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    sa[ty][tx] = (k0 + ty < K && blockIdx.y * 16 + tx < M) ? A[(int64_t)(k0 + ty) * lda + blockIdx.y * 16 + tx] : 0.f;
+    sb[ty][tx] = (k0 + ty < K && col < N) ? B[(int64_t)(k0 + ty) * ldb + col] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fmaf(sa[kk][ty], sb[kk][tx], acc);
+    __syncthreads();
+  }
+  if (row < M && col < N) C[(int64_t)row * ldc + col] = acc;
+}
+
+// C (M x N) = A (M x K row-major) * B (K x N row-major): backpropagation through a layer
+__global__ void k_dense_nn(const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
+                           float *__restrict__ C, int ldc, int M, int N, int K, const float *__restrict__ Zmul) {
+  __shared__ float sa[16][17], sb[16][17];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    sa[ty][tx] = (row < M && k0 + tx < K) ? A[(int64_t)row * lda + k0 + tx] : 0.f;
+    sb[ty][tx] = (k0 + ty < K && col < N) ? B[(int64_t)(k0 + ty) * ldb + col] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fmaf(sa[ty][kk], sb[kk][tx], acc);
+    __syncthreads();
+  }
+  if (row < M && col < N) C[(int64_t)row * ldc + col] = Zmul ? acc * gelu_grad(Zmul[(int64_t)row * ldc + col]) : acc;
+}
+
+// column sums of a (B x N) matrix into out[N] (bias gradients), fixed order
+__global__ void k_colsum(const float *__restrict__ X, int B, int N, float *__restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += X[(int64_t)b * N + c];
+  out[c] = s;
+}
+
+// standardized inputs X~ = (X - mu) / sd
+__global__ void k_standardize(const float *__restrict__ X, int B, const float *__restrict__ params,
+                              float *__restrict__ Xs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * kF) return;
+  const int f = i % kF;
+  Xs[i] = (X[i] - params[oXmu + f]) / params[oXsd + f];
+}
+
+// dO = (O - (Y - ymu)/ysd) / B and the loss sum 0.5 sum (O - Y~)^2 / B (one block)
+__global__ void k_mse(const float *__restrict__ O, const float *__restrict__ Y, int B, const float *__restrict__ params,
+                      float *__restrict__ dO, float *__restrict__ loss) {
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < 2 * B; i += blockDim.x) {
+    const int o = i % 2;
+    const float d = O[i] - (Y[i] - params[oYmu + o]) / params[oYsd + o];
+    dO[i] = d / (float)B;
+    s += 0.5f * d * d;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = red[0] / (float)B;
+}
+
+// de-standardized predictions: out = O * ysd + ymu
+__global__ void k_destandardize(float *__restrict__ O, int B, const float *__restrict__ params) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * B) return;
+  O[i] = O[i] * params[oYsd + i % 2] + params[oYmu + i % 2];
+}
+
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v, const float *__restrict__ g,
+                       int n, float lr, float b1, float b2, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+__global__ void k_gather(const float *__restrict__ x, const float *__restrict__ y, const int *__restrict__ idx, int B,
+                         float *__restrict__ xb, float *__restrict__ yb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B * kF) xb[i] = x[(int64_t)idx[i / kF] * kF + i % kF];
+  if (i < B * 2) yb[i] = y[(int64_t)idx[i / 2] * 2 + i % 2];
+}
+
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// activations of one forward pass (B rows)
+struct Acts {
+  float *Xs, *Z1, *A1, *Z2, *A2, *O;
+};
+
+size_t acts_floats(int B) { return (size_t)B * (kF + 4 * kH + 2); }
+
+Acts carve_acts(float *p, int B) {
+  Acts a;
+  a.Xs = p;
+  a.Z1 = a.Xs + (size_t)B * kF;
+  a.A1 = a.Z1 + (size_t)B * kH;
+  a.Z2 = a.A1 + (size_t)B * kH;
+  a.A2 = a.Z2 + (size_t)B * kH;
+  a.O = a.A2 + (size_t)B * kH;
+  return a;
+}
+
+cudaError_t forward(const float *params, const __nv_bfloat16 *wb, const float *X, int B, Acts a, cudaStream_t s) {
+  GK_LAUNCH(k_standardize<<<cdiv(B * kF, 256), 256, 0, s>>>(X, B, params, a.Xs));
+  const dim3 blk(256);
+  if (wb) {
+    GK_LAUNCH(k_dense<true><<<dim3(cdiv(kH, 16), cdiv(B, 16)), blk, 0, s>>>(a.Xs, kF, nullptr, wb + oW1, kF,
+                                                                            params + ob1, a.A1, kH, B, kH, kF, 1, a.Z1));
+    GK_LAUNCH(k_dense<true><<<dim3(cdiv(kH, 16), cdiv(B, 16)), blk, 0, s>>>(a.A1, kH, nullptr, wb + oW2, kH,
+                                                                            params + ob2, a.A2, kH, B, kH, kH, 1, a.Z2));
+    GK_LAUNCH(k_dense<true><<<dim3(1, cdiv(B, 16)), blk, 0, s>>>(a.A2, kH, nullptr, wb + oW3, kH, params + ob3, a.O, 2,
+                                                                 B, 2, kH, 0, nullptr));
+  } else {
+    GK_LAUNCH(k_dense<false><<<dim3(cdiv(kH, 16), cdiv(B, 16)), blk, 0, s>>>(a.Xs, kF, params + oW1, nullptr, kF,
+                                                                             params + ob1, a.A1, kH, B, kH, kF, 1, a.Z1));
+    GK_LAUNCH(k_dense<false><<<dim3(cdiv(kH, 16), cdiv(B, 16)), blk, 0, s>>>(a.A1, kH, params + oW2, nullptr, kH,
+                                                                             params + ob2, a.A2, kH, B, kH, kH, 1, a.Z2));
+    GK_LAUNCH(k_dense<false><<<dim3(1, cdiv(B, 16)), blk, 0, s>>>(a.A2, kH, params + oW3, nullptr, kH, params + ob3,
+                                                                  a.O, 2, B, 2, kH, 0, nullptr));
+  }
+  return cudaGetLastError();
+}
+
+// gradient of the loss w.r.t. the trainable parameters (written to grad[0..GK_MLP_TRAINABLE))
+cudaError_t backward(const float *params, const float *Y, int B, Acts a, float *grad, float *dbuf, float *loss,
+                     cudaStream_t s) {
+  float *dO = dbuf, *dZ2 = dO + 2 * (size_t)B, *dZ1 = dZ2 + (size_t)B * kH;
+  const dim3 blk(256);
+  GK_LAUNCH(k_mse<<<1, 256, 0, s>>>(a.O, Y, B, params, dO, loss));
+  // layer 3: dW3 = dO^T A2 (2 x 256), db3 = colsum dO
+  GK_LAUNCH(k_dense_tn<<<dim3(cdiv(kH, 16), 1), blk, 0, s>>>(dO, 2, a.A2, kH, grad + oW3, kH, 2, kH, B));
+  GK_LAUNCH(k_colsum<<<1, 256, 0, s>>>(dO, B, 2, grad + ob3));
+  // dZ2 = (dO W3) .* gelu'(Z2)
+  GK_LAUNCH(k_dense_nn<<<dim3(cdiv(kH, 16), cdiv(B, 16)), blk, 0, s>>>(dO, 2, params + oW3, kH, dZ2, kH, B, kH, 2,
+                                                                       a.Z2));
+  GK_LAUNCH(k_dense_tn<<<dim3(cdiv(kH, 16), cdiv(kH, 16)), blk, 0, s>>>(dZ2, kH, a.A1, kH, grad + oW2, kH, kH, kH, B));
+  GK_LAUNCH(k_colsum<<<1, 256, 0, s>>>(dZ2, B, kH, grad + ob2));
+  // dZ1 = (dZ2 W2) .* gelu'(Z1)
+  GK_LAUNCH(k_dense_nn<<<dim3(cdiv(kH, 16), cdiv(B, 16)), blk, 0, s>>>(dZ2, kH, params + oW2, kH, dZ1, kH, B, kH, kH,
+                                                                       a.Z1));
+  GK_LAUNCH(k_dense_tn<<<dim3(cdiv(kF, 16), cdiv(kH, 16)), blk, 0, s>>>(dZ1, kH, a.Xs, kF, grad + oW1, kF, kH, kF, B));
+  GK_LAUNCH(k_colsum<<<1, 256, 0, s>>>(dZ1, B, kH, grad + ob1));
+  return cudaGetLastError();
+}
+
+thread_local char l_err[256] = "";
+
+int check(cudaError_t e) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GK_CUDA_ERROR;
+  }
+  return GK_OK;
+}
+
+bool have_device() {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+}  // namespace gk
+
+using namespace gk;
+
+extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, float *features, const gk_opts *opts) {
+  if (!have_device()) return GK_NO_DEVICE;
+  if (!A || count <= 0 || !features) return GK_INVALID_ARG;
+  cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
+  std::vector<SkProb> pr(count);
+  std::vector<double> cost(count);
+  int64_t nmax = 1;
+  for (int i = 0; i < count; ++i) {
+    const gk_matrix &M = A[i];
+    if (M.kind != GK_DENSE || M.m <= 0 || M.n <= 0 || M.ld < M.n || !M.vals || M.dtype < GK_F64 || M.dtype > GK_F16)
+      return GK_INVALID_ARG;
+    pr[i] = SkProb{M.vals, M.dtype, M.m, M.n, M.ld, M.scale};
+    cost[i] = (double)M.m * (double)M.n;
+    nmax = nmax > M.n ? nmax : M.n;
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  const size_t bytes = sizeof(float) * (size_t)nmax * kS + sizeof(SkProb) * count + sizeof(int) * count + 1024;
+  char *base = nullptr;
+  if (cudaMallocAsync((void **)&base, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OUT_OF_MEMORY;
+  }
+  float *om = (float *)base;
+  SkProb *dpr = (SkProb *)(base + ((sizeof(float) * (size_t)nmax * kS + 255) / 256 * 256));
+  int *dord = (int *)((char *)dpr + ((sizeof(SkProb) * count + 255) / 256 * 256));
+  int rc = GK_OK;
+  do {
+    if ((rc = check(cudaMemcpyAsync(dpr, pr.data(), sizeof(SkProb) * count, cudaMemcpyHostToDevice, s)))) break;
+    if ((rc = check(cudaMemcpyAsync(dord, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s)))) break;
+    GK_LAUNCH(k_omega<<<(int)std::min<int64_t>(4096, (nmax * kS + 255) / 256), 256, 0, s>>>(om, nmax, seed));
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    GK_LAUNCH(k_sketch<<<std::min(count, 4 * sms), 256, 0, s>>>(dpr, dord, count, om, features));
+    if ((rc = check(cudaGetLastError()))) break;
+    rc = check(cudaStreamSynchronize(s));
+  } while (0);
+  cudaFreeAsync(base, s);
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+extern "C" int gk_mlp_forward(const float *params, const float *x, int B, float *out, int bf16_weights,
+                              const gk_opts *opts) {
+  if (!have_device()) return GK_NO_DEVICE;
+  if (!params || !x || !out || B <= 0) return GK_INVALID_ARG;
+  cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
+  const size_t na = acts_floats(B);
+  char *base = nullptr;
+  const size_t bytes = sizeof(float) * na + sizeof(__nv_bfloat16) * GK_MLP_TRAINABLE + 512;
+  if (cudaMallocAsync((void **)&base, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OUT_OF_MEMORY;
+  }
+  Acts a = carve_acts((float *)base, B);
+  __nv_bfloat16 *wb = bf16_weights ? (__nv_bfloat16 *)(base + (sizeof(float) * na + 255) / 256 * 256) : nullptr;
+  int rc = GK_OK;
+  do {
+    if (wb) GK_LAUNCH(k_to_bf16<<<cdiv(GK_MLP_TRAINABLE, 256), 256, 0, s>>>(params, wb, GK_MLP_TRAINABLE));
+    if ((rc = check(forward(params, wb, x, B, a, s)))) break;
+    GK_LAUNCH(k_destandardize<<<cdiv(2 * B, 256), 256, 0, s>>>(a.O, B, params));
+    if ((rc = check(cudaMemcpyAsync(out, a.O, sizeof(float) * 2 * B, cudaMemcpyDefault, s)))) break;
+    rc = check(cudaStreamSynchronize(s));
+  } while (0);
+  cudaFreeAsync(base, s);
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+extern "C" int gk_mlp_grad(const float *params, const float *x, const float *y, int B, float *grad, float *loss,
+                           const gk_opts *opts) {
+  if (!have_device()) return GK_NO_DEVICE;
+  if (!params || !x || !y || !grad || B <= 0) return GK_INVALID_ARG;
+  cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
+  const size_t na = acts_floats(B), nd = (size_t)B * (2 + 2 * kH);
+  char *base = nullptr;
+  if (cudaMallocAsync((void **)&base, sizeof(float) * (na + nd + 1) + 512, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OUT_OF_MEMORY;
+  }
+  Acts a = carve_acts((float *)base, B);
+  float *dbuf = (float *)base + na;
+  float *dloss = dbuf + nd;
+  int rc = GK_OK;
+  do {
+    if ((rc = check(forward(params, nullptr, x, B, a, s)))) break;
+    if ((rc = check(backward(params, y, B, a, grad, dbuf, dloss, s)))) break;
+    if (loss && (rc = check(cudaMemcpyAsync(loss, dloss, sizeof(float), cudaMemcpyDefault, s)))) break;
+    rc = check(cudaStreamSynchronize(s));
+  } while (0);
+  cudaFreeAsync(base, s);
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+extern "C" int gk_mlp_train(float *params, float *adam_m, float *adam_v, int t0, const float *x, const float *y,
+                            int n, int batch, int epochs, float lr, uint64_t seed, float *losses, const gk_opts *opts) {
+  if (!have_device()) return GK_NO_DEVICE;
+  if (!params || !adam_m || !adam_v || !x || !y || n <= 0 || batch <= 0 || epochs <= 0 || !(lr > 0.f))
+    return GK_INVALID_ARG;
+  cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
+  const int B = batch < n ? batch : n;
+  const size_t na = acts_floats(B), nd = (size_t)B * (2 + 2 * kH);
+  char *base = nullptr;
+  const size_t bytes =
+      sizeof(float) * (na + nd + GK_MLP_TRAINABLE + (size_t)B * (kF + 2) + (size_t)epochs) + sizeof(int) * (size_t)n + 2048;
+  if (cudaMallocAsync((void **)&base, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OUT_OF_MEMORY;
+  }
+  Acts a = carve_acts((float *)base, B);
+  float *dbuf = (float *)base + na;
+  float *grad = dbuf + nd;
+  float *xb = grad + GK_MLP_TRAINABLE;
+  float *yb = xb + (size_t)B * kF;
+  float *eloss = yb + (size_t)B * 2;
+  int *dperm = (int *)(eloss + epochs + 64);
+  // minibatches: a seeded permutation per epoch, drawn on the host (SplitMix64 keys)
+  std::vector<int> perm(n);
+  int rc = GK_OK;
+  int t = t0;
+  const float b1 = 0.9f, b2 = 0.999f;
+  uint64_t st = seed;
+  for (int ep = 0; ep < epochs && rc == GK_OK; ++ep) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = n - 1; i > 0; --i) {  // Fisher-Yates with SplitMix64
+      st += 0x9E3779B97F4A7C15ull;
+      uint64_t z = st;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const int j = (int)(z % (uint64_t)(i + 1));
+      std::swap(perm[i], perm[j]);
+    }
+    float *lsum = eloss + ep;
+    if ((rc = check(cudaMemsetAsync(lsum, 0, sizeof(float), s)))) break;
+    if ((rc = check(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)))) break;
+    // the host copy of perm is rewritten next epoch: wait for this one to land
+    if ((rc = check(cudaStreamSynchronize(s)))) break;
+    for (int b0 = 0; b0 + B <= n && rc == GK_OK; b0 += B) {
+      GK_LAUNCH(k_gather<<<cdiv(B * kF, 256), 256, 0, s>>>(x, y, dperm + b0, B, xb, yb));
+      if ((rc = check(forward(params, nullptr, xb, B, a, s)))) break;
+      if ((rc = check(backward(params, yb, B, a, grad, dbuf, nullptr, s)))) break;
+      ++t;
+      const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+      GK_LAUNCH(k_adam<<<cdiv(GK_MLP_TRAINABLE, 256), 256, 0, s>>>(params, adam_m, adam_v, grad, GK_MLP_TRAINABLE, lr, b1,
+                                                                   b2, c1, c2));
+    }
+    // epoch loss on the last minibatch after the update
+    if (rc == GK_OK) {
+      if ((rc = check(forward(params, nullptr, xb, B, a, s)))) break;
+      GK_LAUNCH(k_mse<<<1, 256, 0, s>>>(a.O, yb, B, params, dbuf, lsum));
+    }
+  }
+  if (rc == GK_OK && losses) rc = check(cudaMemcpyAsync(losses, eloss, sizeof(float) * epochs, cudaMemcpyDefault, s));
+  if (rc == GK_OK) rc = check(cudaStreamSynchronize(s));
+  cudaFreeAsync(base, s);
+  cudaStreamSynchronize(s);
+  return rc;
+}

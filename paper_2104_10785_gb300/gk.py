@@ -63,9 +63,9 @@ class gk_batch_item(C.Structure):
     _fields_ = [
         ("A", gk_matrix), ("k", C.c_int32), ("krylov_dim", C.c_int32), ("tol", C.c_double),
         ("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p), ("start", C.c_void_p),
-        ("status", C.c_int32), ("rank", C.c_int32), ("steps", C.c_int32), ("restarts", C.c_int32),
+        ("rank_cut", C.c_double), ("status", C.c_int32), ("rank", C.c_int32), ("steps", C.c_int32), ("restarts", C.c_int32),
         ("cycles", C.c_int32), ("breakdowns", C.c_int32), ("matvecs", C.c_int64),
-        ("resid_est_max", C.c_double), ("sigma_est", C.c_double),
+        ("resid_est_max", C.c_double), ("sigma_est", C.c_double), ("sigma_next", C.c_double),
     ]
 
 
@@ -116,6 +116,15 @@ def lib():
             L.gk_psvd_batched.restype = C.c_int
             L.gk_numrank_batched.argtypes = [P(gk_batch_item), C.c_int, P(gk_opts), P(gk_info)]
             L.gk_numrank_batched.restype = C.c_int
+            L.gk_sketch_batched.argtypes = [P(gk_matrix), C.c_int, C.c_uint64, C.c_void_p, P(gk_opts)]
+            L.gk_sketch_batched.restype = C.c_int
+            L.gk_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, P(gk_opts)]
+            L.gk_mlp_forward.restype = C.c_int
+            L.gk_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
+            L.gk_mlp_grad.restype = C.c_int
+            L.gk_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_int, C.c_int, C.c_float, C.c_uint64, C.c_void_p, P(gk_opts)]
+            L.gk_mlp_train.restype = C.c_int
             L.gk_status_string.argtypes = [C.c_int]
             L.gk_status_string.restype = C.c_char_p
             L.gk_last_cuda_error.argtypes = []
@@ -329,7 +338,8 @@ def _batch_opts(device, seed=None, max_restarts=None, reorth_passes=None, eps_ab
 
 def _item_result(it):
     return dict(status=it.status, rank=it.rank, steps=it.steps, restarts=it.restarts, cycles=it.cycles,
-                breakdowns=it.breakdowns, matvecs=it.matvecs, resid_est_max=it.resid_est_max, sigma_est=it.sigma_est)
+                breakdowns=it.breakdowns, matvecs=it.matvecs, resid_est_max=it.resid_est_max, sigma_est=it.sigma_est,
+                sigma_next=it.sigma_next)
 
 
 def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=None, autotune=False, stream=None,
@@ -337,7 +347,7 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
     """Partial SVDs of many dense device operators in one persistent launch.
 
     problems: sequence of dicts with keys A (2-D CUDA tensor, n <= 4096), k, and optionally
-    krylov_dim, tol (default 1e-8), start.  Returns (list of (U, S, V, result dict), status, info)."""
+    krylov_dim, tol (default 1e-8), start, rank_cut (relative eps; triplets below it are not converged).  Returns (list of (U, S, V, result dict), status, info)."""
     n = len(problems)
     items = (gk_batch_item * n)()
     keep = []
@@ -358,6 +368,7 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
         items[i].k = k
         items[i].krylov_dim = int(pr.get("krylov_dim", 0))
         items[i].tol = float(pr.get("tol", 1e-8))
+        items[i].rank_cut = float(pr.get("rank_cut", 0.0))
         items[i].U, items[i].S, items[i].V = U.data_ptr(), S.data_ptr(), V.data_ptr()
         items[i].start = st.data_ptr() if st is not None else None
         outs.append((U, S, V))
@@ -410,3 +421,66 @@ def gk_numrank_batched(problems, *, seed=None, reorth_passes=None, eps_absolute=
         sg = sigs[i][: r["steps"]] if sigs[i] is not None else None
         res.append((items[i].rank, sg, r))
     return res, status, info.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# learned predictor (sketch features and the MLP)
+# ---------------------------------------------------------------------------
+GK_FEATURES = 35
+GK_MLP_TRAINABLE = 75522
+GK_MLP_PARAMS = 75596
+
+
+def _stream_opts(device, stream=None):
+    o = default_opts()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    o.stream = s.cuda_stream
+    return o
+
+
+def gk_sketch_batched(mats, seed: int = 2104107, stream=None):
+    """35 sketch features per dense device operator (count x 35 float32, device)."""
+    n = len(mats)
+    arr = (gk_matrix * n)()
+    for i, A in enumerate(mats):
+        arr[i], _ = make_matrix(A)
+    feats = torch.empty((n, GK_FEATURES), dtype=torch.float32, device=mats[0].device)
+    st = lib().gk_sketch_batched(arr, n, C.c_uint64(seed & (2**64 - 1)), _ptr(feats),
+                                 C.byref(_stream_opts(mats[0].device, stream)))
+    if st < 0:
+        raise GKError(st, "gk_sketch_batched")
+    return feats
+
+
+def gk_mlp_forward(params, x, bf16_weights: bool = False, stream=None):
+    x = x.to(torch.float32).contiguous()
+    out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+    st = lib().gk_mlp_forward(_ptr(params), _ptr(x), x.shape[0], _ptr(out), int(bf16_weights),
+                              C.byref(_stream_opts(x.device, stream)))
+    if st < 0:
+        raise GKError(st, "gk_mlp_forward")
+    return out
+
+
+def gk_mlp_grad(params, x, y, stream=None):
+    x = x.to(torch.float32).contiguous()
+    y = y.to(torch.float32).contiguous()
+    g = torch.empty(GK_MLP_TRAINABLE, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    st = lib().gk_mlp_grad(_ptr(params), _ptr(x), _ptr(y), x.shape[0], _ptr(g), _ptr(loss),
+                           C.byref(_stream_opts(x.device, stream)))
+    if st < 0:
+        raise GKError(st, "gk_mlp_grad")
+    return g, float(loss)
+
+
+def gk_mlp_train(params, adam_m, adam_v, t0, x, y, batch=256, epochs=1, lr=1e-3, seed=0, stream=None):
+    x = x.to(torch.float32).contiguous()
+    y = y.to(torch.float32).contiguous()
+    losses = torch.zeros(epochs, dtype=torch.float32, device=x.device)
+    st = lib().gk_mlp_train(_ptr(params), _ptr(adam_m), _ptr(adam_v), int(t0), _ptr(x), _ptr(y), x.shape[0],
+                            int(batch), int(epochs), float(lr), C.c_uint64(seed), _ptr(losses),
+                            C.byref(_stream_opts(x.device, stream)))
+    if st < 0:
+        raise GKError(st, "gk_mlp_train")
+    return losses

@@ -1,0 +1,221 @@
+"""Learned rank / Krylov-dimension predictor for the batched solver.
+
+Host orchestration only: every numerical step runs in libgk.so's kernels (sketch
+features, the batched solvers, the MLP forward/backward/Adam).
+
+Targets, measured by the plain method itself on each training matrix:
+  r  = the rank gk_numrank_batched (Algorithm 3) returns at eps;
+  K* = the smallest Krylov dimension in r + {2, 4, 6, 8, 12, 16, 24, 32} (then 2r + 16)
+       at which gk_psvd_batched(k = r, K) converges in ONE cycle at tol (found by a
+       per-problem binary search over that grid; the largest entry if none does).
+The network maps the 35 sketch features to (log r, log K*).
+
+Pipelines on a batch of dense device operators:
+  plain:   gk_numrank_batched -> r; gk_psvd_batched(k = r, default K).
+  learned: sketch + network -> (r^, K^), r^ rounded up with a safety margin;
+           gk_psvd_batched(k = r^, K = K^, rank_cut = eps), the restart loop covering a
+           Krylov dimension that was too small.  The solver's own spectrum judges r^: the
+           triplets below eps * sigma_1 are left out of the convergence test and dropped,
+           so an over-estimate costs a little work; if no Ritz value of the last projected
+           matrix fell below the cut (every theta_i, i <= r^ + 1, above eps * sigma_1) the
+           rank was under-estimated and that problem is re-solved by the plain pipeline.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import gk
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PARAMS_FILE = os.path.join(HERE, "predictor_params.f32")
+SKETCH_SEED = 0x5E7C4
+K_OFFSETS = (2, 4, 6, 8, 12, 16, 24, 32)
+RANK_MARGIN = (1.05, 1)  # r^ = ceil(1.05 * exp(prediction)) + 1: an under-estimate costs a re-solve
+K_MARGIN = 2  # added to the predicted Krylov dimension
+K_LIMIT = 500
+
+
+def k_grid(r, mn):
+    g = [min(r + o, mn) for o in K_OFFSETS] + [min(2 * r + 16, mn)]
+    out = []
+    for v in g:
+        if v > r and v not in out:
+            out.append(v)
+    return out or [mn]
+
+
+def targets(mats, eps=1e-5, tol=1e-8, seed=None):
+    """(rank, K*) per operator, measured with the batched solvers."""
+    res, st, _ = gk.gk_numrank_batched([dict(A=A, eps=eps, kmax=min(min(A.shape), 160)) for A in mats], seed=seed)
+    ranks = [max(1, r[0]) for r in res]
+    grids = [k_grid(r, min(A.shape)) for r, A in zip(ranks, mats)]
+    lo = [0] * len(mats)
+    hi = [len(g) - 1 for g in grids]
+    while any(l < h for l, h in zip(lo, hi)):
+        idx = [i for i in range(len(mats)) if lo[i] < hi[i]]
+        probs = []
+        for i in idx:
+            mid = (lo[i] + hi[i]) // 2
+            probs.append(dict(A=mats[i], k=ranks[i], krylov_dim=grids[i][mid], tol=tol))
+        out, _, _ = gk.gk_psvd_batched(probs, max_restarts=0, seed=seed, check=False)
+        for i, o in zip(idx, out):
+            mid = (lo[i] + hi[i]) // 2
+            if o[3]["status"] == gk.GK_OK:
+                hi[i] = mid
+            else:
+                lo[i] = mid + 1
+    kstar = [g[h] for g, h in zip(grids, hi)]
+    return ranks, kstar
+
+
+def dataset(n_total, seed, batch=512, eps=1e-5, tol=1e-8, log=None):
+    """Features and targets of n_total seeded training operators (recipe of the batched workload)."""
+    import synth
+
+    X, Y = [], []
+    done = 0
+    b = 0
+    while done < n_total:
+        cnt = min(batch, n_total - done)
+        shapes = synth.batched_shapes(cnt, seed + b)
+        mats = synth.torch_batched_products(shapes, 1e-6, seed + b, fast=True)
+        feats = gk.gk_sketch_batched(mats, SKETCH_SEED)
+        r, k = targets(mats, eps, tol, seed=seed + b)
+        X.append(feats)
+        Y.append(torch.tensor(np.log(np.stack([r, k], axis=1)), dtype=torch.float32, device=feats.device))
+        done += cnt
+        b += 1
+        del mats
+        if log:
+            log(f"dataset {done}/{n_total}")
+    return torch.cat(X), torch.cat(Y)
+
+
+def init_params(X, Y, seed=0):
+    """Seeded initial parameters (scaled normal weights, zero biases) plus the
+    standardization statistics of the training features and targets."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    F, H = gk.GK_FEATURES, 256
+
+    def w(o, i):
+        return torch.randn(o, i, generator=g) * math.sqrt(2.0 / i)
+
+    parts = [w(H, F).ravel(), torch.zeros(H), w(H, H).ravel(), torch.zeros(H), w(2, H).ravel() * 0.5, torch.zeros(2)]
+    xmu = X.mean(0).cpu()
+    xsd = X.std(0).cpu().clamp_min(1e-3)
+    ymu = Y.mean(0).cpu()
+    ysd = Y.std(0).cpu().clamp_min(1e-3)
+    p = torch.cat(parts + [xmu, xsd, ymu, ysd]).to(torch.float32)
+    assert p.numel() == gk.GK_MLP_PARAMS
+    return p.to(X.device)
+
+
+def train(X, Y, epochs=200, batch=256, lr=1e-3, seed=0):
+    params = init_params(X, Y, seed)
+    m = torch.zeros(gk.GK_MLP_TRAINABLE, dtype=torch.float32, device=X.device)
+    v = torch.zeros_like(m)
+    losses = gk.gk_mlp_train(params, m, v, 0, X, Y, batch=batch, epochs=epochs, lr=lr, seed=seed)
+    return params, losses
+
+
+def save(params, path=PARAMS_FILE):
+    params.detach().cpu().numpy().astype(np.float32).tofile(path)
+
+
+def load(device="cuda", path=PARAMS_FILE):
+    if not os.path.exists(path):
+        return None
+    a = np.fromfile(path, dtype=np.float32)
+    if a.size != gk.GK_MLP_PARAMS:
+        return None
+    return torch.from_numpy(a).to(device)
+
+
+def predict_raw(mats, params, bf16=True):
+    """The network's de-standardized outputs (log r, log K) per operator (host array)."""
+    feats = gk.gk_sketch_batched(mats, SKETCH_SEED)
+    return gk.gk_mlp_forward(params, feats, bf16_weights=bf16).cpu().numpy()
+
+
+def predict(mats, params, bf16=True):
+    """(r^, K^) per operator: the rank rounded up with the safety margin, K^ >= r^ + 2."""
+    out = predict_raw(mats, params, bf16)
+    with np.errstate(over="ignore", invalid="ignore"):
+        rc = np.exp(np.clip(out[:, 0], -20.0, 20.0))
+        kc = np.exp(np.clip(out[:, 1], -20.0, 20.0))
+    res = []
+    for A, rf, kf in zip(mats, rc, kc):
+        mn = min(A.shape)
+        lim = min(mn, K_LIMIT)
+        ri = int(min(max(1, math.ceil(RANK_MARGIN[0] * rf) + RANK_MARGIN[1]), lim - 1))
+        Ki = int(math.ceil(kf)) + K_MARGIN + (ri - int(round(rf)))
+        Ki = int(min(max(Ki, ri + 2), lim))
+        res.append((ri, Ki))
+    return res
+
+
+def plain_batched(mats, eps=1e-5, tol=1e-8):
+    """Algorithm 3 for the rank, then the top-r partial SVD with the default Krylov dimension."""
+    res, _, info1 = gk.gk_numrank_batched([dict(A=A, eps=eps, kmax=min(min(A.shape), 160)) for A in mats])
+    ranks = [max(1, r[0]) for r in res]
+    out, st, info2 = gk.gk_psvd_batched([dict(A=A, k=r, tol=tol) for A, r in zip(mats, ranks)])
+    return ranks, out, dict(matvecs=info1["matvecs"] + info2["matvecs"], status=st)
+
+
+def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200):
+    """Predicted (rank, K), one batched partial SVD with the rank cut, judged by the solver's spectrum;
+    under-estimated ranks fall back to the plain pipeline."""
+    pred = predict(mats, params)
+    out, st, info = gk.gk_psvd_batched(
+        [dict(A=A, k=r, krylov_dim=K, tol=tol, rank_cut=eps) for A, (r, K) in zip(mats, pred)],
+        max_restarts=max_restarts)
+    ranks = []
+    redo = []
+    for i, (U, S, V, rr) in enumerate(out):
+        s1 = float(S[0]) if S.numel() else 0.0
+        seen_below = rr["rank"] < len(S) or rr["sigma_next"] <= eps * s1
+        if rr["status"] != gk.GK_OK or not seen_below:
+            redo.append(i)
+            ranks.append(None)
+        else:
+            ranks.append(max(1, rr["rank"]))
+    matvecs = info["matvecs"]
+    if redo:
+        rr_, out2, inf2 = plain_batched([mats[i] for i in redo], eps, tol)
+        for j, i in enumerate(redo):
+            ranks[i] = rr_[j]
+            out[i] = out2[j]
+        matvecs += inf2["matvecs"]
+    final = [(U[:, :r], S[:r], V[:, :r], rr) for (U, S, V, rr), r in zip(out, ranks)]
+    return ranks, final, dict(matvecs=matvecs, fallbacks=len(redo), status=st, predicted=pred)
+
+
+def main(argv=None):
+    """Regenerate the committed weights: seeded training operators (the batched workload's recipe),
+    targets measured by the batched solvers, Adam training through the library's kernels."""
+    import argparse
+    import time
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=20480)
+    ap.add_argument("--seed", type=int, default=1000)
+    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default=PARAMS_FILE)
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    X, Y = dataset(a.count, a.seed, log=lambda s: print(s, flush=True))
+    t1 = time.time()
+    params, losses = train(X, Y, epochs=a.epochs, batch=a.batch, lr=a.lr, seed=a.seed)
+    losses = losses.cpu().numpy()
+    save(params, a.out)
+    print(f"dataset {t1 - t0:.1f} s, training {time.time() - t1:.1f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}")
+
+
+if __name__ == "__main__":
+    main()

@@ -206,19 +206,21 @@ def batched_shapes(count: int, seed: int):
     return out[:count]
 
 
-def torch_batched_products(shapes, noise: float, seed: int, device="cuda"):
-    """Dense f32 operators G1 G2 + noise N(0,1) (formed in f64) for each (m, n, r); each stored
-    with its row stride rounded up to a multiple of 4 elements (16-byte rows); returns views m x n."""
+def torch_batched_products(shapes, noise: float, seed: int, device="cuda", fast: bool = False):
+    """Dense f32 operators G1 G2 + noise N(0,1) (formed in f64, or in f32 with fast=True) for each
+    (m, n, r); each stored with its row stride rounded up to a multiple of 4 elements (16-byte
+    rows); returns views m x n."""
     import torch
 
     g = torch.Generator(device=device).manual_seed(seed)
+    dt = torch.float32 if fast else torch.float64
     mats = []
     for (m, n, r) in shapes:
-        G1 = torch.randn(m, r, generator=g, device=device, dtype=torch.float64)
-        G2 = torch.randn(r, n, generator=g, device=device, dtype=torch.float64)
+        G1 = torch.randn(m, r, generator=g, device=device, dtype=dt)
+        G2 = torch.randn(r, n, generator=g, device=device, dtype=dt)
         A = G1 @ G2
         if noise:
-            A += noise * torch.randn(m, n, generator=g, device=device, dtype=torch.float64)
+            A += noise * torch.randn(m, n, generator=g, device=device, dtype=dt)
         ld = (n + 3) // 4 * 4
         buf = torch.zeros(m, ld, device=device, dtype=torch.float32)
         buf[:, :n] = A.to(torch.float32)

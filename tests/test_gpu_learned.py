@@ -1,0 +1,173 @@
+"""The learned predictor's kernels against the oracle (sketch features, MLP forward,
+gradients), training through the library's Adam kernel, and what the trained network
+gains over the plain batched pipeline on the same batch."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def gk():
+    import paper_2104_10785_gb300 as m
+
+    return m
+
+
+def _params(seed=0, scale=0.1):
+    g = np.random.default_rng(seed)
+    p = g.standard_normal(mlp.N_PARAMS) * scale
+    p[mlp.N_TRAINABLE:mlp.N_TRAINABLE + 35] = g.standard_normal(35) * 0.5
+    p[mlp.N_TRAINABLE + 35:mlp.N_TRAINABLE + 70] = 1.0 + 0.2 * np.abs(g.standard_normal(35))
+    p[mlp.N_TRAINABLE + 70:mlp.N_TRAINABLE + 72] = [2.0, 3.0]
+    p[mlp.N_TRAINABLE + 72:] = [0.7, 0.4]
+    return p.astype(np.float32)
+
+
+def test_sketch_features_match_oracle():
+    mats, As = [], []
+    g = synth.rng(44)
+    for i in range(12):
+        m = int(g.integers(40, 700))
+        n = int(g.integers(20, 300))
+        r = int(g.integers(2, 40))
+        A = synth.gaussian_product(m, n, r, 1e-3, seed=i, dtype=np.float32)
+        As.append(A)
+        mats.append(torch.from_numpy(A).cuda())
+    f = gk().gk_sketch_batched(mats, seed=91).cpu().numpy()
+    for i, A in enumerate(As):
+        fo = mlp.sketch_features(A.astype(np.float64), 91)
+        # sigma_i(Y): the f32 products perturb Y by ~2^-24 sqrt(n) ||A|| ||Omega||, i.e. an absolute
+        # error of a few 1e-6 sigma_1 (Weyl), on top of f32 rounding of each feature
+        sg, so = np.exp(f[i, :32].astype(np.float64)), np.exp(fo[:32])
+        assert np.all(np.abs(sg - so) <= 2e-5 * so[0] + 1e-5 * so), (i, np.abs(sg - so).max() / so[0])
+        np.testing.assert_allclose(f[i, 32:], fo[32:], rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("B", [1, 7, 256, 300])
+def test_mlp_forward_matches_oracle(B):
+    p = _params(1)
+    X = np.random.default_rng(B).standard_normal((B, 35)).astype(np.float32)
+    out = gk().gk_mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    ref, _ = mlp.forward(p.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(out, ref, rtol=1e-4, atol=1e-4)
+    outb = gk().gk_mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(), bf16_weights=True)
+    np.testing.assert_allclose(outb.cpu().numpy(), ref, rtol=0.05, atol=0.05)  # bf16 weights: 2^-9 relative each
+
+
+def test_mlp_gradient_matches_oracle():
+    p = _params(2)
+    g = np.random.default_rng(9)
+    X = g.standard_normal((64, 35)).astype(np.float32)
+    Y = (g.standard_normal((64, 2)) * 0.5 + [2.0, 3.0]).astype(np.float32)
+    grad, loss = gk().gk_mlp_grad(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    lo, go = mlp.loss_and_grad(p.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+    np.testing.assert_allclose(loss, lo, rtol=1e-5)
+    grad = grad.cpu().numpy()
+    scale = np.abs(go).max()
+    assert np.abs(grad - go).max() <= 1e-4 * scale
+
+
+def test_training_reduces_the_loss():
+    g = np.random.default_rng(3)
+    X = g.standard_normal((2048, 35)).astype(np.float32)
+    W = g.standard_normal((35, 2)) * 0.3
+    Y = (np.tanh(X @ W) + [2.0, 3.0]).astype(np.float32)
+    from paper_2104_10785_gb300 import predictor
+
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    params, losses = predictor.train(Xd, Yd, epochs=30, batch=128, lr=1e-3, seed=1)
+    losses = losses.cpu().numpy()
+    assert losses[-1] < 0.2 * losses[0], losses
+    # the trained network agrees with the oracle's forward pass on its own parameters
+    out = gk().gk_mlp_forward(params, Xd[:50]).cpu().numpy()
+    ref, _ = mlp.forward(params.cpu().numpy().astype(np.float64), X[:50].astype(np.float64))
+    np.testing.assert_allclose(out, ref, rtol=1e-4, atol=1e-4)
+
+
+def test_batched_rank_cut_returns_the_numerical_rank():
+    """k above the rank with rank_cut = eps: the triplets below eps * sigma_1 leave the convergence
+    test, `rank` counts the rest, and those equal the oracle's top-r triplets."""
+    probs, cases = [], []
+    for i in range(16):
+        g = synth.rng(300 + i)
+        m = int(g.integers(80, 600))
+        n = int(g.integers(40, m + 1))
+        r = int(g.integers(3, 25))
+        A = synth.gaussian_product(m, n, r, 1e-9, seed=400 + i, dtype=np.float64)
+        k = min(r + int(g.integers(1, 6)), min(m, n) - 2)
+        q1 = synth.start_vector(m, i)
+        probs.append(dict(A=torch.from_numpy(A).cuda(), k=k, krylov_dim=min(k + 8, min(m, n)), tol=1e-10,
+                          rank_cut=1e-6, start=torch.from_numpy(q1).cuda()))
+        cases.append((A, r, q1))
+    res, st, info = gk().gk_psvd_batched(probs, max_restarts=100)
+    assert st == 0, [x[3] for x in res]
+    for (U, S, V, rr), (A, r, q1) in zip(res, cases):
+        assert rr["rank"] == r
+        op = oracle.Operator.dense(A)
+        Uo, So, Vo, io = oracle.psvd(op, r, min(r + 12, min(A.shape)), q1, tol=1e-12, max_restarts=500)
+        np.testing.assert_allclose(S.cpu().numpy()[:r], So, rtol=1e-9)
+        r1, r2 = oracle.residuals(op, U.cpu().numpy()[:, :r], S.cpu().numpy()[:r], V.cpu().numpy()[:, :r])
+        assert max(r1.max(), r2.max()) <= 1.01e-10 * So[0]
+
+
+def _held_out(count, seed):
+    shapes = synth.batched_shapes(count, seed)
+    return shapes, synth.torch_batched_products(shapes, 1e-6, seed)
+
+
+def _check_against_plain(ranks, out, ranks_p, out_p, shapes, mats):
+    assert ranks == ranks_p == [s[2] for s in shapes]
+    M = gk()
+    for (U, S, V, _), (Up, Sp, Vp, _), A in zip(out, out_p, mats):
+        np.testing.assert_allclose(S.cpu().numpy(), Sp.cpu().numpy(), rtol=1e-7)
+        r1, r2 = M.gk_residuals(A, U, S, V)
+        r1p, r2p = M.gk_residuals(A, Up, Sp, Vp)
+        # both at the f32-product floor or below the tolerance
+        lim = max(2.0 * float(max(r1p.max(), r2p.max())), 1e-8 * float(Sp[0]))
+        assert float(max(r1.max(), r2.max())) <= lim
+
+
+def test_wrong_predictions_cost_only_work():
+    """A network with random weights: every wrong rank is caught by the solver's own spectrum and
+    re-solved by the plain pipeline, so the results equal the plain ones."""
+    from paper_2104_10785_gb300 import predictor
+
+    shapes, mats = _held_out(48, 4242)
+    p = torch.from_numpy(_params(5, scale=0.05)).cuda()
+    rl, outl, il = predictor.learned_batched(mats, p)
+    rp, outp, ip = predictor.plain_batched(mats)
+    _check_against_plain(rl, outl, rp, outp, shapes, mats)
+
+
+def test_trained_predictor_gains_over_plain():
+    """The committed network on a held-out batch (a seed outside the training range): the same ranks
+    and triplets as the plain pipeline, with fewer products with A and less time."""
+    import time
+
+    from paper_2104_10785_gb300 import predictor
+
+    params = predictor.load()
+    assert params is not None, "trained weights missing"
+    shapes, mats = _held_out(256, 777)
+    runs = {}
+    for name, fn in (("plain", lambda: predictor.plain_batched(mats)),
+                     ("learned", lambda: predictor.learned_batched(mats, params))):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        runs[name] = (time.perf_counter() - t, out)
+    tp, (rp, outp, ip) = runs["plain"]
+    tl, (rl, outl, il) = runs["learned"]
+    _check_against_plain(rl, outl, rp, outp, shapes, mats)
+    assert il["fallbacks"] <= 0.05 * len(mats)
+    assert il["matvecs"] < 0.75 * ip["matvecs"], (il["matvecs"], ip["matvecs"])
+    assert tl < tp, (tl, tp)
