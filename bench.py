@@ -12,6 +12,12 @@ the operator and device-to-host copy of U, S, V inside the timed region).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gk|reference] [--workload NAME]
 
+The line also carries "batched": the 512-problem batched workload (dense f32, uneven sizes,
+ranks 5..64 + 1e-6 noise) solved by the plain pipeline (batched Algorithm 3 for the rank,
+then the batched top-r partial SVD) and by the learned one (sketch + network -> rank and
+Krylov dimension, one batched partial SVD judged by its own spectrum), converged triplets/s
+of each.  `--workload batched_f32_512_rank5to64` makes that the headline line.
+
 With N > 1 (torchrun) every rank solves its own replica (the method has no exchange
 step at this size); value = triplets of all ranks / max time over ranks.
 """
@@ -213,6 +219,58 @@ def cpu_threads():
 
 
 # ---------------------------------------------------------------------------
+# batched workload: plain vs learned pipelines
+# ---------------------------------------------------------------------------
+def batched_leg(device, steps, warmup):
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+    from paper_2104_10785_gb300 import predictor
+    import synth
+
+    w = synth.WORKLOADS["batched_f32_512_rank5to64"]
+    t0 = time.time()
+    shapes = synth.batched_shapes(w["count"], w["seed"])
+    mats = synth.torch_batched_products(shapes, 1e-6, w["seed"], device=device)
+    torch.cuda.synchronize()
+    gen = time.time() - t0
+    params = predictor.load(device=device)
+    if params is None:
+        raise SystemExit("trained predictor weights are missing")
+    truth = [s[2] for s in shapes]
+    stream = torch.cuda.current_stream(device)
+    res = {}
+    for name, fn in (("plain", lambda: predictor.plain_batched(mats, w["eps"], w["tol"])),
+                     ("learned", lambda: predictor.learned_batched(mats, params, w["eps"], w["tol"]))):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        launches0 = gk.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ranks, out, info = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        # bytes of A the pipeline must stream: each product (and the sketch) reads its operator once
+        a_bytes = sum(mv * A.shape[0] * A.shape[1] * 4 for mv, A in zip(info["matvecs_per_problem"], mats))
+        trip = int(sum(ranks))
+        res[name] = {"value": trip / (ms / 1e3), "unit": "triplets/s", "ms_per_step": ms, "triplets": trip,
+                     "matvecs": int(info["matvecs"]), "ranks_equal_truth": ranks == truth,
+                     "status": int(info["status"]), "operator_GB_per_s": a_bytes / (ms / 1e3) / 1e9,
+                     "launches_per_step": (gk.launch_count() - launches0) / steps}
+        if name == "learned":
+            res[name]["fallbacks"] = info["fallbacks"]
+    res["learned_speedup"] = res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"]
+    res["config"] = {"workload": "batched_f32_512_rank5to64", "count": w["count"], "eps": w["eps"], "tol": w["tol"],
+                     "bytes": int(sum(A.numel() * 4 for A in mats)), "gen_seconds": gen,
+                     "l2": "inputs larger than L2 (%.1f GB in total)" % (sum(A.numel() * 4 for A in mats) / 1e9)}
+    return res
+
+
+# ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
@@ -273,6 +331,8 @@ def run_gk(args, rank, world):
     if dist:
         import torch.distributed as tdist
     gk.lib()
+    if args.workload == "batched_f32_512_rank5to64":
+        return run_batched_headline(args, rank, world, device)
     w = make_workload(args.workload, device, want_plain=not args.no_plain)
     k, K, tol = w["k"], w["K"], w["tol"]
     A = w["A"]
@@ -340,6 +400,43 @@ def run_gk(args, rank, world):
     breakdown = {key: tot[key] / args.steps for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "ms_small",
                                                           "ms_restart")}
 
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+        Ah.copy_(A)
+        outs = (torch.empty((k, w["m"]), dtype=torch.float64, pin_memory=True),
+                torch.empty(k, dtype=torch.float64, pin_memory=True),
+                torch.empty((k, w["n"]), dtype=torch.float64, pin_memory=True))
+        gk.gk_psvd(Ah, k, tol, out=outs, **kw)
+        # the host link's bandwidth at this moment, for reading the figure
+        Bd = torch.empty_like(A)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Bd.copy_(Ah, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Bd.copy_(Ah, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = Ah.numel() * Ah.element_size() / (time.perf_counter() - t0) / 1e9
+        del Bd
+        barrier()
+        reps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            Uh, Sh, Vh, sth, infoh = gk.gk_psvd(Ah, k, tol, out=outs, **kw)
+            float(Sh[0])  # the result is read on the host
+        te = (time.perf_counter() - t0) / reps
+        if dist:
+            t = torch.tensor([te], device=device)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": k * world / te, "unit": "triplets/s", "library_ms": infoh["seconds"] * 1e3,
+               "h2d_bytes_per_step": int(Ah.numel() * Ah.element_size()),
+               "d2h_bytes_per_step": int(8 * k * (w["m"] + w["n"] + 1)), "ms_per_step": te * 1e3,
+               "h2d_GBs_torch_copy": h2d_gbs}
+        del Ah
+
     # plain path: the same solve on the f32-stored copy
     plain = None
     if w.get("A_plain") is not None and not args.no_plain:
@@ -363,31 +460,6 @@ def run_gk(args, rank, world):
         del Ap, w["A_plain"]
         torch.cuda.empty_cache()
 
-    # end to end through the C ABI with pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
-        Ah.copy_(A)
-        outs = (torch.empty((k, w["m"]), dtype=torch.float64, pin_memory=True),
-                torch.empty(k, dtype=torch.float64, pin_memory=True),
-                torch.empty((k, w["n"]), dtype=torch.float64, pin_memory=True))
-        gk.gk_psvd(Ah, k, tol, out=outs, **kw)
-        barrier()
-        reps = max(1, min(args.steps, 3))
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            Uh, Sh, Vh, sth, infoh = gk.gk_psvd(Ah, k, tol, out=outs, **kw)
-            float(Sh[0])  # the result is read on the host
-        te = (time.perf_counter() - t0) / reps
-        if dist:
-            t = torch.tensor([te], device=device)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": k * world / te, "unit": "triplets/s",
-               "h2d_bytes_per_step": int(Ah.numel() * Ah.element_size()),
-               "d2h_bytes_per_step": int(8 * k * (w["m"] + w["n"] + 1)), "ms_per_step": te * 1e3}
-        del Ah
-
     # CPU oracle sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -405,25 +477,61 @@ def run_gk(args, rank, world):
                           f"{w['dtype']} operator ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps "
                           f"the solve needed")}
 
+    a_dtype, a_bytes = A.dtype, A.numel() * A.element_size()
+    batched = None
+    if not args.no_batched:
+        del A
+        w.pop("A", None)
+        torch.cuda.empty_cache()
+        batched = batched_leg(device, steps=2, warmup=1)
+
     last = infos[-1]
     out = {
         "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
         "value": value, "unit": "triplets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if A.dtype == torch.bfloat16 else ("f64" if A.dtype == torch.float64 else "f32"),
+        "dtype": "bf16" if a_dtype == torch.bfloat16 else ("f64" if a_dtype == torch.float64 else "f32"),
         "data": "synthetic",
         "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": K, "tol": tol,
                    "storage": w["dtype"], "accumulate": "f32 runs combined in f64; f64 basis, small SVD, residuals",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (operator %.1f GB)" % (A.numel() * A.element_size() / 1e9)},
+                   "l2": "inputs larger than L2 (operator %.1f GB)" % (a_bytes / 1e9)},
         "status": statuses[-1], "resid_max_rel": resid_rel, "sigma_rel_err_vs_prescribed": sig_err,
         "restarts": last["restarts"], "matvecs": last["matvecs"], "steps_per_solve": last["steps"],
         "breakdown_ms_per_step": breakdown,
         "roofline": roof, "clocks": clk, "gpu_launches": None,
         "e2e": e2e, "cpu_baseline": cpu, "plain_f32": plain, "gen_seconds": w["gen_seconds"],
+        "batched": batched,
     }
     out["gpu_launches"] = int(sum(i["launches"] for i in infos))
     return out
+
+
+def run_batched_headline(args, rank, world, device):
+    """The batched workload as the headline: value = converged triplets/s of the learned pipeline
+    (sketch, network, one batched partial SVD judged by its own spectrum, plain fallback); the plain
+    pipeline beside it.  Timed with CUDA events around whole pipeline calls (each synchronizes)."""
+    import torch
+
+    clocks = ClockSampler(device.index or 0)
+    res = batched_leg(device, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms = res["learned"]["ms_per_step"]
+    if world > 1:
+        import torch.distributed as tdist
+
+        t = torch.tensor([ms], device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = res["learned"]["triplets"] * world / (ms / 1e3)
+    return {
+        "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
+        "value": value, "unit": "triplets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": res.pop("config"), "clocks": clk,
+        "gpu_launches": int(res["learned"]["launches_per_step"] * args.steps),
+        "roofline": None, "e2e": None, "cpu_baseline": None, "batched": res,
+    }
 
 
 def main():
@@ -437,6 +545,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this kernel")
     args = ap.parse_args()

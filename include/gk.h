@@ -209,7 +209,12 @@ typedef struct {
  * on the batch itself and remembers the fastest), else 8.  opts->seed + i
  * seeds problem i's start vector when no start is given.  Returns GK_OK, or the
  * worst per-problem status (errors first); gk_info sums the problems' counters
- * and reports the cluster size used in its `reserved` field. */
+ * and reports the cluster size used in its `reserved` field.  With
+ * GK_FLAG_PROFILE the ms_* fields hold cluster-milliseconds summed over the
+ * problems (the leading CTA's SM clock at the max clock rate): ms_matvec the
+ * A v products, ms_matvec_t the A^T u products with their cluster reduction,
+ * ms_orth Gram-Schmidt and normalization, ms_small the projected matrix, its
+ * SVD and the test, ms_restart setup, restarts and the output vectors. */
 int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
 
 /* Many independent rank estimates (Algorithm 3 on Algorithm 1, as in
@@ -290,6 +295,10 @@ const char *gk_last_cuda_error(void);
 
 /* Library version string. */
 const char *gk_version(void);
+
+/* Kernels the calling host thread has launched through this library so far
+ * (every entry point counts its own launches; the counter never resets). */
+int64_t gk_launch_count(void);
 
 #ifdef __cplusplus
 }

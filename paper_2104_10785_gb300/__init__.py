@@ -21,6 +21,7 @@ from .gk import (  # noqa: F401
     gk_residuals,
     gk_sketch_batched,
     last_cuda_error,
+    launch_count,
     lib,
     library_path,
     status_string,

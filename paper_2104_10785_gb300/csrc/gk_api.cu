@@ -1016,4 +1016,6 @@ const char *gk_last_cuda_error(void) { return g_err; }
 
 const char *gk_version(void) { return "gk-gb300 0.1 (sm_103a)"; }
 
+int64_t gk_launch_count(void) { return gk::launch_count(); }
+
 }  // extern "C"

@@ -44,6 +44,7 @@ struct BProb {
   int k, K, keep, max_restarts, passes, eps_rel;
   double tol;  // psvd tolerance or Algorithm 3 eps
   double cut;  // psvd: relative rank cut (0 = none)
+  int prof;    // accumulate phase clocks
   double *U, *S, *V;
   const double *start;
   uint64_t seed;
@@ -54,6 +55,31 @@ struct BRes {
   int status, cycles, restarts, steps, rank, breakdowns, sweeps, pad;
   long long matvecs;
   double resid_est, sigma_est, sigma_next;
+  // with profiling: SM clock cycles of the leading CTA in each phase (A v, A^T u with its
+  // cluster reduction, Gram-Schmidt and normalization, small SVD and test, setup/restart/output)
+  long long cyc[5];
+};
+
+// phase clock of the leading thread (clock64 of one SM; every phase ends at a cluster
+// barrier); the per-phase sums live in shared memory
+struct PhaseClock {
+  long long *acc;  // null: off
+  long long t;
+  __device__ static long long now() {
+#ifdef __CUDA_ARCH__
+    return clock64();
+#else
+    return 0;
+#endif
+  }
+  __device__ explicit PhaseClock(long long *a) : acc(a), t(a ? now() : 0) {}
+  __device__ __forceinline__ void mark(int ph) {
+    if (acc) {
+      const long long n = now();
+      acc[ph] += n - t;
+      t = n;
+    }
+  }
 };
 
 struct BDims {
@@ -109,6 +135,7 @@ struct Shm {
   double *hv;    // kKMax + 8: the cluster totals
   int *redi;     // kKMax: argmax indices
   int *s_rot, *s_any, *s_idx;
+  long long *cyc;  // 5 phase-clock sums (profiling)
 };
 
 __device__ __forceinline__ void slice(int64_t len, unsigned r, unsigned cs, int64_t *a, int64_t *b) {
@@ -457,6 +484,7 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
   slice(n, rank, cs, &v0, &v1);
   double sest = 0.0;
   int64_t nfresh = 0;
+  PhaseClock pc(P.prof != 0 && rank == 0 && threadIdx.x == 0 ? S.cyc : nullptr);
   // start vector, normalized, in w
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) W.w[r] = P.start ? P.start[r] : start_entry(P.seed, r);
   __syncthreads();
@@ -478,10 +506,12 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
   }
   res.matvecs = 1;
   int l = 0;
+  pc.mark(4);
   for (int cycle = 0;; ++cycle) {
     double bprev = 0.0;
     for (int j = l; j < K; ++j) {
       cl.sync();  // v_j complete in every slice
+      pc.mark(2);
       // left: w = A v_j - (beta_{j-1} u_{j-1} | sum_i rho_i u_i)
       if (j == l && l > 0)
         left_product<T>(P, S, r0, r1, W.Vb + (int64_t)j * ldv, W.w, W.Ub, ldu, 0, l, W.rho);
@@ -489,6 +519,7 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
         left_product<T>(P, S, r0, r1, W.Vb + (int64_t)j * ldv, W.w, W.Ub, ldu, j - 1, 1, &bprev);
       else
         left_product<T>(P, S, r0, r1, W.Vb + (int64_t)j * ldv, W.w, W.Ub, ldu, 0, 0, nullptr);
+      pc.mark(0);
       double a = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, j, P.passes);
       sest = fmax(sest, a);
       if (!(a > 0x1.0p-46 * sest)) {
@@ -503,9 +534,11 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
         scale_slice(W.Ub + (int64_t)j * ldu, W.w, r0, r1, 1.0 / a);
       }
       if (rank == 0 && threadIdx.x == 0) W.alpha[j] = a;
+      pc.mark(2);
       // right: z = A^T u_j - alpha_j v_j
       rows_matvec_t<T>(P, S, r0, r1, W.Ub + (int64_t)j * ldu);
       reduce_matvec_t(cl, P, S, v0, v1, W.z, W.Vb + (int64_t)j * ldv, a);
+      pc.mark(1);
       double b = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, j + 1, P.passes);
       sest = fmax(sest, b);
       if (!(b > 0x1.0p-46 * sest)) {
@@ -552,6 +585,7 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
     for (int i = 0; i < k; ++i) above += !(P.cut > 0.0) || __ldcg(W.sigma + i) > P.cut * s1;
     res.rank = above;
     res.cycles = cycle + 1;
+    pc.mark(3);
     res.resid_est = s1 > 0.0 ? mx / s1 : 0.0;
     sest = fmax(sest, s1);
     const bool conv = mx <= P.tol * s1;
@@ -586,6 +620,7 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
     l = keep;
     res.restarts++;
     cl.sync();
+    pc.mark(4);
   }
   res.sigma_est = sest;
   // outputs: U = U_K X_k, V = V_K Y_k, S = sigma_k; sign of the largest |v_i| entry positive
@@ -652,6 +687,7 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
     for (int64_t r = v0 + threadIdx.x; r < v1; r += blockDim.x) P.V[(int64_t)i * n + r] = -P.V[(int64_t)i * n + r];
   }
   cl.sync();
+  pc.mark(4);
 }
 
 // ---------------------------------------------------------------------------
@@ -666,6 +702,7 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
   slice(m, rank, cs, &r0, &r1);
   slice(P.n, rank, cs, &v0, &v1);
   const double eps = P.tol;
+  PhaseClock pc(P.prof != 0 && rank == 0 && threadIdx.x == 0 ? S.cyc : nullptr);
   for (int i = rank * blockDim.x + threadIdx.x; i < kmax + 2; i += cs * blockDim.x) {
     W.alpha[i] = 0.0;
     W.beta[i] = 0.0;
@@ -696,8 +733,10 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
     int j;
     for (j = 1; j <= kmax; ++j) {
       cl.sync();  // p_j complete
+      pc.mark(2);
       const double aj = a;
       left_product<T>(P, S, r0, r1, W.Vb + (int64_t)(j - 1) * ldv, W.w, W.Ub, ldu, j - 1, 1, &aj);
+      pc.mark(0);
       const double b = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, j, P.passes);
       res.matvecs++;
       if (rank == 0 && threadIdx.x == 0) W.beta[j] = b;
@@ -712,8 +751,10 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
         break;
       }
       scale_slice(W.Ub + (int64_t)j * ldu, W.w, r0, r1, 1.0 / b);
+      pc.mark(2);
       rows_matvec_t<T>(P, S, r0, r1, W.Ub + (int64_t)j * ldu);
       reduce_matvec_t(cl, P, S, v0, v1, W.z, W.Vb + (int64_t)(j - 1) * ldv, b);
+      pc.mark(1);
       a = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, j, P.passes);
       res.matvecs++;
       if (rank == 0 && threadIdx.x == 0) W.alpha[j] = a;
@@ -745,6 +786,7 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
   res.status = GK_OK;
   res.pad = reason;
   cl.sync();
+  pc.mark(3);
 }
 
 template <typename T>
@@ -754,6 +796,7 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restric
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_rot, s_any, s_idx;
+  __shared__ long long s_cyc[5];
   Shm S;
   S.xs = reinterpret_cast<float *>(smem);
   S.zp = reinterpret_cast<double *>(smem + sizeof(float) * kNMax);
@@ -763,6 +806,7 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restric
   S.s_rot = &s_rot;
   S.s_any = &s_any;
   S.s_idx = &s_idx;
+  S.cyc = s_cyc;
   const unsigned cid = blockIdx.x / cl.num_blocks();
   char *mine = ws + (size_t)cid * ws_stride;
   for (;;) {
@@ -776,12 +820,17 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restric
     BRes res;
     memset(&res, 0, sizeof(res));
     res.status = GK_OK;
+    if (threadIdx.x < 5) s_cyc[threadIdx.x] = 0;
+    __syncthreads();
     if (P.mode == 0)
       solve_psvd<T>(cl, P, W, D, S, res);
     else
       solve_numrank<T>(cl, P, W, D, S, res);
     cl.sync();
-    if (cl.block_rank() == 0 && threadIdx.x == 0) results[P.out] = res;
+    if (cl.block_rank() == 0 && threadIdx.x == 0) {
+      for (int i = 0; i < 5; ++i) res.cyc[i] = s_cyc[i];
+      results[P.out] = res;
+    }
   }
 }
 
@@ -911,6 +960,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     P.tol = it.tol;
     P.passes = o.reorth_passes;
     P.max_restarts = o.max_restarts;
+    P.prof = (o.flags & GK_FLAG_PROFILE) ? 1 : 0;
     P.eps_rel = o.eps_absolute ? 0 : 1;
     P.start = it.start;
     P.cut = mode == 0 ? it.rank_cut : 0.0;
@@ -1058,6 +1108,10 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
   int worst = GK_OK;
   gk_info inf;
   memset(&inf, 0, sizeof(inf));
+  int clock_khz = 0, dev_id = 0;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev_id);
+  const double ms_per_cycle = clock_khz > 0 ? 1.0 / clock_khz : 0.0;
   for (int i = 0; i < count; ++i) {
     gk_batch_item &it = items[i];
     const BRes &r = res[i];
@@ -1081,6 +1135,11 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     inf.cycles += r.cycles;
     inf.breakdowns += r.breakdowns;
     inf.resid_est_max = std::max(inf.resid_est_max, r.resid_est);
+    inf.ms_matvec += r.cyc[0] * ms_per_cycle;
+    inf.ms_matvec_t += r.cyc[1] * ms_per_cycle;
+    inf.ms_orth += r.cyc[2] * ms_per_cycle;
+    inf.ms_small += r.cyc[3] * ms_per_cycle;
+    inf.ms_restart += r.cyc[4] * ms_per_cycle;
   }
   inf.reserved = cs;  // cluster size used
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -78,88 +78,169 @@ __device__ __forceinline__ float ld_elem<double>(const double *p) {
   return (float)*p;
 }
 
-// one block per problem (grid-stride over the longest-first order)
+// ---- sketch, stage 1: Gram partials of 128-row chunks ---------------------
+// Work item = (problem, 128-row chunk).  The block computes the chunk's rows of
+// Y = A Omega (128 x 32, f32 FMA chains over the columns in increasing order),
+// then the chunk's Gram contribution Y_c^T Y_c (upper triangle, 528 entries,
+// f64 sums of exact f32 x f32 products) and its f32-accumulated ||A_c||_F^2.
+constexpr int kChunk = 128, kTileC = 64, kTri = kS * (kS + 1) / 2;  // 528
+constexpr int kSkThreads = 256;
+
+struct SkItem {
+  int p;
+  int r0;
+};
+
+// this thread's 32 elements of the tile at rows r0.., columns c0.. (element q at
+// tile position tid + 256 q: row (tid + 256 q) / 64, column (tid + 256 q) % 64),
+// zero outside A; all 32 loads are issued before any is used
+constexpr int kPerThr = kChunk * kTileC / kSkThreads;  // 32
 template <typename T>
-__device__ void sketch_one(const SkProb &P, const float *__restrict__ om, float *__restrict__ feat, float *sA,
-                           float *sO, float *sY, double *sG, double *sred) {
-  const T *A = (const T *)P.A;
-  const int tid = threadIdx.x;
-  const int tr = tid / 8, tc = (tid % 8) * 4;  // this thread's Y block entries: row tr, columns tc..tc+3
-  double g[4] = {0.0, 0.0, 0.0, 0.0};          // G entries (gi, gj..gj+3) this thread accumulates
-  const int gi = tid / 8, gj = (tid % 8) * 4;
-  double fro = 0.0;
-  for (int64_t r0 = 0; r0 < P.m; r0 += 32) {
-    float y[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t c0 = 0; c0 < P.n; c0 += 128) {
-      // A tile 32 x 128 and Omega tile 128 x 32 into shared memory
-      for (int e = tid; e < 32 * 128; e += blockDim.x) {
-        const int rr = e / 128, cc = e % 128;
-        float v = 0.f;
-        if (r0 + rr < P.m && c0 + cc < P.n) v = ld_elem<T>(A + (r0 + rr) * P.ld + c0 + cc) * (float)P.scale;
-        sA[rr * 129 + cc] = v;
-        fro += (double)v * (double)v;
-      }
-      for (int e = tid; e < 128 * kS; e += blockDim.x) {
-        const int rr = e / kS, cc = e % kS;
-        sO[rr * kS + cc] = (c0 + rr < P.n) ? om[(c0 + rr) * kS + cc] : 0.f;
-      }
-      __syncthreads();
-#pragma unroll 4
-      for (int kk = 0; kk < 128; ++kk) {
-        const float a = sA[tr * 129 + kk];
-        const float4 o = *reinterpret_cast<const float4 *>(sO + kk * kS + tc);
-        y[0] = fmaf(a, o.x, y[0]);
-        y[1] = fmaf(a, o.y, y[1]);
-        y[2] = fmaf(a, o.z, y[2]);
-        y[3] = fmaf(a, o.w, y[3]);
-      }
-      __syncthreads();
-    }
-    // G += Y_blk^T Y_blk (f32 products summed in f64)
-    for (int q = 0; q < 4; ++q) sY[tr * 33 + tc + q] = y[q];
-    __syncthreads();
-    for (int rr = 0; rr < 32; ++rr) {
-      const double yi = sY[rr * 33 + gi];
+__device__ __forceinline__ void sk_load(const T *A, int64_t ld, int64_t m, int64_t n, int64_t r0, int64_t c0,
+                                        float *v) {
+  // element q sits at row rb + 4 q, column cc (256 threads = 4 rows of 64)
+  const int cc = threadIdx.x % kTileC, rb = threadIdx.x / kTileC;
+  const bool cok = c0 + cc < n;
+  const int64_t avail = m - (r0 + rb);
+  const T *p = A + (r0 + rb) * ld + c0 + cc;
+  const int64_t step = (kSkThreads / kTileC) * ld;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) g[q] = fma(yi, (double)sY[rr * 33 + gj + q], g[q]);
+  for (int q = 0; q < kPerThr; ++q) v[q] = (cok && (int64_t)(kSkThreads / kTileC) * q < avail) ? ld_elem<T>(p + q * step) : 0.f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSkThreads) k_sketch_gram(const SkProb *__restrict__ probs,
+                                                           const SkItem *__restrict__ items, int nitems,
+                                                           const float *__restrict__ om, double *__restrict__ gpart,
+                                                           double *__restrict__ fpart) {
+  __shared__ float sA[kChunk * (kTileC + 1)];  // A tile, later Y (pitch 33)
+  __shared__ __align__(16) float sO[kTileC * kS];
+  __shared__ double sred[kSkThreads / 32];
+  const int tid = threadIdx.x;
+  const int tr = tid / 8, tc = (tid % 8) * 4;  // rows 4 tr .. 4 tr + 3, columns tc .. tc + 3 of Y
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const SkItem I = items[it];
+    const SkProb P = probs[I.p];
+    const T *A = (const T *)P.A;
+    const int64_t m = P.m, n = P.n, ld = P.ld, r0 = I.r0;
+    const float scale = (float)P.scale;
+    float y[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) y[i][j] = 0.f;
+    double fro = 0.0;
+    float v[kPerThr];
+    sk_load<T>(A, ld, m, n, r0, 0, v);
+    for (int64_t c0 = 0; c0 < n; c0 += kTileC) {
+      float fs = 0.f;
+      __syncthreads();  // the previous tile (or item) is consumed
+#pragma unroll
+      for (int q = 0; q < kPerThr; ++q) {
+        const float a = v[q] * scale;
+        sA[(tid / kTileC + (kSkThreads / kTileC) * q) * (kTileC + 1) + tid % kTileC] = a;
+        fs = fmaf(a, a, fs);
+      }
+      for (int e = tid; e < kTileC * kS; e += kSkThreads) {
+        const int rr = e / kS;
+        sO[e] = (c0 + rr < n) ? om[(c0 + rr) * kS + e % kS] : 0.f;
+      }
+      fro += (double)fs;
+      __syncthreads();
+      if (c0 + kTileC < n) sk_load<T>(A, ld, m, n, r0, c0 + kTileC, v);  // next tile in flight
+#pragma unroll 8
+      for (int kk = 0; kk < kTileC; ++kk) {
+        const float4 o = *reinterpret_cast<const float4 *>(sO + kk * kS + tc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float a = sA[(tr * 4 + i) * (kTileC + 1) + kk];
+          y[i][0] = fmaf(a, o.x, y[i][0]);
+          y[i][1] = fmaf(a, o.y, y[i][1]);
+          y[i][2] = fmaf(a, o.z, y[i][2]);
+          y[i][3] = fmaf(a, o.w, y[i][3]);
+        }
+      }
     }
     __syncthreads();
+    float *sY = sA;  // 128 x 33
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sY[(tr * 4 + i) * (kS + 1) + tc + j] = y[i][j];
+    // ||A_c||_F^2: warp sums then a fixed-order block sum
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    if ((tid & 31) == 0) sred[tid >> 5] = fro;
+    __syncthreads();
+    const int rows = (int)((m - r0) < kChunk ? (m - r0) : kChunk);
+    for (int e = tid; e < kTri; e += kSkThreads) {
+      // e -> (a, b), a <= b, row-major over the upper triangle
+      int a = 0, rem = e;
+      while (rem >= kS - a) {
+        rem -= kS - a;
+        ++a;
+      }
+      const int b = a + rem;
+      double g = 0.0;
+      for (int r = 0; r < rows; ++r) g = fma((double)sY[r * (kS + 1) + a], (double)sY[r * (kS + 1) + b], g);
+      gpart[(int64_t)it * kTri + e] = g;
+    }
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kSkThreads / 32; ++w) t += sred[w];
+      fpart[it] = t;
+    }
   }
-  for (int q = 0; q < 4; ++q) sG[gi * kS + gj + q] = g[q];
-  // ||A||_F^2: block sum in thread order
-  sred[tid] = fro;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) t += sred[i];
-    sred[0] = t;
-  }
-  __syncthreads();
-  const double fro2 = sred[0];
-  // eigenvalues of G by cyclic Jacobi (one warp performs the rotations)
-  if (tid < 32) {
-    const int lane = tid;
+}
+
+// ---- sketch, stage 2: per problem, sum the chunk partials in chunk order,
+// eigenvalues of G by cyclic Jacobi (one warp), the 35 features --------------
+__global__ void __launch_bounds__(32) k_sketch_eig(const SkProb *__restrict__ probs, const int *__restrict__ first,
+                                                  int count, const double *__restrict__ gpart,
+                                                  const double *__restrict__ fpart, float *__restrict__ feats) {
+  __shared__ double sG[kS * kS];
+  const int lane = threadIdx.x;
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const SkProb P = probs[p];
+    const int c0 = first[p], c1 = first[p + 1];
+    __syncwarp();
+    for (int e = lane; e < kTri; e += 32) {
+      int a = 0, rem = e;
+      while (rem >= kS - a) {
+        rem -= kS - a;
+        ++a;
+      }
+      const int b = a + rem;
+      double g = 0.0;
+      for (int c = c0; c < c1; ++c) g += gpart[(int64_t)c * kTri + e];
+      sG[a * kS + b] = g;
+      sG[b * kS + a] = g;
+    }
+    double fro2 = 0.0;
+    for (int c = c0; c < c1; ++c) fro2 += fpart[c];
+    __syncwarp();
     for (int sweep = 0; sweep < 30; ++sweep) {
       int rotated = 0;
-      for (int p = 0; p < kS - 1; ++p)
-        for (int q = p + 1; q < kS; ++q) {
-          const double apq = sG[p * kS + q];
-          const double app = sG[p * kS + p], aqq = sG[q * kS + q];
+      for (int pp = 0; pp < kS - 1; ++pp)
+        for (int q = pp + 1; q < kS; ++q) {
+          const double apq = sG[pp * kS + q];
+          const double app = sG[pp * kS + pp], aqq = sG[q * kS + q];
           if (apq == 0.0 || fabs(apq) <= 0x1.0p-52 * sqrt(fabs(app) * fabs(aqq))) continue;
           rotated = 1;
           const double tau = (aqq - app) / (2.0 * apq);
-          const double t = fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double t =
+              fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
           __syncwarp();
-          {  // columns p, q (row-major storage: G[i][p], G[i][q])
-            const double x = sG[lane * kS + p], y2 = sG[lane * kS + q];
-            sG[lane * kS + p] = c * x - s * y2;
+          {  // columns pp, q
+            const double x = sG[lane * kS + pp], y2 = sG[lane * kS + q];
+            sG[lane * kS + pp] = c * x - s * y2;
             sG[lane * kS + q] = s * x + c * y2;
           }
           __syncwarp();
-          {  // rows p, q
-            const double x = sG[p * kS + lane], y2 = sG[q * kS + lane];
-            sG[p * kS + lane] = c * x - s * y2;
+          {  // rows pp, q
+            const double x = sG[pp * kS + lane], y2 = sG[q * kS + lane];
+            sG[pp * kS + lane] = c * x - s * y2;
             sG[q * kS + lane] = s * x + c * y2;
           }
           __syncwarp();
@@ -176,33 +257,14 @@ __device__ void sketch_one(const SkProb &P, const float *__restrict__ om, float 
     const double nf = sqrt(fro2);
     const double ref = sqrt((double)kS) * nf;
     const double sv = sqrt(fmax(lam, 0.0));
-    feat[rk] = (float)log(fmax(sv, 1e-30 * fmax(ref, 1e-300)) / fmax(ref, 1e-300));
-    if (lane == 0) {
-      feat[kS] = (float)log(fmax(nf, 1e-300));
-      feat[kS + 1] = (float)log((double)P.m);
-      feat[kS + 2] = (float)log((double)P.n);
-    }
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(256) k_sketch(const SkProb *__restrict__ probs, const int *__restrict__ order,
-                                                int count, const float *__restrict__ om, float *__restrict__ feats) {
-  __shared__ float sA[32 * 129];
-  __shared__ __align__(16) float sO[128 * kS];
-  __shared__ float sY[32 * 33];
-  __shared__ double sG[kS * kS];
-  __shared__ double sred[256];
-  for (int i = blockIdx.x; i < count; i += gridDim.x) {
-    const int p = order[i];
-    const SkProb P = probs[p];
     float *f = feats + (int64_t)p * kF;
-    switch (P.dtype) {
-      case GK_F64: sketch_one<double>(P, om, f, sA, sO, sY, sG, sred); break;
-      case GK_F32: sketch_one<float>(P, om, f, sA, sO, sY, sG, sred); break;
-      case GK_BF16: sketch_one<__nv_bfloat16>(P, om, f, sA, sO, sY, sG, sred); break;
-      default: sketch_one<__half>(P, om, f, sA, sO, sY, sG, sred); break;
+    f[rk] = (float)log(fmax(sv, 1e-30 * fmax(ref, 1e-300)) / fmax(ref, 1e-300));
+    if (lane == 0) {
+      f[kS] = (float)log(fmax(nf, 1e-300));
+      f[kS + 1] = (float)log((double)P.m);
+      f[kS + 2] = (float)log((double)P.n);
     }
+    __syncwarp();
   }
 }
 
@@ -439,37 +501,53 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
   if (!A || count <= 0 || !features) return GK_INVALID_ARG;
   cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
   std::vector<SkProb> pr(count);
-  std::vector<double> cost(count);
+  std::vector<int> first(count + 1, 0);
+  std::vector<SkItem> items;
   int64_t nmax = 1;
+  const int dtype0 = A[0].dtype;
   for (int i = 0; i < count; ++i) {
     const gk_matrix &M = A[i];
-    if (M.kind != GK_DENSE || M.m <= 0 || M.n <= 0 || M.ld < M.n || !M.vals || M.dtype < GK_F64 || M.dtype > GK_F16)
+    if (M.kind != GK_DENSE || M.m <= 0 || M.n <= 0 || M.ld < M.n || !M.vals || M.dtype != dtype0 ||
+        M.dtype < GK_F64 || M.dtype > GK_F16 || M.m > (int64_t)INT32_MAX)
       return GK_INVALID_ARG;
     pr[i] = SkProb{M.vals, M.dtype, M.m, M.n, M.ld, M.scale};
-    cost[i] = (double)M.m * (double)M.n;
     nmax = nmax > M.n ? nmax : M.n;
+    first[i] = (int)items.size();
+    for (int64_t r = 0; r < M.m; r += kChunk) items.push_back(SkItem{i, (int)r});
   }
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  const size_t bytes = sizeof(float) * (size_t)nmax * kS + sizeof(SkProb) * count + sizeof(int) * count + 1024;
+  first[count] = (int)items.size();
+  const int nitems = (int)items.size();
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_om = up(sizeof(float) * (size_t)nmax * kS), b_pr = up(sizeof(SkProb) * count),
+               b_it = up(sizeof(SkItem) * nitems), b_first = up(sizeof(int) * (count + 1)),
+               b_g = up(sizeof(double) * (size_t)nitems * kTri), b_f = up(sizeof(double) * nitems);
   char *base = nullptr;
-  if (cudaMallocAsync((void **)&base, bytes, s) != cudaSuccess) {
+  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f, s) != cudaSuccess) {
     cudaGetLastError();
     return GK_OUT_OF_MEMORY;
   }
   float *om = (float *)base;
-  SkProb *dpr = (SkProb *)(base + ((sizeof(float) * (size_t)nmax * kS + 255) / 256 * 256));
-  int *dord = (int *)((char *)dpr + ((sizeof(SkProb) * count + 255) / 256 * 256));
+  SkProb *dpr = (SkProb *)(base + b_om);
+  SkItem *dit = (SkItem *)(base + b_om + b_pr);
+  int *dfirst = (int *)(base + b_om + b_pr + b_it);
+  double *gpart = (double *)(base + b_om + b_pr + b_it + b_first);
+  double *fpart = (double *)(base + b_om + b_pr + b_it + b_first + b_g);
   int rc = GK_OK;
   do {
     if ((rc = check(cudaMemcpyAsync(dpr, pr.data(), sizeof(SkProb) * count, cudaMemcpyHostToDevice, s)))) break;
-    if ((rc = check(cudaMemcpyAsync(dord, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s)))) break;
+    if ((rc = check(cudaMemcpyAsync(dit, items.data(), sizeof(SkItem) * nitems, cudaMemcpyHostToDevice, s)))) break;
+    if ((rc = check(cudaMemcpyAsync(dfirst, first.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s))))
+      break;
     GK_LAUNCH(k_omega<<<(int)std::min<int64_t>(4096, (nmax * kS + 255) / 256), 256, 0, s>>>(om, nmax, seed));
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    GK_LAUNCH(k_sketch<<<std::min(count, 4 * sms), 256, 0, s>>>(dpr, dord, count, om, features));
+    switch (dtype0) {
+      case GK_F64: GK_LAUNCH(k_sketch_gram<double><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
+      case GK_F32: GK_LAUNCH(k_sketch_gram<float><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
+      case GK_BF16:
+        GK_LAUNCH(k_sketch_gram<__nv_bfloat16><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart));
+        break;
+      default: GK_LAUNCH(k_sketch_gram<__half><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
+    }
+    GK_LAUNCH(k_sketch_eig<<<count, 32, 0, s>>>(dpr, dfirst, count, gpart, fpart, features));
     if ((rc = check(cudaGetLastError()))) break;
     rc = check(cudaStreamSynchronize(s));
   } while (0);

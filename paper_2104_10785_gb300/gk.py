@@ -131,6 +131,8 @@ def lib():
             L.gk_last_cuda_error.restype = C.c_char_p
             L.gk_version.argtypes = []
             L.gk_version.restype = C.c_char_p
+            L.gk_launch_count.argtypes = []
+            L.gk_launch_count.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -145,6 +147,11 @@ def last_cuda_error() -> str:
 
 def version() -> str:
     return lib().gk_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels this host thread has launched through the library so far."""
+    return int(lib().gk_launch_count())
 
 
 def _ptr(t):
@@ -330,9 +337,9 @@ def gk_numrank_workspace(A, kmax: int = 0) -> int:
 
 
 def _batch_opts(device, seed=None, max_restarts=None, reorth_passes=None, eps_absolute=False, autotune=False,
-                stream=None):
+                stream=None, profile=False):
     o, _ = _opts(device, 0, 0, max_restarts, reorth_passes, eps_absolute, seed, None, stream)
-    o.flags = GK_FLAG_AUTOTUNE if autotune else 0
+    o.flags = (GK_FLAG_AUTOTUNE if autotune else 0) | (GK_FLAG_PROFILE if profile else 0)
     return o
 
 
@@ -343,7 +350,7 @@ def _item_result(it):
 
 
 def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=None, autotune=False, stream=None,
-                    check=True):
+                    check=True, profile=False):
     """Partial SVDs of many dense device operators in one persistent launch.
 
     problems: sequence of dicts with keys A (2-D CUDA tensor, n <= 4096), k, and optionally
@@ -373,7 +380,7 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
         items[i].start = st.data_ptr() if st is not None else None
         outs.append((U, S, V))
         keep.append(A)
-    o = _batch_opts(dev, seed, max_restarts, reorth_passes, False, autotune, stream)
+    o = _batch_opts(dev, seed, max_restarts, reorth_passes, False, autotune, stream, profile)
     info = gk_info()
     status = lib().gk_psvd_batched(items, n, C.byref(o), C.byref(info))
     if check and status < 0:
@@ -382,7 +389,7 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
 
 
 def gk_numrank_batched(problems, *, seed=None, reorth_passes=None, eps_absolute=False, autotune=False, stream=None,
-                       want_sigma=False, check=True):
+                       want_sigma=False, check=True, profile=False):
     """Rank estimates (Algorithm 3) of many dense device operators in one persistent launch.
 
     problems: sequence of dicts with keys A, and optionally kmax (0 = min(m, n, 256)), eps (default 1e-8),
@@ -410,7 +417,7 @@ def gk_numrank_batched(problems, *, seed=None, reorth_passes=None, eps_absolute=
         items[i].start = st.data_ptr() if st is not None else None
         sigs.append(sg)
         keep.append(A)
-    o = _batch_opts(dev, seed, None, reorth_passes, eps_absolute, autotune, stream)
+    o = _batch_opts(dev, seed, None, reorth_passes, eps_absolute, autotune, stream, profile)
     info = gk_info()
     status = lib().gk_numrank_batched(items, n, C.byref(o), C.byref(info))
     if check and status < 0:

@@ -158,21 +158,25 @@ def predict(mats, params, bf16=True):
     return res
 
 
-def plain_batched(mats, eps=1e-5, tol=1e-8):
-    """Algorithm 3 for the rank, then the top-r partial SVD with the default Krylov dimension."""
-    res, _, info1 = gk.gk_numrank_batched([dict(A=A, eps=eps, kmax=min(min(A.shape), 160)) for A in mats])
+def plain_batched(mats, eps=1e-5, tol=1e-8, autotune=True):
+    """Algorithm 3 for the rank, then the top-r partial SVD with the default Krylov dimension
+    (cluster sizes autotuned per batch signature)."""
+    res, st1, info1 = gk.gk_numrank_batched([dict(A=A, eps=eps, kmax=min(min(A.shape), 160)) for A in mats],
+                                            autotune=autotune)
     ranks = [max(1, r[0]) for r in res]
-    out, st, info2 = gk.gk_psvd_batched([dict(A=A, k=r, tol=tol) for A, r in zip(mats, ranks)])
-    return ranks, out, dict(matvecs=info1["matvecs"] + info2["matvecs"], status=st)
+    out, st, info2 = gk.gk_psvd_batched([dict(A=A, k=r, tol=tol) for A, r in zip(mats, ranks)], autotune=autotune)
+    per = [a[2]["matvecs"] + b[3]["matvecs"] for a, b in zip(res, out)]
+    return ranks, out, dict(matvecs=info1["matvecs"] + info2["matvecs"], status=min(st1, st) if min(st1, st) < 0
+                            else max(st1, st), matvecs_per_problem=per)
 
 
-def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200):
+def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200, autotune=True):
     """Predicted (rank, K), one batched partial SVD with the rank cut, judged by the solver's spectrum;
     under-estimated ranks fall back to the plain pipeline."""
     pred = predict(mats, params)
     out, st, info = gk.gk_psvd_batched(
         [dict(A=A, k=r, krylov_dim=K, tol=tol, rank_cut=eps) for A, (r, K) in zip(mats, pred)],
-        max_restarts=max_restarts)
+        max_restarts=max_restarts, autotune=autotune)
     ranks = []
     redo = []
     for i, (U, S, V, rr) in enumerate(out):
@@ -184,14 +188,18 @@ def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200):
         else:
             ranks.append(max(1, rr["rank"]))
     matvecs = info["matvecs"]
+    per = [o[3]["matvecs"] + 1 for o in out]  # + the sketch's pass over A
     if redo:
-        rr_, out2, inf2 = plain_batched([mats[i] for i in redo], eps, tol)
+        rr_, out2, inf2 = plain_batched([mats[i] for i in redo], eps, tol, autotune=False)
         for j, i in enumerate(redo):
             ranks[i] = rr_[j]
             out[i] = out2[j]
+            per[i] += inf2["matvecs_per_problem"][j]
         matvecs += inf2["matvecs"]
+        st = min(st, inf2["status"]) if min(st, inf2["status"]) < 0 else max(st, inf2["status"])
     final = [(U[:, :r], S[:r], V[:, :r], rr) for (U, S, V, rr), r in zip(out, ranks)]
-    return ranks, final, dict(matvecs=matvecs, fallbacks=len(redo), status=st, predicted=pred)
+    return ranks, final, dict(matvecs=matvecs, fallbacks=len(redo), status=st, predicted=pred,
+                              matvecs_per_problem=per)
 
 
 def main(argv=None):
