@@ -209,7 +209,8 @@ typedef struct {
  * on the batch itself and remembers the fastest), else 8.  opts->seed + i
  * seeds problem i's start vector when no start is given.  Returns GK_OK, or the
  * worst per-problem status (errors first); gk_info sums the problems' counters
- * and reports the cluster size used in its `reserved` field.  With
+ * and reports the cluster size used in its `reserved` field and the number of
+ * clusters launched in `kprime`.  With
  * GK_FLAG_PROFILE the ms_* fields hold cluster-milliseconds summed over the
  * problems (the leading CTA's SM clock at the max clock rate): ms_matvec the
  * A v products, ms_matvec_t the A^T u products with their cluster reduction,

@@ -35,6 +35,15 @@ constexpr int kBThreads = 256;
 constexpr int kNMax = 4096;  // columns per problem (shared-memory copies of v and of A^T u partial sums)
 constexpr int kKMax = 512;   // basis columns per problem
 constexpr int kRunRows = 32; // f32 run length in rows before an f64 combine (A^T u)
+// row ring: the CTA's rows of A stream through shared memory by 1-D bulk copies (TMA),
+// kRingStages stages of kRingStage bytes, one mbarrier per stage
+constexpr int kRingStages = 3;
+constexpr int kRingStage = 16384;
+constexpr long long kRingWait = 4000000000ll;  // ~2 s at 2 GHz before a wait gives up
+constexpr size_t kSmemFixed = sizeof(float) * kNMax + sizeof(double) * (kNMax + 2 * (kKMax + 8)) + sizeof(int) * kKMax;
+constexpr size_t kRingOffset = (kSmemFixed + 127) / 128 * 128;
+constexpr size_t kSmemBytes = kRingOffset + (size_t)kRingStages * kRingStage;
+
 
 struct BProb {
   const void *A;
@@ -136,7 +145,129 @@ struct Shm {
   int *redi;     // kKMax: argmax indices
   int *s_rot, *s_any, *s_idx;
   long long *cyc;  // 5 phase-clock sums (profiling)
+  unsigned char *ring;  // kRingStages x kRingStage bytes
+  uint64_t *bar;        // kRingStages mbarriers (one arrival + the copies' bytes per phase)
+  int *dead;            // set when a ring wait timed out: the ring stays unused afterwards
+  int *err;             // kernel-wide timeout flag (global memory) read by the host
+  unsigned seq;         // ring stages consumed so far (the same value in every thread)
 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bounded wait for the phase of the given parity; false if it did not complete in time
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kRingWait) return false;
+  }
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// geometry of the ring for one operator: rows of n elements at a pitch of whole 16-byte
+// groups; the bulk copies move the whole groups (bulk bytes), the consumers read the
+// last partial group, if any, from global memory
+struct RingGeom {
+  int pitch, bulk, rows;  // bytes per staged row, bytes copied per row, rows per stage
+  bool contig;            // rows adjacent in memory: one copy per stage
+};
+
+template <typename T>
+__device__ __forceinline__ bool ring_geom(const BProb &P, const Shm &S, RingGeom *g) {
+  if constexpr (std::is_same<T, double>::value) {
+    return false;
+  } else {
+    const int64_t rowb = P.n * (int64_t)sizeof(T);
+    if (*S.dead || ((uintptr_t)P.A & 15) || ((P.ld * (int64_t)sizeof(T)) & 15) || rowb > kRingStage) return false;
+    g->bulk = (int)(rowb & ~(int64_t)15);
+    g->pitch = (int)((rowb + 15) & ~(int64_t)15);
+    g->rows = kRingStage / g->pitch;
+    g->contig = (P.ld * (int64_t)sizeof(T) == rowb) && (rowb & 15) == 0;
+    return true;
+  }
+}
+
+// thread 0: stage `st` of the rows [r0, r1) into ring slot `slot`
+template <typename T>
+__device__ __forceinline__ void ring_issue(const BProb &P, Shm &S, const RingGeom &g, int64_t r0, int64_t r1,
+                                           int64_t st, int slot) {
+  const int64_t row0 = r0 + st * g.rows;
+  const int cnt = (int)((r1 - row0) < g.rows ? (r1 - row0) : g.rows);
+  uint64_t *b = S.bar + slot;
+  unsigned char *dst = S.ring + (size_t)slot * kRingStage;
+  const char *src = (const char *)P.A + row0 * P.ld * (int64_t)sizeof(T);
+  mbar_expect(b, (unsigned)(cnt * g.bulk));
+  if (g.bulk == 0) return;
+  if (g.contig) {
+    bulk_copy(dst, src, (unsigned)(cnt * g.bulk), b);
+  } else {
+    for (int i = 0; i < cnt; ++i)
+      bulk_copy(dst + (size_t)i * g.pitch, src + (int64_t)i * P.ld * (int64_t)sizeof(T), (unsigned)g.bulk, b);
+  }
+}
+
+// stream the rows [r0, r1) through the ring; consume(stage, first row, rows) runs on every
+// thread once per stage.  Returns false (nothing done) if the ring cannot serve this operator;
+// on a timed-out wait sets the error flags, marks the ring dead and returns true with the
+// remaining stages unconsumed (the caller poisons its result).
+template <typename T, typename F>
+__device__ bool ring_rows(const BProb &P, Shm &S, const RingGeom &g, int64_t r0, int64_t r1, F &&consume,
+                          bool *timed_out) {
+  *timed_out = false;
+  const int64_t nst = (r1 - r0 + g.rows - 1) / g.rows;
+  if (nst <= 0) return true;
+  if (threadIdx.x == 0)
+    for (int64_t st = 0; st < nst && st < kRingStages; ++st) ring_issue<T>(P, S, g, r0, r1, st, (int)((S.seq + st) % kRingStages));
+  for (int64_t st = 0; st < nst; ++st) {
+    const unsigned q = S.seq + (unsigned)st;
+    const int slot = (int)(q % kRingStages);
+    const bool ok = mbar_wait_bounded(S.bar + slot, (q / kRingStages) & 1u);
+    // every thread has finished the previous stage: its slot may be refilled
+    const int bad = __syncthreads_or(!ok);
+    if (threadIdx.x == 0 && st >= 1 && st - 1 + kRingStages < nst && !bad)
+      ring_issue<T>(P, S, g, r0, r1, st - 1 + kRingStages, (int)((q - 1) % kRingStages));
+    if (bad) {
+      if (threadIdx.x == 0) {
+        atomicExch(S.err, 1);
+        *S.dead = 1;
+        // copies still in flight: give each outstanding stage one more bounded wait
+        for (int64_t t = st; t < nst && t < st - 1 + kRingStages; ++t) {
+          const unsigned qt = S.seq + (unsigned)t;
+          mbar_wait_bounded(S.bar + (qt % kRingStages), (qt / kRingStages) & 1u);
+        }
+      }
+      __syncthreads();
+      *timed_out = true;
+      return true;
+    }
+    const int64_t row0 = r0 + st * g.rows;
+    const int cnt = (int)((r1 - row0) < g.rows ? (r1 - row0) : g.rows);
+    consume(S.ring + (size_t)slot * kRingStage, row0, cnt);
+  }
+  __syncthreads();  // the last stage is consumed before the ring is reused
+  S.seq += (unsigned)nst;
+  return true;
+}
 
 __device__ __forceinline__ void slice(int64_t len, unsigned r, unsigned cs, int64_t *a, int64_t *b) {
   *a = len * (int64_t)r / (int64_t)cs;
@@ -268,8 +399,93 @@ __device__ void rows_matvec_f64(const BProb &P, int64_t r0, int64_t r1, const do
 // Every thread owns one 16-byte group of columns per sweep (E columns), walks
 // the slice's rows eight at a time, sums f32 runs of kRunRows rows and combines
 // them in f64; rows that are not 16-byte aligned take the scalar path.
+// A^T u of the CTA's rows through the row ring: the thread owns 16-byte column groups
+// tid, tid + 256, ...; u (f32) staged in S.xs; f32 runs of kRunRows rows combined in f64
+// into S.zp; the columns of the partial last group from global memory
+template <typename T>
+__device__ bool ring_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *u) {
+  if constexpr (std::is_same<T, double>::value) {
+    return false;
+  } else {
+  RingGeom g;
+  if (!ring_geom<T>(P, S, &g) || r1 - r0 > kNMax) return false;
+  using VT = Vec<T>;
+  constexpr int E = VT::E;
+  constexpr int G = kNMax / (E * kBThreads);  // column groups per thread at most (4 f32, 2 bf16/f16)
+  const T *A = (const T *)P.A;
+  const int nvb = g.bulk / 16;
+  const int64_t n = P.n;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) S.xs[r - r0] = (float)u[r];
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) S.zp[c] = 0.0;
+  __syncthreads();
+  float a32[G][E];
+#pragma unroll
+  for (int k = 0; k < G; ++k)
+#pragma unroll
+    for (int e = 0; e < E; ++e) a32[k][e] = 0.f;
+  int run = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int gi = threadIdx.x + k * kBThreads;
+      if (gi < nvb) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          S.zp[gi * E + e] += (double)a32[k][e];
+          a32[k][e] = 0.f;
+        }
+      }
+    }
+  };
+  bool to;
+  ring_rows<T>(
+      P, S, g, r0, r1,
+      [&](const unsigned char *st, int64_t row0, int cnt) {
+        for (int i = 0; i < cnt; ++i) {
+          const typename VT::V *rv = reinterpret_cast<const typename VT::V *>(st + (size_t)i * g.pitch);
+          const float ur = S.xs[row0 + i - r0];
+#pragma unroll
+          for (int k = 0; k < G; ++k) {
+            const int gi = threadIdx.x + k * kBThreads;
+            if (gi < nvb) {
+              float f[E];
+              VT::unpack(rv[gi], f);
+#pragma unroll
+              for (int e = 0; e < E; ++e) a32[k][e] = fmaf(f[e], ur, a32[k][e]);
+            }
+          }
+          if (++run == kRunRows) {
+            flush();
+            run = 0;
+          }
+        }
+      },
+      &to);
+  flush();
+  // columns of the partial last group
+  for (int64_t c = (int64_t)nvb * E + threadIdx.x; c < n; c += blockDim.x) {
+    double acc = 0.0;
+    float sr = 0.f;
+    int rr = 0;
+    for (int64_t r = r0; r < r1; ++r) {
+      sr = fmaf(load_val<T>(A + r * P.ld + c), S.xs[r - r0], sr);
+      if (++rr == kRunRows) {
+        acc += (double)sr;
+        sr = 0.f;
+        rr = 0;
+      }
+    }
+    S.zp[c] = acc + (double)sr;
+  }
+  if (to)
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) S.zp[c] = __longlong_as_double(0x7ff8000000000000ll);
+  return true;
+  }
+}
+
 template <typename T>
 __device__ void rows_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *u) {
+  if (ring_matvec_t<T>(P, S, r0, r1, u)) return;
   const T *A = (const T *)P.A;
   const int64_t n = P.n;
   if constexpr (std::is_same<T, double>::value) {
@@ -465,6 +681,8 @@ __device__ void left_product(const BProb &P, Shm &S, int64_t r0, int64_t r1, con
   if constexpr (std::is_same<T, double>::value)
     rows_matvec_f64(P, r0, r1, v, w, Qb, ldq, c0, cn, coefs);
   else {
+    // the register-streaming kernel measured faster than the row ring for A v on the batched
+    // workload (two rows per warp, eight 16-byte loads per lane in flight); the ring serves A^T u
     stage_x<T>(P, S, v);
     rows_matvec<T>(P, S, r0, r1, w, Qb, ldq, c0, cn, coefs);
   }
@@ -779,7 +997,7 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
   if (rank == 0) {
     __shared__ int s_rank;
     __shared__ double s_s1;
-    dev::block_bidiag_rank(W.alpha, W.beta, kp, eps, P.eps_rel, &s_rank, &s_s1, P.S);
+    dev::block_bidiag_rank(W.alpha, W.beta, kp, eps, P.eps_rel, &s_rank, &s_s1, P.S, S.zp);
     __syncthreads();
     res.rank = s_rank;
   }
@@ -794,9 +1012,10 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restric
                                                        int count, int *next, char *ws, size_t ws_stride, BDims D,
                                                        BRes *results) {
   cg::cluster_group cl = cg::this_cluster();
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_rot, s_any, s_idx;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_rot, s_any, s_idx, s_dead;
   __shared__ long long s_cyc[5];
+  __shared__ __align__(8) uint64_t s_bar[kRingStages];
   Shm S;
   S.xs = reinterpret_cast<float *>(smem);
   S.zp = reinterpret_cast<double *>(smem + sizeof(float) * kNMax);
@@ -807,6 +1026,17 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restric
   S.s_any = &s_any;
   S.s_idx = &s_idx;
   S.cyc = s_cyc;
+  S.ring = smem + kRingOffset;
+  S.bar = s_bar;
+  S.dead = &s_dead;
+  S.err = next + 1;
+  S.seq = 0;
+  if (threadIdx.x == 0) {
+    s_dead = 0;
+    for (int i = 0; i < kRingStages; ++i) mbar_init(&s_bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   const unsigned cid = blockIdx.x / cl.num_blocks();
   char *mine = ws + (size_t)cid * ws_stride;
   for (;;) {
@@ -834,7 +1064,6 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BProb *__restric
   }
 }
 
-constexpr size_t kSmemBytes = sizeof(float) * kNMax + sizeof(double) * (kNMax + 2 * (kKMax + 8)) + sizeof(int) * kKMax;
 
 // ---------------------------------------------------------------------------
 // host side
@@ -881,7 +1110,7 @@ int launch_batched(BatchedKernel kern, int cs, const BProb *dprobs, const int *d
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaMemsetAsync(dnext, 0, sizeof(int), s) != cudaSuccess) return GK_CUDA_ERROR;
+  if (cudaMemsetAsync(dnext, 0, 2 * sizeof(int), s) != cudaSuccess) return GK_CUDA_ERROR;
   if (cudaLaunchKernelEx(&cfg, kern, dprobs, dorder, count, dnext, dws, stride, D, dres) != cudaSuccess)
     return GK_CUDA_ERROR;
   note_launch();
@@ -932,6 +1161,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
   if (dtype_all < GK_F64 || dtype_all > GK_F16) return GK_INVALID_ARG;
   const BatchedKernel kern = kernel_for(dtype_all);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
     return GK_CUDA_ERROR;
@@ -1050,6 +1280,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
   p += al256(sizeof(BRes) * count);
   char *dws = p;
   int rc = GK_OK;
+  int herr = 0, ncl_used = 0;
   std::vector<BRes> res(count);
   do {
     if (cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1092,9 +1323,11 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
       rc = GK_CUDA_ERROR;
       break;
     }
+    ncl_used = ncl;
     rc = launch_batched(kern, cs, dprobs, dorder, count, dnext, dws, stride, D, dres, ncl, s);
     if (rc) break;
     if (cudaMemcpyAsync(res.data(), dres, sizeof(BRes) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&herr, dnext + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       rc = GK_CUDA_ERROR;
       break;
@@ -1105,6 +1338,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     cudaStreamSynchronize(s);
   }
   if (rc) return rc;
+  if (herr) return GK_TIMEOUT;  // a bulk-copy wait gave up: results are not trustworthy
   int worst = GK_OK;
   gk_info inf;
   memset(&inf, 0, sizeof(inf));
@@ -1141,7 +1375,8 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     inf.ms_small += r.cyc[3] * ms_per_cycle;
     inf.ms_restart += r.cyc[4] * ms_per_cycle;
   }
-  inf.reserved = cs;  // cluster size used
+  inf.reserved = cs;    // cluster size used
+  inf.kprime = ncl_used;  // clusters launched
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   inf.launches = launch_count() - l0;
   if (info) *info = inf;

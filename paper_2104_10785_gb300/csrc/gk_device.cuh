@@ -167,11 +167,10 @@ __device__ __forceinline__ int count_below(const double *alpha, const double *be
   return cnt;
 }
 
-__device__ void block_bidiag_rank(const double *__restrict__ alpha,
-                                                     const double *__restrict__ beta, int kp, double eps, int eps_rel,
-                                                     int *__restrict__ rank, double *__restrict__ sigma1,
-                                                     double *__restrict__ sigma) {
-  __shared__ double red[1024];
+// red: shared scratch of blockDim.x doubles
+__device__ void block_bidiag_rank(const double *__restrict__ alpha, const double *__restrict__ beta, int kp, double eps,
+                                  int eps_rel, int *__restrict__ rank, double *__restrict__ sigma1,
+                                  double *__restrict__ sigma, double *__restrict__ red) {
   __shared__ int tbest;
   __shared__ double lo_s, hi_s;
   const int T = blockDim.x;

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(256) k_bidiag_rank(const double *__restrict__ 
                                                      const double *__restrict__ beta, int kp, double eps, int eps_rel,
                                                      int *__restrict__ rank, double *__restrict__ sigma1,
                                                      double *__restrict__ sigma) {
-  dev::block_bidiag_rank(alpha, beta, kp, eps, eps_rel, rank, sigma1, sigma);
+  __shared__ double red[256];
+  dev::block_bidiag_rank(alpha, beta, kp, eps, eps_rel, rank, sigma1, sigma, red);
 }
 
 }  // namespace
