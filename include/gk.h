@@ -97,7 +97,8 @@ typedef struct {
   int32_t kprime;        /* gk_numrank: k' of Algorithm 1 (columns of B_{k'+1,k'}) */
   int32_t stop_reason;   /* gk_numrank: 0 reached kmax, 1 beta break, 2 alpha break */
   int32_t breakdowns;    /* exact breakdowns replaced by fresh directions */
-  int32_t svd_sweeps;    /* gk_psvd: Jacobi sweeps of the last small SVD (negative: sweep limit reached) */
+  int32_t svd_sweeps;    /* gk_psvd: Jacobi sweeps of the last small SVD (negative: sweep limit reached);
+                            batched: the most sweeps any problem's last small SVD took */
   int32_t reserved;      /* batched calls: cluster size used */
   int64_t matvecs;       /* products with A or A^T */
   double resid_est_max;  /* gk_psvd: max_i<k |beta_K X_{K,i}| / sigma_1 (Ritz residual estimate) */

@@ -310,40 +310,37 @@ __device__ void rows_matvec(const BProb &P, Shm &S, int64_t r0, int64_t r1, doub
       const int64_t nv = n / E;
       const typename VT::V *av0 = reinterpret_cast<const typename VT::V *>(A + rb * P.ld);
       const typename VT::V *av1 = reinterpret_cast<const typename VT::V *>(A + (rb + (nr - 1)) * P.ld);
-      int64_t i = lane;
-      for (; i + 32 * 3 < nv; i += 32 * 4) {
-        typename VT::V b0[4], b1[4];
+      // four 16-byte groups per row and lane in flight; the last pass is predicated
+      for (int64_t i = lane; i < nv; i += 32 * 4) {
+        typename VT::V b0[4] = {}, b1[4] = {};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          b0[q] = __ldcs(av0 + i + 32 * q);
-          b1[q] = __ldcs(av1 + i + 32 * q);
-        }
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float f0[E], f1[E];
-          VT::unpack(b0[q], f0);
-          VT::unpack(b1[q], f1);
-          const int64_t ii = i + 32 * q;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const float xv = S.xs[ii * E + e];
-            s0 = fmaf(f0[e], xv, s0);
-            s1 = fmaf(f1[e], xv, s1);
+          if (i + 32 * q < nv) {
+            b0[q] = __ldcs(av0 + i + 32 * q);
+            b1[q] = __ldcs(av1 + i + 32 * q);
           }
         }
-        acc[0] += (double)s0;
-        acc[1] += (double)s1;
-      }
-      for (; i < nv; i += 32) {
-        float f0[E], f1[E];
-        VT::unpack(__ldcs(av0 + i), f0);
-        VT::unpack(__ldcs(av1 + i), f1);
         float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          s0 = fmaf(f0[e], S.xs[i * E + e], s0);
-          s1 = fmaf(f1[e], S.xs[i * E + e], s1);
+        for (int q = 0; q < 4; ++q) {
+          if (i + 32 * q < nv) {
+            float f0[E], f1[E];
+            VT::unpack(b0[q], f0);
+            VT::unpack(b1[q], f1);
+            const float4 *xv = reinterpret_cast<const float4 *>(S.xs + (i + 32 * q) * E);
+#pragma unroll
+            for (int h = 0; h < E / 4; ++h) {
+              const float4 x4 = xv[h];
+              s0 = fmaf(f0[4 * h], x4.x, s0);
+              s0 = fmaf(f0[4 * h + 1], x4.y, s0);
+              s0 = fmaf(f0[4 * h + 2], x4.z, s0);
+              s0 = fmaf(f0[4 * h + 3], x4.w, s0);
+              s1 = fmaf(f1[4 * h], x4.x, s1);
+              s1 = fmaf(f1[4 * h + 1], x4.y, s1);
+              s1 = fmaf(f1[4 * h + 2], x4.z, s1);
+              s1 = fmaf(f1[4 * h + 3], x4.w, s1);
+            }
+          }
         }
         acc[0] += (double)s0;
         acc[1] += (double)s1;
@@ -689,6 +686,117 @@ __device__ void left_product(const BProb &P, Shm &S, int64_t r0, int64_t r1, con
   __syncthreads();
 }
 
+// One-sided Jacobi SVD of the K x K matrix held column-major in shared memory (sB), on
+// the calling CTA alone: the rotations, the tournament ordering and the tolerance of the
+// cluster version, one column pair per 8-lane group (32 pairs per round), block barriers
+// between the rounds.  The skip test compares squares: c^2 <= tol^2 a b.  sY receives the accumulated
+// rotations; outputs sigma (descending), X (normalized columns of the rotated B) and Y
+// (rotations) in global memory, ordered by sigma.  Returns the sweeps (negative if the
+// sweep limit was reached).
+constexpr int kCtaJacobiMax = 78;  // K with 8 K^2 bytes within each of the two shared regions
+
+__device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
+                          int *s_rot) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int grp = lane >> 3, gl = lane & 7;
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) sY[idx] = ((idx % K) == (idx / K)) ? 1.0 : 0.0;
+  const int Kp = K + (K & 1);
+  const double tol = fmax(2.0 * sqrt((double)K) * 0x1.0p-52, (double)K * 0x1.0p-53);
+  int sweep, done = 0;
+  __syncthreads();
+  for (sweep = 1; sweep <= 80; ++sweep) {
+    if (threadIdx.x == 0) *s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < Kp - 1; ++r) {
+      // one pair per 8-lane group: 4 pairs per warp, 32 per round on 8 warps
+      for (int pb = warp * 4; pb < Kp / 2; pb += nw * 4) {
+        const int pi = pb + grp;
+        int p = 0, q = K;
+        if (pi < Kp / 2) {
+          p = dev::player(r, pi, Kp);
+          q = dev::player(r, Kp - 1 - pi, Kp);
+          if (p > q) {
+            const int t = p;
+            p = q;
+            q = t;
+          }
+        }
+        const bool live = q < K;
+        double *bp = sB + p * K, *bq = sB + (live ? q : p) * K;
+        double a = 0.0, b = 0.0, c = 0.0;
+        if (live)
+          for (int i = gl; i < K; i += 8) {
+            const double x = bp[i], y = bq[i];
+            a = fma(x, x, a);
+            b = fma(y, y, b);
+            c = fma(x, y, c);
+          }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (live && !(c == 0.0 || c * c <= tol * tol * a * b)) {
+          if (gl == 0) *s_rot = 1;
+          const double zeta = (b - a) / (2.0 * c);
+          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                              : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = gl; i < K; i += 8) {
+            const double x = bp[i], y = bq[i];
+            bp[i] = cs * x - sn * y;
+            bq[i] = sn * x + cs * y;
+          }
+          double *yp = sY + p * K, *yq = sY + q * K;
+          for (int i = gl; i < K; i += 8) {
+            const double x = yp[i], y = yq[i];
+            yp[i] = cs * x - sn * y;
+            yq[i] = sn * x + cs * y;
+          }
+        }
+        __syncwarp();  // the groups of this warp meet before the next shuffles
+      }
+      __syncthreads();
+    }
+    const int any = *s_rot;
+    __syncthreads();  // every thread has read the flag before it is cleared
+    if (!any) {
+      done = 1;
+      break;
+    }
+  }
+  for (int c = warp; c < K; c += nw) {
+    const double *bc = sB + c * K;
+    double sq = 0.0;
+    for (int i = lane; i < K; i += 32) sq = fma(bc[i], bc[i], sq);
+    sq = dev::warp_sum_d(sq);
+    if (lane == 0) nrm[c] = sqrt(sq);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const double nc = nrm[c];
+    int rk = 0;
+    for (int o = 0; o < K; ++o) {
+      const double no = nrm[o];
+      rk += (no > nc) || (no == nc && o < c);
+    }
+    pos[c] = rk;
+  }
+  __syncthreads();
+  for (int c = warp; c < K; c += nw) {
+    const int pc = pos[c];
+    const double nc = nrm[c];
+    for (int i = lane; i < K; i += 32) {
+      X[(int64_t)pc * K + i] = nc > 0.0 ? sB[c * K + i] / nc : 0.0;
+      Y[(int64_t)pc * K + i] = sY[c * K + i];
+    }
+    if (lane == 0) sigma[pc] = nc;
+  }
+  __syncthreads();
+  return done ? sweep : -(sweep - 1);
+}
+
 // ---------------------------------------------------------------------------
 // restarted partial SVD of one problem on the calling cluster
 // ---------------------------------------------------------------------------
@@ -777,19 +885,37 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
     }
     // B of this cycle, its SVD, the Ritz residual test
     cl.sync();
-    for (int64_t idx = (int64_t)rank * blockDim.x + threadIdx.x; idx < (int64_t)K * K; idx += (int64_t)cs * blockDim.x) {
-      const int r = (int)(idx % K), c = (int)(idx / K);
-      double v = 0.0;
-      if (r < l) {
-        if (c == r) v = W.sigma[r];
-        else if (c == l) v = W.rho[r];
-      } else {
-        if (c == r) v = W.alpha[r];
-        else if (c == r + 1) v = W.beta[r];
+    const bool small_on_cta = K <= kCtaJacobiMax;
+    double *sB = reinterpret_cast<double *>(S.xs), *sYw = reinterpret_cast<double *>(S.ring);
+    if (!small_on_cta || rank == 0) {
+      double *Bdst = small_on_cta ? sB : W.Bm;
+      const unsigned r_lo = small_on_cta ? 0u : rank, r_n = small_on_cta ? 1u : cs;
+      for (int64_t idx = (int64_t)r_lo * blockDim.x + threadIdx.x; idx < (int64_t)K * K;
+           idx += (int64_t)r_n * blockDim.x) {
+        const int r = (int)(idx % K), c = (int)(idx / K);
+        double v = 0.0;
+        if (r < l) {
+          if (c == r) v = W.sigma[r];
+          else if (c == l) v = W.rho[r];
+        } else {
+          if (c == r) v = W.alpha[r];
+          else if (c == r + 1) v = W.beta[r];
+        }
+        Bdst[idx] = v;
       }
-      W.Bm[idx] = v;
     }
-    res.sweeps = dev::cluster_jacobi(cl, W.Bm, W.Yw, K, W.sigma, W.X, W.Y, W.nrm, W.pos, S.s_rot, S.s_any);
+    if (small_on_cta) {
+      // the leading CTA alone, in its shared memory (the vector and ring areas are idle now)
+      int sw = 0;
+      if (rank == 0) {
+        __syncthreads();
+        sw = cta_jacobi(sB, sYw, K, W.sigma, W.X, W.Y, S.red, S.redi, S.s_rot);
+      }
+      cl.sync();  // sigma, X, Y visible to every CTA
+      res.sweeps = sw;
+    } else {
+      res.sweeps = dev::cluster_jacobi(cl, W.Bm, W.Yw, K, W.sigma, W.X, W.Y, W.nrm, W.pos, S.s_rot, S.s_any);
+    }
     const double bK = __ldcg(W.beta + (K - 1));
     const double s1 = __ldcg(W.sigma);
     double mx = 0.0;
@@ -1368,6 +1494,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     inf.restarts += r.restarts;
     inf.cycles += r.cycles;
     inf.breakdowns += r.breakdowns;
+    inf.svd_sweeps = std::max(inf.svd_sweeps, r.sweeps < 0 ? -r.sweeps : r.sweeps);
     inf.resid_est_max = std::max(inf.resid_est_max, r.resid_est);
     inf.ms_matvec += r.cyc[0] * ms_per_cycle;
     inf.ms_matvec_t += r.cyc[1] * ms_per_cycle;

@@ -131,7 +131,18 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_gram(const SkProb *__rest
       for (int j = 0; j < 4; ++j) y[i][j] = 0.f;
     double fro = 0.0;
     float v[kPerThr];
+    constexpr int kOPer = kTileC * kS / kSkThreads;  // 8 Omega entries per thread and tile
+    float ov[kOPer];
+    auto load_om = [&](int64_t c0) {
+#pragma unroll
+      for (int k = 0; k < kOPer; ++k) {
+        const int e = tid + kSkThreads * k;
+        const int64_t rr = c0 + e / kS;
+        ov[k] = rr < n ? om[rr * kS + e % kS] : 0.f;
+      }
+    };
     sk_load<T>(A, ld, m, n, r0, 0, v);
+    load_om(0);
     for (int64_t c0 = 0; c0 < n; c0 += kTileC) {
       float fs = 0.f;
       __syncthreads();  // the previous tile (or item) is consumed
@@ -141,13 +152,14 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_gram(const SkProb *__rest
         sA[(tid / kTileC + (kSkThreads / kTileC) * q) * (kTileC + 1) + tid % kTileC] = a;
         fs = fmaf(a, a, fs);
       }
-      for (int e = tid; e < kTileC * kS; e += kSkThreads) {
-        const int rr = e / kS;
-        sO[e] = (c0 + rr < n) ? om[(c0 + rr) * kS + e % kS] : 0.f;
-      }
+#pragma unroll
+      for (int k = 0; k < kOPer; ++k) sO[tid + kSkThreads * k] = ov[k];
       fro += (double)fs;
       __syncthreads();
-      if (c0 + kTileC < n) sk_load<T>(A, ld, m, n, r0, c0 + kTileC, v);  // next tile in flight
+      if (c0 + kTileC < n) {  // next tile in flight during the products
+        sk_load<T>(A, ld, m, n, r0, c0 + kTileC, v);
+        load_om(c0 + kTileC);
+      }
 #pragma unroll 8
       for (int kk = 0; kk < kTileC; ++kk) {
         const float4 o = *reinterpret_cast<const float4 *>(sO + kk * kS + tc);
@@ -193,12 +205,17 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_gram(const SkProb *__rest
   }
 }
 
+// tournament (circle method) pairing of 32 indices: round r, slot s
+__device__ __forceinline__ int pair_player(int r, int s) { return s == 0 ? 0 : ((s - 1 + r) % (kS - 1)) + 1; }
+
 // ---- sketch, stage 2: per problem, sum the chunk partials in chunk order,
-// eigenvalues of G by cyclic Jacobi (one warp), the 35 features --------------
+// eigenvalues of G by parallel cyclic Jacobi (one warp), the 35 features --------
 __global__ void __launch_bounds__(32) k_sketch_eig(const SkProb *__restrict__ probs, const int *__restrict__ first,
                                                   int count, const double *__restrict__ gpart,
                                                   const double *__restrict__ fpart, float *__restrict__ feats) {
   __shared__ double sG[kS * kS];
+  __shared__ double2 sRot[kS / 2];
+  __shared__ int2 sPair[kS / 2];
   const int lane = threadIdx.x;
   for (int p = blockIdx.x; p < count; p += gridDim.x) {
     const SkProb P = probs[p];
@@ -219,33 +236,54 @@ __global__ void __launch_bounds__(32) k_sketch_eig(const SkProb *__restrict__ pr
     double fro2 = 0.0;
     for (int c = c0; c < c1; ++c) fro2 += fpart[c];
     __syncwarp();
+    // parallel cyclic Jacobi (tournament ordering): each round, lanes 0..15 take one of 16
+    // disjoint index pairs and compute its rotation; the warp then applies all 16 to the
+    // columns (lane = row) and to the rows (lane = column)
     for (int sweep = 0; sweep < 30; ++sweep) {
       int rotated = 0;
-      for (int pp = 0; pp < kS - 1; ++pp)
-        for (int q = pp + 1; q < kS; ++q) {
+      for (int r = 0; r < kS - 1; ++r) {
+        if (lane < kS / 2) {
+          int pp = pair_player(r, lane), q = pair_player(r, kS - 1 - lane);
+          if (pp > q) {
+            const int t = pp;
+            pp = q;
+            q = t;
+          }
           const double apq = sG[pp * kS + q];
           const double app = sG[pp * kS + pp], aqq = sG[q * kS + q];
-          if (apq == 0.0 || fabs(apq) <= 0x1.0p-52 * sqrt(fabs(app) * fabs(aqq))) continue;
-          rotated = 1;
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t =
-              fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-          __syncwarp();
-          {  // columns pp, q
-            const double x = sG[lane * kS + pp], y2 = sG[lane * kS + q];
-            sG[lane * kS + pp] = c * x - s * y2;
-            sG[lane * kS + q] = s * x + c * y2;
+          double c = 1.0, sn = 0.0;
+          if (!(apq == 0.0 || fabs(apq) <= 0x1.0p-52 * sqrt(fabs(app) * fabs(aqq)))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t =
+                fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+            rotated = 1;
           }
-          __syncwarp();
-          {  // rows pp, q
-            const double x = sG[pp * kS + lane], y2 = sG[q * kS + lane];
-            sG[pp * kS + lane] = c * x - s * y2;
-            sG[q * kS + lane] = s * x + c * y2;
-          }
-          __syncwarp();
+          sRot[lane] = make_double2(c, sn);
+          sPair[lane] = make_int2(pp, q);
         }
-      if (!rotated) break;
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < kS / 2; ++k) {  // columns: lane is the row
+          const double2 cs = sRot[k];
+          const int2 pq = sPair[k];
+          const double x = sG[lane * kS + pq.x], y2 = sG[lane * kS + pq.y];
+          sG[lane * kS + pq.x] = cs.x * x - cs.y * y2;
+          sG[lane * kS + pq.y] = cs.y * x + cs.x * y2;
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < kS / 2; ++k) {  // rows: lane is the column
+          const double2 cs = sRot[k];
+          const int2 pq = sPair[k];
+          const double x = sG[pq.x * kS + lane], y2 = sG[pq.y * kS + lane];
+          sG[pq.x * kS + lane] = cs.x * x - cs.y * y2;
+          sG[pq.y * kS + lane] = cs.y * x + cs.x * y2;
+        }
+        __syncwarp();
+      }
+      if (!__any_sync(0xffffffffu, rotated)) break;
     }
     // sort the eigenvalues descending and form the features
     const double lam = sG[lane * kS + lane];
