@@ -114,6 +114,7 @@ typedef struct {
   int64_t n_matvec;
   int64_t n_matvec_t;
   int64_t launches;      /* kernels this call launched (all of them the library's own) */
+  double ms_copy;        /* with GK_FLAG_PROFILE: host<->device copies of host operands and outputs */
 } gk_info;
 
 /* Fill *opts with the defaults above. */

@@ -279,7 +279,7 @@ int acquire(Workspace &ws, size_t bytes, const gk_opts &o, cudaStream_t s) {
 }
 
 // CUDA-event timing of kernel groups (GK_FLAG_PROFILE); events are pooled per thread
-enum ProfCat { PC_MATVEC = 0, PC_MATVEC_T = 1, PC_ORTH = 2, PC_SMALL = 3, PC_RESTART = 4, PC_N = 5 };
+enum ProfCat { PC_MATVEC = 0, PC_MATVEC_T = 1, PC_ORTH = 2, PC_SMALL = 3, PC_RESTART = 4, PC_COPY = 5, PC_N = 6 };
 thread_local std::vector<cudaEvent_t> t_event_pool;
 
 struct Prof {
@@ -322,8 +322,8 @@ struct Prof {
   void finish(gk_info *inf) {
     if (!on) return;
     cudaStreamSynchronize(s);
-    double ms[PC_N] = {0, 0, 0, 0, 0};
-    int64_t cnt[PC_N] = {0, 0, 0, 0, 0};
+    double ms[PC_N] = {0, 0, 0, 0, 0, 0};
+    int64_t cnt[PC_N] = {0, 0, 0, 0, 0, 0};
     for (const Rec &r : recs) {
       float t = 0.f;
       if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
@@ -336,6 +336,7 @@ struct Prof {
     inf->ms_orth = ms[PC_ORTH];
     inf->ms_small = ms[PC_SMALL];
     inf->ms_restart = ms[PC_RESTART];
+    inf->ms_copy = ms[PC_COPY];
     inf->n_matvec = cnt[PC_MATVEC];
     inf->n_matvec_t = cnt[PC_MATVEC_T];
   }
@@ -494,14 +495,16 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   if (rc) return rc;
   op = make_op(Ain);
   psvd_layout(Ain, p, d, st, host_out, host_start, ws.base, &b, &op);
+  Prof prof;
+  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
+  prof.s = s;
+  prof.begin(PC_COPY);
   rc = stage_copy(Ain, st, op, s);
+  prof.end();
   if (rc) return rc;
 
   const int64_t m = p.m, n = p.n, ldu = p.ldu, ldv = p.ldv;
   const int K = p.K;
-  Prof prof;
-  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
-  prof.s = s;
   GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
   GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (K + 2), s));
   GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (K + 2), s));
@@ -640,9 +643,11 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   GK_CUDA(cudaMemcpyAsync(&sk, b.sigma + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
   GK_CUDA(cudaMemcpyAsync(&sweeps, b.sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (host_out) {
+    prof.begin(PC_COPY);
     GK_CUDA(cudaMemcpyAsync(U, Uo, sizeof(double) * m * k, cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaMemcpyAsync(V, Vo, sizeof(double) * n * k, cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaMemcpyAsync(S, So, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    prof.end();
   }
   GK_CUDA(cudaMemcpyAsync(&hc.ctl, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   GK_CUDA(cudaStreamSynchronize(s));

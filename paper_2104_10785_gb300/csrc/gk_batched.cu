@@ -184,6 +184,11 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
                : "memory");
 }
 
+// L2 prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address
+__device__ __forceinline__ void l2_prefetch(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // geometry of the ring for one operator: rows of n elements at a pitch of whole 16-byte
 // groups; the bulk copies move the whole groups (bulk bytes), the consumers read the
 // last partial group, if any, from global memory
@@ -244,8 +249,9 @@ __device__ bool ring_rows(const BProb &P, Shm &S, const RingGeom &g, int64_t r0,
     const bool ok = mbar_wait_bounded(S.bar + slot, (q / kRingStages) & 1u);
     // every thread has finished the previous stage: its slot may be refilled
     const int bad = __syncthreads_or(!ok);
-    if (threadIdx.x == 0 && st >= 1 && st - 1 + kRingStages < nst && !bad)
+    if (threadIdx.x == 0 && st >= 1 && st - 1 + kRingStages < nst && !bad) {
       ring_issue<T>(P, S, g, r0, r1, st - 1 + kRingStages, (int)((q - 1) % kRingStages));
+    }
     if (bad) {
       if (threadIdx.x == 0) {
         atomicExch(S.err, 1);
@@ -301,8 +307,15 @@ __device__ void rows_matvec(const BProb &P, Shm &S, int64_t r0, int64_t r1, doub
   using VT = Vec<T>;
   constexpr int E = VT::E;
   const bool vec = (((uintptr_t)A % 16) == 0 && ((P.ld * (int64_t)sizeof(T)) % 16) == 0);
-  // two rows per warp at a time: 2 x 4 loads of 16 bytes in flight per lane
+  // two rows per warp at a time: 2 x 4 loads of 16 bytes in flight per lane; lane 0 asks L2
+  // for the warp's row pair two passes ahead
+  const unsigned pf_bytes = (unsigned)((n * (int64_t)sizeof(T)) & ~(int64_t)15);
   for (int64_t rb = r0 + 2 * warp; rb < r1; rb += 2 * nw) {
+    if (vec && lane == 0 && pf_bytes > 0) {
+      const int64_t pr = rb + 4 * nw;
+      if (pr < r1) l2_prefetch(A + pr * P.ld, pf_bytes);
+      if (pr + 1 < r1) l2_prefetch(A + (pr + 1) * P.ld, pf_bytes);
+    }
     double acc[2] = {0.0, 0.0};
     const int nr = (r1 - rb) >= 2 ? 2 : 1;  // the second row repeats the first when the slice is odd
     int64_t tail0 = 0;

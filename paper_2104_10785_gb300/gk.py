@@ -53,6 +53,7 @@ class gk_info(C.Structure):
         ("resid_est_max", C.c_double), ("sigma_est", C.c_double), ("seconds", C.c_double),
         ("ms_matvec", C.c_double), ("ms_matvec_t", C.c_double), ("ms_orth", C.c_double), ("ms_small", C.c_double),
         ("ms_restart", C.c_double), ("n_matvec", C.c_int64), ("n_matvec_t", C.c_int64), ("launches", C.c_int64),
+        ("ms_copy", C.c_double),
     ]
 
     def as_dict(self):
