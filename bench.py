@@ -466,11 +466,12 @@ def run_gk(args, rank, world):
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
+        # host buffers from the library's allocator (huge-page backed, registered), on the GPU's
+        # local CPUs
         with near_gpu(gpu_index) as ng:
-            Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
-            outs = (torch.empty((k, w["m"]), dtype=torch.float64, pin_memory=True),
-                    torch.empty(k, dtype=torch.float64, pin_memory=True),
-                    torch.empty((k, w["n"]), dtype=torch.float64, pin_memory=True))
+            Ah = gk.host_empty(A.shape, A.dtype)
+            outs = (gk.host_empty((k, w["m"]), torch.float64), gk.host_empty((k,), torch.float64),
+                    gk.host_empty((k, w["n"]), torch.float64))
         Ah.copy_(A)
         gk.gk_psvd(Ah, k, tol, out=outs, **kw)
         # the host link's bandwidth at this moment, for reading the figure
@@ -503,9 +504,11 @@ def run_gk(args, rank, world):
                "h2d_bytes_per_step": int(Ah.numel() * Ah.element_size()),
                "d2h_bytes_per_step": int(8 * k * (w["m"] + w["n"] + 1)), "ms_per_step": te * 1e3,
                "h2d_GBs_torch_copy": h2d_gbs,
-               "host_buffers": "pinned, allocated on the GPU's local CPUs %s" % (
+               "host_buffers": "gk_host_alloc (huge-page backed, registered), allocated on the GPU's local CPUs %s" % (
                    sorted(ng.cpus) if ng.cpus else "(local CPU list unavailable: default placement)")}
-        del Ah
+        for t in (Ah,) + outs:
+            gk.host_free(t)
+        del Ah, outs
 
     # plain path: the same solve on the f32-stored copy
     plain = None

@@ -299,6 +299,17 @@ const char *gk_last_cuda_error(void);
 /* Library version string. */
 const char *gk_version(void);
 
+/* Pinned host memory for host operands and results (the calls above accept
+ * any host pointer; copies from this memory stay at the link's full rate).
+ * gk_host_alloc maps at least `bytes` of anonymous memory aligned to the
+ * transparent-huge-page size, asks the kernel to back it with huge pages,
+ * zero-fills it and registers it with CUDA (cudaHostRegister); *ptr receives
+ * the address (owned by the library until gk_host_free).  Errors:
+ * GK_INVALID_ARG (null ptr, zero bytes, or an address gk_host_alloc did not
+ * return), GK_NO_DEVICE, GK_OUT_OF_MEMORY (mmap), GK_CUDA_ERROR (registration). */
+int gk_host_alloc(size_t bytes, void **ptr);
+int gk_host_free(void *ptr);
+
 /* Kernels the calling host thread has launched through this library so far
  * (every entry point counts its own launches; the counter never resets). */
 int64_t gk_launch_count(void);

@@ -20,6 +20,8 @@ from .gk import (  # noqa: F401
     gk_psvd_workspace,
     gk_residuals,
     gk_sketch_batched,
+    host_empty,
+    host_free,
     last_cuda_error,
     launch_count,
     lib,

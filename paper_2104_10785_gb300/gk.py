@@ -134,6 +134,10 @@ def lib():
             L.gk_version.restype = C.c_char_p
             L.gk_launch_count.argtypes = []
             L.gk_launch_count.restype = C.c_int64
+            L.gk_host_alloc.argtypes = [C.c_size_t, C.POINTER(C.c_void_p)]
+            L.gk_host_alloc.restype = C.c_int
+            L.gk_host_free.argtypes = [C.c_void_p]
+            L.gk_host_free.restype = C.c_int
             _lib = L
     return _lib
 
@@ -148,6 +152,37 @@ def last_cuda_error() -> str:
 
 def version() -> str:
     return lib().gk_version().decode()
+
+
+_host_bufs = {}
+
+
+def host_empty(shape, dtype=torch.float32):
+    """A host tensor in huge-page-backed pinned memory from gk_host_alloc (release with host_free)."""
+    import numpy as np
+
+    shape = tuple(int(x) for x in shape)
+    esz = torch.empty((), dtype=dtype).element_size()
+    nbytes = esz
+    for d in shape:
+        nbytes *= d
+    p = C.c_void_p()
+    st = lib().gk_host_alloc(max(nbytes, 1), C.byref(p))
+    if st < 0:
+        raise GKError(st, "gk_host_alloc")
+    raw = (C.c_uint8 * max(nbytes, 1)).from_address(p.value)
+    t = torch.from_numpy(np.frombuffer(raw, dtype=np.uint8, count=nbytes)).view(dtype).view(shape)
+    _host_bufs[t.data_ptr()] = (p.value, raw)
+    return t
+
+
+def host_free(t) -> None:
+    ent = _host_bufs.pop(t.data_ptr(), None)
+    if ent is None:
+        raise ValueError("not a tensor from host_empty")
+    st = lib().gk_host_free(C.c_void_p(ent[0]))
+    if st < 0:
+        raise GKError(st, "gk_host_free")
 
 
 def launch_count() -> int:

@@ -282,6 +282,31 @@ def test_psvd_host_buffers_end_to_end():
     np.testing.assert_array_equal(S.numpy(), Sd.cpu().numpy())
 
 
+def test_library_host_buffers():
+    """gk_host_alloc memory: an operator and outputs in it give the device results bit for bit;
+    freeing twice (or a foreign address) is rejected."""
+    M = gk()
+    sig = synth.sigma_geometric(256, 0.85)
+    A, _, _ = synth.prescribed_spectrum(900, 256, sig, seed=6, dtype=np.float32)
+    Ah = M.host_empty(A.shape, torch.float32)
+    assert Ah.is_pinned() and Ah.data_ptr() % 4096 == 0
+    Ah.copy_(torch.from_numpy(A))
+    outs = (M.host_empty((5, 900), torch.float64), M.host_empty((5,), torch.float64),
+            M.host_empty((5, 256), torch.float64))
+    U, S, V, st, info = M.gk_psvd(Ah, 5, 1e-8, krylov_dim=18, out=outs)
+    Ud, Sd, Vd, st2, _ = M.gk_psvd(Ah.cuda(), 5, 1e-8, krylov_dim=18)
+    assert st == st2 == 0
+    np.testing.assert_array_equal(S.numpy(), Sd.cpu().numpy())
+    np.testing.assert_array_equal(U.numpy(), Ud.cpu().numpy())
+    for t in (Ah,) + outs:
+        M.host_free(t)
+    with pytest.raises(ValueError):
+        M.host_free(Ah)
+    from paper_2104_10785_gb300 import gk as gkmod
+
+    assert M.lib().gk_host_free(None) == gkmod.GK_INVALID_ARG
+
+
 def test_invalid_arguments_are_rejected():
     M = gk()
     A = torch.ones((10, 8), dtype=torch.float32, device="cuda")
