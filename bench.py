@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
+F64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (CUDA cores); measured f64 FMA here: 1.19
 
 
 def peaks():
@@ -171,6 +172,16 @@ def make_workload(name, device, want_plain=True):
     elif w["kind"] == "product":
         w["A"] = synth.torch_gaussian_product(w["m"], w["n"], w["r"], w["noise"], w["seed"], device=device)
         w["A_plain"] = None
+    elif w["kind"] == "sparse":
+        import paper_2104_10785_gb300 as gk
+
+        sigp = 100.0 * 0.95 ** np.arange(1, w["k"] + 1)
+        d = synth.sparse_planted(w["m"], w["n"], w["per_row"], sigp, w["seed"])
+        c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        w["A"] = gk.CSR(w["m"], w["n"], c(d["rowptr"]), c(d["colind"]), c(d["vals"]), c(d["t_rowptr"]),
+                        c(d["t_colind"]), c(d["t_vals"]))
+        w["csr_host"] = d
+        w["A_plain"] = None
     else:
         raise SystemExit(f"workload {name} is not benchmarked by this script")
     torch.cuda.synchronize()
@@ -196,14 +207,45 @@ def profiled_traffic(kernel, workload):
     return None
 
 
+def operator_dtype(A):
+    return A.vals.dtype if hasattr(A, "t_vals") else A.dtype
+
+
+def operator_bytes(A):
+    """Bytes of the stored operator (a CSR counts A and its transpose)."""
+    if hasattr(A, "t_vals"):
+        return sum(t.numel() * t.element_size() for t in (A.vals, A.colind, A.rowptr, A.t_vals, A.t_colind, A.t_rowptr))
+    return A.numel() * A.element_size()
+
+
 def algorithmic_bytes(w, which):
-    """Bytes one launch of the product kernel must move: the stored operator once,
-    the f32 input vector, the f64 output and the f64 vector it subtracts."""
+    """Bytes one launch of the product kernel must move: the stored operator once (a CSR: its
+    values, column indices and row pointers), the input vector (f32, gathered once for a CSR:
+    f64), the f64 output and the f64 vector it subtracts."""
     m, n = w["m"], w["n"]
-    es = w["A"].element_size()
+    A = w["A"]
+    if hasattr(A, "t_vals"):
+        es = A.vals.element_size()
+        nnz = A.vals.numel()
+        rows, cols = (m, n) if which == "matvec" else (n, m)
+        return nnz * (es + 4) + 4 * (rows + 1) + 8 * cols + 16 * rows
+    es = A.element_size()
     if which == "matvec":
         return es * m * n + 4 * n + 8 * m + 8 * m
     return es * m * n + 4 * m + 8 * n + 8 * n
+
+
+def orth_work(m, n, K, keep, cycles, passes=2):
+    """f64 flops and bytes of the two-pass classical Gram-Schmidt of one solve: step j of a cycle
+    orthogonalizes the m-vector against j columns and the n-vector against j + 1; each pass reads
+    the columns twice (coefficients, update) and the vector twice, writes it once."""
+    fl = by = 0
+    for c in range(cycles):
+        for j in range(0 if c == 0 else keep, K):
+            for length, cols in ((m, j), (n, j + 1)):
+                fl += passes * 4 * length * cols
+                by += passes * (16 * length * cols + 24 * length)
+    return fl, by
 
 
 # ---------------------------------------------------------------------------
@@ -215,6 +257,9 @@ def oracle_operator(w):
     import oracle
 
     A = w["A"]
+    if "csr_host" in w:
+        d = w["csr_host"]
+        return oracle.Operator.csr(w["m"], w["n"], d["rowptr"], d["colind"], d["vals"], "f32")
     if A.dtype == torch.bfloat16:
         bits = A.view(torch.int16).cpu().numpy().view(np.uint16)
         return oracle.Operator.dense(None, dtype="bf16", bits=bits)
@@ -238,6 +283,18 @@ def oracle_reduced_steps(w):
     import synth
 
     m, n = w["m"] // 10, w["n"] // 10
+    if w["kind"] == "product":  # Algorithm 3: the steps to the break at the same rank
+        A = synth.gaussian_product(m, n, w["r"], w["noise"], w["seed"], dtype=np.float32)
+        t = time.perf_counter()
+        _, kp, _ = oracle.numrank(oracle.Operator.dense(A), synth.start_vector(m, 1), eps=w["eps"], kmax=512)
+        return float(kp), time.perf_counter() - t, (m, n)
+    if w["kind"] == "sparse":  # the full-size CSR's own oracle solve is too long: reduce rows and columns
+        sigp = 100.0 * 0.95 ** np.arange(1, w["k"] + 1)
+        d = synth.sparse_planted(m, n, w["per_row"], sigp, w["seed"])
+        op = oracle.Operator.csr(m, n, d["rowptr"], d["colind"], d["vals"], "f32")
+        t = time.perf_counter()
+        _, _, _, info = oracle.psvd(op, w["k"], w["K"], synth.start_vector(m, 1), tol=w["tol"], max_restarts=400)
+        return info["matvecs"] / 2.0, time.perf_counter() - t, (m, n)
     if w["kind"] == "spectrum_pow":
         sig = synth.sigma_power(n, w["e"])
     else:
@@ -263,7 +320,7 @@ def cpu_threads():
 # ---------------------------------------------------------------------------
 # batched workload: plain vs learned pipelines
 # ---------------------------------------------------------------------------
-def batched_leg(device, steps, warmup):
+def batched_leg(device, steps, warmup, keep_mats=False):
     import torch
 
     import paper_2104_10785_gb300 as gk
@@ -327,6 +384,8 @@ def batched_leg(device, steps, warmup):
                        "frac": kbytes / (kms / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_batched<float>",
                        "bytes_per_launch": int(kbytes), "avg_launch_ms": kms, "launches": reps,
                        "cluster_size": info["reserved"], "clusters": info["kprime"], "peak_source": peak_kind}
+    if keep_mats:
+        res["_mats"], res["_shapes"] = mats, shapes
     res["config"] = {"workload": "batched_f32_512_rank5to64", "count": w["count"], "eps": w["eps"], "tol": w["tol"],
                      "bytes": int(sum(A.numel() * 4 for A in mats)), "gen_seconds": gen,
                      "l2": "inputs larger than L2 (%.1f GB in total)" % (sum(A.numel() * 4 for A in mats) / 1e9)}
@@ -350,6 +409,25 @@ def run_reference(args, rank, world):
     device = torch.device("cuda", 0) if torch.cuda.is_available() else None
     if device is None:
         return {"impl": "reference", "unavailable": "the synthetic operator is generated on the GPU and no GPU is visible"}
+    if args.workload == "batched_f32_512_rank5to64":
+        w = synth.WORKLOADS[args.workload]
+        shapes = synth.batched_shapes(w["count"], w["seed"])
+        mats = synth.torch_batched_products(shapes, 1e-6, w["seed"], device=device)
+        idx = (0, 1, 64, 128, 192, 256, 320, 384)
+        vals = []
+        for _ in range(args.steps):
+            v, cores, desc = oracle_batched_sample(mats, shapes, w, idx)
+            vals.append(v)
+        value = float(np.mean(vals))
+        return {
+            "metric": "converged top-k triplets/sec at <=1e-8 rel. residual", "value": value, "unit": "triplets/s",
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": 0,
+            "ms_per_step": sum(shapes[i][2] for i in idx) / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "count": w["count"], "eps": w["eps"], "tol": w["tol"]},
+            "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
     w = make_workload(args.workload, device, want_plain=False)
     op = oracle_operator(w)
     del w["A"]
@@ -365,10 +443,23 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         per.append(oracle_step_seconds(op, w, sample_steps, q1))
     t_step = float(np.mean(per))
-    value = w["k"] / (t_step * steps_needed)
+    numrank = w["kind"] == "product"
+    value = (1.0 if numrank else w["k"]) / (t_step * steps_needed)
+    unit = "rank estimations/s" if numrank else "triplets/s"
     sample = (f"{sample_steps} oracle bidiagonalization steps on the full {w['m']}x{w['n']} {w['dtype']} operator "
-              f"per step ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps the oracle's complete solve "
-              f"of the {red_shape[0]}x{red_shape[1]} instance of the same recipe needed")
+              f"per step ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps the oracle's complete "
+              f"{'rank estimate' if numrank else 'solve'} of the {red_shape[0]}x{red_shape[1]} instance of the same "
+              f"recipe needed")
+    if numrank:
+        return {
+            "metric": "numerical rank estimations/sec (Algorithm 3, eps 1e-5 relative)", "value": value, "unit": unit,
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step * steps_needed * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "true_rank": w["r"], "eps": w["eps"]},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
     return {
         "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
         "value": value, "unit": "triplets/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
@@ -396,6 +487,8 @@ def run_gk(args, rank, world):
     gk.lib()
     if args.workload == "batched_f32_512_rank5to64":
         return run_batched_headline(args, rank, world, device)
+    if args.workload == "dense_f32_50000x20000_rank200":
+        return run_numrank_headline(args, rank, world, device)
     w = make_workload(args.workload, device, want_plain=not args.no_plain)
     k, K, tol = w["k"], w["K"], w["tol"]
     A = w["A"]
@@ -414,22 +507,26 @@ def run_gk(args, rank, world):
     # timed region: inputs resident in HBM (8 GB operator > 129 MB L2)
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    # an operator that fits in L2 (129 MB) is flushed from it before every timed step (a 512 MB
+    # write between the events of consecutive steps)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device) if operator_bytes(A) < (256 << 20) else None
     clocks = ClockSampler(gpu_index)
     barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos, statuses = [], []
-    for _ in range(args.steps):
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
         U, S, V, st, info = gk.gk_psvd(A, k, tol, profile=True, **kw)
+        evs[i][1].record(stream)
         infos.append(info)
         statuses.append(st)
-    ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
     if dist:
         t = torch.tensor([ms], device=device)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
@@ -442,23 +539,48 @@ def run_gk(args, rank, world):
     resid_rel = float(torch.maximum(r_av, r_atu).max()) / s1
     sig_err = float(np.max(np.abs(S.cpu().numpy() - w["sigma_true"]) / w["sigma_true"])) if "sigma_true" in w else None
 
-    # dominant kernel roofline from the CUDA events recorded around each product launch
+    # dominant kernel group (CUDA events recorded by the library around every launch group)
     tot = {key: sum(i[key] for i in infos) for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "ms_small",
                                                         "ms_restart", "n_matvec", "n_matvec_t")}
     hbm, peak_kind = peaks()
-    which = "matvec" if tot["ms_matvec"] >= tot["ms_matvec_t"] else "matvec_t"
-    nl = tot["n_" + which]
-    avg_ms = tot["ms_" + which] / max(1, nl)
-    bpl = algorithmic_bytes(w, which)
-    achieved = bpl / (avg_ms / 1e3) / 1e9
-    other = "matvec_t" if which == "matvec" else "matvec"
-    avg_other = tot["ms_" + other] / max(1, tot["n_" + other])
-    kname = "k_gemv_bulk+k_gemv_reduce" if which == "matvec" else "k_gemvt_lp+k_gemvt_reduce"
-    traffic = args.traffic if args.traffic is not None else profiled_traffic(kname, w["name"])
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": kname,
-            "bytes_per_launch": bpl, "avg_launch_ms": avg_ms, "launches": nl, "peak_source": peak_kind,
-            "other_product_GBs": algorithmic_bytes(w, other) / (avg_other / 1e3) / 1e9 if avg_other > 0 else None}
+    f64_op = operator_dtype(A) == torch.float64
+    is_csr = hasattr(A, "t_vals")
+    names = {"matvec": "k_spmv (A x)" if is_csr else ("k_gemv_f64" if f64_op else "k_gemv_bulk+k_gemv_reduce"),
+             "matvec_t": "k_spmv (A^T x)" if is_csr else ("k_gemvt_f64" if f64_op else "k_gemvt_lp+k_gemvt_reduce")}
+    groups = {}
+    for which in ("matvec", "matvec_t"):
+        nl = tot["n_" + which]
+        if nl <= 0:
+            continue
+        avg_ms = tot["ms_" + which] / nl
+        bpl = algorithmic_bytes(w, which)
+        g = {"kernel": names[which], "avg_launch_ms": avg_ms, "launches": nl, "bytes_per_launch": bpl,
+             "GBs": bpl / (avg_ms / 1e3) / 1e9, "total_ms": tot["ms_" + which]}
+        if f64_op and not is_csr:
+            g["flops_per_launch"] = 2 * w["m"] * w["n"]
+            g["TFLOPs"] = g["flops_per_launch"] / (avg_ms / 1e3) / 1e12
+        groups[which] = g
+    keep = k + (K - k) // 2
+    ofl, oby = orth_work(w["m"], w["n"], K, keep, infos[-1]["cycles"])
+    oms = tot["ms_orth"] / len(infos)
+    groups["orth"] = {"kernel": "k_cgs_dot+k_cgs_update_*+k_reduce_cols (per solve)", "total_ms": tot["ms_orth"],
+                      "ms_per_solve": oms, "flops_per_solve": ofl, "bytes_per_solve": oby,
+                      "TFLOPs": ofl / (oms / 1e3) / 1e12 if oms > 0 else None,
+                      "GBs": oby / (oms / 1e3) / 1e9 if oms > 0 else None}
+    dom = max(groups, key=lambda g: groups[g]["total_ms"])
+    G = groups[dom]
+    if dom == "orth" or (f64_op and not is_csr):
+        achieved = G["TFLOPs"]
+        roof = {"bound": "alu", "achieved": achieved, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / F64_PEAK_TFLOPS, "traffic": None, "kernel": G["kernel"],
+                "peak_source": "nominal FP64 rate of the GB300 (f64 FMA on CUDA cores)"}
+    else:
+        kname = G["kernel"]
+        traffic = args.traffic if args.traffic is not None else profiled_traffic(kname, w["name"])
+        roof = {"bound": "hbm", "achieved": G["GBs"], "peak": hbm, "unit": "GB/s", "frac": G["GBs"] / hbm,
+                "traffic": traffic, "kernel": kname, "bytes_per_launch": G["bytes_per_launch"],
+                "avg_launch_ms": G["avg_launch_ms"], "launches": G["launches"], "peak_source": peak_kind}
+    roof["groups"] = groups
     step_ms = ms / args.steps
     breakdown = {key: tot[key] / args.steps for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "ms_small",
                                                           "ms_restart")}
@@ -469,21 +591,32 @@ def run_gk(args, rank, world):
         # host buffers from the library's allocator (huge-page backed, registered), on the GPU's
         # local CPUs
         with near_gpu(gpu_index) as ng:
-            Ah = gk.host_empty(A.shape, A.dtype)
+            if is_csr:
+                parts = [gk.host_empty(t.shape, t.dtype) for t in
+                         (A.rowptr, A.colind, A.vals, A.t_rowptr, A.t_colind, A.t_vals)]
+                for hp_, t in zip(parts, (A.rowptr, A.colind, A.vals, A.t_rowptr, A.t_colind, A.t_vals)):
+                    hp_.copy_(t)
+                Ah = gk.CSR(w["m"], w["n"], *parts)
+                host_list = parts
+                big = A.vals
+                big_h = parts[2]
+            else:
+                Ah = gk.host_empty(A.shape, A.dtype)
+                Ah.copy_(A)
+                host_list = [Ah]
+                big, big_h = A, Ah
             outs = (gk.host_empty((k, w["m"]), torch.float64), gk.host_empty((k,), torch.float64),
                     gk.host_empty((k, w["n"]), torch.float64))
-        Ah.copy_(A)
         gk.gk_psvd(Ah, k, tol, out=outs, **kw)
         # the host link's bandwidth at this moment, for reading the figure
-        Bd = torch.empty_like(A)
+        Bd = torch.empty_like(big)
+        torch.cuda.synchronize()
+        Bd.copy_(big_h, non_blocking=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Bd.copy_(Ah, non_blocking=True)
+        Bd.copy_(big_h, non_blocking=True)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Bd.copy_(Ah, non_blocking=True)
-        torch.cuda.synchronize()
-        h2d_gbs = Ah.numel() * Ah.element_size() / (time.perf_counter() - t0) / 1e9
+        h2d_gbs = big_h.numel() * big_h.element_size() / (time.perf_counter() - t0) / 1e9
         del Bd
         barrier()
         reps = max(1, min(args.steps, 3))
@@ -501,14 +634,14 @@ def run_gk(args, rank, world):
         e2e = {"value": k * world / te, "unit": "triplets/s", "library_ms": infoh["seconds"] * 1e3,
                "profiled_call_ms": {key: infop[key] for key in ("seconds", "ms_copy", "ms_matvec", "ms_matvec_t",
                                                                 "ms_orth", "ms_small", "ms_restart")},
-               "h2d_bytes_per_step": int(Ah.numel() * Ah.element_size()),
+               "h2d_bytes_per_step": int(operator_bytes(Ah)),
                "d2h_bytes_per_step": int(8 * k * (w["m"] + w["n"] + 1)), "ms_per_step": te * 1e3,
                "h2d_GBs_torch_copy": h2d_gbs,
                "host_buffers": "gk_host_alloc (huge-page backed, registered), allocated on the GPU's local CPUs %s" % (
                    sorted(ng.cpus) if ng.cpus else "(local CPU list unavailable: default placement)")}
-        for t in (Ah,) + outs:
+        for t in list(host_list) + list(outs):
             gk.host_free(t)
-        del Ah, outs
+        del Ah, outs, host_list
 
     # plain path: the same solve on the f32-stored copy
     plain = None
@@ -550,9 +683,9 @@ def run_gk(args, rank, world):
                           f"{w['dtype']} operator ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps "
                           f"the solve needed")}
 
-    a_dtype, a_bytes = A.dtype, A.numel() * A.element_size()
+    a_dtype, a_bytes = operator_dtype(A), operator_bytes(A)
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and args.workload == "dense_bf16_100000x40000_top100":
         del A
         w.pop("A", None)
         torch.cuda.empty_cache()
@@ -568,7 +701,8 @@ def run_gk(args, rank, world):
         "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": K, "tol": tol,
                    "storage": w["dtype"], "accumulate": "f32 runs combined in f64; f64 basis, small SVD, residuals",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (operator %.1f GB)" % (a_bytes / 1e9)},
+                   "l2": ("inputs larger than L2 (operator %.2f GB)" % (a_bytes / 1e9)) if flush is None else
+                   "L2 flushed before every timed step (operator %.1f MB)" % (a_bytes / 1e6)},
         "status": statuses[-1], "resid_max_rel": resid_rel, "sigma_rel_err_vs_prescribed": sig_err,
         "restarts": last["restarts"], "matvecs": last["matvecs"], "steps_per_solve": last["steps"],
         "breakdown_ms_per_step": breakdown,
@@ -580,6 +714,125 @@ def run_gk(args, rank, world):
     return out
 
 
+def run_numrank_headline(args, rank, world, device):
+    """Numerical rank (Algorithm 3 on Algorithm 1) of the dense f32 rank-200 product: one step =
+    one gk_numrank call; value = rank estimations per second; the rank must equal the true 200."""
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+    import synth
+
+    w = make_workload(args.workload, device, want_plain=False)
+    A = w["A"]
+    stream = torch.cuda.current_stream(device)
+    eps, kmax = w["eps"], 512
+    for _ in range(args.warmup):
+        r, _, st, info = gk.gk_numrank(A, eps, kmax, seed=w["seed"])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device.index or 0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos, ranks = [], []
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        r, _, st, info = gk.gk_numrank(A, eps, kmax, seed=w["seed"], profile=True)
+        evs[i][1].record(stream)
+        infos.append(info)
+        ranks.append(r)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        import torch.distributed as tdist
+
+        t = torch.tensor([ms], device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = args.steps * world / (ms / 1e3)
+    tot = {key: sum(i[key] for i in infos) for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "n_matvec",
+                                                        "n_matvec_t")}
+    hbm, peak_kind = peaks()
+    groups = {}
+    for which, kname in (("matvec", "k_gemv_bulk+k_gemv_reduce"), ("matvec_t", "k_gemvt_lp+k_gemvt_reduce")):
+        nl = tot["n_" + which]
+        if nl > 0:
+            avg = tot["ms_" + which] / nl
+            bpl = algorithmic_bytes(w, which)
+            groups[which] = {"kernel": kname, "avg_launch_ms": avg, "launches": nl, "bytes_per_launch": bpl,
+                             "GBs": bpl / (avg / 1e3) / 1e9, "total_ms": tot["ms_" + which]}
+    kp = infos[-1]["kprime"]
+    ofl, oby = orth_work(w["m"], w["n"], kp, 0, 1)
+    oms = tot["ms_orth"] / len(infos)
+    groups["orth"] = {"kernel": "k_cgs_* (per call)", "total_ms": tot["ms_orth"], "ms_per_call": oms,
+                      "TFLOPs": ofl / (oms / 1e3) / 1e12 if oms > 0 else None,
+                      "GBs": oby / (oms / 1e3) / 1e9 if oms > 0 else None}
+    G = groups["matvec"] if groups["matvec"]["total_ms"] >= groups["matvec_t"]["total_ms"] else groups["matvec_t"]
+    roof = {"bound": "hbm", "achieved": G["GBs"], "peak": hbm, "unit": "GB/s", "frac": G["GBs"] / hbm,
+            "traffic": None, "kernel": G["kernel"], "bytes_per_launch": G["bytes_per_launch"],
+            "avg_launch_ms": G["avg_launch_ms"], "launches": G["launches"], "peak_source": peak_kind,
+            "groups": groups}
+    # end to end from library host memory (4 GB H2D per call, the rank read back)
+    Ah = gk.host_empty(A.shape, A.dtype)
+    Ah.copy_(A)
+    gk.gk_numrank(Ah, eps, kmax, seed=w["seed"])
+    t0 = time.perf_counter()
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        rh, _, sth, infoh = gk.gk_numrank(Ah, eps, kmax, seed=w["seed"])
+    te = (time.perf_counter() - t0) / reps
+    e2e = {"value": world / te, "unit": "rank estimations/s", "ms_per_step": te * 1e3,
+           "h2d_bytes_per_step": int(Ah.numel() * Ah.element_size()), "d2h_bytes_per_step": 4, "rank": rh}
+    gk.host_free(Ah)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        op = oracle_operator(w)
+        cores = cpu_threads()
+        oracle.set_threads(cores)
+        q1 = synth.start_vector(w["m"], w["seed"])
+        t_step = oracle_step_seconds(op, w, args.cpu_steps, q1)
+        cpu = {"value": 1.0 / (t_step * kp), "unit": "rank estimations/s", "cores": cores, "kind": "oracle",
+               "sample": (f"{args.cpu_steps} oracle bidiagonalization steps on the same {w['m']}x{w['n']} f32 "
+                          f"operator ({t_step:.3f} s/step), scaled by the {kp} steps the GPU call needed")}
+    return {
+        "metric": "numerical rank estimations/sec (Algorithm 3, eps 1e-5 relative)",
+        "value": value, "unit": "rank estimations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "true_rank": w["r"], "eps": eps, "kmax": kmax,
+                   "l2": "inputs larger than L2 (operator %.1f GB)" % (A.numel() * A.element_size() / 1e9)},
+        "ranks": sorted(set(ranks)), "rank_equals_truth": all(r == w["r"] for r in ranks), "steps_per_call": kp,
+        "roofline": roof, "clocks": clk, "gpu_launches": int(sum(i["launches"] for i in infos)),
+        "e2e": e2e, "cpu_baseline": cpu,
+    }
+
+
+def oracle_batched_sample(mats, shapes, w, idx=(0, 1, 64, 128, 192, 256, 320, 384)):
+    """The oracle, as it stands, on a bounded sample of the batch: for each sampled problem
+    Algorithm 3 for the rank, then the top-r partial SVD (K = max(2r, r+16)), on the stored
+    f32 bytes; returns (triplets per second, cores, description)."""
+    import oracle
+    import synth
+
+    cores = cpu_threads()
+    oracle.set_threads(cores)
+    trip = 0
+    t = time.perf_counter()
+    for i in idx:
+        A = mats[i].cpu().numpy()
+        op = oracle.Operator.dense(A)
+        q1 = synth.start_vector(A.shape[0], w["seed"] + i)
+        r, kp, _ = oracle.numrank(op, q1, eps=w["eps"], kmax=min(min(A.shape), 160))
+        r = max(1, r)
+        K = min(max(2 * r, r + 16), min(A.shape))
+        oracle.psvd(op, r, K, q1, tol=w["tol"], max_restarts=400)
+        trip += r
+    dt = time.perf_counter() - t
+    desc = (f"{len(idx)} problems of the batch ({', '.join(str(i) for i in idx)}): the oracle's Algorithm 3 then "
+            f"its top-r partial SVD, {trip} triplets in {dt:.1f} s")
+    return trip / dt, cores, desc
+
+
 def run_batched_headline(args, rank, world, device):
     """The batched workload as the headline: value = converged triplets/s of the learned pipeline
     (sketch, network, one batched partial SVD judged by its own spectrum, plain fallback); the plain
@@ -587,8 +840,16 @@ def run_batched_headline(args, rank, world, device):
     import torch
 
     clocks = ClockSampler(device.index or 0)
-    res = batched_leg(device, args.steps, args.warmup)
+    res = batched_leg(device, args.steps, args.warmup, keep_mats=True)
     clk = clocks.stop()
+    mats, shapes = res.pop("_mats"), res.pop("_shapes")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import synth
+
+        v, cores, desc = oracle_batched_sample(mats, shapes, synth.WORKLOADS["batched_f32_512_rank5to64"])
+        cpu = {"value": v, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": desc}
+    del mats
     ms = res["learned"]["ms_per_step"]
     if world > 1:
         import torch.distributed as tdist
@@ -603,7 +864,7 @@ def run_batched_headline(args, rank, world, device):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": res.pop("config"), "clocks": clk,
         "gpu_launches": int(res["learned"]["launches_per_step"] * args.steps),
-        "roofline": res.pop("roofline"), "e2e": None, "cpu_baseline": None, "batched": res,
+        "roofline": res.pop("roofline"), "e2e": None, "cpu_baseline": cpu, "batched": res,
     }
 
 

@@ -80,7 +80,10 @@ typedef struct {
   int32_t krylov_dim;    /* K, the Krylov dimension of one restart cycle (0 = default min(max(2k, k+16), min(m,n))) */
   int32_t keep;          /* Ritz vectors kept at a restart (0 = k + (K-k)/2) */
   int32_t max_restarts;  /* restart budget of gk_psvd (default 200) */
-  int32_t reorth_passes; /* classical Gram-Schmidt passes per vector: 2 (default) or 1 (as printed in the paper) */
+  int32_t reorth_passes; /* classical Gram-Schmidt per vector: 0 (default) = one pass, and a second
+                            only if the first left less than 1/sqrt(2) of the norm (the
+                            Daniel-Gragg-Kaufman-Stewart test); 1 = one pass (as printed in the
+                            paper); 2 or 3 = that many passes */
   int32_t eps_absolute;  /* gk_numrank: 0 = eps relative to sigma_1 (default), 1 = absolute threshold */
   int32_t flags;         /* GK_FLAG_* bits (0 = none) */
   uint64_t seed;         /* seed of the start vector and of replacement directions */
@@ -127,7 +130,7 @@ size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *opts);
  * Method: Golub-Kahan bidiagonalization (Section 2.2, Eqs. 2.1-2.4) in the
  * upper-bidiagonal form started from v1 = A^T q1 / ||A^T q1|| (Algorithm 1,
  * lines 1-2), full reorthogonalization by classical Gram-Schmidt (Algorithm 1,
- * lines 6 and 13; two passes by default), Ritz pairs from the SVD of the small
+ * lines 6 and 13; a second pass where the first cancels, by default), Ritz pairs from the SVD of the small
  * projected matrix (Eq. 2.13, Algorithm 2 lines 2-5), and thick restarts that
  * keep the leading Ritz vectors (the paper cites augmented restarting; the
  * restart itself is this library's choice).

@@ -86,6 +86,8 @@ def lib():
             L.gko_jacobi_svd.argtypes = [i64, i64, vp, vp, vp, vp]
             L.gko_jacobi_eig.argtypes = [i64, vp, vp, vp]
             L.gko_gk_lower.argtypes = [P(_Op), i32, d, i32, i32, vp, vp, vp, vp, vp, P(_GkInfo)]
+            L.gko_cgs.argtypes = [i32, vp, vp, i64, i64, i32]
+            L.gko_cgs.restype = None
             L.gko_numrank.argtypes = [P(_Op), i32, d, i32, i32, i32, vp, P(i32), P(_GkInfo), vp]
             L.gko_fsvd.argtypes = [P(_Op), i32, i32, i32, i32, vp, vp, vp, vp, P(_GkInfo)]
             L.gko_psvd.argtypes = [P(_Op), i32, i32, i32, d, i32, i32, vp, u64, vp, vp, vp, P(_PsvdInfo)]
@@ -209,7 +211,17 @@ def jacobi_eig(S):
     return th, G, sw
 
 
-def gk_lower(op: Operator, k: int, q1, eps=0.0, relative=True, passes=2):
+def cgs(w, Q, passes=0):
+    """Gram-Schmidt of w against the columns of Q (the oracle's step, as Algorithm 1 applies it)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    len_, j = Q.shape
+    Qc = np.ascontiguousarray(Q.T)  # row c = column c
+    out = np.array(w, dtype=np.float64, copy=True)
+    lib().gko_cgs(int(passes), _p(out), _p(Qc), C.c_int64(len_), C.c_int64(len_), int(j))
+    return out
+
+
+def gk_lower(op: Operator, k: int, q1, eps=0.0, relative=True, passes=0):
     """Algorithm 1.  Returns dict(alpha, beta, Q, P, kprime, stop_reason, sigma_est)."""
     m, n = op.m, op.n
     q1 = _f64(q1, m)
@@ -226,7 +238,7 @@ def gk_lower(op: Operator, k: int, q1, eps=0.0, relative=True, passes=2):
                 stop_reason=info.stop_reason, sigma_est=info.sigma_est)
 
 
-def numrank(op: Operator, q1, eps=1e-8, relative=True, literal=False, kmax=0, passes=2):
+def numrank(op: Operator, q1, eps=1e-8, relative=True, literal=False, kmax=0, passes=0):
     """Algorithm 3.  Returns (rank, kprime, sigma(B) descending)."""
     q1 = _f64(q1, op.m)
     mn = min(op.m, op.n)
@@ -241,7 +253,7 @@ def numrank(op: Operator, q1, eps=1e-8, relative=True, literal=False, kmax=0, pa
     return r.value, info.kprime, sig[: info.kprime].copy()
 
 
-def fsvd(op: Operator, k: int, r: int, q1, route=1, passes=2):
+def fsvd(op: Operator, k: int, r: int, q1, route=1, passes=0):
     """Algorithm 2 (F-SVD).  route 0 = eig(B^T B) + A v / sigma; route 1 = SVD of B."""
     q1 = _f64(q1, op.m)
     U = np.zeros((r, op.m))
@@ -254,7 +266,7 @@ def fsvd(op: Operator, k: int, r: int, q1, route=1, passes=2):
     return U.T.copy(), S, V.T.copy(), info.kprime
 
 
-def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, passes=2, seed=0):
+def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, passes=0, seed=0):
     """Thick-restarted partial SVD.  Returns (U m x k, S k, V n x k, info dict)."""
     q1 = _f64(q1, op.m)
     U = np.zeros((k, op.m))
@@ -271,7 +283,7 @@ def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, 
     return U.T.copy(), S, V.T.copy(), d
 
 
-def gk_upper(op: Operator, K: int, q1, passes=2, seed=0):
+def gk_upper(op: Operator, K: int, q1, passes=0, seed=0):
     """One restart-free upper-bidiagonal cycle: (alpha[K], beta[K], U m x K, V n x (K+1))."""
     q1 = _f64(q1, op.m)
     alpha = np.zeros(K)

@@ -197,12 +197,35 @@ static void cgs_pass(double *w, const double *Qb, int64_t len, int64_t ld, int j
   }
 }
 
+static double norm2sq(const double *w, int64_t len)
+{
+  double s = 0.0;
+  for (int64_t i = 0; i < len; ++i) s += w[i] * w[i];
+  return s;
+}
+
+/* passes = 1 or 2: that many classical Gram-Schmidt passes.  passes = 0: one
+ * pass, then a second only if the first left less than 1/sqrt(2) of the norm
+ * (||w1||^2 < ||w0||^2 / 2; Daniel, Gragg, Kaufman and Stewart, Math. Comp.
+ * 1976, the test ARPACK applies after its Gram-Schmidt step). */
 static void cgs(int passes, double *w, const double *Qb, int64_t len, int64_t ld, int j)
 {
   if (j <= 0) return;
   double *h = (double *)malloc(sizeof(double) * (size_t)j);
-  for (int p = 0; p < passes; ++p) cgs_pass(w, Qb, len, ld, j, h);
+  if (passes == 0) {
+    const double n0 = norm2sq(w, len);
+    cgs_pass(w, Qb, len, ld, j, h);
+    if (norm2sq(w, len) < 0.5 * n0) cgs_pass(w, Qb, len, ld, j, h);
+  } else {
+    for (int p = 0; p < passes; ++p) cgs_pass(w, Qb, len, ld, j, h);
+  }
   free(h);
+}
+
+/* The Gram-Schmidt step on its own (len x j column-major basis), for the tests. */
+void gko_cgs(int passes, double *w, const double *Q, int64_t len, int64_t ld, int j)
+{
+  cgs(passes, w, Q, len, ld, j);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -419,7 +442,7 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
 {
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
-  if (k < 1 || k > mn || passes < 1) return -1;
+  if (k < 1 || k > mn || passes < 0 || passes > 3) return -1;
   memset(alpha, 0, sizeof(double) * (size_t)(k + 1));
   memset(beta, 0, sizeof(double) * (size_t)(k + 2));
   memset(Q, 0, sizeof(double) * (size_t)(m * (k + 1)));
@@ -777,7 +800,7 @@ int gko_psvd(const gko_op *A, int k, int K, int keep, double tol, int max_restar
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
   memset(info, 0, sizeof(*info));
-  if (k < 1 || k > mn || K < k || K > mn || passes < 1) return -1;
+  if (k < 1 || k > mn || K < k || K > mn || passes < 0 || passes > 3) return -1;
   if (K == k && K < mn) return -1; /* a restart needs room beyond the k wanted vectors */
   if (keep <= 0) keep = k + (K - k) / 2;
   if (keep < k) keep = k;

@@ -68,11 +68,16 @@ typedef struct {
 
 /* Inputs: A, k (iterations, 1 <= k <= min(m,n)), eps and eps_relative (the
  * break threshold is eps*sigma_est if eps_relative != 0, else eps), passes (1 =
- * one classical Gram-Schmidt pass as printed in the paper, 2 = two passes),
+ * one classical Gram-Schmidt pass as printed in the paper, 2 = two passes,
+ * 0 = a second pass only when the first left less than 1/sqrt(2) of the norm),
  * q1 (m start values, not necessarily normalized).
  * Outputs: alpha[k+1], beta[k+2] (beta[0] = ||q1||, beta[i] = beta_{i+1} of the
  * paper's 1-based notation is stored at index i), Q (m x (k+1), column-major),
  * P (n x (k+1), column-major).  Entries past k' are left zero. */
+/* Classical Gram-Schmidt of w (len) against the j columns of Q (column-major,
+ * leading dimension ld) with the pass rule of gko_gk_lower's `passes`. */
+void gko_cgs(int passes, double *w, const double *Q, int64_t len, int64_t ld, int j);
+
 int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passes,
                  const double *q1, double *alpha, double *beta, double *Q, double *P,
                  gko_gk_info *info);

@@ -97,7 +97,7 @@ gk_opts defaults() {
   o.krylov_dim = 0;
   o.keep = 0;
   o.max_restarts = 200;
-  o.reorth_passes = 2;
+  o.reorth_passes = 0;
   o.eps_absolute = 0;
   o.flags = 0;
   o.seed = 2104107ull;
@@ -381,7 +381,7 @@ size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const Op
   const int64_t gp = gemvt_partials(*op, d);
   if (gp > pcount) pcount = gp;
   b->part = cv.take<double>(pcount);
-  b->h = cv.take<double>(K + 2);
+  b->h = cv.take<double>(2 * (size_t)K + 4);  // two passes' coefficients and norms (adaptive rule)
   b->alpha = cv.take<double>(K + 2);
   b->beta = cv.take<double>(K + 2);
   b->Bm = cv.take<double>((size_t)K * K);
@@ -422,7 +422,7 @@ int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
   if (keep < k) keep = k;
   if (keep >= K) keep = K - 1;
   if (keep < 0) keep = 0;
-  if (o.reorth_passes < 1 || o.reorth_passes > 3) return GK_INVALID_ARG;
+  if (o.reorth_passes < 0 || o.reorth_passes > 3) return GK_INVALID_ARG;
   if (o.max_restarts < 0) return GK_INVALID_ARG;
   p->m = A->m;
   p->n = A->n;
@@ -687,7 +687,7 @@ size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpSt
   const int64_t gp = gemvt_partials(*op, d);
   if (gp > pcount) pcount = gp;
   b->part = cv.take<double>(pcount);
-  b->h = cv.take<double>(kmax + 2);
+  b->h = cv.take<double>(2 * (size_t)kmax + 4);  // two passes' coefficients and norms (adaptive rule)
   b->alpha = cv.take<double>(kmax + 2);
   b->beta = cv.take<double>(kmax + 2);
   b->sig = host_sigma ? cv.take<double>(kmax + 1) : nullptr;
@@ -720,7 +720,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   if (rc) return rc;
   if (!rank || !(eps >= 0.0) || !isfinite(eps)) return GK_INVALID_ARG;
   const gk_opts o = oin ? *oin : defaults();
-  if (o.reorth_passes < 1 || o.reorth_passes > 3) return GK_INVALID_ARG;
+  if (o.reorth_passes < 0 || o.reorth_passes > 3) return GK_INVALID_ARG;
   const int64_t kmax = clamp_kmax(Ain, kmax_in);
   cudaStream_t s = (cudaStream_t)o.stream;
   OpStage st;

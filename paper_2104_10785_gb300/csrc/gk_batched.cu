@@ -585,10 +585,35 @@ __device__ void reduce_matvec_t(cg::cluster_group &cl, const BProb &P, Shm &S, i
 
 // classical Gram-Schmidt of the slice [s0, s1) of vec against j columns of Qb,
 // `passes` times, then the norm (the same value in every CTA)
+// sum over the cluster of the squares of vec[s0, s1) (the same value in every CTA)
+__device__ double cl_norm2(cg::cluster_group &cl, Shm &S, const double *vec, int64_t s0, int64_t s1, int slot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double s = 0.0;
+  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) s = fma(vec[r], vec[r], s);
+  s = dev::warp_sum_d(s);
+  __shared__ double wred[32];
+  if (lane == 0) wred[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += wred[i];
+    S.red[slot] = t;
+  }
+  __syncthreads();
+  return 0.0;
+}
+
+// classical Gram-Schmidt of the slice [s0, s1) of vec against j columns of Qb, then the
+// norm (the same value in every CTA).  passes >= 1: that many passes; passes = 0: one pass,
+// a second only if the first left less than 1/sqrt(2) of the norm (Daniel-Gragg-Kaufman-
+// Stewart); the norm before the first pass rides in the first pass's all-reduce.
 __device__ double cl_cgs_norm(cg::cluster_group &cl, Shm &S, double *vec, int64_t s0, int64_t s1, const double *Qb,
                               int64_t ldq, int j, int passes) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p = 0; p < passes && j > 0; ++p) {
+  const bool adaptive = passes == 0;
+  const int maxp = adaptive ? 2 : passes;
+  double n0 = 0.0;
+  for (int p = 0; p < maxp && j > 0; ++p) {
     for (int c = warp; c < j; c += nw) {
       const double *q = Qb + (int64_t)c * ldq;
       double s0a = 0.0, s1a = 0.0, s2a = 0.0, s3a = 0.0;
@@ -603,25 +628,24 @@ __device__ double cl_cgs_norm(cg::cluster_group &cl, Shm &S, double *vec, int64_
       double s = dev::warp_sum_d((s0a + s1a) + (s2a + s3a));
       if (lane == 0) S.red[c] = s;
     }
-    cl_allreduce(cl, S, j);
+    const bool first_adaptive = adaptive && p == 0;
+    if (first_adaptive) cl_norm2(cl, S, vec, s0, s1, j);
+    cl_allreduce(cl, S, j + (first_adaptive ? 1 : 0));
+    if (first_adaptive) n0 = S.hv[j];
     for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) {
       double acc = vec[r];
       for (int c = 0; c < j; ++c) acc = fma(-Qb[(int64_t)c * ldq + r], S.hv[c], acc);
       vec[r] = acc;
     }
     __syncthreads();
+    if (first_adaptive) {
+      cl_norm2(cl, S, vec, s0, s1, 0);
+      cl_allreduce(cl, S, 1);
+      const double n1 = S.hv[0];
+      if (n1 >= 0.5 * n0) return sqrt(n1);  // no cancellation: one pass is enough
+    }
   }
-  double s = 0.0;
-  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) s = fma(vec[r], vec[r], s);
-  s = dev::warp_sum_d(s);
-  __shared__ double wred[32];
-  if (lane == 0) wred[warp] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < nw; ++i) t += wred[i];
-    S.red[0] = t;
-  }
+  cl_norm2(cl, S, vec, s0, s1, 0);
   cl_allreduce(cl, S, 1);
   return sqrt(S.hv[0]);
 }
@@ -1292,7 +1316,7 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
     o = *oin;
   else
     gk_default_opts(&o);
-  if (o.reorth_passes < 1 || o.reorth_passes > 3 || o.max_restarts < 0) return GK_INVALID_ARG;
+  if (o.reorth_passes < 0 || o.reorth_passes > 3 || o.max_restarts < 0) return GK_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)o.stream;
   const int dtype_all = items[0].A.dtype;
   for (int i = 0; i < count; ++i)

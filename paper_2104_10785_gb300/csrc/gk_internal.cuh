@@ -52,6 +52,7 @@ struct Ctl {
   double eps;        // Algorithm 1 threshold parameter
   int eps_rel;       // 1: threshold eps * sest; 0: eps
   int timeout;       // a bounded device wait gave up (the kernel recorded where: 1 full, 2 empty barrier)
+  int pass2;         // adaptive Gram-Schmidt: the first pass cancelled, the second pass runs
 };
 
 // device view of the operator
@@ -132,8 +133,9 @@ cudaError_t matvec_t(const Op &A, const float *x32, const double *x64, double *y
                      const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d);
 
 // ---- Gram-Schmidt and vector kernels (gk_orth.cu) -------------------------
-// One or two classical Gram-Schmidt passes of w (len) against the first j
-// columns of Q (ld), followed by the norm and its judgement; see NormMode.
+// Classical Gram-Schmidt of w (len) against the first j columns of Q (ld):
+// passes = 1..3 passes, or 0 = one pass and a second only if the first left less
+// than 1/sqrt(2) of the norm; then the norm and its judgement; see NormMode.
 // coef_out receives the accepted norm (0 on breakdown); prev is the previous
 // recurrence coefficient (for the sigma_est update of Algorithm 1).
 cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,

@@ -7,6 +7,12 @@
 //   pass p < passes-1 : h = Q^T w                  (k_cgs_dot, partials per row chunk)
 //                        w -= Q h ; h' = Q^T w      (k_cgs_update_dot)
 //   last pass         : w -= Q h ; ||w||^2         (k_cgs_update_norm)
+// passes = 0 (adaptive): h = Q^T w and ||w||^2 (k_cgs_dot), then w -= Q h and
+// ||w||^2 (k_cgs_update_norm, first stage): if the first pass left at least
+// 1/sqrt(2) of the norm (the Daniel-Gragg-Kaufman-Stewart test) its last block
+// applies the judgement and the second pass's three kernels, launched anyway,
+// return at entry (ctl->pass2 = 0); otherwise they run.  Without cancellation the
+// basis is read twice.
 // Partial sums are written per row chunk and reduced in a fixed order, so the
 // results are bitwise reproducible.  The last block of the norm kernel applies
 // the break / breakdown test and records the event in the control block; every
@@ -45,22 +51,43 @@ __device__ __forceinline__ void chunk_dots(const double *__restrict__ Q, int64_t
   }
 }
 
+// part[j * G + g] = sum over chunk g of ws .* ws (fixed-order tree)
+__device__ __forceinline__ void chunk_norm2(int64_t i0, int64_t i1, const double *ws, double *__restrict__ part, int j,
+                                            int G) {
+  __shared__ double red[kThreads / 32];
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(ws[i - i0], ws[i - i0], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[(int64_t)j * G + blockIdx.x] = t;
+  }
+}
+
+__device__ __forceinline__ bool pass2_off(const Ctl *ctl) {
+  return *reinterpret_cast<const volatile int *>(&ctl->pass2) == 0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_cgs_dot(const double *__restrict__ Q, int64_t ld, int64_t len, int j,
                                                       const double *__restrict__ w, double *__restrict__ part, int S,
-                                                      const Ctl *ctl) {
-  if (halted(ctl)) return;
+                                                      const Ctl *ctl, int with_norm, int gated) {
+  if (halted(ctl) || (gated && pass2_off(ctl))) return;
   __shared__ double ws[kMaxChunk];
   const int64_t i0 = (int64_t)blockIdx.x * S;
   const int64_t i1 = (i0 + S < len) ? i0 + S : len;
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) ws[i - i0] = w[i];
   __syncthreads();
   chunk_dots(Q, ld, i0, i1, j, ws, part, gridDim.x);
+  if (with_norm) chunk_norm2(i0, i1, ws, part, j, gridDim.x);
 }
 
 // h[c] = sum_g part[c * G + g]  (one block per column, fixed-order tree)
 __global__ void __launch_bounds__(128) k_reduce_cols(const double *__restrict__ part, int G, double *__restrict__ h,
-                                                     const Ctl *ctl) {
-  if (halted(ctl)) return;
+                                                     const Ctl *ctl, int gated) {
+  if (halted(ctl) || (gated && pass2_off(ctl))) return;
   __shared__ double red[128];
   const int c = blockIdx.x;
   double s = 0.0;
@@ -172,12 +199,16 @@ __device__ void judge(Ctl *ctl, double nrm2, const NormArgs a) {
   if (a.coef_out) *a.coef_out = nrm;
 }
 
+// stage 0: the last (or only) pass, judged.  Stage 1: the adaptive rule's first pass; h[j]
+// holds ||w||^2 before it: the last block judges and clears ctl->pass2 if the norm kept at
+// least half of its square, else sets it.  Stage 2: the adaptive second pass (returns at
+// entry unless ctl->pass2).
 __global__ void __launch_bounds__(kThreads) k_cgs_update_norm(const double *__restrict__ Q, int64_t ld, int64_t len,
                                                               int j, double *__restrict__ w,
                                                               const double *__restrict__ h,
                                                               double *__restrict__ npart, int S, Ctl *ctl,
-                                                              NormArgs a) {
-  if (halted(ctl)) return;
+                                                              NormArgs a, int stage) {
+  if (halted(ctl) || (stage == 2 && pass2_off(ctl))) return;
   extern __shared__ double dyn[];
   double *hs = dyn;      // j
   double *ws = dyn + j;  // S
@@ -221,7 +252,12 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_norm(const double *__re
     double tot = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
     ctl->cnt[0] = 0u;
-    judge(ctl, tot, a);
+    if (stage == 1 && tot < 0.5 * h[j]) {
+      ctl->pass2 = 1;  // cancellation: the second pass decides
+    } else {
+      if (stage == 1) ctl->pass2 = 0;
+      judge(ctl, tot, a);
+    }
   }
 }
 
@@ -311,6 +347,7 @@ __global__ void k_reset_ctl(Ctl *ctl, double eps, int eps_rel) {
     ctl->eps = eps;
     ctl->eps_rel = eps_rel;
     ctl->timeout = 0;
+    ctl->pass2 = 0;
   }
 }
 
@@ -348,17 +385,27 @@ cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, 
     if (e != cudaSuccess) return e;
   }
   NormArgs a{mode, step, side, coef_out, prev};
-  if (j <= 0 || passes <= 0) {
-    GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, 0, w, h, npart, S, ctl, a));
+  if (j <= 0 || passes < 0) {
+    GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, 0, w, h, npart, S, ctl, a, 0));
     return cudaGetLastError();
   }
-  GK_LAUNCH(k_cgs_dot<<<G, kThreads, 0, s>>>(Q, ld, len, j, w, part, S, ctl));
-  GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl));
+  if (passes == 0) {  // adaptive; part holds j + 1 columns (the last one ||w||^2), npart follows them
+    double *np2 = part + (int64_t)G * (j + 1);
+    GK_LAUNCH(k_cgs_dot<<<G, kThreads, 0, s>>>(Q, ld, len, j, w, part, S, ctl, 1, 0));
+    GK_LAUNCH(k_reduce_cols<<<j + 1, 128, 0, s>>>(part, G, h, ctl, 0));
+    GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, np2, S, ctl, a, 1));
+    GK_LAUNCH(k_cgs_dot<<<G, kThreads, 0, s>>>(Q, ld, len, j, w, part, S, ctl, 0, 1));
+    GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl, 1));
+    GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, np2, S, ctl, a, 2));
+    return cudaGetLastError();
+  }
+  GK_LAUNCH(k_cgs_dot<<<G, kThreads, 0, s>>>(Q, ld, len, j, w, part, S, ctl, 0, 0));
+  GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl, 0));
   for (int p = 1; p < passes; ++p) {
     GK_LAUNCH(k_cgs_update_dot<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, part, S, ctl));
-    GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl));
+    GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, G, h, ctl, 0));
   }
-  GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, npart, S, ctl, a));
+  GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, npart, S, ctl, a, 0));
   return cudaGetLastError();
 }
 

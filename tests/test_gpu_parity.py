@@ -211,6 +211,11 @@ def _compare_psvd(op, At, A64, k, K, tol, q1, s_rtol, v_tol, res_tol, **kw):
     return U, S, V, info
 
 
+def rank_product(m, n, r, seed):
+    g = synth.rng(seed)
+    return g.standard_normal((m, r)) @ g.standard_normal((r, n)) + 1e-12 * g.standard_normal((m, n))
+
+
 def test_psvd_dense_f64_2000x1000_prescribed_spectrum():
     """Dense f64 2000 x 1000, sigma_i = 0.9^i, top 10, Krylov dimension 30, tol 1e-10."""
     w = synth.WORKLOADS["dense_f64_2000x1000_top10"]
@@ -221,6 +226,29 @@ def test_psvd_dense_f64_2000x1000_prescribed_spectrum():
     U, S, V, info = _compare_psvd(op, At, A, w["k"], w["K"], w["tol"], q1, s_rtol=1e-10, v_tol=1e-8, res_tol=1e-10)
     np.testing.assert_allclose(S, sig[: w["k"]], rtol=1e-10)
     assert angle_err(V, V0[:, : w["k"]]) <= 1e-8
+
+
+@pytest.mark.parametrize("passes", [0, 1, 2])
+def test_reorthogonalization_modes_match_oracle(passes):
+    """Each Gram-Schmidt rule (0 = second pass only under cancellation, 1 = one pass as printed,
+    2 = two passes) on both sides: the partial SVD and the rank agree with the oracle's."""
+    sig = synth.sigma_geometric(350, 0.9)
+    A, _, _ = synth.prescribed_spectrum(800, 350, sig, seed=31)
+    q1 = synth.start_vector(800, 31)
+    M = gk()
+    At, qt = torch.from_numpy(A).cuda(), torch.from_numpy(q1).cuda()
+    U, S, V, st, info = M.gk_psvd(At, 8, 1e-10, krylov_dim=24, reorth_passes=passes, start=qt)
+    op = oracle.Operator.dense(A)
+    Uo, So, Vo, io = oracle.psvd(op, 8, 24, q1, tol=1e-10, passes=passes, max_restarts=300)
+    assert st == 0
+    np.testing.assert_allclose(S.cpu().numpy(), So, rtol=1e-10)
+    assert abs(info["restarts"] - io["restarts"]) <= 1
+    G = rank_product(800, 300, 40, 33)
+    r, sig_g, st2, _ = M.gk_numrank(torch.from_numpy(G).cuda(), 1e-8, 200, reorth_passes=passes,
+                                    start=torch.from_numpy(synth.start_vector(800, 2)).cuda(), want_sigma=True)
+    r_o, kp_o, s_o = oracle.numrank(oracle.Operator.dense(G), synth.start_vector(800, 2), eps=1e-8, kmax=200,
+                                    passes=passes)
+    assert r == r_o == 40
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])

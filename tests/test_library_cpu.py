@@ -52,7 +52,7 @@ def test_status_strings_and_defaults():
     assert gk.status_string(0) == "GK_OK"
     assert gk.status_string(-7) == "GK_NO_DEVICE"
     o = raw.default_opts()
-    assert o.reorth_passes == 2 and o.max_restarts == 200 and o.krylov_dim == 0
+    assert o.reorth_passes == 0 and o.max_restarts == 200 and o.krylov_dim == 0
     assert "sm_103a" in gk.version()
 
 

@@ -175,7 +175,8 @@ def _lower_B(d):
     return B
 
 
-@pytest.mark.parametrize("shape,passes", [((120, 80), 2), ((80, 120), 2), ((150, 150), 1)])
+@pytest.mark.parametrize("shape,passes", [((120, 80), 2), ((80, 120), 2), ((150, 150), 1), ((120, 80), 0),
+                                          ((80, 120), 0)])
 def test_alg1_bidiagonal_relations(shape, passes):
     """Eq. 2.4: A P_k = Q_{k+1} B_{k+1,k};  A^T Q_{k+1} = P_k B^T + alpha_{k+1} p_{k+1} e_{k+1}^T;
     Eq. pq_ortho: Q^T Q = I, P^T P = I;  alpha_i, beta_i >= 0."""
@@ -192,7 +193,7 @@ def test_alg1_bidiagonal_relations(shape, passes):
     R = A.T @ Q - P[:, :k] @ B.T
     R[:, k] -= d["alpha"][k] * P[:, k]
     assert np.abs(R).max() < 1e-13 * nA
-    tol_o = 1e-13 if passes == 2 else 1e-10
+    tol_o = 1e-10 if passes == 1 else 1e-13
     assert np.abs(Q.T @ Q - np.eye(k + 1)).max() < tol_o
     assert np.abs(P[:, : k + 1].T @ P[:, : k + 1] - np.eye(k + 1)).max() < tol_o
     assert np.all(d["alpha"][: k + 1] >= 0) and np.all(d["beta"][: k + 2] >= 0)
@@ -200,6 +201,28 @@ def test_alg1_bidiagonal_relations(shape, passes):
     R2 = A.T @ (A @ P[:, :k]) - P[:, :k] @ (B.T @ B)
     R2[:, k - 1] -= d["alpha"][k] * d["beta"][k] * P[:, k]
     assert np.abs(R2).max() < 1e-12 * nA**2
+
+
+def test_adaptive_reorthogonalization_repeats_the_pass_under_cancellation():
+    """The adaptive rule (passes = 0): a vector almost inside span(Q) (w = Q c + 1e-10 z) loses
+    almost all of its norm in the first pass, so the second pass runs and the result is as
+    orthogonal as with two passes, where one pass leaves components ~ eps ||c|| / 1e-10; a vector
+    with no cancellation gets exactly one pass."""
+    rng = _rng(21)
+    m, j = 400, 30
+    Q, _ = np.linalg.qr(rng.standard_normal((m, j)))
+    z = rng.standard_normal(m)
+    z -= Q @ (Q.T @ z)
+    w = Q @ rng.standard_normal(j) + 1e-10 * z
+    res = {}
+    for p in (0, 1, 2):
+        x = oracle.cgs(w, Q, passes=p)
+        res[p] = np.abs(Q.T @ x).max() / np.linalg.norm(x)
+    assert res[0] < 1e-14 and res[2] < 1e-14
+    assert res[1] > 1e3 * res[0]
+    np.testing.assert_array_equal(oracle.cgs(w, Q, passes=0), oracle.cgs(w, Q, passes=2))
+    y = rng.standard_normal(m)  # ||y1|| ~ ||y||: no second pass
+    np.testing.assert_array_equal(oracle.cgs(y, Q, passes=0), oracle.cgs(y, Q, passes=1))
 
 
 def test_alg1_orthogonal_invariance():
