@@ -493,8 +493,109 @@ __device__ bool ring_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, co
   }
 }
 
+// A^T u of the CTA's rows by row-streaming warps: the columns go in panels of 32 lanes x G
+// 16-byte groups (512 f32 or bf16/f16 columns); warp w streams rows r0 + w, r0 + w + 8, ...
+// two at a time (2 G loads of 16 bytes per lane in flight) and accumulates u_r a_r over its
+// rows in f32 runs of 32 rows, combined in f64 per warp in the ring area; after each panel
+// the eight warps' sums are added in warp order into S.zp.  u (f32) is staged in S.xs.
+template <typename T>
+__device__ bool warp_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *u) {
+  if constexpr (std::is_same<T, double>::value) {
+    return false;
+  } else {
+    using VT = Vec<T>;
+    constexpr int E = VT::E;
+    constexpr int G = 16 / E;         // groups per lane and panel: 4 (f32) or 2 (bf16/f16)
+    constexpr int PG = 32 * G;        // groups per panel
+    constexpr int PC = PG * E;        // columns per panel (512)
+    const T *A = (const T *)P.A;
+    if (((uintptr_t)A & 15) || ((P.ld * (int64_t)sizeof(T)) & 15) || r1 - r0 > kNMax) return false;
+    static_assert(8 * PC * sizeof(double) <= (size_t)kRingStages * kRingStage, "panel sums fit the ring area");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t n = P.n, nv = n / E;
+    const int64_t ldv = P.ld / E;
+    double *acc = reinterpret_cast<double *>(S.ring) + (size_t)warp * PC;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) S.xs[r - r0] = (float)u[r];
+    __syncthreads();
+    for (int64_t g0 = 0; g0 < nv; g0 += PG) {
+      for (int c = lane; c < PC; c += 32) acc[c] = 0.0;
+      float a32[G][E];
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+#pragma unroll
+        for (int e = 0; e < E; ++e) a32[q][e] = 0.f;
+      int run = 0;
+      auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            acc[(lane + 32 * q) * E + e] += (double)a32[q][e];
+            a32[q][e] = 0.f;
+          }
+      };
+      const typename VT::V *base = reinterpret_cast<const typename VT::V *>(A) + g0 + lane;
+      for (int64_t r = r0 + warp; r < r1; r += 2 * nw) {
+        const bool two = r + nw < r1;
+        typename VT::V b0[G] = {}, b1[G] = {};
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          if (g0 + lane + 32 * q < nv) {
+            b0[q] = __ldcs(base + r * ldv + 32 * q);
+            if (two) b1[q] = __ldcs(base + (r + nw) * ldv + 32 * q);
+          }
+        }
+        const float u0 = S.xs[r - r0], u1 = two ? S.xs[r + nw - r0] : 0.f;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          float f0[E], f1[E];
+          VT::unpack(b0[q], f0);
+          VT::unpack(b1[q], f1);
+#pragma unroll
+          for (int e = 0; e < E; ++e) a32[q][e] = fmaf(f1[e], u1, fmaf(f0[e], u0, a32[q][e]));
+        }
+        run += 2;
+        if (run >= kRunRows) {
+          flush();
+          run = 0;
+        }
+      }
+      flush();
+      __syncthreads();
+      // the warps' panel sums, added in warp order
+      for (int c = threadIdx.x; c < PC; c += blockDim.x) {
+        const int64_t col = g0 * E + c;
+        if (col >= nv * E) break;
+        const double *a0 = reinterpret_cast<const double *>(S.ring) + c;
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += a0[(size_t)w * PC];
+        S.zp[col] = t;
+      }
+      __syncthreads();
+    }
+    // columns of the partial last group
+    for (int64_t c = nv * E + threadIdx.x; c < n; c += blockDim.x) {
+      double accd = 0.0;
+      float sr = 0.f;
+      int rr = 0;
+      for (int64_t r = r0; r < r1; ++r) {
+        sr = fmaf(load_val<T>(A + r * P.ld + c), S.xs[r - r0], sr);
+        if (++rr == kRunRows) {
+          accd += (double)sr;
+          sr = 0.f;
+          rr = 0;
+        }
+      }
+      S.zp[c] = accd + (double)sr;
+    }
+    __syncthreads();
+    return true;
+  }
+}
+
 template <typename T>
 __device__ void rows_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, const double *u) {
+  if (warp_matvec_t<T>(P, S, r0, r1, u)) return;
   if (ring_matvec_t<T>(P, S, r0, r1, u)) return;
   const T *A = (const T *)P.A;
   const int64_t n = P.n;
