@@ -826,15 +826,17 @@ __device__ void left_product(const BProb &P, Shm &S, int64_t r0, int64_t r1, con
 
 // One-sided Jacobi SVD of the K x K matrix held column-major in shared memory (sB), on
 // the calling CTA alone: the rotations, the tournament ordering and the tolerance of the
-// cluster version, one column pair per 8-lane group (32 pairs per round), block barriers
-// between the rounds.  The skip test compares squares: c^2 <= tol^2 a b.  sY receives the accumulated
+// cluster version.  Each round: the pairs' sums by 8-lane groups, the rotations by one
+// lane per pair (so each pair's f64 divisions and square roots run once, not on eight
+// lanes), then the updates by 8-lane groups; block barriers between the phases.  rot:
+// 4 doubles per pair in shared memory.  The skip test compares squares: c^2 <= tol^2 a b.  sY receives the accumulated
 // rotations; outputs sigma (descending), X (normalized columns of the rotated B) and Y
 // (rotations) in global memory, ordered by sigma.  Returns the sweeps (negative if the
 // sweep limit was reached).
 constexpr int kCtaJacobiMax = 78;  // K with 8 K^2 bytes within each of the two shared regions
 
 __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
-                          int *s_rot) {
+                          int *s_rot, double *rot) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int grp = lane >> 3, gl = lane & 7;
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) sY[idx] = ((idx % K) == (idx / K)) ? 1.0 : 0.0;
@@ -846,7 +848,7 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
     if (threadIdx.x == 0) *s_rot = 0;
     __syncthreads();
     for (int r = 0; r < Kp - 1; ++r) {
-      // one pair per 8-lane group: 4 pairs per warp, 32 per round on 8 warps
+      // (1) one pair per 8-lane group: its three sums a = |b_p|^2, b = |b_q|^2, c = b_p . b_q
       for (int pb = warp * 4; pb < Kp / 2; pb += nw * 4) {
         const int pi = pb + grp;
         int p = 0, q = K;
@@ -860,7 +862,7 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
           }
         }
         const bool live = q < K;
-        double *bp = sB + p * K, *bq = sB + (live ? q : p) * K;
+        const double *bp = sB + p * K, *bq = sB + (live ? q : p) * K;
         double a = 0.0, b = 0.0, c = 0.0;
         if (live)
           for (int i = gl; i < K; i += 8) {
@@ -875,25 +877,54 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
           b += __shfl_xor_sync(0xffffffffu, b, o);
           c += __shfl_xor_sync(0xffffffffu, c, o);
         }
-        if (live && !(c == 0.0 || c * c <= tol * tol * a * b)) {
-          if (gl == 0) *s_rot = 1;
-          const double zeta = (b - a) / (2.0 * c);
-          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
-                                              : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          for (int i = gl; i < K; i += 8) {
-            const double x = bp[i], y = bq[i];
-            bp[i] = cs * x - sn * y;
-            bq[i] = sn * x + cs * y;
-          }
-          double *yp = sY + p * K, *yq = sY + q * K;
-          for (int i = gl; i < K; i += 8) {
-            const double x = yp[i], y = yq[i];
-            yp[i] = cs * x - sn * y;
-            yq[i] = sn * x + cs * y;
-          }
+        if (gl == 0 && pi < Kp / 2) {
+          rot[4 * pi] = a;
+          rot[4 * pi + 1] = b;
+          rot[4 * pi + 2] = live ? c : 0.0;
         }
-        __syncwarp();  // the groups of this warp meet before the next shuffles
+      }
+      __syncthreads();
+      // (2) the rotations, one lane per pair (the f64 divisions and roots once per pair)
+      if (warp == 0)
+        for (int pi = lane; pi < Kp / 2; pi += 32) {
+          const double a = rot[4 * pi], b = rot[4 * pi + 1], c = rot[4 * pi + 2];
+          double cs = 1.0, sn = 0.0;
+          if (!(c == 0.0 || c * c <= tol * tol * a * b)) {
+            *s_rot = 1;
+            const double zeta = (b - a) / (2.0 * c);
+            const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                                : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            cs = 1.0 / sqrt(1.0 + t * t);
+            sn = cs * t;
+          }
+          rot[4 * pi] = cs;
+          rot[4 * pi + 1] = sn;
+          rot[4 * pi + 3] = (cs == 1.0 && sn == 0.0) ? 0.0 : 1.0;
+        }
+      __syncthreads();
+      // (3) apply them, one pair per 8-lane group
+      for (int pb = warp * 4; pb < Kp / 2; pb += nw * 4) {
+        const int pi = pb + grp;
+        if (pi >= Kp / 2 || rot[4 * pi + 3] == 0.0) continue;
+        int p = dev::player(r, pi, Kp), q = dev::player(r, Kp - 1 - pi, Kp);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        const double cs = rot[4 * pi], sn = rot[4 * pi + 1];
+        double *bp = sB + p * K, *bq = sB + q * K;
+        for (int i = gl; i < K; i += 8) {
+          const double x = bp[i], y = bq[i];
+          bp[i] = cs * x - sn * y;
+          bq[i] = sn * x + cs * y;
+        }
+        double *yp = sY + p * K, *yq = sY + q * K;
+        for (int i = gl; i < K; i += 8) {
+          const double x = yp[i], y = yq[i];
+          yp[i] = cs * x - sn * y;
+          yq[i] = sn * x + cs * y;
+        }
       }
       __syncthreads();
     }
@@ -1047,7 +1078,7 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
       int sw = 0;
       if (rank == 0) {
         __syncthreads();
-        sw = cta_jacobi(sB, sYw, K, W.sigma, W.X, W.Y, S.red, S.redi, S.s_rot);
+        sw = cta_jacobi(sB, sYw, K, W.sigma, W.X, W.Y, S.red, S.redi, S.s_rot, S.hv);
       }
       cl.sync();  // sigma, X, Y visible to every CTA
       res.sweeps = sw;
