@@ -835,16 +835,16 @@ __device__ void left_product(const BProb &P, Shm &S, int64_t r0, int64_t r1, con
 // sweep limit was reached).
 constexpr int kCtaJacobiMax = 78;  // K with 8 K^2 bytes within each of the two shared regions
 
-__device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
-                          int *s_rot, double *rot) {
+// One-sided Jacobi sweeps (tournament ordering) on the K x K column-major sB with the
+// rotations accumulated into sY.  A pair rotates unless c^2 <= tol^2 a b, or unless one of its
+// columns has a squared norm at most `floor` (left to a later, more precise stage).
+template <typename R>
+__device__ int cta_sweeps(R *sB, R *sY, int K, R tol, R floor, int max_sweeps, R *rot, int *s_rot) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int grp = lane >> 3, gl = lane & 7;
-  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) sY[idx] = ((idx % K) == (idx / K)) ? 1.0 : 0.0;
   const int Kp = K + (K & 1);
-  const double tol = fmax(2.0 * sqrt((double)K) * 0x1.0p-52, (double)K * 0x1.0p-53);
-  int sweep, done = 0;
-  __syncthreads();
-  for (sweep = 1; sweep <= 80; ++sweep) {
+  int sweep;
+  for (sweep = 1; sweep <= max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *s_rot = 0;
     __syncthreads();
     for (int r = 0; r < Kp - 1; ++r) {
@@ -862,11 +862,11 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
           }
         }
         const bool live = q < K;
-        const double *bp = sB + p * K, *bq = sB + (live ? q : p) * K;
-        double a = 0.0, b = 0.0, c = 0.0;
+        const R *bp = sB + p * K, *bq = sB + (live ? q : p) * K;
+        R a = 0, b = 0, c = 0;
         if (live)
           for (int i = gl; i < K; i += 8) {
-            const double x = bp[i], y = bq[i];
+            const R x = bp[i], y = bq[i];
             a = fma(x, x, a);
             b = fma(y, y, b);
             c = fma(x, y, c);
@@ -880,48 +880,48 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
         if (gl == 0 && pi < Kp / 2) {
           rot[4 * pi] = a;
           rot[4 * pi + 1] = b;
-          rot[4 * pi + 2] = live ? c : 0.0;
+          rot[4 * pi + 2] = live ? c : R(0);
         }
       }
       __syncthreads();
-      // (2) the rotations, one lane per pair (the f64 divisions and roots once per pair)
+      // (2) the rotations, one lane per pair (the divisions and roots once per pair)
       if (warp == 0)
         for (int pi = lane; pi < Kp / 2; pi += 32) {
-          const double a = rot[4 * pi], b = rot[4 * pi + 1], c = rot[4 * pi + 2];
-          double cs = 1.0, sn = 0.0;
-          if (!(c == 0.0 || c * c <= tol * tol * a * b)) {
+          const R a = rot[4 * pi], b = rot[4 * pi + 1], c = rot[4 * pi + 2];
+          R cs = 1, sn = 0;
+          if (!(c == R(0) || c * c <= tol * tol * a * b || a <= floor || b <= floor)) {
             *s_rot = 1;
-            const double zeta = (b - a) / (2.0 * c);
-            const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
-                                                : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            cs = 1.0 / sqrt(1.0 + t * t);
+            const R zeta = (b - a) / (R(2) * c);
+            const R t = fabs(zeta) > R(1e30) ? R(0.5) / zeta
+                                              : (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+            cs = R(1) / sqrt(R(1) + t * t);
             sn = cs * t;
           }
           rot[4 * pi] = cs;
           rot[4 * pi + 1] = sn;
-          rot[4 * pi + 3] = (cs == 1.0 && sn == 0.0) ? 0.0 : 1.0;
+          rot[4 * pi + 3] = (cs == R(1) && sn == R(0)) ? R(0) : R(1);
         }
       __syncthreads();
       // (3) apply them, one pair per 8-lane group
       for (int pb = warp * 4; pb < Kp / 2; pb += nw * 4) {
         const int pi = pb + grp;
-        if (pi >= Kp / 2 || rot[4 * pi + 3] == 0.0) continue;
+        if (pi >= Kp / 2 || rot[4 * pi + 3] == R(0)) continue;
         int p = dev::player(r, pi, Kp), q = dev::player(r, Kp - 1 - pi, Kp);
         if (p > q) {
           const int t = p;
           p = q;
           q = t;
         }
-        const double cs = rot[4 * pi], sn = rot[4 * pi + 1];
-        double *bp = sB + p * K, *bq = sB + q * K;
+        const R cs = rot[4 * pi], sn = rot[4 * pi + 1];
+        R *bp = sB + p * K, *bq = sB + q * K;
         for (int i = gl; i < K; i += 8) {
-          const double x = bp[i], y = bq[i];
+          const R x = bp[i], y = bq[i];
           bp[i] = cs * x - sn * y;
           bq[i] = sn * x + cs * y;
         }
-        double *yp = sY + p * K, *yq = sY + q * K;
+        R *yp = sY + p * K, *yq = sY + q * K;
         for (int i = gl; i < K; i += 8) {
-          const double x = yp[i], y = yq[i];
+          const R x = yp[i], y = yq[i];
           yp[i] = cs * x - sn * y;
           yq[i] = sn * x + cs * y;
         }
@@ -930,11 +930,108 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
     }
     const int any = *s_rot;
     __syncthreads();  // every thread has read the flag before it is cleared
-    if (!any) {
-      done = 1;
-      break;
-    }
+    if (!any) return sweep;
   }
+  return -(sweep - 1);
+}
+
+// the projected matrix's entry (i, c): kept Ritz values sigma_i and the coupling rho_i in
+// column l for the first l rows, alpha_i on and beta_i above the diagonal below them
+struct ProjB {
+  const double *sigma, *rho, *alpha, *beta;
+  int l, K;
+  __device__ __forceinline__ double entry(int i, int c) const {
+    if (i < l) return c == i ? __ldcg(sigma + i) : (c == l ? __ldcg(rho + i) : 0.0);
+    return c == i ? __ldcg(alpha + i) : (c == i + 1 ? __ldcg(beta + i) : 0.0);
+  }
+  // (B Q)(i, c) for column-major Q: B has at most two entries per row
+  __device__ __forceinline__ double times(const double *Q, int i, int c) const {
+    const double *q = Q + (int64_t)c * K;
+    if (i < l) return __ldcg(sigma + i) * q[i] + __ldcg(rho + i) * q[l];
+    double v = __ldcg(alpha + i) * q[i];
+    if (i + 1 < K) v += __ldcg(beta + i) * q[i + 1];
+    return v;
+  }
+};
+
+// SVD of the projected K x K matrix on the calling CTA alone, in shared memory (K <= 78):
+// (1) one-sided Jacobi sweeps in f32 on B / max|B| until its columns are orthogonal to
+// about 1e-5 (f32 work, 64x the FP64 rate); (2) the accumulated f32 rotations, made
+// orthonormal in f64 by two Gram-Schmidt passes per column, give Q; (3) f64 one-sided
+// Jacobi on B Q (formed directly from B's two entries per row) with Q as the starting
+// rotation, to the tolerance of the cluster version; a few sweeps remain.  B V = U S with
+// V = Q J exactly orthogonal in f64, so the outputs are those of a plain f64 Jacobi SVD:
+// sigma descending, X the normalized columns of the rotated matrix, Y the rotations.
+__device__ int cta_svd(double *sB, double *sY, const ProjB &Bp, double *sigma, double *X, double *Y, double *nrm,
+                       int *pos, int *s_rot, double *rot) {
+  const int K = Bp.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float *Bf = reinterpret_cast<float *>(sB), *Yf = Bf + K * K;
+  // (1) f32 sweeps on the scaled matrix
+  __shared__ double s_max;
+  if (threadIdx.x == 0) s_max = 0.0;
+  __syncthreads();
+  double mloc = 0.0;
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) mloc = fmax(mloc, fabs(Bp.entry(idx % K, idx / K)));
+  mloc = dev::warp_max_d(mloc);
+  if (lane == 0) atomicMax(reinterpret_cast<unsigned long long *>(&s_max), (unsigned long long)__double_as_longlong(mloc));
+  __syncthreads();
+  const double inv = s_max > 0.0 ? 1.0 / s_max : 1.0;
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+    Bf[idx] = (float)(Bp.entry(idx % K, idx / K) * inv);
+    Yf[idx] = ((idx % K) == (idx / K)) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  // columns below 1e-10 of the Frobenius norm squared carry f32 rounding more than their
+  // own direction: their rotations wait for the f64 stage
+  double fro = 0.0;
+  if (warp == 0) {
+    for (int idx = lane; idx < K * K; idx += 32) fro = fma((double)Bf[idx], (double)Bf[idx], fro);
+    fro = dev::warp_sum_d(fro);
+    if (lane == 0) rot[0] = fro;
+  }
+  __syncthreads();
+  const float floor32 = (float)(1e-10 * rot[0]);
+  __syncthreads();
+  const int sw32 = cta_sweeps<float>(Bf, Yf, K, 1e-5f, floor32, 40, reinterpret_cast<float *>(rot), s_rot);
+  // (2) Q = Yf made orthonormal in f64, column by column (two passes each)
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) sY[idx] = (double)Yf[idx];
+  __syncthreads();
+  for (int c = 0; c < K; ++c) {
+    double *qc = sY + (int64_t)c * K;
+    for (int pass = 0; pass < 2 && c > 0; ++pass) {
+      for (int k = warp; k < c; k += nw) {
+        const double *qk = sY + (int64_t)k * K;
+        double d = 0.0;
+        for (int i = lane; i < K; i += 32) d = fma(qk[i], qc[i], d);
+        d = dev::warp_sum_d(d);
+        if (lane == 0) rot[k] = d;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        double v = qc[i];
+        for (int k = 0; k < c; ++k) v = fma(-sY[(int64_t)k * K + i], rot[k], v);
+        qc[i] = v;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      double d = 0.0;
+      for (int i = lane; i < K; i += 32) d = fma(qc[i], qc[i], d);
+      d = dev::warp_sum_d(d);
+      if (lane == 0) rot[0] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    const double f = rot[0];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) qc[i] *= f;
+    __syncthreads();
+  }
+  // (3) B Q in f64 (sB's f32 contents are no longer needed), then f64 sweeps
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) sB[idx] = Bp.times(sY, idx % K, idx / K);
+  __syncthreads();
+  const double tol = fmax(2.0 * sqrt((double)K) * 0x1.0p-52, (double)K * 0x1.0p-53);
+  const int sw64 = cta_sweeps<double>(sB, sY, K, tol, 0.0, 80, rot, s_rot);
+  // singular values = column norms, ordered descending (stable by index)
   for (int c = warp; c < K; c += nw) {
     const double *bc = sB + c * K;
     double sq = 0.0;
@@ -963,7 +1060,8 @@ __device__ int cta_jacobi(double *sB, double *sY, int K, double *sigma, double *
     if (lane == 0) sigma[pc] = nc;
   }
   __syncthreads();
-  return done ? sweep : -(sweep - 1);
+  (void)sw32;
+  return sw64;
 }
 
 // ---------------------------------------------------------------------------
@@ -1056,11 +1154,9 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
     cl.sync();
     const bool small_on_cta = K <= kCtaJacobiMax;
     double *sB = reinterpret_cast<double *>(S.xs), *sYw = reinterpret_cast<double *>(S.ring);
-    if (!small_on_cta || rank == 0) {
-      double *Bdst = small_on_cta ? sB : W.Bm;
-      const unsigned r_lo = small_on_cta ? 0u : rank, r_n = small_on_cta ? 1u : cs;
-      for (int64_t idx = (int64_t)r_lo * blockDim.x + threadIdx.x; idx < (int64_t)K * K;
-           idx += (int64_t)r_n * blockDim.x) {
+    if (!small_on_cta) {
+      for (int64_t idx = (int64_t)rank * blockDim.x + threadIdx.x; idx < (int64_t)K * K;
+           idx += (int64_t)cs * blockDim.x) {
         const int r = (int)(idx % K), c = (int)(idx / K);
         double v = 0.0;
         if (r < l) {
@@ -1070,15 +1166,15 @@ __device__ void solve_psvd(cg::cluster_group &cl, const BProb &P, BWork W, const
           if (c == r) v = W.alpha[r];
           else if (c == r + 1) v = W.beta[r];
         }
-        Bdst[idx] = v;
+        W.Bm[idx] = v;
       }
     }
     if (small_on_cta) {
       // the leading CTA alone, in its shared memory (the vector and ring areas are idle now)
       int sw = 0;
       if (rank == 0) {
-        __syncthreads();
-        sw = cta_jacobi(sB, sYw, K, W.sigma, W.X, W.Y, S.red, S.redi, S.s_rot, S.hv);
+        const ProjB Bp{W.sigma, W.rho, W.alpha, W.beta, l, K};
+        sw = cta_svd(sB, sYw, Bp, W.sigma, W.X, W.Y, S.red, S.redi, S.s_rot, S.hv);
       }
       cl.sync();  // sigma, X, Y visible to every CTA
       res.sweeps = sw;

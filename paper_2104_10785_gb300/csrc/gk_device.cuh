@@ -21,6 +21,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // tournament (circle method) pairing: round r, slot s of Kp players
 __device__ __forceinline__ int player(int r, int s, int Kp) { return s == 0 ? 0 : ((s - 1 + r) % (Kp - 1)) + 1; }
 
