@@ -313,6 +313,15 @@ const char *gk_version(void);
 int gk_host_alloc(size_t bytes, void **ptr);
 int gk_host_free(void *ptr);
 
+/* Self-test of the device-side bounded wait that every spin of the library
+ * uses (mbarrier waits of the bulk-copy pipelines): one CTA waits on an
+ * mbarrier that nothing arrives at, for at most `cycles` SM clock cycles, and
+ * returns.  Returns GK_TIMEOUT when the wait gave up (the expected result),
+ * GK_OK if the phase completed, GK_NO_DEVICE, GK_INVALID_ARG (cycles < 0 or
+ * above 4e9, about 2 s),
+ * GK_OUT_OF_MEMORY or GK_CUDA_ERROR.  The context stays usable either way. */
+int gk_wait_selftest(long long cycles);
+
 /* Kernels the calling host thread has launched through this library so far
  * (every entry point counts its own launches; the counter never resets). */
 int64_t gk_launch_count(void);

@@ -28,4 +28,5 @@ from .gk import (  # noqa: F401
     library_path,
     status_string,
     version,
+    wait_selftest,
 )

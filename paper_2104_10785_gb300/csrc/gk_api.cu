@@ -17,6 +17,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <chrono>
 #include <mutex>
 #include <vector>
@@ -971,8 +973,15 @@ size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *oin) {
   return psvd_layout(A, p, d, st, false, false, nullptr, &b, &op);
 }
 
+// NVTX ranges name each entry point's span for profilers (no cost without one attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 int gk_psvd(const gk_matrix *A, int k, double tol, const gk_opts *opts, double *U, double *S, double *V,
             gk_info *info) {
+  NvtxRange r("gk_psvd");
   return psvd_impl(A, k, tol, opts, U, S, V, info);
 }
 
@@ -989,10 +998,12 @@ size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *oin) {
 
 int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, int *rank, double *sigma,
                gk_info *info) {
+  NvtxRange r("gk_numrank");
   return numrank_impl(A, eps, kmax, opts, rank, sigma, info);
 }
 
 int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const gk_opts *opts) {
+  NvtxRange r(trans ? "gk_matvec_t" : "gk_matvec");
   return matvec_impl(A, trans, x, y, opts);
 }
 

@@ -163,7 +163,7 @@ __device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes) {
                : "memory");
 }
 // bounded wait for the phase of the given parity; false if it did not complete in time
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit = kRingWait) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   for (;;) {
@@ -174,8 +174,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kRingWait) return false;
+    if (clock64() - t0 > limit) return false;
   }
+}
+
+// The bounded wait on its own: one CTA waits on an mbarrier that nothing arrives at, with a
+// limit of `limit` SM clock cycles, and records in *out whether it gave up (1) or saw the
+// phase complete (0).  No copy is in flight, so returning after the limit is safe.
+__global__ void k_wait_probe(long long limit, int *out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+  const int bad = __syncthreads_or(!ok);
+  if (threadIdx.x == 0) *out = bad;
 }
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -1777,6 +1792,29 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
 
 }  // namespace
 }  // namespace gk
+
+extern "C" int gk_wait_selftest(long long cycles) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return GK_NO_DEVICE;
+  }
+  if (cycles < 0 || cycles > 4000000000ll) return GK_INVALID_ARG;  // at most about 2 s
+  int *d = nullptr, h = -1;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OUT_OF_MEMORY;
+  }
+  gk::k_wait_probe<<<1, 64>>>(cycles, d);
+  gk::note_launch();
+  const cudaError_t e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GK_CUDA_ERROR;
+  }
+  return h ? GK_TIMEOUT : GK_OK;
+}
 
 extern "C" int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info) {
   return gk::batched_impl(items, count, 0, opts, info);

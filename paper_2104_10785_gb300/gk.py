@@ -134,6 +134,8 @@ def lib():
             L.gk_version.restype = C.c_char_p
             L.gk_launch_count.argtypes = []
             L.gk_launch_count.restype = C.c_int64
+            L.gk_wait_selftest.argtypes = [C.c_longlong]
+            L.gk_wait_selftest.restype = C.c_int
             L.gk_host_alloc.argtypes = [C.c_size_t, C.POINTER(C.c_void_p)]
             L.gk_host_alloc.restype = C.c_int
             L.gk_host_free.argtypes = [C.c_void_p]
@@ -183,6 +185,11 @@ def host_free(t) -> None:
     st = lib().gk_host_free(C.c_void_p(ent[0]))
     if st < 0:
         raise GKError(st, "gk_host_free")
+
+
+def wait_selftest(cycles: int) -> int:
+    """Status of a device wait on a flag that nothing sets, bounded to `cycles` SM cycles."""
+    return int(lib().gk_wait_selftest(int(cycles)))
 
 
 def launch_count() -> int:

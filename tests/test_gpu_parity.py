@@ -251,7 +251,7 @@ def test_reorthogonalization_modes_match_oracle(passes):
     assert r == r_o == 40
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 def test_psvd_reduced_precision_storage(dtype):
     """sigma_i = i^-1.5 spectrum stored in f32 / bf16; parity with the oracle on the stored bytes."""
     m, n, k, K = 3001, 1499, 12, 40
@@ -264,6 +264,27 @@ def test_psvd_reduced_precision_storage(dtype):
     gaps = np.abs(np.diff(sig[: k + 1])).min()
     _compare_psvd(op, At, A64, k, K, 1e-8, q1, s_rtol=1e-7, v_tol=max(1e-6, 10 * (1e-8 + floor) / gaps),
                   res_tol=1e-8 + 10 * floor)
+
+
+def test_psvd_f16_with_scale():
+    """f16 storage of A / s with the operator scale s: the same triplets as the oracle on the
+    stored bytes times s (entries of A here are ~1e-6, below f16's normal range without it)."""
+    m, n, k, K = 1200, 500, 8, 30
+    sig = synth.sigma_power(n, 1.5) * 1e-4
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, seed=78, dtype=np.float64)
+    s = 2.0 ** -14
+    h = np.asarray(A / s, dtype=np.float16)
+    op = oracle.Operator.dense(None, dtype="f16", bits=h.view(np.uint16), scale=s)
+    q1 = synth.start_vector(m, 78)
+    A64 = h.astype(np.float64) * s
+    nf = np.linalg.norm(A64)
+    floor = 64 * U32 * nf / np.sqrt(n)
+    Uo, So, Vo, io = oracle.psvd(op, k, K, q1, tol=1e-12, max_restarts=500)
+    U, S, V, st, info = gk().gk_psvd(cuda(h), k, 1e-8, krylov_dim=K, start=cuda(q1), scale=s)
+    assert st == 0
+    np.testing.assert_allclose(S.cpu().numpy(), So, rtol=1e-6)
+    r1, r2 = oracle.residuals(op, U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy())
+    assert max(r1.max(), r2.max()) <= (1e-8 + 10 * floor / So[0]) * So[0] * 1.01
 
 
 def test_psvd_csr_planted():
@@ -357,3 +378,39 @@ def test_gpu_residuals_entry_point():
     Sp = sig[:5] * 1.001
     r1, r2 = M.gk_residuals(cuda(A), cuda(U0[:, :5]), cuda(Sp), cuda(V0[:, :5]))
     np.testing.assert_allclose(r1.cpu().numpy(), 0.001 * sig[:5], rtol=1e-9)
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives():
+    """A device wait on an mbarrier that nothing arrives at gives up after its limit and the
+    host reads GK_TIMEOUT; the context stays usable for the next calls."""
+    from paper_2104_10785_gb300 import gk as gkmod
+
+    M = gk()
+    assert M.wait_selftest(0) == gkmod.GK_TIMEOUT
+    assert M.wait_selftest(200000) == gkmod.GK_TIMEOUT
+    assert M.wait_selftest(-1) == gkmod.GK_INVALID_ARG
+    A = np.random.default_rng(3).standard_normal((300, 200))
+    x = np.random.default_rng(4).standard_normal(200)
+    y = M.gk_matvec(cuda(A), cuda(x)).cpu().numpy()
+    np.testing.assert_allclose(y, A @ x, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_non_finite_operator_reports_numerical(bad):
+    """A NaN or Inf entry: the single-problem calls and the batched item return GK_NUMERICAL
+    (no hang, no fault); the other problems of the batch are unaffected."""
+    from paper_2104_10785_gb300 import gk as gkmod
+
+    M = gk()
+    A = synth.gaussian_product(200, 120, 6, 1e-6, seed=8, dtype=np.float64)
+    A[17, 33] = bad
+    At = cuda(A)
+    st = M.gk_psvd(At, 3, 1e-8, krylov_dim=12, check=False)[3]
+    assert st == gkmod.GK_NUMERICAL
+    r, _, st2, _ = M.gk_numrank(At, 1e-6, 50, check=False)
+    assert st2 == gkmod.GK_NUMERICAL
+    good = synth.gaussian_product(220, 100, 6, 1e-9, seed=9, dtype=np.float64)
+    out, stb, info = M.gk_psvd_batched([dict(A=At, k=3, krylov_dim=12), dict(A=cuda(good), k=3, krylov_dim=12)],
+                                       check=False)
+    assert out[0][3]["status"] == gkmod.GK_NUMERICAL and out[1][3]["status"] == 0
+    np.testing.assert_allclose(out[1][1].cpu().numpy(), np.linalg.svd(good, compute_uv=False)[:3], rtol=1e-10)
