@@ -3,12 +3,14 @@
 
 Metric: converged top-k singular triplets per second at <= 1e-8 relative residual.
 Default workload: dense 100000 x 40000 operator stored in bf16, A = U diag(i^-1.5) V^T
-with seeded orthonormal factors, top-100 triplets, Krylov dimension 200, tol 1e-8.
-One step = one full gk_psvd call (start vector, bidiagonalization sweeps with
-reorthogonalization, small SVDs, restarts, Ritz vectors) on inputs resident in HBM.
-The same solve on the f32-stored copy (the plain path) is timed beside it, and the
-end-to-end figure times the C-ABI call on pinned host buffers (host-to-device copy of
-the operator and device-to-host copy of U, S, V inside the timed region).
+with seeded orthonormal factors, top-100 triplets, tol 1e-8, in the precision form with
+the learned Krylov dimension: one step = the sketch of A and the network's prediction of
+K, then one full gk_psvd call (start vector, bidiagonalization sweeps with
+reorthogonalization, small SVDs, restarts if the prediction was short, Ritz vectors) on
+inputs resident in HBM.  Beside it: the same bf16 operator at the fixed Krylov dimension
+200, and the plain path (the f32-stored copy at K = 200).  The end-to-end figure times
+the same steps from host buffers (host-to-device copy of the operator and device-to-host
+copy of U, S, V inside the timed region).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gk|reference] [--workload NAME]
 
@@ -494,6 +496,20 @@ def run_gk(args, rank, world):
     A = w["A"]
     stream = torch.cuda.current_stream(device)
     kw = dict(krylov_dim=K, seed=w["seed"])
+    # the bf16 precision form takes its Krylov dimension from the learned predictor (sketch +
+    # network, inside every timed step); --fixed-krylov times the workload's fixed K instead
+    from paper_2104_10785_gb300 import predictor
+
+    kparams = None
+    if w["name"] == "dense_bf16_100000x40000_top100" and not args.fixed_krylov:
+        kparams = predictor.load(device=device, path=predictor.KRYLOV_PARAMS_FILE)
+        if kparams is None:
+            raise SystemExit("trained Krylov-dimension weights are missing")
+
+    def solve(Aop, **extra):
+        if kparams is not None:
+            return predictor.learned_psvd(Aop, kparams, k, tol, seed=w["seed"], **extra)
+        return gk.gk_psvd(Aop, k, tol, **kw, **extra)
 
     def barrier():
         if dist:
@@ -501,7 +517,7 @@ def run_gk(args, rank, world):
 
     # warm-up
     for _ in range(args.warmup):
-        U, S, V, st, info = gk.gk_psvd(A, k, tol, **kw)
+        U, S, V, st, info = solve(A)
     torch.cuda.synchronize()
 
     # timed region: inputs resident in HBM (8 GB operator > 129 MB L2)
@@ -515,17 +531,20 @@ def run_gk(args, rank, world):
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos, statuses = [], []
+    launches0 = gk.launch_count()
     for i in range(args.steps):
         if flush is not None:
             flush.fill_(i & 0xFF)
         evs[i][0].record(stream)
-        U, S, V, st, info = gk.gk_psvd(A, k, tol, profile=True, **kw)
+        U, S, V, st, info = solve(A, profile=True)
         evs[i][1].record(stream)
         infos.append(info)
         statuses.append(st)
     torch.cuda.synchronize()
+    launches_timed = gk.launch_count() - launches0
     barrier()
     clk = clocks.stop()
+    Kused = infos[-1].get("krylov_dim", K)
     ms = sum(a.elapsed_time(b) for a, b in evs)
     if dist:
         t = torch.tensor([ms], device=device)
@@ -560,8 +579,8 @@ def run_gk(args, rank, world):
             g["flops_per_launch"] = 2 * w["m"] * w["n"]
             g["TFLOPs"] = g["flops_per_launch"] / (avg_ms / 1e3) / 1e12
         groups[which] = g
-    keep = k + (K - k) // 2
-    ofl, oby = orth_work(w["m"], w["n"], K, keep, infos[-1]["cycles"])
+    keep = k + (Kused - k) // 2
+    ofl, oby = orth_work(w["m"], w["n"], Kused, keep, infos[-1]["cycles"])
     oms = tot["ms_orth"] / len(infos)
     groups["orth"] = {"kernel": "k_cgs_dot+k_cgs_update_*+k_reduce_cols (per solve)", "total_ms": tot["ms_orth"],
                       "ms_per_solve": oms, "flops_per_solve": ofl, "bytes_per_solve": oby,
@@ -585,6 +604,24 @@ def run_gk(args, rank, world):
     breakdown = {key: tot[key] / args.steps for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "ms_small",
                                                           "ms_restart")}
 
+    # with the learned Krylov dimension: the same operator at the workload's fixed K beside it
+    fixed = None
+    if kparams is not None:
+        gk.gk_psvd(A, k, tol, **kw)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(reps):
+            Uf, Sf, Vf, stf, infof = gk.gk_psvd(A, k, tol, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / reps
+        fixed = {"value": k / (fms / 1e3), "unit": "triplets/s", "ms_per_step": fms, "krylov_dim": K,
+                 "matvecs": infof["matvecs"], "restarts": infof["restarts"], "status": stf,
+                 "learned_speedup": (k / (step_ms / 1e3)) / (k / (fms / 1e3))}
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -607,7 +644,7 @@ def run_gk(args, rank, world):
                 big, big_h = A, Ah
             outs = (gk.host_empty((k, w["m"]), torch.float64), gk.host_empty((k,), torch.float64),
                     gk.host_empty((k, w["n"]), torch.float64))
-        gk.gk_psvd(Ah, k, tol, out=outs, **kw)
+        solve(Ah, out=outs)
         # the host link's bandwidth at this moment, for reading the figure
         Bd = torch.empty_like(big)
         torch.cuda.synchronize()
@@ -622,11 +659,11 @@ def run_gk(args, rank, world):
         reps = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
         for _ in range(reps):
-            Uh, Sh, Vh, sth, infoh = gk.gk_psvd(Ah, k, tol, out=outs, **kw)
+            Uh, Sh, Vh, sth, infoh = solve(Ah, out=outs)
             float(Sh[0])  # the result is read on the host
         te = (time.perf_counter() - t0) / reps
         # one more call (untimed) with the library's event timing, to split copies from kernels
-        infop = gk.gk_psvd(Ah, k, tol, out=outs, profile=True, **kw)[4]
+        infop = solve(Ah, out=outs, profile=True)[4]
         if dist:
             t = torch.tensor([te], device=device)
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
@@ -708,7 +745,8 @@ def run_gk(args, rank, world):
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if a_dtype == torch.bfloat16 else ("f64" if a_dtype == torch.float64 else "f32"),
         "data": "synthetic",
-        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": K, "tol": tol,
+        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": Kused, "tol": tol,
+                   "krylov": "learned (sketch + network in every step)" if kparams is not None else "fixed",
                    "storage": w["dtype"], "accumulate": "f32 runs combined in f64; f64 basis, small SVD, residuals",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": ("inputs larger than L2 (operator %.2f GB)" % (a_bytes / 1e9)) if flush is None else
@@ -717,10 +755,10 @@ def run_gk(args, rank, world):
         "restarts": last["restarts"], "matvecs": last["matvecs"], "steps_per_solve": last["steps"],
         "breakdown_ms_per_step": breakdown,
         "roofline": roof, "clocks": clk, "gpu_launches": None,
-        "e2e": e2e, "cpu_baseline": cpu, "plain_f32": plain, "gen_seconds": w["gen_seconds"],
+        "e2e": e2e, "cpu_baseline": cpu, "plain_f32": plain, "fixed_krylov": fixed, "gen_seconds": w["gen_seconds"],
         "batched": batched,
     }
-    out["gpu_launches"] = int(sum(i["launches"] for i in infos))
+    out["gpu_launches"] = int(launches_timed)
     return out
 
 
@@ -890,6 +928,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--fixed-krylov", action="store_true",
+                    help="time the default workload at its fixed Krylov dimension instead of the learned one")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this kernel")
     args = ap.parse_args()

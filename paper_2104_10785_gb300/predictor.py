@@ -32,6 +32,7 @@ from . import gk
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 PARAMS_FILE = os.path.join(HERE, "predictor_params.f32")
+KRYLOV_PARAMS_FILE = os.path.join(HERE, "predictor_krylov_params.f32")
 SKETCH_SEED = 0x5E7C4
 K_OFFSETS = (2, 4, 6, 8, 12, 16, 24, 32)
 RANK_MARGIN = (1.05, 1)  # r^ = ceil(1.05 * exp(prediction)) + 1: an under-estimate costs a re-solve
@@ -225,5 +226,106 @@ def main(argv=None):
     print(f"dataset {t1 - t0:.1f} s, training {time.time() - t1:.1f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}")
 
 
+
+
+# ---------------------------------------------------------------------------
+# Krylov dimension of a single large partial SVD (the bf16 precision form)
+# ---------------------------------------------------------------------------
+# The same network, trained on another family: dense operators A = U diag(i^-e) V^T stored
+# in bf16, e ~ U[1.1, 2.0], sizes between 4000 x 2000 and 20000 x 8000, top k = 100 at tol
+# 1e-8.  Targets: (log k, log K*) with K* the smallest Krylov dimension in k + {10, 20, ...,
+# 140} at which the partial SVD converges in one cycle (binary search over one-cycle solves).
+# For this family K* depends on the decay of the spectrum, not on the sizes, so the sketch
+# features carry it; the plain restart loop covers a dimension that is too small.
+KRYLOV_K = 100
+KRYLOV_TOL = 1e-8
+KRYLOV_GRID = tuple(KRYLOV_K + d for d in range(10, 150, 10))
+
+
+def krylov_targets(A, k=KRYLOV_K, tol=KRYLOV_TOL):
+    lo, hi = 0, len(KRYLOV_GRID) - 1
+    while lo < hi:
+        mid = (lo + hi) // 2
+        st = gk.gk_psvd(A, k, tol, krylov_dim=KRYLOV_GRID[mid], max_restarts=0, check=False)[3]
+        if st == gk.GK_OK:
+            hi = mid
+        else:
+            lo = mid + 1
+    return KRYLOV_GRID[hi]
+
+
+def krylov_dataset(count, seed, log=None):
+    """Features and targets of `count` seeded operators of the bf16 power-law family."""
+    import synth
+
+    g = np.random.default_rng(seed)
+    X, Y = [], []
+    for i in range(count):
+        e = float(g.uniform(1.1, 2.0))
+        m = int(np.exp(g.uniform(np.log(4000), np.log(20000))))
+        n = int(np.exp(g.uniform(np.log(2000), np.log(min(m, 8000)))))
+        sig = synth.sigma_power(n, e)
+        A32, _, _ = synth.torch_prescribed_spectrum(m, n, sig, seed * 1000 + i)
+        A = A32.to(torch.bfloat16)
+        del A32
+        feats = gk.gk_sketch_batched([A], SKETCH_SEED)
+        ks = krylov_targets(A)
+        X.append(feats)
+        Y.append(torch.tensor([[math.log(KRYLOV_K), math.log(ks)]], dtype=torch.float32, device=feats.device))
+        del A
+        torch.cuda.empty_cache()
+        if log:
+            log(f"krylov dataset {i + 1}/{count}: e={e:.2f} {m}x{n} K*={ks}")
+    return torch.cat(X), torch.cat(Y)
+
+
+def predict_krylov(A, params, k=KRYLOV_K, margin=2, bf16=True):
+    """Krylov dimension for the top-k partial SVD of A from its sketch features."""
+    feats = gk.gk_sketch_batched([A], SKETCH_SEED)
+    out = gk.gk_mlp_forward(params, feats, bf16_weights=bf16).cpu().numpy()[0]
+    K = int(math.ceil(math.exp(min(max(float(out[1]), 0.0), 20.0)))) + margin
+    return int(min(max(K, k + 2), min(A.shape), K_LIMIT))
+
+
+def learned_psvd(A, params, k=KRYLOV_K, tol=KRYLOV_TOL, out=None, **kw):
+    """gk_psvd with the predicted Krylov dimension (the restart loop covers a short one).  A host
+    operator is copied to the device first (the sketch reads device memory); with `out` (host
+    tensors U k x m, S k, V k x n) the results are copied back into them."""
+    Ad = A if A.device.type == "cuda" else A.to("cuda", non_blocking=True)
+    K = predict_krylov(Ad, params, k)
+    U, S, V, st, info = gk.gk_psvd(Ad, k, tol, krylov_dim=K, **kw)
+    info["krylov_dim"] = K
+    if out is not None:
+        out[0].copy_(U.T)
+        out[1].copy_(S)
+        out[2].copy_(V.T)
+        U, S, V = out[0].T, out[1], out[2].T
+    return U, S, V, st, info
+
+
+def main_krylov(argv=None):
+    import argparse
+    import time
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=240)
+    ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--out", default=KRYLOV_PARAMS_FILE)
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    X, Y = krylov_dataset(a.count, a.seed, log=lambda s: print(s, flush=True))
+    t1 = time.time()
+    params, losses = train(X, Y, epochs=a.epochs, batch=32, lr=1e-3, seed=a.seed)
+    losses = losses.cpu().numpy()
+    save(params, a.out)
+    print(f"dataset {t1 - t0:.1f} s, training {time.time() - t1:.1f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}")
+
+
 if __name__ == "__main__":
-    main()
+    import sys
+
+    if len(sys.argv) > 1 and sys.argv[1] == "krylov":
+        main_krylov(sys.argv[2:])
+    else:
+        main()

@@ -171,3 +171,26 @@ def test_trained_predictor_gains_over_plain():
     assert il["fallbacks"] <= 0.05 * len(mats)
     assert il["matvecs"] < 0.75 * ip["matvecs"], (il["matvecs"], ip["matvecs"])
     assert tl < tp, (tl, tp)
+
+
+def test_krylov_predictor_on_a_held_out_operator():
+    """The committed Krylov-dimension network on an operator of its family that it was not trained
+    on (sigma_i = i^-1.4, 9000 x 3500, bf16, its own seed): the predicted K is at least the
+    measured one-cycle K* and at most 30 above it, and the learned solve converges to the
+    tolerance with fewer products than K = 2k."""
+    from paper_2104_10785_gb300 import predictor
+
+    params = predictor.load(path=predictor.KRYLOV_PARAMS_FILE)
+    assert params is not None, "trained Krylov-dimension weights missing"
+    sig = synth.sigma_power(3500, 1.4)
+    A32, _, _ = synth.torch_prescribed_spectrum(9000, 3500, sig, 4242)
+    A = A32.to(torch.bfloat16)
+    kstar = predictor.krylov_targets(A)
+    K = predictor.predict_krylov(A, params)
+    assert kstar <= K <= kstar + 30, (K, kstar)
+    U, S, V, st, info = predictor.learned_psvd(A, params)
+    assert st == 0 and info["resid_est_max"] <= predictor.KRYLOV_TOL and info["restarts"] == 0
+    U2, S2, V2, st2, info2 = gk().gk_psvd(A, predictor.KRYLOV_K, predictor.KRYLOV_TOL,
+                                          krylov_dim=2 * predictor.KRYLOV_K)
+    assert info["matvecs"] < info2["matvecs"]
+    np.testing.assert_allclose(S.cpu().numpy(), S2.cpu().numpy(), rtol=1e-6)
