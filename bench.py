@@ -891,11 +891,52 @@ def run_batched_headline(args, rank, world, device):
     res = batched_leg(device, args.steps, args.warmup, keep_mats=True)
     clk = clocks.stop()
     mats, shapes = res.pop("_mats"), res.pop("_shapes")
+    import paper_2104_10785_gb300 as gk
+    from paper_2104_10785_gb300 import predictor
+    import synth
+
+    wb = synth.WORKLOADS["batched_f32_512_rank5to64"]
+    # end to end: the 512 operators in library host memory, copied in, the learned pipeline, the
+    # triplets copied out, every step
+    e2e = None
+    if not args.no_e2e:
+        params = predictor.load(device=device)
+        # one library host buffer (its allocation granularity is a huge page), carved per operator
+        # at 16-byte aligned offsets
+        offs, tot = [], 0
+        for A in mats:
+            offs.append(tot)
+            tot += (A.numel() + 3) // 4 * 4
+        pool = gk.host_empty((tot,), torch.float32)
+        hosts = [pool[o:o + A.numel()].view(A.shape) for o, A in zip(offs, mats)]
+        for h, A in zip(hosts, mats):
+            h.copy_(A)
+        devs = [torch.empty_like(A) for A in mats]
+
+        def e2e_step():
+            for d, h in zip(devs, hosts):
+                d.copy_(h, non_blocking=True)
+            ranks, out, info = predictor.learned_batched(devs, params, wb["eps"], wb["tol"])
+            res_h = [(U.cpu(), S.cpu(), V.cpu()) for (U, S, V, _) in out]
+            return ranks, res_h
+
+        e2e_step()
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ranks, res_h = e2e_step()
+        te = (time.perf_counter() - t0) / reps
+        trip = int(sum(ranks))
+        e2e = {"value": trip * world / te, "unit": "triplets/s", "ms_per_step": te * 1e3,
+               "h2d_bytes_per_step": int(sum(A.numel() * 4 for A in mats)),
+               "d2h_bytes_per_step": int(sum(8 * r * (A.shape[0] + A.shape[1] + 1) for r, A in zip(ranks, mats)))}
+        del hosts, devs
+        gk.host_free(pool)
+        del pool
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        import synth
-
-        v, cores, desc = oracle_batched_sample(mats, shapes, synth.WORKLOADS["batched_f32_512_rank5to64"])
+        v, cores, desc = oracle_batched_sample(mats, shapes, wb)
         cpu = {"value": v, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": desc}
     del mats
     ms = res["learned"]["ms_per_step"]
@@ -912,7 +953,7 @@ def run_batched_headline(args, rank, world, device):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": res.pop("config"), "clocks": clk,
         "gpu_launches": int(res["learned"]["launches_per_step"] * args.steps),
-        "roofline": res.pop("roofline"), "e2e": None, "cpu_baseline": cpu, "batched": res,
+        "roofline": res.pop("roofline"), "e2e": e2e, "cpu_baseline": cpu, "batched": res,
     }
 
 

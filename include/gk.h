@@ -305,7 +305,9 @@ const char *gk_version(void);
 /* Pinned host memory for host operands and results (the calls above accept
  * any host pointer; copies from this memory stay at the link's full rate).
  * gk_host_alloc maps at least `bytes` of anonymous memory aligned to the
- * transparent-huge-page size, asks the kernel to back it with huge pages,
+ * transparent-huge-page size (the mapping is rounded up to it: 512 MB with
+ * 64 KB base pages, 2 MB with 4 KB ones, so carve many small operands from one
+ * buffer), asks the kernel to back it with huge pages,
  * zero-fills it and registers it with CUDA (cudaHostRegister); *ptr receives
  * the address (owned by the library until gk_host_free).  Errors:
  * GK_INVALID_ARG (null ptr, zero bytes, or an address gk_host_alloc did not

@@ -160,7 +160,9 @@ _host_bufs = {}
 
 
 def host_empty(shape, dtype=torch.float32):
-    """A host tensor in huge-page-backed pinned memory from gk_host_alloc (release with host_free)."""
+    """A host tensor in huge-page-backed pinned memory from gk_host_alloc (release with host_free).
+    The mapping is rounded up to the huge-page size (512 MB with 64 KB pages): carve small operands
+    from one buffer instead of allocating each."""
     import numpy as np
 
     shape = tuple(int(x) for x in shape)
