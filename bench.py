@@ -912,13 +912,27 @@ def run_batched_headline(args, rank, world, device):
         for h, A in zip(hosts, mats):
             h.copy_(A)
         devs = [torch.empty_like(A) for A in mats]
+        # room for up to 80 triplets per problem in a second library host buffer
+        rcap = 80
+        ooffs, otot = [], 0
+        for A in mats:
+            ooffs.append(otot)
+            otot += rcap * (A.shape[0] + A.shape[1] + 1)
+        opool = gk.host_empty((otot,), torch.float64)
 
         def e2e_step():
             for d, h in zip(devs, hosts):
                 d.copy_(h, non_blocking=True)
             ranks, out, info = predictor.learned_batched(devs, params, wb["eps"], wb["tol"])
-            res_h = [(U.cpu(), S.cpu(), V.cpu()) for (U, S, V, _) in out]
-            return ranks, res_h
+            for (U, S, V, _), o, A, r in zip(out, ooffs, mats, ranks):
+                m, n = A.shape
+                r = min(r, rcap)
+                # U[:, :r] and V[:, :r] are transposed views of contiguous r x m and r x n blocks
+                opool[o:o + r * m].view(r, m).copy_(U[:, :r].T, non_blocking=True)
+                opool[o + r * m:o + r * (m + n)].view(r, n).copy_(V[:, :r].T, non_blocking=True)
+                opool[o + r * (m + n):o + r * (m + n) + r].copy_(S[:r], non_blocking=True)
+            torch.cuda.synchronize()
+            return ranks, None
 
         e2e_step()
         torch.cuda.synchronize()
@@ -933,7 +947,8 @@ def run_batched_headline(args, rank, world, device):
                "d2h_bytes_per_step": int(sum(8 * r * (A.shape[0] + A.shape[1] + 1) for r, A in zip(ranks, mats)))}
         del hosts, devs
         gk.host_free(pool)
-        del pool
+        gk.host_free(opool)
+        del pool, opool
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, desc = oracle_batched_sample(mats, shapes, wb)

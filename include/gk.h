@@ -128,10 +128,10 @@ size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *opts);
 
 /* Partial SVD: the k largest singular triplets of A.
  * Method: Golub-Kahan bidiagonalization (Section 2.2, Eqs. 2.1-2.4) in the
- * upper-bidiagonal form started from v1 = A^T q1 / ||A^T q1|| (Algorithm 1,
- * lines 1-2), full reorthogonalization by classical Gram-Schmidt (Algorithm 1,
- * lines 6 and 13; a second pass where the first cancels, by default), Ritz pairs from the SVD of the small
- * projected matrix (Eq. 2.13, Algorithm 2 lines 2-5), and thick restarts that
+ * upper-bidiagonal form started from v1 = A^T q1 / ||A^T q1|| (Algorithm 1),
+ * full reorthogonalization by classical Gram-Schmidt (Algorithm 1; a second
+ * pass where the first cancels, by default), Ritz pairs from the SVD of the
+ * small projected matrix (Eq. 2.13, Algorithm 2), and thick restarts that
  * keep the leading Ritz vectors (the paper cites augmented restarting; the
  * restart itself is this library's choice).
  *  tol: a triplet is converged when ||A^T u_i - s_i v_i|| (the Ritz residual,
@@ -151,11 +151,11 @@ size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *opts);
 
 /* Numerical rank (Algorithm 3): run Algorithm 1 (lower-bidiagonal GK with
  * reorthogonalization) for at most kmax iterations (kmax <= 0 or > min(m,n)
- * means min(m,n), Algorithm 3 line 1), stopping when the new left norm
+ * means min(m,n), as Algorithm 3 sets it), stopping when the new left norm
  * beta_{j+1} (or right norm alpha_{j+1}) is <= eps * sigma_est (relative
  * reading; opts->eps_absolute = 1 compares with eps itself), then count the
  * singular values of B_{k'+1,k'} (square roots of the eigenvalues of
- * B^T B, Algorithm 3 lines 3-4) that exceed eps * sigma_1(B) (or eps).
+ * B^T B, Algorithm 3) that exceed eps * sigma_1(B) (or eps).
  *  rank:  host int, written on success.
  *  sigma: optional (may be NULL) output of the k' singular values of B,
  *         descending (device or host, f64, capacity kmax).
@@ -165,8 +165,8 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
                gk_info *info);
 
 /* y = A x (trans = 0; x: n, y: m) or y = A^T x (trans = 1; x: m, y: n), f64
- * vectors (device or host).  These are the products of Eq. 2.2 (Algorithm 1,
- * lines 5 and 12) run by the same kernels as the sweep: f32/bf16/f16 operators
+ * vectors (device or host).  These are the products of Eq. 2.2 (Algorithm 1)
+ * run by the same kernels as the sweep: f32/bf16/f16 operators
  * multiply in f32 with x rounded to f32 and combine short f32 runs in f64;
  * f64 and CSR operators multiply in f64. */
 int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const gk_opts *opts);

@@ -26,7 +26,7 @@
  *  - The restarted partial SVD (thick restart with Ritz vectors) is not
  *    printed in the paper, which cites augmented restarting; it is written
  *    here in the upper-bidiagonal form started from v1 = A^T q1 / ||A^T q1||
- *    (Algorithm 1, lines 1-2).
+ *    (Algorithm 1).
  */
 #include "gk_oracle.h"
 
@@ -450,13 +450,13 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
   info->kprime = 0;
   info->stop_reason = 0;
 
-  /* line 1: beta_1 = ||q_1||, q_1 = q_1 / beta_1 (Eq. 2.1, beta_1 q_1 = q_1) */
+  /* beta_1 = ||q_1||, q_1 = q_1 / beta_1 (Eq. 2.1, beta_1 q_1 = q_1) */
   const double b1 = norm2(q1, m);
   if (!(b1 > 0.0)) return -2;
   beta[0] = b1;
   scale_into(Q, q1, 1.0 / b1, m);
 
-  /* line 2: p_1 = A^T q_1, alpha_1 = ||p_1||, p_1 = p_1 / alpha_1 (Eq. 2.1) */
+  /* p_1 = A^T q_1, alpha_1 = ||p_1||, p_1 = p_1 / alpha_1 (Eq. 2.1) */
   double *w = (double *)malloc(sizeof(double) * (size_t)m);
   double *z = (double *)malloc(sizeof(double) * (size_t)n);
   gko_apply_t(A, Q, z);
@@ -537,12 +537,12 @@ int gko_numrank(const gko_op *A, int kmax, double eps, int eps_relative, int lit
 {
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
-  if (kmax <= 0 || kmax > mn) kmax = (int)mn; /* line 1: k = min(m, n) */
+  if (kmax <= 0 || kmax > mn) kmax = (int)mn; /* k = min(m, n) */
   double *alpha = (double *)malloc(sizeof(double) * (size_t)(kmax + 1));
   double *beta = (double *)malloc(sizeof(double) * (size_t)(kmax + 2));
   double *Q = (double *)malloc(sizeof(double) * (size_t)(m * (kmax + 1)));
   double *P = (double *)malloc(sizeof(double) * (size_t)(n * (kmax + 1)));
-  /* line 2: run Algorithm 1 */
+  /* run Algorithm 1 */
   int rc = gko_gk_lower(A, kmax, eps, eps_relative, passes, q1, alpha, beta, Q, P, info);
   if (rc != 0) goto out;
   const int kp = info->kprime;
@@ -560,7 +560,7 @@ int gko_numrank(const gko_op *A, int kmax, double eps, int eps_relative, int lit
       free(Uc);
       free(Vc);
     } else {
-      /* lines 3-4 as printed: eigenvalues of B^T B, counted against eps */
+      /* eigenvalues of B^T B, counted against eps */
       double *S = (double *)calloc((size_t)(kp * kp), sizeof(double));
       double *G = (double *)malloc(sizeof(double) * (size_t)(kp * kp));
       for (int c = 0; c < kp; ++c)
@@ -621,7 +621,7 @@ int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double 
   memset(U, 0, sizeof(double) * (size_t)(m * r));
   memset(V, 0, sizeof(double) * (size_t)(n * r));
   memset(S, 0, sizeof(double) * (size_t)r);
-  /* line 1: Algorithm 1 with k iterations and no break (eps = 0, absolute) */
+  /* Algorithm 1 with k iterations and no break (eps = 0, absolute) */
   int rc = gko_gk_lower(A, k, 0.0, 0, passes, q1, alpha, beta, Q, P, info);
   if (rc != 0) goto out;
   const int kp = info->kprime;
@@ -629,7 +629,7 @@ int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double 
   double *B = build_lower_B(kp, alpha, beta);
   const int rr = r < kp ? r : kp;
   if (route == 0) {
-    /* line 2: eigen-decomposition of B^T B */
+    /* eigen-decomposition of B^T B */
     double *Sm = (double *)calloc((size_t)(kp * kp), sizeof(double));
     double *G = (double *)malloc(sizeof(double) * (size_t)(kp * kp));
     double *th = (double *)malloc(sizeof(double) * (size_t)kp);
@@ -640,7 +640,7 @@ int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double 
         Sm[(int64_t)c * kp + rw] = s;
       }
     gko_jacobi_eig(kp, Sm, th, G);
-    /* lines 3-5: V_2 = P V_1, keep the r largest, Sigma_r = sqrt(Sigma_1) */
+    /* V_2 = P V_1, keep the r largest, Sigma_r = sqrt(Sigma_1) */
     for (int i = 0; i < rr; ++i) {
       S[i] = th[i] > 0.0 ? sqrt(th[i]) : 0.0;
       for (int64_t row = 0; row < n; ++row) {
@@ -648,7 +648,7 @@ int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double 
         for (int c = 0; c < kp; ++c) s += P[(int64_t)c * n + row] * G[(int64_t)i * kp + c];
         V[(int64_t)i * n + row] = s;
       }
-      /* lines 6-8: u_i = A v_i / sigma_i (Eq. svdV, read as the left vector) */
+      /* u_i = A v_i / sigma_i (Eq. svdV, read as the left vector) */
       gko_apply(A, V + (int64_t)i * n, U + (int64_t)i * m);
       if (S[i] > 0.0)
         for (int64_t row = 0; row < m; ++row) U[(int64_t)i * m + row] /= S[i];
@@ -820,7 +820,7 @@ int gko_psvd(const gko_op *A, int k, int K, int keep, double tol, int max_restar
   int64_t nfresh = 0;
   double sest = 0.0;
 
-  /* v_1 = A^T q_1 / ||A^T q_1|| (Algorithm 1, lines 1-2) */
+  /* v_1 = A^T q_1 / ||A^T q_1|| (Algorithm 1) */
   {
     double *qn = (double *)malloc(sizeof(double) * (size_t)m);
     const double b1 = norm2(q1, m);

@@ -510,7 +510,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
   GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (K + 2), s));
   GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (K + 2), s));
-  // start vector q1 (Algorithm 1, line 1) and v1 = A^T q1 / ||A^T q1|| (line 2)
+  // start vector q1 (Algorithm 1) and v1 = A^T q1 / ||A^T q1||
   if (o.start) {
     const double *src = o.start;
     if (host_start) {
@@ -750,7 +750,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   GK_CUDA(reset_ctl(b.ctl, eps, eps_rel, s));
   GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (kmax + 2), s));
   GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (kmax + 2), s));
-  // line 1: q1 ~ N(2,1)^m, q1 = q1 / ||q1||, Q_1 = q1
+  // q1 ~ N(2,1)^m, q1 = q1 / ||q1||, Q_1 = q1
   if (o.start) {
     const double *src = o.start;
     if (host_start) {
@@ -763,7 +763,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   }
   GK_CUDA(orthonormalize(b.t, m, nullptr, ldu, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
   GK_CUDA(normalize_append(b.t, m, b.Q, b.x32, b.ctl, s, d));
-  // line 2: p1 = A^T q1, alpha_1 = ||p1||, p1 = p1 / alpha_1
+  // p1 = A^T q1, alpha_1 = ||p1||, p1 = p1 / alpha_1
   GK_CUDA(matvec_t(op, b.x32, b.Q, b.z, nullptr, nullptr, b.part, b.ctl, s, d));
   GK_CUDA(orthonormalize(b.z, n, b.P, ldv, 0, 0, b.part, b.h, b.ctl, NM_BREAK, 0, 1, b.alpha, nullptr, s, d));
   GK_CUDA(normalize_append(b.z, n, b.P, b.x32, b.ctl, s, d));
@@ -815,7 +815,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   }
   inf.kprime = kp;
   inf.steps = kp;
-  // Algorithm 3, lines 3-4: singular values of B_{k'+1,k'} above the threshold
+  // Algorithm 3: singular values of B_{k'+1,k'} above the threshold
   double *sig_dev = sigma ? (host_sigma ? b.sig : sigma) : nullptr;
   prof.begin(PC_SMALL);
   GK_CUDA(bidiag_rank(b.alpha, b.beta, kp, eps, eps_rel, b.rank, b.sigma1, sig_dev, s));

@@ -1331,14 +1331,14 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
     W.alpha[i] = 0.0;
     W.beta[i] = 0.0;
   }
-  // line 1: q1, normalized, is Q[:, 0]
+  // q1, normalized, is Q[:, 0]
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) W.w[r] = P.start ? P.start[r] : start_entry(P.seed, r);
   __syncthreads();
   {
     const double q = cl_cgs_norm(cl, S, W.w, r0, r1, W.Ub, ldu, 0, 0);
     scale_slice(W.Ub, W.w, r0, r1, q > 0.0 ? 1.0 / q : 0.0);
   }
-  // line 2: p1 = A^T q1, alpha_1 = ||p1||
+  // p1 = A^T q1, alpha_1 = ||p1||
   rows_matvec_t<T>(P, S, r0, r1, W.Ub);
   reduce_matvec_t(cl, P, S, v0, v1, W.z, nullptr, 0.0);
   double a = cl_cgs_norm(cl, S, W.z, v0, v1, W.Vb, ldv, 0, 0);

@@ -1,5 +1,5 @@
 // gk_matvec.cu -- the products A x and A^T x of the bidiagonalization sweep
-// (Eq. 2.2: A p_i and A^T q_{i+1}; Algorithm 1, lines 5 and 12).
+// (Eq. 2.2: A p_i and A^T q_{i+1}; Algorithm 1).
 //
 // These passes stream the whole operator once per half-step and are bounded by
 // HBM bandwidth.  Dense operators are row-major:

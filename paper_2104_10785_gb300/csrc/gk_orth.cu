@@ -1,6 +1,6 @@
 // gk_orth.cu -- full reorthogonalization, norms and the break test of the
-// bidiagonalization sweep (Algorithm 1, lines 6-11 and 13-14), plus the seeded
-// start vector (line 1) and replacement directions after an exact breakdown.
+// bidiagonalization sweep (Algorithm 1), plus the seeded
+// start vector and replacement directions after an exact breakdown.
 //
 // Classical Gram-Schmidt of w against the first j basis columns Q (len x j,
 // column-major, f64), `passes` times, then the norm:

@@ -1,8 +1,8 @@
 // gk_small.cu -- the small dense steps of the method:
-//  * the SVD of the projected matrix B (Eq. 2.13; Algorithm 2, lines 2-5),
+//  * the SVD of the projected matrix B (Eq. 2.13; Algorithm 2),
 //    by one-sided Jacobi in f64 with a parallel (round-robin) pair ordering;
 //  * the Ritz residual estimates |beta_K X_{K,i}| and the restart coupling;
-//  * Ritz vectors U_K X and V_K Y (Algorithm 2, line 3: V_2 = P V_1);
+//  * Ritz vectors U_K X and V_K Y (Algorithm 2: V_2 = P V_1);
 //  * the rank count of Algorithm 3 from Sturm sequences of the Golub-Kahan
 //    tridiagonal of B_{k'+1,k'} (its eigenvalues are +-sigma_i(B) and 0).
 #include <float.h>

@@ -13,7 +13,7 @@ produces.  Recipes (sizes as in the workloads they stand for):
                      (values N(0,1)) plus planted sigma_i u_i v_i^T with
                      disjoint random supports (u_i: 200 rows, v_i: 100 columns
                      at full size, scaled down for small cases).
-  start_vector       q1 ~ N(2,1)^m (Algorithm 1, line 1).
+  start_vector       q1 ~ N(2,1)^m (Algorithm 1).
 """
 from __future__ import annotations
 

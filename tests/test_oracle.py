@@ -38,7 +38,7 @@ def test_philox_known_answers():
 
 
 def test_start_vector_is_normal_2_1():
-    # Algorithm 1 line 1: q1 ~ N(2, 1)^m.  Moments and a KS test against N(2,1).
+    # Algorithm 1: q1 ~ N(2, 1)^m.  Moments and a KS test against N(2,1).
     from scipy import stats
 
     q = oracle.start_vector(2104107, 200000)
@@ -355,7 +355,7 @@ def test_alg2_and_first_restart_cycle_share_ritz_values():
     R[:, K - 1] -= be[K - 1] * Vb[:, K]
     assert np.abs(R).max() < 1e-13 * nA
     np.testing.assert_allclose(Vb.T @ Vb, np.eye(K + 1), atol=1e-13)
-    # v1 = A^T q1 / ||A^T q1|| (Algorithm 1 line 2)
+    # v1 = A^T q1 / ||A^T q1|| (Algorithm 1)
     v1 = A.T @ q1
     np.testing.assert_allclose(Vb[:, 0], v1 / np.linalg.norm(v1), atol=1e-14)
 
