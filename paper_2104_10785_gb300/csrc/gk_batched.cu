@@ -550,8 +550,15 @@ __device__ bool warp_matvec_t(const BProb &P, Shm &S, int64_t r0, int64_t r1, co
           }
       };
       const typename VT::V *base = reinterpret_cast<const typename VT::V *>(A) + g0 + lane;
+      const int64_t pgroups = (nv - g0) < PG ? (nv - g0) : PG;
       for (int64_t r = r0 + warp; r < r1; r += 2 * nw) {
         const bool two = r + nw < r1;
+        if (lane == 0) {  // the warp's rows two passes ahead into L2 (this panel's groups)
+          const int64_t pr = r + 4 * nw;
+          if (pr < r1) l2_prefetch(reinterpret_cast<const typename VT::V *>(A) + pr * ldv + g0, (unsigned)(pgroups * 16));
+          if (pr + nw < r1)
+            l2_prefetch(reinterpret_cast<const typename VT::V *>(A) + (pr + nw) * ldv + g0, (unsigned)(pgroups * 16));
+        }
         typename VT::V b0[G] = {}, b1[G] = {};
 #pragma unroll
         for (int q = 0; q < G; ++q) {
