@@ -391,13 +391,16 @@ __device__ void rows_matvec(const BProb &P, Shm &S, int64_t r0, int64_t r1, doub
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) acc[h] = dev::warp_sum_d(acc[h]);
-    if (lane == 0) {
-      for (int h = 0; h < nr; ++h) {
-        const int64_t r = rb + h;
-        double v = acc[h] * P.scale;
-        for (int c = 0; c < cn; ++c) v -= coefs[c] * Qb[(int64_t)(c0 + c) * ldq + r];
-        w[r] = v;
-      }
+    if (lane == 0)
+      for (int h = 0; h < nr; ++h) w[rb + h] = acc[h] * P.scale;
+  }
+  // the basis combination after all rows (coalesced, off the rows' load chain)
+  if (cn > 0) {
+    __syncthreads();
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      double v = w[r];
+      for (int c = 0; c < cn; ++c) v -= coefs[c] * Qb[(int64_t)(c0 + c) * ldq + r];
+      w[r] = v;
     }
   }
 }
