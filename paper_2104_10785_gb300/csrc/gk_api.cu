@@ -206,6 +206,11 @@ Op make_op(const gk_matrix *A) {
   op.m = A->m;
   op.n = A->n;
   op.ld = A->kind == GK_DENSE ? A->ld : 0;
+  op.nnz = 0;
+  if (A->kind == GK_CSR && A->rowptr) {
+    int64_t nz = 0;
+    if (csr_nnz(A->rowptr, A->m, &nz) == GK_OK) op.nnz = nz;
+  }
   op.scale = A->scale;
   op.vals = A->vals;
   op.rowptr = A->rowptr;

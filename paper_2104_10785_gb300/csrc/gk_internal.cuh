@@ -59,6 +59,7 @@ struct Ctl {
 struct Op {
   int kind, dtype;
   int64_t m, n, ld;
+  int64_t nnz;  // CSR: stored entries (0 if unknown); dense: 0
   double scale;
   const void *vals;
   const int32_t *rowptr;

@@ -632,13 +632,19 @@ cudaError_t launch_gemv(const Op &A, const float *x32, double *y, const double *
 }
 
 template <typename T>
-cudaError_t launch_spmv(const int32_t *rp, const int32_t *ci, const void *v, int64_t rows, double scale,
+cudaError_t launch_spmv(const int32_t *rp, const int32_t *ci, const void *v, int64_t rows, int64_t nnz, double scale,
                         const double *x, double *y, const double *sub, const double *coef, const Ctl *ctl,
                         cudaStream_t s, const Dev &d) {
-  // 8 lanes per row suit rows of ~10-40 entries
+  // lanes per row from the mean row length: 4 up to 24 entries, 8 up to 96, else 16
   const int blocks = d.sms * 8;
   const T *vals = (const T *)v;
-  GK_LAUNCH(k_spmv<T, 8><<<blocks, kThreads, 0, s>>>(rp, ci, vals, rows, scale, x, y, sub, coef, ctl));
+  const double mean = rows > 0 && nnz > 0 ? (double)nnz / (double)rows : 32.0;
+  if (mean <= 24.0)
+    GK_LAUNCH(k_spmv<T, 4><<<blocks, kThreads, 0, s>>>(rp, ci, vals, rows, scale, x, y, sub, coef, ctl));
+  else if (mean <= 96.0)
+    GK_LAUNCH(k_spmv<T, 8><<<blocks, kThreads, 0, s>>>(rp, ci, vals, rows, scale, x, y, sub, coef, ctl));
+  else
+    GK_LAUNCH(k_spmv<T, 16><<<blocks, kThreads, 0, s>>>(rp, ci, vals, rows, scale, x, y, sub, coef, ctl));
   return cudaGetLastError();
 }
 
@@ -671,11 +677,11 @@ cudaError_t matvec(const Op &A, const float *x32, const double *x64, double *y, 
                    const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d) {
   if (A.kind == GK_CSR) {
     switch (A.dtype) {
-      case GK_F64: return launch_spmv<double>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
-      case GK_F32: return launch_spmv<float>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
+      case GK_F64: return launch_spmv<double>(A.rowptr, A.colind, A.vals, A.m, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
+      case GK_F32: return launch_spmv<float>(A.rowptr, A.colind, A.vals, A.m, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
       case GK_BF16:
-        return launch_spmv<__nv_bfloat16>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
-      default: return launch_spmv<__half>(A.rowptr, A.colind, A.vals, A.m, A.scale, x64, y, sub, coef, ctl, s, d);
+        return launch_spmv<__nv_bfloat16>(A.rowptr, A.colind, A.vals, A.m, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
+      default: return launch_spmv<__half>(A.rowptr, A.colind, A.vals, A.m, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
     }
   }
   switch (A.dtype) {
@@ -719,14 +725,14 @@ cudaError_t matvec_t(const Op &A, const float *x32, const double *x64, double *y
   if (A.kind == GK_CSR) {
     switch (A.dtype) {
       case GK_F64:
-        return launch_spmv<double>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s, d);
+        return launch_spmv<double>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
       case GK_F32:
-        return launch_spmv<float>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s, d);
+        return launch_spmv<float>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
       case GK_BF16:
-        return launch_spmv<__nv_bfloat16>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s,
+        return launch_spmv<__nv_bfloat16>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.nnz, A.scale, x64, y, sub, coef, ctl, s,
                                           d);
       default:
-        return launch_spmv<__half>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.scale, x64, y, sub, coef, ctl, s, d);
+        return launch_spmv<__half>(A.t_rowptr, A.t_colind, A.t_vals, A.n, A.nnz, A.scale, x64, y, sub, coef, ctl, s, d);
     }
   }
   const int64_t rb = gemvt_row_block(A, d);

@@ -85,6 +85,7 @@ extern "C" int gk_matvec_static(const gk_matrix *A, int trans, const double *x, 
   op.m = A->m;
   op.n = A->n;
   op.ld = A->kind == GK_DENSE ? A->ld : 0;
+  op.nnz = 0;  // no device read here: CSR products take the default lanes per row
   op.scale = A->scale;
   op.vals = A->vals;
   op.rowptr = A->rowptr;
