@@ -105,6 +105,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# replicas: the slowest rank's time and the whole job's rate
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, device=None) -> float:
+    """The maximum of x over the ranks of the default process group (x itself without one).
+    NCCL reduces a device tensor, gloo a host one."""
+    import torch
+    import torch.distributed as tdist
+
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    dev = device if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units all ranks processed (each the same share: weak scaling) per second of the slowest rank."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------------------
 # host buffers next to the GPU
 # ---------------------------------------------------------------------------
 def gpu_local_cpus(gpu_index):
@@ -545,12 +567,8 @@ def run_gk(args, rank, world):
     barrier()
     clk = clocks.stop()
     Kused = infos[-1].get("krylov_dim", K)
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        t = torch.tensor([ms], device=device)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = k * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), device)
+    value = whole_job_rate(k * args.steps, world, ms / 1e3)
 
     # accuracy of the returned triplets on the stored operator (GPU residual kernels)
     r_av, r_atu = gk.gk_residuals(A, U, S, V)
@@ -664,11 +682,8 @@ def run_gk(args, rank, world):
         te = (time.perf_counter() - t0) / reps
         # one more call (untimed) with the library's event timing, to split copies from kernels
         infop = solve(Ah, out=outs, profile=True)[4]
-        if dist:
-            t = torch.tensor([te], device=device)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": k * world / te, "unit": "triplets/s", "library_ms": infoh["seconds"] * 1e3,
+        te = max_over_ranks(te, device)
+        e2e = {"value": whole_job_rate(k, world, te), "unit": "triplets/s", "library_ms": infoh["seconds"] * 1e3,
                "profiled_call_ms": {key: infop[key] for key in ("seconds", "ms_copy", "ms_matvec", "ms_matvec_t",
                                                                 "ms_orth", "ms_small", "ms_restart")},
                "h2d_bytes_per_step": int(operator_bytes(Ah)),
@@ -789,13 +804,8 @@ def run_numrank_headline(args, rank, world, device):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        import torch.distributed as tdist
-
-        t = torch.tensor([ms], device=device)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(ms, device)
+    value = whole_job_rate(args.steps, world, ms / 1e3)
     tot = {key: sum(i[key] for i in infos) for key in ("ms_matvec", "ms_matvec_t", "ms_orth", "n_matvec",
                                                         "n_matvec_t")}
     hbm, peak_kind = peaks()
@@ -955,13 +965,8 @@ def run_batched_headline(args, rank, world, device):
         cpu = {"value": v, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": desc}
     del mats
     ms = res["learned"]["ms_per_step"]
-    if world > 1:
-        import torch.distributed as tdist
-
-        t = torch.tensor([ms], device=device)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = res["learned"]["triplets"] * world / (ms / 1e3)
+    ms = max_over_ranks(ms, device)
+    value = whole_job_rate(res["learned"]["triplets"], world, ms / 1e3)
     return {
         "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
         "value": value, "unit": "triplets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
