@@ -405,13 +405,24 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
     keep = []
     outs = []
     dev = problems[0]["A"].device
+    # one output buffer per kind for the whole batch (views per problem)
+    ks = [int(pr["k"]) for pr in problems]
+    shapes = [pr["A"].shape for pr in problems]
+    uoff, soff, voff = [0], [0], [0]
+    for kk, (mm, nn) in zip(ks, shapes):
+        uoff.append(uoff[-1] + kk * mm)
+        soff.append(soff[-1] + kk)
+        voff.append(voff[-1] + kk * nn)
+    Ubig = torch.empty(max(uoff[-1], 1), dtype=torch.float64, device=dev)
+    Sbig = torch.empty(max(soff[-1], 1), dtype=torch.float64, device=dev)
+    Vbig = torch.empty(max(voff[-1], 1), dtype=torch.float64, device=dev)
     for i, pr in enumerate(problems):
         A = pr["A"]
         M, _ = make_matrix(A)
-        k = int(pr["k"])
-        U = torch.empty((k, A.shape[0]), dtype=torch.float64, device=A.device)
-        S = torch.empty(k, dtype=torch.float64, device=A.device)
-        V = torch.empty((k, A.shape[1]), dtype=torch.float64, device=A.device)
+        k = ks[i]
+        U = Ubig[uoff[i]:uoff[i + 1]].view(k, A.shape[0])
+        S = Sbig[soff[i]:soff[i + 1]]
+        V = Vbig[voff[i]:voff[i + 1]].view(k, A.shape[1])
         st = None
         if pr.get("start") is not None:
             st = pr["start"].to(torch.float64).contiguous()
@@ -430,7 +441,9 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
     status = lib().gk_psvd_batched(items, n, C.byref(o), C.byref(info))
     if check and status < 0:
         raise GKError(status, "gk_psvd_batched")
-    return [(U.T, S, V.T, _item_result(items[i])) for i, (U, S, V) in enumerate(outs)], status, info.as_dict()
+    d = info.as_dict()
+    d["sigma_1"] = Sbig[torch.tensor(soff[:-1], device=dev)]  # each problem's largest value (device)
+    return [(U.T, S, V.T, _item_result(items[i])) for i, (U, S, V) in enumerate(outs)], status, d
 
 
 def gk_numrank_batched(problems, *, seed=None, reorth_passes=None, eps_absolute=False, autotune=False, stream=None,

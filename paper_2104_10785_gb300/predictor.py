@@ -180,8 +180,9 @@ def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200, autotune
         max_restarts=max_restarts, autotune=autotune)
     ranks = []
     redo = []
+    s1s = info["sigma_1"].cpu().numpy()  # one transfer for the whole batch
     for i, (U, S, V, rr) in enumerate(out):
-        s1 = float(S[0]) if S.numel() else 0.0
+        s1 = float(s1s[i]) if S.numel() else 0.0
         seen_below = rr["rank"] < len(S) or rr["sigma_next"] <= eps * s1
         if rr["status"] != gk.GK_OK or not seen_below:
             redo.append(i)
