@@ -148,6 +148,36 @@ def gpu_local_cpus(gpu_index):
         return None
 
 
+def host_page_report():
+    """Transparent huge page mode and this process's huge-page-backed anonymous memory (kB), for
+    reading an end-to-end figure: copies from 64 KB pages run slower after long kernel runs."""
+    rep = {}
+    try:
+        rep["thp"] = open("/sys/kernel/mm/transparent_hugepage/enabled").read().strip()
+    except OSError:
+        rep["thp"] = None
+    try:
+        for line in open("/proc/self/smaps_rollup"):
+            if line.startswith("AnonHugePages:"):
+                rep["anon_huge_kb"] = int(line.split()[1])
+    except OSError:
+        pass
+    return rep
+
+
+def link_rate(host, dev):
+    """H2D copy rate (GB/s) of one host buffer into a device buffer of the same size, after one
+    untimed copy: the state of the host link when the end-to-end figure was taken."""
+    import torch
+
+    dev.copy_(host, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dev.copy_(host, non_blocking=True)
+    torch.cuda.synchronize()
+    return host.numel() * host.element_size() / (time.perf_counter() - t0) / 1e9
+
+
 class near_gpu:
     """Run the block (pinned host allocations) on the GPU's local CPUs, so that the pages land on
     its NUMA node; restores the previous affinity."""
@@ -213,21 +243,23 @@ def make_workload(name, device, want_plain=True):
     return w
 
 
-def profiled_traffic(kernel, workload):
-    """DRAM bytes per full-size launch recorded from an ncu capture in profiles/*.md, used only
-    while the kernels' source file is unchanged since the capture (else None)."""
+def profiled_traffic(kernel, workload, source="gk_matvec.cu", field="bytes_per_launch"):
+    """A figure recorded from an ncu capture in profiles/*.md (DRAM bytes per full-size launch, or
+    with field="ratio" DRAM bytes over algorithmic bytes), used only while the kernel's source
+    file is unchanged since the capture (else None)."""
     import glob
     import hashlib
     import re
 
-    src = os.path.join(ROOT, "paper_2104_10785_gb300", "csrc", "gk_matvec.cu")
+    src = os.path.join(ROOT, "paper_2104_10785_gb300", "csrc", source)
     h = hashlib.md5(open(src, "rb").read()).hexdigest()
-    pat = re.compile(r"roofline-traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)\s+source_md5=(\w+)")
+    pat = re.compile(r"roofline-traffic:\s*kernel=(\S+)\s+workload=(\S+)\s+" + field +
+                     r"=([0-9.]+)\s+source_md5=(\w+)")
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(f):
             mm = pat.search(line)
             if mm and mm.group(1) == kernel and mm.group(2) == workload and mm.group(4) == h:
-                return int(mm.group(3))
+                return float(mm.group(3)) if field == "ratio" else int(mm.group(3))
     return None
 
 
@@ -404,8 +436,12 @@ def batched_leg(device, steps, warmup, keep_mats=False):
     kms = e0.elapsed_time(e1) / reps
     kbytes = sum(o[3]["matvecs"] * A.shape[0] * A.shape[1] * 4 for o, A in zip(out, mats))
     hbm, peak_kind = peaks()
+    # DRAM bytes over algorithmic bytes from a capture of the first 64 problems, scaled to this
+    # launch by the bytes it streams (each product reads its operator once at either size)
+    ratio = profiled_traffic("k_batched<float>", "batched_f32_512_rank5to64", "gk_batched.cu", "ratio")
     res["roofline"] = {"bound": "hbm", "achieved": kbytes / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                       "frac": kbytes / (kms / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_batched<float>",
+                       "frac": kbytes / (kms / 1e3) / 1e9 / hbm,
+                       "traffic": int(ratio * kbytes) if ratio is not None else None, "kernel": "k_batched<float>",
                        "bytes_per_launch": int(kbytes), "avg_launch_ms": kms, "launches": reps,
                        "cluster_size": info["reserved"], "clusters": info["kprime"], "peak_source": peak_kind}
     if keep_mats:
@@ -665,13 +701,8 @@ def run_gk(args, rank, world):
         solve(Ah, out=outs)
         # the host link's bandwidth at this moment, for reading the figure
         Bd = torch.empty_like(big)
-        torch.cuda.synchronize()
-        Bd.copy_(big_h, non_blocking=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Bd.copy_(big_h, non_blocking=True)
-        torch.cuda.synchronize()
-        h2d_gbs = big_h.numel() * big_h.element_size() / (time.perf_counter() - t0) / 1e9
+        h2d_gbs = link_rate(big_h, Bd)
+        pages = host_page_report()
         del Bd
         barrier()
         reps = max(1, min(args.steps, 3))
@@ -688,7 +719,7 @@ def run_gk(args, rank, world):
                                                                 "ms_orth", "ms_small", "ms_restart")},
                "h2d_bytes_per_step": int(operator_bytes(Ah)),
                "d2h_bytes_per_step": int(8 * k * (w["m"] + w["n"] + 1)), "ms_per_step": te * 1e3,
-               "h2d_GBs_torch_copy": h2d_gbs,
+               "h2d_GBs_torch_copy": h2d_gbs, "host_pages": pages,
                "host_buffers": "gk_host_alloc (huge-page backed, registered), allocated on the GPU's local CPUs %s" % (
                    sorted(ng.cpus) if ng.cpus else "(local CPU list unavailable: default placement)")}
         for t in list(host_list) + list(outs):
@@ -911,51 +942,62 @@ def run_batched_headline(args, rank, world, device):
     e2e = None
     if not args.no_e2e:
         params = predictor.load(device=device)
-        # one library host buffer (its allocation granularity is a huge page), carved per operator
-        # at 16-byte aligned offsets
+        # the batch in one library host buffer (huge-page granularity) with the device layout: each
+        # operator's rows padded to 16 bytes (the solver's vector path), operators at 16-byte
+        # offsets; one H2D copy moves the batch into one device buffer of the same layout
         offs, tot = [], 0
-        for A in mats:
+        lds = [int(A.stride(0)) for A in mats]
+        for A, ld in zip(mats, lds):
             offs.append(tot)
-            tot += (A.numel() + 3) // 4 * 4
-        pool = gk.host_empty((tot,), torch.float32)
-        hosts = [pool[o:o + A.numel()].view(A.shape) for o, A in zip(offs, mats)]
+            tot += (A.shape[0] * ld + 3) // 4 * 4
+        with near_gpu(device.index or 0):
+            pool = gk.host_empty((tot,), torch.float32)
+            # room for up to 80 triplets per problem (U^T, S, V^T regions) in a second buffer
+            rcap = 80
+            su, sn = sum(A.shape[0] for A in mats), sum(A.shape[1] for A in mats)
+            opool = gk.host_empty((rcap * (su + sn + len(mats)),), torch.float64)
+        dbuf = torch.empty(tot, dtype=torch.float32, device=device)
+        hosts = [pool[o:o + A.shape[0] * ld].view(A.shape[0], ld)[:, :A.shape[1]] for o, A, ld in zip(offs, mats, lds)]
+        devs = [dbuf[o:o + A.shape[0] * ld].view(A.shape[0], ld)[:, :A.shape[1]] for o, A, ld in zip(offs, mats, lds)]
         for h, A in zip(hosts, mats):
             h.copy_(A)
-        devs = [torch.empty_like(A) for A in mats]
-        # room for up to 80 triplets per problem in a second library host buffer
-        rcap = 80
-        ooffs, otot = [], 0
-        for A in mats:
-            ooffs.append(otot)
-            otot += rcap * (A.shape[0] + A.shape[1] + 1)
-        opool = gk.host_empty((otot,), torch.float64)
+        oregions = (opool[:rcap * su], opool[rcap * su:rcap * su + len(mats) * rcap], opool[rcap * (su + len(mats)):])
 
         def e2e_step():
-            for d, h in zip(devs, hosts):
-                d.copy_(h, non_blocking=True)
+            dbuf.copy_(pool, non_blocking=True)
             ranks, out, info = predictor.learned_batched(devs, params, wb["eps"], wb["tol"])
-            for (U, S, V, _), o, A, r in zip(out, ooffs, mats, ranks):
-                m, n = A.shape
-                r = min(r, rcap)
-                # U[:, :r] and V[:, :r] are transposed views of contiguous r x m and r x n blocks
-                opool[o:o + r * m].view(r, m).copy_(U[:, :r].T, non_blocking=True)
-                opool[o + r * m:o + r * (m + n)].view(r, n).copy_(V[:, :r].T, non_blocking=True)
-                opool[o + r * (m + n):o + r * (m + n) + r].copy_(S[:r], non_blocking=True)
+            bufs = info["outputs"]
+            if bufs is not None and all(b.numel() <= h.numel() for b, h in zip(bufs, oregions)):
+                # three copies: every problem's r^ columns of U^T, the values, the columns of V^T
+                for b, h in zip(bufs, oregions):
+                    h[:b.numel()].copy_(b, non_blocking=True)
+                nbytes = sum(b.numel() * 8 for b in bufs)
+            else:
+                nbytes, o = 0, 0
+                for (U, S, V, _), A, r in zip(out, mats, ranks):
+                    m, n = A.shape
+                    for src in (U[:, :r].T, V[:, :r].T, S[:r]):
+                        opool[o:o + src.numel()].view(src.shape).copy_(src, non_blocking=True)
+                        o += src.numel()
+                    nbytes += 8 * r * (m + n + 1)
             torch.cuda.synchronize()
-            return ranks, None
+            return ranks, nbytes
 
         e2e_step()
         torch.cuda.synchronize()
+        h2d_gbs = link_rate(pool, dbuf)
+        pages = host_page_report()
         reps = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
         for _ in range(reps):
-            ranks, res_h = e2e_step()
+            ranks, d2h = e2e_step()
         te = (time.perf_counter() - t0) / reps
         trip = int(sum(ranks))
         e2e = {"value": trip * world / te, "unit": "triplets/s", "ms_per_step": te * 1e3,
-               "h2d_bytes_per_step": int(sum(A.numel() * 4 for A in mats)),
-               "d2h_bytes_per_step": int(sum(8 * r * (A.shape[0] + A.shape[1] + 1) for r, A in zip(ranks, mats)))}
-        del hosts, devs
+               "h2d_bytes_per_step": int(pool.numel() * 4), "d2h_bytes_per_step": int(d2h),
+               "h2d_GBs_torch_copy": h2d_gbs, "host_pages": pages,
+               "layout": "rows padded to 16 bytes, one host buffer and one device buffer for the batch"}
+        del hosts, devs, dbuf, oregions
         gk.host_free(pool)
         gk.host_free(opool)
         del pool, opool

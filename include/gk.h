@@ -180,7 +180,11 @@ int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, co
 
 /* One problem of a batched call.  The operator is dense, in device memory,
  * with n <= 4096 columns; all problems of one call share one storage type;
- * outputs are device pointers.  The call writes the result fields. */
+ * outputs are device pointers.  The call writes the result fields.
+ * Performance: the products read 16-byte vectors when the operator's address
+ * and its row stride (ld times the element size) are multiples of 16 bytes;
+ * otherwise they read one element at a time, several times slower (pad ld to
+ * a multiple of 4 f32, 8 bf16/f16 or 2 f64 elements). */
 typedef struct {
   gk_matrix A;
   int32_t k;             /* gk_psvd_batched: triplets wanted; gk_numrank_batched: kmax (0 = min(m, n, 256)) */

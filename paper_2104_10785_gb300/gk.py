@@ -443,6 +443,9 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
         raise GKError(status, "gk_psvd_batched")
     d = info.as_dict()
     d["sigma_1"] = Sbig[torch.tensor(soff[:-1], device=dev)]  # each problem's largest value (device)
+    # the three device buffers behind the views: problem i's k x m block of U^T, its k values and
+    # its k x n block of V^T, back to back in problem order
+    d["outputs"] = (Ubig[:uoff[-1]], Sbig[:soff[-1]], Vbig[:voff[-1]])
     return [(U.T, S, V.T, _item_result(items[i])) for i, (U, S, V) in enumerate(outs)], status, d
 
 

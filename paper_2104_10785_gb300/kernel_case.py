@@ -8,7 +8,8 @@ given dtype) and calls gk_matvec(A, x) and gk_matvec(A, y, trans=True) `reps` ti
 Batched (--batched COUNT): the first COUNT problems of the 512-problem batched recipe
 (uneven f32 products of rank 5..64 + 1e-6 noise); runs the learned pipeline's sketch
 (gk_sketch_batched) and its batched partial SVD with the committed network's (rank, K)
-`reps` times.  Everything goes through the C ABI; nothing is timed here.
+`reps` times and prints the operator bytes the last solve streamed (products x m x n x 4).
+Everything goes through the C ABI; nothing is timed here.
 """
 import argparse
 
@@ -41,8 +42,11 @@ def batched(a):
         raise SystemExit("trained predictor weights are missing")
     for _ in range(a.reps):
         pred = predictor.predict(mats, params)
-        gk.gk_psvd_batched([dict(A=A, k=r, krylov_dim=K, tol=w["tol"], rank_cut=w["eps"])
-                            for A, (r, K) in zip(mats, pred)])
+        out, _, _ = gk.gk_psvd_batched([dict(A=A, k=r, krylov_dim=K, tol=w["tol"], rank_cut=w["eps"])
+                                        for A, (r, K) in zip(mats, pred)])
+    # the operator bytes the last launch had to stream: every product reads its A once
+    alg = sum(o[3]["matvecs"] * A.shape[0] * A.shape[1] * 4 for o, A in zip(out, mats))
+    print("algorithmic_bytes_per_launch", alg)
 
 
 def main():

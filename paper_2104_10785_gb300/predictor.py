@@ -200,8 +200,10 @@ def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200, autotune
         matvecs += inf2["matvecs"]
         st = min(st, inf2["status"]) if min(st, inf2["status"]) < 0 else max(st, inf2["status"])
     final = [(U[:, :r], S[:r], V[:, :r], rr) for (U, S, V, rr), r in zip(out, ranks)]
+    # without a fallback every problem's triplets sit in the solve's three output buffers (each
+    # problem's r^ >= r columns back to back): a caller can move them to the host in three copies
     return ranks, final, dict(matvecs=matvecs, fallbacks=len(redo), status=st, predicted=pred,
-                              matvecs_per_problem=per)
+                              matvecs_per_problem=per, outputs=None if redo else info["outputs"])
 
 
 def main(argv=None):
