@@ -5,8 +5,11 @@
 // and after long kernel runs the first full copy of such a buffer measured 25-100 GB/s
 // instead of 210 GB/s.  A buffer backed by transparent huge pages (one translation per
 // huge page) copied at 210 GB/s every time.  gk_host_alloc maps anonymous memory aligned
-// to the huge-page size, advises the kernel to back it with huge pages, touches it and
-// registers it with CUDA; where huge pages are unavailable it is ordinary registered memory.
+// to the huge-page size, advises the kernel to back it with huge pages, touches it, asks
+// the kernel to collapse whatever the first touch left in small pages (a host whose free
+// memory is fragmented grants only part of a large buffer in huge pages at fault time;
+// such buffers measured 4-15 GB/s after kernel runs), and registers it with CUDA; where
+// huge pages are unavailable it is ordinary registered memory.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -65,6 +68,12 @@ extern "C" int gk_host_alloc(size_t bytes, void **ptr) {
   madvise(start, len, MADV_HUGEPAGE);
 #endif
   memset(start, 0, len);  // populate now (huge pages where the kernel grants them)
+#ifndef MADV_COLLAPSE
+#define MADV_COLLAPSE 25
+#endif
+  // best effort (Linux 6.1 and later): synchronous collapse of the range into huge pages;
+  // an older kernel or a failed compaction leaves the small pages, which still work
+  if (hp > (size_t)sysconf(_SC_PAGESIZE)) madvise(start, len, MADV_COLLAPSE);
   if (cudaHostRegister(start, len, cudaHostRegisterDefault) != cudaSuccess) {
     cudaGetLastError();
     munmap(start, len);
