@@ -42,6 +42,11 @@ __device__ __forceinline__ int player(int r, int s, int Kp) { return s == 0 ? 0 
 // normalized, Y = the rotations, in that order.  Returns the sweeps used
 // (negative if the sweep limit was reached).  Every thread of the cluster must
 // call it.
+// NL > 0 (K <= 32 NL): each lane loads its NL elements of the four columns of its pair
+// (B's p and q, Yw's p and q) at once into registers, so a round costs one L2 round trip
+// instead of one per element group and pass; the arithmetic and its order are the same
+// as with NL = 0, which walks the columns in memory (any K).
+template <int NL = 0>
 __device__ int cluster_jacobi(cg::cluster_group &cl, double *__restrict__ B, double *__restrict__ Yw, int K,
                               double *__restrict__ sigma, double *__restrict__ X, double *__restrict__ Y,
                               double *__restrict__ nrm, int *__restrict__ pos, int *s_rot, int *s_any) {
@@ -67,33 +72,76 @@ __device__ int cluster_jacobi(cg::cluster_group &cl, double *__restrict__ B, dou
         }
         if (q >= K) continue;
         double *bp = B + (int64_t)p * K, *bq = B + (int64_t)q * K;
-        double a = 0.0, b = 0.0, c = 0.0;
-        for (int i = lane; i < K; i += 32) {
-          const double x = __ldcg(bp + i), y = __ldcg(bq + i);
-          a = fma(x, x, a);
-          b = fma(y, y, b);
-          c = fma(x, y, c);
-        }
-        a = warp_sum_d(a);
-        b = warp_sum_d(b);
-        c = warp_sum_d(c);
-        if (c == 0.0 || fabs(c) <= tol * sqrt(a) * sqrt(b)) continue;
-        if (lane == 0) *s_rot = 1;
-        // rotation that makes columns p and q orthogonal (Rutishauser's formula)
-        const double zeta = (b - a) / (2.0 * c);
-        const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
-                                            : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-        for (int i = lane; i < K; i += 32) {
-          const double x = __ldcg(bp + i), y = __ldcg(bq + i);
-          bp[i] = cs * x - sn * y;
-          bq[i] = sn * x + cs * y;
-        }
         double *yp = Yw + (int64_t)p * K, *yq = Yw + (int64_t)q * K;
-        for (int i = lane; i < K; i += 32) {
-          const double x = __ldcg(yp + i), y = __ldcg(yq + i);
-          yp[i] = cs * x - sn * y;
-          yq[i] = sn * x + cs * y;
+        if constexpr (NL > 0) {
+          double xb[NL], yb[NL], xy[NL], yy[NL];
+#pragma unroll
+          for (int e = 0; e < NL; ++e) {
+            const int i = lane + 32 * e;
+            xb[e] = yb[e] = xy[e] = yy[e] = 0.0;
+            if (i < K) {
+              xb[e] = __ldcg(bp + i);
+              yb[e] = __ldcg(bq + i);
+              xy[e] = __ldcg(yp + i);
+              yy[e] = __ldcg(yq + i);
+            }
+          }
+          double a = 0.0, b = 0.0, c = 0.0;
+#pragma unroll
+          for (int e = 0; e < NL; ++e) {
+            if (lane + 32 * e < K) {
+              a = fma(xb[e], xb[e], a);
+              b = fma(yb[e], yb[e], b);
+              c = fma(xb[e], yb[e], c);
+            }
+          }
+          a = warp_sum_d(a);
+          b = warp_sum_d(b);
+          c = warp_sum_d(c);
+          if (c == 0.0 || fabs(c) <= tol * sqrt(a) * sqrt(b)) continue;
+          if (lane == 0) *s_rot = 1;
+          const double zeta = (b - a) / (2.0 * c);
+          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                              : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+#pragma unroll
+          for (int e = 0; e < NL; ++e) {
+            const int i = lane + 32 * e;
+            if (i < K) {
+              bp[i] = cs * xb[e] - sn * yb[e];
+              bq[i] = sn * xb[e] + cs * yb[e];
+              yp[i] = cs * xy[e] - sn * yy[e];
+              yq[i] = sn * xy[e] + cs * yy[e];
+            }
+          }
+        } else {
+          double a = 0.0, b = 0.0, c = 0.0;
+          for (int i = lane; i < K; i += 32) {
+            const double x = __ldcg(bp + i), y = __ldcg(bq + i);
+            a = fma(x, x, a);
+            b = fma(y, y, b);
+            c = fma(x, y, c);
+          }
+          a = warp_sum_d(a);
+          b = warp_sum_d(b);
+          c = warp_sum_d(c);
+          if (c == 0.0 || fabs(c) <= tol * sqrt(a) * sqrt(b)) continue;
+          if (lane == 0) *s_rot = 1;
+          // rotation that makes columns p and q orthogonal (Rutishauser's formula)
+          const double zeta = (b - a) / (2.0 * c);
+          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                              : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = lane; i < K; i += 32) {
+            const double x = __ldcg(bp + i), y = __ldcg(bq + i);
+            bp[i] = cs * x - sn * y;
+            bq[i] = sn * x + cs * y;
+          }
+          for (int i = lane; i < K; i += 32) {
+            const double x = __ldcg(yp + i), y = __ldcg(yq + i);
+            yp[i] = cs * x - sn * y;
+            yq[i] = sn * x + cs * y;
+          }
         }
       }
       cl.sync();

@@ -48,6 +48,8 @@ __global__ void k_assemble_B(double *__restrict__ Bm, int K, int l, const double
   }
 }
 
+// NL: elements of a column per lane held in registers during a rotation (0: none, any K)
+template <int NL>
 __global__ void __launch_bounds__(256) k_jacobi_cluster(double *__restrict__ B, double *__restrict__ Yw, int K,
                                                         double *__restrict__ sigma, double *__restrict__ X,
                                                         double *__restrict__ Y, double *__restrict__ nrm,
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double *__restrict__ B, 
   cg::cluster_group cl = cg::this_cluster();
   if (halted(ctl)) return;  // every CTA of the cluster sees the same flag
   __shared__ int s_rot, s_any;
-  const int sw = dev::cluster_jacobi(cl, B, Yw, K, sigma, X, Y, nrm, pos, &s_rot, &s_any);
+  const int sw = dev::cluster_jacobi<NL>(cl, B, Yw, K, sigma, X, Y, nrm, pos, &s_rot, &s_any);
   if (cl.block_rank() == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
 }
 
@@ -177,12 +179,20 @@ cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const doub
 
 cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
                       int *sweeps, const Ctl *ctl, cudaStream_t s) {
+  // registers per lane for a column pair: the smallest of 1, 2, 4, 8, 16 covering K (K <= 512)
+  using Kern = void (*)(double *, double *, int, double *, double *, double *, double *, int *, int *, const Ctl *);
+  Kern kern = K <= 32 ? k_jacobi_cluster<1>
+            : K <= 64 ? k_jacobi_cluster<2>
+            : K <= 128 ? k_jacobi_cluster<4>
+            : K <= 256 ? k_jacobi_cluster<8>
+            : K <= 512 ? k_jacobi_cluster<16>
+                       : k_jacobi_cluster<0>;
   // cluster size: enough warps for the Kp/2 pairs of a round (8 per CTA), a power of two up to 16
   const int pairs = (K + (K & 1)) / 2;
   int want = 1;
   while (want < 16 && want * 8 < pairs) want *= 2;
   {
-    const cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   for (int cs = want; cs >= 1; cs /= 2) {
@@ -199,12 +209,12 @@ cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, d
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int maxc = 0;
-    if (cudaOccupancyMaxPotentialClusterSize(&maxc, k_jacobi_cluster, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxPotentialClusterSize(&maxc, kern, &cfg) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     if (maxc < cs) continue;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Bm, Yw, K, sigma, X, Y, nrm, pos, sweeps, ctl);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, Bm, Yw, K, sigma, X, Y, nrm, pos, sweeps, ctl);
     if (e == cudaSuccess) {
       note_launch();
       return cudaSuccess;
