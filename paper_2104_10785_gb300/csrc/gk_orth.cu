@@ -13,6 +13,8 @@
 // applies the judgement and the second pass's three kernels, launched anyway,
 // return at entry (ctl->pass2 = 0); otherwise they run.  Without cancellation the
 // basis is read twice.
+// Vectors of at most 8192 entries (with len * j <= 2^18) take one kernel, k_cgs_small,
+// that runs the same passes, rule, norm and judgement in a single CTA.
 // Partial sums are written per row chunk and reduced in a fixed order, so the
 // results are bitwise reproducible.  The last block of the norm kernel applies
 // the break / breakdown test and records the event in the control block; every
@@ -261,6 +263,83 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_norm(const double *__re
   }
 }
 
+// Short vectors (len <= kSmallLen, len * j <= kSmallWork): the whole Gram-Schmidt of the
+// orthonormalize() contract -- the passes (or the adaptive rule), the norm and the
+// judgement -- in one CTA with w in shared memory, instead of six launches whose latency a
+// vector of a few thousand entries cannot hide.  Sums are fixed-order (reproducible).
+constexpr int64_t kSmallLen = 8192;
+constexpr int64_t kSmallWork = 1 << 18;
+constexpr int kSmallThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallThreads, 1) k_cgs_small(const double *__restrict__ Q, int64_t ld, int64_t len,
+                                                             int j, double *__restrict__ w, Ctl *ctl, NormArgs a,
+                                                             int passes) {
+  if (halted(ctl)) return;
+  extern __shared__ double dyn[];
+  double *ws = dyn;        // len
+  double *hs = dyn + len;  // j
+  __shared__ double red[kSmallThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) ws[i] = w[i];
+  __syncthreads();
+  auto norm2 = [&]() -> double {
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) v = fma(ws[i], ws[i], v);
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += red[k];
+    __syncthreads();  // red is reused by the next call
+    return t;
+  };
+  auto pass = [&]() {  // h = Q^T w; w -= Q h (eight independent loads in flight per lane)
+    for (int c = warp; c < j; c += nw) {
+      const double *q = Q + (int64_t)c * ld;
+      double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      int64_t i = lane;
+      for (; i + 7 * 32 < len; i += 8 * 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = fma(q[i + 32 * u], ws[i + 32 * u], v[u]);
+      }
+      for (; i < len; i += 32) v[0] = fma(q[i], ws[i], v[0]);
+      double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+      t = warp_sum(t);
+      if (lane == 0) hs[c] = t;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+      double acc = ws[i];
+      int c = 0;
+      for (; c + 8 <= j; c += 8) {
+        double qv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) qv[u] = Q[(int64_t)(c + u) * ld + i];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(-qv[u], hs[c + u], acc);
+      }
+      for (; c < j; ++c) acc = fma(-Q[(int64_t)c * ld + i], hs[c], acc);
+      ws[i] = acc;
+    }
+    __syncthreads();
+  };
+  double tot;
+  if (j > 0 && passes >= 0) {
+    const double before = passes == 0 ? norm2() : 0.0;
+    const int np = passes == 0 ? 1 : passes;
+    for (int p = 0; p < np; ++p) pass();
+    tot = norm2();
+    if (passes == 0 && tot < 0.5 * before) {  // the first pass cancelled: a second one decides
+      pass();
+      tot = norm2();
+    }
+  } else {
+    tot = norm2();
+  }
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) w[i] = ws[i];
+  if (threadIdx.x == 0) judge(ctl, tot, a);
+}
+
 __global__ void k_normalize_append(const double *__restrict__ w, int64_t len, double *__restrict__ q,
                                    float *__restrict__ x32, const Ctl *ctl) {
   if (halted(ctl)) return;
@@ -374,6 +453,16 @@ int cgs_blocks(int64_t len, const Dev &d) {
 cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
                            double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
                            cudaStream_t s, const Dev &d) {
+  if (len <= kSmallLen && len * (int64_t)(j > 0 ? j : 1) <= kSmallWork) {
+    const size_t dyn = sizeof(double) * (size_t)(len + (j > 0 ? j : 1));  // <= (8192 + 1025) doubles
+    if (dyn > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_cgs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+    }
+    GK_LAUNCH(k_cgs_small<<<1, kSmallThreads, dyn, s>>>(Q, ld, len, j, w, ctl,
+                                                          NormArgs{mode, step, side, coef_out, prev}, passes));
+    return cudaGetLastError();
+  }
   const int S = cgs_chunk(len, d);
   const int G = (int)((len + S - 1) / S);
   double *npart = part + (int64_t)G * (j > 0 ? j : 1);
