@@ -251,6 +251,25 @@ def test_reorthogonalization_modes_match_oracle(passes):
     assert r == r_o == 40
 
 
+@pytest.mark.parametrize("shape", [(9000, 300), (300, 9000)])
+@pytest.mark.parametrize("passes", [0, 1, 2])
+def test_reorthogonalization_modes_multiblock(passes, shape):
+    """Vectors longer than 8192 entries take the multi-block Gram-Schmidt kernels (shorter ones
+    the one-CTA kernel): each rule on a 9000-entry side agrees with the oracle's partial SVD."""
+    m, n = shape
+    sig = synth.sigma_geometric(min(m, n), 0.9)
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, seed=41)
+    q1 = synth.start_vector(m, 41)
+    M = gk()
+    At, qt = torch.from_numpy(A).cuda(), torch.from_numpy(q1).cuda()
+    U, S, V, st, info = M.gk_psvd(At, 8, 1e-10, krylov_dim=24, reorth_passes=passes, start=qt)
+    Uo, So, Vo, io = oracle.psvd(oracle.Operator.dense(A), 8, 24, q1, tol=1e-10, passes=passes, max_restarts=300)
+    assert st == 0
+    np.testing.assert_allclose(S.cpu().numpy(), So, rtol=1e-10)
+    assert angle_err(V.cpu().numpy(), Vo) <= 1e-8
+    assert abs(info["restarts"] - io["restarts"]) <= 1
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 def test_psvd_reduced_precision_storage(dtype):
     """sigma_i = i^-1.5 spectrum stored in f32 / bf16; parity with the oracle on the stored bytes."""
