@@ -164,6 +164,24 @@ size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *opts);
 int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, int *rank, double *sigma,
                gk_info *info);
 
+/* F-SVD as printed (Algorithm 2): k steps of Algorithm 1 (lower-bidiagonal GK
+ * with reorthogonalization; only an exact zero norm ends them early), the SVD
+ * of B_{k'+1,k'} = X Sigma Y^T (one-sided Jacobi, the route to eig(B^T B)
+ * without forming B^T B), V = P Y, and, for the r largest:
+ *  route 1: u_i = Q x_i (the left Ritz vectors, Eq. 2.13);
+ *  route 0: u_i = A v_i / sigma_i (the printed formula, one product per
+ *           triplet), which equals Q x_i in exact arithmetic.
+ * No restart: the accuracy is what k steps give (compare gk_psvd).
+ *  k:   Krylov steps, 1 <= k <= min(m, n), k <= 1023.
+ *  r:   triplets wanted, 1 <= r <= k.
+ *  U:   m x r, column-major, f64 (device or host); S: r values, descending;
+ *  V:   n x r, column-major, f64.  Signs as in gk_psvd.
+ * Returns GK_OK, GK_RANK_DEFICIENT when Algorithm 1 stopped at k' < r (the
+ * trailing triplets are zero), GK_NOT_CONVERGED when the Jacobi sweeps hit
+ * their limit, or an error.  info->kprime = k'. */
+int gk_fsvd(const gk_matrix *A, int k, int r, int route, const gk_opts *opts, double *U, double *S, double *V,
+            gk_info *info);
+
 /* y = A x (trans = 0; x: n, y: m) or y = A^T x (trans = 1; x: m, y: n), f64
  * vectors (device or host).  These are the products of Eq. 2.2 (Algorithm 1)
  * run by the same kernels as the sweep: f32/bf16/f16 operators

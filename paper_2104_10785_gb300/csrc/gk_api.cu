@@ -713,45 +713,16 @@ int64_t clamp_kmax(const gk_matrix *A, int kmax) {
   return (kmax <= 0 || kmax > mn) ? mn : kmax;
 }
 
-int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *oin, int *rank, double *sigma,
-                 gk_info *info) {
-  const auto t0 = std::chrono::steady_clock::now();
-  const int64_t l0 = launch_count();
-  g_err[0] = 0;
-  gk_info inf;
-  memset(&inf, 0, sizeof(inf));
-  if (info) *info = inf;
-  Dev d;
-  if (!get_device(&d)) return GK_NO_DEVICE;
-  int rc = check_matrix(Ain);
-  if (rc) return rc;
-  if (!rank || !(eps >= 0.0) || !isfinite(eps)) return GK_INVALID_ARG;
-  const gk_opts o = oin ? *oin : defaults();
-  if (o.reorth_passes < 0 || o.reorth_passes > 3) return GK_INVALID_ARG;
-  const int64_t kmax = clamp_kmax(Ain, kmax_in);
-  cudaStream_t s = (cudaStream_t)o.stream;
-  OpStage st;
-  rc = stage_plan(Ain, &st);
-  if (rc) return rc;
-  const bool host_sigma = sigma && on_host(sigma);
-  const bool host_start = o.start && on_host(o.start);
-  Op op = make_op(Ain);
-  RankBufs b;
-  const size_t bytes = numrank_layout(Ain, kmax, d, st, host_sigma, host_start, nullptr, &b, &op);
-  Workspace ws;
-  rc = acquire(ws, bytes, o, s);
-  if (rc) return rc;
-  op = make_op(Ain);
-  numrank_layout(Ain, kmax, d, st, host_sigma, host_start, ws.base, &b, &op);
-  rc = stage_copy(Ain, st, op, s);
-  if (rc) return rc;
-
+// Algorithm 1 on the staged operator: q1 (given or drawn), then up to kmax steps of the
+// lower bidiagonalization with the break test (threshold eps, relative to the running
+// sigma estimate when eps_rel), in chunks of 8 steps between reads of the control block.
+// Leaves Q (k'+1 columns), P, alpha, beta in b; *kp_out = k'; fills matvecs, stop_reason.
+int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &b, int64_t kmax, double eps,
+                int eps_rel, bool host_start, Prof &prof, gk_info &inf, HostCtl &hc, int *kp_out, cudaStream_t s,
+                const Dev &d) {
   const int64_t m = Ain->m, n = Ain->n, ldu = round_up(m, 32), ldv = round_up(n, 32);
   const int passes = o.reorth_passes;
-  const int eps_rel = o.eps_absolute ? 0 : 1;
-  Prof prof;
-  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
-  prof.s = s;
+  int rc = GK_OK;
   GK_CUDA(reset_ctl(b.ctl, eps, eps_rel, s));
   GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (kmax + 2), s));
   GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (kmax + 2), s));
@@ -773,10 +744,9 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   GK_CUDA(orthonormalize(b.z, n, b.P, ldv, 0, 0, b.part, b.h, b.ctl, NM_BREAK, 0, 1, b.alpha, nullptr, s, d));
   GK_CUDA(normalize_append(b.z, n, b.P, b.x32, b.ctl, s, d));
   inf.matvecs = 1;
-  HostCtl hc;
   rc = read_ctl(b.ctl, nullptr, &hc, s);
   if (rc) return rc;
-  // lines 4-17, in chunks of steps between reads of the control block
+  // the remaining steps, in chunks between reads of the control block
   const int chunk = 8;
   int64_t j = 1;
   while (!hc.ctl.halt && j <= kmax) {
@@ -818,6 +788,51 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
     inf.stop_reason = 0;
     inf.matvecs += 2 * (int64_t)kp;
   }
+  *kp_out = kp;
+  return GK_OK;
+}
+
+int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *oin, int *rank, double *sigma,
+                 gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  g_err[0] = 0;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  if (info) *info = inf;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  if (!rank || !(eps >= 0.0) || !isfinite(eps)) return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  if (o.reorth_passes < 0 || o.reorth_passes > 3) return GK_INVALID_ARG;
+  const int64_t kmax = clamp_kmax(Ain, kmax_in);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  OpStage st;
+  rc = stage_plan(Ain, &st);
+  if (rc) return rc;
+  const bool host_sigma = sigma && on_host(sigma);
+  const bool host_start = o.start && on_host(o.start);
+  Op op = make_op(Ain);
+  RankBufs b;
+  const size_t bytes = numrank_layout(Ain, kmax, d, st, host_sigma, host_start, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, s);
+  if (rc) return rc;
+  op = make_op(Ain);
+  numrank_layout(Ain, kmax, d, st, host_sigma, host_start, ws.base, &b, &op);
+  rc = stage_copy(Ain, st, op, s);
+  if (rc) return rc;
+
+  const int eps_rel = o.eps_absolute ? 0 : 1;
+  Prof prof;
+  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
+  prof.s = s;
+  HostCtl hc;
+  int kp = 0;
+  rc = lower_sweep(Ain, o, op, b, kmax, eps, eps_rel, host_start, prof, inf, hc, &kp, s, d);
+  if (rc) return rc;
   inf.kprime = kp;
   inf.steps = kp;
   // Algorithm 3: singular values of B_{k'+1,k'} above the threshold
@@ -836,6 +851,134 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   inf.launches = launch_count() - l0;
   if (info) *info = inf;
   return GK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gk_fsvd: Algorithm 2 as printed (k steps of Algorithm 1, the SVD of B_{k'+1,k'}, no restart)
+// ---------------------------------------------------------------------------
+struct FsvdBufs {
+  double *Bm, *Yw, *X, *Y, *sigma, *nrm, *Uo, *So, *Vo;
+  int *pos, *sweeps;
+};
+
+size_t fsvd_layout(char *base, int k, int r, int64_t m, int64_t n, bool host_out, FsvdBufs *f) {
+  Carve cv{base, 0};
+  const size_t K = (size_t)k + 1;
+  f->Bm = cv.take<double>(K * K);
+  f->Yw = cv.take<double>(K * K);
+  f->X = cv.take<double>(K * K);
+  f->Y = cv.take<double>(K * K);
+  f->sigma = cv.take<double>(K);
+  f->nrm = cv.take<double>(K);
+  f->pos = cv.take<int>(K);
+  f->sweeps = cv.take<int>(1);
+  f->Uo = host_out ? cv.take<double>((size_t)m * r) : nullptr;
+  f->So = host_out ? cv.take<double>((size_t)r) : nullptr;
+  f->Vo = host_out ? cv.take<double>((size_t)n * r) : nullptr;
+  return cv.off + 256;
+}
+
+int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin, double *U, double *S, double *V,
+              gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  g_err[0] = 0;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  if (info) *info = inf;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  const int64_t m = Ain->m, n = Ain->n, ldu = round_up(m, 32), ldv = round_up(n, 32);
+  const int64_t mn = m < n ? m : n;
+  if (k < 1 || k > mn || k > 1023 || r < 1 || r > k || (route != 0 && route != 1) || !U || !S || !V)
+    return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  if (o.reorth_passes < 0 || o.reorth_passes > 3) return GK_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  OpStage st;
+  rc = stage_plan(Ain, &st);
+  if (rc) return rc;
+  const bool host_start = o.start && on_host(o.start);
+  const bool host_out = on_host(U) || on_host(S) || on_host(V);
+  Op op = make_op(Ain);
+  RankBufs b;
+  FsvdBufs f;
+  const size_t nb = (numrank_layout(Ain, k, d, st, false, host_start, nullptr, &b, &op) + 255) / 256 * 256;
+  const size_t fb = fsvd_layout(nullptr, k, r, m, n, host_out, &f);
+  Workspace ws;
+  rc = acquire(ws, nb + fb, o, s);
+  if (rc) return rc;
+  op = make_op(Ain);
+  numrank_layout(Ain, k, d, st, false, host_start, ws.base, &b, &op);
+  fsvd_layout(ws.base + nb, k, r, m, n, host_out, &f);
+  rc = stage_copy(Ain, st, op, s);
+  if (rc) return rc;
+  Prof prof;
+  prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
+  prof.s = s;
+  HostCtl hc;
+  int kp = 0;
+  // k steps of Algorithm 1; with the absolute threshold 0 only an exact zero ends them early
+  rc = lower_sweep(Ain, o, op, b, k, 0.0, 0, host_start, prof, inf, hc, &kp, s, d);
+  if (rc) return rc;
+  inf.kprime = kp;
+  inf.steps = kp;
+  double *Uo = host_out ? f.Uo : U, *Vo = host_out ? f.Vo : V, *So = host_out ? f.So : S;
+  GK_CUDA(cudaMemsetAsync(Uo, 0, sizeof(double) * (size_t)m * r, s));
+  GK_CUDA(cudaMemsetAsync(Vo, 0, sizeof(double) * (size_t)n * r, s));
+  GK_CUDA(cudaMemsetAsync(So, 0, sizeof(double) * (size_t)r, s));
+  const int rr = r < kp ? r : kp;
+  int sweeps = 0;
+  if (kp > 0) {
+    // a break on the left side appended no q_{k'+1}: its column of Q is zero (beta_{k'+1} = 0)
+    if (hc.ctl.halt && hc.ctl.side == 0) GK_CUDA(cudaMemsetAsync(b.Q + (int64_t)kp * ldu, 0, sizeof(double) * m, s));
+    rc = clear_halt(b.ctl, s);
+    if (rc) return rc;
+    const int K = kp + 1;
+    prof.begin(PC_SMALL);
+    GK_CUDA(assemble_lower(f.Bm, kp, b.alpha, b.beta, s));
+    GK_CUDA(small_svd(f.Bm, f.Yw, K, f.sigma, f.X, f.Y, f.nrm, f.pos, f.sweeps, b.ctl, s));
+    prof.end();
+    prof.begin(PC_RESTART);
+    // V = P Y: the first kp rows of Y (the zero padding column is never rotated)
+    GK_CUDA(ritz_gemm(b.P, ldv, n, kp, f.Y, K, rr, Vo, n, s, d));
+    if (route == 1) {
+      GK_CUDA(ritz_gemm(b.Q, ldu, m, K, f.X, K, rr, Uo, m, s, d));
+    } else {
+      // the printed route: u_i = A v_i / sigma_i, one product per triplet
+      for (int i = 0; i < rr; ++i) {
+        double *vi = Vo + (int64_t)i * n, *ui = Uo + (int64_t)i * m;
+        GK_CUDA(copy_vec(nullptr, b.x32, vi, n, s));
+        GK_CUDA(matvec(op, b.x32, vi, ui, nullptr, nullptr, b.part, b.ctl, s, d));
+        GK_CUDA(scale_inv(ui, m, f.sigma + i, s));
+      }
+      inf.matvecs += rr;
+    }
+    prof.end();
+    GK_CUDA(cudaMemcpyAsync(So, f.sigma, sizeof(double) * rr, cudaMemcpyDeviceToDevice, s));
+    GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, rr, s));
+    GK_CUDA(cudaMemcpyAsync(&sweeps, f.sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  if (host_out) {
+    prof.begin(PC_COPY);
+    GK_CUDA(cudaMemcpyAsync(U, Uo, sizeof(double) * (size_t)m * r, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(V, Vo, sizeof(double) * (size_t)n * r, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(S, So, sizeof(double) * (size_t)r, cudaMemcpyDeviceToHost, s));
+    prof.end();
+  }
+  GK_CUDA(cudaMemcpyAsync(&hc.ctl, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  prof.finish(&inf);
+  inf.svd_sweeps = sweeps;
+  inf.sigma_est = hc.ctl.sest;
+  inf.seconds = seconds_since(t0);
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  if (hc.ctl.timeout) return GK_TIMEOUT;
+  if (sweeps < 0) return GK_NOT_CONVERGED;
+  return rr < r ? GK_RANK_DEFICIENT : GK_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1005,6 +1148,12 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
                gk_info *info) {
   NvtxRange r("gk_numrank");
   return numrank_impl(A, eps, kmax, opts, rank, sigma, info);
+}
+
+int gk_fsvd(const gk_matrix *A, int k, int r, int route, const gk_opts *opts, double *U, double *S, double *V,
+            gk_info *info) {
+  NvtxRange nv("gk_fsvd");
+  return fsvd_impl(A, k, r, route, opts, U, S, V, info);
 }
 
 int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const gk_opts *opts) {

@@ -1409,7 +1409,7 @@ __device__ void solve_numrank(cg::cluster_group &cl, const BProb &P, BWork W, co
   res.steps = kp;
   res.sigma_est = sest;
   cl.sync();
-  // lines 3-4 on one CTA: the singular values of B_{k'+1,k'} above the threshold
+  // Algorithm 3's count on one CTA: the singular values of B_{k'+1,k'} above the threshold
   if (rank == 0) {
     __shared__ int s_rank;
     __shared__ double s_s1;

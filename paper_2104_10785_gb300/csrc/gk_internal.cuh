@@ -163,6 +163,11 @@ cudaError_t reset_ctl(Ctl *ctl, double eps, int eps_rel, cudaStream_t s);
 // for j >= l.
 cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const double *rho, const double *alpha,
                        const double *beta, const Ctl *ctl, cudaStream_t s);
+// Bm = the lower-bidiagonal B_{kp+1,kp} (alpha[0..kp-1] on the diagonal, beta[1..kp] below it)
+// padded with a zero column to (kp+1) x (kp+1), column-major
+cudaError_t assemble_lower(double *Bm, int kp, const double *alpha, const double *beta, cudaStream_t s);
+// y[0:len] /= *d (unchanged when *d <= 0)
+cudaError_t scale_inv(double *y, int64_t len, const double *d, cudaStream_t s);
 // One-sided Jacobi SVD of the K x K matrix Bm (overwritten; Yw is K x K work,
 // nrm/pos K-entry work) on one thread-block cluster: sigma (K, descending),
 // X (K x K left vectors), Y (K x K right vectors), sweeps (negative if the

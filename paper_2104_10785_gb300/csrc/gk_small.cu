@@ -48,6 +48,33 @@ __global__ void k_assemble_B(double *__restrict__ Bm, int K, int l, const double
   }
 }
 
+// The lower-bidiagonal B_{kp+1,kp} of Algorithm 1 (alpha_1..alpha_kp on the diagonal,
+// beta_2..beta_{kp+1} below it: alpha[c] at (c, c), beta[c + 1] at (c + 1, c)) padded with a
+// zero last column to the square K = kp + 1 (column-major) that the Jacobi kernel takes.
+__global__ void k_assemble_lower(double *__restrict__ Bm, int kp, const double *__restrict__ alpha,
+                                 const double *__restrict__ beta) {
+  const int K = kp + 1;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)K * K;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % K), c = (int)(idx / K);
+    double v = 0.0;
+    if (c < kp) {
+      if (r == c) v = alpha[c];
+      else if (r == c + 1) v = beta[c + 1];
+    }
+    Bm[idx] = v;
+  }
+}
+
+// y[i] /= *d for i < len (left as is when *d is not positive)
+__global__ void k_scale_inv(double *__restrict__ y, int64_t len, const double *__restrict__ d) {
+  const double v = *d;
+  if (!(v > 0.0)) return;
+  const double f = 1.0 / v;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] *= f;
+}
+
 // NL: elements of a column per lane held in registers during a rotation (0: none, any K)
 template <int NL>
 __global__ void __launch_bounds__(256) k_jacobi_cluster(double *__restrict__ B, double *__restrict__ Yw, int K,
@@ -174,6 +201,21 @@ cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const doub
   int64_t blocks = ((int64_t)K * K + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   GK_LAUNCH(k_assemble_B<<<(int)blocks, 256, 0, s>>>(Bm, K, l, sigma, rho, alpha, beta, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t assemble_lower(double *Bm, int kp, const double *alpha, const double *beta, cudaStream_t s) {
+  int64_t blocks = ((int64_t)(kp + 1) * (kp + 1) + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  GK_LAUNCH(k_assemble_lower<<<(int)blocks, 256, 0, s>>>(Bm, kp, alpha, beta));
+  return cudaGetLastError();
+}
+
+cudaError_t scale_inv(double *y, int64_t len, const double *d, cudaStream_t s) {
+  int64_t blocks = (len + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  GK_LAUNCH(k_scale_inv<<<(int)blocks, 256, 0, s>>>(y, len, d));
   return cudaGetLastError();
 }
 

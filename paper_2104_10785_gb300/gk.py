@@ -106,6 +106,9 @@ def lib():
             L.gk_numrank.argtypes = [P(gk_matrix), C.c_double, C.c_int, P(gk_opts), P(C.c_int), C.c_void_p,
                                      P(gk_info)]
             L.gk_numrank.restype = C.c_int
+            L.gk_fsvd.argtypes = [P(gk_matrix), C.c_int, C.c_int, C.c_int, P(gk_opts), C.c_void_p, C.c_void_p,
+                                  C.c_void_p, P(gk_info)]
+            L.gk_fsvd.restype = C.c_int
             L.gk_matvec.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
             L.gk_matvec.restype = C.c_int
             L.gk_residuals.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -300,6 +303,28 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     st = lib().gk_psvd(C.byref(M), int(k), float(tol), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
     if check and st < 0:
         raise GKError(st, "gk_psvd")
+    return U.T, S, V.T, st, info.as_dict()
+
+
+def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = None, seed: int | None = None,
+            start=None, stream=None, workspace=None, scale: float = 1.0, check: bool = True, profile: bool = False):
+    """Algorithm 2 as printed: k steps of Algorithm 1, the SVD of B, the r largest triplets
+    (route 1: U = Q X; route 0: u_i = A v_i / sigma_i).  Returns (U m x r, S r, V n x r, status,
+    info dict); outputs live where A lives."""
+    M, keep_a = make_matrix(A, scale)
+    dev = A.device
+    if dev.type != "cuda" and not torch.cuda.is_available():
+        raise RuntimeError("gk_fsvd needs a CUDA device (no host fallback)")
+    pin = dev.type == "cpu"
+    U = torch.empty((r, M.m), dtype=torch.float64, device=dev, pin_memory=pin)
+    V = torch.empty((r, M.n), dtype=torch.float64, device=dev, pin_memory=pin)
+    S = torch.empty(r, dtype=torch.float64, device=dev, pin_memory=pin)
+    o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), 0, 0, None, reorth_passes, False, seed, start,
+                  stream, workspace, profile)
+    info = gk_info()
+    st = lib().gk_fsvd(C.byref(M), int(k), int(r), int(route), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
+    if check and st < 0:
+        raise GKError(st, "gk_fsvd")
     return U.T, S, V.T, st, info.as_dict()
 
 
