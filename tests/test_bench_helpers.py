@@ -1,0 +1,62 @@
+"""Host-side helpers of bench.py (no GPU): the ncu-figure lookup keyed by the kernel source's
+md5, the Gram-Schmidt work count, the products' algorithmic bytes, the host page report."""
+import hashlib
+import os
+
+import pytest
+import torch
+
+import bench
+
+
+def _fake_tree(tmp_path, src_text, lines):
+    csrc = tmp_path / "paper_2104_10785_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "gk_matvec.cu").write_text(src_text)
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "k.md").write_text("\n".join(lines) + "\n")
+    return hashlib.md5(src_text.encode()).hexdigest()
+
+
+def test_profiled_traffic_reads_the_line_for_the_current_source(tmp_path, monkeypatch):
+    h = _fake_tree(tmp_path, "kernel source\n", [])
+    (tmp_path / "profiles" / "k.md").write_text(
+        f"roofline-traffic: kernel=kA workload=w1 bytes_per_launch=123456 source_md5={h}\n"
+        f"roofline-traffic: kernel=kB workload=w1 ratio=0.9647 source_md5={h}\n"
+        f"roofline-traffic: kernel=kA workload=w2 bytes_per_launch=7 source_md5={'0' * 32}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("kA", "w1") == 123456
+    assert bench.profiled_traffic("kB", "w1", field="ratio") == pytest.approx(0.9647)
+    assert bench.profiled_traffic("kA", "w2") is None  # captured from another source
+    assert bench.profiled_traffic("kC", "w1") is None
+    # editing the kernel source retires every figure taken from it
+    (tmp_path / "paper_2104_10785_gb300" / "csrc" / "gk_matvec.cu").write_text("changed\n")
+    assert bench.profiled_traffic("kA", "w1") is None
+
+
+def test_orth_work_counts_one_pass_per_column_and_entry():
+    m, n, K = 7, 5, 4
+    fl, by = bench.orth_work(m, n, K, 0, 1)
+    # step j: the m-vector against j columns, the n-vector against j + 1; 4 flops per entry
+    # and column (dot and update), 16 bytes per entry and column plus 24 per entry
+    assert fl == sum(4 * (m * j + n * (j + 1)) for j in range(K))
+    assert by == sum(16 * (m * j + n * (j + 1)) + 24 * (m + n) for j in range(K))
+    fl2, _ = bench.orth_work(m, n, K, 0, 1, passes=2)
+    assert fl2 == 2 * fl
+    # a restarted cycle starts after the kept columns
+    fl3, _ = bench.orth_work(m, n, K, 2, 2)
+    assert fl3 == fl + sum(4 * (m * j + n * (j + 1)) for j in range(2, K))
+
+
+def test_algorithmic_bytes_of_dense_products():
+    A = torch.empty((6, 10), dtype=torch.bfloat16)
+    w = {"m": 6, "n": 10, "A": A}
+    assert bench.algorithmic_bytes(w, "matvec") == 2 * 60 + 4 * 10 + 16 * 6
+    assert bench.algorithmic_bytes(w, "matvec_t") == 2 * 60 + 4 * 6 + 16 * 10
+
+
+def test_host_page_report_has_the_mode():
+    rep = bench.host_page_report()
+    assert "thp" in rep
+    if os.path.exists("/proc/self/smaps_rollup"):
+        assert rep.get("anon_huge_kb", 0) >= 0
