@@ -329,8 +329,9 @@ const char *gk_version(void);
  * gk_host_alloc maps at least `bytes` of anonymous memory aligned to the
  * transparent-huge-page size (the mapping is rounded up to it: 512 MB with
  * 64 KB base pages, 2 MB with 4 KB ones, so carve many small operands from one
- * buffer), asks the kernel to back it with huge pages,
- * zero-fills it and registers it with CUDA (cudaHostRegister); *ptr receives
+ * buffer), asks the kernel to back it with huge pages, zero-fills it, asks
+ * the kernel to collapse any part the first touch left in small pages (Linux
+ * 6.1+, best effort) and registers it with CUDA (cudaHostRegister); *ptr receives
  * the address (owned by the library until gk_host_free).  Errors:
  * GK_INVALID_ARG (null ptr, zero bytes, or an address gk_host_alloc did not
  * return), GK_NO_DEVICE, GK_OUT_OF_MEMORY (mmap), GK_CUDA_ERROR (registration). */
