@@ -142,21 +142,29 @@ def predict_raw(mats, params, bf16=True):
     return gk.gk_mlp_forward(params, feats, bf16_weights=bf16).cpu().numpy()
 
 
+def margins(rf, kf, mn):
+    """(r^, K^) from the network's rank and Krylov estimates (rf, kf) for an operator with
+    min(m, n) = mn: r^ = ceil(1.05 rf) + 1 and K^ = ceil(kf) + 2 shifted by the same margin,
+    clamped to 1 <= r^ <= K^ <= min(mn, K_LIMIT) with K^ >= r^ + 2 where there is room; a
+    non-finite estimate asks for the whole range."""
+    lim = min(mn, K_LIMIT)
+    if not math.isfinite(rf):
+        rf = float(lim)
+    if not math.isfinite(kf):
+        kf = float(lim)
+    ri = int(min(max(1, math.ceil(RANK_MARGIN[0] * rf) + RANK_MARGIN[1]), max(1, lim - 1)))
+    Ki = int(math.ceil(kf)) + K_MARGIN + (ri - int(round(rf)))
+    Ki = int(min(max(Ki, ri + 2), lim))
+    return ri, max(Ki, ri)
+
+
 def predict(mats, params, bf16=True):
     """(r^, K^) per operator: the rank rounded up with the safety margin, K^ >= r^ + 2."""
     out = predict_raw(mats, params, bf16)
     with np.errstate(over="ignore", invalid="ignore"):
         rc = np.exp(np.clip(out[:, 0], -20.0, 20.0))
         kc = np.exp(np.clip(out[:, 1], -20.0, 20.0))
-    res = []
-    for A, rf, kf in zip(mats, rc, kc):
-        mn = min(A.shape)
-        lim = min(mn, K_LIMIT)
-        ri = int(min(max(1, math.ceil(RANK_MARGIN[0] * rf) + RANK_MARGIN[1]), lim - 1))
-        Ki = int(math.ceil(kf)) + K_MARGIN + (ri - int(round(rf)))
-        Ki = int(min(max(Ki, ri + 2), lim))
-        res.append((ri, Ki))
-    return res
+    return [margins(float(rf), float(kf), min(A.shape)) for A, rf, kf in zip(mats, rc, kc)]
 
 
 def plain_batched(mats, eps=1e-5, tol=1e-8, autotune=True):
