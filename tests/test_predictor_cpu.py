@@ -55,3 +55,33 @@ def test_k_grid_offsets_then_the_fallback():
         g = P.k_grid(r, mn)
         assert len(set(g)) == len(g) and all(K <= mn for K in g)
         assert all(r < K for K in g) or g == [mn]
+
+
+def test_learned_batched_judges_each_prediction_and_re_solves_the_short_ones(monkeypatch):
+    """A solve is accepted when its spectrum shows a value below the cut (reported rank < k, or
+    sigma_{k+1} <= eps sigma_1); otherwise the problem goes to the plain pipeline."""
+    mats = [torch.empty(40, 30) for _ in range(3)]
+    monkeypatch.setattr(P, "predict", lambda m, p: [(3, 8)] * len(m))
+
+    def fake_psvd_batched(probs, **kw):
+        assert all(p["rank_cut"] == 1e-5 and p["k"] == 3 and p["krylov_dim"] == 8 for p in probs)
+        rr = [dict(status=0, rank=2, sigma_next=0.5, matvecs=17),    # a value below the cut: rank 2
+              dict(status=0, rank=3, sigma_next=1e-9, matvecs=17),   # sigma_4 <= eps sigma_1: rank 3
+              dict(status=0, rank=3, sigma_next=1.0, matvecs=17)]    # nothing below: r^ too small
+        out = [(torch.ones(40, 3), torch.tensor([10.0, 5.0, 1.0]), torch.ones(30, 3), r) for r in rr]
+        info = dict(matvecs=51, sigma_1=torch.tensor([10.0, 10.0, 10.0]), outputs=("U", "S", "V"))
+        return out, 0, info
+
+    def fake_plain(ms, eps, tol, autotune=False):
+        assert len(ms) == 1
+        o = (torch.ones(40, 4), torch.tensor([10.0, 5.0, 1.0, 0.5]), torch.ones(30, 4), dict(status=0))
+        return [4], [o], dict(matvecs=40, status=0, matvecs_per_problem=[40])
+
+    monkeypatch.setattr(P.gk, "gk_psvd_batched", fake_psvd_batched)
+    monkeypatch.setattr(P, "plain_batched", fake_plain)
+    ranks, final, info = P.learned_batched(mats, params=None)
+    assert ranks == [2, 3, 4]
+    assert [f[1].numel() for f in final] == [2, 3, 4] and final[0][0].shape == (40, 2)
+    assert info["fallbacks"] == 1 and info["matvecs"] == 51 + 40
+    assert info["matvecs_per_problem"] == [18, 18, 58]  # + one sketch pass each, + the plain re-solve
+    assert info["outputs"] is None  # a re-solved problem's triplets are not in the solve's buffers
