@@ -76,3 +76,30 @@ def test_no_device_means_no_compute():
     assert st == raw.GK_NO_DEVICE
     st = raw.lib().gk_fsvd(C.byref(M), 2, 1, 1, None, U.ctypes.data, S.ctypes.data, V.ctypes.data, None)
     assert st == raw.GK_NO_DEVICE
+
+
+def test_operator_descriptors_from_tensors():
+    """The binding describes what it is given (row stride, storage type, CSR arrays) and
+    refuses layouts the library cannot read, before any call."""
+    import torch
+
+    from paper_2104_10785_gb300 import gk as raw
+
+    buf = torch.zeros(6, 12, dtype=torch.bfloat16)
+    M, keep = raw.make_matrix(buf[:, :10])
+    assert (M.kind, M.dtype, M.m, M.n, M.ld) == (raw.GK_DENSE, raw.GK_BF16, 6, 10, 12)
+    assert M.vals == buf.data_ptr() and keep[0].data_ptr() == buf.data_ptr()
+    for dt, code in ((torch.float64, raw.GK_F64), (torch.float32, raw.GK_F32), (torch.float16, raw.GK_F16)):
+        assert raw.make_matrix(torch.zeros(3, 2, dtype=dt), scale=2.0)[0].dtype == code
+    with pytest.raises(ValueError):
+        raw.make_matrix(torch.zeros(4, 5).T)  # column stride 4
+    with pytest.raises(ValueError):
+        raw.make_matrix(torch.zeros(4, 5, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        raw.make_matrix(torch.zeros(4))
+    i32 = lambda *v: torch.tensor(v, dtype=torch.int32)
+    C = raw.CSR(2, 3, i32(0, 1, 2), i32(0, 2), torch.ones(2), i32(0, 1, 1, 2), i32(0, 1), torch.ones(2))
+    M, _ = raw.make_matrix(C)
+    assert (M.kind, M.dtype, M.m, M.n) == (raw.GK_CSR, raw.GK_F32, 2, 3)
+    with pytest.raises(ValueError):
+        raw.make_matrix(raw.CSR(2, 3, C.rowptr.long(), C.colind, C.vals, C.t_rowptr, C.t_colind, C.t_vals))
