@@ -1047,6 +1047,53 @@ def run_batched_headline(args, rank, world, device):
     }
 
 
+# ---------------------------------------------------------------------------
+# one kernel family on seeded inputs, for ncu captures (nothing is timed or printed as a result)
+# ---------------------------------------------------------------------------
+def profile_case(args):
+    """--case products: A (m x n, N(0,1) drawn by torch's CUDA generator, stored in --dtype) and
+    `reps` calls of gk_matvec(A, x) and gk_matvec(A, y, trans=True).
+    --case psvd: `reps` calls of gk_psvd (k = 16, K = 48, tol 1e-8) on the same kind of operator.
+    --case batched: the first --count problems of the 512-problem batched recipe; `reps` rounds
+    of the learned pipeline's sketch and its batched partial SVD with the committed network's
+    (rank, K); prints the operator bytes the last solve streamed."""
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+    import synth
+
+    torch.cuda.set_device(0)
+    if args.case in ("products", "psvd"):
+        dt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32, "f64": torch.float64}[args.dtype]
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(args.m, args.n, generator=g, device="cuda", dtype=torch.float32).to(dt)
+        x = torch.randn(args.n, generator=g, device="cuda", dtype=torch.float64)
+        y = torch.randn(args.m, generator=g, device="cuda", dtype=torch.float64)
+        for _ in range(args.reps):
+            if args.case == "products":
+                gk.gk_matvec(A, x)
+                gk.gk_matvec(A, y, trans=True)
+            else:
+                gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0)
+    elif args.case == "batched":
+        from paper_2104_10785_gb300 import predictor
+
+        w = synth.WORKLOADS["batched_f32_512_rank5to64"]
+        shapes = synth.batched_shapes(512, w["seed"])[: args.count]
+        mats = synth.torch_batched_products(shapes, 1e-6, w["seed"])
+        params = predictor.load()
+        if params is None:
+            raise SystemExit("trained predictor weights are missing")
+        for _ in range(args.reps):
+            pred = predictor.predict(mats, params)
+            out, _, _ = gk.gk_psvd_batched([dict(A=A, k=r, krylov_dim=K, tol=w["tol"], rank_cut=w["eps"])
+                                            for A, (r, K) in zip(mats, pred)])
+        alg = sum(o[3]["matvecs"] * A.shape[0] * A.shape[1] * 4 for o, A in zip(out, mats))
+        print("algorithmic_bytes_per_launch", alg)
+    torch.cuda.synchronize()
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1063,7 +1110,17 @@ def main():
                     help="time the default workload at its fixed Krylov dimension instead of the learned one")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this kernel")
+    ap.add_argument("--case", default=None, choices=["products", "psvd", "batched"],
+                    help="run one kernel family on seeded inputs for an ncu capture, then exit")
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "f32", "f64"])
+    ap.add_argument("--m", type=int, default=40000)
+    ap.add_argument("--n", type=int, default=20000)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--count", type=int, default=64)
     args = ap.parse_args()
+    if args.case is not None:
+        profile_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1 and args.impl == "gk":

@@ -290,8 +290,9 @@ int gk_mlp_train(float *params, float *adam_m, float *adam_v, int t0, const floa
 /* Size of the device array behind gk_matvec_static (bytes). */
 #define GK_STATIC_SCRATCH_BYTES (32u << 20)
 
-/* gk_matvec_static: y = A x (trans = 0) or y = A^T x (trans = 1) exactly as
- * gk_matvec computes them, but without allocating any device memory.  The
+/* gk_matvec_static: y = A x (trans = 0) or y = A^T x (trans = 1), the product
+ * gk_matvec computes (up to the f32 summation order: A x runs the
+ * row-streaming kernel), but without allocating any device memory.  The
  * paper has no counterpart; this entry point exists for callers that cannot
  * call cudaMalloc: code whose device memory is all owned by another
  * allocator (a framework's caching allocator that has reserved the GPU, so a
@@ -301,10 +302,13 @@ int gk_mlp_train(float *params, float *adam_m, float *adam_v, int t0, const floa
  *    that every GPU loading this library holds until the process exits.
  *    A x needs 256 + 4*max(m,n) bytes of it (it runs the row-streaming
  *    kernel, which keeps no partial sums); dense A^T x also needs its partial
- *    sums, 8*n*(row blocks) bytes (about m*n/128 bytes for large m).
+ *    sums, 8*n*(row blocks) bytes, where a row block has at most 1024 rows
+ *    (about m*n/128 bytes for large m: up to m*n of about 4.1e9 elements).
  *    A problem that needs more returns GK_OUT_OF_MEMORY and computes nothing.
- *  - A, x and y must be device memory (host pointers give GK_INVALID_ARG:
- *    staging them would need an allocation).  x: n (or m) f64, y: m (or n) f64.
+ *  - A, x and y must be device memory of the current device (host pointers or
+ *    another GPU's memory give GK_INVALID_ARG: staging them would need an
+ *    allocation).  x: n (or m) f64, y: m (or n) f64; x and y must not overlap
+ *    (GK_INVALID_ARG).
  *  - The first call on a device looks up the array's device address with
  *    cudaGetSymbolAddress (with that device current); make that first call
  *    before any stream capture.

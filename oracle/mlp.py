@@ -10,6 +10,8 @@ the definitions the CUDA path documents:
   forward / loss / grad: standardize the inputs, two GELU layers (exact, erf), a linear
       output layer; loss 0.5 * mean over rows of the squared error of the standardized
       targets; gradients by the chain rule written out layer by layer.
+  adam_step: one update of the Adam method (Kingma and Ba, ICLR 2015, Algorithm 1) with
+      its bias-corrected moment estimates.
 """
 from __future__ import annotations
 
@@ -101,3 +103,17 @@ def sketch_features(A, seed: int):
     ref = math.sqrt(S) * nf
     f = np.log(np.maximum(s, 1e-30 * ref) / ref)
     return np.concatenate([f, [math.log(nf), math.log(m), math.log(n)]])
+
+
+def adam_step(p, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update at step t (1-based), Kingma and Ba (ICLR 2015), Algorithm 1:
+    m <- beta1 m + (1 - beta1) g;  v <- beta2 v + (1 - beta2) g^2;
+    m^ = m / (1 - beta1^t);  v^ = v / (1 - beta2^t);  p <- p - lr m^ / (sqrt(v^) + eps).
+    Returns (p, m, v) after the update, in f64."""
+    p = np.asarray(p, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m1 = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v1 = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m1 / (1.0 - beta1 ** t)
+    vhat = v1 / (1.0 - beta2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m1, v1

@@ -40,14 +40,23 @@ int scratch_address(int dev, void **out) {
   return GK_OK;
 }
 
-bool device_pointer(const void *p) {
+// true for device memory of device `dev` (or managed memory): the kernels run on the
+// current device and would fault on another GPU's memory without peer access
+bool device_pointer(const void *p, int dev) {
   if (p == nullptr) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// true if the byte ranges [a, a + na) and [b, b + nb) share a byte
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + nb && b0 < a0 + na;
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -68,16 +77,19 @@ extern "C" int gk_matvec_static(const gk_matrix *A, int trans, const double *x, 
   if (!A || A->m <= 0 || A->n <= 0 || A->m > INT32_MAX || A->n > INT32_MAX) return GK_INVALID_ARG;
   if (A->dtype < GK_F64 || A->dtype > GK_F16 || !(A->scale == A->scale) || A->scale == 0.0) return GK_INVALID_ARG;
   if (trans != 0 && trans != 1) return GK_INVALID_ARG;
-  if (!device_pointer(A->vals) || !device_pointer(x) || !device_pointer(y)) return GK_INVALID_ARG;
+  if (!device_pointer(A->vals, dev) || !device_pointer(x, dev) || !device_pointer(y, dev)) return GK_INVALID_ARG;
   if (A->kind == GK_DENSE) {
     if (A->ld < A->n) return GK_INVALID_ARG;
   } else if (A->kind == GK_CSR) {
-    if (!device_pointer(A->rowptr) || !device_pointer(A->colind) || !device_pointer(A->t_vals) ||
-        !device_pointer(A->t_rowptr) || !device_pointer(A->t_colind))
+    if (!device_pointer(A->rowptr, dev) || !device_pointer(A->colind, dev) || !device_pointer(A->t_vals, dev) ||
+        !device_pointer(A->t_rowptr, dev) || !device_pointer(A->t_colind, dev))
       return GK_INVALID_ARG;
   } else {
     return GK_INVALID_ARG;
   }
+  // the kernels read x while other blocks write y: the two must not share memory
+  if (overlap(x, sizeof(double) * (size_t)(trans ? A->m : A->n), y, sizeof(double) * (size_t)(trans ? A->n : A->m)))
+    return GK_INVALID_ARG;
 
   gk::Op op;
   op.kind = A->kind;
@@ -99,7 +111,10 @@ extern "C" int gk_matvec_static(const gk_matrix *A, int trans, const double *x, 
   const int64_t nin = trans ? A->m : A->n;
   const size_t ctl_bytes = align256(sizeof(gk::Ctl));
   const size_t x32_bytes = align256(sizeof(float) * (size_t)gk::round_up(A->m > A->n ? A->m : A->n, 64));
-  const size_t part_bytes = (trans && A->kind == GK_DENSE) ? sizeof(double) * (size_t)gk::gemvt_partials(op, d) : 0;
+  // A^T x keeps one f64 partial sum per (row block, column), the layout k_gemvt_* and
+  // k_gemvt_reduce index; the static A x never runs the chunked kernel that needs more
+  const int64_t row_blocks = (A->m + gk::gemvt_row_block(op, d) - 1) / gk::gemvt_row_block(op, d);
+  const size_t part_bytes = (trans && A->kind == GK_DENSE) ? sizeof(double) * (size_t)row_blocks * (size_t)A->n : 0;
   if (ctl_bytes + x32_bytes + part_bytes > kScratchBytes) return GK_OUT_OF_MEMORY;
 
   void *base = nullptr;

@@ -74,6 +74,46 @@ def test_mlp_gradient_matches_oracle():
     assert np.abs(grad - go).max() <= 1e-4 * scale
 
 
+def test_adam_step_matches_oracle():
+    """One step of gk_mlp_train (epochs = 1 over one full minibatch: a single Adam update at
+    t = t0 + 1) against the oracle's Adam step fed the oracle's own full-batch gradient, with
+    nonzero starting moments and t0 = 3 so that both bias corrections and both beta powers
+    matter.  Tolerance: the gradients agree to 1e-4 max|g| (the gradient parity bound), and an
+    update moves by at most |d update / d g| times that, plus f32 rounding."""
+    p = _params(4)
+    g = np.random.default_rng(12)
+    B = 96
+    X = g.standard_normal((B, 35)).astype(np.float32)
+    Y = (g.standard_normal((B, 2)) * 0.5 + [2.0, 3.0]).astype(np.float32)
+    _, go = mlp.loss_and_grad(p.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+    rms = float(np.sqrt(np.mean(go * go)))
+    nt = mlp.N_TRAINABLE
+    m0 = (g.standard_normal(nt) * rms).astype(np.float32)
+    v0 = (rms * rms * g.uniform(0.5, 2.0, nt)).astype(np.float32)
+    t0, lr, b1, b2, eps = 3, 1e-3, 0.9, 0.999, 1e-8
+    pd = torch.from_numpy(p.copy()).cuda()
+    md = torch.from_numpy(m0.copy()).cuda()
+    vd = torch.from_numpy(v0.copy()).cuda()
+    gk().gk_mlp_train(pd, md, vd, t0, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), batch=B, epochs=1,
+                      lr=lr, seed=5)
+    pn, mn, vn = pd.cpu().numpy().astype(np.float64), md.cpu().numpy(), vd.cpu().numpy()
+    po, mo, vo = mlp.adam_step(p[:nt].astype(np.float64), m0, v0, go, t0 + 1, lr)
+    # the non-trainable tail (standardization) is left alone
+    assert np.array_equal(pn[nt:], p[nt:].astype(np.float64))
+    t = t0 + 1
+    c1, c2 = 1 - b1 ** t, 1 - b2 ** t
+    dg = 1e-4 * np.abs(go).max()
+    sv = np.sqrt(vo / c2)
+    du_dg = lr * np.abs((1 - b1) / c1 / (sv + eps) - (mo / c1) * (1 - b2) * go / (c2 * np.maximum(sv, 1e-30) *
+                                                                                 (sv + eps) ** 2))
+    upd = p[:nt].astype(np.float64) - po
+    assert np.all(np.abs(pn[:nt] - po) <= 1.5 * du_dg * dg + 1e-6 * np.abs(upd) + 2.0**-23 * np.abs(po) + 1e-12)
+    assert np.all(np.abs(mn - mo) <= (1 - b1) * dg * 1.01 + 2.0**-23 * np.abs(mo))
+    assert np.all(np.abs(vn - vo) <= (1 - b2) * (2 * np.abs(go) * dg + dg * dg) * 1.01 + 2.0**-23 * np.abs(vo))
+    # the update itself is far above the tolerance: the test sees the rule, not noise
+    assert np.median(np.abs(upd)) > 50 * np.median(1.5 * du_dg * dg)
+
+
 def test_training_reduces_the_loss():
     g = np.random.default_rng(3)
     X = g.standard_normal((2048, 35)).astype(np.float32)

@@ -50,6 +50,19 @@ def test_start_vector_is_normal_2_1():
     assert not np.allclose(q[:100], oracle.start_vector(2104108, 100))
 
 
+def test_splitmix64_matches_published_outputs():
+    """gko_splitmix64(x) is the generator's output for the state x + gamma, so output i of
+    the generator seeded with s is gko_splitmix64(s + i * gamma)."""
+    gamma = 0x9E3779B97F4A7C15
+    path = os.path.join(GOLDEN, "splitmix64_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 2
+    for r in rows:
+        seed, outs = int(r[0]), [int(x) for x in r[1:]]
+        got = [oracle.splitmix64((seed + i * gamma) % 2**64) for i in range(len(outs))]
+        assert got == outs
+
+
 def test_splitmix64_is_a_mixing_bijection_sample():
     xs = [oracle.splitmix64(i) for i in range(4096)]
     assert len(set(xs)) == 4096

@@ -75,3 +75,28 @@ def test_sketch_scale_invariance():
     f2 = mlp.sketch_features(7.5 * A, 3)
     np.testing.assert_allclose(f2[:32], f1[:32], atol=1e-12)
     np.testing.assert_allclose(f2[32], f1[32] + math.log(7.5), atol=1e-12)
+
+
+def test_adam_constant_gradient_closed_form():
+    """From zero moments with a constant gradient g, the bias corrections make m^ = g and
+    v^ = g^2 at every step t, so each update is exactly lr g / (|g| + eps).  A wrong power
+    of beta, a missing correction or eps inside the root fails this (g spans 1e-6..10)."""
+    g = np.array([0.5, -2.0, 1e-4, -1e-6, 10.0])
+    p = np.array([1.0, -1.0, 0.25, 3.0, 0.0])
+    m = np.zeros_like(g)
+    v = np.zeros_like(g)
+    lr = 1e-3
+    for t in range(1, 6):
+        p_new, m, v = mlp.adam_step(p, m, v, g, t, lr)
+        np.testing.assert_allclose(p - p_new, lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+        p = p_new
+
+
+def test_adam_hand_worked_step():
+    """One step with nonzero moments, worked by hand: p = 1, m = 0.1, v = 0.01, g = 0.5,
+    t = 2, lr = 0.1 gives m = 0.14, v = 0.01024, m^ = 0.14 / 0.19 = 14/19,
+    v^ = 0.01024 / 0.001999, update = 0.1 (14/19) / (sqrt(v^) + 1e-8) = 0.0325559858872132."""
+    p, m, v = mlp.adam_step(np.array([1.0]), np.array([0.1]), np.array([0.01]), np.array([0.5]), 2, 0.1)
+    np.testing.assert_allclose(m, [0.14], rtol=1e-15)
+    np.testing.assert_allclose(v, [0.01024], rtol=1e-15)
+    np.testing.assert_allclose(p, [1.0 - 0.0325559858872132], rtol=1e-14)
