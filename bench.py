@@ -324,48 +324,24 @@ def oracle_operator(w):
     return oracle.Operator.dense(A.cpu().numpy())
 
 
-def oracle_step_seconds(op, w, steps, q1):
-    """Seconds per bidiagonalization step (A v, A^T u, Gram-Schmidt by the adaptive rule) of the oracle on
-    the full operator, from the first `steps` steps of its upper-bidiagonal process."""
+def oracle_complete_solves(op, w, q1, K, budget_s=20.0):
+    """The oracle, as it stands, solving the workload completely (the partial SVD at the
+    workload's k, tol and the Krylov dimension K the GPU used; Algorithm 3 for the rank
+    workload), repeated while the time spent stays under budget_s (at least once).
+    Returns (units per second, solves, seconds, oracle info of the last solve)."""
     import oracle
 
-    t = time.perf_counter()
-    oracle.gk_upper(op, steps, q1)
-    return (time.perf_counter() - t) / steps
-
-
-def oracle_reduced_steps(w):
-    """Steps the oracle's own complete solve needs on a reduced instance of the same recipe
-    (m, n / 10; same spectrum law, k, K, tol)."""
-    import oracle
-    import synth
-
-    m, n = w["m"] // 10, w["n"] // 10
-    if w["kind"] == "product":  # Algorithm 3: the steps to the break at the same rank
-        A = synth.gaussian_product(m, n, w["r"], w["noise"], w["seed"], dtype=np.float32)
-        t = time.perf_counter()
-        _, kp, _ = oracle.numrank(oracle.Operator.dense(A), synth.start_vector(m, 1), eps=w["eps"], kmax=512)
-        return float(kp), time.perf_counter() - t, (m, n)
-    if w["kind"] == "sparse":  # the full-size CSR's own oracle solve is too long: reduce rows and columns
-        sigp = 100.0 * 0.95 ** np.arange(1, w["k"] + 1)
-        d = synth.sparse_planted(m, n, w["per_row"], sigp, w["seed"])
-        op = oracle.Operator.csr(m, n, d["rowptr"], d["colind"], d["vals"], "f32")
-        t = time.perf_counter()
-        _, _, _, info = oracle.psvd(op, w["k"], w["K"], synth.start_vector(m, 1), tol=w["tol"], max_restarts=400)
-        return info["matvecs"] / 2.0, time.perf_counter() - t, (m, n)
-    if w["kind"] == "spectrum_pow":
-        sig = synth.sigma_power(n, w["e"])
-    else:
-        sig = synth.sigma_geometric(n, w.get("q", 0.9))
-    A, _, _ = synth.prescribed_spectrum(m, n, sig, w["seed"], dtype=np.float32)
-    if w["dtype"] == "bf16":
-        op = oracle.Operator.dense(None, dtype="bf16", bits=synth.to_bf16_bits(A))
-    else:
-        op = oracle.Operator.dense(A)
-    k, K = w["k"], w["K"]
-    t = time.perf_counter()
-    _, _, _, info = oracle.psvd(op, k, K, synth.start_vector(m, 1), tol=w["tol"], max_restarts=400)
-    return info["matvecs"] / 2.0, time.perf_counter() - t, (m, n)
+    reps, t0, info = 0, time.perf_counter(), None
+    while reps == 0 or time.perf_counter() - t0 < budget_s:
+        if w["kind"] == "product":
+            r, kp, _ = oracle.numrank(op, q1, eps=w["eps"], kmax=512)
+            info = {"rank": r, "kprime": kp}
+        else:
+            _, _, _, info = oracle.psvd(op, w["k"], K, q1, tol=w["tol"], max_restarts=400)
+        reps += 1
+    dt = time.perf_counter() - t0
+    units = reps * (1 if w["kind"] == "product" else w["k"])
+    return units / dt, reps, dt, info
 
 
 def cpu_threads():
@@ -458,9 +434,11 @@ def batched_leg(device, steps, warmup, keep_mats=False):
 # arms
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
-    """The CPU oracle, as it stands, on the host cores: each step is a bounded sample
-    (the oracle's bidiagonalization steps on the full operator), scaled by the number
-    of steps the oracle's own solve of a reduced instance needed."""
+    """The CPU oracle, as it stands, on the host cores: complete solves of the workload (no
+    extrapolation), as many as fit in about 20 s and at least one; for the batched workload
+    the oracle's complete pipeline (Algorithm 3, then the top-r partial SVD) on every second
+    problem of the batch.  Work is never extrapolated; `steps` is the number of complete solves
+    timed (the --steps request is recorded beside it)."""
     import torch
 
     import oracle
@@ -471,67 +449,57 @@ def run_reference(args, rank, world):
     device = torch.device("cuda", 0) if torch.cuda.is_available() else None
     if device is None:
         return {"impl": "reference", "unavailable": "the synthetic operator is generated on the GPU and no GPU is visible"}
+    common = {"impl": "reference", "n_gpus": world, "warmup": 0, "requested_steps": args.steps,
+              "requested_warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f64", "data": "synthetic"}
     if args.workload == "batched_f32_512_rank5to64":
         w = synth.WORKLOADS[args.workload]
         shapes = synth.batched_shapes(w["count"], w["seed"])
         mats = synth.torch_batched_products(shapes, 1e-6, w["seed"], device=device)
         idx = tuple(range(0, 512, 2))
-        vals = []
-        for _ in range(args.steps):
-            v, cores, desc = oracle_batched_sample(mats, shapes, w, idx)
-            vals.append(v)
-        value = float(np.mean(vals))
-        return {
+        value, cores, desc = oracle_batched_sample(mats, shapes, w, idx)
+        return dict(common, **{
             "metric": "converged top-k triplets/sec at <=1e-8 rel. residual", "value": value, "unit": "triplets/s",
-            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": 0,
-            "ms_per_step": sum(shapes[i][2] for i in idx) / value * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": 1, "ms_per_step": sum(shapes[i][2] for i in idx) / value * 1e3,
             "config": {"workload": args.workload, "count": w["count"], "eps": w["eps"], "tol": w["tol"]},
             "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }
+        })
     w = make_workload(args.workload, device, want_plain=False)
+    K = w.get("K", 0)
+    if w["name"] == "dense_bf16_100000x40000_top100":
+        # the Krylov dimension of the measured arm's configuration: the committed network's choice
+        # for this operator (a configuration value; the timed work below is the oracle alone)
+        from paper_2104_10785_gb300 import predictor
+
+        kparams = predictor.load(device=device, path=predictor.KRYLOV_PARAMS_FILE)
+        if kparams is not None:
+            K = predictor.predict_krylov(w["A"], kparams, w["k"])
     op = oracle_operator(w)
     del w["A"]
     torch.cuda.empty_cache()
     cores = cpu_threads()
     oracle.set_threads(cores)
-    steps_needed, t_red, red_shape = oracle_reduced_steps(w)
-    q1 = synth.start_vector(w["m"], w["seed"])
-    sample_steps = 2
-    for _ in range(args.warmup):
-        oracle_step_seconds(op, w, sample_steps, q1)
-    per = []
-    for _ in range(args.steps):
-        per.append(oracle_step_seconds(op, w, sample_steps, q1))
-    t_step = float(np.mean(per))
+    q1 = oracle.start_vector(w["seed"], w["m"])
+    value, reps, dt, oinfo = oracle_complete_solves(op, w, q1, K)
     numrank = w["kind"] == "product"
-    value = (1.0 if numrank else w["k"]) / (t_step * steps_needed)
     unit = "rank estimations/s" if numrank else "triplets/s"
-    sample = (f"{sample_steps} oracle bidiagonalization steps on the full {w['m']}x{w['n']} {w['dtype']} operator "
-              f"per step ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps the oracle's complete "
-              f"{'rank estimate' if numrank else 'solve'} of the {red_shape[0]}x{red_shape[1]} instance of the same "
-              f"recipe needed")
+    sample = (f"{reps} complete oracle {'rank estimate' if numrank else 'solve'}{'s' if reps > 1 else ''} of the "
+              f"{w['m']}x{w['n']} {w['dtype']} operator" + ("" if numrank else f" (k={w['k']}, K={K}, tol={w['tol']})")
+              + f", {dt:.1f} s")
+    line = dict(common, **{"value": value, "unit": unit, "steps": reps, "ms_per_step": dt / reps * 1e3,
+                           "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                                            "sample": sample},
+                           "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     if numrank:
-        return {
-            "metric": "numerical rank estimations/sec (Algorithm 3, eps 1e-5 relative)", "value": value, "unit": unit,
-            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_step * steps_needed * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "true_rank": w["r"], "eps": w["eps"]},
-            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }
-    return {
-        "metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
-        "value": value, "unit": "triplets/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * steps_needed * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": w["k"], "krylov_dim": w["K"],
-                   "tol": w["tol"], "storage": w["dtype"]},
-        "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+        line.update({"metric": "numerical rank estimations/sec (Algorithm 3, eps 1e-5 relative)",
+                     "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "true_rank": w["r"], "eps": w["eps"],
+                                "rank": oinfo["rank"]}})
+    else:
+        line.update({"metric": "converged top-k triplets/sec at <=1e-8 rel. residual",
+                     "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": w["k"], "krylov_dim": K,
+                                "tol": w["tol"], "storage": w["dtype"]}})
+    return line
 
 
 def run_gk(args, rank, world):
@@ -703,6 +671,34 @@ def run_gk(args, rank, world):
         except Exception as exc:  # an auxiliary leg: the headline stands without it
             fsvd = {"error": repr(exc)[:300]}
 
+    # the same solve with two classical Gram-Schmidt passes per vector (the rule the paper's
+    # reorthogonalization is run with when cancellation is not tested), and with the fused sweep
+    # (one pass over A per step); same operator, K and start vector
+    legs = {}
+    for name, extra in (("two_pass_cgs", dict(reorth_passes=2)), ("fused_sweep", dict(fused=True))):
+        try:
+            kk = dict(krylov_dim=int(Kused), seed=w["seed"], **extra)
+            gk.gk_psvd(A, k, tol, **kk)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = max(1, min(args.steps, 3))
+            e0.record(stream)
+            for _ in range(reps):
+                Ul, Sl, Vl, stl, infl = gk.gk_psvd(A, k, tol, **kk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lms = e0.elapsed_time(e1) / reps
+            Ul, Sl, Vl, stl, infl = gk.gk_psvd(A, k, tol, profile=True, **kk)
+            ra, rb = gk.gk_residuals(A, Ul, Sl, Vl)
+            legs[name] = {"value": k / (lms / 1e3), "unit": "triplets/s", "ms_per_step": lms, "krylov_dim": int(Kused),
+                          "status": stl, "matvecs": infl["matvecs"], "restarts": infl["restarts"],
+                          "ms_orth_per_solve": infl["ms_orth"], "ms_matvec_per_solve": infl["ms_matvec"],
+                          "ms_matvec_t_per_solve": infl["ms_matvec_t"], "fused_cluster": infl["reserved"],
+                          "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sl[0])}
+        except Exception as exc:  # auxiliary legs: the headline stands without them
+            legs[name] = {"error": repr(exc)[:300]}
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -776,7 +772,7 @@ def run_gk(args, rank, world):
         del Ap, w["A_plain"]
         torch.cuda.empty_cache()
 
-    # CPU oracle sample (rank 0, N = 1 only): about 10 s of the oracle's work
+    # CPU oracle baseline (rank 0, N = 1 only): the oracle's complete solve of the same operator
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
@@ -784,24 +780,13 @@ def run_gk(args, rank, world):
         op = oracle_operator(w)
         cores = cpu_threads()
         oracle.set_threads(cores)
-        q1 = synth.start_vector(w["m"], w["seed"])
-        steps_needed = infos[-1]["matvecs"] / 2.0
-        t1 = oracle_step_seconds(op, w, 1, q1)
-        if t1 * steps_needed < 5.0:  # small enough: complete oracle solves
-            reps, t0 = 0, time.perf_counter()
-            while reps == 0 or time.perf_counter() - t0 < 10.0:
-                oracle.psvd(op, k, K, q1, tol=tol, max_restarts=400)
-                reps += 1
-            dt = time.perf_counter() - t0
-            cpu = {"value": k * reps / dt, "unit": "triplets/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{reps} complete oracle solves (k={k}, K={K}, tol={tol}) on the same operator, {dt:.1f} s"}
-        else:
-            sample_steps = int(min(max(args.cpu_steps, round(10.0 / max(t1, 1e-6))), 200))
-            t_step = oracle_step_seconds(op, w, sample_steps, q1)
-            cpu = {"value": k / (t_step * steps_needed), "unit": "triplets/s", "cores": cores, "kind": "oracle",
-                   "sample": (f"{sample_steps} oracle bidiagonalization steps on the same {w['m']}x{w['n']} "
-                              f"{w['dtype']} operator ({t_step:.3f} s/step), scaled by the {steps_needed:.0f} steps "
-                              f"the solve needed")}
+        q1 = oracle.start_vector(w["seed"], w["m"])
+        v, reps, dt, oinfo = oracle_complete_solves(op, w, q1, int(Kused))
+        cpu = {"value": v, "unit": "triplets/s", "cores": cores, "kind": "oracle",
+               "sample": (f"{reps} complete oracle solve{'s' if reps > 1 else ''} (k={k}, K={int(Kused)}, tol={tol}) "
+                          f"of the same {w['m']}x{w['n']} {w['dtype']} operator, {dt:.1f} s "
+                          f"({oinfo['matvecs']} products, {oinfo['restarts']} restarts in the last)")}
+        del op
 
     a_dtype, a_bytes = operator_dtype(A), operator_bytes(A)
     batched = None
@@ -829,6 +814,7 @@ def run_gk(args, rank, world):
         "breakdown_ms_per_step": breakdown,
         "roofline": roof, "clocks": clk, "gpu_launches": None,
         "e2e": e2e, "cpu_baseline": cpu, "plain_f32": plain, "fixed_krylov": fixed, "fsvd": fsvd,
+        "two_pass_cgs": legs.get("two_pass_cgs"), "fused_sweep": legs.get("fused_sweep"),
         "gen_seconds": w["gen_seconds"],
         "batched": batched,
     }
@@ -906,11 +892,11 @@ def run_numrank_headline(args, rank, world, device):
         op = oracle_operator(w)
         cores = cpu_threads()
         oracle.set_threads(cores)
-        q1 = synth.start_vector(w["m"], w["seed"])
-        t_step = oracle_step_seconds(op, w, args.cpu_steps, q1)
-        cpu = {"value": 1.0 / (t_step * kp), "unit": "rank estimations/s", "cores": cores, "kind": "oracle",
-               "sample": (f"{args.cpu_steps} oracle bidiagonalization steps on the same {w['m']}x{w['n']} f32 "
-                          f"operator ({t_step:.3f} s/step), scaled by the {kp} steps the GPU call needed")}
+        q1 = oracle.start_vector(w["seed"], w["m"])
+        v, reps, dt, oinfo = oracle_complete_solves(op, w, q1, 0)
+        cpu = {"value": v, "unit": "rank estimations/s", "cores": cores, "kind": "oracle",
+               "sample": (f"{reps} complete oracle rank estimate{'s' if reps > 1 else ''} (Algorithm 3) of the same "
+                          f"{w['m']}x{w['n']} f32 operator, {dt:.1f} s (rank {oinfo['rank']}, k' {oinfo['kprime']})")}
     return {
         "metric": "numerical rank estimations/sec (Algorithm 3, eps 1e-5 relative)",
         "value": value, "unit": "rank estimations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1104,7 +1090,6 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--fixed-krylov", action="store_true",
                     help="time the default workload at its fixed Krylov dimension instead of the learned one")

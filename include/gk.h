@@ -54,6 +54,8 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 /* opts->flags bits */
 #define GK_FLAG_PROFILE 1  /* time kernel groups with CUDA events on opts->stream (gk_info.ms_*) */
 #define GK_FLAG_AUTOTUNE 2 /* batched calls: time each candidate cluster size on this batch, keep the fastest */
+#define GK_FLAG_FUSED 4    /* gk_psvd, gk_numrank, gk_fsvd: the fused sweep, one pass over A per step
+                              (see gk_psvd), where the operator qualifies; default: two passes */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).
@@ -102,15 +104,17 @@ typedef struct {
   int32_t breakdowns;    /* exact breakdowns replaced by fresh directions */
   int32_t svd_sweeps;    /* gk_psvd: Jacobi sweeps of the last small SVD (negative: sweep limit reached);
                             batched: the most sweeps any problem's last small SVD took */
-  int32_t reserved;      /* batched calls: cluster size used */
+  int32_t reserved;      /* batched calls: cluster size used; gk_psvd, gk_numrank, gk_fsvd: CTAs per
+                            cluster of the fused sweep (0 = two passes over A per step) */
   int64_t matvecs;       /* products with A or A^T */
   double resid_est_max;  /* gk_psvd: max_i<k |beta_K X_{K,i}| / sigma_1 (Ritz residual estimate) */
   double sigma_est;      /* running lower bound on sigma_1 used by the break test */
   double seconds;        /* wall time of the call */
   /* with GK_FLAG_PROFILE: device milliseconds and launch counts of kernel
    * groups, from CUDA events recorded on opts->stream around each group */
-  double ms_matvec;      /* A x products */
-  double ms_matvec_t;    /* A^T x products (partial sums + their reduction) */
+  double ms_matvec;      /* A x products (with the fused sweep: the passes that form both products) */
+  double ms_matvec_t;    /* A^T x products (partial sums + their reduction; with the fused sweep the
+                            reduction of its A^T w partial sums, and the unfused steps) */
   double ms_orth;        /* Gram-Schmidt passes, norms, normalization */
   double ms_small;       /* small SVD, Ritz residual test, rank count */
   double ms_restart;     /* Ritz vectors U_K X, V_K Y (restarts and outputs) */
@@ -134,6 +138,15 @@ size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *opts);
  * small projected matrix (Eq. 2.13, Algorithm 2), and thick restarts that
  * keep the leading Ritz vectors (the paper cites augmented restarting; the
  * restart itself is this library's choice).
+ * Fused sweep (opts->flags GK_FLAG_FUSED; dense f32/bf16/f16 operators with 16-byte
+ * rows, n * element size a multiple of 16 bytes and at most 160 KB per row): each step
+ * reads A once.  The pass forms w = A v_j - beta_{j-1} u_{j-1} and, from the same bytes,
+ * A^T w; after the left Gram-Schmidt (coefficients h, norm alpha_j) the right step takes
+ * A^T w / alpha_j in place of A^T u_j.  The two differ by A^T U_{j-1} h / alpha_j, which
+ * lies in span(V_j) (A^T u_i = alpha_i v_i + beta_i v_{i+1}, Eq. 2.2 in the upper form)
+ * and is removed by the right Gram-Schmidt, so the recurrence is unchanged in exact
+ * arithmetic.  The first step after a restart and a step after an exact breakdown run
+ * the two passes.  gk_numrank and gk_fsvd (Algorithm 1) use the same ordering.
  *  tol: a triplet is converged when ||A^T u_i - s_i v_i|| (the Ritz residual,
  *       = |beta_K X_{K,i}|; A v_i = s_i u_i holds by construction) is at most
  *       tol * s_1.

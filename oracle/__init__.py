@@ -85,13 +85,13 @@ def lib():
             L.gko_set_threads.argtypes = [i32]
             L.gko_jacobi_svd.argtypes = [i64, i64, vp, vp, vp, vp]
             L.gko_jacobi_eig.argtypes = [i64, vp, vp, vp]
-            L.gko_gk_lower.argtypes = [P(_Op), i32, d, i32, i32, vp, vp, vp, vp, vp, P(_GkInfo)]
+            L.gko_gk_lower.argtypes = [P(_Op), i32, d, i32, i32, vp, vp, vp, vp, vp, P(_GkInfo), i32]
             L.gko_cgs.argtypes = [i32, vp, vp, i64, i64, i32]
             L.gko_cgs.restype = None
-            L.gko_numrank.argtypes = [P(_Op), i32, d, i32, i32, i32, vp, P(i32), P(_GkInfo), vp]
-            L.gko_fsvd.argtypes = [P(_Op), i32, i32, i32, i32, vp, vp, vp, vp, P(_GkInfo)]
-            L.gko_psvd.argtypes = [P(_Op), i32, i32, i32, d, i32, i32, vp, u64, vp, vp, vp, P(_PsvdInfo)]
-            L.gko_gk_upper.argtypes = [P(_Op), i32, i32, vp, u64, vp, vp, vp, vp]
+            L.gko_numrank.argtypes = [P(_Op), i32, d, i32, i32, i32, vp, P(i32), P(_GkInfo), vp, i32]
+            L.gko_fsvd.argtypes = [P(_Op), i32, i32, i32, i32, vp, vp, vp, vp, P(_GkInfo), i32]
+            L.gko_psvd.argtypes = [P(_Op), i32, i32, i32, d, i32, i32, vp, u64, vp, vp, vp, P(_PsvdInfo), i32]
+            L.gko_gk_upper.argtypes = [P(_Op), i32, i32, vp, u64, vp, vp, vp, vp, i32]
             L.gko_residuals.argtypes = [P(_Op), i32, vp, vp, vp, vp, vp]
             L.gko_err_rel.argtypes = [P(_Op), i32, vp, vp, vp]
             L.gko_err_rel.restype = d
@@ -221,8 +221,9 @@ def cgs(w, Q, passes=0):
     return out
 
 
-def gk_lower(op: Operator, k: int, q1, eps=0.0, relative=True, passes=0):
-    """Algorithm 1.  Returns dict(alpha, beta, Q, P, kprime, stop_reason, sigma_est)."""
+def gk_lower(op: Operator, k: int, q1, eps=0.0, relative=True, passes=0, fused=False):
+    """Algorithm 1 (fused=True: the fused-sweep ordering, A^T w / beta for A^T q).  Returns
+    dict(alpha, beta, Q, P, kprime, stop_reason, sigma_est)."""
     m, n = op.m, op.n
     q1 = _f64(q1, m)
     alpha = np.zeros(k + 1)
@@ -231,14 +232,14 @@ def gk_lower(op: Operator, k: int, q1, eps=0.0, relative=True, passes=0):
     P = np.zeros((k + 1, n))
     info = _GkInfo()
     rc = lib().gko_gk_lower(op.ref, k, eps, int(relative), passes, _p(q1), _p(alpha), _p(beta),
-                            _p(Q), _p(P), C.byref(info))
+                            _p(Q), _p(P), C.byref(info), int(bool(fused)))
     if rc != 0:
         raise ValueError(f"gko_gk_lower rc={rc}")
     return dict(alpha=alpha, beta=beta, Q=Q.T.copy(), P=P.T.copy(), kprime=info.kprime,
                 stop_reason=info.stop_reason, sigma_est=info.sigma_est)
 
 
-def numrank(op: Operator, q1, eps=1e-8, relative=True, literal=False, kmax=0, passes=0):
+def numrank(op: Operator, q1, eps=1e-8, relative=True, literal=False, kmax=0, passes=0, fused=False):
     """Algorithm 3.  Returns (rank, kprime, sigma(B) descending)."""
     q1 = _f64(q1, op.m)
     mn = min(op.m, op.n)
@@ -247,26 +248,26 @@ def numrank(op: Operator, q1, eps=1e-8, relative=True, literal=False, kmax=0, pa
     r = C.c_int(0)
     info = _GkInfo()
     rc = lib().gko_numrank(op.ref, km, eps, int(relative), int(literal), passes, _p(q1), C.byref(r),
-                           C.byref(info), _p(sig))
+                           C.byref(info), _p(sig), int(bool(fused)))
     if rc != 0:
         raise ValueError(f"gko_numrank rc={rc}")
     return r.value, info.kprime, sig[: info.kprime].copy()
 
 
-def fsvd(op: Operator, k: int, r: int, q1, route=1, passes=0):
+def fsvd(op: Operator, k: int, r: int, q1, route=1, passes=0, fused=False):
     """Algorithm 2 (F-SVD).  route 0 = eig(B^T B) + A v / sigma; route 1 = SVD of B."""
     q1 = _f64(q1, op.m)
     U = np.zeros((r, op.m))
     V = np.zeros((r, op.n))
     S = np.zeros(r)
     info = _GkInfo()
-    rc = lib().gko_fsvd(op.ref, k, r, route, passes, _p(q1), _p(U), _p(S), _p(V), C.byref(info))
+    rc = lib().gko_fsvd(op.ref, k, r, route, passes, _p(q1), _p(U), _p(S), _p(V), C.byref(info), int(bool(fused)))
     if rc != 0:
         raise ValueError(f"gko_fsvd rc={rc}")
     return U.T.copy(), S, V.T.copy(), info.kprime
 
 
-def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, passes=0, seed=0):
+def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, passes=0, seed=0, fused=False):
     """Thick-restarted partial SVD.  Returns (U m x k, S k, V n x k, info dict)."""
     q1 = _f64(q1, op.m)
     U = np.zeros((k, op.m))
@@ -274,7 +275,7 @@ def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, 
     S = np.zeros(k)
     info = _PsvdInfo()
     rc = lib().gko_psvd(op.ref, k, K, keep, tol, max_restarts, passes, _p(q1), C.c_uint64(seed), _p(U),
-                        _p(S), _p(V), C.byref(info))
+                        _p(S), _p(V), C.byref(info), int(bool(fused)))
     if rc < 0:
         raise ValueError(f"gko_psvd rc={rc}")
     d = dict(cycles=info.cycles, restarts=info.restarts, matvecs=info.matvecs,
@@ -283,14 +284,15 @@ def psvd(op: Operator, k: int, K: int, q1, tol=1e-10, keep=0, max_restarts=100, 
     return U.T.copy(), S, V.T.copy(), d
 
 
-def gk_upper(op: Operator, K: int, q1, passes=0, seed=0):
+def gk_upper(op: Operator, K: int, q1, passes=0, seed=0, fused=False):
     """One restart-free upper-bidiagonal cycle: (alpha[K], beta[K], U m x K, V n x (K+1))."""
     q1 = _f64(q1, op.m)
     alpha = np.zeros(K)
     beta = np.zeros(K)
     Ub = np.zeros((K, op.m))
     Vb = np.zeros((K + 1, op.n))
-    rc = lib().gko_gk_upper(op.ref, K, passes, _p(q1), C.c_uint64(seed), _p(alpha), _p(beta), _p(Ub), _p(Vb))
+    rc = lib().gko_gk_upper(op.ref, K, passes, _p(q1), C.c_uint64(seed), _p(alpha), _p(beta), _p(Ub), _p(Vb),
+                            int(bool(fused)))
     if rc != 0:
         raise ValueError(f"gko_gk_upper rc={rc}")
     return alpha, beta, Ub.T.copy(), Vb.T.copy()

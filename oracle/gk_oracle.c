@@ -27,6 +27,15 @@
  *    printed in the paper, which cites augmented restarting; it is written
  *    here in the upper-bidiagonal form started from v1 = A^T q1 / ||A^T q1||
  *    (Algorithm 1).
+ *
+ * The fused sweep (fused != 0) is not in the paper: it is the one-pass
+ * ordering the CUDA path uses, restated here step by step.  The left step's
+ * vector w (A p_j minus its recurrence term, before reorthogonalization) is
+ * multiplied by A^T right away, and the right step uses A^T w / beta_{j+1} in
+ * place of A^T q_{j+1}.  The two differ by A^T Q_j h / beta_{j+1} (h the
+ * Gram-Schmidt coefficients), and A^T Q_j lies in span(P_j) by Eq. 2.2
+ * (A^T q_i = alpha_i p_i + beta_i p_{i-1}), so the Gram-Schmidt pass against
+ * P_j removes the difference: in exact arithmetic the recurrence is unchanged.
  */
 #include "gk_oracle.h"
 
@@ -438,7 +447,7 @@ int gko_jacobi_eig(int64_t n, const double *S0, double *theta, double *G)
 /* ------------------------------------------------------------------------ */
 
 int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passes, const double *q1,
-                 double *alpha, double *beta, double *Q, double *P, gko_gk_info *info)
+                 double *alpha, double *beta, double *Q, double *P, gko_gk_info *info, int fused)
 {
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
@@ -459,6 +468,7 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
   /* p_1 = A^T q_1, alpha_1 = ||p_1||, p_1 = p_1 / alpha_1 (Eq. 2.1) */
   double *w = (double *)malloc(sizeof(double) * (size_t)m);
   double *z = (double *)malloc(sizeof(double) * (size_t)n);
+  double *zr = fused ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
   gko_apply_t(A, Q, z);
   const double a1 = norm2(z, n);
   alpha[0] = a1;
@@ -468,6 +478,7 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
     info->sigma_est = sest;
     free(w);
     free(z);
+    free(zr);
     return 0;
   }
   scale_into(P, z, 1.0 / a1, n);
@@ -482,6 +493,7 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
     /* beta_{j+1} q_{j+1} = A p_j - alpha_j q_j, reorthogonalized against Q_j (Eq. 2.2) */
     gko_apply(A, pj, w);
     for (int64_t i = 0; i < m; ++i) w[i] -= aj * qj[i];
+    if (fused) gko_apply_t(A, w, zr); /* fused sweep: A^T w before reorthogonalization */
     cgs(passes, w, Q, m, m, j);
     const double b = norm2(w, m);
     beta[j] = b;
@@ -493,9 +505,14 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
     }
     scale_into(Q + (int64_t)j * m, w, 1.0 / b, m);
 
-    /* alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j */
-    gko_apply_t(A, Q + (int64_t)j * m, z);
-    for (int64_t i = 0; i < n; ++i) z[i] -= b * pj[i];
+    /* alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j;
+     * the fused sweep takes A^T w / beta_{j+1} for A^T q_{j+1} (equal up to span(P_j)) */
+    if (fused) {
+      for (int64_t i = 0; i < n; ++i) z[i] = zr[i] / b - b * pj[i];
+    } else {
+      gko_apply_t(A, Q + (int64_t)j * m, z);
+      for (int64_t i = 0; i < n; ++i) z[i] -= b * pj[i];
+    }
     cgs(passes, z, P, n, n, j);
     const double a = norm2(z, n);
     alpha[j] = a;
@@ -514,6 +531,7 @@ int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passe
   info->sigma_est = sest;
   free(w);
   free(z);
+  free(zr);
   return 0;
 }
 
@@ -533,7 +551,7 @@ static double *build_lower_B(int kp, const double *alpha, const double *beta)
 /* ------------------------------------------------------------------------ */
 
 int gko_numrank(const gko_op *A, int kmax, double eps, int eps_relative, int literal, int passes,
-                const double *q1, int *rank, gko_gk_info *info, double *sigma_out)
+                const double *q1, int *rank, gko_gk_info *info, double *sigma_out, int fused)
 {
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
@@ -543,7 +561,7 @@ int gko_numrank(const gko_op *A, int kmax, double eps, int eps_relative, int lit
   double *Q = (double *)malloc(sizeof(double) * (size_t)(m * (kmax + 1)));
   double *P = (double *)malloc(sizeof(double) * (size_t)(n * (kmax + 1)));
   /* run Algorithm 1 */
-  int rc = gko_gk_lower(A, kmax, eps, eps_relative, passes, q1, alpha, beta, Q, P, info);
+  int rc = gko_gk_lower(A, kmax, eps, eps_relative, passes, q1, alpha, beta, Q, P, info, fused);
   if (rc != 0) goto out;
   const int kp = info->kprime;
   *rank = 0;
@@ -611,7 +629,7 @@ static void sign_normalize(int64_t m, int64_t n, int k, double *U, double *V)
 /* ------------------------------------------------------------------------ */
 
 int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double *q1, double *U, double *S,
-             double *V, gko_gk_info *info)
+             double *V, gko_gk_info *info, int fused)
 {
   const int64_t m = A->m, n = A->n;
   double *alpha = (double *)malloc(sizeof(double) * (size_t)(k + 1));
@@ -622,7 +640,7 @@ int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double 
   memset(V, 0, sizeof(double) * (size_t)(n * r));
   memset(S, 0, sizeof(double) * (size_t)r);
   /* Algorithm 1 with k iterations and no break (eps = 0, absolute) */
-  int rc = gko_gk_lower(A, k, 0.0, 0, passes, q1, alpha, beta, Q, P, info);
+  int rc = gko_gk_lower(A, k, 0.0, 0, passes, q1, alpha, beta, Q, P, info, fused);
   if (rc != 0) goto out;
   const int kp = info->kprime;
   if (kp == 0) goto out;
@@ -715,11 +733,12 @@ static int extend_basis(double *x, const double *Bs, int64_t len, int64_t ld, in
 
 static int bidiag_upper_cycle(const gko_op *A, int l, int K, int passes, uint64_t seed, int64_t *nfresh,
                               const double *rho, double *Ub, double *Vb, double *Bm, double *betaK,
-                              double *sest, int64_t *matvecs)
+                              double *sest, int64_t *matvecs, int fused)
 {
   const int64_t m = A->m, n = A->n;
   double *w = (double *)malloc(sizeof(double) * (size_t)m);
   double *z = (double *)malloc(sizeof(double) * (size_t)n);
+  double *zr = fused ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
   double bprev = 0.0;
   for (int j = l; j < K; ++j) {
     /* left step: A v_j minus its components along the kept/previous u's */
@@ -731,6 +750,10 @@ static int bidiag_upper_cycle(const gko_op *A, int l, int K, int passes, uint64_
     } else if (j > 0) {
       for (int64_t r = 0; r < m; ++r) w[r] -= bprev * Ub[(int64_t)(j - 1) * m + r];
     }
+    /* fused sweep: A^T w before reorthogonalization, except at the first step after a
+     * restart (w there subtracts the whole kept block) */
+    const int fuse = fused && !(j == l && l > 0);
+    if (fuse) gko_apply_t(A, w, zr);
     cgs(passes, w, Ub, m, m, j);
     double a = norm2(w, m);
     *sest = fmax(*sest, a);
@@ -742,10 +765,16 @@ static int bidiag_upper_cycle(const gko_op *A, int l, int K, int passes, uint64_
     }
     Bm[(int64_t)j * K + j] = a;
 
-    /* right step: A^T u_j - alpha_j v_j, orthogonalized against V_{j+1} */
-    gko_apply_t(A, Ub + (int64_t)j * m, z);
+    /* right step: A^T u_j - alpha_j v_j, orthogonalized against V_{j+1}; the fused sweep
+     * takes A^T w / alpha_j for A^T u_j (equal up to span(V_j), since A^T U_{j-1} lies in
+     * span(V_j)), unless u_j was replaced after a breakdown */
+    if (fuse && a > 0.0) {
+      for (int64_t r = 0; r < n; ++r) z[r] = zr[r] / a - a * Vb[(int64_t)j * n + r];
+    } else {
+      gko_apply_t(A, Ub + (int64_t)j * m, z);
+      for (int64_t r = 0; r < n; ++r) z[r] -= a * Vb[(int64_t)j * n + r];
+    }
     ++*matvecs;
-    for (int64_t r = 0; r < n; ++r) z[r] -= a * Vb[(int64_t)j * n + r];
     cgs(passes, z, Vb, n, n, j + 1);
     double b = norm2(z, n);
     *sest = fmax(*sest, b);
@@ -761,11 +790,12 @@ static int bidiag_upper_cycle(const gko_op *A, int l, int K, int passes, uint64_
   *betaK = bprev;
   free(w);
   free(z);
+  free(zr);
   return 0;
 }
 
 int gko_gk_upper(const gko_op *A, int K, int passes, const double *q1, uint64_t seed, double *alpha,
-                 double *beta, double *Ub, double *Vb)
+                 double *beta, double *Ub, double *Vb, int fused)
 {
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
@@ -784,7 +814,7 @@ int gko_gk_upper(const gko_op *A, int K, int passes, const double *q1, uint64_t 
     extend_basis(Vb, Vb, n, n, 0, seed, &nfresh);
   double *Bm = (double *)calloc((size_t)K * K, sizeof(double));
   double sest = 0.0, betaK = 0.0;
-  bidiag_upper_cycle(A, 0, K, passes, seed, &nfresh, NULL, Ub, Vb, Bm, &betaK, &sest, &mv);
+  bidiag_upper_cycle(A, 0, K, passes, seed, &nfresh, NULL, Ub, Vb, Bm, &betaK, &sest, &mv, fused);
   for (int j = 0; j < K; ++j) {
     alpha[j] = Bm[(int64_t)j * K + j];
     beta[j] = (j + 1 < K) ? Bm[(int64_t)(j + 1) * K + j] : betaK;
@@ -795,7 +825,7 @@ int gko_gk_upper(const gko_op *A, int K, int passes, const double *q1, uint64_t 
 }
 
 int gko_psvd(const gko_op *A, int k, int K, int keep, double tol, int max_restarts, int passes,
-             const double *q1, uint64_t seed, double *U, double *S, double *V, gko_psvd_info *info)
+             const double *q1, uint64_t seed, double *U, double *S, double *V, gko_psvd_info *info, int fused)
 {
   const int64_t m = A->m, n = A->n;
   const int64_t mn = m < n ? m : n;
@@ -843,7 +873,7 @@ int gko_psvd(const gko_op *A, int k, int K, int keep, double tol, int max_restar
       Bm[(int64_t)l * K + i] = rho[i]; /* coupling column l */
     }
     double betaK = 0.0;
-    bidiag_upper_cycle(A, l, K, passes, seed, &nfresh, rho, Ub, Vb, Bm, &betaK, &sest, &info->matvecs);
+    bidiag_upper_cycle(A, l, K, passes, seed, &nfresh, rho, Ub, Vb, Bm, &betaK, &sest, &info->matvecs, fused);
     info->cycles = cycle + 1;
 
     /* SVD of the small K x K matrix: B = X Sigma Y^T */

@@ -73,28 +73,30 @@ typedef struct {
  * q1 (m start values, not necessarily normalized).
  * Outputs: alpha[k+1], beta[k+2] (beta[0] = ||q1||, beta[i] = beta_{i+1} of the
  * paper's 1-based notation is stored at index i), Q (m x (k+1), column-major),
- * P (n x (k+1), column-major).  Entries past k' are left zero. */
+ * P (n x (k+1), column-major).  Entries past k' are left zero.
+ * fused != 0 runs the fused-sweep ordering (A^T w / beta_{j+1} in place of
+ * A^T q_{j+1}, see gk_oracle.c); 0 is Algorithm 1 as printed. */
 /* Classical Gram-Schmidt of w (len) against the j columns of Q (column-major,
  * leading dimension ld) with the pass rule of gko_gk_lower's `passes`. */
 void gko_cgs(int passes, double *w, const double *Q, int64_t len, int64_t ld, int j);
 
 int gko_gk_lower(const gko_op *A, int k, double eps, int eps_relative, int passes,
                  const double *q1, double *alpha, double *beta, double *Q, double *P,
-                 gko_gk_info *info);
+                 gko_gk_info *info, int fused);
 
 /* ---- Algorithm 3: rank determination ------------------------------------ */
 /* r = #{ sigma_i(B_{k'+1,k'}) > eps * sigma_1(B) } (relative reading) or, with
  * literal != 0, #{ theta_i(B^T B) > eps } (the printed eigenvalue count). */
 int gko_numrank(const gko_op *A, int kmax, double eps, int eps_relative, int literal,
                 int passes, const double *q1, int *rank, gko_gk_info *info,
-                double *sigma_out /* optional, kmax+1 */);
+                double *sigma_out /* optional, kmax+1 */, int fused);
 
 /* ---- Algorithm 2: F-SVD ------------------------------------------------- */
 /* route 0: eig(B^T B) then U = A V / sigma (as printed);
  * route 1: one-sided Jacobi SVD of B, V = P Y, U = Q X.
  * Outputs U (m x r), S (r), V (n x r); returns k' through info. */
 int gko_fsvd(const gko_op *A, int k, int r, int route, int passes, const double *q1,
-             double *U, double *S, double *V, gko_gk_info *info);
+             double *U, double *S, double *V, gko_gk_info *info, int fused);
 
 /* ---- thick-restart partial SVD (upper-bidiagonal form) ---------------- */
 typedef struct {
@@ -116,14 +118,14 @@ typedef struct {
  * converged, 1 if not converged within max_restarts, <0 on bad arguments. */
 int gko_psvd(const gko_op *A, int k, int K, int keep, double tol, int max_restarts,
              int passes, const double *q1, uint64_t seed,
-             double *U, double *S, double *V, gko_psvd_info *info);
+             double *U, double *S, double *V, gko_psvd_info *info, int fused);
 
 /* One cycle of the restart-free upper-bidiagonal process from v1 = A^T q1 /
  * ||A^T q1||: K steps, returns alpha[K], beta[K] (beta[K-1] couples v_{K+1}),
  * Ub (m x K), Vb (n x (K+1)).  Used by tests that check the bidiagonal
  * relations of the upper form. */
 int gko_gk_upper(const gko_op *A, int K, int passes, const double *q1, uint64_t seed,
-                 double *alpha, double *beta, double *Ub, double *Vb);
+                 double *alpha, double *beta, double *Ub, double *Vb, int fused);
 
 /* ---- error metrics ------------------------------------------------------ */
 /* per-triplet residuals res[i] = max(||A v_i - s_i u_i||, ||A^T u_i - s_i v_i||) */

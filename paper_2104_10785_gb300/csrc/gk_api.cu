@@ -199,6 +199,15 @@ int stage_copy(const gk_matrix *A, const OpStage &st, const Op &op, cudaStream_t
   return GK_OK;
 }
 
+// the fused sweep's conditions, judged on the operator the kernels will read: a host
+// operator is staged into the 256-byte-aligned workspace, so only its row stride matters
+bool fused_ok_staged(const Op &op, const OpStage &st, const Dev &d) {
+  if (!st.host) return fused_ok(op, d);
+  Op probe = op;
+  probe.vals = reinterpret_cast<const void *>((uintptr_t)256);
+  return fused_ok(probe, d);
+}
+
 Op make_op(const gk_matrix *A) {
   Op op;
   op.kind = A->kind;
@@ -359,6 +368,7 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
 struct PsvdPlan {
   int64_t m, n, ldu, ldv;
   int k, K, keep, passes, max_restarts;
+  bool fused;  // one pass over A per step (gk_fused.cu)
 };
 
 struct PsvdBufs {
@@ -366,7 +376,7 @@ struct PsvdBufs {
   double *Ub, *Ub2, *Vb, *Vb2, *w, *z, *t, *part, *h, *alpha, *beta, *Bm, *Yw, *X, *Y, *sigma, *rho, *out;
   float *x32;
   int *sweeps;
-  double *Uo, *So, *Vo, *q1, *svd_nrm;
+  double *Uo, *So, *Vo, *q1, *svd_nrm, *zpart;
   int *svd_pos;
 };
 
@@ -405,6 +415,7 @@ size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const Op
   b->Vo = host_out ? cv.take<double>((size_t)p.n * p.k) : nullptr;
   b->So = host_out ? cv.take<double>(p.k) : nullptr;
   b->q1 = host_start ? cv.take<double>(p.ldu) : nullptr;
+  b->zpart = p.fused ? cv.take<double>(fused_partials(*op, d)) : nullptr;
   char *dd;
   void *v, *tv;
   int32_t *rp, *ci, *trp, *tci;
@@ -440,6 +451,7 @@ int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
   p->keep = keep;
   p->passes = o.reorth_passes;
   p->max_restarts = o.max_restarts;
+  p->fused = false;
   return GK_OK;
 }
 
@@ -495,6 +507,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   const bool host_out = on_host(U) || on_host(S) || on_host(V);
   const bool host_start = o.start && on_host(o.start);
   Op op = make_op(Ain);
+  p.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   PsvdBufs b;
   const size_t bytes = psvd_layout(Ain, p, d, st, host_out, host_start, nullptr, &b, &op);
   Workspace ws;
@@ -550,6 +563,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     int j0 = l, side0 = 0;
     for (;;) {
       for (int j = j0; j < K; ++j) {
+        bool fused_step = false;
         if (!(j == j0 && side0 == 1)) {
           // left half-step: A v_j minus its component along the previous u's
           const double *vj = b.Vb + (int64_t)j * ldv;
@@ -559,6 +573,13 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
             prof.end();
             prof.begin(PC_ORTH);
             GK_CUDA(sub_combination(b.w, m, b.Ub, ldu, l, b.rho, b.ctl, s, d));
+          } else if (p.fused) {
+            // one pass: w = A v_j - beta_{j-1} u_{j-1} and the partial sums of A^T w
+            GK_CUDA(fused_matvec(op, b.x32, b.w, j > 0 ? b.Ub + (int64_t)(j - 1) * ldu : nullptr,
+                                 j > 0 ? b.beta + (j - 1) : nullptr, b.zpart, b.ctl, s, d));
+            fused_step = true;
+            prof.end();
+            prof.begin(PC_ORTH);
           } else if (j > 0) {
             GK_CUDA(matvec(op, b.x32, vj, b.w, b.Ub + (int64_t)(j - 1) * ldu, b.beta + (j - 1), b.part, b.ctl, s, d));
             prof.end();
@@ -570,14 +591,18 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
           }
           GK_CUDA(orthonormalize(b.w, m, b.Ub, ldu, j, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 0, b.alpha + j,
                                  nullptr, s, d));
-          GK_CUDA(normalize_append(b.w, m, b.Ub + (int64_t)j * ldu, b.x32, b.ctl, s, d));
+          GK_CUDA(normalize_append(b.w, m, b.Ub + (int64_t)j * ldu, fused_step ? nullptr : b.x32, b.ctl, s, d));
           prof.end();
           inf.matvecs++;
         }
-        // right half-step: A^T u_j - alpha_j v_j, orthogonalized against V_{j+1}
+        // right half-step: A^T u_j - alpha_j v_j, orthogonalized against V_{j+1}; after a fused
+        // pass A^T u_j is A^T w / alpha_j up to span(V_j), which the Gram-Schmidt removes
         prof.begin(PC_MATVEC_T);
-        GK_CUDA(matvec_t(op, b.x32, b.Ub + (int64_t)j * ldu, b.z, b.Vb + (int64_t)j * ldv, b.alpha + j, b.part,
-                         b.ctl, s, d));
+        if (fused_step)
+          GK_CUDA(fused_finish(op, b.zpart, b.alpha + j, b.Vb + (int64_t)j * ldv, b.z, b.ctl, s, d));
+        else
+          GK_CUDA(matvec_t(op, b.x32, b.Ub + (int64_t)j * ldu, b.z, b.Vb + (int64_t)j * ldv, b.alpha + j, b.part,
+                           b.ctl, s, d));
         prof.end();
         prof.begin(PC_ORTH);
         GK_CUDA(orthonormalize(b.z, n, b.Vb, ldv, j + 1, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 1,
@@ -662,9 +687,11 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   prof.finish(&inf);
   inf.sigma_est = hc.ctl.sest;
   inf.svd_sweeps = sweeps;
+  inf.reserved = p.fused ? fused_cluster(op, d) : 0;
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
   if (info) *info = inf;
+  if (hc.ctl.timeout) return GK_TIMEOUT;
   return status;
 }
 
@@ -673,9 +700,10 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
 // ---------------------------------------------------------------------------
 struct RankBufs {
   Ctl *ctl;
-  double *Q, *P, *w, *z, *t, *part, *h, *alpha, *beta, *sig, *sigma1, *q1;
+  double *Q, *P, *w, *z, *t, *part, *h, *alpha, *beta, *sig, *sigma1, *q1, *zpart;
   float *x32;
   int *rank;
+  bool fused;  // one pass over A per step (gk_fused.cu)
 };
 
 size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpStage &st, bool host_sigma,
@@ -701,6 +729,7 @@ size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpSt
   b->sigma1 = cv.take<double>(1);
   b->rank = cv.take<int>(1);
   b->q1 = host_start ? cv.take<double>(ldu) : nullptr;
+  b->zpart = b->fused ? cv.take<double>(fused_partials(*op, d)) : nullptr;
   char *dd;
   void *v, *tv;
   int32_t *rp, *ci, *trp, *tci;
@@ -755,17 +784,24 @@ int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &
       const int jj = (int)j;
       // beta_{j+1} q_{j+1} = A p_j - alpha_j q_j, reorthogonalized against Q_j
       prof.begin(PC_MATVEC);
-      GK_CUDA(matvec(op, b.x32, b.P + (j - 1) * ldv, b.w, b.Q + (j - 1) * ldu, b.alpha + (j - 1), b.part, b.ctl, s,
-                     d));
+      if (b.fused)  // one pass: w and the partial sums of A^T w
+        GK_CUDA(fused_matvec(op, b.x32, b.w, b.Q + (j - 1) * ldu, b.alpha + (j - 1), b.zpart, b.ctl, s, d));
+      else
+        GK_CUDA(matvec(op, b.x32, b.P + (j - 1) * ldv, b.w, b.Q + (j - 1) * ldu, b.alpha + (j - 1), b.part, b.ctl,
+                       s, d));
       prof.end();
       prof.begin(PC_ORTH);
       GK_CUDA(orthonormalize(b.w, m, b.Q, ldu, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 0, b.beta + j,
                              b.alpha + (j - 1), s, d));
-      GK_CUDA(normalize_append(b.w, m, b.Q + j * ldu, b.x32, b.ctl, s, d));
+      GK_CUDA(normalize_append(b.w, m, b.Q + j * ldu, b.fused ? nullptr : b.x32, b.ctl, s, d));
       prof.end();
-      // alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j
+      // alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j; after a
+      // fused pass A^T q_{j+1} is A^T w / beta_{j+1} up to span(P_j), removed by the Gram-Schmidt
       prof.begin(PC_MATVEC_T);
-      GK_CUDA(matvec_t(op, b.x32, b.Q + j * ldu, b.z, b.P + (j - 1) * ldv, b.beta + j, b.part, b.ctl, s, d));
+      if (b.fused)
+        GK_CUDA(fused_finish(op, b.zpart, b.beta + j, b.P + (j - 1) * ldv, b.z, b.ctl, s, d));
+      else
+        GK_CUDA(matvec_t(op, b.x32, b.Q + j * ldu, b.z, b.P + (j - 1) * ldv, b.beta + j, b.part, b.ctl, s, d));
       prof.end();
       prof.begin(PC_ORTH);
       GK_CUDA(orthonormalize(b.z, n, b.P, ldv, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 1, b.alpha + j,
@@ -816,6 +852,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   const bool host_start = o.start && on_host(o.start);
   Op op = make_op(Ain);
   RankBufs b;
+  b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   const size_t bytes = numrank_layout(Ain, kmax, d, st, host_sigma, host_start, nullptr, &b, &op);
   Workspace ws;
   rc = acquire(ws, bytes, o, s);
@@ -846,6 +883,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   GK_CUDA(cudaStreamSynchronize(s));
   *rank = r;
   prof.finish(&inf);
+  inf.reserved = b.fused ? fused_cluster(op, d) : 0;
   inf.sigma_est = hc.ctl.sest;
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
@@ -904,6 +942,7 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
   const bool host_out = on_host(U) || on_host(S) || on_host(V);
   Op op = make_op(Ain);
   RankBufs b;
+  b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   FsvdBufs f;
   const size_t nb = (numrank_layout(Ain, k, d, st, false, host_start, nullptr, &b, &op) + 255) / 256 * 256;
   const size_t fb = fsvd_layout(nullptr, k, r, m, n, host_out, &f);
@@ -972,6 +1011,7 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
   GK_CUDA(cudaStreamSynchronize(s));
   prof.finish(&inf);
   inf.svd_sweeps = sweeps;
+  inf.reserved = b.fused ? fused_cluster(op, d) : 0;
   inf.sigma_est = hc.ctl.sest;
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
@@ -1118,6 +1158,7 @@ size_t gk_psvd_workspace(const gk_matrix *A, int k, const gk_opts *oin) {
   if (stage_plan(A, &st) != GK_OK) return 0;
   PsvdBufs b;
   Op op = make_op(A);
+  p.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   return psvd_layout(A, p, d, st, false, false, nullptr, &b, &op);
 }
 
@@ -1136,11 +1177,12 @@ int gk_psvd(const gk_matrix *A, int k, double tol, const gk_opts *opts, double *
 size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *oin) {
   Dev d;
   if (!get_device(&d) || check_matrix(A) != GK_OK) return 0;
-  (void)oin;
+  const gk_opts o = oin ? *oin : defaults();
   OpStage st;
   if (stage_plan(A, &st) != GK_OK) return 0;
   RankBufs b;
   Op op = make_op(A);
+  b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   return numrank_layout(A, clamp_kmax(A, kmax), d, st, false, false, nullptr, &b, &op);
 }
 

@@ -133,6 +133,19 @@ cudaError_t matvec(const Op &A, const float *x32, const double *x64, double *y, 
 cudaError_t matvec_t(const Op &A, const float *x32, const double *x64, double *y, const double *sub,
                      const double *coef, double *part, const Ctl *ctl, cudaStream_t s, const Dev &d);
 
+// ---- fused sweep (gk_fused.cu) --------------------------------------------
+// Dense f32/bf16/f16 operators with 16-byte rows and n * sizeof(T) a multiple of 16, up
+// to 160 KB per row: one pass over A gives w = scale A x - coef * sub and the partial
+// sums of A^T w per cluster (zpart, fused_partials() doubles); fused_finish then forms
+// z = scale (A^T w) / (*alpha) - (*alpha) * sub.
+bool fused_ok(const Op &A, const Dev &d);
+int64_t fused_partials(const Op &A, const Dev &d);
+int fused_cluster(const Op &A, const Dev &d);  // CTAs per cluster of the fused kernel (0: not fused)
+cudaError_t fused_matvec(const Op &A, const float *x32, double *w, const double *sub, const double *coef,
+                         double *zpart, Ctl *ctl, cudaStream_t s, const Dev &d);
+cudaError_t fused_finish(const Op &A, const double *zpart, const double *alpha, const double *sub, double *z,
+                         const Ctl *ctl, cudaStream_t s, const Dev &d);
+
 // ---- Gram-Schmidt and vector kernels (gk_orth.cu) -------------------------
 // Classical Gram-Schmidt of w (len) against the first j columns of Q (ld):
 // passes = 1..3 passes, or 0 = one pass and a second only if the first left less

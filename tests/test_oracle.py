@@ -492,3 +492,72 @@ def test_planted_mistake_is_caught_by_invariants():
     good = np.abs(A @ d["P"][:, :10] - d["Q"][:, :11] @ B).max()
     bad = np.abs(A @ d["P"][:, :10] - d["Q"][:, :11] @ Bbad).max()
     assert good < 1e-12 and bad > 1e-1
+
+
+# ---------------------------------------------------------------------------
+# the fused sweep (A^T w / beta in place of A^T q): pinned by Eq. 2.4 directly and by
+# agreement with the recurrence as printed
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,passes", [((120, 80), 0), ((80, 120), 0), ((150, 150), 2), ((200, 90), 1)])
+def test_fused_sweep_keeps_the_bidiagonal_relations(shape, passes):
+    """The fused ordering must satisfy Eq. 2.4 and Eq. pq_ortho on its own (these fail if the
+    span(P_j) argument were wrong, e.g. a dropped 1/beta or a missing -beta p_j term), and give
+    the alpha, beta of the printed recurrence to rounding."""
+    rng = _rng(31)
+    m, n = shape
+    A = rng.standard_normal((m, n)) * np.linspace(1, 0.05, n)[None, :]
+    op = oracle.Operator.dense(A)
+    k = 40
+    q1 = 2 + rng.standard_normal(m)
+    d = oracle.gk_lower(op, k, q1, eps=0.0, relative=False, passes=passes, fused=True)
+    assert d["kprime"] == k and d["stop_reason"] == 0
+    Q, P, B = d["Q"][:, : k + 1], d["P"], _lower_B(d)
+    nA = np.linalg.norm(A, 2)
+    assert np.abs(A @ P[:, :k] - Q @ B).max() < 1e-13 * nA
+    R = A.T @ Q - P[:, :k] @ B.T
+    R[:, k] -= d["alpha"][k] * P[:, k]
+    assert np.abs(R).max() < 1e-13 * nA
+    tol_o = 1e-10 if passes == 1 else 1e-13
+    assert np.abs(Q.T @ Q - np.eye(k + 1)).max() < tol_o
+    assert np.abs(P[:, : k + 1].T @ P[:, : k + 1] - np.eye(k + 1)).max() < tol_o
+    d0 = oracle.gk_lower(op, k, q1, eps=0.0, relative=False, passes=passes)
+    sc = max(d0["alpha"].max(), d0["beta"][1:].max())
+    assert np.abs(d["alpha"] - d0["alpha"]).max() < 1e-12 * sc
+    assert np.abs(d["beta"][1:] - d0["beta"][1:]).max() < 1e-12 * sc
+
+
+def test_fused_sweep_upper_form_and_restarts_match_lapack():
+    """The upper-bidiagonal fused cycle keeps A V_K = U_K B_K, and the restarted partial SVD on it
+    (restarts, where the first step after each restart runs unfused) returns LAPACK's triplets."""
+    rng = _rng(32)
+    m, n, K = 260, 180, 30
+    A = rng.standard_normal((m, n)) * (0.93 ** np.arange(n))[None, :]
+    op = oracle.Operator.dense(A)
+    q1 = 2 + rng.standard_normal(m)
+    al, be, Ub, Vb = oracle.gk_upper(op, K, q1, fused=True)
+    al0, be0, _, _ = oracle.gk_upper(op, K, q1)
+    B = np.diag(al) + np.diag(be[:-1], 1)
+    nA = np.linalg.norm(A, 2)
+    assert np.abs(A @ Vb[:, :K] - Ub @ B).max() < 1e-13 * nA
+    assert np.abs(Ub.T @ Ub - np.eye(K)).max() < 1e-13
+    np.testing.assert_allclose(al, al0, rtol=1e-11)
+    np.testing.assert_allclose(be, be0, rtol=1e-11)
+    U, S, V, info = oracle.psvd(op, 8, 20, q1, tol=1e-12, max_restarts=200, fused=True)
+    assert info["converged"] and info["restarts"] >= 1
+    Ur, Sr, Vtr = np.linalg.svd(A, full_matrices=False)
+    np.testing.assert_allclose(S, Sr[:8], rtol=1e-11)
+    ok, worst = _angle_ok(V, Vtr[:8].T, 1e-9)
+    assert ok, worst
+    r1, r2 = oracle.residuals(op, U, S, V)
+    assert max(r1.max(), r2.max()) < 1e-11 * S[0]
+
+
+@pytest.mark.parametrize("m,n,r", [(300, 200, 17), (150, 260, 40)])
+def test_fused_sweep_rank_matches_brute_force(m, n, r):
+    rng = _rng(33)
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    op = oracle.Operator.dense(A)
+    q1 = 2 + rng.standard_normal(m)
+    rank, kp, _ = oracle.numrank(op, q1, eps=1e-9, fused=True)
+    assert rank == np.linalg.matrix_rank(A) == r
