@@ -56,6 +56,9 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 #define GK_FLAG_AUTOTUNE 2 /* batched calls: time each candidate cluster size on this batch, keep the fastest */
 #define GK_FLAG_FUSED 4    /* gk_psvd, gk_numrank, gk_fsvd: the fused sweep, one pass over A per step
                               (see gk_psvd), where the operator qualifies; default: two passes */
+#define GK_FLAG_REFINE 8   /* gk_psvd: check the returned triplets' true residuals with FP64-grade
+                              products (as gk_residuals) and keep restarting, with the Ritz test
+                              tightened 4x each time, while one exceeds tol * s_1 */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).
@@ -122,6 +125,11 @@ typedef struct {
   int64_t n_matvec_t;
   int64_t launches;      /* kernels this call launched (all of them the library's own) */
   double ms_copy;        /* with GK_FLAG_PROFILE: host<->device copies of host operands and outputs */
+  double resid_true_max; /* gk_psvd with GK_FLAG_REFINE: max_i max(||A v_i - s_i u_i||, ||A^T u_i - s_i v_i||)
+                            / s_1 of the returned triplets, FP64-grade (0 when not checked) */
+  double ms_refine;      /* gk_psvd with GK_FLAG_REFINE: wall milliseconds of those checks */
+  int32_t refine_checks; /* gk_psvd with GK_FLAG_REFINE: checks run (1 = the first passed) */
+  int32_t reserved2;
 } gk_info;
 
 /* Fill *opts with the defaults above. */
@@ -205,7 +213,11 @@ int gk_matvec(const gk_matrix *A, int trans, const double *x, double *y, const g
 /* True residuals of k triplets (columns of U m x k, V n x k, column-major,
  * f64; S k values): res_av[i] = ||A v_i - s_i u_i||, res_atu[i] =
  * ||A^T u_i - s_i v_i|| (the quantities behind the paper's err_rel of
- * Section 5 and the tolerance of gk_psvd).  Outputs f64, device or host. */
+ * Section 5 and the tolerance of gk_psvd).  Outputs f64, device or host.
+ * The products are FP64-grade: f64 and CSR operators multiply in f64; f32,
+ * bf16 and f16 operators multiply in double-f32 arithmetic (every product
+ * and partial sum carried exactly to about 2^-47 of sum |a_ij x_j|, the
+ * vectors split into two f32 parts), all k vectors per pass over A. */
 int gk_residuals(const gk_matrix *A, int k, const double *U, const double *S, const double *V, double *res_av,
                  double *res_atu, const gk_opts *opts);
 

@@ -368,7 +368,8 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
 struct PsvdPlan {
   int64_t m, n, ldu, ldv;
   int k, K, keep, passes, max_restarts;
-  bool fused;  // one pass over A per step (gk_fused.cu)
+  bool fused;   // one pass over A per step (gk_fused.cu)
+  bool refine;  // FP64-grade check of the returned triplets (GK_FLAG_REFINE)
 };
 
 struct PsvdBufs {
@@ -376,7 +377,8 @@ struct PsvdBufs {
   double *Ub, *Ub2, *Vb, *Vb2, *w, *z, *t, *part, *h, *alpha, *beta, *Bm, *Yw, *X, *Y, *sigma, *rho, *out;
   float *x32;
   int *sweeps;
-  double *Uo, *So, *Vo, *q1, *svd_nrm, *zpart;
+  double *Uo, *So, *Vo, *q1, *svd_nrm, *zpart, *rY, *rZ, *rr1, *rr2;
+  float *rsplit;
   int *svd_pos;
 };
 
@@ -416,6 +418,17 @@ size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const Op
   b->So = host_out ? cv.take<double>(p.k) : nullptr;
   b->q1 = host_start ? cv.take<double>(p.ldu) : nullptr;
   b->zpart = p.fused ? cv.take<double>(fused_partials(*op, d)) : nullptr;
+  b->rY = b->rZ = b->rr1 = b->rr2 = nullptr;
+  b->rsplit = nullptr;
+  if (p.refine) {
+    b->rr1 = cv.take<double>(p.k);
+    b->rr2 = cv.take<double>(p.k);
+    if (accurate_ok(*op)) {
+      b->rY = cv.take<double>((size_t)p.m * p.k);
+      b->rZ = cv.take<double>((size_t)p.n * p.k);
+      b->rsplit = cv.take<float>(accurate_floats(*op, p.k));
+    }
+  }
   char *dd;
   void *v, *tv;
   int32_t *rp, *ci, *trp, *tci;
@@ -452,6 +465,7 @@ int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
   p->passes = o.reorth_passes;
   p->max_restarts = o.max_restarts;
   p->fused = false;
+  p->refine = (o.flags & GK_FLAG_REFINE) != 0;
   return GK_OK;
 }
 
@@ -480,6 +494,38 @@ int fresh_column(double *wbuf, int64_t len, const double *Qb, int64_t ld, int jc
   GK_CUDA(orthonormalize(wbuf, len, Qb, ld, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
   GK_CUDA(orthonormalize(wbuf, len, Qb, ld, jcols, 2, b.part, b.h, b.ctl, NM_FRESH, -1, 0, nullptr, nullptr, s, d));
   GK_CUDA(normalize_append(wbuf, len, dst, x32, b.ctl, s, d));
+  return GK_OK;
+}
+
+// True residuals of the k output triplets (device Uo m x k, So, Vo n x k): FP64-grade products
+// (double-f32 for reduced-precision dense operators, f64 otherwise); returns
+// max_i max(r_av, r_atu) / s_1 in *rel.
+int refine_check(const Op &op, int64_t m, int64_t n, int k, const double *Uo, const double *So, const double *Vo,
+                 PsvdBufs &b, double *rel, cudaStream_t s, const Dev &d) {
+  if (accurate_ok(op)) {
+    GK_CUDA(accurate_products(op, false, Vo, k, b.rY, b.rsplit, s));
+    GK_CUDA(resid_norms(b.rY, Uo, So, m, k, b.rr1, s));
+    GK_CUDA(accurate_products(op, true, Uo, k, b.rZ, b.rsplit, s));
+    GK_CUDA(resid_norms(b.rZ, Vo, So, n, k, b.rr2, s));
+  } else {
+    for (int i = 0; i < k; ++i) {
+      const double *ui = Uo + (int64_t)i * m, *vi = Vo + (int64_t)i * n;
+      GK_CUDA(copy_vec(nullptr, b.x32, vi, n, s));
+      GK_CUDA(matvec(op, b.x32, vi, b.w, ui, So + i, b.part, b.ctl, s, d));
+      GK_CUDA(orthonormalize(b.w, m, nullptr, m, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, b.rr1 + i, nullptr, s, d));
+      GK_CUDA(copy_vec(nullptr, b.x32, ui, m, s));
+      GK_CUDA(matvec_t(op, b.x32, ui, b.z, vi, So + i, b.part, b.ctl, s, d));
+      GK_CUDA(orthonormalize(b.z, n, nullptr, n, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 1, b.rr2 + i, nullptr, s, d));
+    }
+  }
+  std::vector<double> h(2 * (size_t)k + 1);
+  GK_CUDA(cudaMemcpyAsync(h.data(), b.rr1, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaMemcpyAsync(h.data() + k, b.rr2, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaMemcpyAsync(h.data() + 2 * k, So, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  double mx = 0.0;
+  for (int i = 0; i < 2 * k; ++i) mx = fmax(mx, h[i]);
+  *rel = h[2 * k] > 0.0 ? mx / h[2 * k] : 0.0;
   return GK_OK;
 }
 
@@ -559,6 +605,20 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
 
   int l = 0;
   int status = GK_NOT_CONVERGED;
+  double tol_ritz = tol;      // the Ritz test's tolerance (tightened by failed refinement checks)
+  bool outputs_ready = false;  // Uo, So, Vo already hold the final triplets
+  double *Uo = host_out ? b.Uo : U, *Vo = host_out ? b.Vo : V, *So = host_out ? b.So : S;
+  // outputs: U = U_K X_k, V = V_K Y_k, S = sigma_k, sign convention on v
+  auto form_outputs = [&]() -> int {
+    prof.begin(PC_RESTART);
+    GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, k, Uo, m, s, d));
+    GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, k, Vo, n, s, d));
+    prof.end();
+    GK_CUDA(cudaMemcpyAsync(So, b.sigma, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
+    GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, k, s));
+    return GK_OK;
+  };
+  bool refine_failed = false;
   for (int cycle = 0;; ++cycle) {
     int j0 = l, side0 = 0;
     for (;;) {
@@ -615,7 +675,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
       prof.begin(PC_SMALL);
       GK_CUDA(assemble_B(b.Bm, K, l, b.sigma, b.rho, b.alpha, b.beta, b.ctl, s));
       GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.svd_nrm, b.svd_pos, b.sweeps, b.ctl, s));
-      GK_CUDA(ritz_check(b.sigma, b.X, K, k, b.beta + (K - 1), tol, b.rho, b.out, b.ctl, s));
+      GK_CUDA(ritz_check(b.sigma, b.X, K, k, b.beta + (K - 1), tol_ritz, b.rho, b.out, b.ctl, s));
       prof.end();
       rc = read_ctl(b.ctl, b.out, &hc, s);
       if (rc) return rc;
@@ -642,7 +702,27 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     inf.cycles = cycle + 1;
     inf.resid_est_max = hc.out[1] > 0.0 ? hc.out[0] / hc.out[1] : 0.0;
     const bool conv = hc.out[2] != 0.0;
-    if (conv || cycle >= p.max_restarts) {
+    if (p.refine && (conv || cycle >= p.max_restarts)) {
+      // the returned triplets' true residuals with FP64-grade products
+      rc = form_outputs();
+      if (rc) return rc;
+      outputs_ready = true;
+      const auto tr = std::chrono::steady_clock::now();
+      double rel = 0.0;
+      rc = refine_check(op, m, n, k, Uo, So, Vo, b, &rel, s, d);
+      if (rc) return rc;
+      inf.ms_refine += seconds_since(tr) * 1e3;
+      inf.refine_checks++;
+      inf.resid_true_max = rel;
+      refine_failed = rel > tol;
+      if (refine_failed && conv && cycle < p.max_restarts) {
+        tol_ritz *= 0.25;  // the Ritz residuals must shrink further: restart and test again
+        outputs_ready = false;
+      } else {
+        status = (conv && !refine_failed) ? GK_OK : GK_NOT_CONVERGED;
+        break;
+      }
+    } else if (conv || cycle >= p.max_restarts) {
       status = conv ? GK_OK : GK_NOT_CONVERGED;
       break;
     }
@@ -662,14 +742,10 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     inf.restarts++;
   }
 
-  // outputs: U = U_K X_k, V = V_K Y_k, S = sigma_k, sign convention on v
-  double *Uo = host_out ? b.Uo : U, *Vo = host_out ? b.Vo : V, *So = host_out ? b.So : S;
-  prof.begin(PC_RESTART);
-  GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, k, Uo, m, s, d));
-  GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, k, Vo, n, s, d));
-  prof.end();
-  GK_CUDA(cudaMemcpyAsync(So, b.sigma, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
-  GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, k, s));
+  if (!outputs_ready) {
+    rc = form_outputs();
+    if (rc) return rc;
+  }
   double sk = 0.0;
   int sweeps = 0;
   GK_CUDA(cudaMemcpyAsync(&sk, b.sigma + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1026,8 +1102,8 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
 // ---------------------------------------------------------------------------
 struct VecBufs {
   Ctl *ctl;
-  double *x, *y, *part, *h, *U, *S, *V, *r1, *r2;
-  float *x32;
+  double *x, *y, *part, *h, *U, *S, *V, *r1, *r2, *Y, *Z;
+  float *x32, *split;
 };
 
 size_t vec_layout(const gk_matrix *A, const Dev &d, const OpStage &st, int k, char *base, VecBufs *b, Op *op) {
@@ -1043,12 +1119,19 @@ size_t vec_layout(const gk_matrix *A, const Dev &d, const OpStage &st, int k, ch
   if (gp > pc) pc = gp;
   b->part = cv.take<double>(pc);
   b->h = cv.take<double>(4);
+  b->Y = b->Z = nullptr;
+  b->split = nullptr;
   if (k > 0) {
     b->U = cv.take<double>((size_t)A->m * k);
     b->V = cv.take<double>((size_t)A->n * k);
     b->S = cv.take<double>(k);
     b->r1 = cv.take<double>(k);
     b->r2 = cv.take<double>(k);
+    if (accurate_ok(*op)) {
+      b->Y = cv.take<double>((size_t)A->m * k);
+      b->Z = cv.take<double>((size_t)A->n * k);
+      b->split = cv.take<float>(accurate_floats(*op, k));
+    }
   }
   char *dd;
   void *v, *tv;
@@ -1122,6 +1205,13 @@ int residuals_impl(const gk_matrix *Ain, int k, const double *U, const double *S
   GK_CUDA(cudaMemcpyAsync(b.U, U, sizeof(double) * m * k, cudaMemcpyDefault, s));
   GK_CUDA(cudaMemcpyAsync(b.V, V, sizeof(double) * n * k, cudaMemcpyDefault, s));
   GK_CUDA(cudaMemcpyAsync(b.S, S, sizeof(double) * k, cudaMemcpyDefault, s));
+  if (accurate_ok(op)) {
+    // all k triplets per pass over A, FP64-grade (double-f32) products
+    GK_CUDA(accurate_products(op, false, b.V, k, b.Y, b.split, s));
+    GK_CUDA(resid_norms(b.Y, b.U, b.S, m, k, b.r1, s));
+    GK_CUDA(accurate_products(op, true, b.U, k, b.Z, b.split, s));
+    GK_CUDA(resid_norms(b.Z, b.V, b.S, n, k, b.r2, s));
+  } else {
   for (int i = 0; i < k; ++i) {
     const double *ui = b.U + (int64_t)i * m, *vi = b.V + (int64_t)i * n;
     GK_CUDA(copy_vec(nullptr, b.x32, vi, n, s));
@@ -1130,6 +1220,7 @@ int residuals_impl(const gk_matrix *Ain, int k, const double *U, const double *S
     GK_CUDA(copy_vec(nullptr, b.x32, ui, m, s));
     GK_CUDA(matvec_t(op, b.x32, ui, b.y, vi, b.S + i, b.part, b.ctl, s, d));
     GK_CUDA(orthonormalize(b.y, n, nullptr, n, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 1, b.r2 + i, nullptr, s, d));
+  }
   }
   GK_CUDA(cudaMemcpyAsync(r_av, b.r1, sizeof(double) * k, cudaMemcpyDefault, s));
   GK_CUDA(cudaMemcpyAsync(r_atu, b.r2, sizeof(double) * k, cudaMemcpyDefault, s));

@@ -146,6 +146,18 @@ cudaError_t fused_matvec(const Op &A, const float *x32, double *w, const double 
 cudaError_t fused_finish(const Op &A, const double *zpart, const double *alpha, const double *sub, double *z,
                          const Ctl *ctl, cudaStream_t s, const Dev &d);
 
+// ---- FP64-grade block products (gk_accurate.cu) ----------------------------
+// Dense f32/bf16/f16 operators: out (column-major, ld = output length) = scale op(A) X for
+// the k f64 vectors X (column-major, ld = input length), every product and sum carried in
+// double-f32 (exact to ~2^-47 sum |a x|); split holds accurate_floats() floats.
+bool accurate_ok(const Op &A);
+size_t accurate_floats(const Op &A, int k);
+cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, double *out, float *split,
+                              cudaStream_t s);
+// res[j] = || Y[:, j] - S[j] W[:, j] ||, columns of length len (ld = len)
+cudaError_t resid_norms(const double *Y, const double *W, const double *S, int64_t len, int k, double *res,
+                        cudaStream_t s);
+
 // ---- Gram-Schmidt and vector kernels (gk_orth.cu) -------------------------
 // Classical Gram-Schmidt of w (len) against the first j columns of Q (ld):
 // passes = 1..3 passes, or 0 = one pass and a second only if the first left less

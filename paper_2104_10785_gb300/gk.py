@@ -25,6 +25,7 @@ GK_DENSE, GK_CSR = 0, 1
 GK_FLAG_PROFILE = 1
 GK_FLAG_AUTOTUNE = 2
 GK_FLAG_FUSED = 4
+GK_FLAG_REFINE = 8
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -54,7 +55,8 @@ class gk_info(C.Structure):
         ("resid_est_max", C.c_double), ("sigma_est", C.c_double), ("seconds", C.c_double),
         ("ms_matvec", C.c_double), ("ms_matvec_t", C.c_double), ("ms_orth", C.c_double), ("ms_small", C.c_double),
         ("ms_restart", C.c_double), ("n_matvec", C.c_int64), ("n_matvec_t", C.c_int64), ("launches", C.c_int64),
-        ("ms_copy", C.c_double),
+        ("ms_copy", C.c_double), ("resid_true_max", C.c_double), ("ms_refine", C.c_double),
+        ("refine_checks", C.c_int32), ("reserved2", C.c_int32),
     ]
 
     def as_dict(self):
@@ -252,9 +254,9 @@ def default_opts() -> gk_opts:
 
 
 def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, eps_absolute=False, seed=None,
-          start=None, stream=None, workspace=None, profile=False, fused=False):
+          start=None, stream=None, workspace=None, profile=False, fused=False, refine=False):
     o = default_opts()
-    o.flags = (GK_FLAG_PROFILE if profile else 0) | (GK_FLAG_FUSED if fused else 0)
+    o.flags = (GK_FLAG_PROFILE if profile else 0) | (GK_FLAG_FUSED if fused else 0) | (GK_FLAG_REFINE if refine else 0)
     o.krylov_dim = int(krylov_dim)
     o.keep = int(keep)
     if max_restarts is not None:
@@ -280,13 +282,16 @@ def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, e
 
 def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0, max_restarts: int | None = None,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
-            scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False):
+            scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
+            refine: bool = False):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
     for a host operator: the library copies host data itself).  fused=True runs the fused
     sweep, one pass over A per step (GK_FLAG_FUSED); info["reserved"] is the fused kernel's
-    cluster size (0 when the steps ran as two passes).
+    cluster size (0 when the steps ran as two passes).  refine=True checks the returned
+    triplets' true residuals with FP64-grade products and keeps restarting while one exceeds
+    tol (GK_FLAG_REFINE; info["resid_true_max"], info["ms_refine"]).
     """
     M, keep_a = make_matrix(A, scale)
     dev = A.device
@@ -301,7 +306,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     else:
         U, S, V = out
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
-                  reorth_passes, False, seed, start, stream, workspace, profile, fused)
+                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine)
     info = gk_info()
     st = lib().gk_psvd(C.byref(M), int(k), float(tol), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
     if check and st < 0:

@@ -119,3 +119,44 @@ def test_batched_psvd_autotune_and_single_problem_agree():
         np.testing.assert_allclose(S1.cpu().numpy(), S2.cpu().numpy(), rtol=1e-12)
         Us, Ss, Vs, st, _ = M.gk_psvd(pr["A"], 5, 1e-8, krylov_dim=20)
         np.testing.assert_allclose(S1.cpu().numpy(), Ss.cpu().numpy(), rtol=1e-6)
+
+
+def test_batched_recipe_sample_matches_oracle():
+    """A sample of the benchmark's own 512-problem recipe (dense f32, m up to 4096, ranks 5..64 plus
+    1e-6 noise, rank cut eps = 1e-5, tol 1e-8) in the two configurations the benchmark runs:
+      * plain pipeline: k = the true rank, K = max(2r, r + 16) -- the six highest-rank problems,
+        whose K > 78 takes the cluster-wide Jacobi branch of the small SVD;
+      * learned pipeline: the committed network's (r^, K^) -- the four largest operators (the
+        row-ring and panel paths of the products at m, n near 4096).
+    Each problem's rank, values and FP64 true residuals (oracle) against the oracle's partial SVD of
+    the same stored bytes."""
+    from paper_2104_10785_gb300 import predictor
+
+    w = synth.WORKLOADS["batched_f32_512_rank5to64"]
+    shapes = synth.batched_shapes(w["count"], w["seed"])
+    mats = synth.torch_batched_products(shapes, 1e-6, w["seed"])
+    params = predictor.load()
+    assert params is not None
+    pred = predictor.predict(mats, params)
+    high_r = sorted(range(len(mats)), key=lambda i: -shapes[i][2])[:6]
+    big = sorted((i for i in range(len(mats)) if i not in high_r), key=lambda i: -shapes[i][0] * shapes[i][1])[:4]
+    plain = [dict(A=mats[i], k=shapes[i][2], krylov_dim=min(max(2 * shapes[i][2], shapes[i][2] + 16),
+                                                               min(shapes[i][:2])), tol=w["tol"]) for i in high_r]
+    assert min(p["krylov_dim"] for p in plain) > 78
+    learned = [dict(A=mats[i], k=pred[i][0], krylov_dim=pred[i][1], tol=w["tol"], rank_cut=w["eps"]) for i in big]
+    oracle.set_threads(0)
+    for probs, idx in ((plain, high_r), (learned, big)):
+        res, st, info = gk().gk_psvd_batched(probs)
+        assert st == 0, [r[3]["status"] for r in res]
+        for (U, S, V, rr), i in zip(res, idx):
+            m, n, r = shapes[i]
+            assert rr["rank"] == r, (i, rr["rank"], r)
+            op = oracle.Operator.dense(np.ascontiguousarray(mats[i].cpu().numpy()))
+            K = min(max(2 * r, r + 16), min(m, n))
+            Uo, So, Vo, io = oracle.psvd(op, r, K, synth.start_vector(m, i), tol=1e-12, max_restarts=500)
+            Sg = S.cpu().numpy()[:r]
+            np.testing.assert_allclose(Sg, So, rtol=1e-6)
+            r1, r2 = oracle.residuals(op, U.cpu().numpy()[:, :r], Sg, V.cpu().numpy()[:, :r])
+            res_rel = max(r1.max(), r2.max()) / So[0]
+            # the convergence test bounds the Ritz residual by tol; the f32 products add their floor
+            assert res_rel <= 3e-8, (i, shapes[i], res_rel)

@@ -91,6 +91,35 @@ def test_dense_products_match_oracle(dtype, shape):
         assert np.all(np.abs(got_t - ref_t) <= bound_t)
 
 
+@pytest.mark.parametrize("dtype,m,n", [("bf16", 20000, 8192), ("f32", 50000, 4096)])
+def test_dense_products_bulk_path_many_units_per_block(dtype, m, n):
+    """16-byte rows take the bulk-copy A x kernel; here the work units (row groups of 128 x
+    2048-byte column chunks: 1256 and 3128 of them) outnumber the resident blocks several times,
+    so every block runs its ring of stages across several units (the full-size configuration),
+    and A^T x runs row blocks of 1024 rows.  Element-wise against the oracle."""
+    g = torch.Generator(device="cuda").manual_seed(m + n)
+    At = torch.randn(m, n, generator=g, device="cuda", dtype=torch.float32)
+    At = At.to(torch.bfloat16) if dtype == "bf16" else At
+    x = torch.randn(n, generator=g, device="cuda", dtype=torch.float64)
+    y = torch.randn(m, generator=g, device="cuda", dtype=torch.float64)
+    M = gk()
+    got = M.gk_matvec(At, x).cpu().numpy()
+    got_t = M.gk_matvec(At, y, trans=True).cpu().numpy()
+    if dtype == "bf16":
+        bits = At.view(torch.int16).cpu().numpy().view(np.uint16)
+        op = oracle.Operator.dense(None, dtype="bf16", bits=bits)
+        Ad = synth.bf16_bits_to_f32(bits).astype(np.float64)
+    else:
+        A32 = At.cpu().numpy()
+        op = oracle.Operator.dense(A32)
+        Ad = A32.astype(np.float64)
+    oracle.set_threads(0)
+    xh, yh = x.cpu().numpy(), y.cpu().numpy()
+    ref, ref_t = op.matvec(xh), op.rmatvec(yh)
+    assert np.all(np.abs(got - ref) <= U32 * 66 * (np.abs(Ad) @ np.abs(xh)))
+    assert np.all(np.abs(got_t - ref_t) <= U32 * 66 * (np.abs(Ad).T @ np.abs(yh)))
+
+
 def test_dense_products_padded_rows_and_unaligned_ld():
     """ld > n with rows that are not 16-byte aligned takes the scalar path."""
     g = synth.rng(5)
