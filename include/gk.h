@@ -81,8 +81,12 @@ typedef struct {
   const int32_t *t_colind;
 } gk_matrix;
 
+/* A loaded learned predictor (gk_predictor_load); opaque. */
+typedef struct gk_predictor gk_predictor;
+
 typedef struct {
-  int32_t krylov_dim;    /* K, the Krylov dimension of one restart cycle (0 = default min(max(2k, k+16), min(m,n))) */
+  int32_t krylov_dim;    /* K, the Krylov dimension of one restart cycle (0 = default min(max(2k, k+16), min(m,n)),
+                            or the predictor's choice when opts->predictor is set) */
   int32_t keep;          /* Ritz vectors kept at a restart (0 = k + (K-k)/2) */
   int32_t max_restarts;  /* restart budget of gk_psvd (default 200) */
   int32_t reorth_passes; /* classical Gram-Schmidt per vector: 0 (default) = one pass, and a second
@@ -96,13 +100,16 @@ typedef struct {
   void *stream;          /* cudaStream_t, NULL = legacy default stream */
   void *workspace;       /* optional caller-owned device workspace */
   size_t workspace_bytes;
+  const gk_predictor *predictor; /* optional learned predictor (NULL = none): gk_psvd takes K from it
+                                    when krylov_dim is 0; gk_psvd_batched runs the learned pipeline */
 } gk_opts;
 
 typedef struct {
   int32_t steps;         /* bidiagonalization steps taken (left+right half-steps count as one) */
   int32_t restarts;
   int32_t cycles;
-  int32_t kprime;        /* gk_numrank: k' of Algorithm 1 (columns of B_{k'+1,k'}) */
+  int32_t kprime;        /* gk_numrank, gk_fsvd: k' of Algorithm 1 (columns of B_{k'+1,k'}); gk_psvd: the
+                            Krylov dimension used */
   int32_t stop_reason;   /* gk_numrank: 0 reached kmax, 1 beta break, 2 alpha break */
   int32_t breakdowns;    /* exact breakdowns replaced by fresh directions */
   int32_t svd_sweeps;    /* gk_psvd: Jacobi sweeps of the last small SVD (negative: sweep limit reached);
@@ -129,7 +136,7 @@ typedef struct {
                             / s_1 of the returned triplets, FP64-grade (0 when not checked) */
   double ms_refine;      /* gk_psvd with GK_FLAG_REFINE: wall milliseconds of those checks */
   int32_t refine_checks; /* gk_psvd with GK_FLAG_REFINE: checks run (1 = the first passed) */
-  int32_t reserved2;
+  int32_t fallbacks;     /* gk_psvd_batched with a predictor: problems re-solved by the plain pipeline */
 } gk_info;
 
 /* Fill *opts with the defaults above. */
@@ -186,12 +193,17 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
                gk_info *info);
 
 /* F-SVD as printed (Algorithm 2): k steps of Algorithm 1 (lower-bidiagonal GK
- * with reorthogonalization; only an exact zero norm ends them early), the SVD
- * of B_{k'+1,k'} = X Sigma Y^T (one-sided Jacobi, the route to eig(B^T B)
- * without forming B^T B), V = P Y, and, for the r largest:
- *  route 1: u_i = Q x_i (the left Ritz vectors, Eq. 2.13);
- *  route 0: u_i = A v_i / sigma_i (the printed formula, one product per
- *           triplet), which equals Q x_i in exact arithmetic.
+ * with reorthogonalization; only an exact zero norm ends them early), then for
+ * the r largest:
+ *  route 0 (the printed algorithm): the eigendecomposition of B^T B (formed;
+ *           tridiagonal) = Y Theta Y^T by one-sided Jacobi (its SVD, as it is
+ *           positive semidefinite), sigma_i = sqrt(theta_i), V = P Y, and
+ *           u_i = A v_i / sigma_i for all r triplets in one blocked pass over A
+ *           (FP64-grade products, as gk_residuals);
+ *  route 1: the SVD of B_{k'+1,k'} = X Sigma Y^T itself (one-sided Jacobi,
+ *           without squaring B's condition number), V = P Y, u_i = Q x_i (the
+ *           left Ritz vectors, Eq. 2.13), equal to A v_i / sigma_i in exact
+ *           arithmetic.
  * No restart: the accuracy is what k steps give (compare gk_psvd).
  *  k:   Krylov steps, 1 <= k <= min(m, n), k <= 1023.
  *  r:   triplets wanted, 1 <= r <= k.
@@ -267,7 +279,25 @@ typedef struct {
  * problems (the leading CTA's SM clock at the max clock rate): ms_matvec the
  * A v products, ms_matvec_t the A^T u products with their cluster reduction,
  * ms_orth Gram-Schmidt and normalization, ms_small the projected matrix, its
- * SVD and the test, ms_restart setup, restarts and the output vectors. */
+ * SVD and the test, ms_restart setup, restarts and the output vectors.
+ *
+ * Learned pipeline (opts->predictor set; the paper has no counterpart): each
+ * problem's numerical rank and Krylov dimension come from the network on its
+ * sketch features instead of a separate rank pass.  Per item: k = the capacity
+ * of U, S, V (columns available, >= 1), rank_cut = Algorithm 3's relative
+ * threshold eps (0 < eps < 1, required), tol as usual, krylov_dim 0 (or a
+ * fixed K).  The call predicts (r^, K^) = (ceil(1.05 r) + 1, ceil(K) + 2 + the
+ * same margin, clamped to r^ <= k and r^ + 2 <= K^ <= min(m, n, 500)), solves
+ * every problem for r^ triplets at K^ with the rank cut in one launch, and
+ * judges each by its own spectrum: accepted when some Ritz value of the last
+ * projected matrix fell below the cut (rank < r^, or sigma_next <= eps s_1);
+ * otherwise (r^ too small, or a solve that did not converge) that problem is
+ * re-solved by the plain pipeline -- Algorithm 3 for its rank r (kmax
+ * min(m, n, 160)), then min(r, k) triplets at the default K.  Results: rank
+ * (the numerical rank; above k when the capacity truncated the output), the
+ * last solve's counters, matvecs including the sketch's pass;
+ * gk_info.fallbacks counts the re-solved problems.  A Krylov dimension that
+ * is too small costs restarts; a rank that is too small costs the re-solve. */
 int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
 
 /* Many independent rank estimates (Algorithm 3 on Algorithm 1, as in
@@ -366,6 +396,29 @@ const char *gk_version(void);
  * return), GK_NO_DEVICE, GK_OUT_OF_MEMORY (mmap), GK_CUDA_ERROR (registration). */
 int gk_host_alloc(size_t bytes, void **ptr);
 int gk_host_free(void *ptr);
+
+/* Load the learned predictor's weights (GK_MLP_PARAMS f32 values: the layout of
+ * gk_mlp_train's parameters, host or device memory, `bytes` =
+ * 4 * GK_MLP_PARAMS) into device memory of the current device; *pred receives
+ * a handle for opts->predictor, owned by the caller until gk_predictor_free.
+ * Inference uses the bf16 rounding of the weights with f32 sums, on sketch
+ * features drawn with the seed the committed weights were trained with.
+ * Errors: GK_INVALID_ARG (null pointers, wrong size, a non-finite weight),
+ * GK_NO_DEVICE, GK_OUT_OF_MEMORY, GK_CUDA_ERROR. */
+int gk_predictor_load(const void *weights, size_t bytes, gk_predictor **pred);
+int gk_predictor_free(gk_predictor *pred);
+
+/* The (r^, K^) the learned batched pipeline derives from the network's rank and
+ * Krylov estimates rf = exp(out_r), kf = exp(out_K) for an operator with
+ * min(m, n) = mn and output capacity cap: r^ = min(ceil(1.05 rf) + 1,
+ * min(mn, 500) - 1, cap) (at least 1), K^ = ceil(kf) + 2 + (r^ - round(rf))
+ * within [r^ + 2, min(mn, 500)] where there is room (never below r^); a
+ * non-finite estimate asks for min(mn, 500).  Host-only (no device needed). */
+int gk_predictor_margins(double rf, double kf, int64_t mn, int cap, int *r, int *K);
+
+/* The network's de-standardized outputs (log r, log K) for `count` dense
+ * device operators: out[2 i], out[2 i + 1] (f32, host or device). */
+int gk_predictor_predict(const gk_predictor *pred, const gk_matrix *A, int count, float *out, const gk_opts *opts);
 
 /* Self-test of the device-side bounded wait that every spin of the library
  * uses (mbarrier waits of the bulk-copy pipelines): one CTA waits on an

@@ -542,11 +542,28 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   int rc = check_matrix(Ain);
   if (rc) return rc;
   if (!U || !S || !V || !(tol >= 0.0) || !isfinite(tol)) return GK_INVALID_ARG;
-  const gk_opts o = oin ? *oin : defaults();
+  gk_opts o = oin ? *oin : defaults();
+  cudaStream_t s = (cudaStream_t)o.stream;
+  // the learned Krylov dimension: from the sketch of a device operator now, of a host operator
+  // once it is staged (the workspace is laid out for the largest dimension a prediction allows)
+  bool predict_after_stage = false;
+  if (o.predictor && o.krylov_dim <= 0) {
+    if (Ain->kind != GK_DENSE || k < 1) return GK_INVALID_ARG;
+    const int64_t mn = Ain->m < Ain->n ? Ain->m : Ain->n;
+    if (!on_host(Ain->vals)) {
+      int Kp = 0;
+      rc = predict_krylov(o.predictor, Ain, k, s, &Kp);
+      if (rc) return rc;
+      o.krylov_dim = Kp;
+    } else {
+      const int64_t kmax = mn < 500 ? mn : 500;
+      o.krylov_dim = (int)(kmax > k ? kmax : mn);
+      predict_after_stage = true;
+    }
+  }
   PsvdPlan p;
   rc = psvd_plan(Ain, k, o, &p);
   if (rc) return rc;
-  cudaStream_t s = (cudaStream_t)o.stream;
   OpStage st;
   rc = stage_plan(Ain, &st);
   if (rc) return rc;
@@ -568,6 +585,20 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   rc = stage_copy(Ain, st, op, s);
   prof.end();
   if (rc) return rc;
+  if (predict_after_stage) {
+    gk_matrix Astaged = *Ain;
+    Astaged.vals = op.vals;
+    Astaged.ld = op.ld;
+    int Kp = 0;
+    rc = predict_krylov(o.predictor, &Astaged, k, s, &Kp);
+    if (rc) return rc;
+    o.krylov_dim = Kp;
+    PsvdPlan p2;
+    rc = psvd_plan(Ain, k, o, &p2);
+    if (rc) return rc;
+    p.K = p2.K;  // within the layout: the workspace holds the largest dimension
+    p.keep = p2.keep;
+  }
 
   const int64_t m = p.m, n = p.n, ldu = p.ldu, ldv = p.ldv;
   const int K = p.K;
@@ -764,6 +795,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   inf.sigma_est = hc.ctl.sest;
   inf.svd_sweeps = sweeps;
   inf.reserved = p.fused ? fused_cluster(op, d) : 0;
+  inf.kprime = K;  // the Krylov dimension used
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
   if (info) *info = inf;
@@ -972,10 +1004,11 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
 // ---------------------------------------------------------------------------
 struct FsvdBufs {
   double *Bm, *Yw, *X, *Y, *sigma, *nrm, *Uo, *So, *Vo;
+  float *split;
   int *pos, *sweeps;
 };
 
-size_t fsvd_layout(char *base, int k, int r, int64_t m, int64_t n, bool host_out, FsvdBufs *f) {
+size_t fsvd_layout(char *base, int k, int r, int64_t m, int64_t n, bool host_out, size_t split_floats, FsvdBufs *f) {
   Carve cv{base, 0};
   const size_t K = (size_t)k + 1;
   f->Bm = cv.take<double>(K * K);
@@ -989,6 +1022,7 @@ size_t fsvd_layout(char *base, int k, int r, int64_t m, int64_t n, bool host_out
   f->Uo = host_out ? cv.take<double>((size_t)m * r) : nullptr;
   f->So = host_out ? cv.take<double>((size_t)r) : nullptr;
   f->Vo = host_out ? cv.take<double>((size_t)n * r) : nullptr;
+  f->split = split_floats ? cv.take<float>(split_floats) : nullptr;
   return cv.off + 256;
 }
 
@@ -1021,13 +1055,14 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
   b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   FsvdBufs f;
   const size_t nb = (numrank_layout(Ain, k, d, st, false, host_start, nullptr, &b, &op) + 255) / 256 * 256;
-  const size_t fb = fsvd_layout(nullptr, k, r, m, n, host_out, &f);
+  const size_t split_floats = (route == 0 && accurate_ok(op)) ? accurate_floats(op, r) : 0;
+  const size_t fb = fsvd_layout(nullptr, k, r, m, n, host_out, split_floats, &f);
   Workspace ws;
   rc = acquire(ws, nb + fb, o, s);
   if (rc) return rc;
   op = make_op(Ain);
   numrank_layout(Ain, k, d, st, false, host_start, ws.base, &b, &op);
-  fsvd_layout(ws.base + nb, k, r, m, n, host_out, &f);
+  fsvd_layout(ws.base + nb, k, r, m, n, host_out, split_floats, &f);
   rc = stage_copy(Ain, st, op, s);
   if (rc) return rc;
   Prof prof;
@@ -1051,27 +1086,42 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
     if (hc.ctl.halt && hc.ctl.side == 0) GK_CUDA(cudaMemsetAsync(b.Q + (int64_t)kp * ldu, 0, sizeof(double) * m, s));
     rc = clear_halt(b.ctl, s);
     if (rc) return rc;
-    const int K = kp + 1;
-    prof.begin(PC_SMALL);
-    GK_CUDA(assemble_lower(f.Bm, kp, b.alpha, b.beta, s));
-    GK_CUDA(small_svd(f.Bm, f.Yw, K, f.sigma, f.X, f.Y, f.nrm, f.pos, f.sweeps, b.ctl, s));
-    prof.end();
-    prof.begin(PC_RESTART);
-    // V = P Y: the first kp rows of Y (the zero padding column is never rotated)
-    GK_CUDA(ritz_gemm(b.P, ldv, n, kp, f.Y, K, rr, Vo, n, s, d));
     if (route == 1) {
+      // the SVD of B_{k'+1,k'} itself (padded with a zero column to a square): V = P Y, U = Q X
+      const int K = kp + 1;
+      prof.begin(PC_SMALL);
+      GK_CUDA(assemble_lower(f.Bm, kp, b.alpha, b.beta, s));
+      GK_CUDA(small_svd(f.Bm, f.Yw, K, f.sigma, f.X, f.Y, f.nrm, f.pos, f.sweeps, b.ctl, s));
+      prof.end();
+      prof.begin(PC_RESTART);
+      // V = P Y: the first kp rows of Y (the zero padding column is never rotated)
+      GK_CUDA(ritz_gemm(b.P, ldv, n, kp, f.Y, K, rr, Vo, n, s, d));
       GK_CUDA(ritz_gemm(b.Q, ldu, m, K, f.X, K, rr, Uo, m, s, d));
+      prof.end();
     } else {
-      // the printed route: u_i = A v_i / sigma_i, one product per triplet
-      for (int i = 0; i < rr; ++i) {
-        double *vi = Vo + (int64_t)i * n, *ui = Uo + (int64_t)i * m;
-        GK_CUDA(copy_vec(nullptr, b.x32, vi, n, s));
-        GK_CUDA(matvec(op, b.x32, vi, ui, nullptr, nullptr, b.part, b.ctl, s, d));
-        GK_CUDA(scale_inv(ui, m, f.sigma + i, s));
+      // Algorithm 2 as printed: the eigendecomposition of B^T B (formed, tridiagonal; its one-sided
+      // Jacobi SVD is its eigendecomposition since it is positive semidefinite), sigma = sqrt(theta),
+      // V = P Y, and u_i = A v_i / sigma_i for all r triplets in one blocked pass over A
+      prof.begin(PC_SMALL);
+      GK_CUDA(assemble_btb(f.Bm, kp, b.alpha, b.beta, s));
+      GK_CUDA(small_svd(f.Bm, f.Yw, kp, f.sigma, f.X, f.Y, f.nrm, f.pos, f.sweeps, b.ctl, s));
+      GK_CUDA(sqrt_vals(f.sigma, kp, s));
+      prof.end();
+      prof.begin(PC_RESTART);
+      GK_CUDA(ritz_gemm(b.P, ldv, n, kp, f.Y, kp, rr, Vo, n, s, d));
+      if (accurate_ok(op)) {
+        GK_CUDA(accurate_products(op, false, Vo, rr, Uo, f.split, s));
+      } else {
+        for (int i = 0; i < rr; ++i) {
+          double *vi = Vo + (int64_t)i * n, *ui = Uo + (int64_t)i * m;
+          GK_CUDA(copy_vec(nullptr, b.x32, vi, n, s));
+          GK_CUDA(matvec(op, b.x32, vi, ui, nullptr, nullptr, b.part, b.ctl, s, d));
+        }
       }
+      GK_CUDA(scale_cols(Uo, m, rr, f.sigma, s));
+      prof.end();
       inf.matvecs += rr;
     }
-    prof.end();
     GK_CUDA(cudaMemcpyAsync(So, f.sigma, sizeof(double) * rr, cudaMemcpyDeviceToDevice, s));
     GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, rr, s));
     GK_CUDA(cudaMemcpyAsync(&sweeps, f.sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -1827,6 +1827,7 @@ extern "C" int gk_wait_selftest(long long cycles) {
 }
 
 extern "C" int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info) {
+  if (opts && opts->predictor) return gk::learned_batched(items, count, opts, info);
   return gk::batched_impl(items, count, 0, opts, info);
 }
 

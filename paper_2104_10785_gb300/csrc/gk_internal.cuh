@@ -158,6 +158,13 @@ cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, d
 cudaError_t resid_norms(const double *Y, const double *W, const double *S, int64_t len, int k, double *res,
                         cudaStream_t s);
 
+// ---- learned predictor (gk_predict.cu) -------------------------------------
+// Krylov dimension for the top-k partial SVD of the dense device operator A from its sketch
+// features: ceil(exp(out_K)) + 2, clamped to [k + 2, min(m, n, 500)].
+int predict_krylov(const gk_predictor *p, const gk_matrix *A, int k, cudaStream_t s, int *K);
+// gk_psvd_batched with opts->predictor set
+int learned_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
+
 // ---- Gram-Schmidt and vector kernels (gk_orth.cu) -------------------------
 // Classical Gram-Schmidt of w (len) against the first j columns of Q (ld):
 // passes = 1..3 passes, or 0 = one pass and a second only if the first left less
@@ -191,6 +198,12 @@ cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const doub
 // Bm = the lower-bidiagonal B_{kp+1,kp} (alpha[0..kp-1] on the diagonal, beta[1..kp] below it)
 // padded with a zero column to (kp+1) x (kp+1), column-major
 cudaError_t assemble_lower(double *Bm, int kp, const double *alpha, const double *beta, cudaStream_t s);
+// Bm = B^T B (kp x kp, tridiagonal) of the lower-bidiagonal B_{kp+1,kp}
+cudaError_t assemble_btb(double *Bm, int kp, const double *alpha, const double *beta, cudaStream_t s);
+// theta[0:n] = sqrt(max(theta, 0))
+cudaError_t sqrt_vals(double *theta, int n, cudaStream_t s);
+// column i of U (len x ncol) /= sigma[i] (unchanged when sigma[i] <= 0)
+cudaError_t scale_cols(double *U, int64_t len, int ncol, const double *sigma, cudaStream_t s);
 // y[0:len] /= *d (unchanged when *d <= 0)
 cudaError_t scale_inv(double *y, int64_t len, const double *d, cudaStream_t s);
 // One-sided Jacobi SVD of the K x K matrix Bm (overwritten; Yw is K x K work,

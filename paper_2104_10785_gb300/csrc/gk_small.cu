@@ -66,6 +66,38 @@ __global__ void k_assemble_lower(double *__restrict__ Bm, int kp, const double *
   }
 }
 
+// Bm = B^T B (kp x kp, column-major) for the lower-bidiagonal B_{kp+1,kp} (alpha[0..kp-1] on its
+// diagonal, beta[1..kp] below it): tridiagonal, diag alpha_c^2 + beta_{c+1}^2, off-diagonal
+// beta_{c+1} alpha_{c+1}
+__global__ void k_assemble_btb(double *__restrict__ Bm, int kp, const double *__restrict__ alpha,
+                               const double *__restrict__ beta) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)kp * kp;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % kp), c = (int)(idx / kp);
+    double v = 0.0;
+    if (r == c) v = alpha[c] * alpha[c] + beta[c + 1] * beta[c + 1];
+    else if (r == c + 1) v = beta[c + 1] * alpha[c + 1];
+    else if (c == r + 1) v = beta[r + 1] * alpha[r + 1];
+    Bm[idx] = v;
+  }
+}
+
+// theta[i] = sqrt(max(theta[i], 0)) for i < n
+__global__ void k_sqrt_vals(double *__restrict__ theta, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    theta[i] = theta[i] > 0.0 ? sqrt(theta[i]) : 0.0;
+}
+
+// column i of U (len x ncol, column-major) /= sigma[i] (left as is when sigma[i] is not positive)
+__global__ void k_scale_cols(double *__restrict__ U, int64_t len, int ncol, const double *__restrict__ sigma) {
+  const int c = blockIdx.y;
+  const double v = sigma[c];
+  if (!(v > 0.0)) return;
+  const double f = 1.0 / v;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    U[(int64_t)c * len + i] *= f;
+}
+
 // y[i] /= *d for i < len (left as is when *d is not positive)
 __global__ void k_scale_inv(double *__restrict__ y, int64_t len, const double *__restrict__ d) {
   const double v = *d;
@@ -208,6 +240,28 @@ cudaError_t assemble_lower(double *Bm, int kp, const double *alpha, const double
   int64_t blocks = ((int64_t)(kp + 1) * (kp + 1) + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   GK_LAUNCH(k_assemble_lower<<<(int)blocks, 256, 0, s>>>(Bm, kp, alpha, beta));
+  return cudaGetLastError();
+}
+
+cudaError_t assemble_btb(double *Bm, int kp, const double *alpha, const double *beta, cudaStream_t s) {
+  int64_t blocks = ((int64_t)kp * kp + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  GK_LAUNCH(k_assemble_btb<<<(int)blocks, 256, 0, s>>>(Bm, kp, alpha, beta));
+  return cudaGetLastError();
+}
+
+cudaError_t sqrt_vals(double *theta, int n, cudaStream_t s) {
+  GK_LAUNCH(k_sqrt_vals<<<1, 256, 0, s>>>(theta, n));
+  return cudaGetLastError();
+}
+
+cudaError_t scale_cols(double *U, int64_t len, int ncol, const double *sigma, cudaStream_t s) {
+  if (ncol <= 0) return cudaSuccess;
+  int64_t bx = (len + 255) / 256;
+  if (bx > 256) bx = 256;
+  if (bx < 1) bx = 1;
+  GK_LAUNCH(k_scale_cols<<<dim3((unsigned)bx, (unsigned)ncol), 256, 0, s>>>(U, len, ncol, sigma));
   return cudaGetLastError();
 }
 

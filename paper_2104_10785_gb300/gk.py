@@ -43,7 +43,7 @@ class gk_opts(C.Structure):
         ("krylov_dim", C.c_int32), ("keep", C.c_int32), ("max_restarts", C.c_int32),
         ("reorth_passes", C.c_int32), ("eps_absolute", C.c_int32), ("flags", C.c_int32),
         ("seed", C.c_uint64), ("start", C.c_void_p), ("stream", C.c_void_p),
-        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("predictor", C.c_void_p),
     ]
 
 
@@ -56,7 +56,7 @@ class gk_info(C.Structure):
         ("ms_matvec", C.c_double), ("ms_matvec_t", C.c_double), ("ms_orth", C.c_double), ("ms_small", C.c_double),
         ("ms_restart", C.c_double), ("n_matvec", C.c_int64), ("n_matvec_t", C.c_int64), ("launches", C.c_int64),
         ("ms_copy", C.c_double), ("resid_true_max", C.c_double), ("ms_refine", C.c_double),
-        ("refine_checks", C.c_int32), ("reserved2", C.c_int32),
+        ("refine_checks", C.c_int32), ("fallbacks", C.c_int32),
     ]
 
     def as_dict(self):
@@ -142,6 +142,15 @@ def lib():
             L.gk_launch_count.restype = C.c_int64
             L.gk_wait_selftest.argtypes = [C.c_longlong]
             L.gk_wait_selftest.restype = C.c_int
+            L.gk_predictor_load.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]
+            L.gk_predictor_load.restype = C.c_int
+            L.gk_predictor_free.argtypes = [C.c_void_p]
+            L.gk_predictor_free.restype = C.c_int
+            L.gk_predictor_predict.argtypes = [C.c_void_p, P(gk_matrix), C.c_int, C.c_void_p, P(gk_opts)]
+            L.gk_predictor_predict.restype = C.c_int
+            L.gk_predictor_margins.argtypes = [C.c_double, C.c_double, C.c_int64, C.c_int, C.POINTER(C.c_int),
+                                               C.POINTER(C.c_int)]
+            L.gk_predictor_margins.restype = C.c_int
             L.gk_host_alloc.argtypes = [C.c_size_t, C.POINTER(C.c_void_p)]
             L.gk_host_alloc.restype = C.c_int
             L.gk_host_free.argtypes = [C.c_void_p]
@@ -207,6 +216,43 @@ def launch_count() -> int:
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Predictor:
+    """A learned predictor loaded into the library (gk_predictor_load): pass it as predictor= to
+    gk_psvd (the Krylov dimension) or gk_psvd_batched (the learned pipeline)."""
+
+    def __init__(self, params):
+        w = params.detach().to(torch.float32).contiguous()
+        h = C.c_void_p()
+        st = lib().gk_predictor_load(C.c_void_p(w.data_ptr()), w.numel() * 4, C.byref(h))
+        if st < 0:
+            raise GKError(st, "gk_predictor_load")
+        self.handle = h.value
+        self._lib = lib()
+
+    def predict(self, mats, stream=None):
+        """(count x 2) float32 host array of (log r, log K) for dense device operators."""
+        import numpy as np
+
+        n = len(mats)
+        arr = (gk_matrix * n)()
+        for i, A in enumerate(mats):
+            arr[i], _ = make_matrix(A)
+        out = np.zeros((n, 2), dtype=np.float32)
+        o = default_opts()
+        s = stream if stream is not None else torch.cuda.current_stream(mats[0].device)
+        o.stream = s.cuda_stream
+        st = lib().gk_predictor_predict(C.c_void_p(self.handle), arr, n, C.c_void_p(out.ctypes.data), C.byref(o))
+        if st < 0:
+            raise GKError(st, "gk_predictor_predict")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self._lib.gk_predictor_free(C.c_void_p(h))
+            self.handle = None
 
 
 @dataclass
@@ -283,7 +329,7 @@ def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, e
 def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0, max_restarts: int | None = None,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
             scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
-            refine: bool = False):
+            refine: bool = False, predictor: "Predictor | None" = None):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
@@ -291,7 +337,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     sweep, one pass over A per step (GK_FLAG_FUSED); info["reserved"] is the fused kernel's
     cluster size (0 when the steps ran as two passes).  refine=True checks the returned
     triplets' true residuals with FP64-grade products and keeps restarting while one exceeds
-    tol (GK_FLAG_REFINE; info["resid_true_max"], info["ms_refine"]).
+    tol (GK_FLAG_REFINE; info["resid_true_max"], info["ms_refine"]).  predictor (a Predictor)
+    chooses the Krylov dimension from A's sketch when krylov_dim is 0 (info["kprime"] = K used).
     """
     M, keep_a = make_matrix(A, scale)
     dev = A.device
@@ -307,6 +354,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
         U, S, V = out
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
                   reorth_passes, False, seed, start, stream, workspace, profile, fused, refine)
+    if predictor is not None:
+        o.predictor = predictor.handle
     info = gk_info()
     st = lib().gk_psvd(C.byref(M), int(k), float(tol), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
     if check and st < 0:
@@ -429,11 +478,14 @@ def _item_result(it):
 
 
 def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=None, autotune=False, stream=None,
-                    check=True, profile=False):
+                    check=True, profile=False, predictor=None):
     """Partial SVDs of many dense device operators in one persistent launch.
 
     problems: sequence of dicts with keys A (2-D CUDA tensor, n <= 4096), k, and optionally
-    krylov_dim, tol (default 1e-8), start, rank_cut (relative eps; triplets below it are not converged).  Returns (list of (U, S, V, result dict), status, info)."""
+    krylov_dim, tol (default 1e-8), start, rank_cut (relative eps; triplets below it are not converged).
+    With predictor (a Predictor) the library runs the learned pipeline: k is each problem's output
+    capacity and rank_cut its eps (see gk_psvd_batched in gk.h).  Returns (list of (U, S, V, result
+    dict), status, info)."""
     n = len(problems)
     items = (gk_batch_item * n)()
     keep = []
@@ -471,6 +523,8 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
         outs.append((U, S, V))
         keep.append(A)
     o = _batch_opts(dev, seed, max_restarts, reorth_passes, False, autotune, stream, profile)
+    if predictor is not None:
+        o.predictor = predictor.handle
     info = gk_info()
     status = lib().gk_psvd_batched(items, n, C.byref(o), C.byref(info))
     if check and status < 0:

@@ -1,7 +1,9 @@
-"""Learned rank / Krylov-dimension predictor for the batched solver.
+"""Learned rank / Krylov-dimension predictor: training orchestration and thin wrappers.
 
-Host orchestration only: every numerical step runs in libgk.so's kernels (sketch
-features, the batched solvers, the MLP forward/backward/Adam).
+The inference pipelines (the sketch, the network, the margins, the judge and the plain
+fallback) run inside libgk.so behind the C ABI (gk_predictor_load, opts->predictor in gk_psvd
+and gk_psvd_batched); this module trains the weights with the library's own kernels
+(forward/backward/Adam) and wraps those calls.
 
 Targets, measured by the plain method itself on each training matrix:
   r  = the rank gk_numrank_batched (Algorithm 3) returns at eps;
@@ -136,23 +138,43 @@ def load(device="cuda", path=PARAMS_FILE):
     return torch.from_numpy(a).to(device)
 
 
+def handle(params):
+    """The library-side predictor (gk.Predictor, gk_predictor_load) for a parameter tensor, kept on
+    the tensor itself and reloaded when the tensor has been modified in place since (its version
+    counter moved); a Predictor is returned as is."""
+    if isinstance(params, gk.Predictor):
+        return params
+    cached = getattr(params, "_gk_predictor", None)
+    if cached is not None and cached[0] == params._version:
+        return cached[1]
+    h = gk.Predictor(params)
+    params._gk_predictor = (params._version, h)
+    return h
+
+
 def predict_raw(mats, params, bf16=True):
-    """The network's de-standardized outputs (log r, log K) per operator (host array)."""
+    """The network's de-standardized outputs (log r, log K) per operator (host array): the
+    library's sketch and bf16-weight forward pass (gk_predictor_predict)."""
+    if bf16:
+        return handle(params).predict(mats)
     feats = gk.gk_sketch_batched(mats, SKETCH_SEED)
-    return gk.gk_mlp_forward(params, feats, bf16_weights=bf16).cpu().numpy()
+    return gk.gk_mlp_forward(params, feats, bf16_weights=False).cpu().numpy()
 
 
-def margins(rf, kf, mn):
+def margins(rf, kf, mn, cap=None):
     """(r^, K^) from the network's rank and Krylov estimates (rf, kf) for an operator with
-    min(m, n) = mn: r^ = ceil(1.05 rf) + 1 and K^ = ceil(kf) + 2 shifted by the same margin,
-    clamped to 1 <= r^ <= K^ <= min(mn, K_LIMIT) with K^ >= r^ + 2 where there is room; a
-    non-finite estimate asks for the whole range."""
+    min(m, n) = mn -- the rule the library's learned pipeline applies (gk_psvd_batched with a
+    predictor): r^ = ceil(1.05 rf) + 1 and K^ = ceil(kf) + 2 shifted by the same margin, clamped
+    to 1 <= r^ <= min(cap, K^) and K^ <= min(mn, K_LIMIT) with K^ >= r^ + 2 where there is room;
+    a non-finite estimate asks for the whole range."""
     lim = min(mn, K_LIMIT)
     if not math.isfinite(rf):
         rf = float(lim)
     if not math.isfinite(kf):
         kf = float(lim)
     ri = int(min(max(1, math.ceil(RANK_MARGIN[0] * rf) + RANK_MARGIN[1]), max(1, lim - 1)))
+    if cap is not None:
+        ri = min(ri, cap)
     Ki = int(math.ceil(kf)) + K_MARGIN + (ri - int(round(rf)))
     Ki = int(min(max(Ki, ri + 2), lim))
     return ri, max(Ki, ri)
@@ -179,39 +201,20 @@ def plain_batched(mats, eps=1e-5, tol=1e-8, autotune=True):
                             else max(st1, st), matvecs_per_problem=per)
 
 
-def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200, autotune=True):
-    """Predicted (rank, K), one batched partial SVD with the rank cut, judged by the solver's spectrum;
-    under-estimated ranks fall back to the plain pipeline."""
-    pred = predict(mats, params)
-    out, st, info = gk.gk_psvd_batched(
-        [dict(A=A, k=r, krylov_dim=K, tol=tol, rank_cut=eps) for A, (r, K) in zip(mats, pred)],
-        max_restarts=max_restarts, autotune=autotune)
-    ranks = []
-    redo = []
-    s1s = info["sigma_1"].cpu().numpy()  # one transfer for the whole batch
-    for i, (U, S, V, rr) in enumerate(out):
-        s1 = float(s1s[i]) if S.numel() else 0.0
-        seen_below = rr["rank"] < len(S) or rr["sigma_next"] <= eps * s1
-        if rr["status"] != gk.GK_OK or not seen_below:
-            redo.append(i)
-            ranks.append(None)
-        else:
-            ranks.append(max(1, rr["rank"]))
-    matvecs = info["matvecs"]
-    per = [o[3]["matvecs"] + 1 for o in out]  # + the sketch's pass over A
-    if redo:
-        rr_, out2, inf2 = plain_batched([mats[i] for i in redo], eps, tol, autotune=False)
-        for j, i in enumerate(redo):
-            ranks[i] = rr_[j]
-            out[i] = out2[j]
-            per[i] += inf2["matvecs_per_problem"][j]
-        matvecs += inf2["matvecs"]
-        st = min(st, inf2["status"]) if min(st, inf2["status"]) < 0 else max(st, inf2["status"])
+def learned_batched(mats, params, eps=1e-5, tol=1e-8, max_restarts=200, autotune=True, capacity=80):
+    """The library's learned pipeline (gk_psvd_batched with a predictor): predicted (rank, K), one
+    batched partial SVD with the rank cut, each problem judged by its own spectrum, the rejected ones
+    re-solved by the plain pipeline.  `capacity` = output columns per problem."""
+    h = handle(params)
+    probs = [dict(A=A, k=min(capacity, min(A.shape)), tol=tol, rank_cut=eps) for A in mats]
+    out, st, info = gk.gk_psvd_batched(probs, max_restarts=max_restarts, autotune=autotune, predictor=h)
+    ranks = [max(1, rr["rank"]) for (_, _, _, rr) in out]
     final = [(U[:, :r], S[:r], V[:, :r], rr) for (U, S, V, rr), r in zip(out, ranks)]
-    # without a fallback every problem's triplets sit in the solve's three output buffers (each
-    # problem's r^ >= r columns back to back): a caller can move them to the host in three copies
-    return ranks, final, dict(matvecs=matvecs, fallbacks=len(redo), status=st, predicted=pred,
-                              matvecs_per_problem=per, outputs=None if redo else info["outputs"])
+    # every problem's triplets sit in the call's three output buffers (each problem's capacity
+    # columns back to back): a caller can move them to the host in three copies
+    return ranks, final, dict(matvecs=info["matvecs"], fallbacks=info["fallbacks"], status=st,
+                              matvecs_per_problem=[rr["matvecs"] for (_, _, _, rr) in out],
+                              outputs=info["outputs"])
 
 
 def main(argv=None):
@@ -291,26 +294,19 @@ def krylov_dataset(count, seed, log=None):
 
 
 def predict_krylov(A, params, k=KRYLOV_K, margin=2, bf16=True):
-    """Krylov dimension for the top-k partial SVD of A from its sketch features."""
-    feats = gk.gk_sketch_batched([A], SKETCH_SEED)
-    out = gk.gk_mlp_forward(params, feats, bf16_weights=bf16).cpu().numpy()[0]
+    """Krylov dimension for the top-k partial SVD of A from its sketch features (the rule gk_psvd
+    applies with a predictor: ceil(exp(out_K)) + 2 within [k + 2, min(m, n, 500)])."""
+    out = predict_raw([A], params, bf16)[0]
     K = int(math.ceil(math.exp(min(max(float(out[1]), 0.0), 20.0)))) + margin
     return int(min(max(K, k + 2), min(A.shape), K_LIMIT))
 
 
 def learned_psvd(A, params, k=KRYLOV_K, tol=KRYLOV_TOL, out=None, **kw):
-    """gk_psvd with the predicted Krylov dimension (the restart loop covers a short one).  A host
-    operator is copied to the device first (the sketch reads device memory); with `out` (host
-    tensors U k x m, S k, V k x n) the results are copied back into them."""
-    Ad = A if A.device.type == "cuda" else A.to("cuda", non_blocking=True)
-    K = predict_krylov(Ad, params, k)
-    U, S, V, st, info = gk.gk_psvd(Ad, k, tol, krylov_dim=K, **kw)
-    info["krylov_dim"] = K
-    if out is not None:
-        out[0].copy_(U.T)
-        out[1].copy_(S)
-        out[2].copy_(V.T)
-        U, S, V = out[0].T, out[1], out[2].T
+    """gk_psvd with the predictor's Krylov dimension, through the C ABI (the library sketches the
+    operator; a host operator is staged by the library itself).  `out`: host tensors (U k x m, S k,
+    V k x n) for a host operator's results."""
+    U, S, V, st, info = gk.gk_psvd(A, k, tol, predictor=handle(params), out=out, **kw)
+    info["krylov_dim"] = info["kprime"]
     return U, S, V, st, info
 
 

@@ -64,12 +64,17 @@ def test_fsvd_f32_storage_and_both_routes():
     Uo, So, Vo, kp = oracle.fsvd(oracle.Operator.dense(A32), 40, 8, q1, route=1)
     assert st1 == st0 == 0
     np.testing.assert_allclose(S1.cpu().numpy(), So, rtol=1e-6)
-    np.testing.assert_allclose(S0.cpu().numpy(), S1.cpu().numpy(), rtol=0, atol=0)
+    # route 0's sqrt(eig(B^T B)) against route 1's SVD of B: equal up to the squared condition number
+    np.testing.assert_allclose(S0.cpu().numpy(), S1.cpu().numpy(), rtol=1e-12)
+    Uo0, So0, Vo0, _ = oracle.fsvd(oracle.Operator.dense(A32), 40, 8, q1, route=0)
+    np.testing.assert_allclose(S0.cpu().numpy(), So0, rtol=1e-6)
+    assert angle_err(V0.cpu().numpy(), Vo0) <= 1e-5
+    assert angle_err(U0.cpu().numpy(), Uo0) <= 1e-5
     assert angle_err(V1.cpu().numpy(), Vo) <= 1e-5
     assert angle_err(U1.cpu().numpy(), Uo) <= 1e-5
     # u_i = A v_i / sigma_i equals Q x_i in exact arithmetic (A P Y = Q B Y = Q X Sigma)
     assert angle_err(U0.cpu().numpy(), U1.cpu().numpy()) <= 1e-5
-    # the printed route spends one product per triplet on top of the sweep
+    # the printed route computes one product per triplet on top of the sweep (one blocked pass)
     assert info0["matvecs"] >= 2 * 40 + 8
 
 
@@ -100,3 +105,22 @@ def test_fsvd_rejects_bad_arguments():
             M.gk_fsvd(A, k, r)
     with pytest.raises(M.GKError):
         M.gk_fsvd(A, 10, 3, route=2)
+
+
+def test_fsvd_printed_route_bf16_blocked_products():
+    """Route 0 on a bf16 operator (the blocked double-f32 pass U = A V_r / Sigma): every u_i against
+    the oracle's u_i = A v_i / sigma_i and the true residual A v_i - s_i u_i vanishing to FP64 grade."""
+    m, n, k, r = 3001, 1400, 60, 33
+    sig = synth.sigma_geometric(n, 0.9)
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, seed=54)
+    bits = synth.to_bf16_bits(A.astype(np.float32))
+    op = oracle.Operator.dense(None, dtype="bf16", bits=bits)
+    q1 = synth.start_vector(m, 54)
+    U, S, V, st, info = gk().gk_fsvd(cuda(bits.view(np.int16)).view(torch.bfloat16), k, r, route=0, start=cuda(q1))
+    Uo, So, Vo, kp = oracle.fsvd(op, k, r, q1, route=0)
+    assert st == 0
+    S, U, V = S.cpu().numpy(), U.cpu().numpy(), V.cpu().numpy()
+    np.testing.assert_allclose(S[:12], So[:12], rtol=1e-6)
+    r1, _ = oracle.residuals(op, U, S, V)
+    # A v_i - s_i u_i = 0 by construction; left to the rounding of the blocked products
+    assert r1.max() <= 1e-12 * S[0]

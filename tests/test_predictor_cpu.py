@@ -57,31 +57,27 @@ def test_k_grid_offsets_then_the_fallback():
         assert all(r < K for K in g) or g == [mn]
 
 
-def test_learned_batched_judges_each_prediction_and_re_solves_the_short_ones(monkeypatch):
-    """A solve is accepted when its spectrum shows a value below the cut (reported rank < k, or
-    sigma_{k+1} <= eps sigma_1); otherwise the problem goes to the plain pipeline."""
-    mats = [torch.empty(40, 30) for _ in range(3)]
-    monkeypatch.setattr(P, "predict", lambda m, p: [(3, 8)] * len(m))
+def test_library_margins_follow_the_stated_rule():
+    """The library's (r^, K^) rule (gk_predictor_margins, host-only): hand-worked cases and the
+    module's restatement on a grid, including the capacity clamp and non-finite estimates."""
+    import ctypes as C
 
-    def fake_psvd_batched(probs, **kw):
-        assert all(p["rank_cut"] == 1e-5 and p["k"] == 3 and p["krylov_dim"] == 8 for p in probs)
-        rr = [dict(status=0, rank=2, sigma_next=0.5, matvecs=17),    # a value below the cut: rank 2
-              dict(status=0, rank=3, sigma_next=1e-9, matvecs=17),   # sigma_4 <= eps sigma_1: rank 3
-              dict(status=0, rank=3, sigma_next=1.0, matvecs=17)]    # nothing below: r^ too small
-        out = [(torch.ones(40, 3), torch.tensor([10.0, 5.0, 1.0]), torch.ones(30, 3), r) for r in rr]
-        info = dict(matvecs=51, sigma_1=torch.tensor([10.0, 10.0, 10.0]), outputs=("U", "S", "V"))
-        return out, 0, info
+    from paper_2104_10785_gb300 import gk
 
-    def fake_plain(ms, eps, tol, autotune=False):
-        assert len(ms) == 1
-        o = (torch.ones(40, 4), torch.tensor([10.0, 5.0, 1.0, 0.5]), torch.ones(30, 4), dict(status=0))
-        return [4], [o], dict(matvecs=40, status=0, matvecs_per_problem=[40])
+    def lib_margins(rf, kf, mn, cap):
+        r, K = C.c_int(), C.c_int()
+        assert gk.lib().gk_predictor_margins(rf, kf, mn, cap, C.byref(r), C.byref(K)) == 0
+        return r.value, K.value
 
-    monkeypatch.setattr(P.gk, "gk_psvd_batched", fake_psvd_batched)
-    monkeypatch.setattr(P, "plain_batched", fake_plain)
-    ranks, final, info = P.learned_batched(mats, params=None)
-    assert ranks == [2, 3, 4]
-    assert [f[1].numel() for f in final] == [2, 3, 4] and final[0][0].shape == (40, 2)
-    assert info["fallbacks"] == 1 and info["matvecs"] == 51 + 40
-    assert info["matvecs_per_problem"] == [18, 18, 58]  # + one sketch pass each, + the plain re-solve
-    assert info["outputs"] is None  # a re-solved problem's triplets are not in the solve's buffers
+    # rf = 20: r^ = ceil(21) + 1 = 22; kf = 40.3: K^ = 41 + 2 + (22 - 20) = 45
+    assert lib_margins(20.0, 40.3, 1000, 80) == (22, 45)
+    # capacity 10 clamps r^, and K^ follows it: 41 + 2 + (10 - 20) = 33
+    assert lib_margins(20.0, 40.3, 1000, 10) == (10, 33)
+    # K^ at least r^ + 2; a small operator caps both (min(m, n) = 12: r^ <= 11, K^ <= 12)
+    assert lib_margins(30.0, 5.0, 12, 80) == (11, 12)
+    # non-finite estimates ask for the whole range min(mn, 500)
+    assert lib_margins(float("inf"), float("nan"), 2000, 600) == (499, 500)
+    for rf in (0.3, 1.0, 4.7, 17.2, 63.9, 120.0):
+        for kf in (2.0, 20.4, 77.7, 140.2, 700.0):
+            for mn, cap in ((256, 80), (3000, 80), (64, 30), (5000, 600)):
+                assert lib_margins(rf, kf, mn, cap) == P.margins(rf, kf, mn, cap), (rf, kf, mn, cap)
