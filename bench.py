@@ -1045,7 +1045,8 @@ def run_batched_headline(args, rank, world, device):
 def profile_case(args):
     """--case products: A (m x n, N(0,1) drawn by torch's CUDA generator, stored in --dtype) and
     `reps` calls of gk_matvec(A, x) and gk_matvec(A, y, trans=True).
-    --case psvd: `reps` calls of gk_psvd (k = 16, K = 48, tol 1e-8) on the same kind of operator.
+    --case psvd: `reps` calls of gk_psvd (k = 16, K = 48, tol 1e-8) on the same kind of operator
+    (--fused: with the fused sweep).
     --case batched: the first --count problems of the 512-problem batched recipe; `reps` rounds
     of the learned pipeline's sketch and its batched partial SVD with the committed network's
     (rank, K); prints the operator bytes the last solve streamed."""
@@ -1066,7 +1067,7 @@ def profile_case(args):
                 gk.gk_matvec(A, x)
                 gk.gk_matvec(A, y, trans=True)
             else:
-                gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0)
+                gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0, fused=args.fused)
     elif args.case == "batched":
         from paper_2104_10785_gb300 import predictor
 
@@ -1108,6 +1109,7 @@ def main():
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--count", type=int, default=64)
+    ap.add_argument("--fused", action="store_true", help="--case psvd: run the fused sweep (GK_FLAG_FUSED)")
     args = ap.parse_args()
     if args.case is not None:
         profile_case(args)
