@@ -1,57 +1,54 @@
-// gk_fused.cu -- the fused sweep: one pass over a dense operator per bidiagonalization
-// step produces both products of the step.
+// gk_fused.cu -- the fused sweep: one pass over a dense operator from HBM per
+// bidiagonalization step produces both products of the step.
 //
 // A Golub-Kahan step (Eq. 2.2; Algorithm 1) needs w = A x - c sub (the left vector
 // before reorthogonalization) and then A^T u with u = (w - U h) / ||w - U h|| (h the
 // Gram-Schmidt coefficients).  A^T u = (A^T w - A^T U h) / ||.||, and A^T U lies in the
 // span of the right basis (A^T u_i = alpha_i v_i + beta_i v_{i+1}), which the right
-// Gram-Schmidt removes anyway; so the sweep can form A^T w while w is produced, from the
-// same bytes of A, and divide by the norm afterwards.  That halves the operator traffic
-// of a step (one pass instead of two).
+// Gram-Schmidt removes anyway; so the sweep can form A^T w from the rows that produced w,
+// and divide by the norm afterwards.  The operator then streams from HBM once per step
+// instead of twice.
 //
-// Layout: a thread-block cluster of Q CTAs owns a set of row blocks (rows kFRows at a
-// time, row block b goes to cluster b mod #clusters); CTA q of the cluster owns one tile
-// of columns (a contiguous run of 16-byte vectors) for the whole launch.
-//   producer warp : cp.async.bulk of the CTA's piece of each row of a stage (row block) into
-//                   a kFStages-deep shared-memory ring (mbarrier complete_tx), bounded waits
-//                   for free slots;
-//   8 consumer warps, each on its own (no block-wide barrier in the loop), per stage s:
-//     (a) the warp's partial dot product of each row with x (f32 products over at most 24
-//         columns per lane, a warp tree in f32), stored as one 16-byte remote store into every
-//         CTA of the cluster and announced by a remote mbarrier arrive (release, cluster scope);
-//     (b) the A^T w update of stage s - kFLag: the wait (acquire, cluster scope) for that stage's
-//         8 Q warp partials -- posted a stage earlier, so the exchange hides behind (a) -- their
-//         sum in a fixed order (every warp of every CTA forms the same w_r), then a_rc * w_r
-//         added for the warp's columns (f32 runs of 64 rows, combined in f64 registers); the
-//         last warp through releases the ring slot.
-// The partial sums live in 2 kFStages generations: a CTA can post stage s + 2 kFStages only
-// after every CTA of the cluster has released stage s + kFStages, hence finished stage s.
-// At the end every CTA writes its columns' f64 partial of A^T w for its cluster, and
-// k_fused_finish sums the clusters' partials in a fixed order, divides by the new norm and
-// subtracts the recurrence term: z = scale (A^T w) / alpha - alpha v.  Every reduction has a
-// fixed order (bitwise reproducible).  Every wait is bounded; on expiry the kernel records
-// a timeout in the control block, halts the sweep, lets its own copies land and meets its
-// peers at the final cluster barrier, so no CTA leaves while another may still write into
-// its shared memory.
+// Layout: a thread-block cluster of Q CTAs owns batches of kSRows rows (batch b goes to
+// cluster b mod #clusters); CTA q of the cluster owns one piece of columns (at most
+// kSVPT 16-byte vectors per thread and row) for the whole launch.  Per batch i:
+//   - thread 0 prefetches the CTA's pieces of the rows of batch i + kSAhead into L2
+//     (cp.async.bulk.prefetch), so HBM keeps streaming while the CTA computes;
+//   - (a) every thread forms its share of the dot product of each row with x (f32 over its
+//     vectors -- held in registers since the previous batch -- with x from shared memory, then
+//     a warp tree); after a block barrier warp 0 sums the 8 warp partials in double-f32 and
+//     sends them to every CTA of the cluster (distributed shared memory and a remote mbarrier
+//     arrive with release semantics); the next batch's rows are then loaded;
+//   - (b) the A^T w update of batch i - 1, whose exchange has had a batch to land: the wait
+//     (acquire, cluster scope), w_r summed over the Q CTA partials in a fixed order (every CTA
+//     forms the same w_r), then the batch's rows are read again -- from L2, a few microseconds
+//     after (a) read them -- and a_rc * w_r added to per-thread f32 accumulators that are
+//     folded into f64 (shared memory) every kSRun rows.
+// The exchanged partials live in kSGen generations: a CTA posts batch i only after every CTA
+// of its cluster posted batch i - 2, hence finished the update of batch i - 4.  At the end
+// every CTA writes its columns' f64 partial of A^T w for its cluster, and k_fused_finish sums
+// the clusters' partials in a fixed order, divides by the new norm and subtracts the
+// recurrence term: z = scale (A^T w) / alpha - alpha v.  Every reduction has a fixed order
+// (bitwise reproducible).  Every wait is bounded; a wait that gives up records a timeout in
+// the control block, every thread of the CTA learns of it at the next block barrier (a
+// barrier with an OR reduction) and stops, and the CTAs meet at a final cluster barrier, so
+// no CTA leaves while a peer may still write into its shared memory.
 #include "gk_internal.cuh"
 
 namespace gk {
 
 namespace {
 
-constexpr int kFThreads = 256;                  // consumer threads (8 warps)
-constexpr int kFWarps = kFThreads / 32;
-constexpr int kFBlock = kFThreads + 32;         // + one producer warp
-constexpr int kFRows = 4;                       // rows per stage
-constexpr int kFStages = 5;                     // ring depth
-constexpr int kFGen = 2 * kFStages;             // generations of the exchanged partial sums
-constexpr int kFLag = 1;                        // stages between a stage's dots and its A^T w update
-constexpr int kFVec = 3;                        // 16-byte vectors per consumer lane per row piece (at most)
-constexpr int kFMaxPiece = 10240;               // bytes of one row piece (one CTA's columns of one row)
-constexpr int kFRunRows = 64;                   // rows summed in f32 before an f64 combine (A^T w)
+constexpr int kSThreads = 256;                  // threads per CTA (8 warps)
+constexpr int kSRows = 4;                       // rows per batch
+constexpr int kSWarps = kSThreads / 32;
+constexpr int kSVPT = 5;                        // 16-byte vectors per thread and row (at most)
+constexpr int kSMaxPiece = kSThreads * kSVPT;   // 16-byte vectors of one CTA's column piece
+constexpr int kSGen = 8;                        // generations of the exchanged partial sums
+constexpr int kSAhead = 2;                      // batches prefetched into L2 ahead of the dots
+constexpr int kSRun = 64;                       // rows summed in f32 before an f64 combine (A^T w)
 constexpr int kFMaxCluster = 16;
 constexpr long long kFWaitCycles = 4000000000ll;  // ~2 s of SM clock before a wait gives up
-static_assert(kFMaxPiece <= kFThreads * kFVec * 16, "a row piece must fit the consumers' vectors");
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -84,31 +81,8 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t peer) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_local(uint64_t *bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(saddr(bar)) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar_addr) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(saddr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// bounded wait for phase `parity` (CTA scope: the ring of bulk copies)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  const uint32_t a = saddr(bar);
-  const long long t0 = clock64();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > kFWaitCycles) return false;
-  }
 }
 // bounded wait with cluster-scope acquire (the partial sums stored by the peers)
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, unsigned parity) {
@@ -125,12 +99,6 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, unsigned parity
     if (done) return true;
     if (clock64() - t0 > kFWaitCycles) return false;
   }
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(saddr(dst)),
-      "l"(src), "r"(bytes), "r"(saddr(bar))
-      : "memory");
 }
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
@@ -168,255 +136,240 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// w = scale * A x - coef * sub (rows of this cluster's row blocks; warp 0 of CTA 0 writes)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// w = scale * A x - coef * sub (rows of this cluster's batches; warp 0 of CTA 0 writes)
 // zpart[cluster * n + col] = sum over those rows of a_{r,col} * f32(w_r)  (without scale)
-// Dynamic shared memory: the ring (kFStages x kFRows x piece_vecs x 16 bytes), then the
-// exchanged partials [kFGen][Q][kFWarps][kFRows] f32.
+// Dynamic shared memory: z64 [piece_vecs * E] f64, x of the piece as E / 4 planes of
+// [piece_vecs] float4, then the exchanged partials [kSGen][Q][2 kSRows] f32 (the CTA partial
+// of each row as hi, lo).
 template <typename T>
-__global__ void __launch_bounds__(kFBlock, 1)
+__global__ void __launch_bounds__(kSThreads, 1)
     k_fused(const T *__restrict__ A, int64_t m, int64_t n, int64_t ld, double scale, const float *__restrict__ x,
             double *__restrict__ w, const double *__restrict__ sub, const double *__restrict__ coef,
             double *__restrict__ zpart, int piece_vecs, Ctl *ctl) {
   using VT = Vec<T>;
   using V = typename VT::V;
   constexpr int E = VT::E;
-  extern __shared__ __align__(128) unsigned char ring[];
-  __shared__ __align__(8) uint64_t full[kFStages], empty[kFStages], xbar[kFGen];
-  __shared__ int64_t last_issued[kFStages];
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t xbar[kSGen];
+  __shared__ float wsum[2][kSWarps][kSRows];
   __shared__ int abort_flag;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t q = cluster_rank(), Q = cluster_size(), cid = cluster_id(), NC = cluster_count();
   const int64_t nvec = n / E;  // n * sizeof(T) is a multiple of 16 (checked on the host)
   const int64_t v0 = (int64_t)q * piece_vecs;
   const int nloc = (int)(v0 >= nvec ? 0 : (nvec - v0 < piece_vecs ? nvec - v0 : piece_vecs));
-  const unsigned piece_bytes = (unsigned)nloc * 16u;
-  const size_t stage_bytes = (size_t)kFRows * (size_t)piece_vecs * 16u;
-  float *part = reinterpret_cast<float *>(ring + (size_t)kFStages * stage_bytes);  // [kFGen][Q][kFWarps][kFRows]
-  const int64_t nrb = (m + kFRows - 1) / kFRows;
-  const int64_t ns = nrb > (int64_t)cid ? (nrb - (int64_t)cid + NC - 1) / NC : 0;  // stages of this cluster
+  double *z64 = reinterpret_cast<double *>(smem);
+  float4 *xs = reinterpret_cast<float4 *>(z64 + (size_t)piece_vecs * E);  // [E / 4][piece_vecs]
+  float *slots = reinterpret_cast<float *>(xs + (size_t)(E / 4) * piece_vecs);
+  const int64_t nb = (m + kSRows - 1) / kSRows;
+  const int64_t ns = nb > (int64_t)cid ? (nb - (int64_t)cid + NC - 1) / NC : 0;  // batches of this cluster
 
-  if (tid == 0) {
-    for (int i = 0; i < kFStages; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kFWarps);
-      last_issued[i] = -1;
+  for (int i = tid; i < piece_vecs * E; i += kSThreads) z64[i] = 0.0;
+  // x of this CTA's columns, E / 4 float4 planes (conflict-free 16-byte reads)
+  for (int v = tid; v < piece_vecs; v += kSThreads)
+#pragma unroll
+    for (int h = 0; h < E / 4; ++h) {
+      float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (v < nloc) {
+        const float *xp = x + (v0 + v) * E + 4 * h;
+        t4 = make_float4(xp[0], xp[1], xp[2], xp[3]);
+      }
+      xs[(size_t)h * piece_vecs + v] = t4;
     }
-    for (int i = 0; i < kFGen; ++i) mbar_init(&xbar[i], kFWarps * Q);
+  if (tid == 0) {
+    for (int i = 0; i < kSGen; ++i) mbar_init(&xbar[i], Q);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
   // every CTA's barriers are initialized before any peer arrives on them
   cluster_sync_all();
   const bool skip = halted(ctl);  // the whole cluster reads the same flag: a halted sweep does nothing
   volatile int *abort_v = &abort_flag;
 
-  if (tid >= kFThreads) {
-    // producer: one elected lane issues the stages in order, then waits for its last copies
-    if (tid == kFThreads && !skip) {
-      for (int64_t s = 0; s < ns; ++s) {
-        const int sl = (int)(s % kFStages);
-        if (s >= kFStages && !mbar_wait(&empty[sl], (unsigned)(((s / kFStages) - 1) & 1))) {
-          record_timeout(ctl, 2);
-          *abort_v = 1;
-          break;
-        }
-        const int64_t r0 = ((int64_t)cid + s * (int64_t)NC) * kFRows;
-        const int rows = (int)((m - r0) < kFRows ? (m - r0) : kFRows);
-        mbar_expect_tx(&full[sl], piece_bytes * (unsigned)rows);
-        last_issued[sl] = s;
-        if (piece_bytes)
-          for (int r = 0; r < rows; ++r)
-            bulk_g2s(ring + (size_t)sl * stage_bytes + (size_t)r * piece_vecs * 16, A + (r0 + r) * ld + v0 * E,
-                     piece_bytes, &full[sl]);
+  if (!skip) {
+    const T *Ab = A + v0 * E;  // this CTA's column piece
+    auto row0 = [&](int64_t t) { return ((int64_t)cid + t * (int64_t)NC) * kSRows; };
+    auto nrows = [&](int64_t r0) { return (int)(m - r0 < kSRows ? m - r0 : kSRows); };
+    auto prefetch = [&](int64_t t) {
+      if (t < ns && nloc > 0) {
+        const int64_t r0 = row0(t);
+        const int rows = nrows(r0);
+        for (int r = 0; r < rows; ++r) prefetch_l2(Ab + (r0 + r) * ld, (unsigned)nloc * 16u);
       }
-      // no copy may still be landing when the CTA leaves (each slot's last phase is the only one
-      // that can be pending: the next one was never issued)
-      for (int i = 0; i < kFStages; ++i)
-        if (last_issued[i] >= 0) mbar_wait(&full[i], (unsigned)((last_issued[i] / kFStages) & 1));
-    }
-  } else if (!skip) {
-    const int warp = tid >> 5, lane = tid & 31;
-    const double c = sub ? *coef : 0.0;
-    // this lane's x values (vectors tid, tid + 256, tid + 512 of the CTA's piece)
-    float xr[kFVec][E];
-    float z32[kFVec][E];
-    double z64[kFVec][E];
-#pragma unroll
-    for (int i = 0; i < kFVec; ++i) {
-      const int vl = tid + i * kFThreads;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        z32[i][e] = 0.f;
-        z64[i][e] = 0.0;
-        xr[i][e] = 0.f;
-      }
-      if (vl < nloc) {
-#pragma unroll
-        for (int h = 0; h < E / 4; ++h) {
-          const float4 xx = __ldg(reinterpret_cast<const float4 *>(x + (v0 + vl) * E) + h);
-          xr[i][4 * h + 0] = xx.x;
-          xr[i][4 * h + 1] = xx.y;
-          xr[i][4 * h + 2] = xx.z;
-          xr[i][4 * h + 3] = xx.w;
-        }
-      }
-    }
-    int run = 0;
-    bool ok = true;
-    // sub entry of row rr of the stage being summed next (prefetched one stage ahead)
-    double sub_next = 0.0;
-    {
-      const int rr = lane >> 3;
-      const int64_t r0n = (int64_t)cid * kFRows + rr;
-      if (sub && (lane & 7) == 0 && r0n < m && ns > 0) sub_next = sub[r0n];
-    }
-    // (b) for stage t: the exchanged partials -> w_r, then the A^T w update; releases the slot
-    auto zstage = [&](int64_t t) -> bool {
-      const int sl = (int)(t % kFStages), g = (int)(t % kFGen);
-      const int64_t r0 = ((int64_t)cid + t * (int64_t)NC) * kFRows;
-      const int rows = (int)((m - r0) < kFRows ? (m - r0) : kFRows);
-      const int rr = lane >> 3, src = lane & 7;  // this lane sums row rr's partials of source warp src
-      const double sv = sub_next;
-      {  // the next stage's entry of sub, loaded while this one is summed
-        const int64_t rn = ((int64_t)cid + (t + 1) * (int64_t)NC) * kFRows + rr;
-        sub_next = (sub && src == 0 && rr < kFRows && rn < m && t + 1 < ns) ? sub[rn] : 0.0;
-      }
-      if (!mbar_wait_cluster(&xbar[g], (unsigned)((t / kFGen) & 1))) return false;
-      if (!mbar_wait(&full[sl], (unsigned)((t / kFStages) & 1))) return false;  // complete: orders the staged bytes
-      // the row's 8 Q warp partials in double-f32 (every rounding error kept), fixed order: the
-      // total is then rounded once, to f64
-      float hi = 0.f, lo = 0.f;
-      for (uint32_t p = 0; p < Q; ++p) df_add(hi, lo, part[(((size_t)g * Q + p) * kFWarps + src) * kFRows + rr]);
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        // combine so that both lanes of the pair compute the same sum (lower lane's value first)
-        const bool first = (lane & o) == 0;
-        float s, e;
-        two_sum(first ? hi : h2, first ? h2 : hi, s, e);
-        hi = s;
-        lo = __fadd_rn(__fadd_rn(first ? lo : l2, first ? l2 : lo), e);
-      }
-      float wv32 = 0.f;
-      if ((lane & 7) == 0 && rr < rows) {
-        const double wv = ((double)hi + (double)lo) * scale - c * sv;
-        wv32 = (float)wv;
-        if (q == 0 && warp == 0) w[r0 + rr] = wv;
-      }
-      float wr[kFRows];
-#pragma unroll
-      for (int r = 0; r < kFRows; ++r) wr[r] = __shfl_sync(0xffffffffu, wv32, r * 8);
-      const unsigned char *st = ring + (size_t)sl * stage_bytes;
-#pragma unroll
-      for (int r = 0; r < kFRows; ++r) {
-        if (r < rows) {
-          const V *row = reinterpret_cast<const V *>(st + (size_t)r * piece_vecs * 16);
-#pragma unroll
-          for (int i = 0; i < kFVec; ++i) {
-            const int vl = tid + i * kFThreads;
-            if (vl < nloc) {
-              float f[E];
-              VT::unpack(row[vl], f);
-#pragma unroll
-              for (int e = 0; e < E; ++e) z32[i][e] = fmaf(f[e], wr[r], z32[i][e]);
-            }
-          }
-        }
-      }
-      run += rows;
-      if (run >= kFRunRows) {
-#pragma unroll
-        for (int i = 0; i < kFVec; ++i)
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            z64[i][e] += (double)z32[i][e];
-            z32[i][e] = 0.f;
-          }
-        run = 0;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive_local(&empty[sl]);
-      return true;
     };
-
-    int64_t zdone = 0;  // stages whose A^T w update is done
-    for (int64_t s = 0; s < ns && ok; ++s) {
-      if (*abort_v) {
-        ok = false;
-        break;
-      }
-      const int sl = (int)(s % kFStages), g = (int)(s % kFGen);
-      if (!mbar_wait(&full[sl], (unsigned)((s / kFStages) & 1))) {
-        ok = false;
-        break;
-      }
-      const int64_t r0 = ((int64_t)cid + s * (int64_t)NC) * kFRows;
-      const int rows = (int)((m - r0) < kFRows ? (m - r0) : kFRows);
-      // (a) this warp's partial dot of each row of the stage with x
-      float d[kFRows];
-      const unsigned char *st = ring + (size_t)sl * stage_bytes;
+    auto load = [&](int64_t t, V (&a)[kSRows][kSVPT]) {
+      const int64_t r0 = row0(t);
+      const int rows = nrows(r0);
 #pragma unroll
-      for (int r = 0; r < kFRows; ++r) {
-        d[r] = 0.f;
-        if (r < rows) {
-          const V *row = reinterpret_cast<const V *>(st + (size_t)r * piece_vecs * 16);
+      for (int r = 0; r < kSRows; ++r)
 #pragma unroll
-          for (int i = 0; i < kFVec; ++i) {
-            const int vl = tid + i * kFThreads;
-            if (vl < nloc) {
+        for (int j = 0; j < kSVPT; ++j) {
+          const int v = tid + kSThreads * j;
+          if (r < rows && v < nloc)
+            a[r][j] = __ldg(reinterpret_cast<const V *>(Ab + (r0 + r) * ld) + v);
+          else
+            a[r][j] = V{};
+        }
+    };
+    float za[kSVPT][E];
+#pragma unroll
+    for (int j = 0; j < kSVPT; ++j)
+#pragma unroll
+      for (int e = 0; e < E; ++e) za[j][e] = 0.f;
+    auto flush = [&]() {
+#pragma unroll
+      for (int j = 0; j < kSVPT; ++j) {
+        const int v = tid + kSThreads * j;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (v < nloc) z64[v * E + e] += (double)za[j][e];
+          za[j][e] = 0.f;
+        }
+      }
+    };
+    const double c = sub ? *coef : 0.0;
+    if (tid == 0)
+      for (int t = 0; t < kSAhead; ++t) prefetch(t);
+    V a[kSRows][kSVPT];  // the rows of the next batch's dot products, loaded one batch ahead
+    if (ns > 0) load(0, a);
+    bool fail = false;
+    int run = 0;
+    for (int64_t i = 0; i <= ns; ++i) {
+      if (i < ns) {
+        if (tid == 0) prefetch(i + kSAhead);
+        // (a) this thread's share of the dot product of each row of batch i with x
+        float d[kSRows];
+#pragma unroll
+        for (int r = 0; r < kSRows; ++r) d[r] = 0.f;
+#pragma unroll
+        for (int j = 0; j < kSVPT; ++j) {
+          const int v = tid + kSThreads * j;
+          if (v < nloc) {
+            float xv[E];
+#pragma unroll
+            for (int h = 0; h < E / 4; ++h) {
+              const float4 t4 = xs[(size_t)h * piece_vecs + v];
+              xv[4 * h] = t4.x;
+              xv[4 * h + 1] = t4.y;
+              xv[4 * h + 2] = t4.z;
+              xv[4 * h + 3] = t4.w;
+            }
+#pragma unroll
+            for (int r = 0; r < kSRows; ++r) {
               float f[E];
-              VT::unpack(row[vl], f);
+              VT::unpack(a[r][j], f);
 #pragma unroll
-              for (int e = 0; e < E; ++e) d[r] = fmaf(f[e], xr[i][e], d[r]);
+              for (int e = 0; e < E; ++e) d[r] = fmaf(f[e], xv[e], d[r]);
             }
           }
         }
-      }
 #pragma unroll
-      for (int r = 0; r < kFRows; ++r) d[r] = warp_sum_f(d[r]);
-      // one 16-byte remote store and one remote arrive per peer (lane p serves CTA p)
-      if (lane < (int)Q) {
-        const uint32_t dst = peer_addr(saddr(part + (((size_t)g * Q + q) * kFWarps + warp) * kFRows), (uint32_t)lane);
-        asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "f"(d[0]), "f"(d[1]), "f"(d[2]),
-                     "f"(d[3])
-                     : "memory");
-        mbar_arrive_remote(peer_addr(saddr(&xbar[g]), (uint32_t)lane));
+        for (int r = 0; r < kSRows; ++r) d[r] = warp_sum_f(d[r]);
+        if (lane == 0)
+#pragma unroll
+          for (int r = 0; r < kSRows; ++r) wsum[i & 1][warp][r] = d[r];
       }
-      // (b) the update of the stage kFLag back, whose exchange has had a stage to complete
-      if (s >= kFLag) {
-        if (!zstage(s - kFLag)) {
-          ok = false;
-          break;
+      // every thread takes the same decision at the same barrier
+      if (__syncthreads_or(fail || *abort_v)) {
+        fail = true;
+        break;
+      }
+      if (i < ns && warp == 0) {
+        // the CTA partial of each row (double-f32 over the warps, fixed order), to every CTA
+        float hi = 0.f, lo = 0.f;
+        if (lane < kSRows)
+          for (int ww = 0; ww < kSWarps; ++ww) df_add(hi, lo, wsum[i & 1][ww][lane]);
+        float h[kSRows], l[kSRows];
+#pragma unroll
+        for (int r = 0; r < kSRows; ++r) {
+          h[r] = __shfl_sync(0xffffffffu, hi, r);
+          l[r] = __shfl_sync(0xffffffffu, lo, r);
         }
-        zdone = s - kFLag + 1;
+        if (lane < (int)Q) {
+          const int gen = (int)(i % kSGen);
+          const uint32_t dst = peer_addr(saddr(slots + ((size_t)gen * Q + q) * 2 * kSRows), (uint32_t)lane);
+          asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "f"(h[0]), "f"(h[1]), "f"(h[2]),
+                       "f"(h[3])
+                       : "memory");
+          asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst + 16), "f"(l[0]), "f"(l[1]),
+                       "f"(l[2]), "f"(l[3])
+                       : "memory");
+          mbar_arrive_remote(peer_addr(saddr(&xbar[gen]), (uint32_t)lane));
+        }
+      }
+      // the next batch's rows, in flight while the update below waits for its own
+      if (i + 1 < ns) load(i + 1, a);
+      // (b) the A^T w update of batch i - 1 (its rows read again, now from L2)
+      if (i >= 1 && !fail) {
+        const int64_t t = i - 1;
+        V b2[kSRows][kSVPT];
+        load(t, b2);
+        const int gen = (int)(t % kSGen);
+        if (!mbar_wait_cluster(&xbar[gen], (unsigned)((t / kSGen) & 1))) {
+          fail = true;
+        } else {
+          const int64_t r0 = row0(t);
+          const int rows = nrows(r0);
+          float wv32 = 0.f;
+          if (lane < rows) {
+            float hi = 0.f, lo = 0.f;
+            for (uint32_t p = 0; p < Q; ++p) {
+              const float *sp = slots + ((size_t)gen * Q + p) * 2 * kSRows;
+              df_add(hi, lo, sp[lane]);
+              df_add(hi, lo, sp[kSRows + lane]);
+            }
+            const double wv = ((double)hi + (double)lo) * scale - (sub ? c * sub[r0 + lane] : 0.0);
+            wv32 = (float)wv;
+            if (q == 0 && warp == 0) w[r0 + lane] = wv;
+          }
+          float wr[kSRows];
+#pragma unroll
+          for (int r = 0; r < kSRows; ++r) wr[r] = __shfl_sync(0xffffffffu, wv32, r);
+#pragma unroll
+          for (int r = 0; r < kSRows; ++r)
+#pragma unroll
+            for (int j = 0; j < kSVPT; ++j) {
+              float f[E];
+              VT::unpack(b2[r][j], f);
+#pragma unroll
+              for (int e = 0; e < E; ++e) za[j][e] = fmaf(f[e], wr[r], za[j][e]);
+            }
+          run += rows;
+          if (run >= kSRun) {
+            flush();
+            run = 0;
+          }
+        }
       }
     }
-    for (int64_t t = zdone; ok && t < ns; ++t) {
-      if (*abort_v || !zstage(t)) ok = false;
-    }
-    if (ok) {
-      // this CTA's columns of the cluster's partial A^T w (each warp its own vectors)
+    if (!__syncthreads_or(fail || *abort_v)) {
+      flush();
+      // this thread's columns of the cluster's partial A^T w (its own z64 entries)
 #pragma unroll
-      for (int i = 0; i < kFVec; ++i) {
-        const int vl = tid + i * kFThreads;
-        if (vl < nloc) {
-          double *zp = zpart + (int64_t)cid * n + (v0 + vl) * E;
+      for (int j = 0; j < kSVPT; ++j) {
+        const int v = tid + kSThreads * j;
+        if (v < nloc) {
+          double *zp = zpart + (int64_t)cid * n + (v0 + v) * E;
 #pragma unroll
-          for (int e = 0; e < E; ++e) zp[e] = z64[i][e] + (double)z32[i][e];
+          for (int e = 0; e < E; ++e) zp[e] = z64[v * E + e];
         }
       }
     } else {
-      if (lane == 0) record_timeout(ctl, 1);
+      if (tid == 0) record_timeout(ctl, 1);
       *abort_v = 1;
     }
   }
   // no CTA leaves while a peer may still store into its shared memory
-  __syncwarp();
+  __syncthreads();
   cluster_sync_all();
 }
 
-// z[c] = scale * (sum over clusters of zpart[cl * n + c]) / alpha - alpha * sub[c], alpha = *coef
 __global__ void __launch_bounds__(256) k_fused_finish(const double *__restrict__ zpart, int nc, int64_t n,
                                                       double scale, const double *__restrict__ coef,
                                                       const double *__restrict__ sub, double *__restrict__ z,
@@ -438,28 +391,31 @@ struct FusedPlan {
 
 template <typename T>
 cudaError_t plan_for(const Op &A, const Dev &d, FusedPlan *pl) {
-  const int64_t nvec = A.n * (int64_t)sizeof(T) / 16;
+  constexpr int E = Vec<T>::E;
+  const int64_t nvec = A.n / E;
   auto kern = k_fused<T>;
+  auto smem_for = [&](int64_t pv, int Q) {
+    return (size_t)pv * E * (sizeof(double) + sizeof(float)) + (size_t)kSGen * Q * 2 * kSRows * sizeof(float);
+  };
   static int attr_dev = -1;
   if (attr_dev != d.id) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kFStages * kFRows * kFMaxPiece +
-                                             kFGen * kFMaxCluster * kFWarps * kFRows * (int)sizeof(float));
+                                         (int)smem_for(kSMaxPiece, kFMaxCluster));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     attr_dev = d.id;
   }
-  // among the cluster sizes whose column tile fits a ring slot, the one that keeps the most
-  // SMs busy (clusters are placed within one GPC: sizes that do not divide a GPC idle SMs)
+  // among the cluster sizes whose column piece fits the threads' vectors, the one that keeps
+  // the most SMs busy (clusters are placed within one GPC: sizes that do not divide a GPC
+  // idle SMs); the smaller cluster on a tie
   int best_active = 0;
   for (int Q = 1; Q <= kFMaxCluster; Q *= 2) {
     const int64_t pv = (nvec + Q - 1) / Q;
-    if (pv * 16 > kFMaxPiece) continue;
-    const size_t smem = (size_t)kFStages * kFRows * (size_t)pv * 16 +
-                        (size_t)kFGen * Q * kFWarps * kFRows * sizeof(float);
+    if (pv > kSMaxPiece) continue;
+    const size_t smem = smem_for(pv, Q);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(Q, 1, 1);
-    cfg.blockDim = dim3(kFBlock, 1, 1);
+    cfg.blockDim = dim3(kSThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -525,7 +481,7 @@ bool fused_ok(const Op &A, const Dev &d) {
   if (A.kind != GK_DENSE || A.dtype == GK_F64) return false;
   const int64_t es = A.dtype == GK_F32 ? 4 : 2;
   if ((uintptr_t)A.vals % 16 != 0 || (A.ld * es) % 16 != 0 || (A.n * es) % 16 != 0) return false;
-  if (A.m < 1 || A.n * es > (int64_t)kFMaxCluster * kFMaxPiece) return false;
+  if (A.m < 1 || A.n * es > (int64_t)kFMaxCluster * kSMaxPiece * 16) return false;
   FusedPlan pl;
   return cached_plan(A, d, &pl);
 }
@@ -549,7 +505,7 @@ cudaError_t fused_matvec(const Op &A, const float *x32, double *w, const double 
   if (!fused_ok(A, d) || !cached_plan(A, d, &pl)) return cudaErrorNotSupported;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.NC * pl.Q, 1, 1);
-  cfg.blockDim = dim3(kFBlock, 1, 1);
+  cfg.blockDim = dim3(kSThreads, 1, 1);
   cfg.dynamicSmemBytes = pl.smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];

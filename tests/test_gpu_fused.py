@@ -1,14 +1,16 @@
-"""The fused sweep (one pass over A per bidiagonalization step: w = A v - beta u and A^T w
-from the same bytes; the right step takes A^T w / alpha for A^T u) against the oracle's
-restatement of the same ordering (oracle: fused=True), through the C ABI.
+"""The fused sweep (one pass over A from HBM per bidiagonalization step: w = A v - beta u and
+A^T w from the same rows, the second read from L2; the right step takes A^T w / alpha for
+A^T u) against the oracle's restatement of the same ordering (oracle: fused=True), through the
+C ABI.
 
-Shapes span every cluster size the kernel picks (column tiles of 16-byte vectors up to
-10 KB per CTA), ragged row counts (the last row block of 4 short), clusters that own no
-row block (m < 4 x clusters), and enough rows that every cluster wraps its five-slot ring
-many times.  Tolerances are those of the two-pass path (tests/test_gpu_parity.py): the
-fused kernel's sums are f32 over at most 24 products per thread (a warp tree after them)
-or 32 rows (A^T w), combined in f64, within 2^-24 (64 + 2) sum |a x| of the exact
-products like the two-pass kernels."""
+Shapes span the cluster sizes the kernel picks (column pieces of up to 1280 16-byte vectors
+per CTA, the last CTA's piece short and threads with a partial fifth vector), ragged row
+counts (the last batch of 4 rows short), clusters that own no batch (m < 4 x clusters), and
+enough rows that every cluster wraps its 8 exchange generations many times.  Tolerances are
+those of the two-pass path (tests/test_gpu_parity.py): the fused kernel's sums are f32 over
+at most 40 products per thread (a warp tree after them, double-f32 across warps and CTAs) or
+64 rows (A^T w), combined in f64, within 2^-24 (64 + 2) sum |a x| of the exact products like
+the two-pass kernels."""
 import numpy as np
 import pytest
 import torch
