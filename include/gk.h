@@ -59,6 +59,14 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 #define GK_FLAG_REFINE 8   /* gk_psvd: check the returned triplets' true residuals with FP64-grade
                               products (as gk_residuals) and keep restarting, with the Ritz test
                               tightened 4x each time, while one exceeds tol * s_1 */
+#define GK_FLAG_ORTH_F64 16 /* gk_psvd, gk_numrank, gk_fsvd: Gram-Schmidt with f64 arithmetic on the f64
+                              bases.  Without it, vectors longer than the one-CTA size (8192 entries)
+                              are orthogonalized against a double-f32 copy of each basis (every entry
+                              as two f32, written beside the f64 column; the basis products in
+                              double-f32 arithmetic, ~2^-46 of |q w| per term, w and the norms f64):
+                              the same passes and rules (Algorithm 1 reorthogonalization), on the
+                              FP32 pipes, with the workspace holding the copies (8 bytes per basis
+                              entry) */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).

@@ -23,6 +23,8 @@
 #include <mutex>
 #include <vector>
 
+#include <utility>
+
 #include "gk_internal.cuh"
 
 using namespace gk;
@@ -370,6 +372,7 @@ struct PsvdPlan {
   int k, K, keep, passes, max_restarts;
   bool fused;   // one pass over A per step (gk_fused.cu)
   bool refine;  // FP64-grade check of the returned triplets (GK_FLAG_REFINE)
+  bool df;      // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
 };
 
 struct PsvdBufs {
@@ -380,6 +383,7 @@ struct PsvdBufs {
   double *Uo, *So, *Vo, *q1, *svd_nrm, *zpart, *rY, *rZ, *rr1, *rr2;
   float *rsplit;
   int *svd_pos;
+  float2 *Us, *Us2, *Vs, *Vs2, *ws2;  // double-f32 shadows of Ub, Ub2, Vb, Vb2; split of w (or null)
 };
 
 size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const OpStage &st, bool host_out,
@@ -418,6 +422,11 @@ size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const Op
   b->So = host_out ? cv.take<double>(p.k) : nullptr;
   b->q1 = host_start ? cv.take<double>(p.ldu) : nullptr;
   b->zpart = p.fused ? cv.take<double>(fused_partials(*op, d)) : nullptr;
+  b->Us = p.df ? cv.take<float2>((size_t)p.ldu * K) : nullptr;
+  b->Us2 = p.df ? cv.take<float2>((size_t)p.ldu * K) : nullptr;
+  b->Vs = p.df ? cv.take<float2>((size_t)p.ldv * (K + 1)) : nullptr;
+  b->Vs2 = p.df ? cv.take<float2>((size_t)p.ldv * (K + 1)) : nullptr;
+  b->ws2 = p.df ? cv.take<float2>(p.ldu > p.ldv ? p.ldu : p.ldv) : nullptr;
   b->rY = b->rZ = b->rr1 = b->rr2 = nullptr;
   b->rsplit = nullptr;
   if (p.refine) {
@@ -466,6 +475,7 @@ int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
   p->max_restarts = o.max_restarts;
   p->fused = false;
   p->refine = (o.flags & GK_FLAG_REFINE) != 0;
+  p->df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   return GK_OK;
 }
 
@@ -489,11 +499,13 @@ int clear_halt(Ctl *ctl, cudaStream_t s) {
 // replacement direction for a basis column: fresh values, orthogonalized twice
 // against the first `jcols` columns, normalized (or zero if the basis is full)
 int fresh_column(double *wbuf, int64_t len, const double *Qb, int64_t ld, int jcols, double *dst, float *x32,
-                 uint64_t seed, int64_t *nfresh, PsvdBufs &b, cudaStream_t s, const Dev &d) {
+                 uint64_t seed, int64_t *nfresh, PsvdBufs &b, cudaStream_t s, const Dev &d, const float2 *Qs,
+                 float2 *dsts) {
   GK_CUDA(draw_fresh(wbuf, len, seed, (*nfresh)++, s));
   GK_CUDA(orthonormalize(wbuf, len, Qb, ld, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
-  GK_CUDA(orthonormalize(wbuf, len, Qb, ld, jcols, 2, b.part, b.h, b.ctl, NM_FRESH, -1, 0, nullptr, nullptr, s, d));
-  GK_CUDA(normalize_append(wbuf, len, dst, x32, b.ctl, s, d));
+  GK_CUDA(orthonormalize(wbuf, len, Qb, ld, jcols, 2, b.part, b.h, b.ctl, NM_FRESH, -1, 0, nullptr, nullptr, s, d,
+                         Qs, b.ws2));
+  GK_CUDA(normalize_append(wbuf, len, dst, x32, b.ctl, s, d, dsts));
   return GK_OK;
 }
 
@@ -605,6 +617,12 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   GK_CUDA(reset_ctl(b.ctl, 0.0, 1, s));
   GK_CUDA(cudaMemsetAsync(b.alpha, 0, sizeof(double) * (K + 2), s));
   GK_CUDA(cudaMemsetAsync(b.beta, 0, sizeof(double) * (K + 2), s));
+  if (p.df) {  // the shadows' padding rows (past m, n) are read beside the last odd row: keep them 0
+    GK_CUDA(cudaMemsetAsync(b.Us, 0, sizeof(float2) * ldu * K, s));
+    GK_CUDA(cudaMemsetAsync(b.Us2, 0, sizeof(float2) * ldu * K, s));
+    GK_CUDA(cudaMemsetAsync(b.Vs, 0, sizeof(float2) * ldv * (K + 1), s));
+    GK_CUDA(cudaMemsetAsync(b.Vs2, 0, sizeof(float2) * ldv * (K + 1), s));
+  }
   // start vector q1 (Algorithm 1) and v1 = A^T q1 / ||A^T q1||
   if (o.start) {
     const double *src = o.start;
@@ -620,7 +638,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   GK_CUDA(normalize_append(b.t, m, b.t, b.x32, b.ctl, s, d));
   GK_CUDA(matvec_t(op, b.x32, b.t, b.z, nullptr, nullptr, b.part, b.ctl, s, d));
   GK_CUDA(orthonormalize(b.z, n, b.Vb, ldv, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 1, nullptr, nullptr, s, d));
-  GK_CUDA(normalize_append(b.z, n, b.Vb, b.x32, b.ctl, s, d));
+  GK_CUDA(normalize_append(b.z, n, b.Vb, b.x32, b.ctl, s, d, b.Vs));
   inf.matvecs = 1;
   HostCtl hc;
   rc = read_ctl(b.ctl, nullptr, &hc, s);
@@ -628,7 +646,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   if (!isfinite(hc.ctl.norm)) return GK_NUMERICAL;
   int64_t nfresh = 0;
   if (hc.ctl.norm == 0.0) {  // A^T q1 = 0
-    rc = fresh_column(b.z, n, b.Vb, ldv, 0, b.Vb, b.x32, o.seed, &nfresh, b, s, d);
+    rc = fresh_column(b.z, n, b.Vb, ldv, 0, b.Vb, b.x32, o.seed, &nfresh, b, s, d, b.Vs, b.Vs);
     if (rc) return rc;
     inf.breakdowns++;
   }
@@ -681,8 +699,9 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
             prof.begin(PC_ORTH);
           }
           GK_CUDA(orthonormalize(b.w, m, b.Ub, ldu, j, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 0, b.alpha + j,
-                                 nullptr, s, d));
-          GK_CUDA(normalize_append(b.w, m, b.Ub + (int64_t)j * ldu, fused_step ? nullptr : b.x32, b.ctl, s, d));
+                                 nullptr, s, d, b.Us, b.ws2));
+          GK_CUDA(normalize_append(b.w, m, b.Ub + (int64_t)j * ldu, fused_step ? nullptr : b.x32, b.ctl, s, d,
+                                   b.Us ? b.Us + (int64_t)j * ldu : nullptr));
           prof.end();
           inf.matvecs++;
         }
@@ -697,8 +716,9 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
         prof.end();
         prof.begin(PC_ORTH);
         GK_CUDA(orthonormalize(b.z, n, b.Vb, ldv, j + 1, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 1,
-                               b.beta + j, nullptr, s, d));
-        GK_CUDA(normalize_append(b.z, n, b.Vb + (int64_t)(j + 1) * ldv, b.x32, b.ctl, s, d));
+                               b.beta + j, nullptr, s, d, b.Vs, b.ws2));
+        GK_CUDA(normalize_append(b.z, n, b.Vb + (int64_t)(j + 1) * ldv, b.x32, b.ctl, s, d,
+                                 b.Vs ? b.Vs + (int64_t)(j + 1) * ldv : nullptr));
         prof.end();
         inf.matvecs++;
         inf.steps++;
@@ -719,12 +739,13 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
       if (rc) return rc;
       inf.breakdowns++;
       if (sb == 0) {
-        rc = fresh_column(b.w, m, b.Ub, ldu, jb, b.Ub + (int64_t)jb * ldu, b.x32, o.seed, &nfresh, b, s, d);
+        rc = fresh_column(b.w, m, b.Ub, ldu, jb, b.Ub + (int64_t)jb * ldu, b.x32, o.seed, &nfresh, b, s, d, b.Us,
+                          b.Us ? b.Us + (int64_t)jb * ldu : nullptr);
         j0 = jb;
         side0 = 1;
       } else {
         rc = fresh_column(b.z, n, b.Vb, ldv, jb + 1, b.Vb + (int64_t)(jb + 1) * ldv, b.x32, o.seed, &nfresh, b, s,
-                          d);
+                          d, b.Vs, b.Vs ? b.Vs + (int64_t)(jb + 1) * ldv : nullptr);
         j0 = jb + 1;
         side0 = 0;
       }
@@ -762,6 +783,10 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, p.keep, b.Ub2, ldu, s, d));
     GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, p.keep, b.Vb2, ldv, s, d));
     GK_CUDA(copy_vec(b.Vb2 + (int64_t)p.keep * ldv, b.x32, b.Vb + (int64_t)K * ldv, n, s));
+    if (p.df) {  // the kept columns' shadows
+      GK_CUDA(split_cols(b.Ub2, m, ldu, p.keep, b.Us2, s));
+      GK_CUDA(split_cols(b.Vb2, n, ldv, p.keep + 1, b.Vs2, s));
+    }
     prof.end();
     double *tmp = b.Ub;
     b.Ub = b.Ub2;
@@ -769,6 +794,8 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     tmp = b.Vb;
     b.Vb = b.Vb2;
     b.Vb2 = tmp;
+    std::swap(b.Us, b.Us2);
+    std::swap(b.Vs, b.Vs2);
     l = p.keep;
     inf.restarts++;
   }
@@ -812,6 +839,8 @@ struct RankBufs {
   float *x32;
   int *rank;
   bool fused;  // one pass over A per step (gk_fused.cu)
+  bool df;     // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
+  float2 *Qs, *Ps, *ws2;
 };
 
 size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpStage &st, bool host_sigma,
@@ -838,6 +867,9 @@ size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpSt
   b->rank = cv.take<int>(1);
   b->q1 = host_start ? cv.take<double>(ldu) : nullptr;
   b->zpart = b->fused ? cv.take<double>(fused_partials(*op, d)) : nullptr;
+  b->Qs = b->df ? cv.take<float2>((size_t)ldu * (kmax + 1)) : nullptr;
+  b->Ps = b->df ? cv.take<float2>((size_t)ldv * (kmax + 1)) : nullptr;
+  b->ws2 = b->df ? cv.take<float2>(ldu > ldv ? ldu : ldv) : nullptr;
   char *dd;
   void *v, *tv;
   int32_t *rp, *ci, *trp, *tci;
@@ -874,12 +906,16 @@ int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &
   } else {
     GK_CUDA(draw_start(b.t, m, o.seed, s));
   }
+  if (b.df) {  // the shadows' padding rows (past m, n) are read beside the last odd row: keep them 0
+    GK_CUDA(cudaMemsetAsync(b.Qs, 0, sizeof(float2) * ldu * (kmax + 1), s));
+    GK_CUDA(cudaMemsetAsync(b.Ps, 0, sizeof(float2) * ldv * (kmax + 1), s));
+  }
   GK_CUDA(orthonormalize(b.t, m, nullptr, ldu, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, s, d));
-  GK_CUDA(normalize_append(b.t, m, b.Q, b.x32, b.ctl, s, d));
+  GK_CUDA(normalize_append(b.t, m, b.Q, b.x32, b.ctl, s, d, b.Qs));
   // p1 = A^T q1, alpha_1 = ||p1||, p1 = p1 / alpha_1
   GK_CUDA(matvec_t(op, b.x32, b.Q, b.z, nullptr, nullptr, b.part, b.ctl, s, d));
   GK_CUDA(orthonormalize(b.z, n, b.P, ldv, 0, 0, b.part, b.h, b.ctl, NM_BREAK, 0, 1, b.alpha, nullptr, s, d));
-  GK_CUDA(normalize_append(b.z, n, b.P, b.x32, b.ctl, s, d));
+  GK_CUDA(normalize_append(b.z, n, b.P, b.x32, b.ctl, s, d, b.Ps));
   inf.matvecs = 1;
   rc = read_ctl(b.ctl, nullptr, &hc, s);
   if (rc) return rc;
@@ -900,8 +936,9 @@ int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &
       prof.end();
       prof.begin(PC_ORTH);
       GK_CUDA(orthonormalize(b.w, m, b.Q, ldu, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 0, b.beta + j,
-                             b.alpha + (j - 1), s, d));
-      GK_CUDA(normalize_append(b.w, m, b.Q + j * ldu, b.fused ? nullptr : b.x32, b.ctl, s, d));
+                             b.alpha + (j - 1), s, d, b.Qs, b.ws2));
+      GK_CUDA(normalize_append(b.w, m, b.Q + j * ldu, b.fused ? nullptr : b.x32, b.ctl, s, d,
+                               b.Qs ? b.Qs + j * ldu : nullptr));
       prof.end();
       // alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j; after a
       // fused pass A^T q_{j+1} is A^T w / beta_{j+1} up to span(P_j), removed by the Gram-Schmidt
@@ -913,8 +950,8 @@ int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &
       prof.end();
       prof.begin(PC_ORTH);
       GK_CUDA(orthonormalize(b.z, n, b.P, ldv, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 1, b.alpha + j,
-                             b.beta + j, s, d));
-      GK_CUDA(normalize_append(b.z, n, b.P + j * ldv, b.x32, b.ctl, s, d));
+                             b.beta + j, s, d, b.Ps, b.ws2));
+      GK_CUDA(normalize_append(b.z, n, b.P + j * ldv, b.x32, b.ctl, s, d, b.Ps ? b.Ps + j * ldv : nullptr));
       prof.end();
     }
     rc = read_ctl(b.ctl, nullptr, &hc, s);
@@ -961,6 +998,7 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
   Op op = make_op(Ain);
   RankBufs b;
   b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   const size_t bytes = numrank_layout(Ain, kmax, d, st, host_sigma, host_start, nullptr, &b, &op);
   Workspace ws;
   rc = acquire(ws, bytes, o, s);
@@ -1053,6 +1091,7 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
   Op op = make_op(Ain);
   RankBufs b;
   b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   FsvdBufs f;
   const size_t nb = (numrank_layout(Ain, k, d, st, false, host_start, nullptr, &b, &op) + 255) / 256 * 256;
   const size_t split_floats = (route == 0 && accurate_ok(op)) ? accurate_floats(op, r) : 0;
@@ -1324,6 +1363,7 @@ size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *oin) {
   RankBufs b;
   Op op = make_op(A);
   b.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   return numrank_layout(A, clamp_kmax(A, kmax), d, st, false, false, nullptr, &b, &op);
 }
 

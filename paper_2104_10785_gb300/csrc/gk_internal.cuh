@@ -171,12 +171,17 @@ int learned_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_inf
 // than 1/sqrt(2) of the norm; then the norm and its judgement; see NormMode.
 // coef_out receives the accepted norm (0 on breakdown); prev is the previous
 // recurrence coefficient (for the sigma_est update of Algorithm 1).
+// Qs, ws2 (optional): the basis's double-f32 shadow (Qs[c * ld + i] = (hi, lo) of Q) and a
+// len-entry buffer for w's split; with both, vectors past the one-CTA size run the
+// double-f32 kernels.
 cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
                            double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
-                           cudaStream_t s, const Dev &d);
+                           cudaStream_t s, const Dev &d, const float2 *Qs = nullptr, float2 *ws2 = nullptr);
 // Q[:, col] = w * ctl->inv_norm, x32 = f32 copy (skipped when halted)
 cudaError_t normalize_append(const double *w, int64_t len, double *qcol, float *x32, const Ctl *ctl, cudaStream_t s,
-                             const Dev &d);
+                             const Dev &d, float2 *qs = nullptr);
+// Qs[c * ld + i] = (hi, lo) of Q[c * ld + i] for the first `cols` columns (the shadow of a basis)
+cudaError_t split_cols(const double *Q, int64_t len, int64_t ld, int cols, float2 *Qs, cudaStream_t s);
 // w = (start vector q1 ~ N(2,1), Philox4x32-10 + Box-Muller), len entries
 cudaError_t draw_start(double *w, int64_t len, uint64_t seed, cudaStream_t s);
 // w = replacement direction number dnum (SplitMix64, uniform [-1,1))

@@ -15,6 +15,10 @@
 // basis is read twice.
 // Vectors of at most 8192 entries (with len * j <= 2^18) take one kernel, k_cgs_small,
 // that runs the same passes, rule, norm and judgement in a single CTA.
+// Longer vectors with a double-f32 shadow of the basis (Qs: every entry as two f32, written
+// beside the f64 column) run the same passes and rules with the basis products in
+// double-f32 arithmetic on the FP32 pipes (k_cgs_dot_df, k_cgs_update_df): w, the norms and
+// the judgement stay f64.
 // Partial sums are written per row chunk and reduced in a fixed order, so the
 // results are bitwise reproducible.  The last block of the norm kernel applies
 // the break / breakdown test and records the event in the control block; every
@@ -263,6 +267,253 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_norm(const double *__re
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same Gram-Schmidt on the basis's double-f32 shadow (every entry q = qh + ql, two f32,
+// 8 bytes like the f64 basis).  GB300 runs FP64 at 1/64 of its FP32 rate: an f64 dot product
+// or update at HBM speed needs more FP64 FMAs per second than the chip has, while the same
+// products in double-f32 arithmetic (Dekker's TwoProd by FMA, Knuth's TwoSum) fit the FP32
+// pipes several times over.  w and the norms stay f64; the basis products carry ~2^-46 of
+// |q w| per term and their sums are exact up to the final rounding of each partial to f64.
+// Two rows are packed into f32x2 lanes (sm_100 FFMA2/FADD2/FMUL2).
+// ---------------------------------------------------------------------------
+constexpr int kDfRows = 2048;    // rows per block of the double-f32 dot kernel
+constexpr int kDfCols = 8;       // columns per block (one per warp)
+constexpr int kDfUpdThreads = 128;  // threads per block of the double-f32 update (two rows each)
+constexpr int kDfUnroll = 16;       // basis columns in flight per thread in the update
+
+// 16-byte load through the read-only path
+__device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// (sh, sl) += (ah + al) (bh + bl) per lane: TwoProd of the high parts, the two cross terms
+// in the low word, TwoSum into the running high word (the ah al-bl term, ~2^-48, dropped)
+__device__ __forceinline__ void df2_mac(float2 &sh, float2 &sl, float2 ah, float2 nah, float2 al, float2 bh,
+                                        float2 bl) {
+  const float2 m1 = f2(-1.f, -1.f);
+  const float2 q = __fmul2_rn(nah, bh);     // -p, p = fl(ah bh)
+  float2 e = __ffma2_rn(ah, bh, q);         // ah bh - p (exact)
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  const float2 t = __ffma2_rn(q, m1, sh);   // sh + p
+  const float2 bb = __ffma2_rn(sh, m1, t);  // t - sh
+  const float2 t1 = __ffma2_rn(bb, m1, t);  // t - bb
+  const float2 d1 = __ffma2_rn(t1, m1, sh); // sh - (t - bb)
+  const float2 d2 = __fadd2_rn(q, bb);      // -(p - bb)
+  float2 l = __fadd2_rn(sl, e);
+  l = __fadd2_rn(l, d1);
+  sl = __ffma2_rn(d2, m1, l);               // TwoSum error d1 + (p - bb)
+  sh = t;
+}
+
+// (sh, sl) += (bh, bl) per lane: double-f32 addition (TwoSum of the high words)
+__device__ __forceinline__ void df2_add(float2 &sh, float2 &sl, float2 bh, float2 bl) {
+  const float2 m1 = f2(-1.f, -1.f);
+  const float2 t = __fadd2_rn(sh, bh);
+  const float2 bb = __ffma2_rn(sh, m1, t);   // t - sh
+  const float2 t1 = __ffma2_rn(bb, m1, t);   // t - bb
+  const float2 d1 = __ffma2_rn(t1, m1, sh);  // sh - (t - bb)
+  const float2 d2 = __ffma2_rn(bb, m1, bh);  // bh - bb
+  sl = __fadd2_rn(__fadd2_rn(sl, bl), __fadd2_rn(d1, d2));
+  sh = t;
+}
+
+// (h, l) += (bh, bl): double-f32 addition (TwoSum of the high words)
+__device__ __forceinline__ void df_acc(float &h, float &l, float bh, float bl) {
+  const float t = __fadd_rn(h, bh);
+  const float bb = __fsub_rn(t, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bb)), __fsub_rn(bh, bb));
+  l = __fadd_rn(__fadd_rn(l, bl), err);
+  h = t;
+}
+
+// the f64 entries of a vector (or of `cols` columns with leading dimension ld) as (hi, lo) f32
+__global__ void k_split(const double *__restrict__ x, int64_t len, int64_t ld, int cols, float2 *__restrict__ out) {
+  const int64_t total = len * (int64_t)cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / len, i = t - c * len;
+    const double v = x[c * ld + i];
+    const float h = (float)v;
+    out[c * ld + i] = f2(h, (float)(v - (double)h));
+  }
+}
+
+// part[c * G + g] = Q[:, c] . w over row chunk g (kDfRows rows), one warp per column of the
+// block's column group; with_norm: part[j * G + g] = ||w||^2 over the chunk (f64, group 0)
+__global__ void __launch_bounds__(32 * kDfCols) k_cgs_dot_df(const float2 *__restrict__ Qs, int64_t ld, int64_t len,
+                                                            int j, const double *__restrict__ w,
+                                                            const float2 *__restrict__ ws2,
+                                                            double *__restrict__ part, const Ctl *ctl, int with_norm,
+                                                            int gated) {
+  if (halted(ctl) || (gated && pass2_off(ctl))) return;
+  __shared__ float4 wsh[kDfRows / 2];  // rows (2r, 2r + 1): (hi, lo, hi, lo)
+  const int G = gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * kDfRows;
+  const int rows = (int)(len - i0 < kDfRows ? len - i0 : kDfRows);
+  const int pairs = (rows + 1) / 2;
+  for (int r = threadIdx.x; r < pairs; r += blockDim.x) {
+    const float2 a = ws2[i0 + 2 * r];
+    const float2 b = 2 * r + 1 < rows ? ws2[i0 + 2 * r + 1] : f2(0.f, 0.f);
+    wsh[r] = make_float4(a.x, a.y, b.x, b.y);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.y * kDfCols + warp;
+  if (c < j) {
+    const float4 *q4 = reinterpret_cast<const float4 *>(Qs + (int64_t)c * ld + i0);
+    float2 sh = f2(0.f, 0.f), sl = f2(0.f, 0.f);
+    // rows past the chunk's end pair with zero w (and read q within the column's ld padding)
+    for (int r = lane; r < pairs; r += 32 * 8) {
+      float4 qv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) qv[u] = r + 32 * u < pairs ? ldg4(q4 + r + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // independent products per load (the loads stay in flight together), summed pairwise
+      float2 ph[8], pl[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        ph[u] = f2(0.f, 0.f);
+        pl[u] = f2(0.f, 0.f);
+        if (r + 32 * u < pairs) {
+          const float4 wv = wsh[r + 32 * u];
+          const float2 qh = f2(qv[u].x, qv[u].z), ql = f2(qv[u].y, qv[u].w);
+          df2_mac(ph[u], pl[u], qh, f2(-qh.x, -qh.y), ql, f2(wv.x, wv.z), f2(wv.y, wv.w));
+        }
+      }
+#pragma unroll
+      for (int w2 = 1; w2 < 8; w2 *= 2)
+#pragma unroll
+        for (int u = 0; u + w2 < 8; u += 2 * w2) df2_add(ph[u], pl[u], ph[u + w2], pl[u + w2]);
+      df2_add(sh, sl, ph[0], pl[0]);
+    }
+    float h = sh.x, l = sl.x;
+    df_acc(h, l, sh.y, sl.y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      df_acc(h, l, oh, ol);
+    }
+    if (lane == 0) part[(int64_t)c * G + blockIdx.x] = (double)h + (double)l;
+  }
+  if (with_norm && blockIdx.y == 0) {
+    __shared__ double red[kDfCols];
+    double sq = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      const double v = w[i0 + r];
+      sq = fma(v, v, sq);
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kDfCols; ++k) t += red[k];
+      part[(int64_t)j * G + blockIdx.x] = t;
+    }
+  }
+}
+
+// w -= Q h over this block's rows (two per thread, packed), with h split into (hi, lo) in
+// shared memory; the updated rows go to w, their split to ws2, and the chunk's ||w||^2 to
+// npart.  Stages as k_cgs_update_norm (0: last pass, judged; 1: the adaptive rule's first
+// pass; 2: its second pass, gated) plus 3: an intermediate pass (no norm, no judgement).
+__global__ void __launch_bounds__(kDfUpdThreads) k_cgs_update_df(const float2 *__restrict__ Qs, int64_t ld,
+                                                                 int64_t len, int j, double *__restrict__ w,
+                                                                 float2 *__restrict__ ws2,
+                                                                 const double *__restrict__ h,
+                                                                 double *__restrict__ npart, Ctl *ctl, NormArgs a,
+                                                                 int stage) {
+  if (halted(ctl) || (stage == 2 && pass2_off(ctl))) return;
+  extern __shared__ float2 hsp[];  // j entries: (hi, lo) of h
+  __shared__ double red[kDfUpdThreads / 32];
+  __shared__ bool last;
+  for (int c = threadIdx.x; c < j; c += blockDim.x) {
+    const double v = h[c];
+    const float hh = (float)v;
+    hsp[c] = f2(hh, (float)(v - (double)hh));
+  }
+  __syncthreads();
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;  // rows i, i + 1
+  double sq = 0.0;
+  if (i < len) {
+    const bool two = i + 1 < len;
+    float2 sh = f2(0.f, 0.f), sl = f2(0.f, 0.f);
+    const float4 *q4 = reinterpret_cast<const float4 *>(Qs + i);  // row pair of column 0
+    const int64_t ld2 = ld / 2;                                     // float4 per column
+    int c = 0;
+    for (; c + kDfUnroll <= j; c += kDfUnroll) {
+      float4 qv[kDfUnroll];
+#pragma unroll
+      for (int u = 0; u < kDfUnroll; ++u) qv[u] = ldg4(q4 + (int64_t)(c + u) * ld2);
+      // independent products per column of the batch (no chain through one accumulator, so the
+      // batch's loads are all in flight together), summed in a fixed pairwise order
+      float2 ph[kDfUnroll], pl[kDfUnroll];
+#pragma unroll
+      for (int u = 0; u < kDfUnroll; ++u) {
+        const float2 hc = hsp[c + u];
+        const float2 qh = f2(qv[u].x, qv[u].z), ql = f2(qv[u].y, qv[u].w);
+        ph[u] = f2(0.f, 0.f);
+        pl[u] = f2(0.f, 0.f);
+        df2_mac(ph[u], pl[u], qh, f2(-qh.x, -qh.y), ql, f2(hc.x, hc.x), f2(hc.y, hc.y));
+      }
+#pragma unroll
+      for (int w2 = 1; w2 < kDfUnroll; w2 *= 2)
+#pragma unroll
+        for (int u = 0; u + w2 < kDfUnroll; u += 2 * w2) df2_add(ph[u], pl[u], ph[u + w2], pl[u + w2]);
+      df2_add(sh, sl, ph[0], pl[0]);
+    }
+    for (; c < j; ++c) {
+      const float4 qv = ldg4(q4 + (int64_t)c * ld2);
+      const float2 hc = hsp[c];
+      const float2 qh = f2(qv.x, qv.z), ql = f2(qv.y, qv.w);
+      df2_mac(sh, sl, qh, f2(-qh.x, -qh.y), ql, f2(hc.x, hc.x), f2(hc.y, hc.y));
+    }
+    const double w0 = (w[i] - (double)sh.x) - (double)sl.x;
+    w[i] = w0;
+    const float h0 = (float)w0;
+    ws2[i] = f2(h0, (float)(w0 - (double)h0));
+    sq = w0 * w0;
+    if (two) {
+      const double w1 = (w[i + 1] - (double)sh.y) - (double)sl.y;
+      w[i + 1] = w1;
+      const float h1 = (float)w1;
+      ws2[i + 1] = f2(h1, (float)(w1 - (double)h1));
+      sq = fma(w1, w1, sq);
+    }
+  }
+  if (stage == 3) return;
+  sq = warp_sum(sq);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    npart[blockIdx.x] = t;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->cnt[0], 1u);
+    last = (arrived == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const volatile double *vp = npart;
+  double t = 0.0;
+  for (int g = threadIdx.x; g < (int)gridDim.x; g += blockDim.x) t += vp[g];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
+    ctl->cnt[0] = 0u;
+    if (stage == 1 && tot < 0.5 * h[j]) {
+      ctl->pass2 = 1;  // cancellation: the second pass decides
+    } else {
+      if (stage == 1) ctl->pass2 = 0;
+      judge(ctl, tot, a);
+    }
+  }
+}
+
 // Short vectors (len <= kSmallLen, len * j <= kSmallWork): the whole Gram-Schmidt of the
 // orthonormalize() contract -- the passes (or the adaptive rule), the norm and the
 // judgement -- in one CTA with w in shared memory, instead of six launches whose latency a
@@ -341,13 +592,15 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_cgs_small(const double *__
 }
 
 __global__ void k_normalize_append(const double *__restrict__ w, int64_t len, double *__restrict__ q,
-                                   float *__restrict__ x32, const Ctl *ctl) {
+                                   float *__restrict__ x32, float2 *__restrict__ qs, const Ctl *ctl) {
   if (halted(ctl)) return;
   const double f = ctl->inv_norm;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = w[i] * f;
     q[i] = v;
-    if (x32) x32[i] = (float)v;
+    const float h = (float)v;
+    if (x32) x32[i] = h;
+    if (qs) qs[i] = f2(h, (float)(v - (double)h));
   }
 }
 
@@ -452,7 +705,7 @@ int cgs_blocks(int64_t len, const Dev &d) {
 
 cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
                            double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
-                           cudaStream_t s, const Dev &d) {
+                           cudaStream_t s, const Dev &d, const float2 *Qs, float2 *ws2) {
   if (len <= kSmallLen && len * (int64_t)(j > 0 ? j : 1) <= kSmallWork) {
     const size_t dyn = sizeof(double) * (size_t)(len + (j > 0 ? j : 1));  // <= (8192 + 1025) doubles
     if (dyn > 48 * 1024) {
@@ -478,6 +731,37 @@ cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, 
     GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, 0, w, h, npart, S, ctl, a, 0));
     return cudaGetLastError();
   }
+  if (Qs != nullptr && ws2 != nullptr) {
+    // the double-f32 shadow of the basis: the same passes and rules on the FP32 pipes
+    const int Gd = (int)((len + kDfRows - 1) / kDfRows);
+    const int Gu = (int)((len + 2 * kDfUpdThreads - 1) / (2 * kDfUpdThreads));
+    const dim3 dgrid((unsigned)Gd, (unsigned)((j + kDfCols - 1) / kDfCols));
+    const size_t dynu = sizeof(float2) * (size_t)j;
+    if (dynu > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_cgs_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynu);
+      if (e != cudaSuccess) return e;
+    }
+    double *npu = part + (int64_t)Gd * (j + 1);
+    GK_LAUNCH(k_split<<<vec_blocks(len), 256, 0, s>>>(w, len, len, 1, ws2));
+    if (passes == 0) {  // adaptive: part holds j + 1 columns (the last one ||w||^2)
+      GK_LAUNCH(k_cgs_dot_df<<<dgrid, 32 * kDfCols, 0, s>>>(Qs, ld, len, j, w, ws2, part, ctl, 1, 0));
+      GK_LAUNCH(k_reduce_cols<<<j + 1, 128, 0, s>>>(part, Gd, h, ctl, 0));
+      GK_LAUNCH(k_cgs_update_df<<<Gu, kDfUpdThreads, dynu, s>>>(Qs, ld, len, j, w, ws2, h, npu, ctl, a, 1));
+      GK_LAUNCH(k_cgs_dot_df<<<dgrid, 32 * kDfCols, 0, s>>>(Qs, ld, len, j, w, ws2, part, ctl, 0, 1));
+      GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, Gd, h, ctl, 1));
+      GK_LAUNCH(k_cgs_update_df<<<Gu, kDfUpdThreads, dynu, s>>>(Qs, ld, len, j, w, ws2, h, npu, ctl, a, 2));
+      return cudaGetLastError();
+    }
+    GK_LAUNCH(k_cgs_dot_df<<<dgrid, 32 * kDfCols, 0, s>>>(Qs, ld, len, j, w, ws2, part, ctl, 0, 0));
+    GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, Gd, h, ctl, 0));
+    for (int p = 1; p < passes; ++p) {
+      GK_LAUNCH(k_cgs_update_df<<<Gu, kDfUpdThreads, dynu, s>>>(Qs, ld, len, j, w, ws2, h, npu, ctl, a, 3));
+      GK_LAUNCH(k_cgs_dot_df<<<dgrid, 32 * kDfCols, 0, s>>>(Qs, ld, len, j, w, ws2, part, ctl, 0, 0));
+      GK_LAUNCH(k_reduce_cols<<<j, 128, 0, s>>>(part, Gd, h, ctl, 0));
+    }
+    GK_LAUNCH(k_cgs_update_df<<<Gu, kDfUpdThreads, dynu, s>>>(Qs, ld, len, j, w, ws2, h, npu, ctl, a, 0));
+    return cudaGetLastError();
+  }
   if (passes == 0) {  // adaptive; part holds j + 1 columns (the last one ||w||^2), npart follows them
     double *np2 = part + (int64_t)G * (j + 1);
     GK_LAUNCH(k_cgs_dot<<<G, kThreads, 0, s>>>(Q, ld, len, j, w, part, S, ctl, 1, 0));
@@ -499,9 +783,17 @@ cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, 
 }
 
 cudaError_t normalize_append(const double *w, int64_t len, double *qcol, float *x32, const Ctl *ctl, cudaStream_t s,
-                             const Dev &d) {
+                             const Dev &d, float2 *qs) {
   (void)d;
-  GK_LAUNCH(k_normalize_append<<<vec_blocks(len), 256, 0, s>>>(w, len, qcol, x32, ctl));
+  GK_LAUNCH(k_normalize_append<<<vec_blocks(len), 256, 0, s>>>(w, len, qcol, x32, qs, ctl));
+  return cudaGetLastError();
+}
+
+cudaError_t split_cols(const double *Q, int64_t len, int64_t ld, int cols, float2 *Qs, cudaStream_t s) {
+  if (cols <= 0) return cudaSuccess;
+  int64_t b = (len * cols + 255) / 256;
+  if (b > 8192) b = 8192;
+  GK_LAUNCH(k_split<<<(int)b, 256, 0, s>>>(Q, len, ld, cols, Qs));
   return cudaGetLastError();
 }
 

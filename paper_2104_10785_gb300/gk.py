@@ -26,6 +26,7 @@ GK_FLAG_PROFILE = 1
 GK_FLAG_AUTOTUNE = 2
 GK_FLAG_FUSED = 4
 GK_FLAG_REFINE = 8
+GK_FLAG_ORTH_F64 = 16
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -300,9 +301,10 @@ def default_opts() -> gk_opts:
 
 
 def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, eps_absolute=False, seed=None,
-          start=None, stream=None, workspace=None, profile=False, fused=False, refine=False):
+          start=None, stream=None, workspace=None, profile=False, fused=False, refine=False, orth_f64=False):
     o = default_opts()
-    o.flags = (GK_FLAG_PROFILE if profile else 0) | (GK_FLAG_FUSED if fused else 0) | (GK_FLAG_REFINE if refine else 0)
+    o.flags = ((GK_FLAG_PROFILE if profile else 0) | (GK_FLAG_FUSED if fused else 0) | (GK_FLAG_REFINE if refine else 0)
+               | (GK_FLAG_ORTH_F64 if orth_f64 else 0))
     o.krylov_dim = int(krylov_dim)
     o.keep = int(keep)
     if max_restarts is not None:
@@ -329,7 +331,7 @@ def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, e
 def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0, max_restarts: int | None = None,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
             scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
-            refine: bool = False, predictor: "Predictor | None" = None):
+            refine: bool = False, predictor: "Predictor | None" = None, orth_f64: bool = False):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
@@ -353,7 +355,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     else:
         U, S, V = out
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
-                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine)
+                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine, orth_f64)
     if predictor is not None:
         o.predictor = predictor.handle
     info = gk_info()
@@ -365,7 +367,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
 
 def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = None, seed: int | None = None,
             start=None, stream=None, workspace=None, scale: float = 1.0, check: bool = True, profile: bool = False,
-            fused: bool = False):
+            fused: bool = False, orth_f64: bool = False):
     """Algorithm 2 as printed: k steps of Algorithm 1, the SVD of B, the r largest triplets
     (route 1: U = Q X; route 0: u_i = A v_i / sigma_i).  Returns (U m x r, S r, V n x r, status,
     info dict); outputs live where A lives."""
@@ -378,7 +380,7 @@ def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = No
     V = torch.empty((r, M.n), dtype=torch.float64, device=dev, pin_memory=pin)
     S = torch.empty(r, dtype=torch.float64, device=dev, pin_memory=pin)
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), 0, 0, None, reorth_passes, False, seed, start,
-                  stream, workspace, profile, fused)
+                  stream, workspace, profile, fused, orth_f64=orth_f64)
     info = gk_info()
     st = lib().gk_fsvd(C.byref(M), int(k), int(r), int(route), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
     if check and st < 0:
@@ -388,7 +390,8 @@ def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = No
 
 def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = False, reorth_passes: int | None = None,
                seed: int | None = None, start=None, stream=None, workspace=None, scale: float = 1.0,
-               want_sigma: bool = False, check: bool = True, profile: bool = False, fused: bool = False):
+               want_sigma: bool = False, check: bool = True, profile: bool = False, fused: bool = False,
+               orth_f64: bool = False):
     """Numerical rank by Algorithm 3.  Returns (rank, sigma(B) or None, status, info dict)."""
     M, keep_a = make_matrix(A, scale)
     dev = A.device
@@ -398,7 +401,7 @@ def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = Fals
     km = mn if kmax <= 0 or kmax > mn else kmax
     sig = torch.zeros(km + 1, dtype=torch.float64, device=dev) if want_sigma else None
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), 0, 0, None, reorth_passes, eps_absolute,
-                  seed, start, stream, workspace, profile, fused)
+                  seed, start, stream, workspace, profile, fused, orth_f64=orth_f64)
     info = gk_info()
     r = C.c_int(-1)
     st = lib().gk_numrank(C.byref(M), float(eps), int(kmax), C.byref(o), C.byref(r), _ptr(sig), C.byref(info))
