@@ -401,6 +401,7 @@ size_t psvd_layout(const gk_matrix *A, const PsvdPlan &p, const Dev &d, const Op
   b->x32 = cv.take<float>(p.ldu > p.ldv ? p.ldu : p.ldv);
   const int64_t gmax = cgs_blocks(p.m, d) > cgs_blocks(p.n, d) ? cgs_blocks(p.m, d) : cgs_blocks(p.n, d);
   int64_t pcount = gmax * (K + 2) + gmax;
+  if (coop_partials(K, d) > pcount) pcount = coop_partials(K, d);
   const int64_t gp = gemvt_partials(*op, d);
   if (gp > pcount) pcount = gp;
   b->part = cv.take<double>(pcount);
@@ -698,10 +699,9 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
             prof.end();
             prof.begin(PC_ORTH);
           }
-          GK_CUDA(orthonormalize(b.w, m, b.Ub, ldu, j, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 0, b.alpha + j,
-                                 nullptr, s, d, b.Us, b.ws2));
-          GK_CUDA(normalize_append(b.w, m, b.Ub + (int64_t)j * ldu, fused_step ? nullptr : b.x32, b.ctl, s, d,
-                                   b.Us ? b.Us + (int64_t)j * ldu : nullptr));
+          GK_CUDA(orth_append(b.w, m, b.Ub, ldu, j, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 0, b.alpha + j,
+                              nullptr, b.Ub + (int64_t)j * ldu, fused_step ? nullptr : b.x32, s, d, b.Us, b.ws2,
+                              b.Us ? b.Us + (int64_t)j * ldu : nullptr));
           prof.end();
           inf.matvecs++;
         }
@@ -715,10 +715,9 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
                            b.ctl, s, d));
         prof.end();
         prof.begin(PC_ORTH);
-        GK_CUDA(orthonormalize(b.z, n, b.Vb, ldv, j + 1, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 1,
-                               b.beta + j, nullptr, s, d, b.Vs, b.ws2));
-        GK_CUDA(normalize_append(b.z, n, b.Vb + (int64_t)(j + 1) * ldv, b.x32, b.ctl, s, d,
-                                 b.Vs ? b.Vs + (int64_t)(j + 1) * ldv : nullptr));
+        GK_CUDA(orth_append(b.z, n, b.Vb, ldv, j + 1, p.passes, b.part, b.h, b.ctl, NM_BREAKDOWN, j, 1, b.beta + j,
+                            nullptr, b.Vb + (int64_t)(j + 1) * ldv, b.x32, s, d, b.Vs, b.ws2,
+                            b.Vs ? b.Vs + (int64_t)(j + 1) * ldv : nullptr));
         prof.end();
         inf.matvecs++;
         inf.steps++;
@@ -856,6 +855,7 @@ size_t numrank_layout(const gk_matrix *A, int64_t kmax, const Dev &d, const OpSt
   b->x32 = cv.take<float>(ldu > ldv ? ldu : ldv);
   const int64_t gmax = cgs_blocks(A->m, d) > cgs_blocks(A->n, d) ? cgs_blocks(A->m, d) : cgs_blocks(A->n, d);
   int64_t pcount = gmax * (kmax + 2) + gmax;
+  if (coop_partials((int)kmax, d) > pcount) pcount = coop_partials((int)kmax, d);
   const int64_t gp = gemvt_partials(*op, d);
   if (gp > pcount) pcount = gp;
   b->part = cv.take<double>(pcount);
@@ -935,10 +935,9 @@ int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &
                        s, d));
       prof.end();
       prof.begin(PC_ORTH);
-      GK_CUDA(orthonormalize(b.w, m, b.Q, ldu, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 0, b.beta + j,
-                             b.alpha + (j - 1), s, d, b.Qs, b.ws2));
-      GK_CUDA(normalize_append(b.w, m, b.Q + j * ldu, b.fused ? nullptr : b.x32, b.ctl, s, d,
-                               b.Qs ? b.Qs + j * ldu : nullptr));
+      GK_CUDA(orth_append(b.w, m, b.Q, ldu, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 0, b.beta + j,
+                          b.alpha + (j - 1), b.Q + j * ldu, b.fused ? nullptr : b.x32, s, d, b.Qs, b.ws2,
+                          b.Qs ? b.Qs + j * ldu : nullptr));
       prof.end();
       // alpha_{j+1} p_{j+1} = A^T q_{j+1} - beta_{j+1} p_j, reorthogonalized against P_j; after a
       // fused pass A^T q_{j+1} is A^T w / beta_{j+1} up to span(P_j), removed by the Gram-Schmidt
@@ -949,9 +948,8 @@ int lower_sweep(const gk_matrix *Ain, const gk_opts &o, const Op &op, RankBufs &
         GK_CUDA(matvec_t(op, b.x32, b.Q + j * ldu, b.z, b.P + (j - 1) * ldv, b.beta + j, b.part, b.ctl, s, d));
       prof.end();
       prof.begin(PC_ORTH);
-      GK_CUDA(orthonormalize(b.z, n, b.P, ldv, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 1, b.alpha + j,
-                             b.beta + j, s, d, b.Ps, b.ws2));
-      GK_CUDA(normalize_append(b.z, n, b.P + j * ldv, b.x32, b.ctl, s, d, b.Ps ? b.Ps + j * ldv : nullptr));
+      GK_CUDA(orth_append(b.z, n, b.P, ldv, jj, passes, b.part, b.h, b.ctl, NM_BREAK, jj, 1, b.alpha + j,
+                          b.beta + j, b.P + j * ldv, b.x32, s, d, b.Ps, b.ws2, b.Ps ? b.Ps + j * ldv : nullptr));
       prof.end();
     }
     rc = read_ctl(b.ctl, nullptr, &hc, s);

@@ -180,6 +180,15 @@ cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, 
 // Q[:, col] = w * ctl->inv_norm, x32 = f32 copy (skipped when halted)
 cudaError_t normalize_append(const double *w, int64_t len, double *qcol, float *x32, const Ctl *ctl, cudaStream_t s,
                              const Dev &d, float2 *qs = nullptr);
+// orthonormalize followed by normalize_append into qcol (and its copy qscol, and x32): with a
+// double-f32 copy of the basis and a vector past the one-CTA size whose slabs fit shared
+// memory, one cooperative launch does all of it (gk_orth.cu, k_orth_coop)
+cudaError_t orth_append(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
+                        double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
+                        double *qcol, float *x32, cudaStream_t s, const Dev &d, const float2 *Qs, float2 *ws2,
+                        float2 *qscol);
+// doubles of `part` the cooperative orthonormalization needs for Krylov dimension K
+int64_t coop_partials(int K, const Dev &d);
 // Qs[c * ld + i] = (hi, lo) of Q[c * ld + i] for the first `cols` columns (the shadow of a basis)
 cudaError_t split_cols(const double *Q, int64_t len, int64_t ld, int cols, float2 *Qs, cudaStream_t s);
 // w = (start vector q1 ~ N(2,1), Philox4x32-10 + Box-Muller), len entries

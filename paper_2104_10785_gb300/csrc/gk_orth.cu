@@ -514,6 +514,293 @@ __global__ void __launch_bounds__(kDfUpdThreads) k_cgs_update_df(const float2 *_
   }
 }
 
+// ---------------------------------------------------------------------------
+// One cooperative launch for a whole orthonormalization on the double-f32 copy: the passes
+// (or the adaptive rule), the norm, the judgement and the append of the new column.  Each
+// block (one per SM, all resident) owns a slab of rows and keeps its rows of w -- f64 and
+// split -- in shared memory for the whole call; the phases are separated by a grid barrier:
+//   dots of every column over the slab -> part[c * G + b]          | barrier
+//   block b reduces columns b, b + G, ... (each column's partials by one fixed tree) | barrier
+//   every block takes h, w -= Q h on the slab, the slab's ||w||^2 -> part[slot * G + b] | barrier
+//   the norm (every block the same sum), the adaptive rule's decision; block 0 records the
+//   judgement, every block derives the same outcome and normalizes its rows into the basis
+//   column, its copy and the f32 vector.
+// Barrier waits are bounded (~2 s of SM clock); one that gives up records a timeout in the
+// control block.  The barrier counter (ctl->cnt[2]) is cleared by the last block to leave.
+// ---------------------------------------------------------------------------
+constexpr int kCoopThreads = 512;
+constexpr int kCoopWarps = kCoopThreads / 32;
+constexpr int kCoopBatch = 16;                      // basis columns in flight per thread (update)
+constexpr long long kCoopWaitCycles = 4000000000ll;  // ~2 s of SM clock
+
+struct CoopArgs {
+  const float2 *Qs;
+  int64_t ld, len;
+  int j, passes, rows;  // rows: per block (even)
+  double *w, *qcol, *part;
+  float2 *qscol;
+  float *x32;
+  Ctl *ctl;
+  NormArgs a;
+};
+
+__device__ void coop_timeout(Ctl *ctl) {
+  if (atomicCAS(&ctl->timeout, 0, 3) == 0) {
+    ctl->event = EV_TIMEOUT;
+    __threadfence();
+    atomicExch(&ctl->halt, 1);
+  }
+}
+
+// bounded grid barrier over the G resident blocks; k counts the barriers passed
+__device__ __forceinline__ void grid_sync(Ctl *ctl, unsigned G, unsigned &k) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&ctl->cnt[2], 1u);
+    const unsigned target = (k + 1) * G;
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->cnt[2]) : "memory");
+      if (v >= target) break;
+      if (clock64() - t0 > kCoopWaitCycles) {
+        coop_timeout(ctl);
+        break;
+      }
+    }
+    __threadfence();
+  }
+  ++k;
+  __syncthreads();
+}
+
+// the scale judge() will accept for ||w||^2 = nrm2, from the control block's values before the
+// call (sest0, eps, eps_rel, norm0): -1 where judge() halts the sweep.  The same arithmetic as
+// judge(), so every block reaches block 0's decision without waiting for it.
+__device__ double judge_scale(double nrm2, double sest0, double eps, int eps_rel, double norm0, const NormArgs &a) {
+  const double nrm = sqrt(nrm2);
+  if (!isfinite(nrm)) return -1.0;
+  if (a.mode == NM_BREAK) {
+    const double se = fmax(sest0, a.prev ? hypot(*a.prev, nrm) : nrm);
+    const double thr = eps_rel ? eps * se : eps;
+    if (nrm <= thr) return -1.0;
+  } else if (a.mode == NM_BREAKDOWN) {
+    const double se = fmax(sest0, nrm);
+    if (nrm <= 0x1.0p-46 * se) return -1.0;
+  } else if (a.mode == NM_FRESH) {
+    if (!(nrm > 1e-8 * norm0)) return 0.0;
+  }
+  return nrm > 0.0 ? 1.0 / nrm : 0.0;
+}
+
+__global__ void __launch_bounds__(kCoopThreads, 1) k_orth_coop(CoopArgs p) {
+  Ctl *ctl = p.ctl;
+  if (halted(ctl)) return;  // read before any block can judge (that follows the first barrier)
+  extern __shared__ double cws[];
+  const int R = p.rows, j = p.j;
+  double *ws = cws;                                        // R: this slab's rows of w
+  float4 *wsp = reinterpret_cast<float4 *>(ws + R);        // R / 2: row pairs split (hi, lo, hi, lo)
+  float2 *hs = reinterpret_cast<float2 *>(wsp + R / 2);    // j: (hi, lo) of h
+  __shared__ double red[kCoopWarps];
+  __shared__ double tot_s;
+  const unsigned G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t i0 = (int64_t)b * R;
+  const int rows = (int)(p.len - i0 <= 0 ? 0 : (p.len - i0 < R ? p.len - i0 : R));
+  const int pairs = (rows + 1) / 2;
+  unsigned bk = 0;
+  // the control block's state before this call (block 0 changes it only after the last barrier)
+  const double sest0 = ctl->sest, eps0 = ctl->eps, norm0 = ctl->norm;
+  const int eps_rel0 = ctl->eps_rel;
+
+  for (int r = tid; r < R; r += kCoopThreads) ws[r] = r < rows ? p.w[i0 + r] : 0.0;
+  __syncthreads();
+  auto split_slab = [&]() {
+    for (int pr = tid; pr < R / 2; pr += kCoopThreads) {
+      const double a0 = ws[2 * pr], a1 = ws[2 * pr + 1];
+      const float h0 = (float)a0, h1 = (float)a1;
+      wsp[pr] = make_float4(h0, (float)(a0 - (double)h0), h1, (float)(a1 - (double)h1));
+    }
+    __syncthreads();
+  };
+  // the slab's sum of v over all threads, fixed order
+  auto block_sum = [&](double v) -> double {
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kCoopWarps; ++k) t += red[k];
+      tot_s = t;
+    }
+    __syncthreads();
+    const double t = tot_s;
+    __syncthreads();
+    return t;
+  };
+  auto norm_partial = [&](int slot) {
+    double sq = 0.0;
+    for (int r = tid; r < rows; r += kCoopThreads) sq = fma(ws[r], ws[r], sq);
+    sq = block_sum(sq);
+    if (tid == 0) p.part[(int64_t)slot * G + b] = sq;
+  };
+  // the same total in every block: the G partials of a slot, one per thread, summed by the
+  // same fixed tree in every block (G <= kCoopThreads)
+  auto total = [&](int slot) -> double {
+    const double v = tid < (int)G ? __ldcg(p.part + (int64_t)slot * G + tid) : 0.0;
+    return block_sum(v);
+  };
+  double *hcol = p.part + (int64_t)(j + 3) * G;  // the reduced coefficients h
+  auto dots = [&]() {
+    for (int c = warp; c < j; c += kCoopWarps) {
+      const float4 *q4 = reinterpret_cast<const float4 *>(p.Qs + (int64_t)c * p.ld + i0);
+      float2 sh = f2(0.f, 0.f), sl = f2(0.f, 0.f);
+      for (int r = lane; r < pairs; r += 32 * 8) {
+        float4 qv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) qv[u] = r + 32 * u < pairs ? ldg4(q4 + r + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 ph[8], pl[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          ph[u] = f2(0.f, 0.f);
+          pl[u] = f2(0.f, 0.f);
+          if (r + 32 * u < pairs) {
+            const float4 wv = wsp[r + 32 * u];
+            const float2 qh = f2(qv[u].x, qv[u].z), ql = f2(qv[u].y, qv[u].w);
+            df2_mac(ph[u], pl[u], qh, f2(-qh.x, -qh.y), ql, f2(wv.x, wv.z), f2(wv.y, wv.w));
+          }
+        }
+#pragma unroll
+        for (int w2 = 1; w2 < 8; w2 *= 2)
+#pragma unroll
+          for (int u = 0; u + w2 < 8; u += 2 * w2) df2_add(ph[u], pl[u], ph[u + w2], pl[u + w2]);
+        df2_add(sh, sl, ph[0], pl[0]);
+      }
+      float h = sh.x, l = sl.x;
+      df_acc(h, l, sh.y, sl.y);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        df_acc(h, l, oh, ol);
+      }
+      if (lane == 0) p.part[(int64_t)c * G + b] = (double)h + (double)l;
+    }
+  };
+  // block b reduces columns b, b + G, ... (every column's G partials by the same tree), then,
+  // after a barrier, every block takes all of h
+  auto reduce_h = [&]() {
+    for (int c = b; c < j; c += G) {
+      const double t = total(c);
+      if (tid == 0) hcol[c] = t;
+    }
+    grid_sync(ctl, G, bk);
+    for (int c = tid; c < j; c += kCoopThreads) {
+      const double t = __ldcg(hcol + c);
+      const float hh = (float)t;
+      hs[c] = f2(hh, (float)(t - (double)hh));
+    }
+    __syncthreads();
+  };
+  auto update = [&]() {
+    for (int pr = tid; pr < pairs; pr += kCoopThreads) {
+      const float4 *q4 = reinterpret_cast<const float4 *>(p.Qs + i0) + pr;  // row pair of column 0
+      const int64_t ld2 = p.ld / 2;
+      float2 sh = f2(0.f, 0.f), sl = f2(0.f, 0.f);
+      int c = 0;
+      for (; c + kCoopBatch <= j; c += kCoopBatch) {
+        float4 qv[kCoopBatch];
+#pragma unroll
+        for (int u = 0; u < kCoopBatch; ++u) qv[u] = ldg4(q4 + (int64_t)(c + u) * ld2);
+        float2 ph[kCoopBatch], pl[kCoopBatch];
+#pragma unroll
+        for (int u = 0; u < kCoopBatch; ++u) {
+          const float2 hc = hs[c + u];
+          const float2 qh = f2(qv[u].x, qv[u].z), ql = f2(qv[u].y, qv[u].w);
+          ph[u] = f2(0.f, 0.f);
+          pl[u] = f2(0.f, 0.f);
+          df2_mac(ph[u], pl[u], qh, f2(-qh.x, -qh.y), ql, f2(hc.x, hc.x), f2(hc.y, hc.y));
+        }
+#pragma unroll
+        for (int w2 = 1; w2 < kCoopBatch; w2 *= 2)
+#pragma unroll
+          for (int u = 0; u + w2 < kCoopBatch; u += 2 * w2) df2_add(ph[u], pl[u], ph[u + w2], pl[u + w2]);
+        df2_add(sh, sl, ph[0], pl[0]);
+      }
+      for (; c < j; ++c) {
+        const float4 qv = ldg4(q4 + (int64_t)c * ld2);
+        const float2 hc = hs[c];
+        const float2 qh = f2(qv.x, qv.z), ql = f2(qv.y, qv.w);
+        df2_mac(sh, sl, qh, f2(-qh.x, -qh.y), ql, f2(hc.x, hc.x), f2(hc.y, hc.y));
+      }
+      const double a0 = (ws[2 * pr] - (double)sh.x) - (double)sl.x;
+      const double a1 = 2 * pr + 1 < rows ? (ws[2 * pr + 1] - (double)sh.y) - (double)sl.y : 0.0;
+      ws[2 * pr] = a0;
+      ws[2 * pr + 1] = a1;
+      const float h0 = (float)a0, h1 = (float)a1;
+      wsp[pr] = make_float4(h0, (float)(a0 - (double)h0), h1, (float)(a1 - (double)h1));
+    }
+    __syncthreads();
+  };
+
+  split_slab();
+  double tot;
+  if (p.passes == 0) {
+    // adaptive: one pass, a second only if the first kept less than half of ||w||^2
+    norm_partial(j);
+    dots();
+    grid_sync(ctl, G, bk);
+    const double before = total(j);
+    reduce_h();
+    update();
+    norm_partial(j + 1);
+    grid_sync(ctl, G, bk);
+    tot = total(j + 1);
+    if (tot < 0.5 * before) {
+      dots();
+      grid_sync(ctl, G, bk);
+      reduce_h();
+      update();
+      norm_partial(j + 2);
+      grid_sync(ctl, G, bk);
+      tot = total(j + 2);
+    }
+  } else {
+    for (int ps = 0; ps < p.passes; ++ps) {
+      dots();
+      grid_sync(ctl, G, bk);
+      reduce_h();
+      update();
+      if (ps == p.passes - 1) norm_partial(j + 1);
+      grid_sync(ctl, G, bk);  // every block has read this pass's dots before the next overwrites them
+    }
+    tot = total(j + 1);
+  }
+  if (b == 0 && tid == 0) judge(ctl, tot, p.a);
+  // the judgement's scale, the same in every block (-1: the sweep halts, the column is not written)
+  const double f = judge_scale(tot, sest0, eps0, eps_rel0, norm0, p.a);
+  for (int r = tid; r < rows; r += kCoopThreads) {
+    const double v = ws[r];
+    p.w[i0 + r] = v;
+    if (f >= 0.0) {
+      const double q = v * f;
+      p.qcol[i0 + r] = q;
+      const float qh = (float)q;
+      if (p.x32) p.x32[i0 + r] = qh;
+      p.qscol[i0 + r] = f2(qh, (float)(q - (double)qh));
+    }
+  }
+  // the last block to leave clears the barrier counter for the next launch
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->cnt[3], 1u) == G - 1) {
+      ctl->cnt[2] = 0u;
+      ctl->cnt[3] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 // Short vectors (len <= kSmallLen, len * j <= kSmallWork): the whole Gram-Schmidt of the
 // orthonormalize() contract -- the passes (or the adaptive rule), the norm and the
 // judgement -- in one CTA with w in shared memory, instead of six launches whose latency a
@@ -780,6 +1067,63 @@ cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, 
   }
   GK_LAUNCH(k_cgs_update_norm<<<G, kThreads, dyn, s>>>(Q, ld, len, j, w, h, npart, S, ctl, a, 0));
   return cudaGetLastError();
+}
+
+size_t coop_smem(int rows, int j) { return sizeof(double) * (size_t)rows * 2 + sizeof(float2) * (size_t)j; }
+
+int coop_rows(int64_t len, const Dev &d) {
+  int64_t r = (len + d.sms - 1) / d.sms;
+  return (int)((r + 1) / 2 * 2);
+}
+
+bool coop_ok(int64_t len, int j, const Dev &d) {
+  if (len <= kSmallLen || j <= 0 || d.sms > kCoopThreads) return false;
+  const size_t smem = coop_smem(coop_rows(len, d), j);
+  if (smem > 200 * 1024) return false;
+  static int attr_dev = -1, per_sm = 0;
+  if (attr_dev != d.id) {
+    if (cudaFuncSetAttribute(k_orth_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_orth_coop, kCoopThreads, 200 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+    attr_dev = d.id;
+  }
+  return per_sm >= 1;
+}
+
+int64_t coop_partials(int K, const Dev &d) { return (int64_t)(K + 3) * d.sms + K + 3; }
+
+cudaError_t orth_append(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
+                        double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
+                        double *qcol, float *x32, cudaStream_t s, const Dev &d, const float2 *Qs, float2 *ws2,
+                        float2 *qscol) {
+  if (Qs != nullptr && qscol != nullptr && passes >= 0 && passes <= 3 && coop_ok(len, j, d)) {
+    CoopArgs a;
+    a.Qs = Qs;
+    a.ld = ld;
+    a.len = len;
+    a.j = j;
+    a.passes = passes;
+    a.rows = coop_rows(len, d);
+    a.w = w;
+    a.qcol = qcol;
+    a.part = part;
+    a.qscol = qscol;
+    a.x32 = x32;
+    a.ctl = ctl;
+    a.a = NormArgs{mode, step, side, coef_out, prev};
+    void *args[] = {&a};
+    const size_t smem = coop_smem(a.rows, j);
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_orth_coop, dim3((unsigned)d.sms),
+                                                      dim3(kCoopThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    return cudaSuccess;
+  }
+  cudaError_t e = orthonormalize(w, len, Q, ld, j, passes, part, h, ctl, mode, step, side, coef_out, prev, s, d, Qs, ws2);
+  if (e != cudaSuccess) return e;
+  return normalize_append(w, len, qcol, x32, ctl, s, d, qscol);
 }
 
 cudaError_t normalize_append(const double *w, int64_t len, double *qcol, float *x32, const Ctl *ctl, cudaStream_t s,
