@@ -126,6 +126,28 @@ def sparse_planted(m: int, n: int, per_row: int, sigma: np.ndarray, seed: int, u
 # ---------------------------------------------------------------------------
 # Workload recipes (full size and reduced size) -- parameters only
 # ---------------------------------------------------------------------------
+def rsgd_data(P: int, N: int, d1: int, d2: int, r: int, steps: int, b: int, seed: int):
+    """Paired data for P independent similarity-learning problems (the shape of the paper's
+    Riemannian similarity-learning runs: d1 x d2 parameter matrices of rank r).  Problem p has
+    samples x_i ~ N(0, I_d1), v_i ~ N(0, I_d2) (rows of X[p], Vd[p]) and labels
+    y_i = -sign(x_i^T W*_p v_i) for a planted rank-r W*_p, so that lowering
+    mean(y_i x_i^T W v_i) -- what the printed update W - eta Z does -- moves W towards W*_p.
+    Also W0 ~ N(0, 1) (the algorithm's initialization), the mini-batches (steps x P x b sample
+    indices, drawn without replacement within a batch), one start vector per problem for the
+    inner SVDs (entries N(2, 1), as the library draws them) and W*.  All f64 / int32."""
+    g = rng(seed)
+    X = g.standard_normal((P, N, d1))
+    Vd = g.standard_normal((P, N, d2))
+    Wstar = np.stack([g.standard_normal((d1, r)) @ g.standard_normal((r, d2)) for _ in range(P)])
+    s = np.einsum("pni,pij,pnj->pn", X, Wstar, Vd)
+    y = -np.sign(s)
+    y[y == 0] = -1.0
+    W0 = g.standard_normal((P, d1, d2))
+    batches = np.stack([np.stack([g.choice(N, size=b, replace=False) for _ in range(P)]) for _ in range(steps)])
+    q1 = 2.0 + g.standard_normal((P, d1))
+    return X, Vd, y, W0, batches.astype(np.int32), q1, Wstar
+
+
 WORKLOADS = {
     # dense f64, prescribed spectrum sigma_i = 0.9^i, top-10, Krylov 30, tol 1e-10
     "dense_f64_2000x1000_top10": dict(kind="spectrum", m=2000, n=1000, q=0.9, k=10, K=30, tol=1e-10,
