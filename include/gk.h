@@ -312,6 +312,47 @@ int gk_psvd_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_inf
  * gk_numrank) in one persistent launch, scheduled as gk_psvd_batched. */
 int gk_numrank_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
 
+/* ---- Algorithm 4: fast Riemannian mini-batch gradient descent ---------- */
+/* P independent similarity-learning problems of one shape (Section 4, Algorithm 4), each
+ * minimizing the mini-batch objective over the manifold of rank-r d1 x d2 matrices.  Every
+ * step, for every problem p at once:
+ *   Gr = (1/b) sum_{i in batch} y_i x_i v_i^T - lam W      (the mini-batch gradient, printed sign)
+ *   U_r, V_r = the rank-r SVD of Gr by Algorithm 2
+ *   Z = U U^T Gr V V^T + (I - U U^T) Gr V V^T + U U^T Gr (I - V V^T)   (the Riemannian gradient)
+ *   W = U S V^T, the rank-r SVD of W - eta Z by Algorithm 2  (the SVD retraction)
+ * Each inner SVD ("Algorithm 2") is k_inner Golub-Kahan steps from q1_p without restart, the
+ * SVD of the projected bidiagonal matrix and the Ritz vectors; the P inner SVDs of a step
+ * run in one gk_psvd_batched launch (its statuses GK_NOT_CONVERGED are expected: no restart
+ * is taken), the gradient, the projection and the retraction in this library's kernels.
+ * All pointers are device memory owned by the caller; matrices are f64:
+ *   X       P x N x d1: sample i of problem p is x = X + (p N + i) d1
+ *   Vd      P x N x d2: its partner v = Vd + (p N + i) d2
+ *   y       P x N labels (any real weights)
+ *   batches steps x P x b sample indices in [0, N): step t's batch of problem p starts at
+ *           batches + (t P + p) b (may be NULL when steps is 0)
+ *   q1      P x d1 start vectors of the inner SVDs (nonzero)
+ *   W       P x d1 x d2, row-major per problem: W0 on entry, the iterate after `steps` steps on
+ *           return (the algorithm draws W0 ~ N(0, 1); the caller supplies it)
+ * Limits: P >= 1, N >= b >= 1, 2 <= d1, 2 <= d2 <= 4096, 1 <= r <= 16,
+ * r + 2 <= k_inner <= min(d1, d2, 510), steps >= 0.  opts: stream, reorth_passes of the
+ * inner solves, GK_FLAG_AUTOTUNE for them; seed, start, krylov_dim and predictor are not
+ * used.  info: matvecs and steps summed over the inner solves, cycles = RSGD steps done,
+ * seconds.  Returns GK_OK, GK_INVALID_ARG (limits, null pointers, host pointers),
+ * GK_OUT_OF_MEMORY, GK_CUDA_ERROR, GK_TIMEOUT or GK_NUMERICAL (from an inner solve; W then
+ * holds the last completed step). */
+typedef struct {
+  int32_t P, N, d1, d2; /* problems, samples per problem, W is d1 x d2 */
+  int32_t r;            /* rank of the manifold */
+  int32_t k_inner;      /* Golub-Kahan steps of each inner SVD */
+  int32_t steps, b;     /* iterations, mini-batch size */
+  double eta, lam;      /* training rate, the coefficient of the -lam W term */
+  const double *X, *Vd, *y;
+  const int32_t *batches;
+  const double *q1;
+  double *W;
+} gk_rsgd_args;
+int gk_rsgd_batched(const gk_rsgd_args *a, const gk_opts *opts, gk_info *info);
+
 /* ---- learned predictor of the rank and the Krylov dimension ----------- */
 /* The paper has no counterpart: a small network that maps cheap sketch
  * features of A to (log r, log K) so the batched solver can skip the separate

@@ -20,6 +20,7 @@ from .gk import (  # noqa: F401
     gk_psvd_batched,
     gk_psvd_workspace,
     gk_residuals,
+    gk_rsgd_batched,
     gk_sketch_batched,
     host_empty,
     host_free,

@@ -74,6 +74,15 @@ class gk_batch_item(C.Structure):
     ]
 
 
+class gk_rsgd_args(C.Structure):
+    _fields_ = [
+        ("P", C.c_int32), ("N", C.c_int32), ("d1", C.c_int32), ("d2", C.c_int32), ("r", C.c_int32),
+        ("k_inner", C.c_int32), ("steps", C.c_int32), ("b", C.c_int32), ("eta", C.c_double), ("lam", C.c_double),
+        ("X", C.c_void_p), ("Vd", C.c_void_p), ("y", C.c_void_p), ("batches", C.c_void_p), ("q1", C.c_void_p),
+        ("W", C.c_void_p),
+    ]
+
+
 class GKError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -124,6 +133,8 @@ def lib():
             L.gk_psvd_batched.restype = C.c_int
             L.gk_numrank_batched.argtypes = [P(gk_batch_item), C.c_int, P(gk_opts), P(gk_info)]
             L.gk_numrank_batched.restype = C.c_int
+            L.gk_rsgd_batched.argtypes = [P(gk_rsgd_args), P(gk_opts), P(gk_info)]
+            L.gk_rsgd_batched.restype = C.c_int
             L.gk_sketch_batched.argtypes = [P(gk_matrix), C.c_int, C.c_uint64, C.c_void_p, P(gk_opts)]
             L.gk_sketch_batched.restype = C.c_int
             L.gk_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, P(gk_opts)]
@@ -643,3 +654,30 @@ def gk_mlp_train(params, adam_m, adam_v, t0, x, y, batch=256, epochs=1, lr=1e-3,
     if st < 0:
         raise GKError(st, "gk_mlp_train")
     return losses
+
+
+def gk_rsgd_batched(X, Vd, y, W, batches, q1, eta: float, lam: float, r: int, k_inner: int, *,
+                    reorth_passes: int | None = None, autotune: bool = False, stream=None):
+    """Algorithm 4 for P problems of one shape (see gk_rsgd_batched in gk.h): X (P, N, d1),
+    Vd (P, N, d2), y (P, N), W (P, d1, d2; W0 in, the iterate out, updated in place),
+    batches (steps, P, b) int32, q1 (P, d1): contiguous CUDA tensors (f64 but batches).
+    Returns (status, info dict)."""
+    for t in (X, Vd, y, W, q1):
+        if t.dtype != torch.float64 or not t.is_contiguous() or t.device.type != "cuda":
+            raise ValueError("X, Vd, y, W, q1 must be contiguous float64 CUDA tensors")
+    if batches.dtype != torch.int32 or not batches.is_contiguous() or batches.device.type != "cuda":
+        raise ValueError("batches must be a contiguous int32 CUDA tensor")
+    P, N, d1 = X.shape
+    d2 = Vd.shape[2]
+    steps, _, b = batches.shape
+    a = gk_rsgd_args(P=P, N=N, d1=d1, d2=d2, r=int(r), k_inner=int(k_inner), steps=steps, b=b, eta=float(eta),
+                     lam=float(lam), X=X.data_ptr(), Vd=Vd.data_ptr(), y=y.data_ptr(), batches=batches.data_ptr(),
+                     q1=q1.data_ptr(), W=W.data_ptr())
+    o, ka = _opts(W.device, reorth_passes=reorth_passes, stream=stream)
+    if autotune:
+        o.flags |= GK_FLAG_AUTOTUNE
+    info = gk_info()
+    st = lib().gk_rsgd_batched(C.byref(a), C.byref(o), C.byref(info))
+    if st < 0:
+        raise GKError(st, "gk_rsgd_batched")
+    return st, info.as_dict()

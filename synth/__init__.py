@@ -143,7 +143,10 @@ def rsgd_data(P: int, N: int, d1: int, d2: int, r: int, steps: int, b: int, seed
     y = -np.sign(s)
     y[y == 0] = -1.0
     W0 = g.standard_normal((P, d1, d2))
-    batches = np.stack([np.stack([g.choice(N, size=b, replace=False) for _ in range(P)]) for _ in range(steps)])
+    batches = np.zeros((steps, P, b), dtype=np.int64)
+    for t in range(steps):
+        for p in range(P):
+            batches[t, p] = g.choice(N, size=b, replace=False)
     q1 = 2.0 + g.standard_normal((P, d1))
     return X, Vd, y, W0, batches.astype(np.int32), q1, Wstar
 

@@ -103,3 +103,25 @@ def test_operator_descriptors_from_tensors():
     assert (M.kind, M.dtype, M.m, M.n) == (raw.GK_CSR, raw.GK_F32, 2, 3)
     with pytest.raises(ValueError):
         raw.make_matrix(raw.CSR(2, 3, C.rowptr.long(), C.colind, C.vals, C.t_rowptr, C.t_colind, C.t_vals))
+
+
+def test_rsgd_entry_checks_arguments_before_the_device():
+    """gk_rsgd_batched refuses sizes outside its limits with GK_INVALID_ARG, and a valid request
+    without a device with GK_NO_DEVICE (no host fallback)."""
+    import ctypes as C
+
+    import torch
+    from paper_2104_10785_gb300 import gk as raw
+
+    def args(**kw):
+        base = dict(P=2, N=100, d1=30, d2=20, r=3, k_inner=12, steps=2, b=10, eta=0.5, lam=0.0, X=1, Vd=1, y=1,
+                    batches=1, q1=1, W=1)
+        base.update(kw)
+        return raw.gk_rsgd_args(**base)
+
+    L = raw.lib()
+    for bad in (dict(P=0), dict(b=0), dict(N=5), dict(r=0), dict(r=17), dict(k_inner=4), dict(k_inner=21),
+                dict(d2=5000), dict(d1=1), dict(steps=-1), dict(eta=float("nan"))):
+        assert L.gk_rsgd_batched(C.byref(args(**bad)), None, None) == raw.GK_INVALID_ARG, bad
+    if not torch.cuda.is_available():
+        assert L.gk_rsgd_batched(C.byref(args()), None, None) == raw.GK_NO_DEVICE
