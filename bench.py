@@ -465,6 +465,20 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         })
+    if args.workload == "rsgd_f64_64x784x256_rank5":
+        # the oracle's Algorithm 4 on a bounded sample of the same seeded data (no GPU work)
+        w = dict(synth.WORKLOADS[args.workload], name=args.workload)
+        X, Vd, y, W0, batches, q1, _ = synth.rsgd_data(w["P"], w["N"], w["d1"], w["d2"], w["r"], 3, w["b"],
+                                                       seed=w["seed"])
+        cpu = rsgd_oracle_sample(w, X, Vd, y, W0, batches, q1)
+        return dict(common, **{
+            "metric": "Algorithm 4 problem-steps/sec (two rank-5 inner SVDs per problem-step)", "value": cpu["value"],
+            "unit": "problem-steps/s", "steps": 1, "ms_per_step": 1e3 / cpu["value"],
+            "config": {"workload": args.workload, "problems": w["P"], "d1": w["d1"], "d2": w["d2"], "r": w["r"],
+                       "batch": w["b"], "k_inner": w["k_inner"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": "problem-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        })
     w = make_workload(args.workload, device, want_plain=False)
     K = w.get("K", 0)
     if w["name"] == "dense_bf16_100000x40000_top100":
@@ -519,6 +533,8 @@ def run_gk(args, rank, world):
         return run_batched_headline(args, rank, world, device)
     if args.workload == "dense_f32_50000x20000_rank200":
         return run_numrank_headline(args, rank, world, device)
+    if args.workload == "rsgd_f64_64x784x256_rank5":
+        return run_rsgd_headline(args, rank, world, device)
     w = make_workload(args.workload, device, want_plain=not args.no_plain)
     k, K, tol = w["k"], w["K"], w["tol"]
     A = w["A"]
@@ -922,6 +938,139 @@ def run_numrank_headline(args, rank, world, device):
         "roofline": roof, "clocks": clk, "gpu_launches": int(sum(i["launches"] for i in infos)),
         "e2e": e2e, "cpu_baseline": cpu,
     }
+
+
+def rsgd_flops(w, matvecs):
+    """FP64 flops of one Algorithm 4 call: the inner solves' products (2 per entry of a d1 x d2
+    matrix), the mini-batch gradients, the projection (GV, UG, U C) and the update and
+    retraction passes."""
+    P, d1, d2, r, b = w["P"], w["d1"], w["d2"], w["r"], w["b"]
+    per_step = P * (2 * b * d1 * d2 + 2 * 2 * d1 * d2 * r + 2 * d1 * r * r + 2 * d1 * d2 * 2 * r + 2 * d1 * d2 * r)
+    return 2.0 * d1 * d2 * matvecs, per_step
+
+
+def run_rsgd_headline(args, rank, world, device):
+    """Algorithm 4 for 64 problems at the paper's 784 x 256 shape: one step = one RSGD iteration of
+    every problem (two batched rank-5 inner SVDs); value = problem-steps per second."""
+    import numpy as np
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+    import synth
+
+    w = dict(synth.WORKLOADS[args.workload], name=args.workload)
+    P, N, d1, d2, r, b, kin = w["P"], w["N"], w["d1"], w["d2"], w["r"], w["b"], w["k_inner"]
+    total = args.warmup + args.steps
+    t0 = time.perf_counter()
+    X, Vd, y, W0, batches, q1, Ws = synth.rsgd_data(P, N, d1, d2, r, total, b, seed=w["seed"] + rank)
+    gen_s = time.perf_counter() - t0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    Xd, Vdd, yd, Wd, Bd, qd = dev(X), dev(Vd), dev(y), dev(W0), dev(batches), dev(q1)
+    stream = torch.cuda.current_stream(device)
+    for t in range(args.warmup):
+        gk.gk_rsgd_batched(Xd, Vdd, yd, Wd, Bd[t:t + 1], qd, w["eta"], w["lam"], r, kin)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device.index or 0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    launches0 = gk.launch_count()
+    for i in range(args.steps):
+        t = args.warmup + i
+        evs[i][0].record(stream)
+        st, info = gk.gk_rsgd_batched(Xd, Vdd, yd, Wd, Bd[t:t + 1], qd, w["eta"], w["lam"], r, kin)
+        evs[i][1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    launches = gk.launch_count() - launches0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(bb) for a, bb in evs)
+    ms = max_over_ranks(ms, device)
+    value = whole_job_rate(P * args.steps, world, ms / 1e3)
+    mv = sum(i["matvecs"] for i in infos)
+    f_inner, f_step = rsgd_flops(w, mv)
+    flops = f_inner + f_step * args.steps
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / F64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_batched<double> (inner SVDs) + k_rsgd_* (gradient, projection, retraction)",
+            "flops_per_step": flops / args.steps, "inner_matvecs_per_step": mv / args.steps,
+            "peak_source": "nominal FP64 rate of the GB300 (f64 FMA on CUDA cores); the 64 matrices (103 MB) "
+                           "stay in L2 across an inner solve's products"}
+    Wh = Wd.cpu().numpy()
+    agree = float(np.mean([np.mean(np.sign(np.sum((X[p] @ Wh[p]) * Vd[p], axis=1)) ==
+                                   np.sign(np.sum((X[p] @ Ws[p]) * Vd[p], axis=1))) for p in range(min(P, 8))]))
+    # end to end: every step's mini-batches (P x b pairs and labels) copied in from pinned host
+    # memory as a compact data set, the step, and the P iterates W copied back
+    e2e = None
+    if not args.no_e2e:
+        Xb = torch.empty((P, b, d1), dtype=torch.float64).pin_memory()
+        Vb = torch.empty((P, b, d2), dtype=torch.float64).pin_memory()
+        yb = torch.empty((P, b), dtype=torch.float64).pin_memory()
+        Wout = torch.empty((P, d1, d2), dtype=torch.float64).pin_memory()
+        t = total - 1
+        for p in range(P):
+            Xb[p] = torch.from_numpy(X[p][batches[t, p]])
+            Vb[p] = torch.from_numpy(Vd[p][batches[t, p]])
+            yb[p] = torch.from_numpy(y[p][batches[t, p]])
+        Xbd = torch.empty_like(Xb, device=device)
+        Vbd = torch.empty_like(Vb, device=device)
+        ybd = torch.empty_like(yb, device=device)
+        ident = torch.arange(b, dtype=torch.int32, device=device).repeat(P).view(1, P, b).contiguous()
+
+        def e2e_step():
+            Xbd.copy_(Xb, non_blocking=True)
+            Vbd.copy_(Vb, non_blocking=True)
+            ybd.copy_(yb, non_blocking=True)
+            gk.gk_rsgd_batched(Xbd, Vbd, ybd, Wd, ident, qd, w["eta"], w["lam"], r, kin)
+            Wout.copy_(Wd, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) / reps
+        e2e = {"value": world * P / (te / 1e3), "unit": "problem-steps/s", "ms_per_step": te,
+               "h2d_bytes_per_step": int((Xb.numel() + Vb.numel() + yb.numel()) * 8),
+               "d2h_bytes_per_step": int(Wout.numel() * 8)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = rsgd_oracle_sample(w, X, Vd, y, W0, batches, q1)
+    return {
+        "metric": "Algorithm 4 problem-steps/sec (two rank-5 inner SVDs per problem-step)",
+        "value": value, "unit": "problem-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "problems": P, "samples": N, "d1": d1, "d2": d2, "r": r, "batch": b,
+                   "eta": w["eta"], "lam": w["lam"], "k_inner": kin,
+                   "l2": "working set per step larger than L2 (batches 0.14 GB, W 0.10 GB, Gr and W - eta Z "
+                         "0.21 GB; data set 1.09 GB)"},
+        "status": 0, "sign_agreement_with_planted": agree, "gen_seconds": gen_s,
+        "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu,
+    }
+
+
+def rsgd_oracle_sample(w, X, Vd, y, W0, batches, q1, problems=32, steps=3):
+    """The oracle (oracle/rsgd.py) as it stands on a bounded sample of the workload: the first
+    `problems` problems for `steps` steps; returns the cpu_baseline entry in problem-steps/s."""
+    import oracle
+    from oracle import rsgd as ors
+
+    cores = cpu_threads()
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    for p in range(problems):
+        Wp = W0[p]
+        for t in range(steps):
+            Wp = ors.rsgd_step(X[p], Vd[p], y[p], batches[t, p], Wp, w["eta"], w["lam"], w["r"], w["k_inner"], q1[p])
+    dt = time.perf_counter() - t0
+    return {"value": problems * steps / dt, "unit": "problem-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{problems} of the {w['P']} problems for {steps} steps each ({problems * steps} problem-steps, "
+                      f"{dt:.1f} s)"}
 
 
 def oracle_batched_sample(mats, shapes, w, idx=tuple(range(0, 512, 2))):

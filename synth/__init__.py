@@ -139,7 +139,7 @@ def rsgd_data(P: int, N: int, d1: int, d2: int, r: int, steps: int, b: int, seed
     X = g.standard_normal((P, N, d1))
     Vd = g.standard_normal((P, N, d2))
     Wstar = np.stack([g.standard_normal((d1, r)) @ g.standard_normal((r, d2)) for _ in range(P)])
-    s = np.einsum("pni,pij,pnj->pn", X, Wstar, Vd)
+    s = np.stack([np.sum((X[p] @ Wstar[p]) * Vd[p], axis=1) for p in range(P)])  # x_i^T W* v_i
     y = -np.sign(s)
     y[y == 0] = -1.0
     W0 = g.standard_normal((P, d1, d2))
@@ -167,6 +167,10 @@ WORKLOADS = {
     # dense bf16 1e5 x 4e4, sigma_i = i^-1.5, top-100, tol 1e-8
     "dense_bf16_100000x40000_top100": dict(kind="spectrum_pow", m=100000, n=40000, e=1.5, k=100, K=200,
                                            tol=1e-8, dtype="bf16", seed=BASE_SEED + 4),
+    # Algorithm 4: 64 similarity-learning problems at the paper's 784 x 256 shape, rank 5, 2048 paired
+    # samples each (planted rank-5 similarity), mini-batch 256, eta 50, lam 0, inner Golub-Kahan steps 20
+    "rsgd_f64_64x784x256_rank5": dict(kind="rsgd", P=64, N=2048, d1=784, d2=256, r=5, b=256, eta=50.0, lam=0.0,
+                                      k_inner=20, dtype="f64", seed=BASE_SEED + 6),
 }
 
 
