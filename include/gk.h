@@ -67,6 +67,15 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               the same passes and rules (Algorithm 1 reorthogonalization), on the
                               FP32 pipes, with the workspace holding the copies (8 bytes per basis
                               entry) */
+#define GK_FLAG_PERSISTENT 32 /* gk_psvd: solve a small dense device operator (at most 4096 columns and
+                              24 MB, device outputs, no caller workspace, no fixed keep count, none of
+                              the FUSED/REFINE/predictor options) in one persistent launch of the
+                              batched solver (gk_psvd_batched's method on one problem, one cluster of
+                              16 CTAs) instead of the multi-kernel sweep: the same algorithm in 2
+                              launches instead of ~225 (f64 2000 x 1000, top 10).  Opt-in: measured
+                              6.7 ms against 6.0 ms for the multi-kernel sweep, both bound by f64
+                              arithmetic latency rather than launches.  gk_info then reports its
+                              counters; reserved = 0. */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).

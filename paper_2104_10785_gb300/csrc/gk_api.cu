@@ -542,6 +542,68 @@ int refine_check(const Op &op, int64_t m, int64_t n, int k, const double *Uo, co
   return GK_OK;
 }
 
+// With GK_FLAG_PERSISTENT a small dense device operator goes to the batched solver as a single
+// problem: one persistent launch (one cluster) runs the whole thick-restart solve.
+constexpr size_t kPersistentBytes = 24u << 20;
+
+bool persistent_ok(const gk_matrix *A, const PsvdPlan &p, const gk_opts &o, const gk_opts *oin, const OpStage &st,
+                   bool host_out, bool host_start) {
+  if (A->kind != GK_DENSE || st.host || host_out || host_start) return false;
+  if (!(o.flags & GK_FLAG_PERSISTENT) || (o.flags & (GK_FLAG_FUSED | GK_FLAG_REFINE))) return false;
+  if (o.workspace || o.predictor || (oin && oin->keep > 0)) return false;
+  if (A->n > 4096 || A->ld < A->n || p.K > 500 || A->m > INT32_MAX) return false;
+  return st.vals_bytes <= kPersistentBytes;
+}
+
+int psvd_persistent_call(const gk_matrix *A, int k, double tol, const PsvdPlan &p, const gk_opts &o, double *U,
+                         double *S, double *V, gk_info *info, std::chrono::steady_clock::time_point t0, int64_t l0) {
+  gk_batch_item it;
+  memset(&it, 0, sizeof(it));
+  it.A = *A;
+  it.k = k;
+  it.krylov_dim = p.K;
+  it.tol = tol;
+  it.U = U;
+  it.S = S;
+  it.V = V;
+  it.start = o.start;
+  gk_opts ob = o;
+  ob.flags = o.flags & GK_FLAG_PROFILE;
+  gk_info bi;
+  memset(&bi, 0, sizeof(bi));
+  int rc = psvd_persistent(&it, &ob, &bi);
+  if (rc < 0) return rc;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  // the multi-kernel path's conventions: the sign of each v, and a zero s_k reported
+  GK_CUDA(sign_normalize(U, A->m, A->m, V, A->n, A->n, k, s));
+  double sk = 0.0;
+  GK_CUDA(cudaMemcpyAsync(&sk, S + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaStreamSynchronize(s));
+  int status = it.status;
+  if (status == GK_OK && sk == 0.0) status = GK_RANK_DEFICIENT;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  inf.steps = it.steps;
+  inf.restarts = it.restarts;
+  inf.cycles = it.cycles;
+  inf.breakdowns = it.breakdowns;
+  inf.matvecs = it.matvecs;
+  inf.resid_est_max = it.resid_est_max;
+  inf.sigma_est = it.sigma_est;
+  inf.svd_sweeps = bi.svd_sweeps;
+  inf.ms_matvec = bi.ms_matvec;
+  inf.ms_matvec_t = bi.ms_matvec_t;
+  inf.ms_orth = bi.ms_orth;
+  inf.ms_small = bi.ms_small;
+  inf.ms_restart = bi.ms_restart;
+  inf.kprime = p.K;
+  inf.reserved = 0;
+  inf.seconds = seconds_since(t0);
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  return status;
+}
+
 int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, double *U, double *S, double *V,
               gk_info *info) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -582,6 +644,8 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   if (rc) return rc;
   const bool host_out = on_host(U) || on_host(S) || on_host(V);
   const bool host_start = o.start && on_host(o.start);
+  if (persistent_ok(Ain, p, o, oin, st, host_out, host_start))
+    return psvd_persistent_call(Ain, k, tol, p, o, U, S, V, info, t0, l0);
   Op op = make_op(Ain);
   p.fused = (o.flags & GK_FLAG_FUSED) && fused_ok_staged(op, st, d);
   PsvdBufs b;

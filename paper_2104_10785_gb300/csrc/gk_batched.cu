@@ -1554,7 +1554,7 @@ int max_clusters(BatchedKernel kern, int cs, cudaStream_t s) {
   return n;
 }
 
-int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, gk_info *info) {
+int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, gk_info *info, int cs_force = 0) {
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = launch_count();
   if (info) memset(info, 0, sizeof(*info));
@@ -1657,14 +1657,23 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
-  // cluster size: the autotuned choice for this batch signature, else 8
+  // cluster size: the caller's (a single solve takes the largest cluster that fits), the
+  // autotuned choice for this batch signature, else 8
   const TuneKey key{count, mode, dtype0, work};
   int cs = 8;
   bool tune = (o.flags & GK_FLAG_AUTOTUNE) != 0;
+  if (cs_force > 0) {
+    for (int c = cs_force; c >= 2; c /= 2)
+      if (max_clusters(kern, c, s) > 0) {
+        cs = c;
+        break;
+      }
+    tune = false;
+  }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto itk = g_tuned.find(key);
-    if (itk != g_tuned.end()) {
+    if (cs_force <= 0 && itk != g_tuned.end()) {
       cs = itk->second;
       tune = false;
     }
@@ -1801,6 +1810,11 @@ int batched_impl(gk_batch_item *items, int count, int mode, const gk_opts *oin, 
 }
 
 }  // namespace
+
+int psvd_persistent(gk_batch_item *item, const gk_opts *opts, gk_info *info) {
+  return batched_impl(item, 1, 0, opts, info, 16);
+}
+
 }  // namespace gk
 
 extern "C" int gk_wait_selftest(long long cycles) {

@@ -187,6 +187,9 @@ cudaError_t orth_append(double *w, int64_t len, const double *Q, int64_t ld, int
                         double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
                         double *qcol, float *x32, cudaStream_t s, const Dev &d, const float2 *Qs, float2 *ws2,
                         float2 *qscol);
+// one partial SVD of a small dense device operator in one persistent launch of the batched
+// solver (gk_batched.cu; the largest cluster that fits), for gk_psvd
+int psvd_persistent(gk_batch_item *item, const gk_opts *opts, gk_info *info);
 // doubles of `part` the cooperative orthonormalization needs for Krylov dimension K
 int64_t coop_partials(int K, const Dev &d);
 // Qs[c * ld + i] = (hi, lo) of Q[c * ld + i] for the first `cols` columns (the shadow of a basis)

@@ -878,6 +878,137 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_cgs_small(const double *__
   if (threadIdx.x == 0) judge(ctl, tot, a);
 }
 
+// k_cgs_small on the basis's double-f32 copy: the same passes, rule, norm and judgement, with
+// w (f64 and split into row pairs) in shared memory and the basis products in packed
+// double-f32 arithmetic on the FP32 pipes (one SM's FP64 units would take ~15 us per pass of
+// a 2000 x 30 basis; these take ~2).  h is kept as (hi, lo) f32 pairs; w's update and the
+// norms are f64.
+constexpr int kSmallDfThreads = 512;
+
+__global__ void __launch_bounds__(kSmallDfThreads, 1) k_cgs_small_df(const float2 *__restrict__ Qs, int64_t ld,
+                                                                int64_t len, int j, double *__restrict__ w, Ctl *ctl,
+                                                                NormArgs a, int passes) {
+  if (halted(ctl)) return;
+  extern __shared__ double dyn[];
+  const int lenr = (int)((len + 1) / 2 * 2), pairs = lenr / 2;
+  double *ws = dyn;                                      // lenr
+  float4 *wsp = reinterpret_cast<float4 *>(ws + lenr);   // pairs: (hi, lo, hi, lo) of rows 2r, 2r + 1
+  float2 *hs = reinterpret_cast<float2 *>(wsp + pairs);  // j
+  __shared__ double red[kSmallDfThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < lenr; i += blockDim.x) ws[i] = i < len ? w[i] : 0.0;
+  __syncthreads();
+  auto split = [&]() {
+    for (int r = threadIdx.x; r < pairs; r += blockDim.x) {
+      const double a0 = ws[2 * r], a1 = ws[2 * r + 1];
+      const float h0 = (float)a0, h1 = (float)a1;
+      wsp[r] = make_float4(h0, (float)(a0 - (double)h0), h1, (float)(a1 - (double)h1));
+    }
+    __syncthreads();
+  };
+  auto norm2 = [&]() -> double {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < lenr; i += blockDim.x) v = fma(ws[i], ws[i], v);
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += red[k];
+    __syncthreads();  // red is reused by the next call
+    return t;
+  };
+  auto pass = [&]() {  // h = Q^T w (warp per column); w -= Q h (thread per row pair)
+    for (int c = warp; c < j; c += nw) {
+      const float4 *q4 = reinterpret_cast<const float4 *>(Qs + (int64_t)c * ld);
+      float2 sh = f2(0.f, 0.f), sl = f2(0.f, 0.f);
+      for (int r = lane; r < pairs; r += 32 * 8) {
+        float4 qv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) qv[u] = r + 32 * u < pairs ? ldg4(q4 + r + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 ph[8], pl[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          ph[u] = f2(0.f, 0.f);
+          pl[u] = f2(0.f, 0.f);
+          if (r + 32 * u < pairs) {
+            const float4 wv = wsp[r + 32 * u];
+            const float2 qh = f2(qv[u].x, qv[u].z), ql = f2(qv[u].y, qv[u].w);
+            df2_mac(ph[u], pl[u], qh, f2(-qh.x, -qh.y), ql, f2(wv.x, wv.z), f2(wv.y, wv.w));
+          }
+        }
+#pragma unroll
+        for (int w2 = 1; w2 < 8; w2 *= 2)
+#pragma unroll
+          for (int u = 0; u + w2 < 8; u += 2 * w2) df2_add(ph[u], pl[u], ph[u + w2], pl[u + w2]);
+        df2_add(sh, sl, ph[0], pl[0]);
+      }
+      float h = sh.x, l = sl.x;
+      df_acc(h, l, sh.y, sl.y);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        df_acc(h, l, oh, ol);
+      }
+      if (lane == 0) {
+        const float t = __fadd_rn(h, l);  // normalized pair: t + (l - (t - h)) == h + l
+        hs[c] = f2(t, __fsub_rn(l, __fsub_rn(t, h)));
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < pairs; r += blockDim.x) {
+      const float4 *q4 = reinterpret_cast<const float4 *>(Qs) + r;
+      const int64_t ld2 = ld / 2;
+      float2 sh = f2(0.f, 0.f), sl = f2(0.f, 0.f);
+      int c = 0;
+      for (; c + 8 <= j; c += 8) {
+        float4 qv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) qv[u] = ldg4(q4 + (int64_t)(c + u) * ld2);
+        float2 ph[8], pl[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 hc = hs[c + u];
+          const float2 qh = f2(qv[u].x, qv[u].z), ql = f2(qv[u].y, qv[u].w);
+          ph[u] = f2(0.f, 0.f);
+          pl[u] = f2(0.f, 0.f);
+          df2_mac(ph[u], pl[u], qh, f2(-qh.x, -qh.y), ql, f2(hc.x, hc.x), f2(hc.y, hc.y));
+        }
+#pragma unroll
+        for (int w2 = 1; w2 < 8; w2 *= 2)
+#pragma unroll
+          for (int u = 0; u + w2 < 8; u += 2 * w2) df2_add(ph[u], pl[u], ph[u + w2], pl[u + w2]);
+        df2_add(sh, sl, ph[0], pl[0]);
+      }
+      for (; c < j; ++c) {
+        const float4 qv = ldg4(q4 + (int64_t)c * ld2);
+        const float2 hc = hs[c];
+        const float2 qh = f2(qv.x, qv.z), ql = f2(qv.y, qv.w);
+        df2_mac(sh, sl, qh, f2(-qh.x, -qh.y), ql, f2(hc.x, hc.x), f2(hc.y, hc.y));
+      }
+      ws[2 * r] = (ws[2 * r] - (double)sh.x) - (double)sl.x;
+      if (2 * r + 1 < len) ws[2 * r + 1] = (ws[2 * r + 1] - (double)sh.y) - (double)sl.y;
+    }
+    __syncthreads();
+    split();
+  };
+  split();
+  double tot;
+  if (j > 0 && passes >= 0) {
+    const double before = passes == 0 ? norm2() : 0.0;
+    const int np = passes == 0 ? 1 : passes;
+    for (int p = 0; p < np; ++p) pass();
+    tot = norm2();
+    if (passes == 0 && tot < 0.5 * before) {  // the first pass cancelled: a second one decides
+      pass();
+      tot = norm2();
+    }
+  } else {
+    tot = norm2();
+  }
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) w[i] = ws[i];
+  if (threadIdx.x == 0) judge(ctl, tot, a);
+}
+
 __global__ void k_normalize_append(const double *__restrict__ w, int64_t len, double *__restrict__ q,
                                    float *__restrict__ x32, float2 *__restrict__ qs, const Ctl *ctl) {
   if (halted(ctl)) return;
@@ -993,6 +1124,21 @@ int cgs_blocks(int64_t len, const Dev &d) {
 cudaError_t orthonormalize(double *w, int64_t len, const double *Q, int64_t ld, int j, int passes, double *part,
                            double *h, Ctl *ctl, int mode, int step, int side, double *coef_out, const double *prev,
                            cudaStream_t s, const Dev &d, const float2 *Qs, float2 *ws2) {
+  if (len <= kSmallLen && len * (int64_t)(j > 0 ? j : 1) <= kSmallWork && Qs != nullptr && j > 0) {
+    // the double-f32 copy: w (f64 and split) and h in shared memory, <= 128 KB + 8 j bytes
+    const int64_t lenr = (len + 1) / 2 * 2;
+    const size_t dyn = sizeof(double) * (size_t)lenr * 2 + sizeof(float2) * (size_t)j;
+    static int attr_set = 0;
+    if (!attr_set) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_cgs_small_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+      attr_set = 1;
+    }
+    GK_LAUNCH(k_cgs_small_df<<<1, kSmallDfThreads, dyn, s>>>(Qs, ld, len, j, w, ctl,
+                                                             NormArgs{mode, step, side, coef_out, prev}, passes));
+    return cudaGetLastError();
+  }
   if (len <= kSmallLen && len * (int64_t)(j > 0 ? j : 1) <= kSmallWork) {
     const size_t dyn = sizeof(double) * (size_t)(len + (j > 0 ? j : 1));  // <= (8192 + 1025) doubles
     if (dyn > 48 * 1024) {

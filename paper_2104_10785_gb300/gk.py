@@ -27,6 +27,7 @@ GK_FLAG_AUTOTUNE = 2
 GK_FLAG_FUSED = 4
 GK_FLAG_REFINE = 8
 GK_FLAG_ORTH_F64 = 16
+GK_FLAG_PERSISTENT = 32
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -312,10 +313,11 @@ def default_opts() -> gk_opts:
 
 
 def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, eps_absolute=False, seed=None,
-          start=None, stream=None, workspace=None, profile=False, fused=False, refine=False, orth_f64=False):
+          start=None, stream=None, workspace=None, profile=False, fused=False, refine=False, orth_f64=False,
+          persistent=False):
     o = default_opts()
     o.flags = ((GK_FLAG_PROFILE if profile else 0) | (GK_FLAG_FUSED if fused else 0) | (GK_FLAG_REFINE if refine else 0)
-               | (GK_FLAG_ORTH_F64 if orth_f64 else 0))
+               | (GK_FLAG_ORTH_F64 if orth_f64 else 0) | (GK_FLAG_PERSISTENT if persistent else 0))
     o.krylov_dim = int(krylov_dim)
     o.keep = int(keep)
     if max_restarts is not None:
@@ -342,7 +344,8 @@ def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, e
 def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0, max_restarts: int | None = None,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
             scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
-            refine: bool = False, predictor: "Predictor | None" = None, orth_f64: bool = False):
+            refine: bool = False, predictor: "Predictor | None" = None, orth_f64: bool = False,
+            persistent: bool = False):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
@@ -366,7 +369,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     else:
         U, S, V = out
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
-                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine, orth_f64)
+                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine, orth_f64, persistent)
     if predictor is not None:
         o.predictor = predictor.handle
     info = gk_info()
