@@ -93,10 +93,20 @@ def omega(seed: int, n: int):
     return (start_vector(seed, n * S) - 2.0).reshape(n, S)
 
 
-def sketch_features(A, seed: int):
+def round_bf16(x):
+    """x rounded to bf16 (round to nearest, ties to even), returned as f64."""
+    u = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def sketch_features(A, seed: int, omega_bf16: bool = False):
+    """The 35 features of A's sketch Y = A Omega.  omega_bf16: Omega rounded to bf16 first (the
+    library's definition for bf16-stored operators, whose product runs on the tensor pipe)."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
-    Y = A @ omega(seed, n)
+    Om = omega(seed, n)
+    Y = A @ (round_bf16(Om) if omega_bf16 else Om)
     s = np.linalg.svd(Y, compute_uv=False)
     s = np.concatenate([s, np.zeros(S - len(s))]) if len(s) < S else s
     nf = math.sqrt(float(np.sum(A * A)))

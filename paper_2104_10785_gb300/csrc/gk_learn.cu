@@ -205,6 +205,151 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_gram(const SkProb *__rest
   }
 }
 
+// ---- bf16 operators: Y = A Omega on the tensor pipe ------------------------------------
+// Omega is rounded to bf16 (round to nearest even) and stored transposed, omT[c][k] (32 x nk, nk
+// a multiple of 64, zero past n).  A block takes a 128-row chunk: each of 8 warps owns 16 rows
+// and accumulates its 16 x 32 slice of Y in f32 with mma.sync m16n8k16 (bf16 fragments from
+// shared memory by ldmatrix), streaming 64-column tiles of A and omT through registers; then
+// the chunk's Gram partial and ||A_c||_F^2 exactly as k_sketch_gram does.
+constexpr int kMmK = 64, kMmPitch = kMmK + 8;  // bf16 elements per tile row; padded pitch (144 B)
+
+__global__ void k_omega_t_bf16(const float *__restrict__ om, int64_t n, int64_t nk, __nv_bfloat16 *__restrict__ omT) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nk * kS; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / nk, k = t % nk;
+    omT[t] = __float2bfloat16_rn(k < n ? om[k * kS + c] : 0.f);
+  }
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__global__ void __launch_bounds__(kSkThreads) k_sketch_mma(const SkProb *__restrict__ probs,
+                                                          const SkItem *__restrict__ items, int nitems,
+                                                          const __nv_bfloat16 *__restrict__ omT, int64_t nk,
+                                                          double *__restrict__ gpart, double *__restrict__ fpart) {
+  __shared__ __align__(16) __nv_bfloat16 sA[kChunk * kMmPitch];
+  __shared__ __align__(16) __nv_bfloat16 sO[kS * kMmPitch];
+  __shared__ float sY[kChunk * (kS + 1)];
+  __shared__ double sred[kSkThreads / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t4 = lane & 3;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const SkItem I = items[it];
+    const SkProb P = probs[I.p];
+    const __nv_bfloat16 *A = (const __nv_bfloat16 *)P.A;
+    const int64_t m = P.m, n = P.n, ld = P.ld, r0 = I.r0;
+    float acc[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+    double fro = 0.0;
+    uint4 av[4], ov;
+    // this thread's 4 16-byte vectors of the A tile (vector v = tid + 256 q: row v / 8, columns
+    // 8 (v % 8)..), zero outside A; one vector of omT (row tid / 8, columns 8 (tid % 8)..)
+    auto load = [&](int64_t k0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int v = tid + kSkThreads * q, row = v >> 3, c8 = (v & 7) * 8;
+        const int64_t gr = r0 + row, gc = k0 + c8;
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < m && gc < n) {
+          const __nv_bfloat16 *src = A + gr * ld + gc;
+          if (gc + 8 <= n) {
+            x = *reinterpret_cast<const uint4 *>(src);
+          } else {
+            unsigned short e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i = 0; i < 8 && gc + i < n; ++i) e[i] = __bfloat16_as_ushort(src[i]);
+            x = make_uint4(e[0] | ((unsigned)e[1] << 16), e[2] | ((unsigned)e[3] << 16), e[4] | ((unsigned)e[5] << 16),
+                           e[6] | ((unsigned)e[7] << 16));
+          }
+        }
+        av[q] = x;
+      }
+      ov = *reinterpret_cast<const uint4 *>(omT + (int64_t)(tid >> 3) * nk + k0 + (tid & 7) * 8);
+    };
+    load(0);
+    for (int64_t k0 = 0; k0 < n; k0 += kMmK) {
+      __syncthreads();  // the previous tile (or item) is consumed
+      float fs = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int v = tid + kSkThreads * q, row = v >> 3, c8 = (v & 7) * 8;
+        *reinterpret_cast<uint4 *>(sA + row * kMmPitch + c8) = av[q];
+        const unsigned w4[4] = {av[q].x, av[q].y, av[q].z, av[q].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float lo = __uint_as_float(w4[i] << 16), hi = __uint_as_float(w4[i] & 0xffff0000u);
+          fs = fmaf(lo, lo, fs);
+          fs = fmaf(hi, hi, fs);
+        }
+      }
+      *reinterpret_cast<uint4 *>(sO + (tid >> 3) * kMmPitch + (tid & 7) * 8) = ov;
+      fro += (double)fs;
+      __syncthreads();
+      if (k0 + kMmK < n) load(k0 + kMmK);  // next tile in flight during the products
+#pragma unroll
+      for (int kk = 0; kk < kMmK / 16; ++kk) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_addr(sA + (warp * 16 + (lane & 15)) * kMmPitch + kk * 16 + (lane >> 4) * 8), a0, a1, a2, a3);
+#pragma unroll
+        for (int nt = 0; nt < kS / 8; ++nt) {
+          uint32_t b0, b1;
+          ldsm_x2(smem_addr(sO + (nt * 8 + (lane & 7)) * kMmPitch + kk * 16 + ((lane >> 3) & 1) * 8), b0, b1);
+          mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        }
+      }
+    }
+    __syncthreads();
+    const float scale = (float)P.scale;
+#pragma unroll
+    for (int nt = 0; nt < kS / 8; ++nt) {
+      const int r = warp * 16 + g, c = nt * 8 + 2 * t4;
+      sY[r * (kS + 1) + c] = acc[nt][0] * scale;
+      sY[r * (kS + 1) + c + 1] = acc[nt][1] * scale;
+      sY[(r + 8) * (kS + 1) + c] = acc[nt][2] * scale;
+      sY[(r + 8) * (kS + 1) + c + 1] = acc[nt][3] * scale;
+    }
+    fro *= P.scale * P.scale;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    if (lane == 0) sred[warp] = fro;
+    __syncthreads();
+    const int rows = (int)((m - r0) < kChunk ? (m - r0) : kChunk);
+    for (int e = tid; e < kTri; e += kSkThreads) {
+      int a = 0, rem = e;
+      while (rem >= kS - a) {
+        rem -= kS - a;
+        ++a;
+      }
+      const int b = a + rem;
+      double gg = 0.0;
+      for (int r = 0; r < rows; ++r) gg = fma((double)sY[r * (kS + 1) + a], (double)sY[r * (kS + 1) + b], gg);
+      gpart[(int64_t)it * kTri + e] = gg;
+    }
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kSkThreads / 32; ++w) t += sred[w];
+      fpart[it] = t;
+    }
+  }
+}
+
 // tournament (circle method) pairing of 32 indices: round r, slot s
 __device__ __forceinline__ int pair_player(int r, int s) { return s == 0 ? 0 : ((s - 1 + r) % (kS - 1)) + 1; }
 
@@ -555,12 +700,17 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
   }
   first[count] = (int)items.size();
   const int nitems = (int)items.size();
+  bool mma_ok = dtype0 == GK_BF16;
+  for (int i = 0; i < count && mma_ok; ++i)
+    mma_ok = (uintptr_t)A[i].vals % 16 == 0 && (A[i].ld * 2) % 16 == 0;
+  const int64_t nk = (nmax + kMmK - 1) / kMmK * kMmK;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t b_om = up(sizeof(float) * (size_t)nmax * kS), b_pr = up(sizeof(SkProb) * count),
                b_it = up(sizeof(SkItem) * nitems), b_first = up(sizeof(int) * (count + 1)),
-               b_g = up(sizeof(double) * (size_t)nitems * kTri), b_f = up(sizeof(double) * nitems);
+               b_g = up(sizeof(double) * (size_t)nitems * kTri), b_f = up(sizeof(double) * nitems),
+               b_ot = mma_ok ? up(sizeof(__nv_bfloat16) * (size_t)nk * kS) : 0;
   char *base = nullptr;
-  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f, s) != cudaSuccess) {
+  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f + b_ot, s) != cudaSuccess) {
     cudaGetLastError();
     return GK_OUT_OF_MEMORY;
   }
@@ -570,6 +720,7 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
   int *dfirst = (int *)(base + b_om + b_pr + b_it);
   double *gpart = (double *)(base + b_om + b_pr + b_it + b_first);
   double *fpart = (double *)(base + b_om + b_pr + b_it + b_first + b_g);
+  __nv_bfloat16 *omT = (__nv_bfloat16 *)(base + b_om + b_pr + b_it + b_first + b_g + b_f);
   int rc = GK_OK;
   do {
     if ((rc = check(cudaMemcpyAsync(dpr, pr.data(), sizeof(SkProb) * count, cudaMemcpyHostToDevice, s)))) break;
@@ -577,7 +728,10 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
     if ((rc = check(cudaMemcpyAsync(dfirst, first.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s))))
       break;
     GK_LAUNCH(k_omega<<<(int)std::min<int64_t>(4096, (nmax * kS + 255) / 256), 256, 0, s>>>(om, nmax, seed));
-    switch (dtype0) {
+    if (mma_ok) {  // bf16 rows on 16-byte boundaries: the tensor pipe, Omega rounded to bf16
+      GK_LAUNCH(k_omega_t_bf16<<<(int)std::min<int64_t>(4096, (nk * kS + 255) / 256), 256, 0, s>>>(om, nmax, nk, omT));
+      GK_LAUNCH(k_sketch_mma<<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, omT, nk, gpart, fpart));
+    } else switch (dtype0) {
       case GK_F64: GK_LAUNCH(k_sketch_gram<double><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
       case GK_F32: GK_LAUNCH(k_sketch_gram<float><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
       case GK_BF16:

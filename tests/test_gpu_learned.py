@@ -30,6 +30,31 @@ def _params(seed=0, scale=0.1):
     return p.astype(np.float32)
 
 
+def test_sketch_features_bf16_tensor_path_match_oracle():
+    """bf16 operators take the tensor-pipe sketch (mma.sync bf16 fragments, f32 accumulation) with
+    Omega rounded to bf16; the oracle forms the same features in f64 from the same rounded Omega.
+    Shapes: ragged row chunks, widths not multiples of 8 or 64 (rows padded to 16-byte strides),
+    one wider than a tile row of 64 many times.  Bound as the f32 path's: the f32 sums perturb Y by
+    a few 1e-6 of sigma_1."""
+    mats, As = [], []
+    g = synth.rng(45)
+    for i, (m, n) in enumerate([(1000, 300), (129, 61), (700, 8), (300, 1025), (4000, 200)]):
+        r = int(g.integers(2, 30))
+        A32 = synth.gaussian_product(m, n, r, 1e-3, seed=100 + i, dtype=np.float32)
+        bits = synth.to_bf16_bits(A32)
+        ldp = (n + 7) // 8 * 8
+        T = torch.zeros((m, ldp), dtype=torch.int16)
+        T[:, :n] = torch.from_numpy(bits.view(np.int16))
+        mats.append(T.cuda().view(torch.bfloat16)[:, :n])
+        As.append(synth.bf16_bits_to_f32(bits).astype(np.float64))
+    f = gk().gk_sketch_batched(mats, seed=92).cpu().numpy()
+    for i, A in enumerate(As):
+        fo = mlp.sketch_features(A, 92, omega_bf16=True)
+        sg, so = np.exp(f[i, :32].astype(np.float64)), np.exp(fo[:32])
+        assert np.all(np.abs(sg - so) <= 2e-5 * so[0] + 1e-5 * so), (i, np.abs(sg - so).max() / so[0])
+        np.testing.assert_allclose(f[i, 32:], fo[32:], rtol=1e-6, atol=1e-6)
+
+
 def test_sketch_features_match_oracle():
     mats, As = [], []
     g = synth.rng(44)

@@ -100,3 +100,17 @@ def test_adam_hand_worked_step():
     np.testing.assert_allclose(m, [0.14], rtol=1e-15)
     np.testing.assert_allclose(v, [0.01024], rtol=1e-15)
     np.testing.assert_allclose(p, [1.0 - 0.0325559858872132], rtol=1e-14)
+
+
+def test_round_bf16_matches_torch_conversion():
+    """The oracle's bf16 rounding (used for the sketch's Omega of bf16 operators) against torch's
+    round-to-nearest-even conversion, including ties and values near the f32 limits."""
+    import torch
+
+    from oracle import mlp
+
+    g = np.random.default_rng(8)
+    x = np.concatenate([g.standard_normal(20000).astype(np.float32),
+                        np.array([1 + 2**-8, 1 + 3 * 2**-8, -1 - 2**-8, 3e38, -3e38, 1e-38, 0.0], dtype=np.float32)])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.round_bf16(x), ref)
