@@ -1206,14 +1206,15 @@ def profile_case(args):
     (--fused: with the fused sweep).
     --case batched: the first --count problems of the 512-problem batched recipe; `reps` rounds
     of the learned pipeline's sketch and its batched partial SVD with the committed network's
-    (rank, K); prints the operator bytes the last solve streamed."""
+    (rank, K); prints the operator bytes the last solve streamed.
+    --case sketch: `reps` calls of gk_sketch_batched on the same kind of operator (one problem)."""
     import torch
 
     import paper_2104_10785_gb300 as gk
     import synth
 
     torch.cuda.set_device(0)
-    if args.case in ("products", "psvd"):
+    if args.case in ("products", "psvd", "sketch"):
         dt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32, "f64": torch.float64}[args.dtype]
         g = torch.Generator(device="cuda").manual_seed(1)
         A = torch.randn(args.m, args.n, generator=g, device="cuda", dtype=torch.float32).to(dt)
@@ -1223,6 +1224,8 @@ def profile_case(args):
             if args.case == "products":
                 gk.gk_matvec(A, x)
                 gk.gk_matvec(A, y, trans=True)
+            elif args.case == "sketch":
+                gk.gk_sketch_batched([A], seed=1)
             else:
                 gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0, fused=args.fused)
     elif args.case == "batched":
@@ -1259,7 +1262,7 @@ def main():
                     help="time the default workload at its fixed Krylov dimension instead of the learned one")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this kernel")
-    ap.add_argument("--case", default=None, choices=["products", "psvd", "batched"],
+    ap.add_argument("--case", default=None, choices=["products", "psvd", "batched", "sketch"],
                     help="run one kernel family on seeded inputs for an ncu capture, then exit")
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "f32", "f64"])
     ap.add_argument("--m", type=int, default=40000)
