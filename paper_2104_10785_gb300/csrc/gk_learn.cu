@@ -1,10 +1,11 @@
 // gk_learn.cu -- the learned predictor of the rank and the Krylov dimension.
 //
-// Sketch (per problem, one block): Y = A Omega with Omega (n x 32) drawn N(0,1)
-// from Philox4x32-10 + Box-Muller (entry (j, c) is draw number 32 j + c of the
-// stream seeded with the sketch seed), accumulated in f32 tiles; the 32 x 32
-// Gram matrix G = Y^T Y and ||A||_F^2 are accumulated in f64; the singular
-// values of Y are the square roots of G's eigenvalues (cyclic Jacobi, f64).
+// Sketch (per problem, one block per 128-row chunk): Y = A Omega with Omega (n x 32) drawn
+// N(0,1) from Philox4x32-10 + Box-Muller (entry (j, c) is draw number 32 j + c of the
+// stream seeded with the sketch seed), accumulated in f32 tiles (for bf16 operators on the
+// tensor pipe, with Omega rounded to bf16); each chunk's part of the 32 x 32 Gram matrix
+// G = Y^T Y and of ||A||_F^2 in f64, the chunks summed in order (one thread per entry); the
+// singular values of Y are the square roots of G's eigenvalues (cyclic Jacobi, f64).
 // Features (35): log(sigma_i(Y) / (sqrt(32) ||A||_F)) for i = 1..32,
 // log ||A||_F, log m, log n.
 //
@@ -350,21 +351,40 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch_mma(const SkProb *__restr
   }
 }
 
+// the chunk partials of problem p summed in chunk order: gsum[p * (kTri + 1) + e] for the 528
+// Gram entries and e = kTri for ||A||_F^2 (one thread per entry, each in ascending chunk order)
+__global__ void __launch_bounds__(128) k_sketch_sum(const int *__restrict__ first, int count,
+                                                    const double *__restrict__ gpart,
+                                                    const double *__restrict__ fpart, double *__restrict__ gsum) {
+  const int p = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count || e > kTri) return;
+  const int c0 = first[p], c1 = first[p + 1];
+  double g = 0.0;
+  if (e < kTri) {
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) g += gpart[(int64_t)c * kTri + e];
+  } else {
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) g += fpart[c];
+  }
+  gsum[(int64_t)p * (kTri + 1) + e] = g;
+}
+
 // tournament (circle method) pairing of 32 indices: round r, slot s
 __device__ __forceinline__ int pair_player(int r, int s) { return s == 0 ? 0 : ((s - 1 + r) % (kS - 1)) + 1; }
 
 // ---- sketch, stage 2: per problem, sum the chunk partials in chunk order,
 // eigenvalues of G by parallel cyclic Jacobi (one warp), the 35 features --------
-__global__ void __launch_bounds__(32) k_sketch_eig(const SkProb *__restrict__ probs, const int *__restrict__ first,
-                                                  int count, const double *__restrict__ gpart,
-                                                  const double *__restrict__ fpart, float *__restrict__ feats) {
+__global__ void __launch_bounds__(32) k_sketch_eig(const SkProb *__restrict__ probs, int count,
+                                                  const double *__restrict__ gsum, float *__restrict__ feats) {
   __shared__ double sG[kS * kS];
   __shared__ double2 sRot[kS / 2];
   __shared__ int2 sPair[kS / 2];
   const int lane = threadIdx.x;
   for (int p = blockIdx.x; p < count; p += gridDim.x) {
     const SkProb P = probs[p];
-    const int c0 = first[p], c1 = first[p + 1];
+    const double *gp = gsum + (int64_t)p * (kTri + 1);
     __syncwarp();
     for (int e = lane; e < kTri; e += 32) {
       int a = 0, rem = e;
@@ -373,13 +393,11 @@ __global__ void __launch_bounds__(32) k_sketch_eig(const SkProb *__restrict__ pr
         ++a;
       }
       const int b = a + rem;
-      double g = 0.0;
-      for (int c = c0; c < c1; ++c) g += gpart[(int64_t)c * kTri + e];
+      const double g = gp[e];
       sG[a * kS + b] = g;
       sG[b * kS + a] = g;
     }
-    double fro2 = 0.0;
-    for (int c = c0; c < c1; ++c) fro2 += fpart[c];
+    const double fro2 = gp[kTri];
     __syncwarp();
     // parallel cyclic Jacobi (tournament ordering): each round, lanes 0..15 take one of 16
     // disjoint index pairs and compute its rotation; the warp then applies all 16 to the
@@ -708,9 +726,10 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
   const size_t b_om = up(sizeof(float) * (size_t)nmax * kS), b_pr = up(sizeof(SkProb) * count),
                b_it = up(sizeof(SkItem) * nitems), b_first = up(sizeof(int) * (count + 1)),
                b_g = up(sizeof(double) * (size_t)nitems * kTri), b_f = up(sizeof(double) * nitems),
-               b_ot = mma_ok ? up(sizeof(__nv_bfloat16) * (size_t)nk * kS) : 0;
+               b_ot = mma_ok ? up(sizeof(__nv_bfloat16) * (size_t)nk * kS) : 0,
+               b_gs = up(sizeof(double) * (size_t)count * (kTri + 1));
   char *base = nullptr;
-  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f + b_ot, s) != cudaSuccess) {
+  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f + b_ot + b_gs, s) != cudaSuccess) {
     cudaGetLastError();
     return GK_OUT_OF_MEMORY;
   }
@@ -721,6 +740,7 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
   double *gpart = (double *)(base + b_om + b_pr + b_it + b_first);
   double *fpart = (double *)(base + b_om + b_pr + b_it + b_first + b_g);
   __nv_bfloat16 *omT = (__nv_bfloat16 *)(base + b_om + b_pr + b_it + b_first + b_g + b_f);
+  double *gsum = (double *)(base + b_om + b_pr + b_it + b_first + b_g + b_f + b_ot);
   int rc = GK_OK;
   do {
     if ((rc = check(cudaMemcpyAsync(dpr, pr.data(), sizeof(SkProb) * count, cudaMemcpyHostToDevice, s)))) break;
@@ -739,7 +759,8 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
         break;
       default: GK_LAUNCH(k_sketch_gram<__half><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
     }
-    GK_LAUNCH(k_sketch_eig<<<count, 32, 0, s>>>(dpr, dfirst, count, gpart, fpart, features));
+    GK_LAUNCH(k_sketch_sum<<<dim3((kTri + 1 + 127) / 128, count), 128, 0, s>>>(dfirst, count, gpart, fpart, gsum));
+    GK_LAUNCH(k_sketch_eig<<<count, 32, 0, s>>>(dpr, count, gsum, features));
     if ((rc = check(cudaGetLastError()))) break;
     rc = check(cudaStreamSynchronize(s));
   } while (0);
