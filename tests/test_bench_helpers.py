@@ -60,3 +60,15 @@ def test_host_page_report_has_the_mode():
     assert "thp" in rep
     if os.path.exists("/proc/self/smaps_rollup"):
         assert rep.get("anon_huge_kb", 0) >= 0
+
+
+def test_rsgd_flops_scale_with_products_and_problems():
+    """The Algorithm 4 roofline's FP64 count: the inner solves' share is 2 d1 d2 per product, the
+    rest of a step grows with the number of problems."""
+    w = dict(P=4, d1=784, d2=256, r=5, b=256)
+    inner, step = bench.rsgd_flops(w, 10)
+    assert inner == 2.0 * 784 * 256 * 10
+    inner2, step2 = bench.rsgd_flops(dict(w, P=8), 20)
+    assert inner2 == 2 * inner and step2 == 2 * step
+    # the mini-batch gradient dominates the rest: 2 b d1 d2 per problem
+    assert step > 4 * 2 * 256 * 784 * 256

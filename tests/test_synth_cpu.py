@@ -59,3 +59,29 @@ def test_bf16_rounding_is_round_to_nearest_even():
     assert back[2] == 1.0 + 2.0**-6  # the tie above an odd neighbour rounds up
     assert back[3] == 1.0 + 2.0**-7  # below half an ulp rounds down
     assert back[4] == -2.5 and b[5] == 0x7FC0
+
+
+def test_rsgd_data_follows_the_recipe():
+    """The Algorithm 4 inputs: shapes and dtypes, the same bytes for the same seed, batches drawn
+    without replacement inside a batch, labels -sign(x^T W* v) with a rank-r W*, start vectors
+    around 2."""
+    P, N, d1, d2, r, steps, b = 3, 200, 12, 9, 2, 4, 50
+    out = synth.rsgd_data(P, N, d1, d2, r, steps, b, seed=7)
+    X, Vd, y, W0, batches, q1, Ws = out
+    assert X.shape == (P, N, d1) and Vd.shape == (P, N, d2) and y.shape == (P, N)
+    assert W0.shape == (P, d1, d2) and batches.shape == (steps, P, b) and q1.shape == (P, d1)
+    assert batches.dtype == np.int32 and X.dtype == np.float64
+    again = synth.rsgd_data(P, N, d1, d2, r, steps, b, seed=7)
+    for a, c in zip(out, again):
+        np.testing.assert_array_equal(a, c)
+    assert np.all((batches >= 0) & (batches < N))
+    for t in range(steps):
+        for p in range(P):
+            assert len(set(batches[t, p].tolist())) == b
+    for p in range(P):
+        assert np.linalg.matrix_rank(Ws[p]) == r
+        s = np.array([X[p][i] @ Ws[p] @ Vd[p][i] for i in range(N)])
+        np.testing.assert_array_equal(y[p], np.where(s > 0, -1.0, 1.0))
+    assert abs(q1.mean() - 2.0) < 0.2
+    # zero steps: an empty batch array of the right shape
+    assert synth.rsgd_data(P, N, d1, d2, r, 0, b, seed=7)[4].shape == (0, P, b)
