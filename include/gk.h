@@ -209,6 +209,42 @@ size_t gk_numrank_workspace(const gk_matrix *A, int kmax, const gk_opts *opts);
 int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, int *rank, double *sigma,
                gk_info *info);
 
+/* Numerical rank from a block of s start vectors: Algorithm 1 and Algorithm 3
+ * with each vector replaced by a block (the paper has the single-vector form;
+ * one start vector's Krylov space holds one direction per distinct singular
+ * value, so Algorithm 1 counts a singular value of multiplicity > 1 once, and a
+ * block of s counts multiplicities up to s).  The recurrence, with each block
+ * orthonormalized by QR (diag >= 0) after two classical Gram-Schmidt passes
+ * against the earlier blocks:
+ *   Q_1 R_0 = Q0,  P_1 R_1 = A^T Q_1,
+ *   Q_{j+1} S_{j+1} = A P_j - Q_j R_j^T,  P_{j+1} R_{j+1} = A^T Q_{j+1} - P_j S_{j+1}^T,
+ * so A [P_1..P_k] = [Q_1..Q_{k+1}] B with B block lower bidiagonal (R_j^T on the
+ * diagonal, S_{j+1} below it; the block form of Eq. 2.2).  The sweep stops when
+ * ||S_{j+1}||_2 <= eps * sigma~ (sigma~: the largest block 2-norm so far), when
+ * ||R_{j+1}||_2 <= eps * max(sigma~, ||R_{j+1}||_2) (that block is not kept),
+ * after kmax block steps, or when one more block would exceed min(m, n)
+ * columns; the rank is the number of singular values of B above eps * sigma_1(B).
+ *  s:     block size, 1 <= s <= 32 and s <= min(m, n).
+ *  Q0:    m x s start block, column-major (ld = m), f64, device or host; NULL draws
+ *         column c as Algorithm 1's start vector with seed opts->seed + c.
+ *  eps:   relative threshold (opts->eps_absolute must be 0).
+ *  kmax:  block steps; <= 0 means min(m, n) / s, capped so that (kmax + 1) s <= 1024
+ *         (the order of B's square for the small SVD); a larger explicit kmax is
+ *         GK_INVALID_ARG.
+ *  rank:  host int, written on success.
+ *  sigma: optional (may be NULL): the steps * s singular values of B, descending
+ *         (device or host, f64, capacity kmax * s).
+ *  steps: optional host int: block steps taken.
+ * Dense f32/bf16/f16 operators form each block product in one pass over A with
+ * double-f32 products (as gk_residuals); f64 and CSR operators run one product
+ * per column.  info: steps = block steps, kprime = columns of B, stop_reason 0
+ * kmax, 1 left block break, 2 right block break, 3 the blocks filled min(m, n);
+ * matvecs counts single-vector products.  Returns GK_OK, GK_NOT_CONVERGED when
+ * the small SVD hit its sweep limit, GK_NUMERICAL on a non-finite norm, or an
+ * error. */
+int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, int kmax, const gk_opts *opts, int *rank,
+                     double *sigma, int *steps, gk_info *info);
+
 /* F-SVD as printed (Algorithm 2): k steps of Algorithm 1 (lower-bidiagonal GK
  * with reorthogonalization; only an exact zero norm ends them early), then for
  * the r largest:

@@ -7,6 +7,7 @@ binding.
 from .gk import (  # noqa: F401
     CSR,
     GKError,
+    gk_block_numrank,
     gk_fsvd,
     gk_matvec,
     gk_mlp_forward,

@@ -1100,6 +1100,312 @@ int numrank_impl(const gk_matrix *Ain, double eps, int kmax_in, const gk_opts *o
 }
 
 // ---------------------------------------------------------------------------
+// gk_block_numrank: Algorithm 1 and Algorithm 3 on blocks of s start vectors
+// ---------------------------------------------------------------------------
+constexpr int kBlockMaxOrder = 1024;  // (block steps + 1) * s: the order of B's square (small SVD)
+
+struct BlockBufs {
+  Ctl *ctl;
+  BlockCtl *bc;
+  double *Q, *P, *W, *w, *Xc, *part, *h, *dpart, *raw, *Bf, *Bm, *Yw, *X, *Y, *sigma, *nrm, *q0;
+  float *x32, *split;
+  float2 *Qs, *Ps, *ws2;
+  int *pos, *sweeps, *rank;
+  bool df;   // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
+  bool acc;  // dense reduced-precision operator: block products in one pass (double-f32)
+};
+
+size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const OpStage &st, bool host_q0, char *base,
+                    BlockBufs *b, Op *op) {
+  Carve cv{base, 0};
+  const int64_t m = A->m, n = A->n, ldu = round_up(m, 32), ldv = round_up(n, 32), mx = m > n ? m : n;
+  const int64_t lmax = ldu > ldv ? ldu : ldv;
+  const int64_t cols = (kb + 1) * s;  // basis columns, and the order of B's square
+  b->ctl = cv.take<Ctl>(1);
+  b->bc = cv.take<BlockCtl>(1);
+  b->Q = cv.take<double>((size_t)ldu * cols);
+  b->P = cv.take<double>((size_t)ldv * cols);
+  b->W = cv.take<double>((size_t)mx * s);
+  b->w = cv.take<double>(lmax);
+  b->Xc = b->acc ? cv.take<double>((size_t)mx * s) : nullptr;
+  b->x32 = cv.take<float>(lmax);
+  const int64_t gmax = cgs_blocks(m, d) > cgs_blocks(n, d) ? cgs_blocks(m, d) : cgs_blocks(n, d);
+  int64_t pcount = gmax * (cols + 2) + gmax;
+  if (coop_partials((int)cols, d) > pcount) pcount = coop_partials((int)cols, d);
+  const int64_t gp = gemvt_partials(*op, d);
+  if (gp > pcount) pcount = gp;
+  b->part = cv.take<double>(pcount);
+  b->h = cv.take<double>(2 * (size_t)cols + 4);
+  b->dpart = cv.take<double>((size_t)s * s * block_dot_chunks(mx));
+  b->raw = cv.take<double>((size_t)s * s);
+  b->Bf = cv.take<double>((size_t)cols * cols);
+  b->Bm = cv.take<double>((size_t)cols * cols);
+  b->Yw = cv.take<double>((size_t)cols * cols);
+  b->X = cv.take<double>((size_t)cols * cols);
+  b->Y = cv.take<double>((size_t)cols * cols);
+  b->sigma = cv.take<double>(cols);
+  b->nrm = cv.take<double>(cols);
+  b->pos = cv.take<int>(cols);
+  b->sweeps = cv.take<int>(1);
+  b->rank = cv.take<int>(1);
+  b->split = b->acc ? cv.take<float>(accurate_floats(*op, s)) : nullptr;
+  b->q0 = host_q0 ? cv.take<double>((size_t)m * s) : nullptr;
+  b->Qs = b->df ? cv.take<float2>((size_t)ldu * cols) : nullptr;
+  b->Ps = b->df ? cv.take<float2>((size_t)ldv * cols) : nullptr;
+  b->ws2 = b->df ? cv.take<float2>(lmax) : nullptr;
+  char *dd;
+  void *v, *tv;
+  int32_t *rp, *ci, *trp, *tci;
+  stage_carve(A, st, cv, op, &dd, &v, &rp, &ci, &tv, &trp, &tci);
+  return cv.off + 256;
+}
+
+// block steps: kmax <= 0 means until the blocks fill min(m, n), within the small SVD's order
+int block_steps(const gk_matrix *A, int s, int kmax, int64_t *kb) {
+  const int64_t mn = A->m < A->n ? A->m : A->n;
+  const int64_t cap = kBlockMaxOrder / s - 1;
+  if (kmax <= 0) {
+    int64_t k = mn / s;
+    if (k > cap) k = cap;
+    *kb = k < 1 ? 1 : k;
+    return GK_OK;
+  }
+  if (kmax > cap) return GK_INVALID_ARG;
+  *kb = kmax;
+  return GK_OK;
+}
+
+// W[:, c] = op(A) src[:, c], c < s (W column-major with ld = the output length)
+int block_product(const Op &op, BlockBufs &b, bool trans, const double *src, int64_t ldsrc, int s, cudaStream_t st,
+                  const Dev &d) {
+  const int64_t lin = trans ? op.m : op.n, lout = trans ? op.n : op.m;
+  if (b.acc) {  // one pass over A for the whole block, products exact to ~2^-47
+    GK_CUDA(cudaMemcpy2DAsync(b.Xc, sizeof(double) * lin, src, sizeof(double) * ldsrc, sizeof(double) * lin, s,
+                              cudaMemcpyDeviceToDevice, st));
+    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st));
+    return GK_OK;
+  }
+  for (int c = 0; c < s; ++c) {
+    const double *x = src + (int64_t)c * ldsrc;
+    double *y = b.W + (int64_t)c * lout;
+    GK_CUDA(copy_vec(nullptr, b.x32, x, lin, st));
+    if (trans)
+      GK_CUDA(matvec_t(op, b.x32, x, y, nullptr, nullptr, b.part, b.ctl, st, d));
+    else
+      GK_CUDA(matvec(op, b.x32, x, y, nullptr, nullptr, b.part, b.ctl, st, d));
+  }
+  return GK_OK;
+}
+
+// a column that the Gram-Schmidt reduced to rounding (the block is numerically rank deficient)
+// is replaced by a fresh direction orthogonalized twice against the jc columns before it and
+// normalized: an orthonormal completion, as a Householder QR of the block would give
+int block_fresh(BlockBufs &b, int64_t len, double *Bas, int64_t ld, float2 *Bs, int jc, uint64_t seed, int64_t *nfresh,
+                cudaStream_t st, const Dev &d) {
+  GK_CUDA(draw_fresh(b.w, len, seed, (*nfresh)++, st));
+  GK_CUDA(orthonormalize(b.w, len, Bas, ld, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 0, nullptr, nullptr, st, d));
+  GK_CUDA(orthonormalize(b.w, len, Bas, ld, jc, 2, b.part, b.h, b.ctl, NM_FRESH, -1, 0, nullptr, nullptr, st, d, Bs,
+                         b.ws2));
+  GK_CUDA(normalize_append(b.w, len, Bas + (int64_t)jc * ld, nullptr, b.ctl, st, d, Bs ? Bs + (int64_t)jc * ld : nullptr));
+  return GK_OK;
+}
+
+// columns jc0 .. jc0 + s - 1 of the basis Bas (ld; double-f32 shadow Bs or null): column c of
+// Wsrc (ld ldw) orthonormalized by classical Gram-Schmidt, two passes, against every column
+// before it -- the reorthogonalization and the QR of the block in one.  A column whose norm
+// after the passes is at most 2^-46 of the largest norm so far halts the launches that follow
+// (an exact breakdown); the host then puts a fresh direction in its place and goes on with
+// the next column.
+int block_orth(BlockBufs &b, int64_t len, double *Bas, int64_t ld, float2 *Bs, int jc0, int s, const double *Wsrc,
+               int64_t ldw, int side, uint64_t seed, int64_t *nfresh, int *breakdowns, cudaStream_t st,
+               const Dev &d) {
+  int c0 = 0;
+  while (c0 < s) {
+    for (int c = c0; c < s; ++c) {
+      const int jc = jc0 + c;
+      double *qcol = Bas + (int64_t)jc * ld;
+      float2 *qs = Bs ? Bs + (int64_t)jc * ld : nullptr;
+      GK_CUDA(copy_vec(b.w, nullptr, Wsrc + (int64_t)c * ldw, len, st));
+      if (jc == 0) {
+        GK_CUDA(orthonormalize(b.w, len, nullptr, ld, 0, 0, b.part, b.h, b.ctl, NM_BREAKDOWN, jc, side, nullptr,
+                               nullptr, st, d));
+        GK_CUDA(normalize_append(b.w, len, qcol, nullptr, b.ctl, st, d, qs));
+      } else {
+        GK_CUDA(orth_append(b.w, len, Bas, ld, jc, 2, b.part, b.h, b.ctl, NM_BREAKDOWN, jc, side, nullptr, nullptr,
+                            qcol, nullptr, st, d, Bs, b.ws2, qs));
+      }
+    }
+    HostCtl hc;
+    int rc = read_ctl(b.ctl, nullptr, &hc, st);
+    if (rc) return rc;
+    if (hc.ctl.timeout || hc.ctl.event == EV_TIMEOUT) return GK_TIMEOUT;
+    if (!hc.ctl.halt) return GK_OK;
+    if (hc.ctl.event != EV_BREAKDOWN) return GK_NUMERICAL;
+    const int jb = hc.ctl.step;  // the column the passes reduced to rounding
+    if (jb < jc0 + c0 || jb >= jc0 + s) return GK_NUMERICAL;
+    rc = clear_halt(b.ctl, st);
+    if (rc) return rc;
+    rc = block_fresh(b, len, Bas, ld, Bs, jb, seed, nfresh, st, d);
+    if (rc) return rc;
+    ++*breakdowns;
+    c0 = jb - jc0 + 1;
+  }
+  return GK_OK;
+}
+
+int read_block(const BlockBufs &b, BlockCtl *hb, HostCtl *hc, cudaStream_t st) {
+  GK_CUDA(cudaMemcpyAsync(hb, b.bc, sizeof(BlockCtl), cudaMemcpyDeviceToHost, st));
+  GK_CUDA(cudaMemcpyAsync(&hc->ctl, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  GK_CUDA(cudaStreamSynchronize(st));
+  if (hc->ctl.event == EV_TIMEOUT || hc->ctl.timeout) return GK_TIMEOUT;
+  if (hc->ctl.event == EV_NUMERICAL || hb->brk == 2) return GK_NUMERICAL;
+  return GK_OK;
+}
+
+int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int kmax, const gk_opts *oin, int *rank,
+               double *sigma, int *steps_out, gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  g_err[0] = 0;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  if (info) *info = inf;
+  // the arguments first: a bad request is refused with or without a device
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  const int64_t m = Ain->m, n = Ain->n, mn = m < n ? m : n;
+  if (!rank || s < 1 || s > kBlockMaxS || s > mn || !(eps >= 0.0) || !isfinite(eps)) return GK_INVALID_ARG;
+  const gk_opts o = oin ? *oin : defaults();
+  if (o.eps_absolute) return GK_INVALID_ARG;
+  int64_t kb = 0;
+  rc = block_steps(Ain, s, kmax, &kb);
+  if (rc) return rc;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  OpStage stg;
+  rc = stage_plan(Ain, &stg);
+  if (rc) return rc;
+  const bool host_q0 = Q0 && on_host(Q0);
+  const bool host_sigma = sigma && on_host(sigma);
+  Op op = make_op(Ain);
+  BlockBufs b;
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
+  b.acc = accurate_ok(op);
+  const size_t bytes = block_layout(Ain, s, kb, d, stg, host_q0, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, st);
+  if (rc) return rc;
+  op = make_op(Ain);
+  block_layout(Ain, s, kb, d, stg, host_q0, ws.base, &b, &op);
+  rc = stage_copy(Ain, stg, op, st);
+  if (rc) return rc;
+  const int64_t ldu = round_up(m, 32), ldv = round_up(n, 32), cols = (kb + 1) * s;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
+  GK_CUDA(cudaMemsetAsync(b.bc, 0, sizeof(BlockCtl), st));
+  GK_CUDA(cudaMemsetAsync(b.Bf, 0, sizeof(double) * cols * cols, st));
+  if (b.df) {  // the shadows' padding rows (past m, n) are read beside the last odd row: keep them 0
+    GK_CUDA(cudaMemsetAsync(b.Qs, 0, sizeof(float2) * ldu * cols, st));
+    GK_CUDA(cudaMemsetAsync(b.Ps, 0, sizeof(float2) * ldv * cols, st));
+  }
+  // Q_1 R_0 = Q0: the given block, or column c drawn as Algorithm 1's start vector (seed + c)
+  const double *q0 = Q0;
+  if (host_q0) {
+    GK_CUDA(cudaMemcpyAsync(b.q0, Q0, sizeof(double) * m * s, cudaMemcpyHostToDevice, st));
+    q0 = b.q0;
+  }
+  if (!q0) {
+    for (int c = 0; c < s; ++c) GK_CUDA(draw_start(b.W + (int64_t)c * m, m, o.seed + (uint64_t)c, st));
+    q0 = b.W;
+  }
+  int64_t nfresh = 0;
+  int breakdowns = 0;
+  rc = block_orth(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+  if (rc) return rc;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));  // the breakdown scale follows the blocks' norms from here
+  // P_1 R_1 = A^T Q_1; sigma~ = ||R_1||
+  rc = block_product(op, b, true, b.Q, ldu, s, st, d);
+  if (rc) return rc;
+  rc = block_orth(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+  if (rc) return rc;
+  GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
+  GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, eps, b.bc, st));
+  int64_t matvecs = s;
+  int steps = 1, stop = 0;
+  BlockCtl hb;
+  HostCtl hc;
+  for (;;) {
+    // Q_{j+1} S_{j+1} = A P_j - Q_j R_j^T, reorthogonalized (j = steps)
+    const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
+    rc = block_product(op, b, false, b.P + pj * ldv, ldv, s, st, d);
+    if (rc) return rc;
+    rc = block_orth(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+    if (rc) return rc;
+    GK_CUDA(block_dots(b.Q + qn * ldu, ldu, b.W, m, m, s, b.dpart, b.raw, st));
+    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)pj, 0, eps, b.bc, st));
+    matvecs += s;
+    rc = read_block(b, &hb, &hc, st);
+    if (rc) return rc;
+    if (hb.brk) {
+      stop = 1;
+      break;
+    }
+    if (steps >= kb) {
+      stop = 0;
+      break;
+    }
+    if ((int64_t)(steps + 1) * s > mn) {
+      stop = 3;
+      break;
+    }
+    // P_{j+1} R_{j+1} = A^T Q_{j+1} - P_j S_{j+1}^T, reorthogonalized
+    rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
+    if (rc) return rc;
+    rc = block_orth(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    if (rc) return rc;
+    GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
+    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)qn, 1, eps, b.bc, st));
+    matvecs += s;
+    rc = read_block(b, &hb, &hc, st);
+    if (rc) return rc;
+    if (hb.brk) {
+      stop = 2;
+      break;
+    }
+    ++steps;
+  }
+  // Algorithm 3 on B ((steps + 1) s x steps s), padded with zero columns to its square
+  const int K = (steps + 1) * s, nsig = steps * s;
+  GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * cols, sizeof(double) * K, K,
+                            cudaMemcpyDeviceToDevice, st));
+  GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
+  GK_CUDA(block_count(b.sigma, nsig, eps, b.rank, st));
+  if (sigma) {
+    if (host_sigma)
+      GK_CUDA(cudaMemcpyAsync(sigma, b.sigma, sizeof(double) * nsig, cudaMemcpyDeviceToHost, st));
+    else
+      GK_CUDA(cudaMemcpyAsync(sigma, b.sigma, sizeof(double) * nsig, cudaMemcpyDeviceToDevice, st));
+  }
+  int r = 0, sweeps = 0;
+  GK_CUDA(cudaMemcpyAsync(&r, b.rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GK_CUDA(cudaMemcpyAsync(&sweeps, b.sweeps, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GK_CUDA(cudaStreamSynchronize(st));
+  *rank = r;
+  if (steps_out) *steps_out = steps;
+  inf.steps = steps;
+  inf.kprime = nsig;
+  inf.stop_reason = stop;
+  inf.matvecs = matvecs;
+  inf.svd_sweeps = sweeps;
+  inf.breakdowns = breakdowns;
+  inf.sigma_est = hb.sest;
+  inf.seconds = seconds_since(t0);
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  return sweeps < 0 ? GK_NOT_CONVERGED : GK_OK;
+}
+
+// ---------------------------------------------------------------------------
 // gk_fsvd: Algorithm 2 as printed (k steps of Algorithm 1, the SVD of B_{k'+1,k'}, no restart)
 // ---------------------------------------------------------------------------
 struct FsvdBufs {
@@ -1433,6 +1739,12 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
                gk_info *info) {
   NvtxRange r("gk_numrank");
   return numrank_impl(A, eps, kmax, opts, rank, sigma, info);
+}
+
+int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, int kmax, const gk_opts *opts, int *rank,
+                     double *sigma, int *steps, gk_info *info) {
+  NvtxRange r("gk_block_numrank");
+  return block_impl(A, s, Q0, eps, kmax, opts, rank, sigma, steps, info);
 }
 
 int gk_fsvd(const gk_matrix *A, int k, int r, int route, const gk_opts *opts, double *U, double *S, double *V,

@@ -1,0 +1,201 @@
+// gk_block.cu -- the small kernels of block Golub-Kahan with s start vectors (gk_block_numrank).
+//
+// The block recurrence replaces each vector of Algorithm 1 by an m x s (or n x s) block and
+// each normalization by a QR factorization with diag(R) >= 0:
+//   Q_1 R_0 = Q0,  P_1 R_1 = A^T Q_1,
+//   Q_{j+1} S_{j+1} = A P_j - Q_j R_j^T,   P_{j+1} R_{j+1} = A^T Q_{j+1} - P_j S_{j+1}^T,
+// each new block reorthogonalized against the earlier ones, so that A [P_1..P_k] =
+// [Q_1..Q_{k+1}] B with B block lower bidiagonal (diagonal blocks R_j^T, subdiagonal blocks
+// S_{j+1}), the block form of Eq. 2.2.  The host driver (gk_api.cu) forms a block's columns
+// one at a time by classical Gram-Schmidt (two passes) against every basis column so far:
+// that is the QR of the block after its reorthogonalization, and the triangular factor is
+// Q_{j+1}^T (A P_j) (resp. P_{j+1}^T (A^T Q_{j+1})) because each new column is orthogonal to
+// the earlier blocks.  These kernels form those s x s inner products, keep their upper
+// triangle, place it (or its transpose) into B, and judge the block's 2-norm:
+//   * k_block_dots / k_block_dots_sum: raw = X^T Y for two len x s column blocks, f64, the
+//     row chunks summed in a fixed order;
+//   * k_block_judge: T = triu(raw), ||T||_2 = sqrt(lambda_max(T^T T)) by cyclic Jacobi on one
+//     warp, the running estimate of sigma_1 and the block break tests;
+//   * k_block_count: Algorithm 3's count of the singular values of B above eps sigma_1(B).
+#include <math.h>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kDotRows = 8192;  // rows per partial sum of k_block_dots
+
+__device__ __forceinline__ double warp_sum_b(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// part[pair * G + g] = sum over rows [g kDotRows, (g + 1) kDotRows) of X[i, a] Y[i, b],
+// pair = a + b s (grid: G x s^2)
+__global__ void __launch_bounds__(kDotThreads) k_block_dots(const double *__restrict__ X, int64_t ldx,
+                                                            const double *__restrict__ Y, int64_t ldy, int64_t len,
+                                                            int s, int G, double *__restrict__ part) {
+  __shared__ double red[kDotThreads / 32];
+  const int g = blockIdx.x, pair = blockIdx.y;
+  const int a = pair % s, b = pair / s;
+  const int64_t i0 = (int64_t)g * kDotRows;
+  const int64_t i1 = i0 + kDotRows < len ? i0 + kDotRows : len;
+  const double *x = X + (int64_t)a * ldx;
+  const double *y = Y + (int64_t)b * ldy;
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kDotThreads) acc = fma(x[i], y[i], acc);
+  acc = warp_sum_b(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kDotThreads / 32 ? red[threadIdx.x] : 0.0;
+    v = warp_sum_b(v);
+    if (threadIdx.x == 0) part[(int64_t)pair * G + g] = v;
+  }
+}
+
+// raw[pair] = sum_g part[pair * G + g], g ascending
+__global__ void k_block_dots_sum(const double *__restrict__ part, int G, int pairs, double *__restrict__ raw) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pairs) return;
+  double v = 0.0;
+  for (int g = 0; g < G; ++g) v += part[(int64_t)p * G + g];
+  raw[p] = v;
+}
+
+// One warp.  T = triu(raw) (s x s, T[a + c s] = raw[a + c s] for a <= c, else 0); its 2-norm
+// from the eigenvalues of G = T^T T (cyclic Jacobi: rotations while some |g_pq| exceeds
+// 1e-16 sqrt(|g_pp g_qq|), at most kSweeps sweeps; the largest diagonal entry is a lower
+// bound on lambda_max at any point and equals it on convergence).  side 0 (S_{j+1}, left):
+// sest = max(sest, ||T||), break when eps > 0 and ||T|| <= eps sest; T placed at
+// Bf[row0 + a, col0 + c].  side 1 (R_{j+1}, right): break when eps > 0 and ||T|| <=
+// eps max(sest, ||T||), else sest = max(sest, ||T||) and T^T placed at Bf[row0 + c, col0 + a].
+// side 2 (R_1, the first right block): no test, sest = ||T||, T^T placed.  A non-finite norm
+// sets brk = 2 (nothing placed).
+constexpr int kSweeps = 60;
+
+__global__ void __launch_bounds__(32) k_block_judge(const double *__restrict__ raw, int s, double *__restrict__ Bf,
+                                                    int64_t ldb, int row0, int col0, int side, double eps,
+                                                    BlockCtl *bc) {
+  __shared__ double T[kBlockMaxS * kBlockMaxS];
+  __shared__ double G[kBlockMaxS * kBlockMaxS];
+  __shared__ int s_brk;
+  const int lane = threadIdx.x;
+  const int ss = s * s;
+  for (int e = lane; e < ss; e += 32) T[e] = (e % s) <= (e / s) ? raw[e] : 0.0;
+  __syncwarp();
+  for (int e = lane; e < ss; e += 32) {
+    const int p = e % s, q = e / s;
+    double v = 0.0;
+    for (int a = 0; a < s; ++a) v = fma(T[a + p * s], T[a + q * s], v);
+    G[e] = v;
+  }
+  __syncwarp();
+  int sweeps = 0;
+  for (; sweeps < kSweeps; ++sweeps) {
+    bool rotated = false;
+    for (int p = 0; p < s - 1; ++p) {
+      for (int q = p + 1; q < s; ++q) {
+        __syncwarp();
+        const double apq = G[p + q * s], app = G[p + p * s], aqq = G[q + q * s];
+        if (apq == 0.0 || fabs(apq) <= 1e-16 * sqrt(fabs(app) * fabs(aqq))) continue;  // the same on every lane
+        rotated = true;
+        // the rotation that zeroes g_pq (the symmetric 2 x 2 Schur decomposition)
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+        __syncwarp();
+        if (lane < s) {  // columns p and q
+          const double gp = G[lane + p * s], gq = G[lane + q * s];
+          G[lane + p * s] = c * gp - sn * gq;
+          G[lane + q * s] = sn * gp + c * gq;
+        }
+        __syncwarp();
+        if (lane < s) {  // rows p and q
+          const double gp = G[p + lane * s], gq = G[q + lane * s];
+          G[p + lane * s] = c * gp - sn * gq;
+          G[q + lane * s] = sn * gp + c * gq;
+        }
+      }
+    }
+    if (!rotated) break;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double lmax = 0.0;
+    for (int p = 0; p < s; ++p) lmax = fmax(lmax, G[p + p * s]);
+    const double nrm = sqrt(lmax);
+    double sest = bc->sest;
+    int brk = 0;
+    if (!isfinite(nrm)) {
+      brk = 2;
+    } else if (side == 0) {
+      sest = fmax(sest, nrm);
+      brk = (eps > 0.0 && nrm <= eps * sest) ? 1 : 0;
+    } else if (side == 1) {
+      brk = (eps > 0.0 && nrm <= eps * fmax(sest, nrm)) ? 1 : 0;
+      if (!brk) sest = fmax(sest, nrm);
+    } else {
+      sest = fmax(sest, nrm);
+    }
+    bc->sest = sest;
+    bc->nrm = nrm;
+    bc->brk = brk;
+    bc->sweeps = sweeps;
+    s_brk = brk;
+  }
+  __syncwarp();
+  const bool place = s_brk == 0 || (side == 0 && s_brk == 1);
+  if (!place) return;
+  for (int e = lane; e < ss; e += 32) {
+    const int a = e % s, c = e / s;
+    if (a > c) continue;
+    if (side == 0)
+      Bf[(int64_t)(row0 + a) + (int64_t)(col0 + c) * ldb] = T[e];
+    else
+      Bf[(int64_t)(row0 + c) + (int64_t)(col0 + a) * ldb] = T[e];
+  }
+}
+
+// *rank = #{i < n : sigma[i] > eps * sigma[0]}
+__global__ void k_block_count(const double *__restrict__ sigma, int n, double eps, int *rank) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int r = 0;
+  if (n > 0) {
+    const double thr = eps * sigma[0];
+    for (int i = 0; i < n; ++i) r += sigma[i] > thr ? 1 : 0;
+  }
+  *rank = r;
+}
+
+}  // namespace
+
+int block_dot_chunks(int64_t len) { return (int)((len + kDotRows - 1) / kDotRows); }
+
+cudaError_t block_dots(const double *X, int64_t ldx, const double *Y, int64_t ldy, int64_t len, int s, double *part,
+                       double *raw, cudaStream_t st) {
+  if (s < 1 || s > kBlockMaxS || len < 1) return cudaErrorInvalidValue;
+  const int G = block_dot_chunks(len);
+  const int pairs = s * s;
+  GK_LAUNCH(k_block_dots<<<dim3((unsigned)G, (unsigned)pairs), kDotThreads, 0, st>>>(X, ldx, Y, ldy, len, s, G, part));
+  GK_LAUNCH(k_block_dots_sum<<<(pairs + 127) / 128, 128, 0, st>>>(part, G, pairs, raw));
+  return cudaGetLastError();
+}
+
+cudaError_t block_judge(const double *raw, int s, double *Bf, int64_t ldb, int row0, int col0, int side, double eps,
+                        BlockCtl *bc, cudaStream_t st) {
+  if (s < 1 || s > kBlockMaxS) return cudaErrorInvalidValue;
+  GK_LAUNCH(k_block_judge<<<1, 32, 0, st>>>(raw, s, Bf, ldb, row0, col0, side, eps, bc));
+  return cudaGetLastError();
+}
+
+cudaError_t block_count(const double *sigma, int n, double eps, int *rank, cudaStream_t st) {
+  GK_LAUNCH(k_block_count<<<1, 32, 0, st>>>(sigma, n, eps, rank));
+  return cudaGetLastError();
+}
+
+}  // namespace gk

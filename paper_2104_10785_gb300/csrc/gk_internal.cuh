@@ -205,6 +205,28 @@ cudaError_t sub_combination(double *y, int64_t len, const double *Q, int64_t ld,
                             const Ctl *ctl, cudaStream_t s, const Dev &d);
 cudaError_t reset_ctl(Ctl *ctl, double eps, int eps_rel, cudaStream_t s);
 
+// ---- block Golub-Kahan (gk_block.cu) -----------------------------------------
+constexpr int kBlockMaxS = 32;  // largest block (start vectors per block)
+// state of the block sweep's tests, written by block_judge
+struct BlockCtl {
+  double sest;  // running estimate of sigma_1: the largest block 2-norm so far
+  double nrm;   // 2-norm of the last judged block
+  int brk;      // 1: the last judged block ends the sweep; 2: its norm was not finite
+  int sweeps;   // Jacobi sweeps of the last norm
+};
+// partial sums block_dots needs: s * s * block_dot_chunks(len) doubles
+int block_dot_chunks(int64_t len);
+// raw[a + b s] = X[:, a] . Y[:, b] (a, b < s <= kBlockMaxS; len rows; f64)
+cudaError_t block_dots(const double *X, int64_t ldx, const double *Y, int64_t ldy, int64_t len, int s, double *part,
+                       double *raw, cudaStream_t st);
+// T = triu(raw) (s x s): its 2-norm, the running estimate and the break test of `side`
+// (0: a left block S_{j+1}, placed as T at (row0, col0) of Bf; 1: a right block R_{j+1},
+// placed as T^T unless it ends the sweep; 2: the first right block, no test), into *bc
+cudaError_t block_judge(const double *raw, int s, double *Bf, int64_t ldb, int row0, int col0, int side, double eps,
+                        BlockCtl *bc, cudaStream_t st);
+// *rank = #{i < n : sigma[i] > eps sigma[0]} (device)
+cudaError_t block_count(const double *sigma, int n, double eps, int *rank, cudaStream_t st);
+
 // ---- small dense kernels (gk_small.cu) ----------------------------------
 // B (K x K, column-major) of one restart cycle: kept Ritz values on the
 // diagonal of the first l rows, the coupling column rho in column l, and the

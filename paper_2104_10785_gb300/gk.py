@@ -123,6 +123,9 @@ def lib():
             L.gk_fsvd.argtypes = [P(gk_matrix), C.c_int, C.c_int, C.c_int, P(gk_opts), C.c_void_p, C.c_void_p,
                                   C.c_void_p, P(gk_info)]
             L.gk_fsvd.restype = C.c_int
+            L.gk_block_numrank.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_double, C.c_int, P(gk_opts),
+                                           P(C.c_int), C.c_void_p, P(C.c_int), P(gk_info)]
+            L.gk_block_numrank.restype = C.c_int
             L.gk_matvec.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
             L.gk_matvec.restype = C.c_int
             L.gk_residuals.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -423,6 +426,36 @@ def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = Fals
         raise GKError(st, "gk_numrank")
     d = info.as_dict()
     return r.value, (sig[: d["kprime"]] if sig is not None else None), st, d
+
+
+def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None, seed: int | None = None,
+                     stream=None, workspace=None, scale: float = 1.0, want_sigma: bool = False, check: bool = True,
+                     orth_f64: bool = False):
+    """Numerical rank from a block of s start vectors (block Algorithm 1 + Algorithm 3).
+    start: optional m x s start block.  Returns (rank, sigma(B) or None, block steps, status, info dict)."""
+    M, keep_a = make_matrix(A, scale)
+    dev = A.device
+    if dev.type != "cuda" and not torch.cuda.is_available():
+        raise RuntimeError("gk_block_numrank needs a CUDA device (no host fallback)")
+    mn = min(M.m, M.n)
+    s = int(s)
+    cap_steps = int(kmax) if kmax > 0 else max(1, min(mn // max(s, 1), 1024 // max(s, 1) - 1))
+    sig = torch.zeros(max(cap_steps * s, 1), dtype=torch.float64, device=dev) if want_sigma else None
+    q0 = None
+    if start is not None:
+        # start is m x s; the library reads it column-major (column c contiguous)
+        q0 = start.to(torch.float64).t().contiguous()
+    o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), seed=seed, stream=stream, workspace=workspace,
+                  orth_f64=orth_f64)
+    info = gk_info()
+    r = C.c_int(-1)
+    steps = C.c_int(0)
+    st = lib().gk_block_numrank(C.byref(M), s, _ptr(q0), float(eps), int(kmax), C.byref(o), C.byref(r), _ptr(sig),
+                                C.byref(steps), C.byref(info))
+    if check and st < 0:
+        raise GKError(st, "gk_block_numrank")
+    d = info.as_dict()
+    return r.value, (sig[: d["kprime"]] if sig is not None else None), steps.value, st, d
 
 
 def gk_matvec(A, x, trans: bool = False, *, stream=None, scale: float = 1.0):

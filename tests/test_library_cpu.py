@@ -125,3 +125,31 @@ def test_rsgd_entry_checks_arguments_before_the_device():
         assert L.gk_rsgd_batched(C.byref(args(**bad)), None, None) == raw.GK_INVALID_ARG, bad
     if not torch.cuda.is_available():
         assert L.gk_rsgd_batched(C.byref(args()), None, None) == raw.GK_NO_DEVICE
+
+
+def test_block_numrank_checks_arguments_before_the_device():
+    """gk_block_numrank refuses a block size outside 1..min(32, m, n), a negative or non-finite
+    eps, the absolute threshold and a block count past the small SVD's order with
+    GK_INVALID_ARG; a valid request without a device gets GK_NO_DEVICE (no host fallback)."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+    from paper_2104_10785_gb300 import gk as raw
+
+    A = np.ones((40, 30))
+    M = raw.gk_matrix(raw.GK_DENSE, raw.GK_F64, 40, 30, 30, 1.0, A.ctypes.data, None, None, None, None, None)
+    L = raw.lib()
+
+    def call(s=4, eps=1e-8, kmax=0, absolute=0):
+        o = raw.default_opts()
+        o.eps_absolute = absolute
+        r = C.c_int(-1)
+        return L.gk_block_numrank(C.byref(M), s, None, eps, kmax, C.byref(o), C.byref(r), None, None, None)
+
+    for bad in (dict(s=0), dict(s=33), dict(s=31), dict(eps=-1.0), dict(eps=float("nan")), dict(eps=float("inf")),
+                dict(absolute=1), dict(s=4, kmax=256), dict(s=1, kmax=1024)):
+        assert call(**bad) == raw.GK_INVALID_ARG, bad
+    if not torch.cuda.is_available():
+        assert call() == raw.GK_NO_DEVICE
+        assert call(s=4, kmax=255) == raw.GK_NO_DEVICE  # (255 + 1) * 4 = 1024
