@@ -76,6 +76,11 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               6.7 ms against 6.0 ms for the multi-kernel sweep, both bound by f64
                               arithmetic latency rather than launches.  gk_info then reports its
                               counters; reserved = 0. */
+#define GK_FLAG_SKETCH_TC 64 /* gk_sketch_batched, one bf16 operator with rows on 16-byte boundaries:
+                              Y = A Omega on the tcgen05 tensor cores with TMA-staged tiles and the
+                              accumulator in tensor memory, instead of mma.sync.  Experimental: not
+                              yet run on a GPU; returns GK_TIMEOUT if one of its bounded waits gives
+                              up. */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).

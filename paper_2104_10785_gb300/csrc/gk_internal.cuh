@@ -158,6 +158,16 @@ cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, d
 cudaError_t resid_norms(const double *Y, const double *W, const double *S, int64_t len, int k, double *res,
                         cudaStream_t s);
 
+// ---- the sketch on the tensor cores (gk_sketch_tc.cu) ------------------------
+// bf16 operator whose rows start on 16-byte boundaries (the TMA's requirement)
+bool sketch_tc_ok(const void *A, int64_t m, int64_t n, int64_t ld);
+// per 128-row chunk c of A: gpart[c * 528 + e] = the chunk's Gram entries of Y = scale A Omega
+// (upper triangle, row-major order), fpart[c] = its ||A_c||_F^2; omT = Omega^T in bf16,
+// 32 x nk (nk a multiple of 64, zero past n); *err (zeroed by the caller) != 0 when a bounded
+// wait gave up
+cudaError_t sketch_tc(const void *A, int64_t m, int64_t n, int64_t ld, double scale, const void *omT, int64_t nk,
+                      double *gpart, double *fpart, int *err, cudaStream_t s);
+
 // ---- learned predictor (gk_predict.cu) -------------------------------------
 // Krylov dimension for the top-k partial SVD of the dense device operator A from its sketch
 // features: ceil(exp(out_K)) + 2, clamped to [k + 2, min(m, n, 500)].

@@ -727,9 +727,14 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
                b_it = up(sizeof(SkItem) * nitems), b_first = up(sizeof(int) * (count + 1)),
                b_g = up(sizeof(double) * (size_t)nitems * kTri), b_f = up(sizeof(double) * nitems),
                b_ot = mma_ok ? up(sizeof(__nv_bfloat16) * (size_t)nk * kS) : 0,
-               b_gs = up(sizeof(double) * (size_t)count * (kTri + 1));
+               b_gs = up(sizeof(double) * (size_t)count * (kTri + 1)), b_err = up(sizeof(int));
+  // the tensor-core form (opt-in): one bf16 operator whose rows the TMA can address
+  const bool tc = mma_ok && count == 1 && opts && (opts->flags & GK_FLAG_SKETCH_TC) &&
+                  sketch_tc_ok(A[0].vals, A[0].m, A[0].n, A[0].ld);
+  if (opts && (opts->flags & GK_FLAG_SKETCH_TC) && !tc) return GK_INVALID_ARG;
   char *base = nullptr;
-  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f + b_ot + b_gs, s) != cudaSuccess) {
+  if (cudaMallocAsync((void **)&base, b_om + b_pr + b_it + b_first + b_g + b_f + b_ot + b_gs + b_err, s) !=
+      cudaSuccess) {
     cudaGetLastError();
     return GK_OUT_OF_MEMORY;
   }
@@ -741,7 +746,8 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
   double *fpart = (double *)(base + b_om + b_pr + b_it + b_first + b_g);
   __nv_bfloat16 *omT = (__nv_bfloat16 *)(base + b_om + b_pr + b_it + b_first + b_g + b_f);
   double *gsum = (double *)(base + b_om + b_pr + b_it + b_first + b_g + b_f + b_ot);
-  int rc = GK_OK;
+  int *derr = (int *)(base + b_om + b_pr + b_it + b_first + b_g + b_f + b_ot + b_gs);
+  int rc = GK_OK, herr = 0;
   do {
     if ((rc = check(cudaMemcpyAsync(dpr, pr.data(), sizeof(SkProb) * count, cudaMemcpyHostToDevice, s)))) break;
     if ((rc = check(cudaMemcpyAsync(dit, items.data(), sizeof(SkItem) * nitems, cudaMemcpyHostToDevice, s)))) break;
@@ -750,7 +756,13 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
     GK_LAUNCH(k_omega<<<(int)std::min<int64_t>(4096, (nmax * kS + 255) / 256), 256, 0, s>>>(om, nmax, seed));
     if (mma_ok) {  // bf16 rows on 16-byte boundaries: the tensor pipe, Omega rounded to bf16
       GK_LAUNCH(k_omega_t_bf16<<<(int)std::min<int64_t>(4096, (nk * kS + 255) / 256), 256, 0, s>>>(om, nmax, nk, omT));
-      GK_LAUNCH(k_sketch_mma<<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, omT, nk, gpart, fpart));
+      if (tc) {
+        if ((rc = check(cudaMemsetAsync(derr, 0, sizeof(int), s)))) break;
+        if ((rc = check(sketch_tc(A[0].vals, A[0].m, A[0].n, A[0].ld, A[0].scale, omT, nk, gpart, fpart, derr, s))))
+          break;
+      } else {
+        GK_LAUNCH(k_sketch_mma<<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, omT, nk, gpart, fpart));
+      }
     } else switch (dtype0) {
       case GK_F64: GK_LAUNCH(k_sketch_gram<double><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
       case GK_F32: GK_LAUNCH(k_sketch_gram<float><<<nitems, kSkThreads, 0, s>>>(dpr, dit, nitems, om, gpart, fpart)); break;
@@ -762,7 +774,9 @@ extern "C" int gk_sketch_batched(const gk_matrix *A, int count, uint64_t seed, f
     GK_LAUNCH(k_sketch_sum<<<dim3((kTri + 1 + 127) / 128, count), 128, 0, s>>>(dfirst, count, gpart, fpart, gsum));
     GK_LAUNCH(k_sketch_eig<<<count, 32, 0, s>>>(dpr, count, gsum, features));
     if ((rc = check(cudaGetLastError()))) break;
+    if (tc && (rc = check(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s)))) break;
     rc = check(cudaStreamSynchronize(s));
+    if (rc == GK_OK && herr != 0) rc = GK_TIMEOUT;
   } while (0);
   cudaFreeAsync(base, s);
   cudaStreamSynchronize(s);

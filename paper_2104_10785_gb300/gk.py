@@ -28,6 +28,7 @@ GK_FLAG_FUSED = 4
 GK_FLAG_REFINE = 8
 GK_FLAG_ORTH_F64 = 16
 GK_FLAG_PERSISTENT = 32
+GK_FLAG_SKETCH_TC = 64
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -644,15 +645,18 @@ def _stream_opts(device, stream=None):
     return o
 
 
-def gk_sketch_batched(mats, seed: int = 2104107, stream=None):
-    """35 sketch features per dense device operator (count x 35 float32, device)."""
+def gk_sketch_batched(mats, seed: int = 2104107, stream=None, tcgen05: bool = False):
+    """35 sketch features per dense device operator (count x 35 float32, device).
+    tcgen05: the tensor-core form for one bf16 operator (GK_FLAG_SKETCH_TC)."""
     n = len(mats)
     arr = (gk_matrix * n)()
     for i, A in enumerate(mats):
         arr[i], _ = make_matrix(A)
     feats = torch.empty((n, GK_FEATURES), dtype=torch.float32, device=mats[0].device)
-    st = lib().gk_sketch_batched(arr, n, C.c_uint64(seed & (2**64 - 1)), _ptr(feats),
-                                 C.byref(_stream_opts(mats[0].device, stream)))
+    o = _stream_opts(mats[0].device, stream)
+    if tcgen05:
+        o.flags |= GK_FLAG_SKETCH_TC
+    st = lib().gk_sketch_batched(arr, n, C.c_uint64(seed & (2**64 - 1)), _ptr(feats), C.byref(o))
     if st < 0:
         raise GKError(st, "gk_sketch_batched")
     return feats
