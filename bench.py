@@ -1207,14 +1207,17 @@ def profile_case(args):
     --case batched: the first --count problems of the 512-problem batched recipe; `reps` rounds
     of the learned pipeline's sketch and its batched partial SVD with the committed network's
     (rank, K); prints the operator bytes the last solve streamed.
-    --case sketch: `reps` calls of gk_sketch_batched on the same kind of operator (one problem)."""
+    --case sketch: `reps` calls of gk_sketch_batched on the same kind of operator (one problem;
+    --tcgen05: the tensor-core form).
+    --case block: `reps` calls of gk_block_numrank (block size --s, --kmax block steps, eps 1e-8)
+    on the same kind of operator."""
     import torch
 
     import paper_2104_10785_gb300 as gk
     import synth
 
     torch.cuda.set_device(0)
-    if args.case in ("products", "psvd", "sketch"):
+    if args.case in ("products", "psvd", "sketch", "block"):
         dt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32, "f64": torch.float64}[args.dtype]
         g = torch.Generator(device="cuda").manual_seed(1)
         A = torch.randn(args.m, args.n, generator=g, device="cuda", dtype=torch.float32).to(dt)
@@ -1225,7 +1228,9 @@ def profile_case(args):
                 gk.gk_matvec(A, x)
                 gk.gk_matvec(A, y, trans=True)
             elif args.case == "sketch":
-                gk.gk_sketch_batched([A], seed=1)
+                gk.gk_sketch_batched([A], seed=1, tcgen05=args.tcgen05)
+            elif args.case == "block":
+                gk.gk_block_numrank(A, args.s, 1e-8, args.kmax)
             else:
                 gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0, fused=args.fused)
     elif args.case == "batched":
@@ -1262,7 +1267,7 @@ def main():
                     help="time the default workload at its fixed Krylov dimension instead of the learned one")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this kernel")
-    ap.add_argument("--case", default=None, choices=["products", "psvd", "batched", "sketch"],
+    ap.add_argument("--case", default=None, choices=["products", "psvd", "batched", "sketch", "block"],
                     help="run one kernel family on seeded inputs for an ncu capture, then exit")
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "f32", "f64"])
     ap.add_argument("--m", type=int, default=40000)
@@ -1270,6 +1275,9 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--fused", action="store_true", help="--case psvd: run the fused sweep (GK_FLAG_FUSED)")
+    ap.add_argument("--tcgen05", action="store_true", help="--case sketch: the tensor-core form (GK_FLAG_SKETCH_TC)")
+    ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")
+    ap.add_argument("--kmax", type=int, default=16, help="--case block: block steps")
     args = ap.parse_args()
     if args.case is not None:
         profile_case(args)
