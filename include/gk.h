@@ -78,9 +78,9 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               counters; reserved = 0. */
 #define GK_FLAG_SKETCH_TC 64 /* gk_sketch_batched, one bf16 operator with rows on 16-byte boundaries:
                               Y = A Omega on the tcgen05 tensor cores with TMA-staged tiles and the
-                              accumulator in tensor memory, instead of mma.sync.  Experimental: not
-                              yet run on a GPU; returns GK_TIMEOUT if one of its bounded waits gives
-                              up. */
+                              accumulator in tensor memory, instead of mma.sync (GK_INVALID_ARG for
+                              any other request with this flag).  Experimental: not yet run on a GPU;
+                              returns GK_TIMEOUT if one of its bounded waits gives up. */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).
@@ -249,6 +249,10 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
  * error. */
 int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, int kmax, const gk_opts *opts, int *rank,
                      double *sigma, int *steps, gk_info *info);
+
+/* Device workspace (bytes) gk_block_numrank needs for this operator, s, kmax and opts
+ * (0 for invalid arguments or without a device). */
+size_t gk_block_numrank_workspace(const gk_matrix *A, int s, int kmax, const gk_opts *opts);
 
 /* F-SVD as printed (Algorithm 2): k steps of Algorithm 1 (lower-bidiagonal GK
  * with reorthogonalization; only an exact zero norm ends them early), then for

@@ -8,6 +8,7 @@ from .gk import (  # noqa: F401
     CSR,
     GKError,
     gk_block_numrank,
+    gk_block_numrank_workspace,
     gk_fsvd,
     gk_matvec,
     gk_mlp_forward,

@@ -1115,8 +1115,8 @@ struct BlockBufs {
   bool acc;  // dense reduced-precision operator: block products in one pass (double-f32)
 };
 
-size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const OpStage &st, bool host_q0, char *base,
-                    BlockBufs *b, Op *op) {
+size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const OpStage &st, char *base, BlockBufs *b,
+                    Op *op) {
   Carve cv{base, 0};
   const int64_t m = A->m, n = A->n, ldu = round_up(m, 32), ldv = round_up(n, 32), mx = m > n ? m : n;
   const int64_t lmax = ldu > ldv ? ldu : ldv;
@@ -1149,7 +1149,7 @@ size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const O
   b->sweeps = cv.take<int>(1);
   b->rank = cv.take<int>(1);
   b->split = b->acc ? cv.take<float>(accurate_floats(*op, s)) : nullptr;
-  b->q0 = host_q0 ? cv.take<double>((size_t)m * s) : nullptr;
+  b->q0 = cv.take<double>((size_t)m * s);  // staging of a host start block
   b->Qs = b->df ? cv.take<float2>((size_t)ldu * cols) : nullptr;
   b->Ps = b->df ? cv.take<float2>((size_t)ldv * cols) : nullptr;
   b->ws2 = b->df ? cv.take<float2>(lmax) : nullptr;
@@ -1292,12 +1292,12 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   BlockBufs b;
   b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   b.acc = accurate_ok(op);
-  const size_t bytes = block_layout(Ain, s, kb, d, stg, host_q0, nullptr, &b, &op);
+  const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
   Workspace ws;
   rc = acquire(ws, bytes, o, st);
   if (rc) return rc;
   op = make_op(Ain);
-  block_layout(Ain, s, kb, d, stg, host_q0, ws.base, &b, &op);
+  block_layout(Ain, s, kb, d, stg, ws.base, &b, &op);
   rc = stage_copy(Ain, stg, op, st);
   if (rc) return rc;
   const int64_t ldu = round_up(m, 32), ldv = round_up(n, 32), cols = (kb + 1) * s;
@@ -1739,6 +1739,21 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
                gk_info *info) {
   NvtxRange r("gk_numrank");
   return numrank_impl(A, eps, kmax, opts, rank, sigma, info);
+}
+
+size_t gk_block_numrank_workspace(const gk_matrix *A, int s, int kmax, const gk_opts *oin) {
+  Dev d;
+  if (check_matrix(A) != GK_OK || s < 1 || s > kBlockMaxS || s > A->m || s > A->n) return 0;
+  int64_t kb = 0;
+  if (block_steps(A, s, kmax, &kb) != GK_OK || !get_device(&d)) return 0;
+  const gk_opts o = oin ? *oin : defaults();
+  OpStage st;
+  if (stage_plan(A, &st) != GK_OK) return 0;
+  Op op = make_op(A);
+  BlockBufs b;
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
+  b.acc = accurate_ok(op);
+  return block_layout(A, s, kb, d, st, nullptr, &b, &op);
 }
 
 int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, int kmax, const gk_opts *opts, int *rank,

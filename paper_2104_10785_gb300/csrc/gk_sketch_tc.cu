@@ -310,11 +310,19 @@ cudaError_t sketch_tc(const void *A, int64_t m, int64_t n, int64_t ld, double sc
   if (!sketch_tc_ok(A, m, n, ld) || nk % kTcK != 0 || nk < n) return cudaErrorInvalidValue;
   CUtensorMap tmA, tmO;
   if (!tc_map(&tmA, A, m, n, ld, kTcRows) || !tc_map(&tmO, omT, kTcN, nk, nk, kTcN)) return cudaErrorNotSupported;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once,
-                 [] { attr_err = cudaFuncSetAttribute(k_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem); });
-  if (attr_err != cudaSuccess) return attr_err;
+  static std::mutex attr_mu;
+  static int attr_dev = -1;  // the device whose shared-memory limit for the kernel was raised
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(attr_mu);
+    if (attr_dev != dev) {
+      e = cudaFuncSetAttribute(k_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+      if (e != cudaSuccess) return e;
+      attr_dev = dev;
+    }
+  }
   const int nitems = (int)((m + kTcRows - 1) / kTcRows);
   GK_LAUNCH(k_sketch_tc<<<nitems, kTcThreads, kTcSmem, s>>>(tmA, tmO, m, (int)(nk / kTcK), scale, gpart, fpart, err));
   return cudaGetLastError();

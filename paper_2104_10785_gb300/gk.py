@@ -127,6 +127,8 @@ def lib():
             L.gk_block_numrank.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_double, C.c_int, P(gk_opts),
                                            P(C.c_int), C.c_void_p, P(C.c_int), P(gk_info)]
             L.gk_block_numrank.restype = C.c_int
+            L.gk_block_numrank_workspace.argtypes = [P(gk_matrix), C.c_int, C.c_int, P(gk_opts)]
+            L.gk_block_numrank_workspace.restype = C.c_size_t
             L.gk_matvec.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
             L.gk_matvec.restype = C.c_int
             L.gk_residuals.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -457,6 +459,13 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
         raise GKError(st, "gk_block_numrank")
     d = info.as_dict()
     return r.value, (sig[: d["kprime"]] if sig is not None else None), steps.value, st, d
+
+
+def gk_block_numrank_workspace(A, s: int, kmax: int = 0, *, orth_f64: bool = False) -> int:
+    M, _ = make_matrix(A)
+    o = default_opts()
+    o.flags = GK_FLAG_ORTH_F64 if orth_f64 else 0
+    return int(lib().gk_block_numrank_workspace(C.byref(M), int(s), int(kmax), C.byref(o)))
 
 
 def gk_matvec(A, x, trans: bool = False, *, stream=None, scale: float = 1.0):

@@ -150,6 +150,10 @@ def test_block_numrank_checks_arguments_before_the_device():
     for bad in (dict(s=0), dict(s=33), dict(s=31), dict(eps=-1.0), dict(eps=float("nan")), dict(eps=float("inf")),
                 dict(absolute=1), dict(s=4, kmax=256), dict(s=1, kmax=1024)):
         assert call(**bad) == raw.GK_INVALID_ARG, bad
+    for s_bad in (0, 33, 31):
+        assert L.gk_block_numrank_workspace(C.byref(M), s_bad, 0, None) == 0
+    assert L.gk_block_numrank_workspace(C.byref(M), 4, 256, None) == 0
     if not torch.cuda.is_available():
         assert call() == raw.GK_NO_DEVICE
         assert call(s=4, kmax=255) == raw.GK_NO_DEVICE  # (255 + 1) * 4 = 1024
+        assert L.gk_block_numrank_workspace(C.byref(M), 4, 0, None) == 0
