@@ -318,6 +318,12 @@ def default_opts() -> gk_opts:
     return o
 
 
+def _check_start(start, m):
+    """The library reads m values from a start vector: refuse any other length here."""
+    if start is not None and start.numel() != m:
+        raise ValueError(f"start vector must have m = {m} entries, got {start.numel()}")
+
+
 def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, eps_absolute=False, seed=None,
           start=None, stream=None, workspace=None, profile=False, fused=False, refine=False, orth_f64=False,
           persistent=False):
@@ -363,6 +369,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     chooses the Krylov dimension from A's sketch when krylov_dim is 0 (info["kprime"] = K used).
     """
     M, keep_a = make_matrix(A, scale)
+    _check_start(start, M.m)
     dev = A.device
     if dev.type != "cuda" and not torch.cuda.is_available():
         raise RuntimeError("gk_psvd needs a CUDA device (no host fallback)")
@@ -392,6 +399,7 @@ def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = No
     (route 1: U = Q X; route 0: u_i = A v_i / sigma_i).  Returns (U m x r, S r, V n x r, status,
     info dict); outputs live where A lives."""
     M, keep_a = make_matrix(A, scale)
+    _check_start(start, M.m)
     dev = A.device
     if dev.type != "cuda" and not torch.cuda.is_available():
         raise RuntimeError("gk_fsvd needs a CUDA device (no host fallback)")
@@ -414,6 +422,7 @@ def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = Fals
                orth_f64: bool = False):
     """Numerical rank by Algorithm 3.  Returns (rank, sigma(B) or None, status, info dict)."""
     M, keep_a = make_matrix(A, scale)
+    _check_start(start, M.m)
     dev = A.device
     if dev.type != "cuda" and not torch.cuda.is_available():
         raise RuntimeError("gk_numrank needs a CUDA device (no host fallback)")
@@ -437,6 +446,8 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
     """Numerical rank from a block of s start vectors (block Algorithm 1 + Algorithm 3).
     start: optional m x s start block.  Returns (rank, sigma(B) or None, block steps, status, info dict)."""
     M, keep_a = make_matrix(A, scale)
+    if start is not None and tuple(start.shape) != (M.m, int(s)):
+        raise ValueError(f"start block must be m x s = {M.m} x {int(s)}, got {tuple(start.shape)}")
     dev = A.device
     if dev.type != "cuda" and not torch.cuda.is_available():
         raise RuntimeError("gk_block_numrank needs a CUDA device (no host fallback)")
@@ -571,6 +582,7 @@ def gk_psvd_batched(problems, *, seed=None, max_restarts=None, reorth_passes=Non
         V = Vbig[voff[i]:voff[i + 1]].view(k, A.shape[1])
         st = None
         if pr.get("start") is not None:
+            _check_start(pr["start"], A.shape[0])
             st = pr["start"].to(torch.float64).contiguous()
             keep.append(st)
         items[i].A = M
@@ -617,6 +629,7 @@ def gk_numrank_batched(problems, *, seed=None, reorth_passes=None, eps_absolute=
         sg = torch.zeros(cap + 2, dtype=torch.float64, device=A.device) if want_sigma else None
         st = None
         if pr.get("start") is not None:
+            _check_start(pr["start"], A.shape[0])
             st = pr["start"].to(torch.float64).contiguous()
             keep.append(st)
         items[i].A = M

@@ -157,3 +157,33 @@ def test_block_numrank_checks_arguments_before_the_device():
         assert call() == raw.GK_NO_DEVICE
         assert call(s=4, kmax=255) == raw.GK_NO_DEVICE  # (255 + 1) * 4 = 1024
         assert L.gk_block_numrank_workspace(C.byref(M), 4, 0, None) == 0
+
+
+def test_block_numrank_binding_checks_the_start_block_shape():
+    """The binding refuses a start block that is not m x s before anything reaches the library
+    (the library reads m * s values from it)."""
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+
+    A = torch.zeros(10, 6, dtype=torch.float64)
+    for bad in (torch.zeros(10, 3), torch.zeros(9, 2), torch.zeros(20)):
+        with pytest.raises(ValueError):
+            gk.gk_block_numrank(A, 2, start=bad)
+
+
+def test_bindings_check_the_start_vector_length():
+    """gk_psvd, gk_fsvd and gk_numrank refuse a start vector whose length is not m before the
+    library would read m values from it."""
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+
+    A = torch.zeros(10, 6, dtype=torch.float64)
+    bad = torch.zeros(9, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        gk.gk_psvd(A, 2, start=bad)
+    with pytest.raises(ValueError):
+        gk.gk_fsvd(A, 3, 2, start=bad)
+    with pytest.raises(ValueError):
+        gk.gk_numrank(A, 1e-8, start=bad)
