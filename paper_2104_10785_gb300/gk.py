@@ -482,6 +482,8 @@ def gk_block_numrank_workspace(A, s: int, kmax: int = 0, *, orth_f64: bool = Fal
 def gk_matvec(A, x, trans: bool = False, *, stream=None, scale: float = 1.0):
     """y = A x (or A^T x) through the library's product kernels; x, y f64."""
     M, keep_a = make_matrix(A, scale)
+    if x.numel() != (M.m if trans else M.n):
+        raise ValueError(f"x must have {M.m if trans else M.n} entries, got {x.numel()}")
     dev = A.device
     xx = x.to(torch.float64).contiguous()
     y = torch.empty(M.n if trans else M.m, dtype=torch.float64, device=xx.device)
@@ -499,6 +501,8 @@ def gk_matvec_static(A, x, out, trans: bool = False, *, stream=None, scale: floa
     M, keep_a = make_matrix(A, scale)
     if x.dtype != torch.float64 or not x.is_contiguous() or out.dtype != torch.float64 or not out.is_contiguous():
         raise ValueError("x and out must be contiguous float64 device tensors")
+    if x.numel() != (M.m if trans else M.n) or out.numel() != (M.n if trans else M.m):
+        raise ValueError("x and out must have the lengths of the product's input and output")
     o = gk_opts()
     lib().gk_default_opts(C.byref(o))
     s = stream if stream is not None else torch.cuda.current_stream(out.device)
@@ -511,6 +515,8 @@ def gk_residuals(A, U, S, V, *, stream=None, scale: float = 1.0):
     M, keep_a = make_matrix(A, scale)
     dev = A.device
     k = S.numel()
+    if tuple(U.shape) != (M.m, k) or tuple(V.shape) != (M.n, k):
+        raise ValueError(f"U must be {M.m} x {k} and V {M.n} x {k}, got {tuple(U.shape)} and {tuple(V.shape)}")
     Uc = U.T.contiguous().to(torch.float64)
     Vc = V.T.contiguous().to(torch.float64)
     Sc = S.to(torch.float64).contiguous()
@@ -729,9 +735,17 @@ def gk_rsgd_batched(X, Vd, y, W, batches, q1, eta: float, lam: float, r: int, k_
             raise ValueError("X, Vd, y, W, q1 must be contiguous float64 CUDA tensors")
     if batches.dtype != torch.int32 or not batches.is_contiguous() or batches.device.type != "cuda":
         raise ValueError("batches must be a contiguous int32 CUDA tensor")
+    if X.dim() != 3 or Vd.dim() != 3 or batches.dim() != 3:
+        raise ValueError("X, Vd and batches must be 3-D")
     P, N, d1 = X.shape
     d2 = Vd.shape[2]
     steps, _, b = batches.shape
+    if (tuple(Vd.shape) != (P, N, d2) or tuple(y.shape) != (P, N) or tuple(W.shape) != (P, d1, d2)
+            or tuple(q1.shape) != (P, d1) or batches.shape[1] != P):
+        raise ValueError("shapes: X (P, N, d1), Vd (P, N, d2), y (P, N), W (P, d1, d2), q1 (P, d1), "
+                         "batches (steps, P, b)")
+    if batches.numel() and (int(batches.min()) < 0 or int(batches.max()) >= N):
+        raise ValueError("batch indices must lie in [0, N)")
     a = gk_rsgd_args(P=P, N=N, d1=d1, d2=d2, r=int(r), k_inner=int(k_inner), steps=steps, b=b, eta=float(eta),
                      lam=float(lam), X=X.data_ptr(), Vd=Vd.data_ptr(), y=y.data_ptr(), batches=batches.data_ptr(),
                      q1=q1.data_ptr(), W=W.data_ptr())

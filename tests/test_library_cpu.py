@@ -187,3 +187,21 @@ def test_bindings_check_the_start_vector_length():
         gk.gk_fsvd(A, 3, 2, start=bad)
     with pytest.raises(ValueError):
         gk.gk_numrank(A, 1e-8, start=bad)
+
+
+def test_bindings_check_vector_and_factor_shapes():
+    """gk_matvec and gk_residuals refuse vectors and factors whose sizes do not match the
+    operator before the library would read past them."""
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+
+    A = torch.zeros(10, 6, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        gk.gk_matvec(A, torch.zeros(10, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        gk.gk_matvec(A, torch.zeros(6, dtype=torch.float64), trans=True)
+    with pytest.raises(ValueError):
+        gk.gk_residuals(A, torch.zeros(10, 2), torch.zeros(2), torch.zeros(5, 2))
+    with pytest.raises(ValueError):
+        gk.gk_residuals(A, torch.zeros(10, 3), torch.zeros(2), torch.zeros(6, 2))
