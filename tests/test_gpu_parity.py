@@ -352,6 +352,22 @@ def test_psvd_wide_and_tiny_shapes():
         np.testing.assert_allclose(S.cpu().numpy(), np.linalg.svd(A, compute_uv=False)[:k], rtol=1e-11, atol=1e-13)
 
 
+def test_psvd_of_the_transpose_swaps_the_factors():
+    """psvd(A^T) = swap(psvd(A)): the same singular values with the left and right vectors
+    exchanged (the method is shape-agnostic; here a tall and a wide operator)."""
+    sig = synth.sigma_geometric(700, 0.9)
+    A, _, _ = synth.prescribed_spectrum(1500, 700, sig, seed=41, dtype=np.float64)
+    M = gk()
+    U1, S1, V1, st1, _ = M.gk_psvd(cuda(A), 8, 1e-10, krylov_dim=30)
+    U2, S2, V2, st2, _ = M.gk_psvd(cuda(A.T), 8, 1e-10, krylov_dim=30)
+    assert st1 == st2 == 0
+    np.testing.assert_allclose(S1.cpu().numpy(), sig[:8], rtol=1e-10)
+    np.testing.assert_allclose(S2.cpu().numpy(), sig[:8], rtol=1e-10)
+    # vectors to ~tol sigma_1 / gap (gap >= 0.1 sigma_8 here)
+    assert angle_err(U1.cpu().numpy(), V2.cpu().numpy()) < 1e-7
+    assert angle_err(V1.cpu().numpy(), U2.cpu().numpy()) < 1e-7
+
+
 def test_psvd_zero_and_rank_deficient():
     M = gk()
     Z = torch.zeros((30, 20), dtype=torch.float64, device="cuda")
