@@ -201,13 +201,15 @@ class near_gpu:
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def make_workload(name, device, want_plain=True):
+def make_workload(name, device, want_plain=True, seed=None):
     import torch
 
     import synth
 
     w = dict(synth.WORKLOADS[name])
     w["name"] = name
+    if seed is not None:  # another draw of the same recipe (operator, start vector)
+        w["seed"] = int(seed)
     t0 = time.time()
     if w["kind"] == "spectrum_pow":
         sig = synth.sigma_power(w["n"], w["e"])
@@ -479,7 +481,7 @@ def run_reference(args, rank, world):
             "cpu_baseline": cpu,
             "e2e": {"value": cpu["value"], "unit": "problem-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         })
-    w = make_workload(args.workload, device, want_plain=False)
+    w = make_workload(args.workload, device, want_plain=False, seed=args.seed)
     K = w.get("K", 0)
     if w["name"] == "dense_bf16_100000x40000_top100":
         # the Krylov dimension of the measured arm's configuration: the committed network's choice
@@ -535,7 +537,7 @@ def run_gk(args, rank, world):
         return run_numrank_headline(args, rank, world, device)
     if args.workload == "rsgd_f64_64x784x256_rank5":
         return run_rsgd_headline(args, rank, world, device)
-    w = make_workload(args.workload, device, want_plain=not args.no_plain)
+    w = make_workload(args.workload, device, want_plain=not args.no_plain, seed=args.seed)
     k, K, tol = w["k"], w["K"], w["tol"]
     A = w["A"]
     stream = torch.cuda.current_stream(device)
@@ -832,7 +834,7 @@ def run_gk(args, rank, world):
         "dtype": "bf16" if a_dtype == torch.bfloat16 else ("f64" if a_dtype == torch.float64 else "f32"),
         "data": "synthetic",
         "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": Kused, "tol": tol,
-                   "krylov": "learned (sketch + network in every step)" if kparams is not None else "fixed",
+                   "seed": w["seed"], "krylov": "learned (sketch + network in every step)" if kparams is not None else "fixed",
                    "storage": w["dtype"], "accumulate": "f32 runs combined in f64; f64 basis, small SVD, residuals",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": ("inputs larger than L2 (operator %.2f GB)" % (a_bytes / 1e9)) if flush is None else
@@ -859,7 +861,7 @@ def run_numrank_headline(args, rank, world, device):
     import paper_2104_10785_gb300 as gk
     import synth
 
-    w = make_workload(args.workload, device, want_plain=False)
+    w = make_workload(args.workload, device, want_plain=False, seed=args.seed)
     A = w["A"]
     stream = torch.cuda.current_stream(device)
     eps, kmax = w["eps"], 512
@@ -1263,6 +1265,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--seed", type=int, default=None,
+                    help="draw the workload (operator and start vector) with this seed instead of its recipe's")
     ap.add_argument("--fixed-krylov", action="store_true",
                     help="time the default workload at its fixed Krylov dimension instead of the learned one")
     ap.add_argument("--traffic", type=float, default=None,
