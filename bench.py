@@ -418,7 +418,7 @@ def batched_leg(device, steps, warmup, keep_mats=False):
     hbm, peak_kind = peaks()
     # DRAM bytes over algorithmic bytes from a capture of the first 64 problems, scaled to this
     # launch by the bytes it streams (each product reads its operator once at either size)
-    ratio = profiled_traffic("k_batched<float>", "batched_f32_512_rank5to64", "gk_batched.cu", "ratio")
+    ratio = profiled_traffic("k_batched<float>", "batched_f32_512_rank5to64", "gk_batched_kernel.cuh", "ratio")
     res["roofline"] = {"bound": "hbm", "achieved": kbytes / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                        "frac": kbytes / (kms / 1e3) / 1e9 / hbm,
                        "traffic": int(ratio * kbytes) if ratio is not None else None, "kernel": "k_batched<float>",
