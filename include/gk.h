@@ -81,6 +81,11 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               accumulator in tensor memory, instead of mma.sync (GK_INVALID_ARG for
                               any other request with this flag).  Experimental: not yet run on a GPU;
                               returns GK_TIMEOUT if one of its bounded waits gives up. */
+#define GK_FLAG_BDSVD 128 /* gk_psvd: in a cycle without kept Ritz vectors (the first, or every cycle when
+                              the Krylov dimension is reached without a restart) the projected matrix is
+                              upper bidiagonal: its SVD by implicitly shifted Golub-Kahan SVD steps on one
+                              CTA instead of the cluster Jacobi (K <= 1024).  Experimental: the step and
+                              rotation code is tested on the host; the kernel has not yet run on a GPU. */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).

@@ -373,6 +373,7 @@ struct PsvdPlan {
   bool fused;   // one pass over A per step (gk_fused.cu)
   bool refine;  // FP64-grade check of the returned triplets (GK_FLAG_REFINE)
   bool df;      // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
+  bool bdsvd;   // cycles without kept vectors: the bidiagonal B by Golub-Kahan SVD steps (GK_FLAG_BDSVD)
 };
 
 struct PsvdBufs {
@@ -477,6 +478,7 @@ int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
   p->fused = false;
   p->refine = (o.flags & GK_FLAG_REFINE) != 0;
   p->df = (o.flags & GK_FLAG_ORTH_F64) == 0;
+  p->bdsvd = (o.flags & GK_FLAG_BDSVD) != 0 && K <= kBdMaxK;
   return GK_OK;
 }
 
@@ -787,8 +789,12 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
         inf.steps++;
       }
       prof.begin(PC_SMALL);
-      GK_CUDA(assemble_B(b.Bm, K, l, b.sigma, b.rho, b.alpha, b.beta, b.ctl, s));
-      GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.svd_nrm, b.svd_pos, b.sweeps, b.ctl, s));
+      if (l == 0 && p.bdsvd) {  // B is upper bidiagonal (alpha on the diagonal, beta above it)
+        GK_CUDA(bd_svd(b.alpha, b.beta, K, b.sigma, b.X, b.Y, b.Bm, b.Yw, b.sweeps, b.ctl, s));
+      } else {
+        GK_CUDA(assemble_B(b.Bm, K, l, b.sigma, b.rho, b.alpha, b.beta, b.ctl, s));
+        GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.svd_nrm, b.svd_pos, b.sweeps, b.ctl, s));
+      }
       GK_CUDA(ritz_check(b.sigma, b.X, K, k, b.beta + (K - 1), tol_ritz, b.rho, b.out, b.ctl, s));
       prof.end();
       rc = read_ctl(b.ctl, b.out, &hc, s);

@@ -64,9 +64,11 @@ __host__ __device__ inline void bd_init(BdState *st, const double *d, const doub
   st->max_steps = 30 * n * n + 100;
 }
 
-// One step.  Returns 0 when B is diagonal (done), 1 after recording a step's rotations in
-// rotL[0..*nL) (left: rows) and rotR[0..*nR) (right: columns), -1 when the step budget is
-// spent.  rotL and rotR need room for n - 1 rotations each.
+// One step.  Returns 0 when B is diagonal (done), -1 when the step budget is spent, else the
+// step's rotations are in rotL[0..*nL) (left: rows) and rotR[0..*nR) (right: columns) and the
+// return value says their shape: 1 for a Golub-Kahan step (both lists are (k, k+1) for
+// k = lo, lo+1, ..., hi-1, so bd_apply_chase may apply them), 2 for a zero-diagonal chase
+// (any pairs: bd_apply_row).  rotL and rotR need room for n - 1 rotations each.
 __host__ __device__ inline int bd_step(double *d, double *e, BdState *st, BdRot *rotL, int *nL, BdRot *rotR, int *nR) {
   const int n = st->n;
   *nL = 0;
@@ -116,7 +118,7 @@ __host__ __device__ inline int bd_step(double *d, double *e, BdState *st, BdRot 
         }
       }
     }
-    return 1;
+    return 2;
   }
   // Wilkinson shift from the trailing 2 x 2 of B^T B on the block
   const double dm = d[hi - 1], dn = d[hi], em = e[hi - 1];
@@ -162,6 +164,21 @@ __host__ __device__ inline void bd_apply_row(double *x, long long stride, const 
     *pi = R.c * a + R.s * b;
     *pj = -R.s * a + R.c * b;
   }
+}
+
+// the rotations of a Golub-Kahan step (pairs (k, k+1), k increasing from rot[0].i) on one row:
+// each entry is read once and written once, the running entry carried in a register
+__host__ __device__ inline void bd_apply_chase(double *x, long long stride, const BdRot *rot, int nrot) {
+  if (nrot <= 0) return;
+  const int k0 = rot[0].i;
+  double carry = x[(long long)k0 * stride];
+  for (int t = 0; t < nrot; ++t) {
+    const double b = x[(long long)(k0 + t + 1) * stride];
+    const double c = rot[t].c, s = rot[t].s;
+    x[(long long)(k0 + t) * stride] = c * carry + s * b;
+    carry = -s * carry + c * b;
+  }
+  x[(long long)(k0 + nrot) * stride] = carry;
 }
 
 }  // namespace gk

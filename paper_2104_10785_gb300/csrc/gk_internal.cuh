@@ -261,6 +261,11 @@ cudaError_t scale_inv(double *y, int64_t len, const double *d, cudaStream_t s);
 // sweep limit was reached).
 cudaError_t small_svd(double *Bm, double *Yw, int K, double *sigma, double *X, double *Y, double *nrm, int *pos,
                       int *sweeps, const Ctl *ctl, cudaStream_t s);
+// The same outputs for an upper-bidiagonal B (alpha on the diagonal, beta[0..K-1) above it) by
+// Golub-Kahan SVD steps on one CTA (gk_bdsvd.cuh); Xw, Yw: K x K work.  K <= kBdMaxK.
+constexpr int kBdMaxK = 1024;
+cudaError_t bd_svd(const double *alpha, const double *beta, int K, double *sigma, double *X, double *Y, double *Xw,
+                   double *Yw, int *sweeps, const Ctl *ctl, cudaStream_t s);
 // Restart bookkeeping: rho_i = betaK X_{K,i} (all i < K), and
 // out[0] = max_{i<k} |rho_i|, out[1] = sigma_1, out[2] = converged (0/1).
 cudaError_t ritz_check(const double *sigma, const double *X, int K, int k, const double *betaK, double tol,

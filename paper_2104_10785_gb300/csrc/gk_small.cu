@@ -8,8 +8,11 @@
 #include <float.h>
 #include <math.h>
 
+#include <mutex>
+
 #include <cooperative_groups.h>
 
+#include "gk_bdsvd.cuh"
 #include "gk_device.cuh"
 #include "gk_internal.cuh"
 
@@ -226,6 +229,83 @@ __global__ void __launch_bounds__(256) k_bidiag_rank(const double *__restrict__ 
   dev::block_bidiag_rank(alpha, beta, kp, eps, eps_rel, rank, sigma1, sigma, red);
 }
 
+// SVD of the upper-bidiagonal B (d = alpha[0..K), e = beta[0..K-1)) by Golub-Kahan SVD steps
+// (gk_bdsvd.cuh) on one CTA: thread 0 takes the steps, then every thread applies the step's
+// rotations to its rows of the work copies Xw (left) and Yw (right), column-major K x K; at the
+// end the values are made nonnegative (a sign flip of Y's column), ordered descending (stable
+// by index) by counting ranks, and X, Y gathered in that order.  sweeps_out: steps taken
+// (negative if the step budget was spent).
+constexpr int kBdThreads = 256;
+
+__global__ void __launch_bounds__(kBdThreads) k_bdsvd(const double *__restrict__ alpha, const double *__restrict__ beta,
+                                                     int K, double *__restrict__ sigma, double *__restrict__ X,
+                                                     double *__restrict__ Y, double *__restrict__ Xw,
+                                                     double *__restrict__ Yw, int *__restrict__ sweeps_out,
+                                                     const Ctl *ctl) {
+  if (halted(ctl)) return;
+  extern __shared__ __align__(16) unsigned char bd_smem[];
+  double *d = reinterpret_cast<double *>(bd_smem);
+  double *e = d + K;
+  BdRot *rl = reinterpret_cast<BdRot *>(e + K);
+  BdRot *rr = rl + K;
+  int *rank = reinterpret_cast<int *>(rr + K);
+  __shared__ int s_rc, s_nl, s_nr;
+  __shared__ BdState st;
+  const int tid = threadIdx.x;
+  for (int64_t idx = tid; idx < (int64_t)K * K; idx += blockDim.x) {
+    const double v = (idx % K) == (idx / K) ? 1.0 : 0.0;
+    Xw[idx] = v;
+    Yw[idx] = v;
+  }
+  for (int k = tid; k < K; k += blockDim.x) {
+    d[k] = alpha[k];
+    e[k] = k + 1 < K ? beta[k] : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) bd_init(&st, d, e, K);
+  int rc;
+  for (;;) {
+    if (tid == 0) {
+      int nl = 0, nr = 0;
+      s_rc = bd_step(d, e, &st, rl, &nl, rr, &nr);
+      s_nl = nl;
+      s_nr = nr;
+    }
+    __syncthreads();
+    rc = s_rc;
+    if (rc <= 0) break;
+    const int nl = s_nl, nr = s_nr;
+    for (int i = tid; i < K; i += blockDim.x) {
+      if (rc == 1) {
+        bd_apply_chase(Xw + i, K, rl, nl);
+        bd_apply_chase(Yw + i, K, rr, nr);
+      } else {
+        bd_apply_row(Xw + i, K, rl, nl);
+        bd_apply_row(Yw + i, K, rr, nr);
+      }
+    }
+    __syncthreads();  // the rotations are applied before thread 0 records the next step's
+  }
+  for (int k = tid; k < K; k += blockDim.x) {
+    const double a = fabs(d[k]);
+    int r = 0;
+    for (int j = 0; j < K; ++j) {
+      const double b = fabs(d[j]);
+      r += (b > a || (b == a && j < k)) ? 1 : 0;
+    }
+    rank[k] = r;
+  }
+  __syncthreads();
+  for (int k = tid; k < K; k += blockDim.x) sigma[rank[k]] = fabs(d[k]);
+  for (int64_t idx = tid; idx < (int64_t)K * K; idx += blockDim.x) {
+    const int k = (int)(idx / K), i = (int)(idx % K);
+    const int64_t t = (int64_t)rank[k] * K + i;
+    X[t] = Xw[idx];
+    Y[t] = d[k] < 0.0 ? -Yw[idx] : Yw[idx];
+  }
+  if (tid == 0 && sweeps_out) *sweeps_out = rc < 0 ? -st.steps : st.steps;
+}
+
 }  // namespace
 
 cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const double *rho, const double *alpha,
@@ -332,6 +412,27 @@ cudaError_t ritz_gemm(const double *Q, int64_t ldq, int64_t len, int K, const do
   if (ncol <= 0 || len <= 0) return cudaSuccess;
   dim3 grid((unsigned)((len + 255) / 256), (unsigned)((ncol + 15) / 16));
   GK_LAUNCH(k_ritz_gemm<<<grid, 256, 0, s>>>(Q, ldq, len, K, X, ldx, ncol, C, ldc));
+  return cudaGetLastError();
+}
+
+cudaError_t bd_svd(const double *alpha, const double *beta, int K, double *sigma, double *X, double *Y, double *Xw,
+                   double *Yw, int *sweeps, const Ctl *ctl, cudaStream_t s) {
+  if (K < 1 || K > kBdMaxK) return cudaErrorInvalidValue;
+  const size_t per = 2 * sizeof(double) + 2 * sizeof(BdRot) + sizeof(int);
+  static std::mutex mu;
+  static int attr_dev = -1;  // the device whose shared-memory limit for the kernel was raised
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (attr_dev != dev) {
+      e = cudaFuncSetAttribute(k_bdsvd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * kBdMaxK));
+      if (e != cudaSuccess) return e;
+      attr_dev = dev;
+    }
+  }
+  GK_LAUNCH(k_bdsvd<<<1, kBdThreads, per * (size_t)K, s>>>(alpha, beta, K, sigma, X, Y, Xw, Yw, sweeps, ctl));
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ GK_FLAG_REFINE = 8
 GK_FLAG_ORTH_F64 = 16
 GK_FLAG_PERSISTENT = 32
 GK_FLAG_SKETCH_TC = 64
+GK_FLAG_BDSVD = 128
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -326,10 +327,11 @@ def _check_start(start, m):
 
 def _opts(device, krylov_dim=0, keep=0, max_restarts=None, reorth_passes=None, eps_absolute=False, seed=None,
           start=None, stream=None, workspace=None, profile=False, fused=False, refine=False, orth_f64=False,
-          persistent=False):
+          persistent=False, bdsvd=False):
     o = default_opts()
     o.flags = ((GK_FLAG_PROFILE if profile else 0) | (GK_FLAG_FUSED if fused else 0) | (GK_FLAG_REFINE if refine else 0)
-               | (GK_FLAG_ORTH_F64 if orth_f64 else 0) | (GK_FLAG_PERSISTENT if persistent else 0))
+               | (GK_FLAG_ORTH_F64 if orth_f64 else 0) | (GK_FLAG_PERSISTENT if persistent else 0)
+               | (GK_FLAG_BDSVD if bdsvd else 0))
     o.krylov_dim = int(krylov_dim)
     o.keep = int(keep)
     if max_restarts is not None:
@@ -357,7 +359,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
             scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
             refine: bool = False, predictor: "Predictor | None" = None, orth_f64: bool = False,
-            persistent: bool = False):
+            persistent: bool = False, bdsvd: bool = False):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
@@ -367,6 +369,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     triplets' true residuals with FP64-grade products and keeps restarting while one exceeds
     tol (GK_FLAG_REFINE; info["resid_true_max"], info["ms_refine"]).  predictor (a Predictor)
     chooses the Krylov dimension from A's sketch when krylov_dim is 0 (info["kprime"] = K used).
+    bdsvd=True takes the SVD of a cycle's bidiagonal projected matrix by Golub-Kahan SVD steps
+    (GK_FLAG_BDSVD, experimental).
     """
     M, keep_a = make_matrix(A, scale)
     _check_start(start, M.m)
@@ -382,7 +386,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     else:
         U, S, V = out
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
-                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine, orth_f64, persistent)
+                  reorth_passes, False, seed, start, stream, workspace, profile, fused, refine, orth_f64, persistent,
+                  bdsvd)
     if predictor is not None:
         o.predictor = predictor.handle
     info = gk_info()

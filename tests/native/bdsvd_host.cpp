@@ -9,7 +9,8 @@
 #include "../../paper_2104_10785_gb300/csrc/gk_bdsvd.cuh"
 
 extern "C" int bd_svd_host(const double *d_in, const double *e_in, int n, double *sigma, double *X, double *Y,
-                           int *steps) {
+                           int *steps, int *chases) {
+  chases[0] = chases[1] = 0;  // Golub-Kahan steps, zero-diagonal chases
   if (n <= 0) return -2;
   std::vector<double> d(d_in, d_in + n), e(n > 1 ? n - 1 : 1, 0.0);
   for (int k = 0; k + 1 < n; ++k) e[k] = e_in[k];
@@ -23,9 +24,15 @@ extern "C" int bd_svd_host(const double *d_in, const double *e_in, int n, double
     int nl = 0, nr = 0;
     rc = gk::bd_step(d.data(), e.data(), &st, rl.data(), &nl, rr.data(), &nr);
     if (rc <= 0) break;
+    ++chases[rc == 1 ? 0 : 1];
     for (int i = 0; i < n; ++i) {
-      gk::bd_apply_row(Xw.data() + i, n, rl.data(), nl);
-      gk::bd_apply_row(Yw.data() + i, n, rr.data(), nr);
+      if (rc == 1) {  // a Golub-Kahan step: adjacent pairs, the carried-register form
+        gk::bd_apply_chase(Xw.data() + i, n, rl.data(), nl);
+        gk::bd_apply_chase(Yw.data() + i, n, rr.data(), nr);
+      } else {
+        gk::bd_apply_row(Xw.data() + i, n, rl.data(), nl);
+        gk::bd_apply_row(Yw.data() + i, n, rr.data(), nr);
+      }
     }
   }
   *steps = st.steps;

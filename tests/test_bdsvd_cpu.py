@@ -26,7 +26,7 @@ def bdsvd(tmp_path_factory):
                     os.path.join(HERE, "native", "bdsvd_host.cpp")], check=True)
     L = C.CDLL(out)
     P = C.POINTER(C.c_double)
-    L.bd_svd_host.argtypes = [P, P, C.c_int, P, P, P, C.POINTER(C.c_int)]
+    L.bd_svd_host.argtypes = [P, P, C.c_int, P, P, P, C.POINTER(C.c_int), C.POINTER(C.c_int * 2)]
     L.bd_svd_host.restype = C.c_int
 
     def run(d, e):
@@ -35,8 +35,10 @@ def bdsvd(tmp_path_factory):
         e = np.ascontiguousarray(e if n > 1 else [0.0], dtype=np.float64)
         s, X, Y = np.zeros(n), np.zeros(n * n), np.zeros(n * n)
         steps = C.c_int(0)
+        chases = (C.c_int * 2)()
         rc = L.bd_svd_host(d.ctypes.data_as(P), e.ctypes.data_as(P), n, s.ctypes.data_as(P), X.ctypes.data_as(P),
-                           Y.ctypes.data_as(P), C.byref(steps))
+                           Y.ctypes.data_as(P), C.byref(steps), C.byref(chases))
+        run.chases = (chases[0], chases[1])
         return rc, s, X.reshape(n, n).T, Y.reshape(n, n).T, steps.value
 
     return run
@@ -77,6 +79,7 @@ def test_zero_entries(bdsvd):
     d = g.standard_normal(60)
     d[[0, 17, 59]] = 0.0
     check(bdsvd, d, g.standard_normal(59))
+    assert bdsvd.chases[1] > 0  # the zero-diagonal chases ran (the general rotation form)
     e = g.standard_normal(59)
     e[[5, 30]] = 0.0
     check(bdsvd, g.standard_normal(60), e)
