@@ -542,6 +542,14 @@ def run_gk(args, rank, world):
     A = w["A"]
     stream = torch.cuda.current_stream(device)
     kw = dict(krylov_dim=K, seed=w["seed"])
+    # experimental kernels, off unless asked for: the bidiagonal SVD of a restart-free cycle and
+    # the predictor's sketch on the tcgen05 tensor cores
+    exp = {}
+    if args.bdsvd:
+        exp["bdsvd"] = True
+    if args.sketch_tc:
+        exp["sketch_tc"] = True
+    kw.update(exp)
     # the bf16 precision form takes its Krylov dimension from the learned predictor (sketch +
     # network, inside every timed step); --fixed-krylov times the workload's fixed K instead
     from paper_2104_10785_gb300 import predictor
@@ -554,7 +562,7 @@ def run_gk(args, rank, world):
 
     def solve(Aop, **extra):
         if kparams is not None:
-            return predictor.learned_psvd(Aop, kparams, k, tol, seed=w["seed"], **extra)
+            return predictor.learned_psvd(Aop, kparams, k, tol, seed=w["seed"], **exp, **extra)
         return gk.gk_psvd(Aop, k, tol, **kw, **extra)
 
     def barrier():
@@ -834,7 +842,7 @@ def run_gk(args, rank, world):
         "dtype": "bf16" if a_dtype == torch.bfloat16 else ("f64" if a_dtype == torch.float64 else "f32"),
         "data": "synthetic",
         "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "k": k, "krylov_dim": Kused, "tol": tol,
-                   "seed": w["seed"], "krylov": "learned (sketch + network in every step)" if kparams is not None else "fixed",
+                   "seed": w["seed"], **({"experimental": sorted(exp)} if exp else {}), "krylov": "learned (sketch + network in every step)" if kparams is not None else "fixed",
                    "storage": w["dtype"], "accumulate": "f32 runs combined in f64; f64 basis, small SVD, residuals",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": ("inputs larger than L2 (operator %.2f GB)" % (a_bytes / 1e9)) if flush is None else
@@ -1280,6 +1288,10 @@ def main():
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--fused", action="store_true", help="--case psvd: run the fused sweep (GK_FLAG_FUSED)")
     ap.add_argument("--tcgen05", action="store_true", help="--case sketch: the tensor-core form (GK_FLAG_SKETCH_TC)")
+    ap.add_argument("--bdsvd", action="store_true",
+                    help="headline solve: the bidiagonal SVD kernel for restart-free cycles (GK_FLAG_BDSVD)")
+    ap.add_argument("--sketch-tc", action="store_true",
+                    help="headline solve: the predictor's sketch on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC)")
     ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")
     ap.add_argument("--kmax", type=int, default=16, help="--case block: block steps")
     args = ap.parse_args()

@@ -79,7 +79,8 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 #define GK_FLAG_SKETCH_TC 64 /* gk_sketch_batched, one bf16 operator with rows on 16-byte boundaries:
                               Y = A Omega on the tcgen05 tensor cores with TMA-staged tiles and the
                               accumulator in tensor memory, instead of mma.sync (GK_INVALID_ARG for
-                              any other request with this flag).  Experimental: not yet run on a GPU;
+                              any other request with this flag); gk_psvd with a predictor: the same
+                              for the sketch of such an operator (others keep the default sketch).  Experimental: not yet run on a GPU;
                               returns GK_TIMEOUT if one of its bounded waits gives up. */
 #define GK_FLAG_BDSVD 128 /* gk_psvd: in a cycle without kept Ritz vectors (the first, or every cycle when
                               the Krylov dimension is reached without a restart) the projected matrix is

@@ -629,7 +629,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     const int64_t mn = Ain->m < Ain->n ? Ain->m : Ain->n;
     if (!on_host(Ain->vals)) {
       int Kp = 0;
-      rc = predict_krylov(o.predictor, Ain, k, s, &Kp);
+      rc = predict_krylov(o.predictor, Ain, k, s, &Kp, o.flags);
       if (rc) return rc;
       o.krylov_dim = Kp;
     } else {
@@ -669,7 +669,7 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     Astaged.vals = op.vals;
     Astaged.ld = op.ld;
     int Kp = 0;
-    rc = predict_krylov(o.predictor, &Astaged, k, s, &Kp);
+    rc = predict_krylov(o.predictor, &Astaged, k, s, &Kp, o.flags);
     if (rc) return rc;
     o.krylov_dim = Kp;
     PsvdPlan p2;

@@ -171,7 +171,8 @@ cudaError_t sketch_tc(const void *A, int64_t m, int64_t n, int64_t ld, double sc
 // ---- learned predictor (gk_predict.cu) -------------------------------------
 // Krylov dimension for the top-k partial SVD of the dense device operator A from its sketch
 // features: ceil(exp(out_K)) + 2, clamped to [k + 2, min(m, n, 500)].
-int predict_krylov(const gk_predictor *p, const gk_matrix *A, int k, cudaStream_t s, int *K);
+// sketch_flags: GK_FLAG_SKETCH_TC selects the tensor-core sketch (other bits are ignored).
+int predict_krylov(const gk_predictor *p, const gk_matrix *A, int k, cudaStream_t s, int *K, int sketch_flags);
 // gk_psvd_batched with opts->predictor set
 int learned_batched(gk_batch_item *items, int count, const gk_opts *opts, gk_info *info);
 

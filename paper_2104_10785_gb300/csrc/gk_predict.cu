@@ -55,7 +55,8 @@ void margins(double rf, double kf, int64_t mn, int cap, int *r_out, int *K_out) 
   *K_out = (int)Ki;
 }
 
-int predict_raw(const gk_predictor *p, const gk_matrix *A, int count, std::vector<float> &out, cudaStream_t s) {
+int predict_raw(const gk_predictor *p, const gk_matrix *A, int count, std::vector<float> &out, cudaStream_t s,
+                int sketch_flags) {
   float *feat = nullptr;
   if (cudaMallocAsync((void **)&feat, sizeof(float) * (size_t)count * GK_FEATURES, s) != cudaSuccess) {
     cudaGetLastError();
@@ -64,7 +65,12 @@ int predict_raw(const gk_predictor *p, const gk_matrix *A, int count, std::vecto
   gk_opts o;
   gk_default_opts(&o);
   o.stream = s;
+  // the tensor-core sketch where it applies (one bf16 operator whose rows the TMA can address)
+  if ((sketch_flags & GK_FLAG_SKETCH_TC) && count == 1 && A[0].kind == GK_DENSE && A[0].dtype == GK_BF16 &&
+      sketch_tc_ok(A[0].vals, A[0].m, A[0].n, A[0].ld))
+    o.flags = GK_FLAG_SKETCH_TC;
   int rc = gk_sketch_batched(A, count, kSketchSeed, feat, &o);
+  o.flags = 0;
   out.assign(2 * (size_t)count, 0.f);
   if (rc == GK_OK) rc = gk_mlp_forward(p->params, feat, count, out.data(), 1, &o);
   cudaFreeAsync(feat, s);
@@ -72,9 +78,9 @@ int predict_raw(const gk_predictor *p, const gk_matrix *A, int count, std::vecto
   return rc;
 }
 
-int predict_krylov(const gk_predictor *p, const gk_matrix *A, int k, cudaStream_t s, int *K) {
+int predict_krylov(const gk_predictor *p, const gk_matrix *A, int k, cudaStream_t s, int *K, int sketch_flags) {
   std::vector<float> out;
-  const int rc = predict_raw(p, A, 1, out, s);
+  const int rc = predict_raw(p, A, 1, out, s, sketch_flags);
   if (rc) return rc;
   double kf = out[1];
   kf = kf < 0.0 ? 0.0 : (kf > 20.0 ? 20.0 : kf);
@@ -104,7 +110,7 @@ int learned_batched(gk_batch_item *items, int count, const gk_opts *oin, gk_info
   std::vector<gk_matrix> mats(count);
   for (int i = 0; i < count; ++i) mats[i] = items[i].A;
   std::vector<float> out;
-  int rc = predict_raw(pred, mats.data(), count, out, s);
+  int rc = predict_raw(pred, mats.data(), count, out, s, 0);
   if (rc) return rc;
   // one batched partial SVD at the predicted (rank, K) with the rank cut
   std::vector<gk_batch_item> run(items, items + count);
@@ -280,7 +286,7 @@ extern "C" int gk_predictor_predict(const gk_predictor *pred, const gk_matrix *A
   if (!pred || !A || count <= 0 || !out) return GK_INVALID_ARG;
   cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
   std::vector<float> h;
-  const int rc = gk::predict_raw(pred, A, count, h, s);
+  const int rc = gk::predict_raw(pred, A, count, h, s, 0);
   if (rc) return rc;
   if (cudaMemcpy(out, h.data(), sizeof(float) * 2 * (size_t)count, cudaMemcpyDefault) != cudaSuccess) {
     cudaGetLastError();

@@ -359,7 +359,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
             scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
             refine: bool = False, predictor: "Predictor | None" = None, orth_f64: bool = False,
-            persistent: bool = False, bdsvd: bool = False):
+            persistent: bool = False, bdsvd: bool = False, sketch_tc: bool = False):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
@@ -370,7 +370,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     tol (GK_FLAG_REFINE; info["resid_true_max"], info["ms_refine"]).  predictor (a Predictor)
     chooses the Krylov dimension from A's sketch when krylov_dim is 0 (info["kprime"] = K used).
     bdsvd=True takes the SVD of a cycle's bidiagonal projected matrix by Golub-Kahan SVD steps
-    (GK_FLAG_BDSVD, experimental).
+    (GK_FLAG_BDSVD, experimental); sketch_tc=True runs the predictor's sketch of a bf16 operator
+    on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC, experimental).
     """
     M, keep_a = make_matrix(A, scale)
     _check_start(start, M.m)
@@ -388,6 +389,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), krylov_dim, keep, max_restarts,
                   reorth_passes, False, seed, start, stream, workspace, profile, fused, refine, orth_f64, persistent,
                   bdsvd)
+    if sketch_tc:
+        o.flags |= GK_FLAG_SKETCH_TC
     if predictor is not None:
         o.predictor = predictor.handle
     info = gk_info()
