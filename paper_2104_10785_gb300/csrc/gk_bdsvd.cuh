@@ -11,9 +11,11 @@
 //     block, then either one Golub-Kahan step on it (shift: the eigenvalue of the trailing 2 x 2
 //     of B^T B closer to its last entry) or, for a diagonal entry <= tol ||B||, the chase that
 //     zeroes its row's (or, at the block's end, its column's) off-diagonal entry;
-//   * bd_apply_row, per row of X or Y: the step's rotations in order, on that row's entries.
-// The GPU kernel runs bd_step on one thread and bd_apply_row on one thread per row; the CPU
-// tests run the same two functions on the host.
+//   * bd_apply_row / bd_apply_chase, per row of X or Y: the step's rotations in order, on that
+//     row's entries (bd_apply_chase for the adjacent pairs of a Golub-Kahan step, with the
+//     running entry in a register).
+// The GPU kernel runs bd_step on one thread and the row functions on one thread per row; the
+// CPU tests run the same functions on the host.
 #pragma once
 
 #include <math.h>
@@ -47,9 +49,9 @@ __host__ __device__ inline void bd_givens(double a, double b, double *c, double 
     *r = fabs(a);
     return;
   }
-  const double h = hypot(a, b);
-  *c = a / h;
-  *s = b / h;
+  const double h = hypot(a, b), inv = 1.0 / h;  // one division per rotation
+  *c = a * inv;
+  *s = b * inv;
   *r = h;
 }
 
