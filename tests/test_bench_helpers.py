@@ -72,3 +72,24 @@ def test_rsgd_flops_scale_with_products_and_problems():
     assert inner2 == 2 * inner and step2 == 2 * step
     # the mini-batch gradient dominates the rest: 2 b d1 d2 per problem
     assert step > 4 * 2 * 256 * 784 * 256
+
+
+def test_err_rel_from_residuals_matches_the_oracles_definition():
+    """err_rel_paper (from the per-triplet residuals gk_residuals returns) equals the oracle's
+    err_rel of Section 5 computed from the factors themselves."""
+    import numpy as np
+
+    import bench
+    import oracle
+
+    g = np.random.default_rng(5)
+    A = g.standard_normal((40, 25))
+    U0, s0, Vt0 = np.linalg.svd(A, full_matrices=False)
+    k = 6
+    U, V = U0[:, :k], Vt0[:k].T
+    S = s0[:k] * (1 + 1e-3 * g.standard_normal(k))  # perturbed values: err_rel > 0
+    r_atu = np.linalg.norm(A.T @ U - V * S, axis=0)
+    got = bench.err_rel_paper(r_atu, S)
+    want = oracle.err_rel(oracle.Operator.dense(A), U, S, V)
+    assert want > 1e-6
+    np.testing.assert_allclose(got, want, rtol=1e-12)
