@@ -165,6 +165,8 @@ typedef struct {
   double ms_refine;      /* gk_psvd with GK_FLAG_REFINE: wall milliseconds of those checks */
   int32_t refine_checks; /* gk_psvd with GK_FLAG_REFINE: checks run (1 = the first passed) */
   int32_t fallbacks;     /* gk_psvd_batched with a predictor: problems re-solved by the plain pipeline */
+  double err_rel;        /* gk_psvd with GK_FLAG_REFINE: the paper's err_rel (Section 5),
+                            ||A^T U - V S||_F / ||S||_F of the returned triplets (0 when not checked) */
 } gk_info;
 
 /* Fill *opts with the defaults above. */

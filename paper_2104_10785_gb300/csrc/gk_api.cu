@@ -516,7 +516,7 @@ int fresh_column(double *wbuf, int64_t len, const double *Qb, int64_t ld, int jc
 // (double-f32 for reduced-precision dense operators, f64 otherwise); returns
 // max_i max(r_av, r_atu) / s_1 in *rel.
 int refine_check(const Op &op, int64_t m, int64_t n, int k, const double *Uo, const double *So, const double *Vo,
-                 PsvdBufs &b, double *rel, cudaStream_t s, const Dev &d) {
+                 PsvdBufs &b, double *rel, double *err_rel, cudaStream_t s, const Dev &d) {
   if (accurate_ok(op)) {
     GK_CUDA(accurate_products(op, false, Vo, k, b.rY, b.rsplit, s));
     GK_CUDA(resid_norms(b.rY, Uo, So, m, k, b.rr1, s));
@@ -533,14 +533,20 @@ int refine_check(const Op &op, int64_t m, int64_t n, int k, const double *Uo, co
       GK_CUDA(orthonormalize(b.z, n, nullptr, n, 0, 0, b.part, b.h, b.ctl, NM_PLAIN, -1, 1, b.rr2 + i, nullptr, s, d));
     }
   }
-  std::vector<double> h(2 * (size_t)k + 1);
+  std::vector<double> h(3 * (size_t)k);
   GK_CUDA(cudaMemcpyAsync(h.data(), b.rr1, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   GK_CUDA(cudaMemcpyAsync(h.data() + k, b.rr2, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-  GK_CUDA(cudaMemcpyAsync(h.data() + 2 * k, So, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GK_CUDA(cudaMemcpyAsync(h.data() + 2 * k, So, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   GK_CUDA(cudaStreamSynchronize(s));
-  double mx = 0.0;
+  double mx = 0.0, r2 = 0.0, s2 = 0.0;
   for (int i = 0; i < 2 * k; ++i) mx = fmax(mx, h[i]);
+  for (int i = 0; i < k; ++i) {
+    r2 += h[k + i] * h[k + i];
+    s2 += h[2 * k + i] * h[2 * k + i];
+  }
   *rel = h[2 * k] > 0.0 ? mx / h[2 * k] : 0.0;
+  // the paper's err_rel (Section 5): ||A^T U - V Sigma||_F / ||Sigma||_F
+  *err_rel = s2 > 0.0 ? sqrt(r2 / s2) : 0.0;
   return GK_OK;
 }
 
@@ -829,12 +835,13 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
       if (rc) return rc;
       outputs_ready = true;
       const auto tr = std::chrono::steady_clock::now();
-      double rel = 0.0;
-      rc = refine_check(op, m, n, k, Uo, So, Vo, b, &rel, s, d);
+      double rel = 0.0, erel = 0.0;
+      rc = refine_check(op, m, n, k, Uo, So, Vo, b, &rel, &erel, s, d);
       if (rc) return rc;
       inf.ms_refine += seconds_since(tr) * 1e3;
       inf.refine_checks++;
       inf.resid_true_max = rel;
+      inf.err_rel = erel;
       refine_failed = rel > tol;
       if (refine_failed && conv && cycle < p.max_restarts) {
         tol_ritz *= 0.25;  // the Ritz residuals must shrink further: restart and test again

@@ -60,7 +60,7 @@ class gk_info(C.Structure):
         ("ms_matvec", C.c_double), ("ms_matvec_t", C.c_double), ("ms_orth", C.c_double), ("ms_small", C.c_double),
         ("ms_restart", C.c_double), ("n_matvec", C.c_int64), ("n_matvec_t", C.c_int64), ("launches", C.c_int64),
         ("ms_copy", C.c_double), ("resid_true_max", C.c_double), ("ms_refine", C.c_double),
-        ("refine_checks", C.c_int32), ("fallbacks", C.c_int32),
+        ("refine_checks", C.c_int32), ("fallbacks", C.c_int32), ("err_rel", C.c_double),
     ]
 
     def as_dict(self):

@@ -83,6 +83,10 @@ def test_refine_accepts_converged_triplets_and_reports_the_true_residual():
     true_rel = max(o1.max(), o2.max()) / float(S[0])
     assert true_rel <= 1e-8
     assert abs(info["resid_true_max"] - true_rel) <= 1e-12
+    # the paper's err_rel from the same check: each residual within 1e-12 sigma_1 of the oracle's,
+    # so err_rel within sqrt(k) 1e-12
+    err_or = oracle.err_rel(op, U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy())
+    assert 0.0 < info["err_rel"] and abs(info["err_rel"] - err_or) <= 1e-11
 
 
 def test_refine_keeps_restarting_while_the_true_residual_exceeds_tol():
