@@ -205,3 +205,33 @@ def test_bindings_check_vector_and_factor_shapes():
         gk.gk_residuals(A, torch.zeros(10, 2), torch.zeros(2), torch.zeros(5, 2))
     with pytest.raises(ValueError):
         gk.gk_residuals(A, torch.zeros(10, 3), torch.zeros(2), torch.zeros(6, 2))
+
+
+def test_plain_c_client_compiles_links_and_gets_no_device(tmp_path):
+    """tests/native/abi_client.c references every entry point of include/gk.h from C11 (pedantic,
+    warnings as errors) and links against libgk.so; without a device its calls return
+    GK_NO_DEVICE, and a refused argument GK_INVALID_ARG, before any pointer is touched."""
+    import shutil
+
+    import torch
+
+    import paper_2104_10785_gb300 as gk
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = gk.library_path()
+    gk.lib()
+    exe = str(tmp_path / "abi_client")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-o", exe,
+                    os.path.join(ROOT, "tests", "native", "abi_client.c"), "-L" + os.path.dirname(lib), "-lgk",
+                    "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    if torch.cuda.is_available():
+        return  # the expected statuses below are those of a machine without a GPU
+    env = dict(os.environ)
+    dirs = ["/usr/local/cuda/lib64", os.path.join(os.path.dirname(torch.__file__), "lib")]
+    env["LD_LIBRARY_PATH"] = ":".join(dirs + [env.get("LD_LIBRARY_PATH", "")])
+    out = subprocess.run([exe], capture_output=True, text=True, env=env, check=True).stdout.split()
+    no_dev, inval = str(-7), str(-1)
+    assert out[:6] == [no_dev, no_dev, no_dev, no_dev, inval, no_dev], out
+    assert out[6] == "GK_NO_DEVICE"
