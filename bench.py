@@ -551,13 +551,15 @@ def run_gk(args, rank, world):
     A = w["A"]
     stream = torch.cuda.current_stream(device)
     kw = dict(krylov_dim=K, seed=w["seed"])
-    # experimental kernels, off unless asked for: the bidiagonal SVD of a restart-free cycle and
-    # the predictor's sketch on the tcgen05 tensor cores
+    # experimental kernels, off unless asked for: the bidiagonal SVD of a restart-free cycle, the
+    # predictor's sketch on the tcgen05 tensor cores, the Ritz vectors in double-f32
     exp = {}
     if args.bdsvd:
         exp["bdsvd"] = True
     if args.sketch_tc:
         exp["sketch_tc"] = True
+    if args.ritz_df:
+        exp["ritz_df"] = True
     kw.update(exp)
     # the bf16 precision form takes its Krylov dimension from the learned predictor (sketch +
     # network, inside every timed step); --fixed-krylov times the workload's fixed K instead
@@ -1300,6 +1302,8 @@ def main():
     ap.add_argument("--tcgen05", action="store_true", help="--case sketch: the tensor-core form (GK_FLAG_SKETCH_TC)")
     ap.add_argument("--bdsvd", action="store_true",
                     help="headline solve: the bidiagonal SVD kernel for restart-free cycles (GK_FLAG_BDSVD)")
+    ap.add_argument("--ritz-df", action="store_true",
+                    help="headline solve: Ritz vectors from the double-f32 basis copies (GK_FLAG_RITZ_DF)")
     ap.add_argument("--sketch-tc", action="store_true",
                     help="headline solve: the predictor's sketch on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC)")
     ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")

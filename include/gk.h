@@ -87,6 +87,11 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               upper bidiagonal: its SVD by implicitly shifted Golub-Kahan SVD steps on one
                               CTA instead of the cluster Jacobi (K <= 1024).  Experimental: the step and
                               rotation code is tested on the host; the kernel has not yet run on a GPU. */
+#define GK_FLAG_RITZ_DF 256 /* gk_psvd (with the double-f32 basis copies, i.e. without GK_FLAG_ORTH_F64): the
+                              Ritz vectors U_K X and V_K Y (restarts and outputs) from the copies in
+                              double-f32 arithmetic on the FP32 pipes (exact to ~2^-46 of sum |q x|)
+                              instead of f64 products.  Experimental: the product code is tested on the
+                              host; the kernel has not yet run on a GPU. */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).

@@ -374,6 +374,7 @@ struct PsvdPlan {
   bool refine;  // FP64-grade check of the returned triplets (GK_FLAG_REFINE)
   bool df;      // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
   bool bdsvd;   // cycles without kept vectors: the bidiagonal B by Golub-Kahan SVD steps (GK_FLAG_BDSVD)
+  bool ritz_df; // Ritz vectors from the bases' double-f32 copies (GK_FLAG_RITZ_DF, needs df)
 };
 
 struct PsvdBufs {
@@ -479,6 +480,7 @@ int psvd_plan(const gk_matrix *A, int k, const gk_opts &o, PsvdPlan *p) {
   p->refine = (o.flags & GK_FLAG_REFINE) != 0;
   p->df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   p->bdsvd = (o.flags & GK_FLAG_BDSVD) != 0 && K <= kBdMaxK;
+  p->ritz_df = (o.flags & GK_FLAG_RITZ_DF) != 0 && p->df;
   return GK_OK;
 }
 
@@ -731,10 +733,17 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
   bool outputs_ready = false;  // Uo, So, Vo already hold the final triplets
   double *Uo = host_out ? b.Uo : U, *Vo = host_out ? b.Vo : V, *So = host_out ? b.So : S;
   // outputs: U = U_K X_k, V = V_K Y_k, S = sigma_k, sign convention on v
+  // Ritz vectors C = Q X: in f64, or from the basis's double-f32 copy (b.Yw, free after the small
+  // SVD, holds X's split)
+  auto ritz = [&](const double *Qb, const float2 *Qsh, int64_t ld, int64_t len, const double *Xm, int ncol,
+                  double *C, int64_t ldc) -> cudaError_t {
+    if (p.ritz_df && Qsh) return ritz_gemm_df(Qsh, ld, len, K, Xm, K, ncol, C, ldc, reinterpret_cast<float2 *>(b.Yw), s);
+    return ritz_gemm(Qb, ld, len, K, Xm, K, ncol, C, ldc, s, d);
+  };
   auto form_outputs = [&]() -> int {
     prof.begin(PC_RESTART);
-    GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, k, Uo, m, s, d));
-    GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, k, Vo, n, s, d));
+    GK_CUDA(ritz(b.Ub, b.Us, ldu, m, b.X, k, Uo, m));
+    GK_CUDA(ritz(b.Vb, b.Vs, ldv, n, b.Y, k, Vo, n));
     prof.end();
     GK_CUDA(cudaMemcpyAsync(So, b.sigma, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
     GK_CUDA(sign_normalize(Uo, m, m, Vo, n, n, k, s));
@@ -856,8 +865,8 @@ int psvd_impl(const gk_matrix *Ain, int k, double tol, const gk_opts *oin, doubl
     }
     // thick restart: U' = U_K X_keep, V' = [V_K Y_keep, v_{K+1}]
     prof.begin(PC_RESTART);
-    GK_CUDA(ritz_gemm(b.Ub, ldu, m, K, b.X, K, p.keep, b.Ub2, ldu, s, d));
-    GK_CUDA(ritz_gemm(b.Vb, ldv, n, K, b.Y, K, p.keep, b.Vb2, ldv, s, d));
+    GK_CUDA(ritz(b.Ub, b.Us, ldu, m, b.X, p.keep, b.Ub2, ldu));
+    GK_CUDA(ritz(b.Vb, b.Vs, ldv, n, b.Y, p.keep, b.Vb2, ldv));
     GK_CUDA(copy_vec(b.Vb2 + (int64_t)p.keep * ldv, b.x32, b.Vb + (int64_t)K * ldv, n, s));
     if (p.df) {  // the kept columns' shadows
       GK_CUDA(split_cols(b.Ub2, m, ldu, p.keep, b.Us2, s));

@@ -274,6 +274,10 @@ cudaError_t ritz_check(const double *sigma, const double *X, int K, int k, const
 // C[:, 0:ncol] = Q[:, 0:K] * X[:, 0:ncol]   (C may alias nothing in Q)
 cudaError_t ritz_gemm(const double *Q, int64_t ldq, int64_t len, int K, const double *X, int ldx, int ncol,
                       double *C, int64_t ldc, cudaStream_t s, const Dev &d);
+// the same product from the double-f32 copy Qs of Q (gk_ritz_df.cuh) on the FP32 pipes, exact to
+// ~2^-46 of sum |q x|; Xs: K * ncol float2 of scratch for X's split
+cudaError_t ritz_gemm_df(const float2 *Qs, int64_t ldq, int64_t len, int K, const double *X, int ldx, int ncol,
+                         double *C, int64_t ldc, float2 *Xs, cudaStream_t s);
 // sign convention: largest-|v_i| entry positive (flips u_i and v_i)
 cudaError_t sign_normalize(double *U, int64_t ldu, int64_t m, double *V, int64_t ldv, int64_t n, int k,
                            cudaStream_t s);

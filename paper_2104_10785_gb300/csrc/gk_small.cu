@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "gk_bdsvd.cuh"
+#include "gk_ritz_df.cuh"
 #include "gk_device.cuh"
 #include "gk_internal.cuh"
 
@@ -306,6 +307,29 @@ __global__ void __launch_bounds__(kBdThreads) k_bdsvd(const double *__restrict__
   if (tid == 0 && sweeps_out) *sweeps_out = rc < 0 ? -st.steps : st.steps;
 }
 
+// C[:, c] = Q[:, 0:K] X[:, c] from the double-f32 copy Qs of Q (gk_ritz_df.cuh): one thread per row
+// and group of kRitzCols columns; Xs = X split into f32 pairs (K x ncol, ld K)
+__global__ void __launch_bounds__(256) k_ritz_df(const float2 *__restrict__ Qs, int64_t ldq, int64_t len, int K,
+                                                 const float2 *__restrict__ Xs, int ncol, double *__restrict__ C,
+                                                 int64_t ldc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  const int c0 = blockIdx.y * kRitzCols;
+  const int nc = ncol - c0 < kRitzCols ? ncol - c0 : kRitzCols;
+  ritz_df_row(reinterpret_cast<const DfPair *>(Qs), ldq, i, K, reinterpret_cast<const DfPair *>(Xs), K, c0, nc, C,
+              ldc);
+}
+
+// Xs[c * K + k] = the f32 pair of X[c * ldx + k]
+__global__ void k_split_x(const double *__restrict__ X, int ldx, int K, int ncol, float2 *__restrict__ Xs) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)K * ncol;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / K), k = (int)(idx % K);
+    const DfPair v = df_split(X[(int64_t)c * ldx + k]);
+    Xs[idx] = make_float2(v.hi, v.lo);
+  }
+}
+
 }  // namespace
 
 cudaError_t assemble_B(double *Bm, int K, int l, const double *sigma, const double *rho, const double *alpha,
@@ -412,6 +436,17 @@ cudaError_t ritz_gemm(const double *Q, int64_t ldq, int64_t len, int K, const do
   if (ncol <= 0 || len <= 0) return cudaSuccess;
   dim3 grid((unsigned)((len + 255) / 256), (unsigned)((ncol + 15) / 16));
   GK_LAUNCH(k_ritz_gemm<<<grid, 256, 0, s>>>(Q, ldq, len, K, X, ldx, ncol, C, ldc));
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_gemm_df(const float2 *Qs, int64_t ldq, int64_t len, int K, const double *X, int ldx, int ncol,
+                         double *C, int64_t ldc, float2 *Xs, cudaStream_t s) {
+  if (ncol <= 0 || len <= 0) return cudaSuccess;
+  int64_t b = ((int64_t)K * ncol + 255) / 256;
+  if (b > 1024) b = 1024;
+  GK_LAUNCH(k_split_x<<<(int)b, 256, 0, s>>>(X, ldx, K, ncol, Xs));
+  dim3 grid((unsigned)((len + 255) / 256), (unsigned)((ncol + kRitzCols - 1) / kRitzCols));
+  GK_LAUNCH(k_ritz_df<<<grid, 256, 0, s>>>(Qs, ldq, len, K, Xs, ncol, C, ldc));
   return cudaGetLastError();
 }
 

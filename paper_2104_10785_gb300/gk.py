@@ -30,6 +30,7 @@ GK_FLAG_ORTH_F64 = 16
 GK_FLAG_PERSISTENT = 32
 GK_FLAG_SKETCH_TC = 64
 GK_FLAG_BDSVD = 128
+GK_FLAG_RITZ_DF = 256
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -359,7 +360,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
             reorth_passes: int | None = None, seed: int | None = None, start=None, stream=None, workspace=None,
             scale: float = 1.0, out=None, check: bool = True, profile: bool = False, fused: bool = False,
             refine: bool = False, predictor: "Predictor | None" = None, orth_f64: bool = False,
-            persistent: bool = False, bdsvd: bool = False, sketch_tc: bool = False):
+            persistent: bool = False, bdsvd: bool = False, sketch_tc: bool = False, ritz_df: bool = False):
     """k largest singular triplets of A.  Returns (U m x k, S k, V n x k, status, info dict).
 
     Outputs live where A lives (device tensors for a CUDA operator, host tensors
@@ -371,7 +372,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
     chooses the Krylov dimension from A's sketch when krylov_dim is 0 (info["kprime"] = K used).
     bdsvd=True takes the SVD of a cycle's bidiagonal projected matrix by Golub-Kahan SVD steps
     (GK_FLAG_BDSVD, experimental); sketch_tc=True runs the predictor's sketch of a bf16 operator
-    on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC, experimental).
+    on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC, experimental); ritz_df=True forms the Ritz
+    vectors from the bases' double-f32 copies on the FP32 pipes (GK_FLAG_RITZ_DF, experimental).
     """
     M, keep_a = make_matrix(A, scale)
     _check_start(start, M.m)
@@ -391,6 +393,8 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
                   bdsvd)
     if sketch_tc:
         o.flags |= GK_FLAG_SKETCH_TC
+    if ritz_df:
+        o.flags |= GK_FLAG_RITZ_DF
     if predictor is not None:
         o.predictor = predictor.handle
     info = gk_info()
