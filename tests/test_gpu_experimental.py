@@ -1,0 +1,66 @@
+"""The opt-in kernels that have not yet run on a GPU, against the default paths they would replace.
+Skipped unless GK_EXPERIMENTAL=1: each kernel's host-testable part is covered by the CPU tests
+(tests/test_bdsvd_cpu.py, tests/test_ritz_df_cpu.py), and its first GPU run is this file.
+
+  * GK_FLAG_BDSVD (k_bdsvd): the SVD of a restart-free cycle's bidiagonal B by Golub-Kahan SVD
+    steps, against the cluster Jacobi: the same triplets (sigma 1e-10 relative to the planted
+    values, vectors 1e-8) on f64 operators, one cycle and with restarts;
+  * GK_FLAG_RITZ_DF (k_ritz_df): the Ritz vectors from the double-f32 basis copies (exact to
+    ~2^-46 of sum |q x|, ~1e-14 here), against the f64 products: sigma 1e-10, vectors 1e-8;
+  * GK_FLAG_SKETCH_TC (k_sketch_tc): the sketch on tcgen05 against mma.sync on the same bf16
+    operator: both accumulate bf16 products in f32 in the tensor pipe, in different orders, so
+    the features (logs of the sketch's singular values) agree to ~1e-5; 1e-4 is the bound."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("GK_EXPERIMENTAL") != "1",
+                                 reason="experimental kernels: set GK_EXPERIMENTAL=1 for their first GPU run")]
+
+
+def gk():
+    import paper_2104_10785_gb300 as m
+
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def angle_err(X, Y):
+    s = np.sign(np.sum(X * Y, axis=0))
+    s[s == 0] = 1
+    return np.linalg.norm(X - Y * s[None, :], axis=0).max()
+
+
+@pytest.mark.parametrize("m,n,k,K", [(2000, 1000, 10, 30), (1500, 700, 8, 171), (900, 1200, 5, 64)])
+@pytest.mark.parametrize("flag", ["bdsvd", "ritz_df"])
+def test_experimental_psvd_matches_the_default(m, n, k, K, flag):
+    sig = synth.sigma_geometric(min(m, n), 0.9)
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, seed=m + K, dtype=np.float64)
+    q1 = cuda(synth.start_vector(m, 3))
+    At = cuda(A)
+    M = gk()
+    U1, S1, V1, st1, i1 = M.gk_psvd(At, k, 1e-10, krylov_dim=K, start=q1, **{flag: True})
+    U2, S2, V2, st2, i2 = M.gk_psvd(At, k, 1e-10, krylov_dim=K, start=q1)
+    assert st1 == st2 == 0
+    np.testing.assert_allclose(S1.cpu().numpy(), sig[:k], rtol=1e-10)
+    np.testing.assert_allclose(S1.cpu().numpy(), S2.cpu().numpy(), rtol=1e-10)
+    assert angle_err(V1.cpu().numpy(), V2.cpu().numpy()) < 1e-8
+    assert angle_err(U1.cpu().numpy(), U2.cpu().numpy()) < 1e-8
+
+
+@pytest.mark.parametrize("m,n", [(1000, 640), (1037, 777), (300, 64), (129, 4000)])
+def test_tensor_core_sketch_matches_mma_sync(m, n):
+    A = synth.gaussian_product(m, n, 20, 1e-3, seed=m + n, dtype=np.float32)
+    At = cuda(synth.to_bf16_bits(A).view(np.int16)).view(torch.bfloat16)
+    M = gk()
+    f1 = M.gk_sketch_batched([At], seed=5).cpu().numpy()
+    f2 = M.gk_sketch_batched([At], seed=5, tcgen05=True).cpu().numpy()
+    np.testing.assert_allclose(f2, f1, rtol=0, atol=1e-4)
