@@ -85,8 +85,10 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 #define GK_FLAG_BDSVD 128 /* gk_psvd: in a cycle without kept Ritz vectors (the first, or every cycle when
                               the Krylov dimension is reached without a restart) the projected matrix is
                               upper bidiagonal: its SVD by implicitly shifted Golub-Kahan SVD steps on one
-                              CTA instead of the cluster Jacobi (K <= 1024).  Experimental: the step and
-                              rotation code is tested on the host; the kernel has not yet run on a GPU. */
+                              CTA instead of the cluster Jacobi (K <= 1024); gk_fsvd route 1: the same for
+                              B_{k'+1,k'} (through its transpose, upper bidiagonal).  Experimental: the
+                              step and rotation code is tested on the host; the kernel has not yet run
+                              on a GPU. */
 #define GK_FLAG_RITZ_DF 256 /* gk_psvd (with the double-f32 basis copies, i.e. without GK_FLAG_ORTH_F64): the
                               Ritz vectors U_K X and V_K Y (restarts and outputs) from the copies in
                               double-f32 arithmetic on the FP32 pipes (exact to ~2^-46 of sum |q x|)

@@ -1519,8 +1519,16 @@ int fsvd_impl(const gk_matrix *Ain, int k, int r, int route, const gk_opts *oin,
       // the SVD of B_{k'+1,k'} itself (padded with a zero column to a square): V = P Y, U = Q X
       const int K = kp + 1;
       prof.begin(PC_SMALL);
-      GK_CUDA(assemble_lower(f.Bm, kp, b.alpha, b.beta, s));
-      GK_CUDA(small_svd(f.Bm, f.Yw, K, f.sigma, f.X, f.Y, f.nrm, f.pos, f.sweeps, b.ctl, s));
+      if ((o.flags & GK_FLAG_BDSVD) && K <= kBdMaxK) {
+        // Golub-Kahan SVD steps on the transpose: the padded B^T is upper bidiagonal with
+        // alpha_1..alpha_k' on the diagonal (the padding's 0 last), beta_2..beta_{k'+1} above it;
+        // B^T = X' S Y'^T gives B = Y' S X'^T, so X' is B's right and Y' its left vectors
+        GK_CUDA(cudaMemsetAsync(b.alpha + kp, 0, sizeof(double), s));
+        GK_CUDA(bd_svd(b.alpha, b.beta + 1, K, f.sigma, f.Y, f.X, f.Bm, f.Yw, f.sweeps, b.ctl, s));
+      } else {
+        GK_CUDA(assemble_lower(f.Bm, kp, b.alpha, b.beta, s));
+        GK_CUDA(small_svd(f.Bm, f.Yw, K, f.sigma, f.X, f.Y, f.nrm, f.pos, f.sweeps, b.ctl, s));
+      }
       prof.end();
       prof.begin(PC_RESTART);
       // V = P Y: the first kp rows of Y (the zero padding column is never rotated)

@@ -406,7 +406,7 @@ def gk_psvd(A, k: int, tol: float = 1e-8, *, krylov_dim: int = 0, keep: int = 0,
 
 def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = None, seed: int | None = None,
             start=None, stream=None, workspace=None, scale: float = 1.0, check: bool = True, profile: bool = False,
-            fused: bool = False, orth_f64: bool = False):
+            fused: bool = False, orth_f64: bool = False, bdsvd: bool = False):
     """Algorithm 2 as printed: k steps of Algorithm 1, the SVD of B, the r largest triplets
     (route 1: U = Q X; route 0: u_i = A v_i / sigma_i).  Returns (U m x r, S r, V n x r, status,
     info dict); outputs live where A lives."""
@@ -421,6 +421,8 @@ def gk_fsvd(A, k: int, r: int, *, route: int = 1, reorth_passes: int | None = No
     S = torch.empty(r, dtype=torch.float64, device=dev, pin_memory=pin)
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), 0, 0, None, reorth_passes, False, seed, start,
                   stream, workspace, profile, fused, orth_f64=orth_f64)
+    if bdsvd:
+        o.flags |= GK_FLAG_BDSVD
     info = gk_info()
     st = lib().gk_fsvd(C.byref(M), int(k), int(r), int(route), C.byref(o), _ptr(U), _ptr(S), _ptr(V), C.byref(info))
     if check and st < 0:

@@ -113,3 +113,22 @@ def test_golub_kahan_bidiagonal_of_a_power_law_operator(bdsvd):
     check(bdsvd, d, e)
     rc, s, X, Y, _ = bdsvd(d, e)
     np.testing.assert_allclose(s[:5], np.arange(1, 6) ** -1.5, rtol=1e-8)
+
+
+def test_lower_bidiagonal_through_its_transpose(bdsvd):
+    """gk_fsvd's route 1 reading: B_{k'+1,k'} (alpha on the diagonal, beta below it) padded with a
+    zero column has an upper-bidiagonal transpose (alpha then 0 on the diagonal, beta above it);
+    B^T = X' S Y'^T gives B = Y' S X'^T, so X' holds B's right vectors and Y' its left ones, with a
+    zero last entry in every right vector of a nonzero value (the padding column is never used)."""
+    g = np.random.default_rng(11)
+    kp = 40
+    alpha, beta = np.abs(g.standard_normal(kp)) + 0.1, np.abs(g.standard_normal(kp)) + 0.1
+    K = kp + 1
+    Bpad = np.zeros((K, K))
+    Bpad[np.arange(kp), np.arange(kp)] = alpha
+    Bpad[np.arange(1, K), np.arange(kp)] = beta
+    rc, s, Xp, Yp, _ = bdsvd(np.append(alpha, 0.0), beta)
+    assert rc == 0
+    np.testing.assert_allclose(s, np.linalg.svd(Bpad, compute_uv=False), rtol=0, atol=1e-13 * s[0])
+    assert np.linalg.norm(Bpad - Yp @ np.diag(s) @ Xp.T) <= 1e-13 * s[0] * K
+    assert np.all(np.abs(Xp[K - 1, :kp]) <= 1e-13)

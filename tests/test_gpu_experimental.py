@@ -64,3 +64,17 @@ def test_tensor_core_sketch_matches_mma_sync(m, n):
     f1 = M.gk_sketch_batched([At], seed=5).cpu().numpy()
     f2 = M.gk_sketch_batched([At], seed=5, tcgen05=True).cpu().numpy()
     np.testing.assert_allclose(f2, f1, rtol=0, atol=1e-4)
+
+
+@pytest.mark.parametrize("m,n,k,r", [(2000, 1000, 60, 10), (700, 1500, 171, 20)])
+def test_fsvd_route_1_with_bidiagonal_svd_matches_the_default(m, n, k, r):
+    sig = synth.sigma_geometric(min(m, n), 0.9)
+    A, _, _ = synth.prescribed_spectrum(m, n, sig, seed=m + k, dtype=np.float64)
+    q1 = cuda(synth.start_vector(m, 5))
+    M = gk()
+    U1, S1, V1, st1, _ = M.gk_fsvd(cuda(A), k, r, route=1, start=q1, bdsvd=True)
+    U2, S2, V2, st2, _ = M.gk_fsvd(cuda(A), k, r, route=1, start=q1)
+    assert st1 == st2 == 0
+    np.testing.assert_allclose(S1.cpu().numpy(), S2.cpu().numpy(), rtol=1e-12)
+    assert angle_err(V1.cpu().numpy(), V2.cpu().numpy()) < 1e-9
+    assert angle_err(U1.cpu().numpy(), U2.cpu().numpy()) < 1e-9
