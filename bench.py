@@ -703,14 +703,14 @@ def run_gk(args, rank, world):
     if kparams is not None:
         try:
             kf = int(Kused)
-            gk.gk_fsvd(A, kf, k, route=1)
+            gk.gk_fsvd(A, kf, k, route=1, bdsvd=args.bdsvd)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             reps = max(1, min(args.steps, 3))
             e0.record(stream)
             for _ in range(reps):
-                Uq, Sq, Vq, stq, infq = gk.gk_fsvd(A, kf, k, route=1)
+                Uq, Sq, Vq, stq, infq = gk.gk_fsvd(A, kf, k, route=1, bdsvd=args.bdsvd)
             e1.record(stream)
             torch.cuda.synchronize()
             qms = e0.elapsed_time(e1) / reps
