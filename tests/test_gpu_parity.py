@@ -352,6 +352,27 @@ def test_psvd_wide_and_tiny_shapes():
         np.testing.assert_allclose(S.cpu().numpy(), np.linalg.svd(A, compute_uv=False)[:k], rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("restarts", [0, 3])
+def test_ritz_estimates_and_restarts_cycle_by_cycle(restarts):
+    """The convergence test's quantity (max_{i<k} |beta_K X_{K,i}| / sigma_1) and the thick restart,
+    cycle by cycle: with the same Krylov dimension, keep rule and restart budget, and tol 1e-14 (no
+    cycle converges; sigma_i = i^-0.5 and K = 16 leave the estimate at ~8e-2 after one cycle and
+    ~2e-4 after four), the GPU and the oracle run the same cycles; the Ritz values and the Ritz
+    residual estimate agree after the budget (rounding only: ~1e-13 in the values; the estimate's
+    last-row entries carry ~1e-15 absolute, ~1e-11 relative to it)."""
+    sig = synth.sigma_power(1000, 0.5)
+    A, _, _ = synth.prescribed_spectrum(2000, 1000, sig, seed=17, dtype=np.float64)
+    op, At, _ = dense_pair(A, "f64")
+    q1 = synth.start_vector(2000, 17)
+    Uo, So, Vo, io = oracle.psvd(op, 10, 16, q1, tol=1e-14, max_restarts=restarts)
+    U, S, V, st, info = gk().gk_psvd(At, 10, 1e-14, krylov_dim=16, start=cuda(q1), max_restarts=restarts)
+    assert not io["converged"] and st == 1  # GK_NOT_CONVERGED: outputs hold the last Ritz triplets
+    assert info["cycles"] == io["cycles"] == restarts + 1 and info["restarts"] == restarts
+    np.testing.assert_allclose(S.cpu().numpy(), So, rtol=1e-10)
+    np.testing.assert_allclose(info["resid_est_max"], io["resid_est_max"], rtol=1e-6)
+    assert angle_err(V.cpu().numpy()[:, :5], Vo[:, :5]) <= 1e-6
+
+
 def test_psvd_of_the_transpose_swaps_the_factors():
     """psvd(A^T) = swap(psvd(A)): the same singular values with the left and right vectors
     exchanged (the method is shape-agnostic; here a tall and a wide operator)."""
