@@ -547,7 +547,7 @@ def run_gk(args, rank, world):
     if args.workload == "rsgd_f64_64x784x256_rank5":
         return run_rsgd_headline(args, rank, world, device)
     w = make_workload(args.workload, device, want_plain=not args.no_plain, seed=args.seed)
-    k, K, tol = w["k"], w["K"], w["tol"]
+    k, K, tol = w["k"], (args.krylov if args.krylov else w["K"]), w["tol"]
     A = w["A"]
     stream = torch.cuda.current_stream(device)
     kw = dict(krylov_dim=K, seed=w["seed"])
@@ -1287,6 +1287,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--seed", type=int, default=None,
                     help="draw the workload (operator and start vector) with this seed instead of its recipe's")
+    ap.add_argument("--krylov", type=int, default=0,
+                    help="with --fixed-krylov: this Krylov dimension instead of the workload's")
     ap.add_argument("--fixed-krylov", action="store_true",
                     help="time the default workload at its fixed Krylov dimension instead of the learned one")
     ap.add_argument("--traffic", type=float, default=None,
