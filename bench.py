@@ -1232,7 +1232,7 @@ def profile_case(args):
     --case sketch: `reps` calls of gk_sketch_batched on the same kind of operator (one problem;
     --tcgen05: the tensor-core form).
     --case block: `reps` calls of gk_block_numrank (block size --s, --kmax block steps, eps 1e-8)
-    on the same kind of operator."""
+    on the same kind of operator (--block-f32: its f32 block products)."""
     import torch
 
     import paper_2104_10785_gb300 as gk
@@ -1252,7 +1252,7 @@ def profile_case(args):
             elif args.case == "sketch":
                 gk.gk_sketch_batched([A], seed=1, tcgen05=args.tcgen05)
             elif args.case == "block":
-                gk.gk_block_numrank(A, args.s, 1e-8, args.kmax)
+                gk.gk_block_numrank(A, args.s, 1e-8, args.kmax, f32_products=args.block_f32)
             else:
                 gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0, fused=args.fused)
     elif args.case == "batched":
@@ -1310,6 +1310,7 @@ def main():
                     help="headline solve: the predictor's sketch on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC)")
     ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")
     ap.add_argument("--kmax", type=int, default=16, help="--case block: block steps")
+    ap.add_argument("--block-f32", action="store_true", help="--case block: f32 block products (GK_FLAG_BLOCK_F32)")
     args = ap.parse_args()
     if args.case is not None:
         profile_case(args)

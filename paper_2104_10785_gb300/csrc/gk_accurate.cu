@@ -55,7 +55,11 @@ __device__ __forceinline__ void df_madd(float2 &hi, float2 &lo, float2 a2, float
 
 // out[j * ldo + o] = scale * sum_c op(A)[o][c] * X[j][c]   (X given as hi/lo f32, [j * ldx + c])
 // TRANS = false: op(A) = A (o: row, c: column); TRANS = true: op(A) = A^T (o: column, c: row).
-template <typename T, bool TRANS>
+// FAST = true: the same tiling in f32 -- x rounded to f32 (its high word), each 32-term chunk of
+// products summed in f32, the chunk sums combined in double-f32 (TwoSum): every output within
+// about 2^-24 (32 + 2) sum |a x| of the exact product, the precision model of gk_matvec's kernels,
+// at about one FMA per product instead of eleven packed operations per two.
+template <typename T, bool TRANS, bool FAST = false>
 __global__ void __launch_bounds__(kAThreads) k_acc_gemm(const T *__restrict__ A, int64_t m, int64_t n, int64_t ld,
                                                         double scale, const float *__restrict__ xh,
                                                         const float *__restrict__ xl, int64_t ldx, int k,
@@ -107,19 +111,53 @@ __global__ void __launch_bounds__(kAThreads) k_acc_gemm(const T *__restrict__ A,
       Xl[cc][vv] = b;
     }
     __syncthreads();
+    if constexpr (FAST) {
+      float2 cs[kATR][kATP];  // this chunk's f32 sums
+#pragma unroll
+      for (int r = 0; r < kATR; ++r)
+#pragma unroll
+        for (int p = 0; p < kATP; ++p) cs[r][p] = f2(0.f, 0.f);
 #pragma unroll 4
-    for (int cc = 0; cc < kAChunk; ++cc) {
-      const float4 a4 = *reinterpret_cast<const float4 *>(&As[cc][to]);
-      const float av[kATR] = {a4.x, a4.y, a4.z, a4.w};
-      const float4 h4 = *reinterpret_cast<const float4 *>(&Xh[cc][tv]);
-      const float4 l4 = *reinterpret_cast<const float4 *>(&Xl[cc][tv]);
-      const float2 xhp[kATP] = {f2(h4.x, h4.y), f2(h4.z, h4.w)};
-      const float2 xlp[kATP] = {f2(l4.x, l4.y), f2(l4.z, l4.w)};
+      for (int cc = 0; cc < kAChunk; ++cc) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(&As[cc][to]);
+        const float av[kATR] = {a4.x, a4.y, a4.z, a4.w};
+        const float4 h4 = *reinterpret_cast<const float4 *>(&Xh[cc][tv]);
+        const float2 xhp[kATP] = {f2(h4.x, h4.y), f2(h4.z, h4.w)};
 #pragma unroll
-      for (int r = 0; r < kATR; ++r) {
-        const float2 a2 = f2(av[r], av[r]), na2 = f2(-av[r], -av[r]);
+        for (int r = 0; r < kATR; ++r) {
+          const float2 a2 = f2(av[r], av[r]);
 #pragma unroll
-        for (int p = 0; p < kATP; ++p) df_madd(hi[r][p], lo[r][p], a2, na2, xhp[p], xlp[p]);
+          for (int p = 0; p < kATP; ++p) cs[r][p] = __ffma2_rn(a2, xhp[p], cs[r][p]);
+        }
+      }
+      // (hi, lo) += chunk sum, TwoSum
+      const float2 m1 = f2(-1.f, -1.f);
+#pragma unroll
+      for (int r = 0; r < kATR; ++r)
+#pragma unroll
+        for (int p = 0; p < kATP; ++p) {
+          const float2 sm = __fadd2_rn(hi[r][p], cs[r][p]);
+          const float2 bb = __ffma2_rn(hi[r][p], m1, sm);                  // s - hi
+          const float2 d1 = __ffma2_rn(__ffma2_rn(bb, m1, sm), m1, hi[r][p]);  // hi - (s - bb)
+          const float2 d2 = __ffma2_rn(bb, m1, cs[r][p]);                  // c - bb
+          lo[r][p] = __fadd2_rn(lo[r][p], __fadd2_rn(d1, d2));
+          hi[r][p] = sm;
+        }
+    } else {
+#pragma unroll 4
+      for (int cc = 0; cc < kAChunk; ++cc) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(&As[cc][to]);
+        const float av[kATR] = {a4.x, a4.y, a4.z, a4.w};
+        const float4 h4 = *reinterpret_cast<const float4 *>(&Xh[cc][tv]);
+        const float4 l4 = *reinterpret_cast<const float4 *>(&Xl[cc][tv]);
+        const float2 xhp[kATP] = {f2(h4.x, h4.y), f2(h4.z, h4.w)};
+        const float2 xlp[kATP] = {f2(l4.x, l4.y), f2(l4.z, l4.w)};
+#pragma unroll
+        for (int r = 0; r < kATR; ++r) {
+          const float2 a2 = f2(av[r], av[r]), na2 = f2(-av[r], -av[r]);
+#pragma unroll
+          for (int p = 0; p < kATP; ++p) df_madd(hi[r][p], lo[r][p], a2, na2, xhp[p], xlp[p]);
+        }
       }
     }
     __syncthreads();
@@ -171,9 +209,18 @@ __global__ void __launch_bounds__(256) k_resid_norm(const double *__restrict__ Y
 
 template <typename T>
 cudaError_t launch_acc(const Op &A, bool trans, const float *xh, const float *xl, int64_t ldx, int k, double *out,
-                       int64_t ldo, cudaStream_t s) {
+                       int64_t ldo, cudaStream_t s, bool fast) {
   const int64_t nout = trans ? A.n : A.m;
   dim3 grid((unsigned)((nout + kAOut - 1) / kAOut), (unsigned)((k + kAVec - 1) / kAVec));
+  if (fast) {
+    if (trans)
+      GK_LAUNCH(k_acc_gemm<T, true, true><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, xh,
+                                                                       xl, ldx, k, out, ldo));
+    else
+      GK_LAUNCH(k_acc_gemm<T, false, true><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, xh,
+                                                                        xl, ldx, k, out, ldo));
+    return cudaGetLastError();
+  }
   if (trans)
     GK_LAUNCH(k_acc_gemm<T, true><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx,
                                                                k, out, ldo));
@@ -193,7 +240,7 @@ size_t accurate_floats(const Op &A, int k) {
 }
 
 cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, double *out, float *split,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool fast) {
   const int64_t len = trans ? A.m : A.n;  // length of the input vectors
   const int64_t cnt = len * (int64_t)k;
   float *xh = split, *xl = split + cnt;
@@ -204,9 +251,9 @@ cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, d
   if (e != cudaSuccess) return e;
   const int64_t ldo = trans ? A.n : A.m;
   switch (A.dtype) {
-    case GK_F32: return launch_acc<float>(A, trans, xh, xl, len, k, out, ldo, s);
-    case GK_BF16: return launch_acc<__nv_bfloat16>(A, trans, xh, xl, len, k, out, ldo, s);
-    case GK_F16: return launch_acc<__half>(A, trans, xh, xl, len, k, out, ldo, s);
+    case GK_F32: return launch_acc<float>(A, trans, xh, xl, len, k, out, ldo, s, fast);
+    case GK_BF16: return launch_acc<__nv_bfloat16>(A, trans, xh, xl, len, k, out, ldo, s, fast);
+    case GK_F16: return launch_acc<__half>(A, trans, xh, xl, len, k, out, ldo, s, fast);
     default: return cudaErrorNotSupported;
   }
 }

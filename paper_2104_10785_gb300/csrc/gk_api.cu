@@ -1135,6 +1135,7 @@ struct BlockBufs {
   int *pos, *sweeps, *rank;
   bool df;   // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
   bool acc;  // dense reduced-precision operator: block products in one pass (double-f32)
+  bool f32;  // with acc: the f32 form of that pass (GK_FLAG_BLOCK_F32)
 };
 
 size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const OpStage &st, char *base, BlockBufs *b,
@@ -1204,7 +1205,7 @@ int block_product(const Op &op, BlockBufs &b, bool trans, const double *src, int
   if (b.acc) {  // one pass over A for the whole block, products exact to ~2^-47
     GK_CUDA(cudaMemcpy2DAsync(b.Xc, sizeof(double) * lin, src, sizeof(double) * ldsrc, sizeof(double) * lin, s,
                               cudaMemcpyDeviceToDevice, st));
-    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st));
+    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st, b.f32));
     return GK_OK;
   }
   for (int c = 0; c < s; ++c) {
@@ -1314,6 +1315,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   BlockBufs b;
   b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   b.acc = accurate_ok(op);
+  b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
   const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
   Workspace ws;
   rc = acquire(ws, bytes, o, st);

@@ -31,6 +31,7 @@ GK_FLAG_PERSISTENT = 32
 GK_FLAG_SKETCH_TC = 64
 GK_FLAG_BDSVD = 128
 GK_FLAG_RITZ_DF = 256
+GK_FLAG_BLOCK_F32 = 512
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -456,9 +457,11 @@ def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = Fals
 
 def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None, seed: int | None = None,
                      stream=None, workspace=None, scale: float = 1.0, want_sigma: bool = False, check: bool = True,
-                     orth_f64: bool = False):
+                     orth_f64: bool = False, f32_products: bool = False):
     """Numerical rank from a block of s start vectors (block Algorithm 1 + Algorithm 3).
-    start: optional m x s start block.  Returns (rank, sigma(B) or None, block steps, status, info dict)."""
+    start: optional m x s start block.  f32_products: the block products of a reduced-precision
+    dense operator in f32 (GK_FLAG_BLOCK_F32, experimental).  Returns (rank, sigma(B) or None,
+    block steps, status, info dict)."""
     M, keep_a = make_matrix(A, scale)
     if start is not None and tuple(start.shape) != (M.m, int(s)):
         raise ValueError(f"start block must be m x s = {M.m} x {int(s)}, got {tuple(start.shape)}")
@@ -475,6 +478,8 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
         q0 = start.to(torch.float64).t().contiguous()
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), seed=seed, stream=stream, workspace=workspace,
                   orth_f64=orth_f64)
+    if f32_products:
+        o.flags |= GK_FLAG_BLOCK_F32
     info = gk_info()
     r = C.c_int(-1)
     steps = C.c_int(0)

@@ -9,7 +9,10 @@ Skipped unless GK_EXPERIMENTAL=1: each kernel's host-testable part is covered by
     ~2^-46 of sum |q x|, ~1e-14 here), against the f64 products: sigma 1e-10, vectors 1e-8;
   * GK_FLAG_SKETCH_TC (k_sketch_tc): the sketch on tcgen05 against mma.sync on the same bf16
     operator: both accumulate bf16 products in f32 in the tensor pipe, in different orders, so
-    the features (logs of the sketch's singular values) agree to ~1e-5; 1e-4 is the bound."""
+    the features (logs of the sketch's singular values) agree to ~1e-5; 1e-4 is the bound;
+  * GK_FLAG_BLOCK_F32 (k_acc_gemm in f32): the block rank with f32 block products against the
+    oracle: the rank exactly, sigma(B) above the cut within 1e-5 relative (f32 products carry
+    ~2^-24 (34) sum |a x| per entry)."""
 import os
 
 import numpy as np
@@ -78,3 +81,21 @@ def test_fsvd_route_1_with_bidiagonal_svd_matches_the_default(m, n, k, r):
     np.testing.assert_allclose(S1.cpu().numpy(), S2.cpu().numpy(), rtol=1e-12)
     assert angle_err(V1.cpu().numpy(), V2.cpu().numpy()) < 1e-9
     assert angle_err(U1.cpu().numpy(), U2.cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("dtype,m,n,r,s,eps", [("bf16", 3000, 1000, 40, 5, 1e-2), ("f32", 20000, 1500, 60, 8, 1e-5)])
+def test_block_rank_with_f32_products(dtype, m, n, r, s, eps):
+    from oracle import block_gk as bgk
+
+    A = synth.gaussian_product(m, n, r, 1e-7, seed=m + n + s, dtype=np.float64)
+    if dtype == "bf16":
+        bits = synth.to_bf16_bits(A.astype(np.float32))
+        At, Ad = cuda(bits.view(np.int16)).view(torch.bfloat16), synth.bf16_bits_to_f32(bits).astype(np.float64)
+    else:
+        A32 = A.astype(np.float32)
+        At, Ad = cuda(A32), A32.astype(np.float64)
+    Q0 = synth.rng(s + m).standard_normal((m, s))
+    rk, sig, steps, st, info = gk().gk_block_numrank(At, s, eps, start=cuda(Q0), want_sigma=True, f32_products=True)
+    r_or, sig_or, k_or = bgk.block_numrank(Ad, Q0, eps=eps)
+    assert st == 0 and rk == r_or == r
+    np.testing.assert_allclose(sig.cpu().numpy()[:r], sig_or[:r], rtol=1e-5)
