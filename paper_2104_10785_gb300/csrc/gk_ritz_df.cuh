@@ -17,10 +17,13 @@
 #define __host__
 #define __device__
 #define GK_RITZ_ALIGN8 alignas(8)
-#define GK_RITZ_UNROLL
 #else
 #define GK_RITZ_ALIGN8 __align__(8)
+#endif
+#ifdef __CUDA_ARCH__
 #define GK_RITZ_UNROLL _Pragma("unroll")
+#else
+#define GK_RITZ_UNROLL
 #endif
 
 namespace gk {

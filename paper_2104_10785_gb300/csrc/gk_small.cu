@@ -27,11 +27,6 @@ __device__ __forceinline__ bool halted(const Ctl *ctl) {
   return ctl != nullptr && *reinterpret_cast<const volatile int *>(&ctl->halt) != 0;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __global__ void k_assemble_B(double *__restrict__ Bm, int K, int l, const double *__restrict__ sigma,
                              const double *__restrict__ rho, const double *__restrict__ alpha,
