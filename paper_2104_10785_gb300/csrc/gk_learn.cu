@@ -673,7 +673,6 @@ cudaError_t backward(const float *params, const float *Y, int B, Acts a, float *
   return cudaGetLastError();
 }
 
-thread_local char l_err[256] = "";
 
 int check(cudaError_t e) {
   if (e != cudaSuccess) {
