@@ -22,6 +22,8 @@ largest block norm so far), or when the right block vanishes, ||R_{j+1}||_2 <= e
 (the block form of the alpha break that also ends Algorithm 1), or when the next block would
 exceed min(m, n) columns.
 The rank (Algorithm 3 on blocks) is the number of singular values of B above eps * sigma_1(B).
+block_fsvd is one cycle of the block form of Algorithm 2 (route 1, the SVD of B itself) with each
+triplet's right residual from the recurrence (below).
 """
 import numpy as np
 
@@ -90,3 +92,26 @@ def block_numrank(A, Q0, eps=1e-8, kmax=0):
     _, _, B, steps = block_gk(A, Q0, k, eps=eps)
     sig = np.linalg.svd(B, compute_uv=False)
     return int(np.sum(sig > eps * sig[0])), sig, steps
+
+
+def block_fsvd(A, Q0, steps, r, passes=2):
+    """The r largest triplets from `steps` block steps (no break test): B = X diag(sigma) Y^T (the
+    SVD of the (k+1)s x ks block lower bidiagonal B), U = Q X_r, V = P Y_r (the block form of
+    Algorithm 2, route 1).  A V = U diag(sigma) holds by construction (A P = Q B).  The right
+    residual follows from the next right block: A^T Q = P B^T + P_{k+1} R_{k+1} E^T (E picks the
+    last block of Q; P_{k+1} R_{k+1} = A^T Q_{k+1} - P_k S_{k+1}^T, reorthogonalized), so
+    A^T u_i - sigma_i v_i = P_{k+1} R_{k+1} x_i' with x_i' the last s entries of x_i and
+    ||A^T u_i - sigma_i v_i|| = ||R_{k+1} x_i'||.  Returns (U, sigma, V, residuals)."""
+    A = np.asarray(A, dtype=np.float64)
+    s = Q0.shape[1]
+    Q, P, B, st = block_gk(A, Q0, steps, eps=0.0, passes=passes)
+    ks = st * s
+    X, S, Yt = np.linalg.svd(B, full_matrices=False)
+    r = min(r, ks)
+    U = Q @ X[:, :r]
+    V = P @ Yt[:r].T
+    Qn, Sn, Pk = Q[:, ks:], B[ks:, ks - s:ks], P[:, ks - s:]
+    Z = _reorth(A.T @ Qn - Pk @ Sn.T, P, passes)
+    _, Rn = _qr_pos(Z)
+    est = np.linalg.norm(Rn @ X[ks:, :r], axis=0)
+    return U, S[:r], V, est

@@ -92,3 +92,48 @@ def test_recurrence_terms_without_reorthogonalization():
     assert np.linalg.norm(A.T @ Q[:, :ks] - P @ B[:ks, :ks].T) <= 1e-12 * na
     assert np.linalg.norm(Q.T @ Q - np.eye(Q.shape[1])) <= 1e-9
     assert np.linalg.norm(P.T @ P - np.eye(P.shape[1])) <= 1e-9
+
+
+def test_block_fsvd_relations_and_residuals():
+    """block_fsvd: A V = U diag(sigma) exactly (A P = Q B), orthonormal U and V, and the residual
+    from the recurrence (||R_{k+1} x_i'||) equal to ||A^T u_i - sigma_i v_i|| computed directly."""
+    A = synth.gaussian_product(400, 300, 60, 1e-3, seed=21, dtype=np.float64)
+    Q0 = np.random.default_rng(21).standard_normal((400, 4))
+    U, S, V, est = bgk.block_fsvd(A, Q0, 10, 12)
+    assert U.shape == (400, 12) and V.shape == (300, 12) and np.all(np.diff(S) <= 0)
+    assert np.linalg.norm(A @ V - U * S) <= 1e-12 * S[0]
+    assert np.linalg.norm(U.T @ U - np.eye(12)) <= 1e-12 and np.linalg.norm(V.T @ V - np.eye(12)) <= 1e-12
+    direct = np.linalg.norm(A.T @ U - V * S, axis=0)
+    assert est.max() > 1e-6 * S[0]  # not converged: the residuals are real numbers to compare
+    np.testing.assert_allclose(est, direct, rtol=1e-8, atol=1e-13 * S[0])
+
+
+def test_block_fsvd_single_vector_is_algorithm_2():
+    """s = 1 is Algorithm 2 (route 1): the same Ritz values and vectors as the single-vector oracle
+    after the same number of steps."""
+    A = synth.gaussian_product(300, 200, 200, 0.0, seed=22, dtype=np.float64)
+    q1 = synth.start_vector(300, 22)
+    U, S, V, est = bgk.block_fsvd(A, q1[:, None], 30, 5)
+    Uo, So, Vo, kp = oracle.fsvd(oracle.Operator.dense(A), 30, 5, q1, route=1)
+    assert kp == 30
+    np.testing.assert_allclose(S, So, rtol=1e-10)
+    sgn = np.sign(np.sum(V * Vo, axis=0))
+    assert np.linalg.norm(V - Vo * sgn, axis=0).max() <= 1e-8
+    assert np.linalg.norm(U - Uo * sgn, axis=0).max() <= 1e-8
+
+
+def test_block_fsvd_full_space_and_multiplicities():
+    """Blocks filling the column space give A's SVD with zero residuals; a block of 3 finds the
+    triple singular value 5 three times where one start vector finds it once."""
+    g = np.random.default_rng(23)
+    A = g.standard_normal((30, 20))
+    U, S, V, est = bgk.block_fsvd(A, g.standard_normal((30, 2)), 10, 20)
+    np.testing.assert_allclose(S, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
+    assert est.max() <= 1e-12 * S[0]
+    sigma = np.array([5.0, 5.0, 5.0, 3.0, 3.0, 1.0, 1.0, 1.0])
+    B8, _, _ = synth.prescribed_spectrum(70, 40, sigma, seed=24, dtype=np.float64)
+    _, S3, _, _ = bgk.block_fsvd(B8, g.standard_normal((70, 3)), 3, 3)
+    np.testing.assert_allclose(S3, [5.0, 5.0, 5.0], rtol=1e-10)
+    # one vector: three steps exhaust its Krylov space (one direction per distinct value)
+    _, S1, _, _ = bgk.block_fsvd(B8, g.standard_normal((70, 1)), 3, 3)
+    np.testing.assert_allclose(S1, [5.0, 3.0, 1.0], rtol=1e-10)
