@@ -269,6 +269,20 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
 int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, int kmax, const gk_opts *opts, int *rank,
                      double *sigma, int *steps, gk_info *info);
 
+/* One cycle of the block form of Algorithm 2 (route 1): `steps` block steps of the recurrence
+ * above from Q0 (or drawn as in gk_block_numrank) without a break test (fewer only when the
+ * blocks fill min(m, n)), the SVD of the block lower bidiagonal B = X S Y^T, and the r largest
+ * triplets U = Q X_r, V = P Y_r (A V = U S holds by construction), with each triplet's right
+ * residual ||A^T u_i - s_i v_i|| = ||R_{k+1} x_i'|| read from the next right block (x_i' the
+ * last s entries of x_i).  No restart: the accuracy is what the steps give.
+ *  steps: block steps, (steps + 1) s <= 1024;  r: 1 <= r <= steps * s.
+ *  U: m x r, S: r, V: n x r, resid: r -- device memory, column-major, f64; signs as gk_psvd.
+ * GK_FLAG_BLOCK_F32 applies (the block products in f32).  Returns GK_OK, GK_RANK_DEFICIENT
+ * when the blocks filled the space with fewer than r columns, GK_NOT_CONVERGED when the small
+ * SVD hit its sweep limit, or an error.  Experimental: not yet run on a GPU. */
+int gk_block_fsvd(const gk_matrix *A, int s, const double *Q0, int steps, int r, const gk_opts *opts, double *U,
+                  double *S, double *V, double *resid, gk_info *info);
+
 /* Device workspace (bytes) gk_block_numrank needs for this operator, s, kmax and opts
  * (0 for invalid arguments or without a device). */
 size_t gk_block_numrank_workspace(const gk_matrix *A, int s, int kmax, const gk_opts *opts);

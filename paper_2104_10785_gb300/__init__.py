@@ -7,6 +7,7 @@ binding.
 from .gk import (  # noqa: F401
     CSR,
     GKError,
+    gk_block_fsvd,
     gk_block_numrank,
     gk_block_numrank_workspace,
     gk_fsvd,

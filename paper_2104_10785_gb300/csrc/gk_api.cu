@@ -1429,6 +1429,141 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   return sweeps < 0 ? GK_NOT_CONVERGED : GK_OK;
 }
 
+// One cycle of the block form of Algorithm 2 (route 1): `steps` block steps without a break
+// test, the SVD of B (padded with zero columns to its square), U = Q X_r, V = P Y_r, and each
+// triplet's right residual ||R_{k+1} x_i'|| from the next right block (formed, never kept).
+int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in, int r, const gk_opts *oin, double *U,
+                    double *S, double *V, double *resid, gk_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launch_count();
+  g_err[0] = 0;
+  gk_info inf;
+  memset(&inf, 0, sizeof(inf));
+  if (info) *info = inf;
+  int rc = check_matrix(Ain);
+  if (rc) return rc;
+  const int64_t m = Ain->m, n = Ain->n, mn = m < n ? m : n;
+  if (s < 1 || s > kBlockMaxS || s > mn || steps_in < 1 || r < 1 || !U || !S || !V || !resid) return GK_INVALID_ARG;
+  int64_t kb = 0;
+  rc = block_steps(Ain, s, steps_in, &kb);
+  if (rc) return rc;
+  if ((int64_t)r > kb * s) return GK_INVALID_ARG;
+  Dev d;
+  if (!get_device(&d)) return GK_NO_DEVICE;
+  if (on_host(U) || on_host(S) || on_host(V) || on_host(resid)) return GK_INVALID_ARG;  // device outputs only
+  const gk_opts o = oin ? *oin : defaults();
+  cudaStream_t st = (cudaStream_t)o.stream;
+  OpStage stg;
+  rc = stage_plan(Ain, &stg);
+  if (rc) return rc;
+  const bool host_q0 = Q0 && on_host(Q0);
+  Op op = make_op(Ain);
+  BlockBufs b;
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
+  b.acc = accurate_ok(op);
+  b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
+  const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
+  Workspace ws;
+  rc = acquire(ws, bytes, o, st);
+  if (rc) return rc;
+  op = make_op(Ain);
+  block_layout(Ain, s, kb, d, stg, ws.base, &b, &op);
+  rc = stage_copy(Ain, stg, op, st);
+  if (rc) return rc;
+  const int64_t ldu = round_up(m, 32), ldv = round_up(n, 32), cols = (kb + 1) * s;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
+  GK_CUDA(cudaMemsetAsync(b.bc, 0, sizeof(BlockCtl), st));
+  GK_CUDA(cudaMemsetAsync(b.Bf, 0, sizeof(double) * cols * cols, st));
+  if (b.df) {
+    GK_CUDA(cudaMemsetAsync(b.Qs, 0, sizeof(float2) * ldu * cols, st));
+    GK_CUDA(cudaMemsetAsync(b.Ps, 0, sizeof(float2) * ldv * cols, st));
+  }
+  const double *q0 = Q0;
+  if (host_q0) {
+    GK_CUDA(cudaMemcpyAsync(b.q0, Q0, sizeof(double) * m * s, cudaMemcpyHostToDevice, st));
+    q0 = b.q0;
+  }
+  if (!q0) {
+    for (int c = 0; c < s; ++c) GK_CUDA(draw_start(b.W + (int64_t)c * m, m, o.seed + (uint64_t)c, st));
+    q0 = b.W;
+  }
+  int64_t nfresh = 0;
+  int breakdowns = 0;
+  rc = block_orth(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+  if (rc) return rc;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
+  rc = block_product(op, b, true, b.Q, ldu, s, st, d);
+  if (rc) return rc;
+  rc = block_orth(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+  if (rc) return rc;
+  GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
+  GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, 0.0, b.bc, st));
+  int64_t matvecs = s;
+  int steps = 1;
+  BlockCtl hb;
+  HostCtl hc;
+  for (;;) {  // eps = 0: no block ends the sweep; it runs kb steps or until the blocks fill min(m, n)
+    const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
+    rc = block_product(op, b, false, b.P + pj * ldv, ldv, s, st, d);
+    if (rc) return rc;
+    rc = block_orth(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+    if (rc) return rc;
+    GK_CUDA(block_dots(b.Q + qn * ldu, ldu, b.W, m, m, s, b.dpart, b.raw, st));
+    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)pj, 0, 0.0, b.bc, st));
+    matvecs += s;
+    rc = read_block(b, &hb, &hc, st);
+    if (rc) return rc;
+    if (steps >= kb || (int64_t)(steps + 1) * s > mn) break;
+    rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
+    if (rc) return rc;
+    rc = block_orth(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    if (rc) return rc;
+    GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
+    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)qn, 1, 0.0, b.bc, st));
+    matvecs += s;
+    rc = read_block(b, &hb, &hc, st);
+    if (rc) return rc;
+    ++steps;
+  }
+  const int K = (steps + 1) * s, ks = steps * s;
+  const int rr = r < ks ? r : ks;
+  // the next right block P_{k+1} R_{k+1} = A^T Q_{k+1} - P_k S_{k+1}^T (reorthogonalized): R_{k+1}
+  // in b.raw for the residuals
+  {
+    const int64_t qn = (int64_t)steps * s;
+    rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
+    if (rc) return rc;
+    rc = block_orth(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    if (rc) return rc;
+    GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
+    matvecs += s;
+  }
+  GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * cols, sizeof(double) * K, K,
+                            cudaMemcpyDeviceToDevice, st));
+  GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
+  // U = Q X_r (all K rows of X), V = P_{1..k} Y_r (the first ks rows: the padding columns of B
+  // never enter the right vectors of nonzero values)
+  GK_CUDA(ritz_gemm(b.Q, ldu, m, K, b.X, K, rr, U, m, st, d));
+  GK_CUDA(ritz_gemm(b.P, ldv, n, ks, b.Y, K, rr, V, n, st, d));
+  GK_CUDA(block_resid(b.raw, s, b.X, K, ks, rr, resid, st));
+  GK_CUDA(cudaMemcpyAsync(S, b.sigma, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
+  GK_CUDA(sign_normalize(U, m, m, V, n, n, rr, st));
+  int sweeps = 0;
+  GK_CUDA(cudaMemcpyAsync(&sweeps, b.sweeps, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GK_CUDA(cudaStreamSynchronize(st));
+  inf.steps = steps;
+  inf.kprime = ks;
+  inf.matvecs = matvecs;
+  inf.svd_sweeps = sweeps;
+  inf.breakdowns = breakdowns;
+  inf.sigma_est = hb.sest;
+  inf.seconds = seconds_since(t0);
+  inf.launches = launch_count() - l0;
+  if (info) *info = inf;
+  if (sweeps < 0) return GK_NOT_CONVERGED;
+  return rr < r ? GK_RANK_DEFICIENT : GK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // gk_fsvd: Algorithm 2 as printed (k steps of Algorithm 1, the SVD of B_{k'+1,k'}, no restart)
 // ---------------------------------------------------------------------------
@@ -1771,6 +1906,12 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
                gk_info *info) {
   NvtxRange r("gk_numrank");
   return numrank_impl(A, eps, kmax, opts, rank, sigma, info);
+}
+
+int gk_block_fsvd(const gk_matrix *A, int s, const double *Q0, int steps, int r, const gk_opts *opts, double *U,
+                  double *S, double *V, double *resid, gk_info *info) {
+  NvtxRange nv("gk_block_fsvd");
+  return block_fsvd_impl(A, s, Q0, steps, r, opts, U, S, V, resid, info);
 }
 
 size_t gk_block_numrank_workspace(const gk_matrix *A, int s, int kmax, const gk_opts *oin) {

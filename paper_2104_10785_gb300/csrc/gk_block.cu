@@ -161,6 +161,22 @@ __global__ void __launch_bounds__(32) k_block_judge(const double *__restrict__ r
   }
 }
 
+// est[i] = || R x_i' || for i < r: R = triu(raw) (s x s), x_i' = X[row0 .. row0 + s), column i
+// (column-major, ld ldx) -- the right residual of the block form of Algorithm 2's i-th triplet
+__global__ void k_block_resid(const double *__restrict__ raw, int s, const double *__restrict__ X, int ldx, int row0,
+                              int r, double *__restrict__ est) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r) return;
+  const double *x = X + (int64_t)i * ldx + row0;
+  double t = 0.0;
+  for (int a = 0; a < s; ++a) {
+    double v = 0.0;
+    for (int c = a; c < s; ++c) v = fma(raw[a + c * s], x[c], v);
+    t = fma(v, v, t);
+  }
+  est[i] = sqrt(t);
+}
+
 // *rank = #{i < n : sigma[i] > eps * sigma[0]}
 __global__ void k_block_count(const double *__restrict__ sigma, int n, double eps, int *rank) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -190,6 +206,13 @@ cudaError_t block_judge(const double *raw, int s, double *Bf, int64_t ldb, int r
                         BlockCtl *bc, cudaStream_t st) {
   if (s < 1 || s > kBlockMaxS) return cudaErrorInvalidValue;
   GK_LAUNCH(k_block_judge<<<1, 32, 0, st>>>(raw, s, Bf, ldb, row0, col0, side, eps, bc));
+  return cudaGetLastError();
+}
+
+cudaError_t block_resid(const double *raw, int s, const double *X, int ldx, int row0, int r, double *est,
+                        cudaStream_t st) {
+  if (r <= 0) return cudaSuccess;
+  GK_LAUNCH(k_block_resid<<<(r + 127) / 128, 128, 0, st>>>(raw, s, X, ldx, row0, r, est));
   return cudaGetLastError();
 }
 

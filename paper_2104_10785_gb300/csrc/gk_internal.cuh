@@ -237,6 +237,9 @@ cudaError_t block_dots(const double *X, int64_t ldx, const double *Y, int64_t ld
 // placed as T^T unless it ends the sweep; 2: the first right block, no test), into *bc
 cudaError_t block_judge(const double *raw, int s, double *Bf, int64_t ldb, int row0, int col0, int side, double eps,
                         BlockCtl *bc, cudaStream_t st);
+// est[i] = ||triu(raw) X[row0 .. row0 + s, i]|| for i < r (X column-major, ld ldx; device)
+cudaError_t block_resid(const double *raw, int s, const double *X, int ldx, int row0, int r, double *est,
+                        cudaStream_t st);
 // *rank = #{i < n : sigma[i] > eps sigma[0]} (device)
 cudaError_t block_count(const double *sigma, int n, double eps, int *rank, cudaStream_t st);
 

@@ -130,6 +130,9 @@ def lib():
             L.gk_block_numrank.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_double, C.c_int, P(gk_opts),
                                            P(C.c_int), C.c_void_p, P(C.c_int), P(gk_info)]
             L.gk_block_numrank.restype = C.c_int
+            L.gk_block_fsvd.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_int, C.c_int, P(gk_opts), C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, P(gk_info)]
+            L.gk_block_fsvd.restype = C.c_int
             L.gk_block_numrank_workspace.argtypes = [P(gk_matrix), C.c_int, C.c_int, P(gk_opts)]
             L.gk_block_numrank_workspace.restype = C.c_size_t
             L.gk_matvec.argtypes = [P(gk_matrix), C.c_int, C.c_void_p, C.c_void_p, P(gk_opts)]
@@ -489,6 +492,33 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
         raise GKError(st, "gk_block_numrank")
     d = info.as_dict()
     return r.value, (sig[: d["kprime"]] if sig is not None else None), steps.value, st, d
+
+
+def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None = None, stream=None,
+                  workspace=None, scale: float = 1.0, check: bool = True, orth_f64: bool = False,
+                  f32_products: bool = False):
+    """One cycle of the block form of Algorithm 2 on a CUDA operator (gk_block_fsvd, experimental).
+    Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on A's device."""
+    M, keep_a = make_matrix(A, scale)
+    if start is not None and tuple(start.shape) != (M.m, int(s)):
+        raise ValueError(f"start block must be m x s = {M.m} x {int(s)}, got {tuple(start.shape)}")
+    dev = A.device
+    if dev.type != "cuda":
+        raise ValueError("gk_block_fsvd takes a CUDA operator (its outputs are device tensors)")
+    U = torch.empty((r, M.m), dtype=torch.float64, device=dev)
+    V = torch.empty((r, M.n), dtype=torch.float64, device=dev)
+    S = torch.empty(r, dtype=torch.float64, device=dev)
+    res = torch.empty(r, dtype=torch.float64, device=dev)
+    q0 = start.to(torch.float64).t().contiguous() if start is not None else None
+    o, ka = _opts(dev, seed=seed, stream=stream, workspace=workspace, orth_f64=orth_f64)
+    if f32_products:
+        o.flags |= GK_FLAG_BLOCK_F32
+    info = gk_info()
+    st = lib().gk_block_fsvd(C.byref(M), int(s), _ptr(q0), int(steps), int(r), C.byref(o), _ptr(U), _ptr(S), _ptr(V),
+                             _ptr(res), C.byref(info))
+    if check and st < 0:
+        raise GKError(st, "gk_block_fsvd")
+    return U.T, S, V.T, res, st, info.as_dict()
 
 
 def gk_block_numrank_workspace(A, s: int, kmax: int = 0, *, orth_f64: bool = False) -> int:

@@ -35,7 +35,7 @@ int main(void) {
   st[4] = gk_block_numrank(&M, 0, NULL, 1e-8, 0, &o, &r, NULL, &steps, &info); /* s = 0: refused */
   st[5] = gk_matvec(&M, 0, S, U, &o);
   /* referenced for the link check only (not called) */
-  any_fn refs[] = {(any_fn)gk_psvd_workspace, (any_fn)gk_numrank_workspace, (any_fn)gk_block_numrank_workspace,
+  any_fn refs[] = {(any_fn)gk_psvd_workspace, (any_fn)gk_numrank_workspace, (any_fn)gk_block_numrank_workspace, (any_fn)gk_block_fsvd,
                   (any_fn)gk_residuals, (any_fn)gk_psvd_batched, (any_fn)gk_numrank_batched,
                   (any_fn)gk_rsgd_batched, (any_fn)gk_sketch_batched, (any_fn)gk_mlp_forward, (any_fn)gk_mlp_grad,
                   (any_fn)gk_mlp_train, (any_fn)gk_matvec_static, (any_fn)gk_predictor_load,

@@ -235,3 +235,27 @@ def test_plain_c_client_compiles_links_and_gets_no_device(tmp_path):
     no_dev, inval = str(-7), str(-1)
     assert out[:6] == [no_dev, no_dev, no_dev, no_dev, inval, no_dev], out
     assert out[6] == "GK_NO_DEVICE"
+
+
+def test_block_fsvd_checks_arguments_before_the_device():
+    """gk_block_fsvd refuses a block size outside 1..min(32, m, n), no steps, (steps + 1) s past
+    1024, and r outside 1..steps s with GK_INVALID_ARG before it looks for a device."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+    from paper_2104_10785_gb300 import gk as raw
+
+    A = np.ones((40, 30))
+    M = raw.gk_matrix(raw.GK_DENSE, raw.GK_F64, 40, 30, 30, 1.0, A.ctypes.data, None, None, None, None, None)
+    L = raw.lib()
+    buf = np.zeros(40 * 30)
+    p = buf.ctypes.data
+
+    def call(s=4, steps=3, r=5):
+        return L.gk_block_fsvd(C.byref(M), s, None, steps, r, None, p, p, p, p, None)
+
+    for bad in (dict(s=0), dict(s=33), dict(steps=0), dict(s=4, steps=256), dict(r=0), dict(s=4, steps=3, r=13)):
+        assert call(**bad) == raw.GK_INVALID_ARG, bad
+    if not torch.cuda.is_available():
+        assert call() == raw.GK_NO_DEVICE
