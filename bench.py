@@ -1232,7 +1232,8 @@ def profile_case(args):
     --case sketch: `reps` calls of gk_sketch_batched on the same kind of operator (one problem;
     --tcgen05: the tensor-core form).
     --case block: `reps` calls of gk_block_numrank (block size --s, --kmax block steps, eps 1e-8)
-    on the same kind of operator (--block-f32: its f32 block products)."""
+    on the same kind of operator (--block-f32: its f32 block products; --fsvd R: gk_block_fsvd for R
+    triplets after --kmax block steps instead)."""
     import torch
 
     import paper_2104_10785_gb300 as gk
@@ -1251,6 +1252,8 @@ def profile_case(args):
                 gk.gk_matvec(A, y, trans=True)
             elif args.case == "sketch":
                 gk.gk_sketch_batched([A], seed=1, tcgen05=args.tcgen05)
+            elif args.case == "block" and args.fsvd > 0:
+                gk.gk_block_fsvd(A, args.s, args.kmax, args.fsvd, f32_products=args.block_f32)
             elif args.case == "block":
                 gk.gk_block_numrank(A, args.s, 1e-8, args.kmax, f32_products=args.block_f32)
             else:
@@ -1311,6 +1314,8 @@ def main():
     ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")
     ap.add_argument("--kmax", type=int, default=16, help="--case block: block steps")
     ap.add_argument("--block-f32", action="store_true", help="--case block: f32 block products (GK_FLAG_BLOCK_F32)")
+    ap.add_argument("--fsvd", type=int, default=0,
+                    help="--case block: the block form of Algorithm 2 for this many triplets instead of the rank")
     args = ap.parse_args()
     if args.case is not None:
         profile_case(args)
