@@ -1527,6 +1527,12 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   }
   const int K = (steps + 1) * s, ks = steps * s;
   const int rr = r < ks ? r : ks;
+  if (rr < r) {  // the blocks filled the space first: the trailing triplets are zero
+    GK_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * (size_t)m * r, st));
+    GK_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)n * r, st));
+    GK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * (size_t)r, st));
+    GK_CUDA(cudaMemsetAsync(resid, 0, sizeof(double) * (size_t)r, st));
+  }
   // the next right block P_{k+1} R_{k+1} = A^T Q_{k+1} - P_k S_{k+1}^T (reorthogonalized): R_{k+1}
   // in b.raw for the residuals
   {
