@@ -259,3 +259,35 @@ def test_block_fsvd_checks_arguments_before_the_device():
         assert call(**bad) == raw.GK_INVALID_ARG, bad
     if not torch.cuda.is_available():
         assert call() == raw.GK_NO_DEVICE
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """Every struct the binding mirrors (gk_matrix, gk_opts, gk_info, gk_batch_item, gk_rsgd_args)
+    has, under the C compiler and include/gk.h, the same size and the same offset for each field
+    as its ctypes class: a field added on one side only would shift every field after it."""
+    import ctypes
+    import shutil
+
+    from paper_2104_10785_gb300 import gk as binding
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [binding.gk_matrix, binding.gk_opts, binding.gk_info, binding.gk_batch_item, binding.gk_rsgd_args]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gk.h"', "int main(void) {"]
+    want = []
+    for cls in structs:
+        name = cls.__name__
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % name)
+        want.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (name, f))
+            want.append(getattr(cls, f).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"), "-o", exe, str(src)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
