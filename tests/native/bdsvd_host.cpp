@@ -24,6 +24,7 @@ extern "C" int bd_svd_host(const double *d_in, const double *e_in, int n, double
     int nl = 0, nr = 0;
     rc = gk::bd_step(d.data(), e.data(), &st, rl.data(), &nl, rr.data(), &nr);
     if (rc <= 0) break;
+    if (nl < 0 || nl > n || nr < 0 || nr > n) return -3;  // the kernel has room for n rotations a side
     ++chases[rc == 1 ? 0 : 1];
     for (int i = 0; i < n; ++i) {
       if (rc == 1) {  // a Golub-Kahan step: adjacent pairs, the carried-register form

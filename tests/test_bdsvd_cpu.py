@@ -132,3 +132,23 @@ def test_lower_bidiagonal_through_its_transpose(bdsvd):
     np.testing.assert_allclose(s, np.linalg.svd(Bpad, compute_uv=False), rtol=0, atol=1e-13 * s[0])
     assert np.linalg.norm(Bpad - Yp @ np.diag(s) @ Xp.T) <= 1e-13 * s[0] * K
     assert np.all(np.abs(Xp[K - 1, :kp]) <= 1e-13)
+
+
+def test_no_access_outside_the_kernels_buffers_under_sanitizers(tmp_path):
+    """The step and row functions, built with AddressSanitizer and UndefinedBehaviorSanitizer and
+    driven over orders 1..64 (random, zero diagonal entries, splits, graded, clustered;
+    tests/native/bdsvd_fuzz.cpp): no access outside d, e (n entries) and the n rotations a side
+    that the GPU kernel gives each step, no undefined behaviour, every call finished."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path / "bdsvd_fuzz")
+    build = subprocess.run([cxx, "-O1", "-g", "-std=c++17", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+                            "-o", exe, os.path.join(HERE, "native", "bdsvd_fuzz.cpp"),
+                            os.path.join(HERE, "native", "bdsvd_host.cpp")], capture_output=True, text=True)
+    if build.returncode != 0:
+        pytest.skip("the compiler has no sanitizer runtime: " + build.stderr.strip().splitlines()[-1][:200])
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0")
+    out = subprocess.run([exe, "64"], capture_output=True, text=True, env=env)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert int(out.stdout.split()[-1]) == 64 * 5
