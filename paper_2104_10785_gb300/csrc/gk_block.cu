@@ -14,11 +14,13 @@
 // triangle, place it (or its transpose) into B, and judge the block's 2-norm:
 //   * k_block_dots / k_block_dots_sum: raw = X^T Y for two len x s column blocks, f64, the
 //     row chunks summed in a fixed order;
-//   * k_block_judge: T = triu(raw), ||T||_2 = sqrt(lambda_max(T^T T)) by cyclic Jacobi on one
-//     warp, the running estimate of sigma_1 and the block break tests;
+//   * k_block_judge: T = triu(raw), ||T||_2 by cyclic Jacobi on the scaled T^T T on one warp,
+//     the running estimate of sigma_1 and the block break tests (the arithmetic in
+//     gk_block_judge.cuh, which the CPU tests also build for the host);
 //   * k_block_count: Algorithm 3's count of the singular values of B above eps sigma_1(B).
 #include <math.h>
 
+#include "gk_block_judge.cuh"
 #include "gk_internal.cuh"
 
 namespace gk {
@@ -67,17 +69,11 @@ __global__ void k_block_dots_sum(const double *__restrict__ part, int G, int pai
   raw[p] = v;
 }
 
-// One warp.  T = triu(raw) (s x s, T[a + c s] = raw[a + c s] for a <= c, else 0); its 2-norm
-// from the eigenvalues of G = T^T T (cyclic Jacobi: rotations while some |g_pq| exceeds
-// 1e-16 sqrt(|g_pp g_qq|), at most kSweeps sweeps; the largest diagonal entry is a lower
-// bound on lambda_max at any point and equals it on convergence).  side 0 (S_{j+1}, left):
-// sest = max(sest, ||T||), break when eps > 0 and ||T|| <= eps sest; T placed at
-// Bf[row0 + a, col0 + c].  side 1 (R_{j+1}, right): break when eps > 0 and ||T|| <=
-// eps max(sest, ||T||), else sest = max(sest, ||T||) and T^T placed at Bf[row0 + c, col0 + a].
-// side 2 (R_1, the first right block): no test, sest = ||T||, T^T placed.  A non-finite norm
-// sets brk = 2 (nothing placed).
-constexpr int kSweeps = 60;
-
+// One warp: the block judge of gk_block_judge.cuh -- T = triu(raw), mu = max |t_ac| (a warp
+// reduction), G = (T / mu)^T (T / mu), cyclic Jacobi with the rotations' column and row updates
+// spread over the lanes, then lane 0 takes ||T||_2 and the side's break test (sest, nrm, brk and
+// the sweeps in *bc).  T (side 0) or T^T (sides 1, 2) is placed into Bf at (row0, col0) unless the
+// block broke (a left block that breaks is placed: it is B's last row block).
 __global__ void __launch_bounds__(32) k_block_judge(const double *__restrict__ raw, int s, double *__restrict__ Bf,
                                                     int64_t ldb, int row0, int col0, int side, double eps,
                                                     BlockCtl *bc) {
@@ -86,62 +82,40 @@ __global__ void __launch_bounds__(32) k_block_judge(const double *__restrict__ r
   __shared__ int s_brk;
   const int lane = threadIdx.x;
   const int ss = s * s;
-  for (int e = lane; e < ss; e += 32) T[e] = (e % s) <= (e / s) ? raw[e] : 0.0;
-  __syncwarp();
+  double mu = 0.0;
   for (int e = lane; e < ss; e += 32) {
-    const int p = e % s, q = e / s;
-    double v = 0.0;
-    for (int a = 0; a < s; ++a) v = fma(T[a + p * s], T[a + q * s], v);
-    G[e] = v;
+    T[e] = bj_triu(raw, s, e);
+    mu = bj_absmax(mu, fabs(T[e]));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mu = bj_absmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+  const double rmu = bj_rscale(mu);
+  __syncwarp();
+  for (int e = lane; e < ss; e += 32) G[e] = bj_gram(T, s, rmu, e);
   __syncwarp();
   int sweeps = 0;
-  for (; sweeps < kSweeps; ++sweeps) {
-    bool rotated = false;
-    for (int p = 0; p < s - 1; ++p) {
-      for (int q = p + 1; q < s; ++q) {
-        __syncwarp();
-        const double apq = G[p + q * s], app = G[p + p * s], aqq = G[q + q * s];
-        if (apq == 0.0 || fabs(apq) <= 1e-16 * sqrt(fabs(app) * fabs(aqq))) continue;  // the same on every lane
-        rotated = true;
-        // the rotation that zeroes g_pq (the symmetric 2 x 2 Schur decomposition)
-        const double tau = (aqq - app) / (2.0 * apq);
-        const double t = fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
-        __syncwarp();
-        if (lane < s) {  // columns p and q
-          const double gp = G[lane + p * s], gq = G[lane + q * s];
-          G[lane + p * s] = c * gp - sn * gq;
-          G[lane + q * s] = sn * gp + c * gq;
-        }
-        __syncwarp();
-        if (lane < s) {  // rows p and q
-          const double gp = G[p + lane * s], gq = G[q + lane * s];
-          G[p + lane * s] = c * gp - sn * gq;
-          G[q + lane * s] = sn * gp + c * gq;
+  if (rmu > 0.0) {
+    for (; sweeps < kBlockSweeps; ++sweeps) {
+      bool rotated = false;
+      for (int p = 0; p < s - 1; ++p) {
+        for (int q = p + 1; q < s; ++q) {
+          __syncwarp();
+          double c, sn;
+          if (!bj_rotation(G, s, p, q, &c, &sn)) continue;  // the same on every lane
+          rotated = true;
+          __syncwarp();
+          if (lane < s) bj_col(G, s, p, q, c, sn, lane);
+          __syncwarp();
+          if (lane < s) bj_row(G, s, p, q, c, sn, lane);
         }
       }
+      if (!rotated) break;
     }
-    if (!rotated) break;
   }
   __syncwarp();
   if (lane == 0) {
-    double lmax = 0.0;
-    for (int p = 0; p < s; ++p) lmax = fmax(lmax, G[p + p * s]);
-    const double nrm = sqrt(lmax);
-    double sest = bc->sest;
-    int brk = 0;
-    if (!isfinite(nrm)) {
-      brk = 2;
-    } else if (side == 0) {
-      sest = fmax(sest, nrm);
-      brk = (eps > 0.0 && nrm <= eps * sest) ? 1 : 0;
-    } else if (side == 1) {
-      brk = (eps > 0.0 && nrm <= eps * fmax(sest, nrm)) ? 1 : 0;
-      if (!brk) sest = fmax(sest, nrm);
-    } else {
-      sest = fmax(sest, nrm);
-    }
+    double sest = bc->sest, nrm = 0.0;
+    const int brk = bj_decide(G, s, mu, side, eps, &sest, &nrm);
     bc->sest = sest;
     bc->nrm = nrm;
     bc->brk = brk;
@@ -153,11 +127,7 @@ __global__ void __launch_bounds__(32) k_block_judge(const double *__restrict__ r
   if (!place) return;
   for (int e = lane; e < ss; e += 32) {
     const int a = e % s, c = e / s;
-    if (a > c) continue;
-    if (side == 0)
-      Bf[(int64_t)(row0 + a) + (int64_t)(col0 + c) * ldb] = T[e];
-    else
-      Bf[(int64_t)(row0 + c) + (int64_t)(col0 + a) * ldb] = T[e];
+    if (a <= c) Bf[bj_place(side, row0, col0, a, c, ldb)] = T[e];
   }
 }
 
