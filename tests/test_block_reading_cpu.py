@@ -101,3 +101,127 @@ def test_column_wise_block_qr_gives_the_oracles_B(case):
         np.testing.assert_allclose(sig, sig_or[: k * s], rtol=0, atol=1e-13 * sig_or[0])
     if case in ("repeated_s3", "product_s3", "product_s8"):
         assert replaced > 0  # the rank-deficient blocks were exercised
+
+
+def column_block_fsvd(A, Q0, steps, r, fresh_seed=0):
+    """gk_block_fsvd's flow in numpy: `steps` block steps without a break test by the column-wise
+    QR above, the next right block's R_{k+1} as the inner products P_{k+1}^T (A^T Q_{k+1}), the SVD
+    of B padded with zero columns to its square, U = Q X_r (all (k+1)s rows of X), V = P Y_r (the
+    first ks rows of Y) and residuals ||R_{k+1} x_i'|| (x_i' = rows ks .. ks + s of x_i)."""
+    m, n = A.shape
+    s = Q0.shape[1]
+    mn = min(m, n)
+    cols = (steps + 1) * s
+    Q, P, B = np.zeros((m, cols)), np.zeros((n, cols)), np.zeros((cols, cols))
+    g = np.random.default_rng(fresh_seed)
+    scale = [0.0]
+
+    def orth(Bas, jc0, W):
+        for c in range(W.shape[1]):
+            jc = jc0 + c
+            w = W[:, c].copy()
+            for _ in range(2 if jc > 0 else 0):
+                w -= Bas[:, :jc] @ (Bas[:, :jc].T @ w)
+            nrm = np.linalg.norm(w)
+            scale[0] = max(scale[0], nrm)
+            if nrm <= 2.0**-46 * scale[0]:
+                # a fresh direction; zero when the basis already spans the space (NM_FRESH)
+                f = g.uniform(-1.0, 1.0, Bas.shape[0])
+                f0 = np.linalg.norm(f)
+                for _ in range(2):
+                    f -= Bas[:, :jc] @ (Bas[:, :jc].T @ f)
+                nf = np.linalg.norm(f)
+                Bas[:, jc] = f / nf if nf > 1e-8 * f0 else 0.0
+            else:
+                Bas[:, jc] = w / nrm
+
+    orth(Q, 0, Q0)
+    scale[0] = 0.0
+    W = A.T @ Q[:, :s]
+    orth(P, 0, W)
+    B[:s, :s] = np.triu(P[:, :s].T @ W).T
+    k = 1
+    while True:
+        pj, qn = (k - 1) * s, k * s
+        W = A @ P[:, pj:pj + s]
+        orth(Q, qn, W)
+        B[qn:qn + s, pj:pj + s] = np.triu(Q[:, qn:qn + s].T @ W)
+        if k >= steps or (k + 1) * s > mn:
+            break
+        W = A.T @ Q[:, qn:qn + s]
+        orth(P, qn, W)
+        B[qn:qn + s, qn:qn + s] = np.triu(P[:, qn:qn + s].T @ W).T
+        k += 1
+    qn = k * s
+    W = A.T @ Q[:, qn:qn + s]
+    orth(P, qn, W)
+    R = np.triu(P[:, qn:qn + s].T @ W)
+    K, ks = (k + 1) * s, k * s
+    rr = min(r, ks)
+    X, S, Yt = np.linalg.svd(B[:K, :K])
+    U = Q[:, :K] @ X[:, :rr]
+    V = P[:, :ks] @ Yt[:rr, :ks].T
+    res = np.linalg.norm(R @ X[ks:ks + s, :rr], axis=0)
+    return U, S[:rr], V, res, k
+
+
+def angle_err(X, Y):
+    sg = np.sign(np.sum(X * Y, axis=0))
+    sg[sg == 0] = 1
+    return np.linalg.norm(X - Y * sg[None, :], axis=0).max()
+
+
+@pytest.mark.parametrize("m,n,s,steps,r,rank", [(400, 300, 4, 10, 12, 0), (300, 200, 1, 30, 5, 0),
+                                                (500, 240, 8, 6, 30, 0), (260, 180, 4, 5, 8, 12)])
+def test_column_wise_block_fsvd_gives_the_oracles_triplets(m, n, s, steps, r, rank):
+    """The flow gk_block_fsvd runs gives oracle/block_gk.block_fsvd's triplets and residuals: values
+    to 1e-12 relative, vectors to 1e-9, residuals to 1e-10 relative (1e-13 sigma_1 absolute for the
+    converged ones); with rank > 0 the operator has that rank, the blocks run past it (fresh
+    completions, whichever stream draws them) and the r < rank leading triplets are exact."""
+    if rank:
+        A = synth.gaussian_product(m, n, rank, 0.0, seed=m + s, dtype=np.float64)
+    else:
+        A = synth.gaussian_product(m, n, min(m, n), 1e-3, seed=m + s, dtype=np.float64)
+    Q0 = np.random.default_rng(m + steps).standard_normal((m, s))
+    Uo, So, Vo, reso = bgk.block_fsvd(A, Q0, steps, r)
+    for fresh_seed in (0, 1):
+        U, S, V, res, k = column_block_fsvd(A, Q0, steps, r, fresh_seed)
+        assert k == steps
+        np.testing.assert_allclose(S, So, rtol=1e-12)
+        assert angle_err(U, Uo) < 1e-9 and angle_err(V, Vo) < 1e-9
+        np.testing.assert_allclose(res, reso, rtol=1e-10, atol=1e-13 * So[0])
+        if rank:
+            np.testing.assert_allclose(S, np.linalg.svd(A, compute_uv=False)[:r], rtol=1e-12)
+            assert res.max() <= 1e-12 * So[0]
+
+
+def test_block_fsvd_when_the_blocks_fill_the_space():
+    """min(m, n) = 40 columns filled after 5 blocks of 8 (of the 10 asked for): the sweep stops, the
+    values are A's (LAPACK), every residual is at rounding level (the next right block lies in
+    the filled space), and the oracle agrees."""
+    A = np.random.default_rng(3).standard_normal((60, 40))
+    Q0 = np.random.default_rng(4).standard_normal((60, 8))
+    U, S, V, res, k = column_block_fsvd(A, Q0, 10, 40)
+    assert k == 5
+    np.testing.assert_allclose(S, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
+    assert res.max() <= 1e-12 * S[0]
+    np.testing.assert_allclose(A @ V, U * S, rtol=0, atol=1e-12 * S[0])
+    Uo, So, Vo, reso = bgk.block_fsvd(A, Q0, 10, 40)
+    np.testing.assert_allclose(S, So, rtol=1e-12)
+    assert reso.max() <= 1e-12 * S[0]
+
+
+@pytest.mark.parametrize("m,n,s", [(20, 30, 4), (21, 20, 4), (30, 20, 4), (24, 24, 8)])
+def test_blocks_past_the_left_space_are_zero(m, n, s):
+    """When the last left block Q_{k+1} has more columns than R^m has room for (a wide operator, or
+    m < (k + 1) s), the fresh completions of its excess columns are zero (NM_FRESH), so their
+    entries of S_{k+1} = Q_{k+1}^T (A P_k) are zero and sigma(B) = sigma(A) (LAPACK) once the right
+    blocks fill min(m, n); the oracle (Householder QR of the reorthogonalized block) agrees."""
+    A = np.random.default_rng(m * n).standard_normal((m, n))
+    Q0 = np.random.default_rng(s).standard_normal((m, s))
+    r, sig, k, _ = column_block_gk(A, Q0, 1e-8, 0)
+    assert k * s == min(m, n) and r == min(m, n)
+    np.testing.assert_allclose(sig, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
+    r_or, sig_or, k_or = bgk.block_numrank(A, Q0, eps=1e-8)
+    assert (r_or, k_or) == (r, k)
+    np.testing.assert_allclose(sig, sig_or[: k * s], rtol=1e-12)

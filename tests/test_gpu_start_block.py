@@ -111,13 +111,16 @@ def test_block_rank_csr_matches_oracle():
     assert res[2] == 8 and res[4]["stop_reason"] == 0
 
 
-@pytest.mark.parametrize("m,n,s", [(30, 20, 4), (50, 20, 20)])
+@pytest.mark.parametrize("m,n,s", [(30, 20, 4), (50, 20, 20), (20, 30, 4), (21, 20, 4), (24, 24, 8)])
 def test_blocks_filling_the_space_give_lapack_singular_values(m, n, s):
-    """When the blocks fill min(m, n) = n columns, P is square orthogonal and sigma(B) = sigma(A)."""
+    """When the right blocks fill min(m, n) columns, P spans A's row space and sigma(B) = sigma(A);
+    a last left block with more columns than R^m has room for (wide, square, m just above n) gets
+    zero columns for the excess (the fresh completions find no direction), whose entries of
+    S_{k+1} are zero."""
     A = synth.rng(m + s).standard_normal((m, n))
     Q0 = synth.rng(s).standard_normal((m, s))
     rk, sig, steps, st, info = gk().gk_block_numrank(cuda(A), s, 1e-8, start=cuda(Q0), want_sigma=True)
-    assert st == 0 and steps * s == n and rk == n
+    assert st == 0 and steps * s == min(m, n) and rk == min(m, n)
     np.testing.assert_allclose(sig.cpu().numpy(), np.linalg.svd(A, compute_uv=False), rtol=1e-12)
 
 
