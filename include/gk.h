@@ -277,14 +277,15 @@ int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, in
  * last s entries of x_i).  No restart: the accuracy is what the steps give.
  *  steps: block steps, (steps + 1) s <= 1024;  r: 1 <= r <= steps * s.
  *  U: m x r, S: r, V: n x r, resid: r -- device memory, column-major, f64; signs as gk_psvd.
- * GK_FLAG_BLOCK_F32 applies (the block products in f32).  Returns GK_OK, GK_RANK_DEFICIENT
- * when the blocks filled the space with fewer than r columns, GK_NOT_CONVERGED when the small
+ * GK_FLAG_BLOCK_F32 applies (the block products in f32).  A caller workspace (opts->workspace)
+ * needs gk_block_numrank_workspace(A, s, steps, opts) bytes.  Returns GK_OK, GK_RANK_DEFICIENT
+ * when the blocks filled the space with fewer than r columns (the trailing triplets zero), GK_NOT_CONVERGED when the small
  * SVD hit its sweep limit, or an error.  Experimental: not yet run on a GPU. */
 int gk_block_fsvd(const gk_matrix *A, int s, const double *Q0, int steps, int r, const gk_opts *opts, double *U,
                   double *S, double *V, double *resid, gk_info *info);
 
-/* Device workspace (bytes) gk_block_numrank needs for this operator, s, kmax and opts
- * (0 for invalid arguments or without a device). */
+/* Device workspace (bytes) gk_block_numrank needs for this operator, s, kmax and opts, and
+ * gk_block_fsvd with steps = kmax (0 for invalid arguments or without a device). */
 size_t gk_block_numrank_workspace(const gk_matrix *A, int s, int kmax, const gk_opts *opts);
 
 /* F-SVD as printed (Algorithm 2): k steps of Algorithm 1 (lower-bidiagonal GK
