@@ -721,6 +721,33 @@ def run_gk(args, rank, world):
         except Exception as exc:  # an auxiliary leg: the headline stands without it
             fsvd = {"error": repr(exc)[:300]}
 
+    # the block form of Algorithm 2 on the same operator (experimental, --block-leg S,STEPS): one
+    # cycle of STEPS blocks of S start vectors, the k largest triplets, their FP64-grade residuals
+    block = None
+    if args.block_leg:
+        try:
+            bs, bsteps = (int(v) for v in args.block_leg.split(","))
+            bkw = dict(seed=w["seed"], f32_products=args.block_f32)
+            gk.gk_block_fsvd(A, bs, bsteps, k, **bkw)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = max(1, min(args.steps, 3))
+            e0.record(stream)
+            for _ in range(reps):
+                Ub, Sb, Vb, rb_est, stb, infb = gk.gk_block_fsvd(A, bs, bsteps, k, **bkw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bms = e0.elapsed_time(e1) / reps
+            ra, rb = gk.gk_residuals(A, Ub, Sb, Vb)
+            block = {"value": k / (bms / 1e3), "unit": "triplets/s", "ms_per_step": bms, "s": bs, "block_steps": bsteps,
+                     "f32_products": bool(args.block_f32), "status": stb, "matvecs": infb["matvecs"],
+                     "breakdowns": infb["breakdowns"], "launches": infb["launches"],
+                     "resid_est_max_rel": float(rb_est.max()) / float(Sb[0]),
+                     "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sb[0])}
+        except Exception as exc:  # an auxiliary leg: the headline stands without it
+            block = {"error": repr(exc)[:300]}
+
     # the same solve with two classical Gram-Schmidt passes per vector (the rule the paper's
     # reorthogonalization is run with when cancellation is not tested), and with the fused sweep
     # (one pass over A per step); same operator, K and start vector
@@ -865,6 +892,7 @@ def run_gk(args, rank, world):
         "breakdown_ms_per_step": breakdown,
         "roofline": roof, "clocks": clk, "gpu_launches": None,
         "e2e": e2e, "cpu_baseline": cpu, "plain_f32": plain, "fixed_krylov": fixed, "fsvd": fsvd,
+        **({"block_fsvd": block} if args.block_leg else {}),
         "two_pass_cgs": legs.get("two_pass_cgs"), "fused_sweep": legs.get("fused_sweep"),
         "gen_seconds": w["gen_seconds"],
         "batched": batched,
@@ -1311,6 +1339,9 @@ def main():
                     help="headline solve: Ritz vectors from the double-f32 basis copies (GK_FLAG_RITZ_DF)")
     ap.add_argument("--sketch-tc", action="store_true",
                     help="headline solve: the predictor's sketch on the tcgen05 tensor cores (GK_FLAG_SKETCH_TC)")
+    ap.add_argument("--block-leg", default=None, metavar="S,STEPS",
+                    help="headline: also time gk_block_fsvd (S start vectors, STEPS block steps, the workload's k "
+                         "triplets; --block-f32 for its f32 products) on the same operator (experimental)")
     ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")
     ap.add_argument("--kmax", type=int, default=16, help="--case block: block steps")
     ap.add_argument("--block-f32", action="store_true", help="--case block: f32 block products (GK_FLAG_BLOCK_F32)")
