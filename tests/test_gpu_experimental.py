@@ -10,9 +10,10 @@ Skipped unless GK_EXPERIMENTAL=1: each kernel's host-testable part is covered by
   * GK_FLAG_SKETCH_TC (k_sketch_tc): the sketch on tcgen05 against mma.sync on the same bf16
     operator: both accumulate bf16 products in f32 in the tensor pipe, in different orders, so
     the features (logs of the sketch's singular values) agree to ~1e-5; 1e-4 is the bound;
-  * GK_FLAG_BLOCK_F32 (k_acc_gemm in f32): the block rank with f32 block products against the
-    oracle: the rank exactly, sigma(B) above the cut within 1e-5 relative (f32 products carry
-    ~2^-24 (34) sum |a x| per entry)."""
+  * GK_FLAG_BLOCK_F32 (k_acc_gemm_narrow for blocks of up to 16 vectors, k_acc_gemm's FAST
+    instantiation above): the block rank with f32 block products against the oracle: the rank
+    exactly, sigma(B) above the cut within 1e-5 relative (f32 products carry ~2^-24 (34) sum |a x|
+    per entry)."""
 import os
 
 import numpy as np
@@ -83,8 +84,11 @@ def test_fsvd_route_1_with_bidiagonal_svd_matches_the_default(m, n, k, r):
     assert angle_err(U1.cpu().numpy(), U2.cpu().numpy()) < 1e-9
 
 
-@pytest.mark.parametrize("dtype,m,n,r,s,eps", [("bf16", 3000, 1000, 40, 5, 1e-2), ("f32", 20000, 1500, 60, 8, 1e-5)])
+@pytest.mark.parametrize("dtype,m,n,r,s,eps", [("bf16", 3000, 1000, 40, 5, 1e-2), ("f32", 20000, 1500, 60, 8, 1e-5),
+                                                ("f32", 5000, 1300, 50, 12, 1e-5), ("bf16", 2500, 900, 45, 20, 1e-2)])
 def test_block_rank_with_f32_products(dtype, m, n, r, s, eps):
+    """s <= 8 and s <= 16 take the narrow tiles (k_acc_gemm_narrow, 8 or 16 vectors per CTA), s = 20
+    the 32-vector tile of k_acc_gemm's FAST instantiation."""
     from oracle import block_gk as bgk
 
     A = synth.gaussian_product(m, n, r, 1e-7, seed=m + n + s, dtype=np.float64)
