@@ -727,7 +727,7 @@ def run_gk(args, rank, world):
     if args.block_leg:
         try:
             bs, bsteps = (int(v) for v in args.block_leg.split(","))
-            bkw = dict(seed=w["seed"], f32_products=args.block_f32)
+            bkw = dict(seed=w["seed"], f32_products=args.block_f32, ritz_df=args.ritz_df)
             gk.gk_block_fsvd(A, bs, bsteps, k, **bkw)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -741,7 +741,7 @@ def run_gk(args, rank, world):
             bms = e0.elapsed_time(e1) / reps
             ra, rb = gk.gk_residuals(A, Ub, Sb, Vb)
             block = {"value": k / (bms / 1e3), "unit": "triplets/s", "ms_per_step": bms, "s": bs, "block_steps": bsteps,
-                     "f32_products": bool(args.block_f32), "status": stb, "matvecs": infb["matvecs"],
+                     "f32_products": bool(args.block_f32), "ritz_df": bool(args.ritz_df), "status": stb, "matvecs": infb["matvecs"],
                      "breakdowns": infb["breakdowns"], "launches": infb["launches"],
                      "resid_est_max_rel": float(rb_est.max()) / float(Sb[0]),
                      "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sb[0])}

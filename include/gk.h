@@ -277,7 +277,8 @@ int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, in
  * last s entries of x_i).  No restart: the accuracy is what the steps give.
  *  steps: block steps, (steps + 1) s <= 1024;  r: 1 <= r <= steps * s.
  *  U: m x r, S: r, V: n x r, resid: r -- device memory, column-major, f64; signs as gk_psvd.
- * GK_FLAG_BLOCK_F32 applies (the block products in f32).  A caller workspace (opts->workspace)
+ * GK_FLAG_BLOCK_F32 applies (the block products in f32), and GK_FLAG_RITZ_DF (U and V from the
+ * bases' double-f32 copies; not with GK_FLAG_ORTH_F64).  A caller workspace (opts->workspace)
  * needs gk_block_numrank_workspace(A, s, steps, opts) bytes.  Returns GK_OK, GK_RANK_DEFICIENT
  * when the blocks filled the space with fewer than r columns (the trailing triplets zero), GK_NOT_CONVERGED when the small
  * SVD hit its sweep limit, or an error.  Experimental: not yet run on a GPU. */

@@ -1548,9 +1548,15 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
                             cudaMemcpyDeviceToDevice, st));
   GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
   // U = Q X_r (all K rows of X), V = P_{1..k} Y_r (the first ks rows: the padding columns of B
-  // never enter the right vectors of nonzero values)
-  GK_CUDA(ritz_gemm(b.Q, ldu, m, K, b.X, K, rr, U, m, st, d));
-  GK_CUDA(ritz_gemm(b.P, ldv, n, ks, b.Y, K, rr, V, n, st, d));
+  // never enter the right vectors of nonzero values); with GK_FLAG_RITZ_DF from the bases'
+  // double-f32 copies (b.Yw, free after the small SVD, holds X's and then Y's split)
+  if ((o.flags & GK_FLAG_RITZ_DF) && b.df) {
+    GK_CUDA(ritz_gemm_df(b.Qs, ldu, m, K, b.X, K, rr, U, m, reinterpret_cast<float2 *>(b.Yw), st));
+    GK_CUDA(ritz_gemm_df(b.Ps, ldv, n, ks, b.Y, K, rr, V, n, reinterpret_cast<float2 *>(b.Yw), st));
+  } else {
+    GK_CUDA(ritz_gemm(b.Q, ldu, m, K, b.X, K, rr, U, m, st, d));
+    GK_CUDA(ritz_gemm(b.P, ldv, n, ks, b.Y, K, rr, V, n, st, d));
+  }
   GK_CUDA(block_resid(b.raw, s, b.X, K, ks, rr, resid, st));
   GK_CUDA(cudaMemcpyAsync(S, b.sigma, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
   GK_CUDA(sign_normalize(U, m, m, V, n, n, rr, st));

@@ -496,9 +496,11 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
 
 def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None = None, stream=None,
                   workspace=None, scale: float = 1.0, check: bool = True, orth_f64: bool = False,
-                  f32_products: bool = False):
+                  f32_products: bool = False, ritz_df: bool = False):
     """One cycle of the block form of Algorithm 2 on a CUDA operator (gk_block_fsvd, experimental).
-    Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on A's device."""
+    f32_products: GK_FLAG_BLOCK_F32; ritz_df: the Ritz vectors from the bases' double-f32 copies
+    (GK_FLAG_RITZ_DF).  Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on
+    A's device."""
     M, keep_a = make_matrix(A, scale)
     if start is not None and tuple(start.shape) != (M.m, int(s)):
         raise ValueError(f"start block must be m x s = {M.m} x {int(s)}, got {tuple(start.shape)}")
@@ -513,6 +515,8 @@ def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None
     o, ka = _opts(dev, seed=seed, stream=stream, workspace=workspace, orth_f64=orth_f64)
     if f32_products:
         o.flags |= GK_FLAG_BLOCK_F32
+    if ritz_df:
+        o.flags |= GK_FLAG_RITZ_DF
     info = gk_info()
     st = lib().gk_block_fsvd(C.byref(M), int(s), _ptr(q0), int(steps), int(r), C.byref(o), _ptr(U), _ptr(S), _ptr(V),
                              _ptr(res), C.byref(info))

@@ -120,3 +120,26 @@ def test_block_fsvd_matches_the_block_oracle(m, n, s, steps, r):
     np.testing.assert_allclose(S.cpu().numpy(), So, rtol=1e-10)
     assert angle_err(V.cpu().numpy(), Vo) < 1e-8 and angle_err(U.cpu().numpy(), Uo) < 1e-8
     np.testing.assert_allclose(res.cpu().numpy(), reso, rtol=1e-6, atol=1e-13 * So[0])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "bf16"])
+def test_block_fsvd_ritz_vectors_in_double_f32(dtype):
+    """gk_block_fsvd with GK_FLAG_RITZ_DF: U = Q X and V = P Y from the bases' double-f32 copies,
+    against the f64 products: the values and residuals are the same numbers (they do not depend on
+    U, V), the vectors agree to 1e-12 (the copies hold ~2^-48 of each entry, the products ~2^-46
+    of sum |q x|)."""
+    m, n, s, steps, r = 3000, 1400, 8, 10, 40
+    A = synth.gaussian_product(m, n, min(m, n), 1e-3, seed=7, dtype=np.float64)
+    if dtype == "bf16":
+        At = cuda(synth.to_bf16_bits(A.astype(np.float32)).view(np.int16)).view(torch.bfloat16)
+    else:
+        At = cuda(A)
+    Q0 = cuda(synth.rng(8).standard_normal((m, s)))
+    M = gk()
+    U1, S1, V1, r1, st1, _ = M.gk_block_fsvd(At, s, steps, r, start=Q0)
+    U2, S2, V2, r2, st2, _ = M.gk_block_fsvd(At, s, steps, r, start=Q0, ritz_df=True)
+    assert st1 == st2 == 0
+    np.testing.assert_array_equal(S1.cpu().numpy(), S2.cpu().numpy())
+    np.testing.assert_array_equal(r1.cpu().numpy(), r2.cpu().numpy())
+    assert np.abs(U1.cpu().numpy() - U2.cpu().numpy()).max() <= 1e-12
+    assert np.abs(V1.cpu().numpy() - V2.cpu().numpy()).max() <= 1e-12
