@@ -175,13 +175,14 @@ __global__ void __launch_bounds__(kAThreads) k_acc_gemm(const T *__restrict__ A,
   }
 }
 
-// The FAST products for narrow blocks (k <= VEC, VEC = 8 or 16 vectors): k_acc_gemm's 32-vector
-// tile would multiply zero padding in 3/4 (or 1/2) of its FMAs, which at 8 vectors puts the pass
-// above the FP32 pipes' rate at HBM speed.  Same thread work (4 outputs x 4 vectors), the 256
-// threads spread over VEC / 4 vector rows and 1024 / VEC outputs' groups: 512 outputs per CTA at
-// VEC = 8 (contraction chunks of 16), 256 at VEC = 16 (chunks of 32); shared memory ~33 KB.  Each
-// chunk's products summed in f32, the chunk sums combined in double-f32 (TwoSum), as the FAST
-// instantiation above.
+// The block calls' products for narrow blocks (k <= VEC, VEC = 8 or 16 vectors): k_acc_gemm's
+// 32-vector tile would spend 3/4 (or 1/2) of its arithmetic on zero padding, which at 8 vectors
+// puts a pass over a bf16 operator well above the FP32 pipes' rate at HBM speed.  Same thread work
+// (4 outputs x 4 vectors), the 256 threads spread over VEC / 4 vector rows and 1024 / VEC output
+// groups: 512 outputs per CTA at VEC = 8 (contraction chunks of 16), 256 at VEC = 16 (chunks of
+// 32); shared memory ~35-38 KB.  FAST: each chunk's products summed in f32, the chunk sums
+// combined in double-f32 (TwoSum), as k_acc_gemm's FAST instantiation; otherwise every product and
+// sum in double-f32 (df_madd), as k_acc_gemm.
 template <int VEC>
 struct NarrowTile {
   static constexpr int kRows = VEC / 4;                   // thread rows (4 vectors each)
@@ -190,16 +191,17 @@ struct NarrowTile {
   static constexpr int kChunk = VEC == 8 ? 16 : 32;       // contraction indices per chunk
 };
 
-template <typename T, bool TRANS, int VEC>
+template <typename T, bool TRANS, bool FAST, int VEC>
 __global__ void __launch_bounds__(kAThreads) k_acc_gemm_narrow(const T *__restrict__ A, int64_t m, int64_t n,
                                                                int64_t ld, double scale, const float *__restrict__ xh,
-                                                               int64_t ldx, int k, double *__restrict__ out,
-                                                               int64_t ldo) {
+                                                               const float *__restrict__ xl, int64_t ldx, int k,
+                                                               double *__restrict__ out, int64_t ldo) {
   using Tl = NarrowTile<VEC>;
   static_assert(VEC == 8 || VEC == 16, "narrow tiles of 8 or 16 vectors");
   static_assert(Tl::kRows * 2 * kATP == VEC && Tl::kRows * Tl::kCols == kAThreads, "thread grid covers the tile");
   __shared__ __align__(16) float As[Tl::kChunk][Tl::kOut + 4];
   __shared__ __align__(16) float Xh[Tl::kChunk][VEC + 4];
+  __shared__ __align__(16) float Xl[FAST ? 1 : Tl::kChunk][VEC + 4];
   const int64_t nout = TRANS ? n : m;
   const int64_t ncon = TRANS ? m : n;
   const int64_t o0 = (int64_t)blockIdx.x * Tl::kOut;
@@ -234,39 +236,59 @@ __global__ void __launch_bounds__(kAThreads) k_acc_gemm_narrow(const T *__restri
       const int vv = i / Tl::kChunk, cc = i % Tl::kChunk;
       const int64_t c = c0 + cc;
       const int j = j0 + vv;
-      Xh[cc][vv] = (j < k && c < ncon) ? xh[(int64_t)j * ldx + c] : 0.f;
+      const bool in = j < k && c < ncon;
+      Xh[cc][vv] = in ? xh[(int64_t)j * ldx + c] : 0.f;
+      if constexpr (!FAST) Xl[cc][vv] = in ? xl[(int64_t)j * ldx + c] : 0.f;
     }
     __syncthreads();
-    float2 cs[kATR][kATP];
+    if constexpr (FAST) {
+      float2 cs[kATR][kATP];  // this chunk's f32 sums
 #pragma unroll
-    for (int r = 0; r < kATR; ++r)
+      for (int r = 0; r < kATR; ++r)
 #pragma unroll
-      for (int p = 0; p < kATP; ++p) cs[r][p] = f2(0.f, 0.f);
+        for (int p = 0; p < kATP; ++p) cs[r][p] = f2(0.f, 0.f);
 #pragma unroll 4
-    for (int cc = 0; cc < Tl::kChunk; ++cc) {
-      const float4 a4 = *reinterpret_cast<const float4 *>(&As[cc][to]);
-      const float av[kATR] = {a4.x, a4.y, a4.z, a4.w};
-      const float4 h4 = *reinterpret_cast<const float4 *>(&Xh[cc][tv]);
-      const float2 xhp[kATP] = {f2(h4.x, h4.y), f2(h4.z, h4.w)};
+      for (int cc = 0; cc < Tl::kChunk; ++cc) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(&As[cc][to]);
+        const float av[kATR] = {a4.x, a4.y, a4.z, a4.w};
+        const float4 h4 = *reinterpret_cast<const float4 *>(&Xh[cc][tv]);
+        const float2 xhp[kATP] = {f2(h4.x, h4.y), f2(h4.z, h4.w)};
 #pragma unroll
-      for (int r = 0; r < kATR; ++r) {
-        const float2 a2 = f2(av[r], av[r]);
+        for (int r = 0; r < kATR; ++r) {
+          const float2 a2 = f2(av[r], av[r]);
 #pragma unroll
-        for (int p = 0; p < kATP; ++p) cs[r][p] = __ffma2_rn(a2, xhp[p], cs[r][p]);
+          for (int p = 0; p < kATP; ++p) cs[r][p] = __ffma2_rn(a2, xhp[p], cs[r][p]);
+        }
+      }
+      const float2 m1 = f2(-1.f, -1.f);
+#pragma unroll
+      for (int r = 0; r < kATR; ++r)
+#pragma unroll
+        for (int p = 0; p < kATP; ++p) {  // (hi, lo) += chunk sum, TwoSum
+          const float2 sm = __fadd2_rn(hi[r][p], cs[r][p]);
+          const float2 bb = __ffma2_rn(hi[r][p], m1, sm);
+          const float2 d1 = __ffma2_rn(__ffma2_rn(bb, m1, sm), m1, hi[r][p]);
+          const float2 d2 = __ffma2_rn(bb, m1, cs[r][p]);
+          lo[r][p] = __fadd2_rn(lo[r][p], __fadd2_rn(d1, d2));
+          hi[r][p] = sm;
+        }
+    } else {
+#pragma unroll 4
+      for (int cc = 0; cc < Tl::kChunk; ++cc) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(&As[cc][to]);
+        const float av[kATR] = {a4.x, a4.y, a4.z, a4.w};
+        const float4 h4 = *reinterpret_cast<const float4 *>(&Xh[cc][tv]);
+        const float4 l4 = *reinterpret_cast<const float4 *>(&Xl[cc][tv]);
+        const float2 xhp[kATP] = {f2(h4.x, h4.y), f2(h4.z, h4.w)};
+        const float2 xlp[kATP] = {f2(l4.x, l4.y), f2(l4.z, l4.w)};
+#pragma unroll
+        for (int r = 0; r < kATR; ++r) {
+          const float2 a2 = f2(av[r], av[r]), na2 = f2(-av[r], -av[r]);
+#pragma unroll
+          for (int p = 0; p < kATP; ++p) df_madd(hi[r][p], lo[r][p], a2, na2, xhp[p], xlp[p]);
+        }
       }
     }
-    const float2 m1 = f2(-1.f, -1.f);
-#pragma unroll
-    for (int r = 0; r < kATR; ++r)
-#pragma unroll
-      for (int p = 0; p < kATP; ++p) {  // (hi, lo) += chunk sum, TwoSum
-        const float2 sm = __fadd2_rn(hi[r][p], cs[r][p]);
-        const float2 bb = __ffma2_rn(hi[r][p], m1, sm);
-        const float2 d1 = __ffma2_rn(__ffma2_rn(bb, m1, sm), m1, hi[r][p]);
-        const float2 d2 = __ffma2_rn(bb, m1, cs[r][p]);
-        lo[r][p] = __fadd2_rn(lo[r][p], __fadd2_rn(d1, d2));
-        hi[r][p] = sm;
-      }
     __syncthreads();
   }
 #pragma unroll
@@ -314,28 +336,32 @@ __global__ void __launch_bounds__(256) k_resid_norm(const double *__restrict__ Y
   }
 }
 
-template <typename T, int VEC>
-cudaError_t launch_narrow(const Op &A, bool trans, const float *xh, int64_t ldx, int k, double *out, int64_t ldo,
-                          cudaStream_t s) {
+template <typename T, bool FAST, int VEC>
+cudaError_t launch_narrow(const Op &A, bool trans, const float *xh, const float *xl, int64_t ldx, int k, double *out,
+                          int64_t ldo, cudaStream_t s) {
   const int64_t nout = trans ? A.n : A.m;
   constexpr int kOut = NarrowTile<VEC>::kOut;
   dim3 grid((unsigned)((nout + kOut - 1) / kOut), (unsigned)((k + VEC - 1) / VEC));
   if (trans)
-    GK_LAUNCH(k_acc_gemm_narrow<T, true, VEC><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale,
-                                                                         xh, ldx, k, out, ldo));
+    GK_LAUNCH(k_acc_gemm_narrow<T, true, FAST, VEC><<<grid, kAThreads, 0, s>>>(
+        (const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx, k, out, ldo));
   else
-    GK_LAUNCH(k_acc_gemm_narrow<T, false, VEC><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale,
-                                                                          xh, ldx, k, out, ldo));
+    GK_LAUNCH(k_acc_gemm_narrow<T, false, FAST, VEC><<<grid, kAThreads, 0, s>>>(
+        (const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx, k, out, ldo));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_acc(const Op &A, bool trans, const float *xh, const float *xl, int64_t ldx, int k, double *out,
-                       int64_t ldo, cudaStream_t s, bool fast) {
+                       int64_t ldo, cudaStream_t s, bool fast, bool narrow) {
   const int64_t nout = trans ? A.n : A.m;
   dim3 grid((unsigned)((nout + kAOut - 1) / kAOut), (unsigned)((k + kAVec - 1) / kAVec));
-  if (fast && k <= 8) return launch_narrow<T, 8>(A, trans, xh, ldx, k, out, ldo, s);
-  if (fast && k <= 16) return launch_narrow<T, 16>(A, trans, xh, ldx, k, out, ldo, s);
+  if (narrow && k <= 8)
+    return fast ? launch_narrow<T, true, 8>(A, trans, xh, xl, ldx, k, out, ldo, s)
+                : launch_narrow<T, false, 8>(A, trans, xh, xl, ldx, k, out, ldo, s);
+  if (narrow && k <= 16)
+    return fast ? launch_narrow<T, true, 16>(A, trans, xh, xl, ldx, k, out, ldo, s)
+                : launch_narrow<T, false, 16>(A, trans, xh, xl, ldx, k, out, ldo, s);
   if (fast) {
     if (trans)
       GK_LAUNCH(k_acc_gemm<T, true, true><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, xh,
@@ -364,7 +390,7 @@ size_t accurate_floats(const Op &A, int k) {
 }
 
 cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, double *out, float *split,
-                              cudaStream_t s, bool fast) {
+                              cudaStream_t s, bool fast, bool narrow) {
   const int64_t len = trans ? A.m : A.n;  // length of the input vectors
   const int64_t cnt = len * (int64_t)k;
   float *xh = split, *xl = split + cnt;
@@ -375,9 +401,9 @@ cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, d
   if (e != cudaSuccess) return e;
   const int64_t ldo = trans ? A.n : A.m;
   switch (A.dtype) {
-    case GK_F32: return launch_acc<float>(A, trans, xh, xl, len, k, out, ldo, s, fast);
-    case GK_BF16: return launch_acc<__nv_bfloat16>(A, trans, xh, xl, len, k, out, ldo, s, fast);
-    case GK_F16: return launch_acc<__half>(A, trans, xh, xl, len, k, out, ldo, s, fast);
+    case GK_F32: return launch_acc<float>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow);
+    case GK_BF16: return launch_acc<__nv_bfloat16>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow);
+    case GK_F16: return launch_acc<__half>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow);
     default: return cudaErrorNotSupported;
   }
 }

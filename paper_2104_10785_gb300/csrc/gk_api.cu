@@ -1205,7 +1205,7 @@ int block_product(const Op &op, BlockBufs &b, bool trans, const double *src, int
   if (b.acc) {  // one pass over A for the whole block, products exact to ~2^-47
     GK_CUDA(cudaMemcpy2DAsync(b.Xc, sizeof(double) * lin, src, sizeof(double) * ldsrc, sizeof(double) * lin, s,
                               cudaMemcpyDeviceToDevice, st));
-    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st, b.f32));
+    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st, b.f32, true));
     return GK_OK;
   }
   for (int c = 0; c < s; ++c) {

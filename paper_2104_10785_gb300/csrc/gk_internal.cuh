@@ -152,10 +152,11 @@ cudaError_t fused_finish(const Op &A, const double *zpart, const double *alpha, 
 // double-f32 (exact to ~2^-47 sum |a x|); split holds accurate_floats() floats.
 bool accurate_ok(const Op &A);
 size_t accurate_floats(const Op &A, int k);
-// fast = true: f32 products (x rounded to f32, 32-term f32 chunk sums combined in double-f32), the
-// precision of matvec, at about a tenth of the arithmetic
+// fast = true: f32 products (x rounded to f32, 16- or 32-term f32 chunk sums combined in
+// double-f32), the precision of matvec, at about a tenth of the arithmetic.  narrow = true (the
+// block calls): blocks of up to 8 or 16 vectors take tiles of that width instead of 32
 cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, double *out, float *split,
-                              cudaStream_t s, bool fast = false);
+                              cudaStream_t s, bool fast = false, bool narrow = false);
 // res[j] = || Y[:, j] - S[j] W[:, j] ||, columns of length len (ld = len)
 cudaError_t resid_norms(const double *Y, const double *W, const double *S, int64_t len, int k, double *res,
                         cudaStream_t s);
