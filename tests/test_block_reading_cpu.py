@@ -19,8 +19,12 @@ def tri_norm(T):
     return float(np.sqrt(max(np.linalg.eigvalsh(T.T @ T).max(), 0.0)))
 
 
-def column_block_gk(A, Q0, eps, kmax, fresh_seed=0):
-    """(rank, sigma(B), block steps, replaced columns) by the library's column-wise flow."""
+def column_block_gk(A, Q0, eps, kmax, fresh_seed=0, block_gs=False, fallback=True):
+    """(rank, sigma(B), block steps, replaced columns) by the library's column-wise flow, or with
+    block_gs by its block Gram-Schmidt (GK_FLAG_BLOCK_GS): the block projected against the earlier
+    basis twice (H = Q^T W, W -= Q H), then each column orthogonalized twice against the block's
+    earlier columns only, with one more pass against every column where that step cancels (the
+    squared norm below half of its value before it; `fallback`)."""
     m, n = A.shape
     s = Q0.shape[1]
     mn = min(m, n)
@@ -32,11 +36,22 @@ def column_block_gk(A, Q0, eps, kmax, fresh_seed=0):
     replaced = [0]
 
     def orth(Bas, jc0, W):
+        if block_gs and jc0 > 0:
+            W = W.copy()
+            for _ in range(2):
+                W -= Bas[:, :jc0] @ (Bas[:, :jc0].T @ W)
         for c in range(W.shape[1]):
             jc = jc0 + c
             w = W[:, c].copy()
-            for _ in range(2 if jc > 0 else 0):
-                w -= Bas[:, :jc] @ (Bas[:, :jc].T @ w)
+            if block_gs:
+                n0 = np.linalg.norm(w)
+                for _ in range(2 if c > 0 else 0):
+                    w -= Bas[:, jc0:jc] @ (Bas[:, jc0:jc].T @ w)
+                if fallback and c > 0 and np.linalg.norm(w) ** 2 < 0.5 * n0**2:
+                    w -= Bas[:, :jc] @ (Bas[:, :jc].T @ w)
+            else:
+                for _ in range(2 if jc > 0 else 0):
+                    w -= Bas[:, :jc] @ (Bas[:, :jc].T @ w)
             nrm = np.linalg.norm(w)
             scale[0] = max(scale[0], nrm)
             if nrm <= 2.0**-46 * scale[0]:
@@ -80,6 +95,35 @@ def column_block_gk(A, Q0, eps, kmax, fresh_seed=0):
     K = (steps + 1) * s
     sig = np.linalg.svd(B[:K, :K], compute_uv=False)[: steps * s]
     return int(np.sum(sig > eps * sig[0])), sig, steps, replaced[0]
+
+
+def operator_case(case):
+    if case.startswith("repeated"):
+        return synth.prescribed_spectrum(70, 40, np.array([5.0, 5.0, 5.0, 3.0, 3.0, 1.0, 1.0, 1.0]), seed=4,
+                                         dtype=np.float64)[0]
+    if case.startswith("product"):
+        return synth.gaussian_product(300, 200, 20, 0.0, seed=5, dtype=np.float64)
+    return synth.gaussian_product(400, 250, 16, 1e-7, seed=6, dtype=np.float64)
+
+
+@pytest.mark.parametrize("case", ["repeated_s3", "repeated_s1", "product_s3", "product_s8", "noisy_s4"])
+def test_block_gram_schmidt_gives_the_oracles_B(case):
+    """The block Gram-Schmidt flow (two block passes against the earlier basis, then the block's
+    own columns, with the full pass where that cancels) gives the oracle's steps, rank and sigma(B);
+    without the full pass a cancelling column keeps the old basis' directions its rounding
+    brought in, and the rank-deficient blocks of product_s8 go wrong."""
+    A = operator_case(case)
+    s = int(case.split("_s")[1])
+    eps = 1e-5 if case.startswith("noisy") else 1e-8
+    Q0 = np.random.default_rng(s).standard_normal((A.shape[0], s))
+    r_or, sig_or, k_or = bgk.block_numrank(A, Q0, eps=eps)
+    for fresh_seed in (0, 1):
+        r, sig, k, _ = column_block_gk(A, Q0, eps, 0, fresh_seed, block_gs=True)
+        assert (r, k) == (r_or, k_or)
+        np.testing.assert_allclose(sig, sig_or[: k * s], rtol=0, atol=1e-13 * sig_or[0])
+    if case == "product_s8":
+        r, sig, k, _ = column_block_gk(A, Q0, eps, 0, 0, block_gs=True, fallback=False)
+        assert (r, k) != (r_or, k_or) or np.abs(sig - sig_or[: k * s]).max() > 1e-8 * sig_or[0]
 
 
 @pytest.mark.parametrize("case", ["repeated_s3", "repeated_s1", "product_s3", "product_s8", "noisy_s4"])
