@@ -727,7 +727,7 @@ def run_gk(args, rank, world):
     if args.block_leg:
         try:
             bs, bsteps = (int(v) for v in args.block_leg.split(","))
-            bkw = dict(seed=w["seed"], f32_products=args.block_f32, ritz_df=args.ritz_df)
+            bkw = dict(seed=w["seed"], f32_products=args.block_f32, ritz_df=args.ritz_df, block_gs=args.block_gs)
             gk.gk_block_fsvd(A, bs, bsteps, k, **bkw)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -741,7 +741,8 @@ def run_gk(args, rank, world):
             bms = e0.elapsed_time(e1) / reps
             ra, rb = gk.gk_residuals(A, Ub, Sb, Vb)
             block = {"value": k / (bms / 1e3), "unit": "triplets/s", "ms_per_step": bms, "s": bs, "block_steps": bsteps,
-                     "f32_products": bool(args.block_f32), "ritz_df": bool(args.ritz_df), "status": stb, "matvecs": infb["matvecs"],
+                     "f32_products": bool(args.block_f32), "ritz_df": bool(args.ritz_df),
+                     "block_gs": bool(args.block_gs), "status": stb, "matvecs": infb["matvecs"],
                      "breakdowns": infb["breakdowns"], "launches": infb["launches"],
                      "resid_est_max_rel": float(rb_est.max()) / float(Sb[0]),
                      "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sb[0])}
@@ -1281,9 +1282,9 @@ def profile_case(args):
             elif args.case == "sketch":
                 gk.gk_sketch_batched([A], seed=1, tcgen05=args.tcgen05)
             elif args.case == "block" and args.fsvd > 0:
-                gk.gk_block_fsvd(A, args.s, args.kmax, args.fsvd, f32_products=args.block_f32)
+                gk.gk_block_fsvd(A, args.s, args.kmax, args.fsvd, f32_products=args.block_f32, block_gs=args.block_gs)
             elif args.case == "block":
-                gk.gk_block_numrank(A, args.s, 1e-8, args.kmax, f32_products=args.block_f32)
+                gk.gk_block_numrank(A, args.s, 1e-8, args.kmax, f32_products=args.block_f32, block_gs=args.block_gs)
             else:
                 gk.gk_psvd(A, 16, 1e-8, krylov_dim=48, max_restarts=0, fused=args.fused)
     elif args.case == "batched":
@@ -1342,6 +1343,8 @@ def main():
     ap.add_argument("--block-leg", default=None, metavar="S,STEPS",
                     help="headline: also time gk_block_fsvd (S start vectors, STEPS block steps, the workload's k "
                          "triplets; --block-f32 for its f32 products) on the same operator (experimental)")
+    ap.add_argument("--block-gs", action="store_true",
+                    help="--block-leg and --case block: the block Gram-Schmidt (GK_FLAG_BLOCK_GS)")
     ap.add_argument("--s", type=int, default=8, help="--case block: start vectors per block")
     ap.add_argument("--kmax", type=int, default=16, help="--case block: block steps")
     ap.add_argument("--block-f32", action="store_true", help="--case block: f32 block products (GK_FLAG_BLOCK_F32)")

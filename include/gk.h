@@ -98,6 +98,12 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               (x rounded to f32, 32-term f32 sums combined in double-f32: the precision
                               of gk_matvec) instead of double-f32, about a tenth of the arithmetic per
                               product.  Experimental: not yet run on a GPU. */
+#define GK_FLAG_BLOCK_GS 1024 /* gk_block_numrank, gk_block_fsvd (with the double-f32 basis copies, i.e.
+                              without GK_FLAG_ORTH_F64): each block orthogonalized against the earlier
+                              basis as a block (reorthogonalized block classical Gram-Schmidt: the block
+                              projected, its own QR column by column, projected again, QR again), the
+                              basis read twice per projection of s columns instead of four times per
+                              column.  Experimental: not yet run on a GPU. */
 typedef enum { GK_DENSE = 0, GK_CSR = 1 } gk_kind;
 
 /* The operator A (m x n).

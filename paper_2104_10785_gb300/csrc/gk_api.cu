@@ -1132,8 +1132,11 @@ struct BlockBufs {
   double *Q, *P, *W, *w, *Xc, *part, *h, *dpart, *raw, *Bf, *Bm, *Yw, *X, *Y, *sigma, *nrm, *q0;
   float *x32, *split;
   float2 *Qs, *Ps, *ws2;
+  double *gW, *gC, *gH, *gpart;  // block Gram-Schmidt: projected block, Q H, H, Q^T X partials
+  float2 *gWs, *gHs;             // and the double-f32 copies of the source block and of H
   int *pos, *sweeps, *rank;
   bool df;   // Gram-Schmidt on the bases' double-f32 shadows (not GK_FLAG_ORTH_F64)
+  bool bgs;  // with df: the block Gram-Schmidt (GK_FLAG_BLOCK_GS)
   bool acc;  // dense reduced-precision operator: block products in one pass (double-f32)
   bool f32;  // with acc: the f32 form of that pass (GK_FLAG_BLOCK_F32)
 };
@@ -1176,6 +1179,12 @@ size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const O
   b->Qs = b->df ? cv.take<float2>((size_t)ldu * cols) : nullptr;
   b->Ps = b->df ? cv.take<float2>((size_t)ldv * cols) : nullptr;
   b->ws2 = b->df ? cv.take<float2>(lmax) : nullptr;
+  b->gW = b->bgs ? cv.take<double>((size_t)mx * s) : nullptr;
+  b->gC = b->bgs ? cv.take<double>((size_t)mx * s) : nullptr;
+  b->gH = b->bgs ? cv.take<double>((size_t)cols * s) : nullptr;
+  b->gpart = b->bgs ? cv.take<double>((size_t)bgs_dot_chunks(mx) * cols * s) : nullptr;
+  b->gWs = b->bgs ? cv.take<float2>((size_t)mx * s) : nullptr;
+  b->gHs = b->bgs ? cv.take<float2>((size_t)cols * s) : nullptr;
   char *dd;
   void *v, *tv;
   int32_t *rp, *ci, *trp, *tci;
@@ -1234,28 +1243,32 @@ int block_fresh(BlockBufs &b, int64_t len, double *Bas, int64_t ld, float2 *Bs, 
 }
 
 // columns jc0 .. jc0 + s - 1 of the basis Bas (ld; double-f32 shadow Bs or null): column c of
-// Wsrc (ld ldw) orthonormalized by classical Gram-Schmidt, two passes, against every column
-// before it -- the reorthogonalization and the QR of the block in one.  A column whose norm
-// after the passes is at most 2^-46 of the largest norm so far halts the launches that follow
-// (an exact breakdown); the host then puts a fresh direction in its place and goes on with
-// the next column.
+// Wsrc (ld ldw) orthonormalized by classical Gram-Schmidt, two passes, against the columns jlo ..
+// before it -- with jlo = 0 the reorthogonalization and the QR of the block in one; with jlo = jc0
+// the block's own QR (the block Gram-Schmidt projects against the earlier basis first).  With
+// mode NM_BREAKDOWN a column whose norm after the passes is at most 2^-46 of the largest norm so
+// far halts the launches that follow (an exact breakdown); the host then puts a fresh direction,
+// orthogonalized against every column before it, in its place and goes on with the next column.
+// NM_PLAIN only normalizes.
 int block_orth(BlockBufs &b, int64_t len, double *Bas, int64_t ld, float2 *Bs, int jc0, int s, const double *Wsrc,
                int64_t ldw, int side, uint64_t seed, int64_t *nfresh, int *breakdowns, cudaStream_t st,
-               const Dev &d) {
+               const Dev &d, int jlo = 0, int mode = NM_BREAKDOWN) {
   int c0 = 0;
+  double *Blo = Bas + (int64_t)jlo * ld;
+  float2 *Bslo = Bs ? Bs + (int64_t)jlo * ld : nullptr;
   while (c0 < s) {
     for (int c = c0; c < s; ++c) {
       const int jc = jc0 + c;
       double *qcol = Bas + (int64_t)jc * ld;
       float2 *qs = Bs ? Bs + (int64_t)jc * ld : nullptr;
       GK_CUDA(copy_vec(b.w, nullptr, Wsrc + (int64_t)c * ldw, len, st));
-      if (jc == 0) {
-        GK_CUDA(orthonormalize(b.w, len, nullptr, ld, 0, 0, b.part, b.h, b.ctl, NM_BREAKDOWN, jc, side, nullptr,
-                               nullptr, st, d));
+      if (jc == jlo) {
+        GK_CUDA(orthonormalize(b.w, len, nullptr, ld, 0, 0, b.part, b.h, b.ctl, mode, jc, side, nullptr, nullptr, st,
+                               d));
         GK_CUDA(normalize_append(b.w, len, qcol, nullptr, b.ctl, st, d, qs));
       } else {
-        GK_CUDA(orth_append(b.w, len, Bas, ld, jc, 2, b.part, b.h, b.ctl, NM_BREAKDOWN, jc, side, nullptr, nullptr,
-                            qcol, nullptr, st, d, Bs, b.ws2, qs));
+        GK_CUDA(orth_append(b.w, len, Blo, ld, jc - jlo, 2, b.part, b.h, b.ctl, mode, jc, side, nullptr, nullptr,
+                            qcol, nullptr, st, d, Bslo, b.ws2, qs));
       }
     }
     HostCtl hc;
@@ -1274,6 +1287,27 @@ int block_orth(BlockBufs &b, int64_t len, double *Bas, int64_t ld, float2 *Bs, i
     c0 = jb - jc0 + 1;
   }
   return GK_OK;
+}
+
+// the block's columns by the block Gram-Schmidt (reorthogonalized block classical Gram-Schmidt,
+// Barlow and Smoktunowicz 2013): W1 = W - Q (Q^T W) against the jc0 columns before the block, the
+// block's own QR (with the breakdown test and fresh completions), W2 = W1' - Q (Q^T W1') for the
+// orthonormal block W1' (removing what the QR's rounding brought back of Q's directions where a
+// column cancelled), and the QR of W2 (plain normalization: its norms are ~1).  The column-wise
+// flow where there is no earlier basis or no double-f32 copy of it.
+int block_orth_bgs(BlockBufs &b, int64_t len, double *Bas, int64_t ld, float2 *Bs, int jc0, int s,
+                   const double *Wsrc, int64_t ldw, int side, uint64_t seed, int64_t *nfresh, int *breakdowns,
+                   cudaStream_t st, const Dev &d) {
+  if (!b.bgs || jc0 == 0 || !Bs)
+    return block_orth(b, len, Bas, ld, Bs, jc0, s, Wsrc, ldw, side, seed, nfresh, breakdowns, st, d);
+  GK_CUDA(split_cols(Wsrc, len, ldw, s, b.gWs, st));
+  GK_CUDA(bgs_project(Bs, ld, len, jc0, Wsrc, ldw, b.gWs, ldw, s, b.gpart, b.gH, b.gHs, b.gC, b.gW, st));
+  int rc = block_orth(b, len, Bas, ld, Bs, jc0, s, b.gW, len, side, seed, nfresh, breakdowns, st, d, jc0,
+                      NM_BREAKDOWN);
+  if (rc) return rc;
+  GK_CUDA(bgs_project(Bs, ld, len, jc0, Bas + (int64_t)jc0 * ld, ld, Bs + (int64_t)jc0 * ld, ld, s, b.gpart, b.gH,
+                      b.gHs, b.gC, b.gW, st));
+  return block_orth(b, len, Bas, ld, Bs, jc0, s, b.gW, len, side, seed, nfresh, breakdowns, st, d, jc0, NM_PLAIN);
 }
 
 int read_block(const BlockBufs &b, BlockCtl *hb, HostCtl *hc, cudaStream_t st) {
@@ -1312,10 +1346,11 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   const bool host_q0 = Q0 && on_host(Q0);
   const bool host_sigma = sigma && on_host(sigma);
   Op op = make_op(Ain);
-  BlockBufs b;
+  BlockBufs b{};
   b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   b.acc = accurate_ok(op);
   b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
+  b.bgs = b.df && (o.flags & GK_FLAG_BLOCK_GS) != 0;
   const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
   Workspace ws;
   rc = acquire(ws, bytes, o, st);
@@ -1344,13 +1379,13 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   }
   int64_t nfresh = 0;
   int breakdowns = 0;
-  rc = block_orth(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+  rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
   if (rc) return rc;
   GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));  // the breakdown scale follows the blocks' norms from here
   // P_1 R_1 = A^T Q_1; sigma~ = ||R_1||
   rc = block_product(op, b, true, b.Q, ldu, s, st, d);
   if (rc) return rc;
-  rc = block_orth(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+  rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
   if (rc) return rc;
   GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
   GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, eps, b.bc, st));
@@ -1363,7 +1398,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
     const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
     rc = block_product(op, b, false, b.P + pj * ldv, ldv, s, st, d);
     if (rc) return rc;
-    rc = block_orth(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+    rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
     if (rc) return rc;
     GK_CUDA(block_dots(b.Q + qn * ldu, ldu, b.W, m, m, s, b.dpart, b.raw, st));
     GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)pj, 0, eps, b.bc, st));
@@ -1385,7 +1420,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
     // P_{j+1} R_{j+1} = A^T Q_{j+1} - P_j S_{j+1}^T, reorthogonalized
     rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
     if (rc) return rc;
-    rc = block_orth(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
     if (rc) return rc;
     GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
     GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)qn, 1, eps, b.bc, st));
@@ -1458,10 +1493,11 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   if (rc) return rc;
   const bool host_q0 = Q0 && on_host(Q0);
   Op op = make_op(Ain);
-  BlockBufs b;
+  BlockBufs b{};
   b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   b.acc = accurate_ok(op);
   b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
+  b.bgs = b.df && (o.flags & GK_FLAG_BLOCK_GS) != 0;
   const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
   Workspace ws;
   rc = acquire(ws, bytes, o, st);
@@ -1489,12 +1525,12 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   }
   int64_t nfresh = 0;
   int breakdowns = 0;
-  rc = block_orth(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+  rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
   if (rc) return rc;
   GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
   rc = block_product(op, b, true, b.Q, ldu, s, st, d);
   if (rc) return rc;
-  rc = block_orth(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+  rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
   if (rc) return rc;
   GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
   GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, 0.0, b.bc, st));
@@ -1506,7 +1542,7 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
     const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
     rc = block_product(op, b, false, b.P + pj * ldv, ldv, s, st, d);
     if (rc) return rc;
-    rc = block_orth(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
+    rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
     if (rc) return rc;
     GK_CUDA(block_dots(b.Q + qn * ldu, ldu, b.W, m, m, s, b.dpart, b.raw, st));
     GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)pj, 0, 0.0, b.bc, st));
@@ -1516,7 +1552,7 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
     if (steps >= kb || (int64_t)(steps + 1) * s > mn) break;
     rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
     if (rc) return rc;
-    rc = block_orth(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
     if (rc) return rc;
     GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
     GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)qn, 1, 0.0, b.bc, st));
@@ -1539,7 +1575,7 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
     const int64_t qn = (int64_t)steps * s;
     rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
     if (rc) return rc;
-    rc = block_orth(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
     if (rc) return rc;
     GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
     matvecs += s;
@@ -1935,9 +1971,11 @@ size_t gk_block_numrank_workspace(const gk_matrix *A, int s, int kmax, const gk_
   OpStage st;
   if (stage_plan(A, &st) != GK_OK) return 0;
   Op op = make_op(A);
-  BlockBufs b;
+  BlockBufs b{};
   b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
   b.acc = accurate_ok(op);
+  b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
+  b.bgs = b.df && (o.flags & GK_FLAG_BLOCK_GS) != 0;
   return block_layout(A, s, kb, d, st, nullptr, &b, &op);
 }
 

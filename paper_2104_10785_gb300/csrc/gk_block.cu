@@ -17,11 +17,15 @@
 //   * k_block_judge: T = triu(raw), ||T||_2 by cyclic Jacobi on the scaled T^T T on one warp,
 //     the running estimate of sigma_1 and the block break tests (the arithmetic in
 //     gk_block_judge.cuh, which the CPU tests also build for the host);
-//   * k_block_count: Algorithm 3's count of the singular values of B above eps sigma_1(B).
+//   * k_block_count: Algorithm 3's count of the singular values of B above eps sigma_1(B);
+//   * k_bgs_dots, k_bgs_sub (with k_block_dots_sum and the double-f32 Ritz product): the block
+//     Gram-Schmidt's projection out = X - Q (Q^T X) of a whole block, the basis read twice per
+//     block instead of four times per column (GK_FLAG_BLOCK_GS).
 #include <math.h>
 
 #include "gk_block_judge.cuh"
 #include "gk_internal.cuh"
+#include "gk_ritz_df.cuh"
 
 namespace gk {
 
@@ -158,7 +162,88 @@ __global__ void k_block_count(const double *__restrict__ sigma, int n, double ep
   *rank = r;
 }
 
+// ---- block Gram-Schmidt (GK_FLAG_BLOCK_GS): out = X - Q (Q^T X) for an s-column block X ----
+// part[(v * j + c) * G + g] = sum over rows [g kBgsRows, (g + 1) kBgsRows) of q_ic x_iv, from the
+// double-f32 copies of Q (Qs) and of X (Xs): each thread's terms in double-f32 (gk_ritz_df.cuh's
+// df_fma, renormalized every four), then the threads' f64 sums in a fixed tree (grid: G x j)
+constexpr int kBgsThreads = 256;
+constexpr int kBgsRows = 4096;
+
+template <int S>
+__global__ void __launch_bounds__(kBgsThreads) k_bgs_dots(const float2 *__restrict__ Qs, int64_t ldq, int64_t len,
+                                                          int j, const float2 *__restrict__ Xs, int64_t ldxs, int s,
+                                                          int G, double *__restrict__ part) {
+  __shared__ double red[kBgsThreads / 32][S];
+  const int g = blockIdx.x, c = blockIdx.y;
+  const int64_t i0 = (int64_t)g * kBgsRows;
+  const int64_t i1 = i0 + kBgsRows < len ? i0 + kBgsRows : len;
+  const DfPair *q = reinterpret_cast<const DfPair *>(Qs) + (int64_t)c * ldq;
+  const DfPair *x = reinterpret_cast<const DfPair *>(Xs);
+  float hi[S], lo[S];
+#pragma unroll
+  for (int v = 0; v < S; ++v) hi[v] = lo[v] = 0.f;
+  int t = 0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kBgsThreads) {
+    const DfPair qi = q[i];
+#pragma unroll
+    for (int v = 0; v < S; ++v)
+      if (v < s) df_fma(hi[v], lo[v], qi, x[(int64_t)v * ldxs + i]);
+    if ((++t & 3) == 0) {
+#pragma unroll
+      for (int v = 0; v < S; ++v) df_renorm(hi[v], lo[v]);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < S; ++v) {
+    double a = (double)hi[v] + (double)lo[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[warp][v] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < s) {
+    double a = 0.0;
+    for (int w = 0; w < kBgsThreads / 32; ++w) a += red[w][threadIdx.x];
+    part[((int64_t)threadIdx.x * j + c) * G + g] = a;
+  }
+}
+
+// out[v * len + i] = X[v * ldx + i] - C[v * len + i]
+__global__ void k_bgs_sub(const double *__restrict__ X, int64_t ldx, const double *__restrict__ C, int64_t len, int s,
+                          double *__restrict__ out) {
+  const int64_t total = len * (int64_t)s;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t / len, i = t % len;
+    out[t] = X[v * ldx + i] - C[t];
+  }
+}
+
 }  // namespace
+
+int bgs_dot_chunks(int64_t len) { return (int)((len + kBgsRows - 1) / kBgsRows); }
+
+cudaError_t bgs_project(const float2 *Qs, int64_t ldq, int64_t len, int j, const double *X, int64_t ldx,
+                        const float2 *Xs, int64_t ldxs, int s, double *part, double *H, float2 *Hs, double *C,
+                        double *out, cudaStream_t st) {
+  if (s < 1 || s > kBlockMaxS || j < 1 || len < 1) return cudaErrorInvalidValue;
+  const int G = bgs_dot_chunks(len);
+  const dim3 grid((unsigned)G, (unsigned)j);
+  if (s <= 8)
+    GK_LAUNCH(k_bgs_dots<8><<<grid, kBgsThreads, 0, st>>>(Qs, ldq, len, j, Xs, ldxs, s, G, part));
+  else if (s <= 16)
+    GK_LAUNCH(k_bgs_dots<16><<<grid, kBgsThreads, 0, st>>>(Qs, ldq, len, j, Xs, ldxs, s, G, part));
+  else
+    GK_LAUNCH(k_bgs_dots<32><<<grid, kBgsThreads, 0, st>>>(Qs, ldq, len, j, Xs, ldxs, s, G, part));
+  const int pairs = j * s;  // H (j x s, column-major): the partials of each entry summed in chunk order
+  GK_LAUNCH(k_block_dots_sum<<<(pairs + 127) / 128, 128, 0, st>>>(part, G, pairs, H));
+  cudaError_t e = ritz_gemm_df(Qs, ldq, len, j, H, j, s, C, len, Hs, st);  // C = Q H
+  if (e != cudaSuccess) return e;
+  int64_t b = (len * s + 255) / 256;
+  if (b > 4096) b = 4096;
+  GK_LAUNCH(k_bgs_sub<<<(int)b, 256, 0, st>>>(X, ldx, C, len, s, out));
+  return cudaGetLastError();
+}
 
 int block_dot_chunks(int64_t len) { return (int)((len + kDotRows - 1) / kDotRows); }
 

@@ -243,6 +243,14 @@ cudaError_t block_resid(const double *raw, int s, const double *X, int ldx, int 
                         cudaStream_t st);
 // *rank = #{i < n : sigma[i] > eps sigma[0]} (device)
 cudaError_t block_count(const double *sigma, int n, double eps, int *rank, cudaStream_t st);
+// the block Gram-Schmidt's projection out (len x s, ld len) = X - Q (Q^T X) for the first j
+// columns of Q, from the double-f32 copies Qs (ld ldq) and Xs (ld ldxs) of Q and X: Q^T X in
+// double-f32 per thread, f64 across threads and row chunks (part: bgs_dot_chunks(len) j s
+// doubles), H (j x s) and its split Hs, C = Q H in double-f32 (len x s)
+int bgs_dot_chunks(int64_t len);
+cudaError_t bgs_project(const float2 *Qs, int64_t ldq, int64_t len, int j, const double *X, int64_t ldx,
+                        const float2 *Xs, int64_t ldxs, int s, double *part, double *H, float2 *Hs, double *C,
+                        double *out, cudaStream_t st);
 
 // ---- small dense kernels (gk_small.cu) ----------------------------------
 // B (K x K, column-major) of one restart cycle: kept Ritz values on the

@@ -32,6 +32,7 @@ GK_FLAG_SKETCH_TC = 64
 GK_FLAG_BDSVD = 128
 GK_FLAG_RITZ_DF = 256
 GK_FLAG_BLOCK_F32 = 512
+GK_FLAG_BLOCK_GS = 1024
 
 _DTYPE = {torch.float64: GK_F64, torch.float32: GK_F32, torch.bfloat16: GK_BF16, torch.float16: GK_F16}
 
@@ -460,11 +461,12 @@ def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = Fals
 
 def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None, seed: int | None = None,
                      stream=None, workspace=None, scale: float = 1.0, want_sigma: bool = False, check: bool = True,
-                     orth_f64: bool = False, f32_products: bool = False):
+                     orth_f64: bool = False, f32_products: bool = False, block_gs: bool = False):
     """Numerical rank from a block of s start vectors (block Algorithm 1 + Algorithm 3).
     start: optional m x s start block.  f32_products: the block products of a reduced-precision
-    dense operator in f32 (GK_FLAG_BLOCK_F32, experimental).  Returns (rank, sigma(B) or None,
-    block steps, status, info dict)."""
+    dense operator in f32 (GK_FLAG_BLOCK_F32, experimental); block_gs: the block Gram-Schmidt
+    (GK_FLAG_BLOCK_GS, experimental).  Returns (rank, sigma(B) or None, block steps, status,
+    info dict)."""
     M, keep_a = make_matrix(A, scale)
     if start is not None and tuple(start.shape) != (M.m, int(s)):
         raise ValueError(f"start block must be m x s = {M.m} x {int(s)}, got {tuple(start.shape)}")
@@ -483,6 +485,8 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
                   orth_f64=orth_f64)
     if f32_products:
         o.flags |= GK_FLAG_BLOCK_F32
+    if block_gs:
+        o.flags |= GK_FLAG_BLOCK_GS
     info = gk_info()
     r = C.c_int(-1)
     steps = C.c_int(0)
@@ -496,10 +500,10 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
 
 def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None = None, stream=None,
                   workspace=None, scale: float = 1.0, check: bool = True, orth_f64: bool = False,
-                  f32_products: bool = False, ritz_df: bool = False):
+                  f32_products: bool = False, ritz_df: bool = False, block_gs: bool = False):
     """One cycle of the block form of Algorithm 2 on a CUDA operator (gk_block_fsvd, experimental).
     f32_products: GK_FLAG_BLOCK_F32; ritz_df: the Ritz vectors from the bases' double-f32 copies
-    (GK_FLAG_RITZ_DF).  Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on
+    (GK_FLAG_RITZ_DF); block_gs: the block Gram-Schmidt (GK_FLAG_BLOCK_GS).  Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on
     A's device."""
     M, keep_a = make_matrix(A, scale)
     if start is not None and tuple(start.shape) != (M.m, int(s)):
@@ -517,6 +521,8 @@ def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None
         o.flags |= GK_FLAG_BLOCK_F32
     if ritz_df:
         o.flags |= GK_FLAG_RITZ_DF
+    if block_gs:
+        o.flags |= GK_FLAG_BLOCK_GS
     info = gk_info()
     st = lib().gk_block_fsvd(C.byref(M), int(s), _ptr(q0), int(steps), int(r), C.byref(o), _ptr(U), _ptr(S), _ptr(V),
                              _ptr(res), C.byref(info))
@@ -525,10 +531,10 @@ def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None
     return U.T, S, V.T, res, st, info.as_dict()
 
 
-def gk_block_numrank_workspace(A, s: int, kmax: int = 0, *, orth_f64: bool = False) -> int:
+def gk_block_numrank_workspace(A, s: int, kmax: int = 0, *, orth_f64: bool = False, block_gs: bool = False) -> int:
     M, _ = make_matrix(A)
     o = default_opts()
-    o.flags = GK_FLAG_ORTH_F64 if orth_f64 else 0
+    o.flags = (GK_FLAG_ORTH_F64 if orth_f64 else 0) | (GK_FLAG_BLOCK_GS if block_gs else 0)
     return int(lib().gk_block_numrank_workspace(C.byref(M), int(s), int(kmax), C.byref(o)))
 
 

@@ -143,3 +143,70 @@ def test_block_fsvd_ritz_vectors_in_double_f32(dtype):
     np.testing.assert_array_equal(r1.cpu().numpy(), r2.cpu().numpy())
     assert np.abs(U1.cpu().numpy() - U2.cpu().numpy()).max() <= 1e-12
     assert np.abs(V1.cpu().numpy() - V2.cpu().numpy()).max() <= 1e-12
+
+
+@pytest.mark.parametrize("kind,m,n,r,s,dtype,eps", [
+    ("product", 700, 500, 40, 4, "f64", 1e-8),     # rank-deficient blocks: fresh completions in the block QR
+    ("product", 2000, 900, 100, 32, "f64", 1e-8),  # the largest block
+    ("noisy", 20000, 1500, 60, 8, "f32", 1e-5),    # left vectors past the one-CTA size
+    ("full", 60, 40, 40, 8, "f64", 1e-8),          # the blocks fill the space
+])
+def test_block_rank_with_block_gram_schmidt(kind, m, n, r, s, dtype, eps):
+    """GK_FLAG_BLOCK_GS (reorthogonalized block Gram-Schmidt: k_bgs_dots, k_bgs_sub and the
+    double-f32 Ritz product project each block against the earlier basis) against the oracle:
+    the same steps and rank, sigma(B) within 1e-10 sigma_1 (tests/test_block_reading_cpu.py
+    restates the flow)."""
+    from oracle import block_gk as bgk
+
+    if kind == "full":
+        A = synth.rng(m * n).standard_normal((m, n))
+    else:
+        A = synth.gaussian_product(m, n, r, 0.0 if kind == "product" else 1e-7, seed=m + n + s, dtype=np.float64)
+    if dtype == "f32":
+        A32 = A.astype(np.float32)
+        At, Ad = cuda(A32), A32.astype(np.float64)
+    else:
+        At, Ad = cuda(A), A
+    Q0 = synth.rng(s + m).standard_normal((m, s))
+    rk, sig, steps, st, info = gk().gk_block_numrank(At, s, eps, start=cuda(Q0), want_sigma=True, block_gs=True)
+    r_or, sig_or, k_or = bgk.block_numrank(Ad, Q0, eps=eps)
+    assert st == 0 and steps == k_or and rk == r_or == r
+    np.testing.assert_allclose(sig.cpu().numpy(), sig_or[: steps * s], rtol=0, atol=1e-10 * sig_or[0])
+
+
+def test_block_rank_csr_with_block_gram_schmidt():
+    import scipy.sparse as sp
+
+    from oracle import block_gk as bgk
+
+    m, n, s = 2003, 1499, 4
+    d = synth.sparse_planted(m, n, 12, 10.0 * 0.9 ** np.arange(1, 6), 11, usup=200, vsup=100, dtype=np.float64)
+    Ad = sp.csr_matrix((d["vals"], d["colind"], d["rowptr"]), shape=(m, n)).toarray()
+    M = gk()
+    A = M.CSR(m, n, cuda(d["rowptr"]), cuda(d["colind"]), cuda(d["vals"]), cuda(d["t_rowptr"]), cuda(d["t_colind"]),
+              cuda(d["t_vals"]))
+    Q0 = synth.rng(12).standard_normal((m, s))
+    rk, sig, steps, st, info = M.gk_block_numrank(A, s, 1e-8, 8, start=cuda(Q0), want_sigma=True, block_gs=True)
+    r_or, sig_or, k_or = bgk.block_numrank(Ad, Q0, eps=1e-8, kmax=8)
+    assert st == 0 and steps == k_or == 8 and rk == r_or
+    np.testing.assert_allclose(sig.cpu().numpy(), sig_or[: steps * s], rtol=0, atol=1e-10 * sig_or[0])
+
+
+@pytest.mark.parametrize("m,n,s,steps,r,dtype", [(2000, 1200, 8, 12, 40, "f64"), (3000, 1400, 8, 10, 40, "bf16")])
+def test_block_fsvd_with_block_gram_schmidt(m, n, s, steps, r, dtype):
+    """gk_block_fsvd with GK_FLAG_BLOCK_GS against the column-wise flow on the same start block:
+    values to 1e-10, vectors to 1e-8, residuals to 1e-6 relative (1e-13 sigma_1 absolute)."""
+    A = synth.gaussian_product(m, n, min(m, n), 1e-3, seed=m + s, dtype=np.float64)
+    if dtype == "bf16":
+        At = cuda(synth.to_bf16_bits(A.astype(np.float32)).view(np.int16)).view(torch.bfloat16)
+    else:
+        At = cuda(A)
+    Q0 = cuda(synth.rng(m + steps).standard_normal((m, s)))
+    M = gk()
+    U1, S1, V1, r1, st1, _ = M.gk_block_fsvd(At, s, steps, r, start=Q0)
+    U2, S2, V2, r2, st2, _ = M.gk_block_fsvd(At, s, steps, r, start=Q0, block_gs=True)
+    assert st1 == st2 == 0
+    S1n = S1.cpu().numpy()
+    np.testing.assert_allclose(S2.cpu().numpy(), S1n, rtol=1e-10)
+    assert angle_err(U2.cpu().numpy(), U1.cpu().numpy()) < 1e-8 and angle_err(V2.cpu().numpy(), V1.cpu().numpy()) < 1e-8
+    np.testing.assert_allclose(r2.cpu().numpy(), r1.cpu().numpy(), rtol=1e-6, atol=1e-13 * S1n[0])
