@@ -270,3 +270,18 @@ def test_blocks_past_the_left_space_are_zero(m, n, s):
     r_or, sig_or, k_or = bgk.block_numrank(A, Q0, eps=1e-8)
     assert (r_or, k_or) == (r, k)
     np.testing.assert_allclose(sig, sig_or[: k * s], rtol=1e-12)
+
+
+@pytest.mark.parametrize("noise,eps,s", [(1e-12, 1e-14, 4), (1e-12, 1e-14, 8), (1e-11, 1e-13, 8)])
+def test_block_gram_schmidt_through_near_breakdowns(noise, eps, s):
+    """Past the planted rank the blocks' new directions come from a noise floor 1e-12 or 1e-11 of
+    sigma_1: the projections cancel to just above the 2^-46 breakdown test, the hardest case for a
+    block Gram-Schmidt; with eps below the floor the sweep runs through them for 12 steps, and the
+    block flow gives the oracle's rank and sigma(B) as the column-wise flow does."""
+    A = synth.gaussian_product(300, 200, 20, noise, seed=5, dtype=np.float64)
+    Q0 = np.random.default_rng(s).standard_normal((300, s))
+    r_or, sig_or, k_or = bgk.block_numrank(A, Q0, eps=eps, kmax=12)
+    for gs in (False, True):
+        r, sig, k, _ = column_block_gk(A, Q0, eps, 12, 0, block_gs=gs)
+        assert (r, k) == (r_or, k_or) == (12 * s, 12)
+        np.testing.assert_allclose(sig, sig_or[: k * s], rtol=0, atol=1e-13 * sig_or[0])
