@@ -1319,6 +1319,116 @@ int read_block(const BlockBufs &b, BlockCtl *hb, HostCtl *hc, cudaStream_t st) {
   return GK_OK;
 }
 
+// One block sweep's state (block_impl, block_fsvd_impl): options, operator, buffers and counts.
+struct BlockRun {
+  gk_opts o;
+  cudaStream_t st = nullptr;
+  Dev d;
+  OpStage stg;
+  Op op;
+  BlockBufs b{};
+  Workspace ws;
+  int64_t m = 0, n = 0, ldu = 0, ldv = 0, cols = 0, kb = 0;
+  int s = 0;
+  int64_t nfresh = 0, matvecs = 0;
+  int breakdowns = 0;
+};
+
+// The workspace and the staged operator; Q_1 R_0 = Q0 (the given block, or column c drawn as
+// Algorithm 1's start vector with seed + c); P_1 R_1 = A^T Q_1 and sigma~ = ||R_1|| (the first
+// right block judged with eps).
+int block_begin(BlockRun &R, const gk_matrix *Ain, int s, const double *Q0, int64_t kb, const gk_opts &o,
+                const Dev &d, double eps) {
+  R.o = o;
+  R.st = (cudaStream_t)o.stream;
+  R.d = d;
+  R.s = s;
+  R.kb = kb;
+  R.m = Ain->m;
+  R.n = Ain->n;
+  const cudaStream_t st = R.st;
+  int rc = stage_plan(Ain, &R.stg);
+  if (rc) return rc;
+  const bool host_q0 = Q0 && on_host(Q0);
+  BlockBufs &b = R.b;
+  R.op = make_op(Ain);
+  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
+  b.acc = accurate_ok(R.op);
+  b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
+  b.bgs = b.df && (o.flags & GK_FLAG_BLOCK_GS) != 0;
+  const size_t bytes = block_layout(Ain, s, kb, d, R.stg, nullptr, &b, &R.op);
+  rc = acquire(R.ws, bytes, o, st);
+  if (rc) return rc;
+  R.op = make_op(Ain);
+  block_layout(Ain, s, kb, d, R.stg, R.ws.base, &b, &R.op);
+  rc = stage_copy(Ain, R.stg, R.op, st);
+  if (rc) return rc;
+  const int64_t m = R.m, n = R.n;
+  R.ldu = round_up(m, 32);
+  R.ldv = round_up(n, 32);
+  R.cols = (kb + 1) * s;
+  const int64_t ldu = R.ldu, ldv = R.ldv, cols = R.cols;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
+  GK_CUDA(cudaMemsetAsync(b.bc, 0, sizeof(BlockCtl), st));
+  GK_CUDA(cudaMemsetAsync(b.Bf, 0, sizeof(double) * cols * cols, st));
+  if (b.df) {  // the shadows' padding rows (past m, n) are read beside the last odd row: keep them 0
+    GK_CUDA(cudaMemsetAsync(b.Qs, 0, sizeof(float2) * ldu * cols, st));
+    GK_CUDA(cudaMemsetAsync(b.Ps, 0, sizeof(float2) * ldv * cols, st));
+  }
+  const double *q0 = Q0;
+  if (host_q0) {
+    GK_CUDA(cudaMemcpyAsync(b.q0, Q0, sizeof(double) * m * s, cudaMemcpyHostToDevice, st));
+    q0 = b.q0;
+  }
+  if (!q0) {
+    for (int c = 0; c < s; ++c) GK_CUDA(draw_start(b.W + (int64_t)c * m, m, o.seed + (uint64_t)c, st));
+    q0 = b.W;
+  }
+  rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &R.nfresh, &R.breakdowns, st, d);
+  if (rc) return rc;
+  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));  // the breakdown scale follows the blocks' norms from here
+  rc = block_product(R.op, b, true, b.Q, ldu, s, st, d);
+  if (rc) return rc;
+  rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &R.nfresh, &R.breakdowns, st, d);
+  if (rc) return rc;
+  GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
+  GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, eps, b.bc, st));
+  R.matvecs = s;
+  return GK_OK;
+}
+
+// Q_{j+1} S_{j+1} = A P_j - Q_j R_j^T, reorthogonalized, judged (left side) and read back (j = steps)
+int block_left_step(BlockRun &R, int steps, double eps, BlockCtl *hb, HostCtl *hc) {
+  BlockBufs &b = R.b;
+  const int s = R.s;
+  const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
+  int rc = block_product(R.op, b, false, b.P + pj * R.ldv, R.ldv, s, R.st, R.d);
+  if (rc) return rc;
+  rc = block_orth_bgs(b, R.m, b.Q, R.ldu, b.Qs, (int)qn, s, b.W, R.m, 0, R.o.seed, &R.nfresh, &R.breakdowns, R.st,
+                      R.d);
+  if (rc) return rc;
+  GK_CUDA(block_dots(b.Q + qn * R.ldu, R.ldu, b.W, R.m, R.m, s, b.dpart, b.raw, R.st));
+  GK_CUDA(block_judge(b.raw, s, b.Bf, R.cols, (int)qn, (int)pj, 0, eps, b.bc, R.st));
+  R.matvecs += s;
+  return read_block(b, hb, hc, R.st);
+}
+
+// P_{j+1} R_{j+1} = A^T Q_{j+1} - P_j S_{j+1}^T, reorthogonalized, judged (right side) and read back
+int block_right_step(BlockRun &R, int steps, double eps, BlockCtl *hb, HostCtl *hc) {
+  BlockBufs &b = R.b;
+  const int s = R.s;
+  const int64_t qn = (int64_t)steps * s;
+  int rc = block_product(R.op, b, true, b.Q + qn * R.ldu, R.ldu, s, R.st, R.d);
+  if (rc) return rc;
+  rc = block_orth_bgs(b, R.n, b.P, R.ldv, b.Ps, (int)qn, s, b.W, R.n, 1, R.o.seed, &R.nfresh, &R.breakdowns, R.st,
+                      R.d);
+  if (rc) return rc;
+  GK_CUDA(block_dots(b.P + qn * R.ldv, R.ldv, b.W, R.n, R.n, s, b.dpart, b.raw, R.st));
+  GK_CUDA(block_judge(b.raw, s, b.Bf, R.cols, (int)qn, (int)qn, 1, eps, b.bc, R.st));
+  R.matvecs += s;
+  return read_block(b, hb, hc, R.st);
+}
+
 int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int kmax, const gk_opts *oin, int *rank,
                double *sigma, int *steps_out, gk_info *info) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -1330,7 +1440,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   // the arguments first: a bad request is refused with or without a device
   int rc = check_matrix(Ain);
   if (rc) return rc;
-  const int64_t m = Ain->m, n = Ain->n, mn = m < n ? m : n;
+  const int64_t mn = Ain->m < Ain->n ? Ain->m : Ain->n;
   if (!rank || s < 1 || s > kBlockMaxS || s > mn || !(eps >= 0.0) || !isfinite(eps)) return GK_INVALID_ARG;
   const gk_opts o = oin ? *oin : defaults();
   if (o.eps_absolute) return GK_INVALID_ARG;
@@ -1339,71 +1449,17 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   if (rc) return rc;
   Dev d;
   if (!get_device(&d)) return GK_NO_DEVICE;
-  cudaStream_t st = (cudaStream_t)o.stream;
-  OpStage stg;
-  rc = stage_plan(Ain, &stg);
-  if (rc) return rc;
-  const bool host_q0 = Q0 && on_host(Q0);
   const bool host_sigma = sigma && on_host(sigma);
-  Op op = make_op(Ain);
-  BlockBufs b{};
-  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
-  b.acc = accurate_ok(op);
-  b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
-  b.bgs = b.df && (o.flags & GK_FLAG_BLOCK_GS) != 0;
-  const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
-  Workspace ws;
-  rc = acquire(ws, bytes, o, st);
+  BlockRun R;
+  rc = block_begin(R, Ain, s, Q0, kb, o, d, eps);
   if (rc) return rc;
-  op = make_op(Ain);
-  block_layout(Ain, s, kb, d, stg, ws.base, &b, &op);
-  rc = stage_copy(Ain, stg, op, st);
-  if (rc) return rc;
-  const int64_t ldu = round_up(m, 32), ldv = round_up(n, 32), cols = (kb + 1) * s;
-  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
-  GK_CUDA(cudaMemsetAsync(b.bc, 0, sizeof(BlockCtl), st));
-  GK_CUDA(cudaMemsetAsync(b.Bf, 0, sizeof(double) * cols * cols, st));
-  if (b.df) {  // the shadows' padding rows (past m, n) are read beside the last odd row: keep them 0
-    GK_CUDA(cudaMemsetAsync(b.Qs, 0, sizeof(float2) * ldu * cols, st));
-    GK_CUDA(cudaMemsetAsync(b.Ps, 0, sizeof(float2) * ldv * cols, st));
-  }
-  // Q_1 R_0 = Q0: the given block, or column c drawn as Algorithm 1's start vector (seed + c)
-  const double *q0 = Q0;
-  if (host_q0) {
-    GK_CUDA(cudaMemcpyAsync(b.q0, Q0, sizeof(double) * m * s, cudaMemcpyHostToDevice, st));
-    q0 = b.q0;
-  }
-  if (!q0) {
-    for (int c = 0; c < s; ++c) GK_CUDA(draw_start(b.W + (int64_t)c * m, m, o.seed + (uint64_t)c, st));
-    q0 = b.W;
-  }
-  int64_t nfresh = 0;
-  int breakdowns = 0;
-  rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
-  if (rc) return rc;
-  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));  // the breakdown scale follows the blocks' norms from here
-  // P_1 R_1 = A^T Q_1; sigma~ = ||R_1||
-  rc = block_product(op, b, true, b.Q, ldu, s, st, d);
-  if (rc) return rc;
-  rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
-  if (rc) return rc;
-  GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
-  GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, eps, b.bc, st));
-  int64_t matvecs = s;
+  BlockBufs &b = R.b;
+  const cudaStream_t st = R.st;
   int steps = 1, stop = 0;
   BlockCtl hb;
   HostCtl hc;
   for (;;) {
-    // Q_{j+1} S_{j+1} = A P_j - Q_j R_j^T, reorthogonalized (j = steps)
-    const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
-    rc = block_product(op, b, false, b.P + pj * ldv, ldv, s, st, d);
-    if (rc) return rc;
-    rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
-    if (rc) return rc;
-    GK_CUDA(block_dots(b.Q + qn * ldu, ldu, b.W, m, m, s, b.dpart, b.raw, st));
-    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)pj, 0, eps, b.bc, st));
-    matvecs += s;
-    rc = read_block(b, &hb, &hc, st);
+    rc = block_left_step(R, steps, eps, &hb, &hc);
     if (rc) return rc;
     if (hb.brk) {
       stop = 1;
@@ -1417,15 +1473,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
       stop = 3;
       break;
     }
-    // P_{j+1} R_{j+1} = A^T Q_{j+1} - P_j S_{j+1}^T, reorthogonalized
-    rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
-    if (rc) return rc;
-    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
-    if (rc) return rc;
-    GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
-    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)qn, 1, eps, b.bc, st));
-    matvecs += s;
-    rc = read_block(b, &hb, &hc, st);
+    rc = block_right_step(R, steps, eps, &hb, &hc);
     if (rc) return rc;
     if (hb.brk) {
       stop = 2;
@@ -1435,7 +1483,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   }
   // Algorithm 3 on B ((steps + 1) s x steps s), padded with zero columns to its square
   const int K = (steps + 1) * s, nsig = steps * s;
-  GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * cols, sizeof(double) * K, K,
+  GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * R.cols, sizeof(double) * K, K,
                             cudaMemcpyDeviceToDevice, st));
   GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
   GK_CUDA(block_count(b.sigma, nsig, eps, b.rank, st));
@@ -1454,9 +1502,9 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   inf.steps = steps;
   inf.kprime = nsig;
   inf.stop_reason = stop;
-  inf.matvecs = matvecs;
+  inf.matvecs = R.matvecs;
   inf.svd_sweeps = sweeps;
-  inf.breakdowns = breakdowns;
+  inf.breakdowns = R.breakdowns;
   inf.sigma_est = hb.sest;
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
@@ -1487,77 +1535,20 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   if (!get_device(&d)) return GK_NO_DEVICE;
   if (on_host(U) || on_host(S) || on_host(V) || on_host(resid)) return GK_INVALID_ARG;  // device outputs only
   const gk_opts o = oin ? *oin : defaults();
-  cudaStream_t st = (cudaStream_t)o.stream;
-  OpStage stg;
-  rc = stage_plan(Ain, &stg);
+  BlockRun R;
+  rc = block_begin(R, Ain, s, Q0, kb, o, d, 0.0);
   if (rc) return rc;
-  const bool host_q0 = Q0 && on_host(Q0);
-  Op op = make_op(Ain);
-  BlockBufs b{};
-  b.df = (o.flags & GK_FLAG_ORTH_F64) == 0;
-  b.acc = accurate_ok(op);
-  b.f32 = (o.flags & GK_FLAG_BLOCK_F32) != 0;
-  b.bgs = b.df && (o.flags & GK_FLAG_BLOCK_GS) != 0;
-  const size_t bytes = block_layout(Ain, s, kb, d, stg, nullptr, &b, &op);
-  Workspace ws;
-  rc = acquire(ws, bytes, o, st);
-  if (rc) return rc;
-  op = make_op(Ain);
-  block_layout(Ain, s, kb, d, stg, ws.base, &b, &op);
-  rc = stage_copy(Ain, stg, op, st);
-  if (rc) return rc;
-  const int64_t ldu = round_up(m, 32), ldv = round_up(n, 32), cols = (kb + 1) * s;
-  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
-  GK_CUDA(cudaMemsetAsync(b.bc, 0, sizeof(BlockCtl), st));
-  GK_CUDA(cudaMemsetAsync(b.Bf, 0, sizeof(double) * cols * cols, st));
-  if (b.df) {
-    GK_CUDA(cudaMemsetAsync(b.Qs, 0, sizeof(float2) * ldu * cols, st));
-    GK_CUDA(cudaMemsetAsync(b.Ps, 0, sizeof(float2) * ldv * cols, st));
-  }
-  const double *q0 = Q0;
-  if (host_q0) {
-    GK_CUDA(cudaMemcpyAsync(b.q0, Q0, sizeof(double) * m * s, cudaMemcpyHostToDevice, st));
-    q0 = b.q0;
-  }
-  if (!q0) {
-    for (int c = 0; c < s; ++c) GK_CUDA(draw_start(b.W + (int64_t)c * m, m, o.seed + (uint64_t)c, st));
-    q0 = b.W;
-  }
-  int64_t nfresh = 0;
-  int breakdowns = 0;
-  rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &nfresh, &breakdowns, st, d);
-  if (rc) return rc;
-  GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));
-  rc = block_product(op, b, true, b.Q, ldu, s, st, d);
-  if (rc) return rc;
-  rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
-  if (rc) return rc;
-  GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
-  GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, 0.0, b.bc, st));
-  int64_t matvecs = s;
+  BlockBufs &b = R.b;
+  const cudaStream_t st = R.st;
+  const int64_t ldu = R.ldu, ldv = R.ldv;
   int steps = 1;
   BlockCtl hb;
   HostCtl hc;
   for (;;) {  // eps = 0: no block ends the sweep; it runs kb steps or until the blocks fill min(m, n)
-    const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
-    rc = block_product(op, b, false, b.P + pj * ldv, ldv, s, st, d);
-    if (rc) return rc;
-    rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, (int)qn, s, b.W, m, 0, o.seed, &nfresh, &breakdowns, st, d);
-    if (rc) return rc;
-    GK_CUDA(block_dots(b.Q + qn * ldu, ldu, b.W, m, m, s, b.dpart, b.raw, st));
-    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)pj, 0, 0.0, b.bc, st));
-    matvecs += s;
-    rc = read_block(b, &hb, &hc, st);
+    rc = block_left_step(R, steps, 0.0, &hb, &hc);
     if (rc) return rc;
     if (steps >= kb || (int64_t)(steps + 1) * s > mn) break;
-    rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
-    if (rc) return rc;
-    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
-    if (rc) return rc;
-    GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
-    GK_CUDA(block_judge(b.raw, s, b.Bf, cols, (int)qn, (int)qn, 1, 0.0, b.bc, st));
-    matvecs += s;
-    rc = read_block(b, &hb, &hc, st);
+    rc = block_right_step(R, steps, 0.0, &hb, &hc);
     if (rc) return rc;
     ++steps;
   }
@@ -1573,14 +1564,14 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   // in b.raw for the residuals
   {
     const int64_t qn = (int64_t)steps * s;
-    rc = block_product(op, b, true, b.Q + qn * ldu, ldu, s, st, d);
+    rc = block_product(R.op, b, true, b.Q + qn * ldu, ldu, s, st, d);
     if (rc) return rc;
-    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &nfresh, &breakdowns, st, d);
+    rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &R.nfresh, &R.breakdowns, st, d);
     if (rc) return rc;
     GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
-    matvecs += s;
+    R.matvecs += s;
   }
-  GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * cols, sizeof(double) * K, K,
+  GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * R.cols, sizeof(double) * K, K,
                             cudaMemcpyDeviceToDevice, st));
   GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
   // U = Q X_r (all K rows of X), V = P_{1..k} Y_r (the first ks rows: the padding columns of B
@@ -1601,9 +1592,9 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   GK_CUDA(cudaStreamSynchronize(st));
   inf.steps = steps;
   inf.kprime = ks;
-  inf.matvecs = matvecs;
+  inf.matvecs = R.matvecs;
   inf.svd_sweeps = sweeps;
-  inf.breakdowns = breakdowns;
+  inf.breakdowns = R.breakdowns;
   inf.sigma_est = hb.sest;
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
