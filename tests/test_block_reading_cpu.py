@@ -7,7 +7,10 @@ column the passes reduce to <= 2^-46 of the largest norm so far, and takes each 
 factor as Q_{j+1}^T (A P_j) (resp. P_{j+1}^T (A^T Q_{j+1})).  This module restates that flow in
 numpy and checks that it gives the oracle's block steps, rank and singular values of B, with
 rank-deficient blocks (the fresh completions) included -- the reading the GPU parity tests rely
-on, pinned independently of the GPU."""
+on, pinned independently of the GPU.  The same for gk_block_fsvd's flow (the next right block's
+R_{k+1} as inner products, U from all rows of X, V from the first ks rows of Y, the residuals
+from rows ks .. ks + s of X), for blocks that run past the space (zero completions), and for the
+block Gram-Schmidt of GK_FLAG_BLOCK_GS (reorthogonalized block classical Gram-Schmidt)."""
 import numpy as np
 import pytest
 
