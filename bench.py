@@ -740,7 +740,12 @@ def run_gk(args, rank, world):
             torch.cuda.synchronize()
             bms = e0.elapsed_time(e1) / reps
             ra, rb = gk.gk_residuals(A, Ub, Sb, Vb)
+            passes = infb["matvecs"] / bs  # block products: one pass over A each
             block = {"value": k / (bms / 1e3), "unit": "triplets/s", "ms_per_step": bms, "s": bs, "block_steps": bsteps,
+                     "operator_passes": passes,
+                     # the operator's bytes over the whole solve's time: a lower bound on the block
+                     # products' achieved rate (the solve also spends time outside them)
+                     "operator_gbs_whole_solve": passes * operator_bytes(A) / (bms / 1e3) / 1e9,
                      "f32_products": bool(args.block_f32), "ritz_df": bool(args.ritz_df),
                      "block_gs": bool(args.block_gs), "status": stb, "matvecs": infb["matvecs"],
                      "breakdowns": infb["breakdowns"], "launches": infb["launches"],
