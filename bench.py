@@ -740,7 +740,7 @@ def run_gk(args, rank, world):
             torch.cuda.synchronize()
             bms = e0.elapsed_time(e1) / reps
             ra, rb = gk.gk_residuals(A, Ub, Sb, Vb)
-            passes = infb["matvecs"] / bs  # block products: one pass over A each
+            passes = infb["matvecs"] / bs  # one pass over a dense reduced-precision A per block product
             block = {"value": k / (bms / 1e3), "unit": "triplets/s", "ms_per_step": bms, "s": bs, "block_steps": bsteps,
                      "operator_passes": passes,
                      # the operator's bytes over the whole solve's time: a lower bound on the block
