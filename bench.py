@@ -740,6 +740,7 @@ def run_gk(args, rank, world):
             torch.cuda.synchronize()
             bms = e0.elapsed_time(e1) / reps
             ra, rb = gk.gk_residuals(A, Ub, Sb, Vb)
+            infp = gk.gk_block_fsvd(A, bs, bsteps, k, profile=True, **bkw)[5]  # phase times, untimed
             passes = infb["matvecs"] / bs  # one pass over a dense reduced-precision A per block product
             block = {"value": k / (bms / 1e3), "unit": "triplets/s", "ms_per_step": bms, "s": bs, "block_steps": bsteps,
                      "operator_passes": passes,
@@ -750,7 +751,9 @@ def run_gk(args, rank, world):
                      "block_gs": bool(args.block_gs), "status": stb, "matvecs": infb["matvecs"],
                      "breakdowns": infb["breakdowns"], "launches": infb["launches"],
                      "resid_est_max_rel": float(rb_est.max()) / float(Sb[0]),
-                     "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sb[0])}
+                     "resid_max_rel": float(torch.maximum(ra, rb).max()) / float(Sb[0]),
+                     "ms_phases": {"A_P": infp["ms_matvec"], "At_Q": infp["ms_matvec_t"], "gram_schmidt": infp["ms_orth"],
+                                   "small_kernels_and_svd": infp["ms_small"], "ritz_vectors": infp["ms_restart"]}}
         except Exception as exc:  # an auxiliary leg: the headline stands without it
             block = {"error": repr(exc)[:300]}
 

@@ -1332,6 +1332,7 @@ struct BlockRun {
   int s = 0;
   int64_t nfresh = 0, matvecs = 0;
   int breakdowns = 0;
+  Prof prof;  // GK_FLAG_PROFILE: products (A P, A^T Q), Gram-Schmidt, small kernels and SVD, Ritz vectors
 };
 
 // The workspace and the staged operator; Q_1 R_0 = Q0 (the given block, or column c drawn as
@@ -1346,6 +1347,8 @@ int block_begin(BlockRun &R, const gk_matrix *Ain, int s, const double *Q0, int6
   R.kb = kb;
   R.m = Ain->m;
   R.n = Ain->n;
+  R.prof.on = (o.flags & GK_FLAG_PROFILE) != 0;
+  R.prof.s = R.st;
   const cudaStream_t st = R.st;
   int rc = stage_plan(Ain, &R.stg);
   if (rc) return rc;
@@ -1384,15 +1387,23 @@ int block_begin(BlockRun &R, const gk_matrix *Ain, int s, const double *Q0, int6
     for (int c = 0; c < s; ++c) GK_CUDA(draw_start(b.W + (int64_t)c * m, m, o.seed + (uint64_t)c, st));
     q0 = b.W;
   }
+  R.prof.begin(PC_ORTH);
   rc = block_orth_bgs(b, m, b.Q, ldu, b.Qs, 0, s, q0, m, 0, o.seed, &R.nfresh, &R.breakdowns, st, d);
   if (rc) return rc;
+  R.prof.end();
   GK_CUDA(reset_ctl(b.ctl, 0.0, 1, st));  // the breakdown scale follows the blocks' norms from here
+  R.prof.begin(PC_MATVEC_T);
   rc = block_product(R.op, b, true, b.Q, ldu, s, st, d);
   if (rc) return rc;
+  R.prof.end();
+  R.prof.begin(PC_ORTH);
   rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, 0, s, b.W, n, 1, o.seed, &R.nfresh, &R.breakdowns, st, d);
   if (rc) return rc;
+  R.prof.end();
+  R.prof.begin(PC_SMALL);
   GK_CUDA(block_dots(b.P, ldv, b.W, n, n, s, b.dpart, b.raw, st));
   GK_CUDA(block_judge(b.raw, s, b.Bf, cols, 0, 0, 2, eps, b.bc, st));
+  R.prof.end();
   R.matvecs = s;
   return GK_OK;
 }
@@ -1402,13 +1413,19 @@ int block_left_step(BlockRun &R, int steps, double eps, BlockCtl *hb, HostCtl *h
   BlockBufs &b = R.b;
   const int s = R.s;
   const int64_t pj = (int64_t)(steps - 1) * s, qn = (int64_t)steps * s;
+  R.prof.begin(PC_MATVEC);
   int rc = block_product(R.op, b, false, b.P + pj * R.ldv, R.ldv, s, R.st, R.d);
   if (rc) return rc;
+  R.prof.end();
+  R.prof.begin(PC_ORTH);
   rc = block_orth_bgs(b, R.m, b.Q, R.ldu, b.Qs, (int)qn, s, b.W, R.m, 0, R.o.seed, &R.nfresh, &R.breakdowns, R.st,
                       R.d);
   if (rc) return rc;
+  R.prof.end();
+  R.prof.begin(PC_SMALL);
   GK_CUDA(block_dots(b.Q + qn * R.ldu, R.ldu, b.W, R.m, R.m, s, b.dpart, b.raw, R.st));
   GK_CUDA(block_judge(b.raw, s, b.Bf, R.cols, (int)qn, (int)pj, 0, eps, b.bc, R.st));
+  R.prof.end();
   R.matvecs += s;
   return read_block(b, hb, hc, R.st);
 }
@@ -1418,13 +1435,19 @@ int block_right_step(BlockRun &R, int steps, double eps, BlockCtl *hb, HostCtl *
   BlockBufs &b = R.b;
   const int s = R.s;
   const int64_t qn = (int64_t)steps * s;
+  R.prof.begin(PC_MATVEC_T);
   int rc = block_product(R.op, b, true, b.Q + qn * R.ldu, R.ldu, s, R.st, R.d);
   if (rc) return rc;
+  R.prof.end();
+  R.prof.begin(PC_ORTH);
   rc = block_orth_bgs(b, R.n, b.P, R.ldv, b.Ps, (int)qn, s, b.W, R.n, 1, R.o.seed, &R.nfresh, &R.breakdowns, R.st,
                       R.d);
   if (rc) return rc;
+  R.prof.end();
+  R.prof.begin(PC_SMALL);
   GK_CUDA(block_dots(b.P + qn * R.ldv, R.ldv, b.W, R.n, R.n, s, b.dpart, b.raw, R.st));
   GK_CUDA(block_judge(b.raw, s, b.Bf, R.cols, (int)qn, (int)qn, 1, eps, b.bc, R.st));
+  R.prof.end();
   R.matvecs += s;
   return read_block(b, hb, hc, R.st);
 }
@@ -1483,10 +1506,12 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   }
   // Algorithm 3 on B ((steps + 1) s x steps s), padded with zero columns to its square
   const int K = (steps + 1) * s, nsig = steps * s;
+  R.prof.begin(PC_SMALL);
   GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * R.cols, sizeof(double) * K, K,
                             cudaMemcpyDeviceToDevice, st));
   GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
   GK_CUDA(block_count(b.sigma, nsig, eps, b.rank, st));
+  R.prof.end();
   if (sigma) {
     if (host_sigma)
       GK_CUDA(cudaMemcpyAsync(sigma, b.sigma, sizeof(double) * nsig, cudaMemcpyDeviceToHost, st));
@@ -1506,6 +1531,7 @@ int block_impl(const gk_matrix *Ain, int s, const double *Q0, double eps, int km
   inf.svd_sweeps = sweeps;
   inf.breakdowns = R.breakdowns;
   inf.sigma_est = hb.sest;
+  R.prof.finish(&inf);
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
   if (info) *info = inf;
@@ -1564,16 +1590,23 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   // in b.raw for the residuals
   {
     const int64_t qn = (int64_t)steps * s;
+    R.prof.begin(PC_MATVEC_T);
     rc = block_product(R.op, b, true, b.Q + qn * ldu, ldu, s, st, d);
     if (rc) return rc;
+    R.prof.end();
+    R.prof.begin(PC_ORTH);
     rc = block_orth_bgs(b, n, b.P, ldv, b.Ps, (int)qn, s, b.W, n, 1, o.seed, &R.nfresh, &R.breakdowns, st, d);
     if (rc) return rc;
+    R.prof.end();
     GK_CUDA(block_dots(b.P + qn * ldv, ldv, b.W, n, n, s, b.dpart, b.raw, st));
     R.matvecs += s;
   }
+  R.prof.begin(PC_SMALL);
   GK_CUDA(cudaMemcpy2DAsync(b.Bm, sizeof(double) * K, b.Bf, sizeof(double) * R.cols, sizeof(double) * K, K,
                             cudaMemcpyDeviceToDevice, st));
   GK_CUDA(small_svd(b.Bm, b.Yw, K, b.sigma, b.X, b.Y, b.nrm, b.pos, b.sweeps, b.ctl, st));
+  R.prof.end();
+  R.prof.begin(PC_RESTART);
   // U = Q X_r (all K rows of X), V = P_{1..k} Y_r (the first ks rows: the padding columns of B
   // never enter the right vectors of nonzero values); with GK_FLAG_RITZ_DF from the bases'
   // double-f32 copies (b.Yw, free after the small SVD, holds X's and then Y's split)
@@ -1584,6 +1617,7 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
     GK_CUDA(ritz_gemm(b.Q, ldu, m, K, b.X, K, rr, U, m, st, d));
     GK_CUDA(ritz_gemm(b.P, ldv, n, ks, b.Y, K, rr, V, n, st, d));
   }
+  R.prof.end();
   GK_CUDA(block_resid(b.raw, s, b.X, K, ks, rr, resid, st));
   GK_CUDA(cudaMemcpyAsync(S, b.sigma, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
   GK_CUDA(sign_normalize(U, m, m, V, n, n, rr, st));
@@ -1596,6 +1630,7 @@ int block_fsvd_impl(const gk_matrix *Ain, int s, const double *Q0, int steps_in,
   inf.svd_sweeps = sweeps;
   inf.breakdowns = R.breakdowns;
   inf.sigma_est = hb.sest;
+  R.prof.finish(&inf);
   inf.seconds = seconds_since(t0);
   inf.launches = launch_count() - l0;
   if (info) *info = inf;

@@ -461,12 +461,13 @@ def gk_numrank(A, eps: float = 1e-8, kmax: int = 0, *, eps_absolute: bool = Fals
 
 def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None, seed: int | None = None,
                      stream=None, workspace=None, scale: float = 1.0, want_sigma: bool = False, check: bool = True,
-                     orth_f64: bool = False, f32_products: bool = False, block_gs: bool = False):
+                     orth_f64: bool = False, f32_products: bool = False, block_gs: bool = False,
+                     profile: bool = False):
     """Numerical rank from a block of s start vectors (block Algorithm 1 + Algorithm 3).
     start: optional m x s start block.  f32_products: the block products of a reduced-precision
     dense operator in f32 (GK_FLAG_BLOCK_F32, experimental); block_gs: the block Gram-Schmidt
-    (GK_FLAG_BLOCK_GS, experimental).  Returns (rank, sigma(B) or None, block steps, status,
-    info dict)."""
+    (GK_FLAG_BLOCK_GS, experimental); profile: the info dict's ms_* phase times (GK_FLAG_PROFILE).
+    Returns (rank, sigma(B) or None, block steps, status, info dict)."""
     M, keep_a = make_matrix(A, scale)
     if start is not None and tuple(start.shape) != (M.m, int(s)):
         raise ValueError(f"start block must be m x s = {M.m} x {int(s)}, got {tuple(start.shape)}")
@@ -482,7 +483,7 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
         # start is m x s; the library reads it column-major (column c contiguous)
         q0 = start.to(torch.float64).t().contiguous()
     o, ka = _opts(dev if dev.type == "cuda" else torch.device("cuda"), seed=seed, stream=stream, workspace=workspace,
-                  orth_f64=orth_f64)
+                  orth_f64=orth_f64, profile=profile)
     if f32_products:
         o.flags |= GK_FLAG_BLOCK_F32
     if block_gs:
@@ -500,10 +501,12 @@ def gk_block_numrank(A, s: int, eps: float = 1e-8, kmax: int = 0, *, start=None,
 
 def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None = None, stream=None,
                   workspace=None, scale: float = 1.0, check: bool = True, orth_f64: bool = False,
-                  f32_products: bool = False, ritz_df: bool = False, block_gs: bool = False):
+                  f32_products: bool = False, ritz_df: bool = False, block_gs: bool = False,
+                  profile: bool = False):
     """One cycle of the block form of Algorithm 2 on a CUDA operator (gk_block_fsvd, experimental).
     f32_products: GK_FLAG_BLOCK_F32; ritz_df: the Ritz vectors from the bases' double-f32 copies
-    (GK_FLAG_RITZ_DF); block_gs: the block Gram-Schmidt (GK_FLAG_BLOCK_GS).  Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on
+    (GK_FLAG_RITZ_DF); block_gs: the block Gram-Schmidt (GK_FLAG_BLOCK_GS); profile: the info dict's
+    ms_* phase times (GK_FLAG_PROFILE).  Returns (U m x r, S r, V n x r, residuals r, status, info dict), all on
     A's device."""
     M, keep_a = make_matrix(A, scale)
     if start is not None and tuple(start.shape) != (M.m, int(s)):
@@ -516,7 +519,7 @@ def gk_block_fsvd(A, s: int, steps: int, r: int, *, start=None, seed: int | None
     S = torch.empty(r, dtype=torch.float64, device=dev)
     res = torch.empty(r, dtype=torch.float64, device=dev)
     q0 = start.to(torch.float64).t().contiguous() if start is not None else None
-    o, ka = _opts(dev, seed=seed, stream=stream, workspace=workspace, orth_f64=orth_f64)
+    o, ka = _opts(dev, seed=seed, stream=stream, workspace=workspace, orth_f64=orth_f64, profile=profile)
     if f32_products:
         o.flags |= GK_FLAG_BLOCK_F32
     if ritz_df:

@@ -210,3 +210,21 @@ def test_block_fsvd_with_block_gram_schmidt(m, n, s, steps, r, dtype):
     np.testing.assert_allclose(S2.cpu().numpy(), S1n, rtol=1e-10)
     assert angle_err(U2.cpu().numpy(), U1.cpu().numpy()) < 1e-8 and angle_err(V2.cpu().numpy(), V1.cpu().numpy()) < 1e-8
     np.testing.assert_allclose(r2.cpu().numpy(), r1.cpu().numpy(), rtol=1e-6, atol=1e-13 * S1n[0])
+
+
+def test_block_calls_report_phase_times():
+    """GK_FLAG_PROFILE in the block calls: CUDA-event times of the products (A P, A^T Q), the
+    Gram-Schmidt, the small kernels and SVD, and (gk_block_fsvd) the Ritz vectors, all positive,
+    and the same results as without it."""
+    m, n, s = 3000, 1400, 8
+    A = cuda(synth.gaussian_product(m, n, min(m, n), 1e-3, seed=17, dtype=np.float64))
+    Q0 = cuda(synth.rng(18).standard_normal((m, s)))
+    M = gk()
+    r1, s1, k1, st1, i1 = M.gk_block_numrank(A, s, 1e-8, 6, start=Q0, want_sigma=True)
+    r2, s2, k2, st2, i2 = M.gk_block_numrank(A, s, 1e-8, 6, start=Q0, want_sigma=True, profile=True)
+    assert st1 == st2 == 0 and (r1, k1) == (r2, k2)
+    np.testing.assert_array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+    assert i1["ms_matvec"] == 0.0
+    assert min(i2["ms_matvec"], i2["ms_matvec_t"], i2["ms_orth"], i2["ms_small"]) > 0.0
+    *_, st3, i3 = M.gk_block_fsvd(A, s, 6, 20, start=Q0, profile=True)
+    assert st3 == 0 and min(i3["ms_matvec"], i3["ms_matvec_t"], i3["ms_orth"], i3["ms_small"], i3["ms_restart"]) > 0.0
