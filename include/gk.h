@@ -269,7 +269,9 @@ int gk_numrank(const gk_matrix *A, double eps, int kmax, const gk_opts *opts, in
  * double-f32 products (as gk_residuals); f64 and CSR operators run one product
  * per column.  info: steps = block steps, kprime = columns of B, stop_reason 0
  * kmax, 1 left block break, 2 right block break, 3 the blocks filled min(m, n);
- * matvecs counts single-vector products.  Returns GK_OK, GK_NOT_CONVERGED when
+ * matvecs counts single-vector products.  With GK_FLAG_PROFILE: ms_matvec (the A P block
+ * products), ms_matvec_t (A^T Q), ms_orth (the blocks' Gram-Schmidt), ms_small (the triangular
+ * factors, their judges and the SVD of B) and, for gk_block_fsvd, ms_restart (U and V).  Returns GK_OK, GK_NOT_CONVERGED when
  * the small SVD hit its sweep limit, GK_NUMERICAL on a non-finite norm, or an
  * error. */
 int gk_block_numrank(const gk_matrix *A, int s, const double *Q0, double eps, int kmax, const gk_opts *opts, int *rank,
