@@ -154,16 +154,18 @@ def test_host_operator_start_and_sigma():
     np.testing.assert_allclose(sh.numpy(), sd.cpu().numpy(), rtol=0, atol=1e-12 * sd[0].item())
 
 
-def test_caller_workspace_of_the_queried_size():
-    """A caller workspace of exactly gk_block_numrank_workspace() bytes gives the same result."""
+@pytest.mark.parametrize("block_gs", [False, True])
+def test_caller_workspace_of_the_queried_size(block_gs):
+    """A caller workspace of exactly gk_block_numrank_workspace() bytes gives the same result (with
+    the block Gram-Schmidt's buffers when it is asked for)."""
     m, n, s = 800, 500, 4
     A = cuda(synth.gaussian_product(m, n, 22, 0.0, seed=31, dtype=np.float64))
     Q0 = cuda(synth.rng(32).standard_normal((m, s)))
     M = gk()
-    nbytes = M.gk_block_numrank_workspace(A, s)
+    nbytes = M.gk_block_numrank_workspace(A, s, block_gs=block_gs)
     assert nbytes > 0
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    r1, s1, k1, st1, _ = M.gk_block_numrank(A, s, 1e-8, start=Q0, want_sigma=True, workspace=ws)
-    r2, s2, k2, st2, _ = M.gk_block_numrank(A, s, 1e-8, start=Q0, want_sigma=True)
+    r1, s1, k1, st1, _ = M.gk_block_numrank(A, s, 1e-8, start=Q0, want_sigma=True, workspace=ws, block_gs=block_gs)
+    r2, s2, k2, st2, _ = M.gk_block_numrank(A, s, 1e-8, start=Q0, want_sigma=True, block_gs=block_gs)
     assert st1 == st2 == 0 and r1 == r2 == 22 and k1 == k2
     np.testing.assert_array_equal(s1.cpu().numpy(), s2.cpu().numpy())
