@@ -191,11 +191,14 @@ struct NarrowTile {
   static constexpr int kChunk = VEC == 8 ? 16 : 32;       // contraction indices per chunk
 };
 
+// The contraction may be split over blockIdx.z (slices of cspan indices, a multiple of the chunk):
+// with part, each slice writes its unscaled sums to part[(z * k + j) * ldo + o] for k_acc_reduce.
 template <typename T, bool TRANS, bool FAST, int VEC>
 __global__ void __launch_bounds__(kAThreads) k_acc_gemm_narrow(const T *__restrict__ A, int64_t m, int64_t n,
                                                                int64_t ld, double scale, const float *__restrict__ xh,
                                                                const float *__restrict__ xl, int64_t ldx, int k,
-                                                               double *__restrict__ out, int64_t ldo) {
+                                                               double *__restrict__ out, int64_t ldo, int64_t cspan,
+                                                               double *__restrict__ part) {
   using Tl = NarrowTile<VEC>;
   static_assert(VEC == 8 || VEC == 16, "narrow tiles of 8 or 16 vectors");
   static_assert(Tl::kRows * 2 * kATP == VEC && Tl::kRows * Tl::kCols == kAThreads, "thread grid covers the tile");
@@ -217,7 +220,9 @@ __global__ void __launch_bounds__(kAThreads) k_acc_gemm_narrow(const T *__restri
       hi[r][p] = f2(0.f, 0.f);
       lo[r][p] = f2(0.f, 0.f);
     }
-  for (int64_t c0 = 0; c0 < ncon; c0 += Tl::kChunk) {
+  const int64_t cbeg = (int64_t)blockIdx.z * cspan;
+  const int64_t cend = cbeg + cspan < ncon ? cbeg + cspan : ncon;  // this slice of the contraction
+  for (int64_t c0 = cbeg; c0 < cend; c0 += Tl::kChunk) {
     for (int i = tid; i < Tl::kChunk * Tl::kOut; i += kAThreads) {
       int cc, oo;
       if (TRANS) {  // consecutive threads: consecutive columns of one row of A
@@ -229,14 +234,14 @@ __global__ void __launch_bounds__(kAThreads) k_acc_gemm_narrow(const T *__restri
       }
       const int64_t o = o0 + oo, c = c0 + cc;
       float v = 0.f;
-      if (o < nout && c < ncon) v = Vec<T>::one(TRANS ? A + c * ld + o : A + o * ld + c);
+      if (o < nout && c < cend) v = Vec<T>::one(TRANS ? A + c * ld + o : A + o * ld + c);
       As[cc][oo] = v;
     }
     for (int i = tid; i < Tl::kChunk * VEC; i += kAThreads) {
       const int vv = i / Tl::kChunk, cc = i % Tl::kChunk;
       const int64_t c = c0 + cc;
       const int j = j0 + vv;
-      const bool in = j < k && c < ncon;
+      const bool in = j < k && c < cend;
       Xh[cc][vv] = in ? xh[(int64_t)j * ldx + c] : 0.f;
       if constexpr (!FAST) Xl[cc][vv] = in ? xl[(int64_t)j * ldx + c] : 0.f;
     }
@@ -298,10 +303,42 @@ __global__ void __launch_bounds__(kAThreads) k_acc_gemm_narrow(const T *__restri
 #pragma unroll
     for (int p = 0; p < kATP; ++p) {
       const int j = j0 + tv + 2 * p;
-      if (j < k) out[(int64_t)j * ldo + o] = ((double)hi[r][p].x + (double)lo[r][p].x) * scale;
-      if (j + 1 < k) out[(int64_t)(j + 1) * ldo + o] = ((double)hi[r][p].y + (double)lo[r][p].y) * scale;
+      const double v0 = (double)hi[r][p].x + (double)lo[r][p].x, v1 = (double)hi[r][p].y + (double)lo[r][p].y;
+      if (part) {
+        double *pz = part + (int64_t)blockIdx.z * k * ldo;
+        if (j < k) pz[(int64_t)j * ldo + o] = v0;
+        if (j + 1 < k) pz[(int64_t)(j + 1) * ldo + o] = v1;
+      } else {
+        if (j < k) out[(int64_t)j * ldo + o] = v0 * scale;
+        if (j + 1 < k) out[(int64_t)(j + 1) * ldo + o] = v1 * scale;
+      }
     }
   }
+}
+
+// out[j * ldo + o] = scale * sum_{z < Z} part[(z * k + j) * ldo + o], z ascending (o < nout, j < k)
+__global__ void k_acc_reduce(const double *__restrict__ part, int Z, int k, int64_t nout, int64_t ldo, double scale,
+                             double *__restrict__ out) {
+  const int64_t total = nout * (int64_t)k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / nout, o = t % nout;
+    double a = 0.0;
+    for (int z = 0; z < Z; ++z) a += part[((int64_t)z * k + j) * ldo + o];
+    out[j * ldo + o] = a * scale;
+  }
+}
+
+// contraction slices of a narrow-tile launch: enough CTAs for about 1024 in flight, each slice at
+// least 8 chunks, at most 64 slices
+template <int VEC>
+int narrow_splits(int64_t nout, int64_t ncon, int k) {
+  using Tl = NarrowTile<VEC>;
+  const int64_t ctas = ((nout + Tl::kOut - 1) / Tl::kOut) * ((k + VEC - 1) / VEC);
+  int64_t z = (1024 + ctas - 1) / ctas;
+  const int64_t zmax = (ncon + 8 * Tl::kChunk - 1) / (8 * Tl::kChunk);
+  if (z > zmax) z = zmax;
+  if (z > 64) z = 64;
+  return z < 1 ? 1 : (int)z;
 }
 
 // x = hi + lo (two f32), the f64 vectors of a block (count entries)
@@ -338,30 +375,39 @@ __global__ void __launch_bounds__(256) k_resid_norm(const double *__restrict__ Y
 
 template <typename T, bool FAST, int VEC>
 cudaError_t launch_narrow(const Op &A, bool trans, const float *xh, const float *xl, int64_t ldx, int k, double *out,
-                          int64_t ldo, cudaStream_t s) {
-  const int64_t nout = trans ? A.n : A.m;
-  constexpr int kOut = NarrowTile<VEC>::kOut;
-  dim3 grid((unsigned)((nout + kOut - 1) / kOut), (unsigned)((k + VEC - 1) / VEC));
+                          int64_t ldo, cudaStream_t s, double *npart) {
+  using Tl = NarrowTile<VEC>;
+  const int64_t nout = trans ? A.n : A.m, ncon = trans ? A.m : A.n;
+  const int Z = npart ? narrow_splits<VEC>(nout, ncon, k) : 1;
+  int64_t cspan = (ncon + Z - 1) / Z;
+  cspan = (cspan + Tl::kChunk - 1) / Tl::kChunk * Tl::kChunk;
+  double *part = Z > 1 ? npart : nullptr;
+  dim3 grid((unsigned)((nout + Tl::kOut - 1) / Tl::kOut), (unsigned)((k + VEC - 1) / VEC), (unsigned)Z);
   if (trans)
     GK_LAUNCH(k_acc_gemm_narrow<T, true, FAST, VEC><<<grid, kAThreads, 0, s>>>(
-        (const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx, k, out, ldo));
+        (const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx, k, out, ldo, cspan, part));
   else
     GK_LAUNCH(k_acc_gemm_narrow<T, false, FAST, VEC><<<grid, kAThreads, 0, s>>>(
-        (const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx, k, out, ldo));
+        (const T *)A.vals, A.m, A.n, A.ld, A.scale, xh, xl, ldx, k, out, ldo, cspan, part));
+  if (part) {
+    int64_t b = (nout * k + 255) / 256;
+    if (b > 4096) b = 4096;
+    GK_LAUNCH(k_acc_reduce<<<(int)b, 256, 0, s>>>(part, Z, k, nout, ldo, A.scale, out));
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_acc(const Op &A, bool trans, const float *xh, const float *xl, int64_t ldx, int k, double *out,
-                       int64_t ldo, cudaStream_t s, bool fast, bool narrow) {
+                       int64_t ldo, cudaStream_t s, bool fast, bool narrow, double *npart) {
   const int64_t nout = trans ? A.n : A.m;
   dim3 grid((unsigned)((nout + kAOut - 1) / kAOut), (unsigned)((k + kAVec - 1) / kAVec));
   if (narrow && k <= 8)
-    return fast ? launch_narrow<T, true, 8>(A, trans, xh, xl, ldx, k, out, ldo, s)
-                : launch_narrow<T, false, 8>(A, trans, xh, xl, ldx, k, out, ldo, s);
+    return fast ? launch_narrow<T, true, 8>(A, trans, xh, xl, ldx, k, out, ldo, s, npart)
+                : launch_narrow<T, false, 8>(A, trans, xh, xl, ldx, k, out, ldo, s, npart);
   if (narrow && k <= 16)
-    return fast ? launch_narrow<T, true, 16>(A, trans, xh, xl, ldx, k, out, ldo, s)
-                : launch_narrow<T, false, 16>(A, trans, xh, xl, ldx, k, out, ldo, s);
+    return fast ? launch_narrow<T, true, 16>(A, trans, xh, xl, ldx, k, out, ldo, s, npart)
+                : launch_narrow<T, false, 16>(A, trans, xh, xl, ldx, k, out, ldo, s, npart);
   if (fast) {
     if (trans)
       GK_LAUNCH(k_acc_gemm<T, true, true><<<grid, kAThreads, 0, s>>>((const T *)A.vals, A.m, A.n, A.ld, A.scale, xh,
@@ -389,8 +435,20 @@ size_t accurate_floats(const Op &A, int k) {
   return 2 * (size_t)len * (size_t)k;
 }
 
+size_t accurate_narrow_doubles(const Op &A, int k) {
+  if (k < 1 || k > 16) return 0;
+  size_t need = 0;
+  for (int t = 0; t < 2; ++t) {
+    const int64_t nout = t ? A.n : A.m, ncon = t ? A.m : A.n;
+    const int z = k <= 8 ? narrow_splits<8>(nout, ncon, k) : narrow_splits<16>(nout, ncon, k);
+    const size_t d = z > 1 ? (size_t)z * (size_t)k * (size_t)nout : 0;
+    if (d > need) need = d;
+  }
+  return need;
+}
+
 cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, double *out, float *split,
-                              cudaStream_t s, bool fast, bool narrow) {
+                              cudaStream_t s, bool fast, bool narrow, double *npart) {
   const int64_t len = trans ? A.m : A.n;  // length of the input vectors
   const int64_t cnt = len * (int64_t)k;
   float *xh = split, *xl = split + cnt;
@@ -401,9 +459,9 @@ cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, d
   if (e != cudaSuccess) return e;
   const int64_t ldo = trans ? A.n : A.m;
   switch (A.dtype) {
-    case GK_F32: return launch_acc<float>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow);
-    case GK_BF16: return launch_acc<__nv_bfloat16>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow);
-    case GK_F16: return launch_acc<__half>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow);
+    case GK_F32: return launch_acc<float>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow, npart);
+    case GK_BF16: return launch_acc<__nv_bfloat16>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow, npart);
+    case GK_F16: return launch_acc<__half>(A, trans, xh, xl, len, k, out, ldo, s, fast, narrow, npart);
     default: return cudaErrorNotSupported;
   }
 }

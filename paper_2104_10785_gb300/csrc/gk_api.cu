@@ -1132,6 +1132,7 @@ struct BlockBufs {
   double *Q, *P, *W, *w, *Xc, *part, *h, *dpart, *raw, *Bf, *Bm, *Yw, *X, *Y, *sigma, *nrm, *q0;
   float *x32, *split;
   float2 *Qs, *Ps, *ws2;
+  double *npart;                 // the narrow block products' contraction-slice partials
   double *gW, *gC, *gH, *gpart;  // block Gram-Schmidt: projected block, Q H, H, Q^T X partials
   float2 *gWs, *gHs;             // and the double-f32 copies of the source block and of H
   int *pos, *sweeps, *rank;
@@ -1175,6 +1176,8 @@ size_t block_layout(const gk_matrix *A, int s, int64_t kb, const Dev &d, const O
   b->sweeps = cv.take<int>(1);
   b->rank = cv.take<int>(1);
   b->split = b->acc ? cv.take<float>(accurate_floats(*op, s)) : nullptr;
+  const size_t nparts = b->acc ? accurate_narrow_doubles(*op, s) : 0;
+  b->npart = nparts ? cv.take<double>(nparts) : nullptr;
   b->q0 = cv.take<double>((size_t)m * s);  // staging of a host start block
   b->Qs = b->df ? cv.take<float2>((size_t)ldu * cols) : nullptr;
   b->Ps = b->df ? cv.take<float2>((size_t)ldv * cols) : nullptr;
@@ -1214,7 +1217,7 @@ int block_product(const Op &op, BlockBufs &b, bool trans, const double *src, int
   if (b.acc) {  // one pass over A for the whole block, products exact to ~2^-47
     GK_CUDA(cudaMemcpy2DAsync(b.Xc, sizeof(double) * lin, src, sizeof(double) * ldsrc, sizeof(double) * lin, s,
                               cudaMemcpyDeviceToDevice, st));
-    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st, b.f32, true));
+    GK_CUDA(accurate_products(op, trans, b.Xc, s, b.W, b.split, st, b.f32, true, b.npart));
     return GK_OK;
   }
   for (int c = 0; c < s; ++c) {

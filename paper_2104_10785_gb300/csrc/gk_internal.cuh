@@ -154,9 +154,11 @@ bool accurate_ok(const Op &A);
 size_t accurate_floats(const Op &A, int k);
 // fast = true: f32 products (x rounded to f32, 16- or 32-term f32 chunk sums combined in
 // double-f32), the precision of matvec, at about a tenth of the arithmetic.  narrow = true (the
-// block calls): blocks of up to 8 or 16 vectors take tiles of that width instead of 32
+// block calls): blocks of up to 8 or 16 vectors take tiles of that width instead of 32, the
+// contraction split over slices when npart (accurate_narrow_doubles() doubles) is given
+size_t accurate_narrow_doubles(const Op &A, int k);
 cudaError_t accurate_products(const Op &A, bool trans, const double *X, int k, double *out, float *split,
-                              cudaStream_t s, bool fast = false, bool narrow = false);
+                              cudaStream_t s, bool fast = false, bool narrow = false, double *npart = nullptr);
 // res[j] = || Y[:, j] - S[j] W[:, j] ||, columns of length len (ld = len)
 cudaError_t resid_norms(const double *Y, const double *W, const double *S, int64_t len, int k, double *res,
                         cudaStream_t s);
