@@ -94,10 +94,10 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
                               double-f32 arithmetic on the FP32 pipes (exact to ~2^-46 of sum |q x|)
                               instead of f64 products.  Experimental: the product code is tested on the
                               host; the kernel has not yet run on a GPU. */
-#define GK_FLAG_BLOCK_F32 512 /* gk_block_numrank on a dense f32/bf16/f16 operator: the block products in f32
-                              (x rounded to f32, 32-term f32 sums combined in double-f32: the precision
-                              of gk_matvec) instead of double-f32, about a tenth of the arithmetic per
-                              product.  Experimental: not yet run on a GPU. */
+#define GK_FLAG_BLOCK_F32 512 /* gk_block_numrank, gk_block_fsvd on a dense f32/bf16/f16 operator: the block
+                              products in f32 (x rounded to f32, 16- or 32-term f32 sums combined in
+                              double-f32: the precision of gk_matvec) instead of double-f32, about a
+                              tenth of the arithmetic per product.  Experimental: not yet run on a GPU. */
 #define GK_FLAG_BLOCK_GS 1024 /* gk_block_numrank, gk_block_fsvd (with the double-f32 basis copies, i.e.
                               without GK_FLAG_ORTH_F64): each block orthogonalized against the earlier
                               basis as a block (reorthogonalized block classical Gram-Schmidt: the block
