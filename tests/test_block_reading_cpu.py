@@ -267,12 +267,13 @@ def test_blocks_past_the_left_space_are_zero(m, n, s):
     blocks fill min(m, n); the oracle (Householder QR of the reorthogonalized block) agrees."""
     A = np.random.default_rng(m * n).standard_normal((m, n))
     Q0 = np.random.default_rng(s).standard_normal((m, s))
-    r, sig, k, _ = column_block_gk(A, Q0, 1e-8, 0)
-    assert k * s == min(m, n) and r == min(m, n)
-    np.testing.assert_allclose(sig, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
     r_or, sig_or, k_or = bgk.block_numrank(A, Q0, eps=1e-8)
-    assert (r_or, k_or) == (r, k)
-    np.testing.assert_allclose(sig, sig_or[: k * s], rtol=1e-12)
+    for gs in (False, True):  # the column-wise flow and the block Gram-Schmidt
+        r, sig, k, _ = column_block_gk(A, Q0, 1e-8, 0, block_gs=gs)
+        assert k * s == min(m, n) and r == min(m, n)
+        np.testing.assert_allclose(sig, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
+        assert (r_or, k_or) == (r, k)
+        np.testing.assert_allclose(sig, sig_or[: k * s], rtol=1e-12)
 
 
 @pytest.mark.parametrize("noise,eps,s", [(1e-12, 1e-14, 4), (1e-12, 1e-14, 8), (1e-11, 1e-13, 8)])
