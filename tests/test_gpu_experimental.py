@@ -10,10 +10,18 @@ Skipped unless GK_EXPERIMENTAL=1: each kernel's host-testable part is covered by
   * GK_FLAG_SKETCH_TC (k_sketch_tc): the sketch on tcgen05 against mma.sync on the same bf16
     operator: both accumulate bf16 products in f32 in the tensor pipe, in different orders, so
     the features (logs of the sketch's singular values) agree to ~1e-5; 1e-4 is the bound;
-  * GK_FLAG_BLOCK_F32 (k_acc_gemm_narrow for blocks of up to 16 vectors, k_acc_gemm's FAST
-    instantiation above): the block rank with f32 block products against the oracle: the rank
-    exactly, sigma(B) above the cut within 1e-5 relative (f32 products carry ~2^-24 (34) sum |a x|
-    per entry)."""
+  * GK_FLAG_BLOCK_F32 (k_acc_gemm_narrow for blocks of up to 16 vectors, its contraction split
+    over slices summed by k_acc_reduce; k_acc_gemm's FAST instantiation above): the block rank
+    with f32 block products against the oracle: the rank exactly, sigma(B) above the cut within
+    1e-5 relative (f32 products carry ~2^-24 (34) sum |a x| per entry);
+  * gk_block_fsvd against oracle/block_gk.block_fsvd, and with GK_FLAG_RITZ_DF (U, V from the
+    double-f32 basis copies) against itself;
+  * GK_FLAG_BLOCK_GS (the block Gram-Schmidt: k_bgs_dots, k_bgs_sub, k_ritz_df): the block rank
+    against the oracle (rank-deficient blocks, the largest block, long left vectors, a full
+    space, CSR) and gk_block_fsvd against the column-wise flow;
+  * GK_FLAG_PROFILE in the block calls: phase times present, results unchanged.
+The default block path (k_acc_gemm_narrow in double-f32, the block judge) is in
+tests/test_gpu_start_block.py, gated the same way."""
 import os
 
 import numpy as np
